@@ -1,0 +1,216 @@
+/*
+ * pic.h — C ABI of the GB300 (sm_103a) hot path of the implicit, energy- and
+ * charge-conserving electromagnetic PIC/MCC method of Eremin et al.,
+ * arXiv:2212.08836 ("Modeling of VHF large-electrode CCPs with a fully
+ * electromagnetic PIC code").
+ *
+ * One time step = Picard iteration of [CN particle push with cell-crossing
+ * sub-steps + charge-conserving deposit (Sec. 2.1, Eqs. 3-4)] and [implicit
+ * CN Maxwell solve for H_theta (Eqs. 1-2)], a commit push, null-collision MCC
+ * (Sec. 2.1) and a per-step sort of the particle store by cell.
+ *
+ * Conventions shared by every entry point
+ *   - Grid: nr x nz uniform cells on r in [0,R], z in [0,L]; z fastest.
+ *       Er edge (i+1/2, j)  -> er[i*(nz+1)+j], i < nr, j <= nz
+ *       Ez edge (i, j+1/2)  -> ez[i*nz+j],     i <= nr, j < nz
+ *       H_theta (i+1/2,j+1/2)-> h[i*nz+j]
+ *       node (i, j)         -> q[i*(nz+1)+j]
+ *     "Current" arrays ir/iz hold the charge [C] that crossed the dual face
+ *     of each edge during one step (flux form of Eq. 3).
+ *   - Particles: species 0 = electrons, 1 = Ar+; structure of arrays
+ *     cell (int32, ic*nz+jc, -1 = absorbed), a, b (offsets in [0,1] inside
+ *     the cell), vr, vt, vz [m/s], w (physical particles per macro-particle),
+ *     id (uint32, RNG counter word).  Stored sorted by cell.
+ *   - Memory: the library never allocates device memory.  The caller passes
+ *     one device workspace (size from pic_workspace_size) that it owns and
+ *     frees after pic_destroy.  Pointers named *_dev are device pointers,
+ *     everything else is host memory.
+ *   - Streams: all work is enqueued on the cudaStream_t given to pic_init
+ *     (passed as void*).  Calls that return host values synchronise it.
+ *   - Errors: every int-returning call returns PIC_OK (0) or a negative
+ *     PIC_E_* code; it never aborts and never prints.  After an error other
+ *     than PIC_E_CUDA the context stays usable.
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIC_OK 0
+#define PIC_E_CONFIG -1    /* invalid configuration or argument */
+#define PIC_E_CUDA -2      /* a CUDA call failed (context may be unusable) */
+#define PIC_E_NOCONV -3    /* Picard iteration did not reach picard_tol in picard_max */
+#define PIC_E_SUBSTEP -4   /* a particle needed more than 64 sub-steps in one pass */
+#define PIC_E_CAPACITY -5  /* ionization would exceed the particle capacity */
+#define PIC_E_NAN -6       /* non-finite field or residual */
+#define PIC_E_STATE -7     /* state arrays inconsistent (counts beyond capacity) */
+#define PIC_E_WORKSPACE -8 /* workspace missing, too small or misaligned */
+
+#define PIC_FP64 0         /* plain method: FP64 particles, push and deposit */
+
+typedef struct pic_ctx pic_ctx; /* opaque; host memory owned by the library */
+
+/* Problem definition, copied at pic_init.  Zero eps/mu select vacuum values. */
+typedef struct pic_config {
+  int nr, nz;                 /* cells in r and z (nr, nz >= 2) */
+  double R, L;                /* electrode radius and gap [m] */
+  double dt;                  /* time step [s] */
+  double freq, volt;          /* V(t) = volt*sin(2*pi*freq*t) on the powered electrode z = 0 */
+  double gas_pressure;        /* argon pressure [Pa] (neutral density p/(k T)) */
+  double gas_temp;            /* neutral temperature [K] */
+  double n0;                  /* initial plasma density [m^-3] */
+  double te_ev, ti_ev;        /* initial electron / ion temperatures [eV] */
+  long long np_init;          /* macro-particles per species loaded by pic_load_particles */
+  double capacity_factor;     /* capacity per species = ceil(capacity_factor * np_init) (>= 1) */
+  double picard_tol;          /* relative Picard tolerance on E (e.g. 1e-8) */
+  int picard_max;             /* maximum Picard iterations per step (e.g. 50) */
+  int mcc_on;                 /* 1: null-collision MCC after every step */
+  double bz;                  /* external uniform B_z [T]; 0 in production (Sec. 2.1) */
+  double eps, mu;             /* permittivity / permeability; 0 -> eps0 / mu0 */
+  unsigned long long seed;    /* RNG key word (Philox4x64-10) */
+  int precision;              /* PIC_FP64 */
+} pic_config;
+
+/* Per-step statistics (host struct). */
+typedef struct pic_step_stats {
+  int picard_iters;           /* iterations of the last step */
+  int converged;              /* 1 if the last step converged */
+  double last_res;            /* last Picard residual */
+  double src_energy;          /* energy delivered through the drive gap in the last step [J] */
+  double ke_lost;             /* kinetic energy of particles absorbed at walls [J] */
+  double de_coll;             /* kinetic-energy change from collisions [J] */
+  long long substep_err;      /* particles that hit the sub-step cap (commit pass) */
+  long long absorbed;         /* particles absorbed at walls (commit pass) */
+  long long substeps;         /* accepted sub-steps (commit pass) */
+  long long fallbacks;        /* trial halvings (commit pass) */
+  long long mcc[8];           /* cand_e, elastic, excitation, ionization, cand_i, cx, gmax overflow, capacity */
+  long long n[2];             /* macro-particles per species after the step */
+  long long pushes;           /* particle pushes performed by the step (all passes) */
+  long long launches;         /* kernels launched by the step */
+} pic_step_stats;
+
+/* Device pointers and sizes of the context's arrays (for parity tests,
+ * checkpoints and callers that fill state directly). */
+typedef struct pic_view {
+  int32_t *cell[2];
+  double *a[2], *b[2], *vr[2], *vt[2], *vz[2], *w[2];
+  uint32_t *id[2];
+  long long n[2], cap[2];
+  uint32_t next_id[2];
+  double *er, *ez, *h;        /* E^n, H^n */
+  long long step;             /* index n of the next step */
+} pic_view;
+
+/* Conservation diagnostics (row a9), host struct filled by pic_diag. */
+typedef struct pic_diag_out {
+  double kinetic[2];          /* sum 1/2 m w |v|^2 per species [J] */
+  double field;               /* discrete field energy over unknown edges and H cells [J] */
+  double charge[2];           /* sum q w per species [C] */
+  long long n[2];
+} pic_diag_out;
+
+/* Human-readable name of a status code (static string). */
+const char *pic_strerror(int code);
+
+/* Library build identifier (static string). */
+const char *pic_version(void);
+
+/* Bytes of device workspace pic_init needs for cfg (256-byte aligned base).
+ * Errors: PIC_E_CONFIG. */
+int pic_workspace_size(const pic_config *cfg, size_t *bytes);
+
+/* Create a context on the current CUDA device over a caller-owned device
+ * workspace (workspace_dev, workspace_bytes >= pic_workspace_size).  Builds
+ * the mesh metrics and the factorised field operator of Eq. 2 (host set-up,
+ * then copied into the workspace on `stream`).  Fields start at zero and no
+ * particles are loaded.  Errors: PIC_E_CONFIG, PIC_E_WORKSPACE, PIC_E_CUDA. */
+int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes, void *stream,
+             pic_ctx **out);
+
+/* Release the host context.  The workspace stays the caller's. */
+void pic_destroy(pic_ctx *ctx);
+
+/* Row a1 (Sec. 2.1: weights proportional to r*J_r): load np_init electron /
+ * Ar+ pairs at identical positions, uniform in the logical coordinates,
+ * Maxwellian velocities, on the GPU; then sort by cell.  E = H = 0 is then
+ * Gauss-consistent.  Errors: PIC_E_CAPACITY, PIC_E_CUDA. */
+int pic_load_particles(pic_ctx *ctx);
+
+/* Advance nsteps full time steps (rows a2-a8; a9 counters in stats).
+ * stats may be NULL.  On PIC_E_NOCONV the context holds step n unchanged.
+ * Synchronises the stream (Picard convergence test).
+ * Errors: PIC_E_NOCONV, PIC_E_SUBSTEP, PIC_E_CAPACITY, PIC_E_NAN, PIC_E_CUDA. */
+int pic_step(pic_ctx *ctx, int nsteps, pic_step_stats *stats);
+
+/* Rows a2+a3 (a6 when write != 0), Eq. 4 with cell-crossing sub-steps and
+ * the deposit of Eq. 3: one pass over both species with the half-step field
+ * er_half_dev / ez_half_dev (layout above).  Adds the crossed charges into
+ * ir_dev / iz_dev (caller zeroes them).  write = 0 leaves the particles
+ * untouched; write = 1 stores state n+1 (cell -1 for absorbed particles).
+ * counters_dev (nullable, 4 x uint64): substep errors, absorbed, substeps,
+ * fallbacks; ke_lost_dev (nullable, double): absorbed kinetic energy.
+ * Asynchronous.  Errors: PIC_E_CONFIG, PIC_E_CUDA. */
+int pic_push_deposit(pic_ctx *ctx, const double *er_half_dev, const double *ez_half_dev,
+                     double *ir_dev, double *iz_dev, int write,
+                     unsigned long long *counters_dev, double *ke_lost_dev);
+
+/* Row a4, Eqs. 1-2 in CN form: one implicit field solve.  Inputs E^n, H^n,
+ * crossed charges, drive voltages V^n (v0) and V^{n+1} (v1); outputs E^{n+1},
+ * H^{n+1} and, if src_dev != NULL, the energy delivered through the drive
+ * gap (double).  All arrays are device arrays in the layout above; outputs
+ * must not alias inputs.  Asynchronous.  Errors: PIC_E_CONFIG, PIC_E_CUDA. */
+int pic_field_solve(pic_ctx *ctx, const double *er0_dev, const double *ez0_dev,
+                    const double *h0_dev, const double *ir_dev, const double *iz_dev, double v0,
+                    double v1, double *er1_dev, double *ez1_dev, double *h1_dev, double *src_dev);
+
+/* Row a7 (Sec. 2.1, null collision after Mertmann et al. 2011): one MCC pass
+ * over the context's particles for step index `step`, appending ionization
+ * pairs in parent order.  counts (host, nullable, 8 entries as in
+ * pic_step_stats.mcc); de_coll (host, nullable).  Synchronises.
+ * Errors: PIC_E_CAPACITY, PIC_E_CUDA. */
+int pic_mcc(pic_ctx *ctx, unsigned long long step, long long *counts, double *de_coll);
+
+/* Row a8: counting sort of both species by cell, dropping absorbed
+ * particles (cell < 0).  Synchronises (new counts).  Errors: PIC_E_CUDA. */
+int pic_sort(pic_ctx *ctx);
+
+/* Row a9: FP64 kinetic and field energies and charges.  Synchronises. */
+int pic_diag(pic_ctx *ctx, pic_diag_out *out);
+
+/* Node charge by S1 x S1 weighting of both species, added into q_dev
+ * ((nr+1)*(nz+1) doubles, caller zeroes).  Asynchronous. */
+int pic_node_charge(pic_ctx *ctx, double *q_dev);
+
+/* Device pointers, counts and capacities of the context's state. */
+int pic_get_view(pic_ctx *ctx, pic_view *out);
+
+/* Set particle counts / next ids / step index after the caller wrote state
+ * through pic_get_view.  Errors: PIC_E_STATE (count beyond capacity). */
+int pic_set_counts(pic_ctx *ctx, long long ne, long long ni, uint32_t next_id_e,
+                   uint32_t next_id_i, long long step);
+
+/* Maximum collision frequencies used by the MCC (host values): electron
+ * nu_max [1/s], ion g_max [m/s], null-collision probabilities. */
+int pic_mcc_constants(pic_ctx *ctx, double *numax_e, double *gmax, double *pnull_e,
+                      double *pnull_i);
+
+/* Opt-in timing of the push+deposit launches (rows a2/a3/a6): enable != 0
+ * creates CUDA events and records a pair around every push pass on the
+ * context stream; totals are reset by every call.  Synchronises.
+ * Errors: PIC_E_CUDA. */
+int pic_profile(pic_ctx *ctx, int enable);
+
+/* Accumulated device time [ms] of the timed push passes and the number of
+ * push kernel launches they contained.  Synchronises.  Errors: PIC_E_CUDA. */
+int pic_profile_read(pic_ctx *ctx, double *push_ms, long long *push_launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIC_H */

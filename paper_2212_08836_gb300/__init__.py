@@ -1,0 +1,310 @@
+"""GB300 (sm_103a) hot path of the implicit energy- and charge-conserving
+EM PIC/MCC method of arXiv:2212.08836 — Python binding.
+
+Argument marshalling only: every step of the method runs in the CUDA kernels
+of ``libpic.so`` (C ABI in ``include/pic.h``).  PyTorch provides the device
+workspace and the stream.  There is no CPU fallback: importing the binding
+without the compiled library raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpic.so")
+
+PIC_OK = 0
+PIC_E_CONFIG = -1
+PIC_E_CUDA = -2
+PIC_E_NOCONV = -3
+PIC_E_SUBSTEP = -4
+PIC_E_CAPACITY = -5
+PIC_E_NAN = -6
+PIC_E_STATE = -7
+PIC_E_WORKSPACE = -8
+PIC_FP64 = 0
+
+_P = C.c_void_p
+_D = C.c_double
+_I = C.c_int
+_LL = C.c_longlong
+
+
+class Config(C.Structure):
+    _fields_ = [("nr", _I), ("nz", _I), ("R", _D), ("L", _D), ("dt", _D), ("freq", _D),
+                ("volt", _D), ("gas_pressure", _D), ("gas_temp", _D), ("n0", _D),
+                ("te_ev", _D), ("ti_ev", _D), ("np_init", _LL), ("capacity_factor", _D),
+                ("picard_tol", _D), ("picard_max", _I), ("mcc_on", _I), ("bz", _D),
+                ("eps", _D), ("mu", _D), ("seed", C.c_ulonglong), ("precision", _I)]
+
+
+class StepStats(C.Structure):
+    _fields_ = [("picard_iters", _I), ("converged", _I), ("last_res", _D), ("src_energy", _D),
+                ("ke_lost", _D), ("de_coll", _D), ("substep_err", _LL), ("absorbed", _LL),
+                ("substeps", _LL), ("fallbacks", _LL), ("mcc", _LL * 8), ("n", _LL * 2),
+                ("pushes", _LL), ("launches", _LL)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("mcc", "n")}
+        d["mcc"] = list(self.mcc)
+        d["n"] = list(self.n)
+        return d
+
+
+class View(C.Structure):
+    _fields_ = [("cell", _P * 2), ("a", _P * 2), ("b", _P * 2), ("vr", _P * 2), ("vt", _P * 2),
+                ("vz", _P * 2), ("w", _P * 2), ("id", _P * 2), ("n", _LL * 2), ("cap", _LL * 2),
+                ("next_id", C.c_uint32 * 2), ("er", _P), ("ez", _P), ("h", _P), ("step", _LL)]
+
+
+class DiagOut(C.Structure):
+    _fields_ = [("kinetic", _D * 2), ("field", _D), ("charge", _D * 2), ("n", _LL * 2)]
+
+
+def _load_lib():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libpic.so is not built (run __graft_entry__.build() or "
+                          "python paper_2212_08836_gb300/build.py); there is no CPU fallback")
+    L = C.CDLL(LIB_PATH)
+    L.pic_strerror.restype = C.c_char_p
+    L.pic_strerror.argtypes = [_I]
+    L.pic_version.restype = C.c_char_p
+    L.pic_workspace_size.argtypes = [C.POINTER(Config), C.POINTER(C.c_size_t)]
+    L.pic_init.argtypes = [C.POINTER(Config), _P, C.c_size_t, _P, C.POINTER(_P)]
+    L.pic_destroy.argtypes = [_P]
+    L.pic_destroy.restype = None
+    L.pic_load_particles.argtypes = [_P]
+    L.pic_step.argtypes = [_P, _I, C.POINTER(StepStats)]
+    L.pic_push_deposit.argtypes = [_P, _P, _P, _P, _P, _I, _P, _P]
+    L.pic_field_solve.argtypes = [_P, _P, _P, _P, _P, _P, _D, _D, _P, _P, _P, _P]
+    L.pic_mcc.argtypes = [_P, C.c_ulonglong, _P, _P]
+    L.pic_sort.argtypes = [_P]
+    L.pic_diag.argtypes = [_P, C.POINTER(DiagOut)]
+    L.pic_node_charge.argtypes = [_P, _P]
+    L.pic_get_view.argtypes = [_P, C.POINTER(View)]
+    L.pic_set_counts.argtypes = [_P, _LL, _LL, C.c_uint32, C.c_uint32, _LL]
+    L.pic_mcc_constants.argtypes = [_P, _P, _P, _P, _P]
+    L.pic_profile.argtypes = [_P, _I]
+    L.pic_profile_read.argtypes = [_P, _P, _P]
+    return L
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = _load_lib()
+    return _lib
+
+
+class PicError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__("%s: %s (%d)" % (what, lib().pic_strerror(code).decode(), code))
+
+
+def _check(code, what):
+    if code != PIC_OK:
+        raise PicError(code, what)
+    return code
+
+
+# ----------------------------------------------------------- named workloads
+def small_reactor(**kw):
+    """32(r) x 64(z), R = 0.1 m, L = 0.03 m, argon 2 Pa / 300 K, 60 MHz 100 V,
+    40k macro-particles per species at 1e15 m^-3, Te = 3 eV, Ti = 0.026 eV,
+    dt = 1/(200 f), Picard tolerance 1e-8, seed 0."""
+    f = 60e6
+    cfg = dict(nr=32, nz=64, R=0.1, L=0.03, dt=1.0 / (200 * f), freq=f, volt=100.0,
+               gas_pressure=2.0, gas_temp=300.0, n0=1e15, te_ev=3.0, ti_ev=0.026,
+               np_init=40000, capacity_factor=1.5, picard_tol=1e-8, picard_max=50, mcc_on=1,
+               bz=0.0, eps=0.0, mu=0.0, seed=0, precision=PIC_FP64)
+    cfg.update(kw)
+    return cfg
+
+
+def large_reactor(**kw):
+    """256(r) x 384(z), R = 0.3 m, L = 0.03 m, argon 2 Pa / 300 K, 100 MHz 200 V,
+    16M macro-particles per species at 1e15 m^-3 (Te = 3 eV, Ti = 0.026 eV),
+    dt = 1/(400 f), Picard tolerance 1e-8, seed 1."""
+    f = 100e6
+    cfg = dict(nr=256, nz=384, R=0.3, L=0.03, dt=1.0 / (400 * f), freq=f, volt=200.0,
+               gas_pressure=2.0, gas_temp=300.0, n0=1e15, te_ev=3.0, ti_ev=0.026,
+               np_init=16 * 1024 * 1024, capacity_factor=1.25, picard_tol=1e-8, picard_max=50,
+               mcc_on=1, bz=0.0, eps=0.0, mu=0.0, seed=1, precision=PIC_FP64)
+    cfg.update(kw)
+    return cfg
+
+
+FIELDS = ("cell", "a", "b", "vr", "vt", "vz", "w", "id")
+
+
+class Pic:
+    """One discharge on one GPU.  Owns a torch uint8 workspace on ``device``."""
+
+    def __init__(self, cfg: dict, device="cuda:0", stream=None):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device(device)
+        self.cfg = dict(cfg)
+        self._c = Config(**self.cfg)
+        nbytes = C.c_size_t(0)
+        _check(lib().pic_workspace_size(C.byref(self._c), C.byref(nbytes)), "pic_workspace_size")
+        self.ws_bytes = int(nbytes.value)
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = _P()
+        _check(lib().pic_init(C.byref(self._c), self.ws.data_ptr(), self.ws_bytes,
+                              self.stream.cuda_stream, C.byref(h)), "pic_init")
+        self._h = h
+        self.nr, self.nz = self.cfg["nr"], self.cfg["nz"]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pic_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ methods
+    def load_particles(self):
+        _check(lib().pic_load_particles(self._h), "pic_load_particles")
+
+    def step(self, n=1, check=True):
+        st = StepStats()
+        rc = lib().pic_step(self._h, int(n), C.byref(st))
+        if check:
+            _check(rc, "pic_step")
+        return rc, st.as_dict()
+
+    def push_deposit(self, er_half, ez_half, ir, iz, write=False, counters=None, ke_lost=None):
+        _check(lib().pic_push_deposit(self._h, er_half.data_ptr(), ez_half.data_ptr(),
+                                      ir.data_ptr(), iz.data_ptr(), 1 if write else 0,
+                                      counters.data_ptr() if counters is not None else None,
+                                      ke_lost.data_ptr() if ke_lost is not None else None),
+               "pic_push_deposit")
+
+    def field_solve(self, er0, ez0, h0, ir, iz, v0, v1, er1, ez1, h1, src=None):
+        _check(lib().pic_field_solve(self._h, er0.data_ptr(), ez0.data_ptr(), h0.data_ptr(),
+                                     ir.data_ptr(), iz.data_ptr(), float(v0), float(v1),
+                                     er1.data_ptr(), ez1.data_ptr(), h1.data_ptr(),
+                                     src.data_ptr() if src is not None else None),
+               "pic_field_solve")
+
+    def mcc(self, step):
+        counts = (_LL * 8)()
+        de = _D(0.0)
+        rc = lib().pic_mcc(self._h, int(step), C.addressof(counts), C.addressof(de))
+        return rc, list(counts), de.value
+
+    def sort(self):
+        _check(lib().pic_sort(self._h), "pic_sort")
+
+    def diag(self):
+        d = DiagOut()
+        _check(lib().pic_diag(self._h, C.byref(d)), "pic_diag")
+        return {"kinetic": list(d.kinetic), "field": d.field, "charge": list(d.charge),
+                "n": list(d.n)}
+
+    def node_charge(self):
+        t = self.torch
+        q = t.zeros((self.nr + 1) * (self.nz + 1), dtype=t.float64, device=self.device)
+        _check(lib().pic_node_charge(self._h, q.data_ptr()), "pic_node_charge")
+        return q
+
+    def mcc_constants(self):
+        v = [_D(0.0) for _ in range(4)]
+        _check(lib().pic_mcc_constants(self._h, *[C.addressof(x) for x in v]), "pic_mcc_constants")
+        return tuple(x.value for x in v)
+
+    def profile(self, enable=True):
+        _check(lib().pic_profile(self._h, 1 if enable else 0), "pic_profile")
+
+    def profile_read(self):
+        ms = _D(0.0)
+        nl = _LL(0)
+        _check(lib().pic_profile_read(self._h, C.addressof(ms), C.addressof(nl)),
+               "pic_profile_read")
+        return ms.value, nl.value
+
+    # ---------------------------------------------------------- state views
+    def _raw_view(self):
+        v = View()
+        _check(lib().pic_get_view(self._h, C.byref(v)), "pic_get_view")
+        return v
+
+    def _tensor(self, ptr, count, dtype):
+        t = self.torch
+        itemsize = t.empty((), dtype=dtype).element_size()
+        off = ptr - self.ws.data_ptr()
+        assert 0 <= off and off + count * itemsize <= self.ws_bytes
+        return self.ws[off: off + count * itemsize].view(dtype)
+
+    def view(self):
+        """torch views (no copy) of the current particle arrays and fields."""
+        t = self.torch
+        v = self._raw_view()
+        out = {"n": list(v.n), "cap": list(v.cap), "next_id": list(v.next_id), "step": v.step,
+               "species": []}
+        dt = {"cell": t.int32, "id": t.int32}
+        for s in range(2):
+            out["species"].append({k: self._tensor(getattr(v, k)[s], v.cap[s],
+                                                   dt.get(k, t.float64)) for k in FIELDS})
+        nr, nz = self.nr, self.nz
+        out["er"] = self._tensor(v.er, nr * (nz + 1), t.float64)
+        out["ez"] = self._tensor(v.ez, (nr + 1) * nz, t.float64)
+        out["h"] = self._tensor(v.h, nr * nz, t.float64)
+        return out
+
+    def set_state(self, species, er=None, ez=None, h=None, next_ids=None, step=0):
+        """Copy host (numpy) species dicts and fields into the context."""
+        t = self.torch
+        v = self.view()
+        ns = []
+        for s, sp in enumerate(species):
+            n = len(sp["cell"])
+            if n > v["cap"][s]:
+                raise PicError(PIC_E_STATE, "set_state")
+            for k in FIELDS:
+                src = np.ascontiguousarray(sp[k])
+                if k == "id":
+                    src = src.astype(np.uint32).view(np.int32)
+                v["species"][s][k][:n].copy_(t.from_numpy(src))
+            ns.append(n)
+        for name, arr in (("er", er), ("ez", ez), ("h", h)):
+            if arr is not None:
+                v[name].copy_(t.from_numpy(np.ascontiguousarray(arr, dtype=np.float64)))
+        if next_ids is None:
+            next_ids = [int(np.max(sp["id"])) + 1 if len(sp["id"]) else 0 for sp in species]
+        self.torch.cuda.synchronize(self.device)
+        _check(lib().pic_set_counts(self._h, ns[0], ns[1], next_ids[0], next_ids[1], step),
+               "pic_set_counts")
+
+    def get_state(self, s):
+        v = self.view()
+        n = v["n"][s]
+        self.torch.cuda.synchronize(self.device)
+        out = {k: v["species"][s][k][:n].cpu().numpy().copy() for k in FIELDS}
+        out["id"] = out["id"].view(np.uint32)
+        return out
+
+    def fields(self):
+        v = self.view()
+        self.torch.cuda.synchronize(self.device)
+        return tuple(v[k].cpu().numpy().copy() for k in ("er", "ez", "h"))
+
+
+def drive_voltage(cfg, step):
+    t = step * cfg["dt"]
+    return cfg["volt"] * math.sin(6.283185307179586 * cfg["freq"] * t)

@@ -1,0 +1,249 @@
+// Row a4: implicit Crank-Nicolson Maxwell solve (Eqs. 1-2, TM: Er, Ez, H_theta;
+// H_theta is the primary unknown, Sec. 2.1), integral Yee form:
+//   Faraday: mu*Vh*(H1 - H0) = -dt * C^T L E_half
+//   Ampere:  eps*A*(E1 - E0) = dt * C H_half - dQ          (unknown edges)
+// Eliminating E gives (2 mu Vh + dt^2/2 C^T W C) H_half = rhs.  On the uniform
+// mesh with PEC plates (Er = 0 at z = 0, L) and the gap source on r = R, this
+// operator is exactly  diag_r(.) (x) T_z + R_r (x) I_z  with T_z the Neumann
+// Laplacian along z, so a DCT-II along z diagonalises it into nz independent
+// SPD tridiagonal systems along r.  Solve = DCT (FP64 GEMM), Thomas per mode,
+// inverse DCT; then H1 = 2 H_half - H0 and E1 explicitly from Ampere.
+#include "pic_internal.cuh"
+
+namespace pic {
+namespace {
+
+__device__ __forceinline__ double rhalf(double dr, int i) { return ((double)i + 0.5) * dr; }
+__device__ __forceinline__ double area_r(double dr, double dz, int i) {
+  return kTwoPi * rhalf(dr, i) * dz;
+}
+__device__ __forceinline__ double area_z(double dr, int i) {
+  if (i == 0) return kPi * (0.5 * dr) * (0.5 * dr);
+  return kTwoPi * ((double)i * dr) * dr;
+}
+
+__global__ void k_half(long long n1, long long n2, const double *er0, const double *ez0,
+                       const double *er1, const double *ez1, double *erh, double *ezh) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n1) erh[t] = 0.5 * (er0[t] + er1[t]);
+  else if (t < n1 + n2) {
+    long long u = t - n1;
+    ezh[u] = 0.5 * (ez0[u] + ez1[u]);
+  }
+}
+
+// rhs(i,j) = 2 mu Vh H0 - dt * C^T L Et   (Et = E0 - dQ/(2 eps A), or the prescribed half value)
+__global__ void k_rhs(FieldOp F, const double *er0, const double *ez0, const double *h0,
+                      const double *ir, const double *iz, double v0, double v1) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  int nr = F.nr, nz = F.nz, nz1 = nz + 1;
+  if (c >= nr * nz) return;
+  int i = c / nz, j = c - (c / nz) * nz;
+  double dr = F.dr, dz = F.dz, eps = F.eps;
+  double s = kTwoPi * rhalf(dr, i);
+  double ar = area_r(dr, dz, i);
+  double etb = 0.0, ett = 0.0;
+  if (j != 0) etb = er0[i * nz1 + j] - ir[i * nz1 + j] / (2.0 * eps * ar);
+  if (j + 1 != nz) ett = er0[i * nz1 + j + 1] - ir[i * nz1 + j + 1] / (2.0 * eps * ar);
+  double etl = ez0[i * nz + j] - iz[i * nz + j] / (2.0 * eps * area_z(dr, i));
+  double etr;
+  if (i + 1 == nr) etr = 0.5 * (v0 + v1) / F.L;
+  else etr = ez0[(i + 1) * nz + j] - iz[(i + 1) * nz + j] / (2.0 * eps * area_z(dr, i + 1));
+  double vh = kTwoPi * rhalf(dr, i) * dr * dz;
+  double curl = (-s) * dr * etb + s * dr * ett + s * dz * etl + (-s) * dz * etr;
+  F.rhs[c] = 2.0 * F.mu * vh * h0[c] - F.dt * curl;
+}
+
+// C[M x N] = A[M x K] * B[K x N], row-major FP64, 32x32 tile per block, 2x2 per thread
+constexpr int TM = 32, TK = 16;
+__global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, const double *__restrict__ A,
+                                              const double *__restrict__ B,
+                                              double *__restrict__ Cm) {
+  __shared__ double As[TK][TM + 1];
+  __shared__ double Bs[TK][TM + 1];
+  int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  int row0 = blockIdx.y * TM, col0 = blockIdx.x * TM;
+  double acc[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
+  for (int k0 = 0; k0 < K; k0 += TK) {
+    // load A tile (TM rows x TK cols) and B tile (TK rows x TM cols): 512 elements each
+    for (int e = threadIdx.x; e < TM * TK; e += 256) {
+      int r = e / TK, kk = e - (e / TK) * TK;
+      int gr = row0 + r, gk = k0 + kk;
+      As[kk][r] = (gr < M && gk < K) ? A[(long long)gr * K + gk] : 0.0;
+      int kb = e / TM, cc = e - (e / TM) * TM;
+      int gkb = k0 + kb, gc = col0 + cc;
+      Bs[kb][cc] = (gkb < K && gc < N) ? B[(long long)gkb * N + gc] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < TK; ++kk) {
+      double a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
+      double b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
+      acc[0][0] += a0 * b0;
+      acc[0][1] += a0 * b1;
+      acc[1][0] += a1 * b0;
+      acc[1][1] += a1 * b1;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int v = 0; v < 2; ++v) {
+      int gr = row0 + ty * 2 + u, gc = col0 + tx * 2 + v;
+      if (gr < M && gc < N) Cm[(long long)gr * N + gc] = acc[u][v];
+    }
+}
+
+// Thomas solve per DCT mode m along r; MB modes per block staged in shared memory
+__global__ void k_tridiag(FieldOp F, int mb) {
+  extern __shared__ double sm[];
+  int nr = F.nr, nz = F.nz;
+  int m0 = blockIdx.x * mb;
+  double *x = sm;                 // nr x mb
+  double *l = sm + nr * mb;       // nr x mb
+  double *ci = sm + 2 * nr * mb;  // nr x mb
+  for (int e = threadIdx.x; e < nr * mb; e += blockDim.x) {
+    int i = e / mb, k = e - (e / mb) * mb;
+    int m = m0 + k;
+    bool ok = m < nz;
+    x[e] = ok ? F.hat[i * nz + m] : 0.0;
+    l[e] = ok ? F.lfac[i * nz + m] : 0.0;
+    ci[e] = ok ? F.cinv[i * nz + m] : 0.0;
+  }
+  __syncthreads();
+  int k = threadIdx.x;
+  if (k < mb && m0 + k < nz) {
+    for (int i = 1; i < nr; ++i) x[i * mb + k] -= l[i * mb + k] * x[(i - 1) * mb + k];
+    x[(nr - 1) * mb + k] *= ci[(nr - 1) * mb + k];
+    for (int i = nr - 2; i >= 0; --i)
+      x[i * mb + k] = (x[i * mb + k] - F.eoff[i + 1] * x[(i + 1) * mb + k]) * ci[i * mb + k];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nr * mb; e += blockDim.x) {
+    int i = e / mb, kk = e - (e / mb) * mb;
+    int m = m0 + kk;
+    if (m < nz) F.hat[i * nz + m] = x[e];
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// H1 = 2 H_half - H0; E1 from Ampere; Picard norms and drive-gap energy
+__global__ void __launch_bounds__(256) k_update(FieldOp F, const double *er0, const double *ez0,
+                                                const double *h0, const double *ir,
+                                                const double *iz, double v0, double v1,
+                                                double *er1, double *ez1, double *h1,
+                                                const double *er_it, const double *ez_it,
+                                                DevCounters *cnt) {
+  int nr = F.nr, nz = F.nz, nz1 = nz + 1;
+  long long ner = (long long)nr * nz1, nez = (long long)(nr + 1) * nz, nh = (long long)nr * nz;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double dn = 0.0, nn = 0.0, src = 0.0;
+  const double *hh = F.hhalf;
+  double dr = F.dr, dz = F.dz, eps = F.eps, dt = F.dt;
+  if (t < nh) {
+    h1[t] = 2.0 * hh[t] - h0[t];
+  }
+  if (t < ner) {
+    int i = (int)(t / nz1), j = (int)(t - (t / nz1) * nz1);
+    if (j == 0 || j == nz) {
+      er1[t] = 0.0;
+    } else {
+      double s = kTwoPi * rhalf(dr, i);
+      double ch = -s * hh[i * nz + j] + s * hh[i * nz + j - 1];
+      double e1 = er0[t] + (dt * ch - ir[t]) / (eps * area_r(dr, dz, i));
+      er1[t] = e1;
+      if (er_it) {
+        double d = e1 - er_it[t];
+        dn += d * d;
+        nn += e1 * e1;
+      }
+    }
+  }
+  if (t < nez) {
+    int i = (int)(t / nz), j = (int)(t - (t / nz) * nz);
+    double ch = 0.0;
+    if (i <= nr - 1) ch += kTwoPi * rhalf(dr, i) * hh[i * nz + j];
+    if (i >= 1) ch += -kTwoPi * rhalf(dr, i - 1) * hh[(i - 1) * nz + j];
+    if (i == nr) {
+      ez1[t] = v1 / F.L;
+      double eh = 0.5 * (v0 + v1) / F.L;
+      src += eh * dz * (iz[t] - dt * ch);
+    } else {
+      double e1 = ez0[t] + (dt * ch - iz[t]) / (eps * area_z(dr, i));
+      ez1[t] = e1;
+      if (ez_it) {
+        double d = e1 - ez_it[t];
+        dn += d * d;
+        nn += e1 * e1;
+      }
+    }
+  }
+  __shared__ double red[3][8];
+  dn = warp_sum(dn);
+  nn = warp_sum(nn);
+  src = warp_sum(src);
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    red[0][w] = dn;
+    red[1][w] = nn;
+    red[2][w] = src;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      a += red[0][k];
+      b += red[1][k];
+      c += red[2][k];
+    }
+    if (a != 0.0) atomicAdd(&cnt->norm[0], a);
+    if (b != 0.0) atomicAdd(&cnt->norm[1], b);
+    if (c != 0.0) atomicAdd(&cnt->src, c);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_half_field(const Grid &g, const double *er0, const double *ez0,
+                              const double *er1, const double *ez1, double *erh, double *ezh,
+                              cudaStream_t s) {
+  long long n1 = (long long)g.nr * (g.nz + 1), n2 = (long long)(g.nr + 1) * g.nz;
+  long long n = n1 + n2;
+  k_half<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n1, n2, er0, ez0, er1, ez1, erh, ezh);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_field_solve(const FieldOp &F, const double *er0, const double *ez0,
+                               const double *h0, const double *ir, const double *iz, double v0,
+                               double v1, double *er1, double *ez1, double *h1, const double *er_it,
+                               const double *ez_it, DevCounters *cnt, cudaStream_t s) {
+  cudaError_t e;
+  int nc = F.nr * F.nz;
+  if ((e = cudaMemsetAsync(&cnt->norm[0], 0, 3 * sizeof(double), s)) != cudaSuccess) return e;
+  k_rhs<<<(nc + 255) / 256, 256, 0, s>>>(F, er0, ez0, h0, ir, iz, v0, v1);
+  dim3 grid((F.nz + TM - 1) / TM, (F.nr + TM - 1) / TM);
+  k_gemm<<<grid, 256, 0, s>>>(F.nr, F.nz, F.nz, F.rhs, F.Q, F.hat);
+  int mb = 16;
+  while (mb > 1 && (size_t)3 * F.nr * mb * sizeof(double) > 200 * 1024) mb >>= 1;
+  size_t smem = (size_t)3 * F.nr * mb * sizeof(double);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    attr_set = true;
+  }
+  k_tridiag<<<(F.nz + mb - 1) / mb, 64, smem, s>>>(F, mb);
+  k_gemm<<<grid, 256, 0, s>>>(F.nr, F.nz, F.nz, F.hat, F.QT, F.hhalf);
+  long long ner = (long long)F.nr * (F.nz + 1), nez = (long long)(F.nr + 1) * F.nz;
+  long long n = ner > nez ? ner : nez;
+  k_update<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(F, er0, ez0, h0, ir, iz, v0, v1, er1, ez1,
+                                                       h1, er_it, ez_it, cnt);
+  return cudaGetLastError();
+}
+
+}  // namespace pic

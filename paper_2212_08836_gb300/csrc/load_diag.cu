@@ -1,0 +1,147 @@
+// Row a1: pair loading (uniform in the logical coordinates, weight
+// proportional to r*J_r as in Sec. 2.1, Maxwellian velocities) and row a9:
+// FP64 conservation diagnostics (kinetic and field energy, node charge).
+#include "pic_internal.cuh"
+
+namespace pic {
+namespace {
+
+__global__ void __launch_bounds__(256) k_load(Grid g, long long n, double n0, double vthe,
+                                              double vthi, uint64_t seed, Parts e, Parts i) {
+  long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  double u[4];
+  draw4(seed, kStreamLoadPos, (uint64_t)p, kLoadStep, 0, u);
+  double xi = (double)g.nr * u[0];
+  double eta = (double)g.nz * u[1];
+  int ic = (int)floor(xi), jc = (int)floor(eta);
+  if (ic > g.nr - 1) ic = g.nr - 1;
+  if (jc > g.nz - 1) jc = g.nz - 1;
+  int32_t cell = ic * g.nz + jc;
+  double a = xi - (double)ic, b = eta - (double)jc;
+  double w = n0 * (kTwoPi * (xi * g.dr)) * g.R * g.L / (double)n;
+  e.cell[p] = cell; e.a[p] = a; e.b[p] = b; e.w[p] = w; e.id[p] = (uint32_t)p;
+  i.cell[p] = cell; i.a[p] = a; i.b[p] = b; i.w[p] = w; i.id[p] = (uint32_t)p;
+  double g1, g2, g3, g4;
+  draw4(seed, kStreamLoadVe, (uint64_t)p, kLoadStep, 0, u);
+  gauss2(u[0], u[1], g1, g2);
+  gauss2(u[2], u[3], g3, g4);
+  e.vr[p] = vthe * g1; e.vt[p] = vthe * g2; e.vz[p] = vthe * g3;
+  draw4(seed, kStreamLoadVi, (uint64_t)p, kLoadStep, 0, u);
+  gauss2(u[0], u[1], g1, g2);
+  gauss2(u[2], u[3], g3, g4);
+  i.vr[p] = vthi * g1; i.vt[p] = vthi * g2; i.vz[p] = vthi * g3;
+}
+
+__device__ __forceinline__ double wsum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block reduction of two doubles into out[0], out[1] (atomics)
+__device__ void block_add2(double x, double y, double *out) {
+  __shared__ double s[2][32];
+  x = wsum(x);
+  y = wsum(y);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) { s[0][w] = x; s[1][w] = y; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { a += s[0][k]; b += s[1][k]; }
+    atomicAdd(&out[0], a);
+    atomicAdd(&out[1], b);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_kinetic(Parts p, long long n, double m, double q,
+                                                 double *out2) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double k = 0.0, c = 0.0;
+  if (t < n && p.cell[t] >= 0) {
+    double vr = p.vr[t], vt = p.vt[t], vz = p.vz[t], w = p.w[t];
+    k = 0.5 * m * w * (vr * vr + vt * vt + vz * vz);
+    c = q * w;
+  }
+  block_add2(k, c, out2);
+}
+
+__global__ void __launch_bounds__(256) k_field_energy(Grid g, double eps, double mu,
+                                                      const double *er, const double *ez,
+                                                      const double *h, double *out) {
+  int nr = g.nr, nz = g.nz, nz1 = nz + 1;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long ner = (long long)nr * nz1, nez = (long long)(nr + 1) * nz, nh = (long long)nr * nz;
+  double W = 0.0;
+  double dr = g.dr, dz = g.dz;
+  if (t < ner) {
+    int i = (int)(t / nz1), j = (int)(t - (t / nz1) * nz1);
+    if (j != 0 && j != nz) {
+      double e = er[t];
+      W += 0.5 * eps * e * e * (kTwoPi * (((double)i + 0.5) * dr) * dz) * dr;
+    }
+  }
+  if (t < nez) {
+    int i = (int)(t / nz);
+    if (i < nr) {
+      double e = ez[t];
+      double A = i == 0 ? kPi * (0.5 * dr) * (0.5 * dr) : kTwoPi * ((double)i * dr) * dr;
+      W += 0.5 * eps * e * e * A * dz;
+    }
+  }
+  if (t < nh) {
+    int i = (int)(t / nz);
+    double hh = h[t];
+    W += 0.5 * mu * hh * hh * (kTwoPi * (((double)i + 0.5) * dr) * dr * dz);
+  }
+  block_add2(W, 0.0, out);
+}
+
+__global__ void __launch_bounds__(256) k_node_charge(Grid g, Parts p, long long n, double q,
+                                                     double *Q) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  int c = p.cell[t];
+  if (c < 0) return;
+  int nz = g.nz, nz1 = nz + 1;
+  int ic = c / nz, jc = c - (c / nz) * nz;
+  double a = p.a[t], b = p.b[t], qw = q * p.w[t];
+  atomicAdd(&Q[ic * nz1 + jc], qw * (1.0 - a) * (1.0 - b));
+  atomicAdd(&Q[(ic + 1) * nz1 + jc], qw * a * (1.0 - b));
+  atomicAdd(&Q[ic * nz1 + jc + 1], qw * (1.0 - a) * b);
+  atomicAdd(&Q[(ic + 1) * nz1 + jc + 1], qw * a * b);
+}
+
+}  // namespace
+
+cudaError_t launch_load(const Grid &g, long long n, double n0, double te_ev, double ti_ev,
+                        uint64_t seed, Parts e, Parts i, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  double vthe = sqrt(te_ev * kQE / kME), vthi = sqrt(ti_ev * kQE / kMAr);
+  k_load<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, n, n0, vthe, vthi, seed, e, i);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kinetic(const Parts &p, long long n, double m, double q, double *out2,
+                           cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_kinetic<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, n, m, q, out2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_field_energy(const Grid &g, double eps, double mu, const double *er,
+                                const double *ez, const double *h, double *out, cudaStream_t s) {
+  long long n = (long long)(g.nr + 1) * (g.nz + 1);
+  k_field_energy<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, eps, mu, er, ez, h, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_node_charge(const Grid &g, const Parts &p, long long n, double q, double *Q,
+                               cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  k_node_charge<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, p, n, q, Q);
+  return cudaGetLastError();
+}
+
+}  // namespace pic

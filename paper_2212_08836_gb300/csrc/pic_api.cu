@@ -1,0 +1,704 @@
+// C ABI of include/pic.h: context over a caller-owned device workspace, the
+// field-operator set-up and the per-step driver (Picard loop of Sec. 2.1:
+// push+deposit with E^{n+1/2,k}, implicit field solve, relative-change test;
+// then commit push, MCC, sort).  No device allocation anywhere.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "pic_internal.cuh"
+
+using namespace pic;
+
+struct pic_ctx {
+  pic_config cfg;
+  Grid g;
+  cudaStream_t s;
+  double eps, mu, ng;
+  char *ws;
+  size_t ws_bytes;
+  long long cap[2], n[2];
+  uint32_t next_id[2];
+  long long step;
+  Parts P[2][2];
+  int cur[2];
+  double *er, *ez, *h;      // E^n, H^n
+  double *er1, *ez1;        // Picard iterate E^{n+1,k}
+  double *er2, *ez2, *h2;   // solver output
+  double *erh, *ezh;        // E^{n+1/2,k}
+  double *ir, *iz;          // crossed charge of the pass
+  double *wall;             // 2 species x (2(nr+1) + nz+1)
+  FieldOp F;
+  DevCounters *cnt;
+  int32_t *flag, *offs, *counts, *coffs, *cursor;
+  long long *total;
+  void *scan_scratch;
+  double *diag;             // 8 doubles
+  double numax_e, gmax, pnull_e, pnull_i;
+  long long launches;       // kernels enqueued by this context (host count)
+  // optional timing of the push launches (CUDA events on the context stream)
+  int prof;
+  int nev;
+  cudaEvent_t ev[2 * 128];
+  double push_ms;
+  long long push_launches, pending_launches;
+};
+
+namespace {
+
+const double kSigmaCx = 5e-19;
+
+double h_sig_el(double eps) {
+  double x = eps / 12.0;
+  return 1.5e-19 * x / (1.0 + x * x) + 1e-20;
+}
+double h_sig_ex(double eps) {
+  if (!(eps > 11.5)) return 0.0;
+  double u = eps / 11.5;
+  return 4e-20 * log(u) / u;
+}
+double h_sig_iz(double eps) {
+  if (!(eps > 15.76)) return 0.0;
+  double u = eps / 15.76;
+  return 8e-20 * log(u) / u;
+}
+
+struct Carver {
+  char *base;
+  size_t off, cap;
+  bool ok;
+  void *take(size_t bytes) {
+    off = (off + 255) & ~(size_t)255;
+    void *p = base ? base + off : nullptr;
+    off += bytes;
+    if (off > cap) ok = false;
+    return p;
+  }
+};
+
+bool valid(const pic_config *c) {
+  if (!c) return false;
+  if (c->nr < 2 || c->nz < 2 || c->nr > 8192 || c->nz > 8192) return false;
+  if (!(c->R > 0) || !(c->L > 0) || !(c->dt > 0)) return false;
+  if (c->np_init < 0 || !(c->capacity_factor >= 1.0)) return false;
+  if (!(c->picard_tol > 0) || c->picard_max < 1) return false;
+  if (c->precision != PIC_FP64) return false;
+  if (c->mcc_on && (!(c->gas_pressure > 0) || !(c->gas_temp > 0))) return false;
+  return true;
+}
+
+long long capacity(const pic_config *c) {
+  double v = ceil(c->capacity_factor * (double)c->np_init);
+  long long k = (long long)v;
+  return k < 1 ? 1 : k;
+}
+
+// lays out (or measures, when base == nullptr) the workspace
+bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *used) {
+  Carver K{base, 0, cap, true};
+  int nr = c->nr, nz = c->nz;
+  long long pc = capacity(c);
+  size_t ner = (size_t)nr * (nz + 1), nez = (size_t)(nr + 1) * nz, nh = (size_t)nr * nz;
+  for (int s = 0; s < 2; ++s)
+    for (int b = 0; b < 2; ++b) {
+      Parts &P = x->P[s][b];
+      P.cell = (int32_t *)K.take(pc * 4);
+      P.a = (double *)K.take(pc * 8);
+      P.b = (double *)K.take(pc * 8);
+      P.vr = (double *)K.take(pc * 8);
+      P.vt = (double *)K.take(pc * 8);
+      P.vz = (double *)K.take(pc * 8);
+      P.w = (double *)K.take(pc * 8);
+      P.id = (uint32_t *)K.take(pc * 4);
+    }
+  x->er = (double *)K.take(ner * 8);
+  x->ez = (double *)K.take(nez * 8);
+  x->h = (double *)K.take(nh * 8);
+  x->er1 = (double *)K.take(ner * 8);
+  x->ez1 = (double *)K.take(nez * 8);
+  x->er2 = (double *)K.take(ner * 8);
+  x->ez2 = (double *)K.take(nez * 8);
+  x->h2 = (double *)K.take(nh * 8);
+  x->erh = (double *)K.take(ner * 8);
+  x->ezh = (double *)K.take(nez * 8);
+  x->ir = (double *)K.take(ner * 8);
+  x->iz = (double *)K.take(nez * 8);
+  x->wall = (double *)K.take((size_t)2 * (2 * (nr + 1) + nz + 1) * 8);
+  x->F.Q = (double *)K.take((size_t)nz * nz * 8);
+  x->F.QT = (double *)K.take((size_t)nz * nz * 8);
+  x->F.lfac = (double *)K.take(nh * 8);
+  x->F.cinv = (double *)K.take(nh * 8);
+  x->F.eoff = (double *)K.take((size_t)nr * 8);
+  x->F.rhs = (double *)K.take(nh * 8);
+  x->F.hat = (double *)K.take(nh * 8);
+  x->F.hhalf = (double *)K.take(nh * 8);
+  x->cnt = (DevCounters *)K.take(sizeof(DevCounters));
+  x->flag = (int32_t *)K.take(pc * 4);
+  x->offs = (int32_t *)K.take(pc * 4);
+  int ncell = nr * nz;
+  x->counts = (int32_t *)K.take((size_t)(ncell + 1) * 4);
+  x->coffs = (int32_t *)K.take((size_t)(ncell + 1) * 4);
+  x->cursor = (int32_t *)K.take((size_t)ncell * 4);
+  x->total = (long long *)K.take(8);
+  long long sn = pc > ncell + 1 ? pc : ncell + 1;
+  x->scan_scratch = K.take(scan_scratch_bytes(sn));
+  x->diag = (double *)K.take(8 * 8);
+  K.take(0);
+  *used = K.off;
+  return K.ok;
+}
+
+int cuda_rc(cudaError_t e) { return e == cudaSuccess ? PIC_OK : PIC_E_CUDA; }
+
+Parts &cur(pic_ctx *x, int s) { return x->P[s][x->cur[s]]; }
+
+double volt_at(const pic_ctx *x, long long step) {
+  double t = (double)step * x->cfg.dt;
+  return x->cfg.volt * sin(kTwoPi * x->cfg.freq * t);
+}
+
+__global__ void k_fill(double *p, int n, double v) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) p[t] = v;
+}
+
+// fold finished event pairs into the push timing totals (stream must be idle)
+void prof_collect(pic_ctx *x) {
+  for (int k = 0; k < x->nev; ++k) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, x->ev[2 * k], x->ev[2 * k + 1]) == cudaSuccess) x->push_ms += ms;
+  }
+  x->nev = 0;
+  x->push_launches += x->pending_launches;
+  x->pending_launches = 0;
+}
+
+int push_all(pic_ctx *x, const double *erh, const double *ezh, double *ir, double *iz, int write,
+             unsigned long long *counters, double *kel, double *wall) {
+  bool timed = x->prof && x->nev < 128;
+  if (timed) cudaEventRecord(x->ev[2 * x->nev], x->s);
+  for (int s = 0; s < 2; ++s) {
+    PushLaunch L;
+    L.g = x->g;
+    L.dt = x->cfg.dt;
+    L.q = s == 0 ? -kQE : kQE;
+    L.m = s == 0 ? kME : kMAr;
+    L.qm = L.q / L.m;
+    L.wb = L.qm * x->cfg.bz;
+    L.n = x->n[s];
+    L.p = cur(x, s);
+    L.er = erh;
+    L.ez = ezh;
+    L.ir = ir;
+    L.iz = iz;
+    L.write = write;
+    int nr = x->g.nr, nz = x->g.nz;
+    if (wall) {
+      double *ws = wall + (size_t)s * (2 * (nr + 1) + nz + 1);
+      L.wall_z0 = ws;
+      L.wall_zl = ws + (nr + 1);
+      L.wall_r = ws + 2 * (nr + 1);
+    } else {
+      L.wall_z0 = L.wall_zl = L.wall_r = nullptr;
+    }
+    L.counters = counters;
+    L.ke_lost = kel;
+    cudaError_t e = launch_push_fp64(L, x->s);
+    if (e != cudaSuccess) return PIC_E_CUDA;
+    if (L.n > 0) {
+      x->launches += 1;
+      if (timed) x->pending_launches += 1;
+    }
+  }
+  if (timed) {
+    cudaEventRecord(x->ev[2 * x->nev + 1], x->s);
+    x->nev += 1;
+  }
+  return PIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pic_strerror(int code) {
+  switch (code) {
+    case PIC_OK: return "ok";
+    case PIC_E_CONFIG: return "invalid configuration or argument";
+    case PIC_E_CUDA: return "CUDA error";
+    case PIC_E_NOCONV: return "Picard iteration did not converge";
+    case PIC_E_SUBSTEP: return "particle exceeded the sub-step limit";
+    case PIC_E_CAPACITY: return "particle capacity exceeded";
+    case PIC_E_NAN: return "non-finite field or residual";
+    case PIC_E_STATE: return "inconsistent state";
+    case PIC_E_WORKSPACE: return "workspace missing, too small or misaligned";
+    default: return "unknown status";
+  }
+}
+
+const char *pic_version(void) { return "pic-gb300 fp64 sm_103a 1"; }
+
+int pic_workspace_size(const pic_config *cfg, size_t *bytes) {
+  if (!valid(cfg) || !bytes) return PIC_E_CONFIG;
+  pic_ctx tmp;
+  memset(&tmp, 0, sizeof(tmp));
+  size_t used = 0;
+  layout(&tmp, cfg, nullptr, (size_t)-1, &used);
+  *bytes = used + 256;
+  return PIC_OK;
+}
+
+int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes, void *stream,
+             pic_ctx **out) {
+  if (!out) return PIC_E_CONFIG;
+  *out = nullptr;
+  if (!valid(cfg)) return PIC_E_CONFIG;
+  if (!workspace_dev || ((uintptr_t)workspace_dev & 255)) return PIC_E_WORKSPACE;
+  pic_ctx *x = (pic_ctx *)calloc(1, sizeof(pic_ctx));
+  if (!x) return PIC_E_CONFIG;
+  x->cfg = *cfg;
+  x->s = (cudaStream_t)stream;
+  size_t used = 0;
+  if (!layout(x, cfg, (char *)workspace_dev, workspace_bytes, &used)) {
+    free(x);
+    return PIC_E_WORKSPACE;
+  }
+  x->ws = (char *)workspace_dev;
+  x->ws_bytes = workspace_bytes;
+  int nr = cfg->nr, nz = cfg->nz;
+  x->g.nr = nr;
+  x->g.nz = nz;
+  x->g.R = cfg->R;
+  x->g.L = cfg->L;
+  x->g.dr = cfg->R / nr;
+  x->g.dz = cfg->L / nz;
+  x->eps = cfg->eps > 0 ? cfg->eps : kEps0;
+  x->mu = cfg->mu > 0 ? cfg->mu : kMu0;
+  x->cap[0] = x->cap[1] = capacity(cfg);
+  x->ng = cfg->mcc_on ? cfg->gas_pressure / (kKB * cfg->gas_temp) : 0.0;
+
+  // MCC constants (host): nu_max over eps <= 1 keV (x 1.01), ion g_max
+  if (cfg->mcc_on) {
+    double best = 0.0;
+    for (int k = 1; k <= 200000; ++k) {
+      double e = 1000.0 * (double)k / 200000.0;
+      double v = sqrt(2.0 * e * kQE / kME);
+      double nu = x->ng * (h_sig_el(e) + h_sig_ex(e) + h_sig_iz(e)) * v;
+      if (nu > best) best = nu;
+    }
+    x->numax_e = 1.01 * best;
+    double vthg = sqrt(kKB * cfg->gas_temp / kMAr);
+    x->gmax = sqrt(2.0 * kQE * 1000.0 / kMAr) + 5.0 * vthg;
+    double nu_i = x->ng * kSigmaCx * x->gmax;
+    x->pnull_e = -expm1(-x->numax_e * cfg->dt);
+    x->pnull_i = -expm1(-nu_i * cfg->dt);
+  }
+
+  // field operator: DCT-II along z diagonalises the Neumann Laplacian T_z;
+  // per mode m an SPD tridiagonal system along r, factorised once (Thomas)
+  FieldOp &F = x->F;
+  F.nr = nr;
+  F.nz = nz;
+  F.dr = x->g.dr;
+  F.dz = x->g.dz;
+  F.dt = cfg->dt;
+  F.eps = x->eps;
+  F.mu = x->mu;
+  F.L = cfg->L;
+  double dr = F.dr, dz = F.dz, hdt2 = 0.5 * cfg->dt * cfg->dt;
+  std::vector<double> Q((size_t)nz * nz), QT((size_t)nz * nz), lam(nz);
+  for (int m = 0; m < nz; ++m) {
+    double cm = m == 0 ? sqrt(1.0 / nz) : sqrt(2.0 / nz);
+    lam[m] = 2.0 - 2.0 * cos(kPi * m / nz);
+    for (int j = 0; j < nz; ++j) {
+      double v = cm * cos(kPi * m * (j + 0.5) / nz);
+      Q[(size_t)j * nz + m] = v;
+      QT[(size_t)m * nz + j] = v;
+    }
+  }
+  std::vector<double> mass(nr), kz(nr), kdiag(nr), eoff(nr, 0.0);
+  auto rh = [&](int i) { return ((double)i + 0.5) * dr; };
+  auto az = [&](int i) { return i == 0 ? kPi * (0.5 * dr) * (0.5 * dr) : kTwoPi * ((double)i * dr) * dr; };
+  for (int i = 0; i < nr; ++i) {
+    mass[i] = 2.0 * x->mu * (kTwoPi * rh(i) * dr * dz);
+    double ar = kTwoPi * rh(i) * dz;
+    double s = kTwoPi * rh(i);
+    kz[i] = hdt2 * (dr / (x->eps * ar)) * s * s;
+    double wz_i = dz / (x->eps * az(i));
+    double d = wz_i * s * s;
+    if (i + 1 <= nr - 1) d += (dz / (x->eps * az(i + 1))) * s * s;
+    kdiag[i] = hdt2 * d;
+    if (i >= 1) eoff[i] = hdt2 * wz_i * (-kTwoPi * rh(i - 1)) * s;
+  }
+  std::vector<double> lf((size_t)nr * nz), ci((size_t)nr * nz);
+  for (int m = 0; m < nz; ++m) {
+    double c = mass[0] + kz[0] * lam[m] + kdiag[0];
+    lf[m] = 0.0;
+    ci[m] = 1.0 / c;
+    for (int i = 1; i < nr; ++i) {
+      double d = mass[i] + kz[i] * lam[m] + kdiag[i];
+      double l = eoff[i] / c;
+      c = d - l * eoff[i];
+      lf[(size_t)i * nz + m] = l;
+      ci[(size_t)i * nz + m] = 1.0 / c;
+    }
+  }
+  cudaError_t e = cudaSuccess;
+  auto up = [&](const void *dst, const void *src, size_t b) {
+    if (e == cudaSuccess) e = cudaMemcpyAsync((void *)dst, src, b, cudaMemcpyHostToDevice, x->s);
+  };
+  up(F.Q, Q.data(), Q.size() * 8);
+  up(F.QT, QT.data(), QT.size() * 8);
+  up(F.lfac, lf.data(), lf.size() * 8);
+  up(F.cinv, ci.data(), ci.size() * 8);
+  up(F.eoff, eoff.data(), eoff.size() * 8);
+  size_t ner = (size_t)nr * (nz + 1), nez = (size_t)(nr + 1) * nz, nh = (size_t)nr * nz;
+  if (e == cudaSuccess) e = cudaMemsetAsync(x->er, 0, ner * 8, x->s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(x->ez, 0, nez * 8, x->s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(x->h, 0, nh * 8, x->s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(x->wall, 0, (size_t)2 * (2 * (nr + 1) + nz + 1) * 8, x->s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(x->cnt, 0, sizeof(DevCounters), x->s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(x->s);
+  if (e != cudaSuccess) {
+    free(x);
+    return PIC_E_CUDA;
+  }
+  *out = x;
+  return PIC_OK;
+}
+
+void pic_destroy(pic_ctx *ctx) {
+  if (!ctx) return;
+  if (ctx->prof) {
+    cudaStreamSynchronize(ctx->s);
+    for (int k = 0; k < 2 * 128; ++k) cudaEventDestroy(ctx->ev[k]);
+  }
+  free(ctx);
+}
+
+int pic_profile(pic_ctx *x, int enable) {
+  if (!x) return PIC_E_CONFIG;
+  if (cudaStreamSynchronize(x->s) != cudaSuccess) return PIC_E_CUDA;
+  if (enable && !x->prof) {
+    for (int k = 0; k < 2 * 128; ++k)
+      if (cudaEventCreate(&x->ev[k]) != cudaSuccess) return PIC_E_CUDA;
+    x->prof = 1;
+  }
+  x->nev = 0;
+  x->push_ms = 0.0;
+  x->push_launches = x->pending_launches = 0;
+  if (!enable && x->prof) {
+    for (int k = 0; k < 2 * 128; ++k) cudaEventDestroy(x->ev[k]);
+    x->prof = 0;
+  }
+  return PIC_OK;
+}
+
+int pic_profile_read(pic_ctx *x, double *push_ms, long long *push_launches) {
+  if (!x) return PIC_E_CONFIG;
+  if (cudaStreamSynchronize(x->s) != cudaSuccess) return PIC_E_CUDA;
+  if (x->prof) prof_collect(x);
+  if (push_ms) *push_ms = x->push_ms;
+  if (push_launches) *push_launches = x->push_launches;
+  return PIC_OK;
+}
+
+int pic_sort(pic_ctx *x) {
+  if (!x) return PIC_E_CONFIG;
+  for (int s = 0; s < 2; ++s) {
+    SortLaunch S;
+    S.ncell = x->g.nr * x->g.nz;
+    S.n = x->n[s];
+    S.src = cur(x, s);
+    S.dst = x->P[s][x->cur[s] ^ 1];
+    S.counts = x->counts;
+    S.offs = x->coffs;
+    S.cursor = x->cursor;
+    S.total = x->total;
+    S.scan_scratch = x->scan_scratch;
+    if (launch_sort(S, x->s) != cudaSuccess) return PIC_E_CUDA;
+    x->launches += S.n > 0 ? 5 : 3;
+    long long tot = 0;
+    if (cudaMemcpyAsync(&tot, x->total, 8, cudaMemcpyDeviceToHost, x->s) != cudaSuccess)
+      return PIC_E_CUDA;
+    if (cudaStreamSynchronize(x->s) != cudaSuccess) return PIC_E_CUDA;
+    x->n[s] = tot;
+    x->cur[s] ^= 1;
+  }
+  return PIC_OK;
+}
+
+int pic_load_particles(pic_ctx *x) {
+  if (!x) return PIC_E_CONFIG;
+  long long n = x->cfg.np_init;
+  if (n > x->cap[0] || n > x->cap[1] || n > 0xFFFFFFFFll) return PIC_E_CAPACITY;
+  if (launch_load(x->g, n, x->cfg.n0, x->cfg.te_ev, x->cfg.ti_ev, x->cfg.seed, cur(x, 0),
+                  cur(x, 1), x->s) != cudaSuccess)
+    return PIC_E_CUDA;
+  if (n > 0) x->launches += 1;
+  x->n[0] = x->n[1] = n;
+  x->next_id[0] = x->next_id[1] = (uint32_t)n;
+  return pic_sort(x);
+}
+
+int pic_push_deposit(pic_ctx *x, const double *erh, const double *ezh, double *ir, double *iz,
+                     int write, unsigned long long *counters, double *kel) {
+  if (!x || !erh || !ezh) return PIC_E_CONFIG;
+  return push_all(x, erh, ezh, ir, iz, write, counters, kel, write ? x->wall : nullptr);
+}
+
+int pic_field_solve(pic_ctx *x, const double *er0, const double *ez0, const double *h0,
+                    const double *ir, const double *iz, double v0, double v1, double *er1,
+                    double *ez1, double *h1, double *src) {
+  if (!x || !er0 || !ez0 || !h0 || !ir || !iz || !er1 || !ez1 || !h1) return PIC_E_CONFIG;
+  cudaError_t e = launch_field_solve(x->F, er0, ez0, h0, ir, iz, v0, v1, er1, ez1, h1, nullptr,
+                                     nullptr, x->cnt, x->s);
+  x->launches += 5;
+  if (e == cudaSuccess && src)
+    e = cudaMemcpyAsync(src, &x->cnt->src, 8, cudaMemcpyDeviceToDevice, x->s);
+  return cuda_rc(e);
+}
+
+int pic_mcc(pic_ctx *x, unsigned long long step, long long *counts, double *de_coll) {
+  if (!x) return PIC_E_CONFIG;
+  cudaError_t e = cudaMemsetAsync(x->cnt->mcc, 0, sizeof(x->cnt->mcc), x->s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(&x->cnt->de_coll, 0, 8, x->s);
+  MccLaunch M;
+  M.seed = x->cfg.seed;
+  M.step = step;
+  M.ng = x->ng;
+  M.tg = x->cfg.gas_temp;
+  M.numax_e = x->numax_e;
+  M.pnull_e = x->pnull_e;
+  M.pnull_i = x->pnull_i;
+  M.gmax = x->gmax;
+  M.ne = x->n[0];
+  M.ni = x->n[1];
+  M.e = cur(x, 0);
+  M.i = cur(x, 1);
+  M.flag = x->flag;
+  M.offs = x->offs;
+  M.cnt = x->cnt;
+  if (e == cudaSuccess) e = launch_mcc_collide(M, x->s);
+  if (e == cudaSuccess) e = scan_exclusive(x->flag, x->offs, M.ne, x->total, x->scan_scratch, x->s);
+  x->launches += (M.ne > 0 || M.ni > 0 ? 1 : 0) + (M.ne > 0 ? 3 : 0);
+  long long tot = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&tot, x->total, 8, cudaMemcpyDeviceToHost, x->s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(x->s);
+  if (e != cudaSuccess) return PIC_E_CUDA;
+  int rc = PIC_OK;
+  unsigned long long capov = 0;
+  if (tot > 0) {
+    if (x->n[0] + tot > x->cap[0] || x->n[1] + tot > x->cap[1] ||
+        (long long)x->next_id[0] + tot > 0xFFFFFFFFll || (long long)x->next_id[1] + tot > 0xFFFFFFFFll) {
+      rc = PIC_E_CAPACITY;
+      capov = (unsigned long long)tot;
+    } else {
+      e = launch_mcc_append(M, x->n[0], x->n[1], x->next_id[0], x->next_id[1], x->s);
+      if (e != cudaSuccess) return PIC_E_CUDA;
+      x->launches += 1;
+      x->n[0] += tot;
+      x->n[1] += tot;
+      x->next_id[0] += (uint32_t)tot;
+      x->next_id[1] += (uint32_t)tot;
+    }
+  }
+  if (counts || de_coll) {
+    unsigned long long hc[8];
+    double de = 0.0;
+    e = cudaMemcpyAsync(hc, x->cnt->mcc, sizeof(hc), cudaMemcpyDeviceToHost, x->s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&de, &x->cnt->de_coll, 8, cudaMemcpyDeviceToHost, x->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(x->s);
+    if (e != cudaSuccess) return PIC_E_CUDA;
+    hc[7] = capov;
+    if (counts)
+      for (int k = 0; k < 8; ++k) counts[k] = (long long)hc[k];
+    if (de_coll) *de_coll = de;
+  }
+  return rc;
+}
+
+int pic_step(pic_ctx *x, int nsteps, pic_step_stats *st) {
+  if (!x || nsteps < 0) return PIC_E_CONFIG;
+  int nr = x->g.nr, nz = x->g.nz;
+  size_t ner = (size_t)nr * (nz + 1), nez = (size_t)(nr + 1) * nz;
+  int rc = PIC_OK;
+  for (int it = 0; it < nsteps; ++it) {
+    pic_step_stats S;
+    memset(&S, 0, sizeof(S));
+    long long l0 = x->launches;
+    double v0 = volt_at(x, x->step), v1 = volt_at(x, x->step + 1);
+    cudaStream_t s = x->s;
+    cudaError_t e = cudaMemcpyAsync(x->er1, x->er, ner * 8, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(x->ez1, x->ez, nez * 8, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) {
+      k_fill<<<(nz + 127) / 128, 128, 0, s>>>(x->ez1 + (size_t)nr * nz, nz, v1 / x->cfg.L);
+      e = cudaGetLastError();
+      x->launches += 1;
+    }
+    if (e != cudaSuccess) return PIC_E_CUDA;
+    bool conv = false;
+    double res = 0.0, src = 0.0;
+    int k;
+    for (k = 0; k < x->cfg.picard_max; ++k) {
+      if (launch_half_field(x->g, x->er, x->ez, x->er1, x->ez1, x->erh, x->ezh, s) != cudaSuccess)
+        return PIC_E_CUDA;
+      x->launches += 1;
+      if (cudaMemsetAsync(x->ir, 0, ner * 8, s) != cudaSuccess) return PIC_E_CUDA;
+      if (cudaMemsetAsync(x->iz, 0, nez * 8, s) != cudaSuccess) return PIC_E_CUDA;
+      int r = push_all(x, x->erh, x->ezh, x->ir, x->iz, 0, nullptr, nullptr, nullptr);
+      if (r) return r;
+      S.pushes += x->n[0] + x->n[1];
+      if (launch_field_solve(x->F, x->er, x->ez, x->h, x->ir, x->iz, v0, v1, x->er2, x->ez2, x->h2,
+                             x->er1, x->ez1, x->cnt, s) != cudaSuccess)
+        return PIC_E_CUDA;
+      x->launches += 5;
+      double hn[3];
+      if (cudaMemcpyAsync(hn, x->cnt->norm, 3 * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return PIC_E_CUDA;
+      if (cudaStreamSynchronize(s) != cudaSuccess) return PIC_E_CUDA;
+      if (x->prof) prof_collect(x);
+      res = sqrt(hn[0]) / fmax(sqrt(hn[1]), 1e-30);
+      src = hn[2];
+      double *t;
+      t = x->er1; x->er1 = x->er2; x->er2 = t;
+      t = x->ez1; x->ez1 = x->ez2; x->ez2 = t;
+      if (!isfinite(res)) {
+        S.picard_iters = k + 1;
+        if (st) *st = S;
+        return PIC_E_NAN;
+      }
+      if (res < x->cfg.picard_tol) {
+        conv = true;
+        break;
+      }
+    }
+    S.picard_iters = conv ? k + 1 : k;
+    S.last_res = res;
+    S.converged = conv ? 1 : 0;
+    if (!conv) {
+      S.n[0] = x->n[0];
+      S.n[1] = x->n[1];
+      if (st) *st = S;
+      return PIC_E_NOCONV;
+    }
+    // commit: the half field of the last iteration fed the last solve
+    if (cudaMemsetAsync(x->ir, 0, ner * 8, s) != cudaSuccess) return PIC_E_CUDA;
+    if (cudaMemsetAsync(x->iz, 0, nez * 8, s) != cudaSuccess) return PIC_E_CUDA;
+    if (cudaMemsetAsync(x->cnt->push, 0, sizeof(x->cnt->push), s) != cudaSuccess) return PIC_E_CUDA;
+    if (cudaMemsetAsync(&x->cnt->ke_lost, 0, 8, s) != cudaSuccess) return PIC_E_CUDA;
+    int r = push_all(x, x->erh, x->ezh, x->ir, x->iz, 1, x->cnt->push, &x->cnt->ke_lost, x->wall);
+    if (r) return r;
+    S.pushes += x->n[0] + x->n[1];
+    double *t;
+    t = x->er; x->er = x->er1; x->er1 = t;
+    t = x->ez; x->ez = x->ez1; x->ez1 = t;
+    t = x->h; x->h = x->h2; x->h2 = t;
+    S.src_energy = src;
+    if (x->cfg.mcc_on) {
+      int mr = pic_mcc(x, (unsigned long long)x->step, S.mcc, &S.de_coll);
+      if (mr && mr != PIC_E_CAPACITY) return mr;
+      if (mr) rc = mr;
+    }
+    int sr = pic_sort(x);
+    if (sr) return sr;
+    unsigned long long pc[4];
+    double kel = 0.0;
+    if (cudaMemcpyAsync(pc, x->cnt->push, sizeof(pc), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return PIC_E_CUDA;
+    if (cudaMemcpyAsync(&kel, &x->cnt->ke_lost, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return PIC_E_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return PIC_E_CUDA;
+    if (x->prof) prof_collect(x);
+    S.substep_err = (long long)pc[0];
+    S.absorbed = (long long)pc[1];
+    S.substeps = (long long)pc[2];
+    S.fallbacks = (long long)pc[3];
+    S.ke_lost = kel;
+    S.n[0] = x->n[0];
+    S.n[1] = x->n[1];
+    S.launches = x->launches - l0;
+    x->step += 1;
+    if (st) *st = S;
+    if (S.substep_err && !rc) rc = PIC_E_SUBSTEP;
+  }
+  return rc;
+}
+
+int pic_diag(pic_ctx *x, pic_diag_out *out) {
+  if (!x || !out) return PIC_E_CONFIG;
+  cudaError_t e = cudaMemsetAsync(x->diag, 0, 8 * 8, x->s);
+  if (e == cudaSuccess) e = launch_kinetic(cur(x, 0), x->n[0], kME, -kQE, x->diag, x->s);
+  x->launches += 3;
+  if (e == cudaSuccess) e = launch_kinetic(cur(x, 1), x->n[1], kMAr, kQE, x->diag + 2, x->s);
+  if (e == cudaSuccess)
+    e = launch_field_energy(x->g, x->eps, x->mu, x->er, x->ez, x->h, x->diag + 4, x->s);
+  double h[8];
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, x->diag, 64, cudaMemcpyDeviceToHost, x->s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(x->s);
+  if (e != cudaSuccess) return PIC_E_CUDA;
+  out->kinetic[0] = h[0];
+  out->charge[0] = h[1];
+  out->kinetic[1] = h[2];
+  out->charge[1] = h[3];
+  out->field = h[4];
+  out->n[0] = x->n[0];
+  out->n[1] = x->n[1];
+  return PIC_OK;
+}
+
+int pic_node_charge(pic_ctx *x, double *q) {
+  if (!x || !q) return PIC_E_CONFIG;
+  cudaError_t e = launch_node_charge(x->g, cur(x, 0), x->n[0], -kQE, q, x->s);
+  if (e == cudaSuccess) e = launch_node_charge(x->g, cur(x, 1), x->n[1], kQE, q, x->s);
+  return cuda_rc(e);
+}
+
+int pic_get_view(pic_ctx *x, pic_view *v) {
+  if (!x || !v) return PIC_E_CONFIG;
+  for (int s = 0; s < 2; ++s) {
+    Parts &P = cur(x, s);
+    v->cell[s] = P.cell;
+    v->a[s] = P.a;
+    v->b[s] = P.b;
+    v->vr[s] = P.vr;
+    v->vt[s] = P.vt;
+    v->vz[s] = P.vz;
+    v->w[s] = P.w;
+    v->id[s] = P.id;
+    v->n[s] = x->n[s];
+    v->cap[s] = x->cap[s];
+    v->next_id[s] = x->next_id[s];
+  }
+  v->er = x->er;
+  v->ez = x->ez;
+  v->h = x->h;
+  v->step = x->step;
+  return PIC_OK;
+}
+
+int pic_set_counts(pic_ctx *x, long long ne, long long ni, uint32_t nide, uint32_t nidi,
+                   long long step) {
+  if (!x) return PIC_E_CONFIG;
+  if (ne < 0 || ni < 0 || ne > x->cap[0] || ni > x->cap[1] || step < 0) return PIC_E_STATE;
+  x->n[0] = ne;
+  x->n[1] = ni;
+  x->next_id[0] = nide;
+  x->next_id[1] = nidi;
+  x->step = step;
+  return PIC_OK;
+}
+
+int pic_mcc_constants(pic_ctx *x, double *numax_e, double *gmax, double *pnull_e,
+                      double *pnull_i) {
+  if (!x) return PIC_E_CONFIG;
+  if (numax_e) *numax_e = x->numax_e;
+  if (gmax) *gmax = x->gmax;
+  if (pnull_e) *pnull_e = x->pnull_e;
+  if (pnull_i) *pnull_i = x->pnull_i;
+  return PIC_OK;
+}
+
+}  // extern "C"

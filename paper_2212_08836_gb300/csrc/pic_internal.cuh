@@ -1,0 +1,163 @@
+// Internal declarations of the GB300 hot path (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pic.h"
+
+namespace pic {
+
+// CODATA 2018
+constexpr double kQE = 1.602176634e-19;
+constexpr double kME = 9.1093837015e-31;
+constexpr double kAMU = 1.66053906660e-27;
+constexpr double kMAr = 39.948 * kAMU;
+constexpr double kKB = 1.380649e-23;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kMu0 = 1.25663706212e-6;
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kTwoPi = 6.283185307179586;
+
+// Philox streams (key word 1) and the step word used while loading
+constexpr uint64_t kStreamLoadPos = 0x20, kStreamLoadVe = 0x21, kStreamLoadVi = 0x22;
+constexpr uint64_t kStreamMccE = 0x10, kStreamMccI = 0x11;
+constexpr uint64_t kLoadStep = 0xFFFFFFFFFFFFFFFFull;
+
+// Sub-step solver limits (FP64 form)
+constexpr int kNsubMax = 64;
+constexpr int kNewtonMax = 30;
+constexpr double kTolX = 1e-14;
+constexpr double kTolT = 1e-14;
+
+// Philox4x64-10 (Salmon et al., SC'11): 64x64 -> 128-bit products via umul64hi.
+__device__ __forceinline__ void philox4x64(uint64_t c[4], uint64_t k0, uint64_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t m0 = 0xD2E7470EE14C6C93ull, m1 = 0xCA5A826395121157ull;
+    uint64_t hi0 = __umul64hi(m0, c[0]), lo0 = m0 * c[0];
+    uint64_t hi1 = __umul64hi(m1, c[2]), lo1 = m1 * c[2];
+    uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    k0 += 0x9E3779B97F4A7C15ull;
+    k1 += 0xBB67AE8584CAA73Bull;
+  }
+}
+
+__device__ __forceinline__ double u01(uint64_t x) {
+  return (double)(x >> 11) * (1.0 / 9007199254740992.0);
+}
+
+__device__ __forceinline__ void draw4(uint64_t seed, uint64_t stream, uint64_t id, uint64_t step,
+                                      uint64_t block, double u[4]) {
+  uint64_t c[4] = {id, step, block, 0};
+  philox4x64(c, seed, stream);
+  u[0] = u01(c[0]); u[1] = u01(c[1]); u[2] = u01(c[2]); u[3] = u01(c[3]);
+}
+
+__device__ __forceinline__ void gauss2(double ua, double ub, double &g1, double &g2) {
+  double rho = sqrt(-2.0 * log(1.0 - ua));
+  double ang = kTwoPi * ub;
+  g1 = rho * cos(ang);
+  g2 = rho * sin(ang);
+}
+
+struct Grid {
+  int nr, nz;
+  double dr, dz, R, L;
+};
+
+// Particle structure of arrays of one species (FP64 form)
+struct Parts {
+  int32_t *cell;
+  double *a, *b, *vr, *vt, *vz, *w;
+  uint32_t *id;
+};
+
+// Device counters written by the push / MCC kernels
+struct DevCounters {
+  unsigned long long push[4];  // substep errors, absorbed, substeps, fallbacks
+  unsigned long long mcc[8];
+  double ke_lost;
+  double de_coll;
+  double norm[2];              // Picard: sum (E_new - E_it)^2, sum E_new^2
+  double src;                  // drive-gap energy of the last solve
+  double pad[3];
+};
+
+// Field operator (separable direct solve of the H_theta system)
+struct FieldOp {
+  int nr, nz;
+  double dr, dz, dt, eps, mu, L;
+  const double *Q;     // nz x nz DCT-II basis, Q[j*nz+m]
+  const double *QT;    // transpose, QT[m*nz+j]
+  const double *lfac;  // nr x nz: Thomas multipliers l[i*nz+m] (i >= 1)
+  const double *cinv;  // nr x nz: 1 / pivots
+  const double *eoff;  // nr: off-diagonal e_i (coupling i-1, i), e_0 = 0
+  double *rhs;         // nr x nz scratch
+  double *hat;         // nr x nz scratch
+  double *hhalf;       // nr x nz: H^{n+1/2}
+};
+
+struct PushLaunch {
+  Grid g;
+  double dt, q, qm, wb, m;
+  long long n;
+  Parts p;
+  const double *er, *ez;
+  double *ir, *iz;
+  int write;
+  double *wall_z0, *wall_zl, *wall_r;
+  unsigned long long *counters;
+  double *ke_lost;
+};
+
+// launchers (return cudaError_t of the launch)
+cudaError_t launch_push_fp64(const PushLaunch &L, cudaStream_t s);
+cudaError_t launch_field_solve(const FieldOp &F, const double *er0, const double *ez0,
+                               const double *h0, const double *ir, const double *iz, double v0,
+                               double v1, double *er1, double *ez1, double *h1, const double *er_it,
+                               const double *ez_it, DevCounters *cnt, cudaStream_t s);
+cudaError_t launch_half_field(const Grid &g, const double *er0, const double *ez0,
+                              const double *er1, const double *ez1, double *erh, double *ezh,
+                              cudaStream_t s);
+cudaError_t launch_load(const Grid &g, long long n, double n0, double te_ev, double ti_ev,
+                        uint64_t seed, Parts e, Parts i, cudaStream_t s);
+
+struct MccLaunch {
+  uint64_t seed, step;
+  double ng, tg, numax_e, pnull_e, pnull_i, gmax;
+  long long ne, ni;
+  Parts e, i;
+  int32_t *flag, *offs;   // per-electron ionization flags / exclusive scan
+  DevCounters *cnt;
+};
+cudaError_t launch_mcc_collide(const MccLaunch &M, cudaStream_t s);
+cudaError_t launch_mcc_append(const MccLaunch &M, long long ne_new0, long long ni_new0,
+                              uint32_t id_e0, uint32_t id_i0, cudaStream_t s);
+
+// exclusive scan of n int32 values; total written to *total_dev (int64)
+size_t scan_scratch_bytes(long long n);
+cudaError_t scan_exclusive(const int32_t *in, int32_t *out, long long n, long long *total_dev,
+                           void *scratch, cudaStream_t s);
+
+struct SortLaunch {
+  int ncell;
+  long long n;
+  Parts src, dst;
+  int32_t *counts;   // ncell + 1
+  int32_t *offs;     // ncell + 1
+  int32_t *cursor;   // ncell
+  long long *total;
+  void *scan_scratch;
+};
+cudaError_t launch_sort(const SortLaunch &S, cudaStream_t s);
+
+cudaError_t launch_kinetic(const Parts &p, long long n, double m, double q, double *out2,
+                           cudaStream_t s);
+cudaError_t launch_field_energy(const Grid &g, double eps, double mu, const double *er,
+                                const double *ez, const double *h, double *out, cudaStream_t s);
+cudaError_t launch_node_charge(const Grid &g, const Parts &p, long long n, double q, double *Q,
+                               cudaStream_t s);
+
+}  // namespace pic
