@@ -88,6 +88,7 @@ def _load_lib():
     L.pic_get_view.argtypes = [_P, C.POINTER(View)]
     L.pic_set_counts.argtypes = [_P, _LL, _LL, C.c_uint32, C.c_uint32, _LL]
     L.pic_mcc_constants.argtypes = [_P, _P, _P, _P, _P]
+    L.pic_sort_cells_noalloc.argtypes = [_I, _I, _LL] + [_P] * 16 + [_P, _P]
     L.pic_profile.argtypes = [_P, _I]
     L.pic_profile_read.argtypes = [_P, _P, _P]
     return L

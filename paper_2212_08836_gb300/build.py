@@ -25,6 +25,7 @@ UNITS = {
     "sort.cu": [],
     "load_diag.cu": ["--fmad=false"],
     "pic_api.cu": ["--fmad=false"],
+    "sort_noalloc.cu": [],
 }
 
 
