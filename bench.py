@@ -32,13 +32,15 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particle-pushes/s per nonlinear iter"
 UNIT = "particle-pushes/s"
-# FP64 operations per particle push of the FP64 mover+deposit kernel on this
-# workload, from the ncu DADD/DMUL/DFMA instruction counts (profiles/).
-FP64_FLOP_PER_PUSH = None
+# FP64 peak of GB300: ncu reports 304 thread-DFMA per cycle GPU-wide
+# (sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained), 2 flops each,
+# at the maximum SM clock of MEASURED_PEAKS.json.
+DFMA_PER_CYCLE = 304
 # algorithmic bytes per push of the FP64 kernel: cell (4) + a, b, vr, vt, vz, w (48)
 BYTES_PER_PUSH_FP64 = 52
-# measured ncu DRAM traffic per push launch of this workload (null until measured)
-TRAFFIC_PER_LAUNCH = None
+# ncu DRAM bytes (read + write) per push of the current FP64 kernel, from the
+# profile in profiles/ (None when the kernel changed after the capture)
+TRAFFIC_PER_PUSH = 54.07  # profiles/push_fp64_large_reactor.md: (222.16 + 4.63) MB / 4194304 pushes
 
 
 def peaks():
@@ -161,21 +163,9 @@ def run_reference(args):
     return 0
 
 
-def run_ours(args):
-    import torch
-
-    ws, rank, local = dist_env()
-    dist = ws > 1
-    if dist:
-        import torch.distributed as D
-
-        D.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    import paper_2212_08836_gb300 as P
-
-    P.lib()
-    cfg = P.large_reactor(seed=1 + rank)
+def measure(P, torch, dev, cfg, args, dist, D, do_e2e, sample_clocks, local):
+    """Load, warm up, then time args.steps whole steps (device-resident state)
+    and optionally the same through the C ABI with pinned host buffers."""
     pic = P.Pic(cfg, device=dev)
     pic.load_particles()
     stream = pic.stream
@@ -187,119 +177,195 @@ def run_ours(args):
 
     for _ in range(args.warmup):
         pic.step(1)
-
-    # ---------------- timed region (device-resident state)
     pic.profile(True)
     barrier()
-    pushes = 0
-    launches = 0
-    iters = []
-    with ClockSampler(local) as clk:
-        ev0 = torch.cuda.Event(enable_timing=True)
-        ev1 = torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        for _ in range(args.steps):
-            _, st = pic.step(1)
-            pushes += st["pushes"]
-            launches += st["launches"]
-            iters.append(st["picard_iters"])
-        ev1.record(stream)
-        barrier()
-    t_ms = ev0.elapsed_time(ev1)
-    push_ms, push_launches = pic.profile_read()
-    pic.profile(False)
-    clocks = clk.summary()
-
-    # ---------------- end to end through the C ABI with host buffers
-    v = pic.view()
-    host = []
-    for s in range(2):
-        n = v["cap"][s]
-        host.append({k: torch.empty_like(v["species"][s][k], device="cpu").pin_memory()
-                     for k in P.FIELDS})
-    hf = {k: torch.empty_like(v[k], device="cpu").pin_memory() for k in ("er", "ez", "h")}
-    for s in range(2):
-        for k in P.FIELDS:
-            host[s][k].copy_(v["species"][s][k])
-    for k in hf:
-        hf[k].copy_(v[k])
-    torch.cuda.synchronize(dev)
-    barrier()
-    e2e_pushes = 0
-    h2d = d2h = 0
-    t0 = time.perf_counter()
-    ev2 = torch.cuda.Event(enable_timing=True)
-    ev3 = torch.cuda.Event(enable_timing=True)
-    ev2.record(stream)
+    r = {"pushes": 0, "launches": 0, "iters": [], "flops": 0, "commit_pushes": 0,
+         "bytes": 0}
+    clk = ClockSampler(local) if sample_clocks else None
+    if clk:
+        clk.__enter__()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
     for _ in range(args.steps):
-        v = pic.view()
-        with torch.cuda.stream(stream):
-            for s in range(2):
-                n = v["n"][s]
-                for k in P.FIELDS:
-                    v["species"][s][k][:n].copy_(host[s][k][:n], non_blocking=True)
-                    h2d += host[s][k][:n].numel() * host[s][k].element_size()
-            for k in hf:
-                v[k].copy_(hf[k], non_blocking=True)
-                h2d += hf[k].numel() * hf[k].element_size()
         _, st = pic.step(1)
-        e2e_pushes += st["pushes"]
-        v = pic.view()
-        with torch.cuda.stream(stream):
-            for s in range(2):
-                n = v["n"][s]
-                for k in P.FIELDS:
-                    host[s][k][:n].copy_(v["species"][s][k][:n], non_blocking=True)
-                    d2h += host[s][k][:n].numel() * host[s][k].element_size()
-            for k in hf:
-                hf[k].copy_(v[k], non_blocking=True)
-                d2h += hf[k].numel() * hf[k].element_size()
-    ev3.record(stream)
+        k = st["picard_iters"]
+        n_commit = st["pushes"] // (k + 1)
+        r["pushes"] += st["pushes"]
+        r["launches"] += st["launches"]
+        r["iters"].append(k)
+        r["flops"] += st["push_flops"]
+        r["commit_pushes"] += n_commit
+        rb, wb = (28, 24) if cfg["precision"] == P.PIC_MIXED else (52, 48)
+        r["bytes"] += st["pushes"] * rb + n_commit * wb
+    ev1.record(stream)
     barrier()
-    e2e_ms = ev2.elapsed_time(ev3)
+    if clk:
+        clk.__exit__()
+        r["clocks"] = clk.summary()
+    r["t_ms"] = ev0.elapsed_time(ev1)
+    r["push_ms"], r["push_launches"] = pic.profile_read()
+    pic.profile(False)
+    r["e2e_ms"] = None
+    if do_e2e:
+        v = pic.view()
+        host = []
+        for s in range(2):
+            host.append({k: torch.empty_like(v["species"][s][k], device="cpu").pin_memory()
+                         for k in P.FIELDS})
+        hf = {k: torch.empty_like(v[k], device="cpu").pin_memory() for k in ("er", "ez", "h")}
+        for s in range(2):
+            for k in P.FIELDS:
+                host[s][k].copy_(v["species"][s][k])
+        for k in hf:
+            hf[k].copy_(v[k])
+        barrier()
+        e2e_pushes = h2d = d2h = 0
+        ev2 = torch.cuda.Event(enable_timing=True)
+        ev3 = torch.cuda.Event(enable_timing=True)
+        ev2.record(stream)
+        for _ in range(args.steps):
+            v = pic.view()
+            with torch.cuda.stream(stream):
+                for s in range(2):
+                    n = v["n"][s]
+                    for k in P.FIELDS:
+                        v["species"][s][k][:n].copy_(host[s][k][:n], non_blocking=True)
+                        h2d += host[s][k][:n].numel() * host[s][k].element_size()
+                for k in hf:
+                    v[k].copy_(hf[k], non_blocking=True)
+                    h2d += hf[k].numel() * hf[k].element_size()
+            _, st = pic.step(1)
+            e2e_pushes += st["pushes"]
+            v = pic.view()
+            with torch.cuda.stream(stream):
+                for s in range(2):
+                    n = v["n"][s]
+                    for k in P.FIELDS:
+                        host[s][k][:n].copy_(v["species"][s][k][:n], non_blocking=True)
+                        d2h += host[s][k][:n].numel() * host[s][k].element_size()
+                for k in hf:
+                    hf[k].copy_(v[k], non_blocking=True)
+                    d2h += hf[k].numel() * hf[k].element_size()
+        ev3.record(stream)
+        barrier()
+        r["e2e_ms"] = ev2.elapsed_time(ev3)
+        r["e2e_pushes"] = e2e_pushes
+        r["h2d"] = h2d // args.steps
+        r["d2h"] = d2h // args.steps
+    pic.close()
+    del pic
+    torch.cuda.empty_cache()
+    return r
 
-    # max over ranks
-    t_max, e2e_max = t_ms, e2e_ms
-    tot_pushes, tot_e2e = pushes, e2e_pushes
+
+def run_ours(args):
+    import torch
+
+    ws, rank, local = dist_env()
+    dist = ws > 1
+    D = None
     if dist:
-        tt = torch.tensor([t_ms, e2e_ms], dtype=torch.float64, device=dev)
-        D.all_reduce(tt, op=D.ReduceOp.MAX)
-        pp = torch.tensor([pushes, e2e_pushes], dtype=torch.float64, device=dev)
-        D.all_reduce(pp)
-        t_max, e2e_max = tt.tolist()
-        tot_pushes, tot_e2e = pp.tolist()
-    value = tot_pushes / (t_max * 1e-3)
+        import torch.distributed as D
 
+        D.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2212_08836_gb300 as P
+
+    P.lib()
     pk, pk_kind = peaks()
-    avg_launch_ms = push_ms / max(push_launches, 1)
-    pushes_per_launch = pushes / max(push_launches, 1)
-    if FP64_FLOP_PER_PUSH is not None:
-        fp64_peak = args.fp64_peak_tflops
-        achieved = FP64_FLOP_PER_PUSH * pushes_per_launch / (avg_launch_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak, "traffic": TRAFFIC_PER_LAUNCH,
-                "kernel": "k_push_fp64", "peak_kind": "FP64 FMA rate (see DESIGN.md)"}
-    else:
-        achieved = BYTES_PER_PUSH_FP64 * pushes_per_launch / (avg_launch_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / pk["hbm_gbs"], "traffic": TRAFFIC_PER_LAUNCH,
-                "kernel": "k_push_fp64", "peak_kind": pk_kind}
-    roof["avg_launch_ms"] = avg_launch_ms
-    roof["launches"] = push_launches
+    sm_max = pk.get("sm_max_mhz", 2070.0)
 
+    def maxsum(t, n):
+        if not dist:
+            return t, n
+        tt = torch.tensor([t], dtype=torch.float64, device=dev)
+        D.all_reduce(tt, op=D.ReduceOp.MAX)
+        nn = torch.tensor([n], dtype=torch.float64, device=dev)
+        D.all_reduce(nn)
+        return tt.item(), nn.item()
+
+    forms = args.forms.split(",")
+    if "plain" not in forms:
+        # profiling aid: only the mixed form (no headline line is printed)
+        cfgm = P.large_reactor(seed=1 + rank, precision=P.PIC_MIXED)
+        if args.np:
+            cfgm["np_init"] = args.np
+        rm = measure(P, torch, dev, cfgm, args, dist, D, False, False, local)
+        if rank == 0:
+            print(json.dumps({"mixed_only": True, "ms_per_step": rm["t_ms"] / args.steps,
+                              "push_ms_per_launch": rm["push_ms"] / max(rm["push_launches"], 1)}))
+        return 0
+    # ---- plain FP64 method on the 256 x 384 reactor (the headline workload)
+    cfg = P.large_reactor(seed=1 + rank)
+    if args.np:
+        cfg["np_init"] = args.np
+    r = measure(P, torch, dev, cfg, args, dist, D, not args.no_e2e, True, local)
+    t_max, tot = maxsum(r["t_ms"], r["pushes"])
+    value = tot / (t_max * 1e-3)
+    avg_launch_ms = r["push_ms"] / max(r["push_launches"], 1)
+    pushes_per_launch = r["pushes"] / max(r["push_launches"], 1)
+    flop_per_push = r["flops"] / max(r["commit_pushes"], 1)
+    fp64_peak = DFMA_PER_CYCLE * 2 * sm_max * 1e6 / 1e12
+    achieved = flop_per_push * pushes_per_launch / (avg_launch_ms * 1e-3) / 1e12
+    hbm_achieved = r["bytes"] / (r["push_ms"] * 1e-3) / 1e9
+    roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp64_peak,
+            "traffic": TRAFFIC_PER_PUSH * pushes_per_launch if TRAFFIC_PER_PUSH else None,
+            "kernel": "k_push_fp64 (mover+deposit, FP64)",
+            "peak_kind": "FP64: 304 DFMA/cycle (ncu unit count) x 2 x max SM clock",
+            "flop_per_push": flop_per_push, "avg_launch_ms": avg_launch_ms,
+            "launches": r["push_launches"],
+            "hbm": {"achieved_gbs": hbm_achieved, "peak_gbs": pk["hbm_gbs"],
+                    "frac": hbm_achieved / pk["hbm_gbs"], "peak_kind": pk_kind}}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "large-electrode VHF reactor 256x384, R=0.3 m, L=0.03 m, Ar 2 Pa, "
-                                   "100 MHz 200 V, 16M macro-particles/species, FP64 plain, tol 1e-8",
+                                   "100 MHz 200 V, %d macro-particles/species, FP64 plain, tol 1e-8"
+                                   % cfg["np_init"],
                        "l2": "inputs larger than L2 (particle store ~1.9 GB)",
                        "parallelism": "replicas" if ws > 1 else "single GPU",
-                       "picard_iters": iters},
-            "clocks": clocks,
-            "e2e": {"value": tot_e2e / (e2e_max * 1e-3), "unit": UNIT,
-                    "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps},
-            "gpu_launches": launches,
+                       "picard_iters": r["iters"]},
+            "clocks": r.get("clocks"),
+            "gpu_launches": r["launches"],
             "roofline": roof}
+    if r["e2e_ms"] is not None:
+        te, ne = maxsum(r["e2e_ms"], r["e2e_pushes"])
+        line["e2e"] = {"value": ne / (te * 1e-3), "unit": UNIT,
+                       "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]}
+    steps_per_cycle = 1.0 / (cfg["dt"] * cfg["freq"])
+    wall = {"plain_fp64": t_max / args.steps * 1e-3 * steps_per_cycle}
+
+    # ---- mixed-precision form on the same reactor (FP32 push/deposit)
+    if "mixed" in forms:
+        cfgm = P.large_reactor(seed=1 + rank, precision=P.PIC_MIXED)
+        if args.np:
+            cfgm["np_init"] = args.np
+        rm = measure(P, torch, dev, cfgm, args, dist, D, False, False, local)
+        tm, totm = maxsum(rm["t_ms"], rm["pushes"])
+        alm = rm["push_ms"] / max(rm["push_launches"], 1)
+        hbm_m = rm["bytes"] / (rm["push_ms"] * 1e-3) / 1e9
+        fp32_peak = 128 * 2 * 152 * sm_max * 1e6 / 1e12
+        flm = rm["flops"] / max(rm["commit_pushes"], 1)
+        ppl = rm["pushes"] / max(rm["push_launches"], 1)
+        line["mixed_form"] = {
+            "value": totm / (tm * 1e-3), "unit": UNIT, "ms_per_step": tm / args.steps,
+            "dtype": "f32 particles / f64 fields", "picard_iters": rm["iters"],
+            "gpu_launches": rm["launches"],
+            "roofline": {"bound": "hbm", "achieved": hbm_m, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                         "frac": hbm_m / pk["hbm_gbs"], "traffic": None,
+                         "kernel": "k_push_fp32 (mover+deposit, FP32)", "peak_kind": pk_kind,
+                         "bytes_per_push": "28 read (+24 written in the commit pass)",
+                         "avg_launch_ms": alm, "launches": rm["push_launches"],
+                         "alu": {"flop_per_push": flm,
+                                 "achieved_tflops": flm * ppl / (alm * 1e-3) / 1e12,
+                                 "peak_tflops": fp32_peak,
+                                 "peak_kind": "FP32: 128 lanes x 152 SMs x 2 x max SM clock"}}}
+        wall["mixed"] = tm / args.steps * 1e-3 * steps_per_cycle
+    line["wall_s_per_rf_cycle"] = wall
+
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, secs, npush = cpu_oracle_rate(args.cpu_sample, steps=1)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -321,8 +387,12 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=1 << 22)
     ap.add_argument("--ref-sample", type=int, default=1 << 20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--fp64-peak-tflops", type=float, default=1.25)
+    ap.add_argument("--np", type=int, default=0, help="macro-particles per species (profiling runs)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--forms", default="plain,mixed",
+                    help="comma list of plain (FP64) and mixed (FP32 push) forms to time")
     args = ap.parse_args()
+    args.steps_e2e = args.steps
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

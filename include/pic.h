@@ -52,6 +52,8 @@ extern "C" {
 #define PIC_E_WORKSPACE -8 /* workspace missing, too small or misaligned */
 
 #define PIC_FP64 0         /* plain method: FP64 particles, push and deposit */
+#define PIC_MIXED 1        /* FP32 particle state, push and deposit; FP64 field solve,
+                              Picard norms, current accumulation and diagnostics */
 
 typedef struct pic_ctx pic_ctx; /* opaque; host memory owned by the library */
 
@@ -73,7 +75,7 @@ typedef struct pic_config {
   double bz;                  /* external uniform B_z [T]; 0 in production (Sec. 2.1) */
   double eps, mu;             /* permittivity / permeability; 0 -> eps0 / mu0 */
   unsigned long long seed;    /* RNG key word (Philox4x64-10) */
-  int precision;              /* PIC_FP64 */
+  int precision;              /* PIC_FP64 or PIC_MIXED */
 } pic_config;
 
 /* Per-step statistics (host struct). */
@@ -92,18 +94,20 @@ typedef struct pic_step_stats {
   long long n[2];             /* macro-particles per species after the step */
   long long pushes;           /* particle pushes performed by the step (all passes) */
   long long launches;         /* kernels launched by the step */
+  long long push_flops;       /* algorithmic FP64 operations of the commit pass */
 } pic_step_stats;
 
 /* Device pointers and sizes of the context's arrays (for parity tests,
  * checkpoints and callers that fill state directly). */
 typedef struct pic_view {
   int32_t *cell[2];
-  double *a[2], *b[2], *vr[2], *vt[2], *vz[2], *w[2];
+  void *a[2], *b[2], *vr[2], *vt[2], *vz[2], *w[2]; /* double (PIC_FP64) or float (PIC_MIXED) */
   uint32_t *id[2];
   long long n[2], cap[2];
   uint32_t next_id[2];
   double *er, *ez, *h;        /* E^n, H^n */
   long long step;             /* index n of the next step */
+  int real_size;              /* bytes per element of a..w: 8 or 4 */
 } pic_view;
 
 /* Conservation diagnostics (row a9), host struct filled by pic_diag. */
@@ -152,8 +156,9 @@ int pic_step(pic_ctx *ctx, int nsteps, pic_step_stats *stats);
  * er_half_dev / ez_half_dev (layout above).  Adds the crossed charges into
  * ir_dev / iz_dev (caller zeroes them).  write = 0 leaves the particles
  * untouched; write = 1 stores state n+1 (cell -1 for absorbed particles).
- * counters_dev (nullable, 4 x uint64): substep errors, absorbed, substeps,
- * fallbacks; ke_lost_dev (nullable, double): absorbed kinetic energy.
+ * counters_dev (nullable, 5 x uint64): substep errors, absorbed, substeps,
+ * fallbacks, algorithmic FP64 operations (add/sub/mul/div of the source);
+ * ke_lost_dev (nullable, double): absorbed kinetic energy.
  * Asynchronous.  Errors: PIC_E_CONFIG, PIC_E_CUDA. */
 int pic_push_deposit(pic_ctx *ctx, const double *er_half_dev, const double *ez_half_dev,
                      double *ir_dev, double *iz_dev, int write,

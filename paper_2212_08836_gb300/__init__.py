@@ -27,6 +27,7 @@ PIC_E_NAN = -6
 PIC_E_STATE = -7
 PIC_E_WORKSPACE = -8
 PIC_FP64 = 0
+PIC_MIXED = 1
 
 _P = C.c_void_p
 _D = C.c_double
@@ -46,7 +47,7 @@ class StepStats(C.Structure):
     _fields_ = [("picard_iters", _I), ("converged", _I), ("last_res", _D), ("src_energy", _D),
                 ("ke_lost", _D), ("de_coll", _D), ("substep_err", _LL), ("absorbed", _LL),
                 ("substeps", _LL), ("fallbacks", _LL), ("mcc", _LL * 8), ("n", _LL * 2),
-                ("pushes", _LL), ("launches", _LL)]
+                ("pushes", _LL), ("launches", _LL), ("push_flops", _LL)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("mcc", "n")}
@@ -58,7 +59,8 @@ class StepStats(C.Structure):
 class View(C.Structure):
     _fields_ = [("cell", _P * 2), ("a", _P * 2), ("b", _P * 2), ("vr", _P * 2), ("vt", _P * 2),
                 ("vz", _P * 2), ("w", _P * 2), ("id", _P * 2), ("n", _LL * 2), ("cap", _LL * 2),
-                ("next_id", C.c_uint32 * 2), ("er", _P), ("ez", _P), ("h", _P), ("step", _LL)]
+                ("next_id", C.c_uint32 * 2), ("er", _P), ("ez", _P), ("h", _P), ("step", _LL),
+                ("real_size", _I)]
 
 
 class DiagOut(C.Structure):
@@ -258,10 +260,12 @@ class Pic:
         v = self._raw_view()
         out = {"n": list(v.n), "cap": list(v.cap), "next_id": list(v.next_id), "step": v.step,
                "species": []}
+        real = t.float32 if v.real_size == 4 else t.float64
         dt = {"cell": t.int32, "id": t.int32}
         for s in range(2):
             out["species"].append({k: self._tensor(getattr(v, k)[s], v.cap[s],
-                                                   dt.get(k, t.float64)) for k in FIELDS})
+                                                   dt.get(k, real)) for k in FIELDS})
+        out["real_dtype"] = real
         nr, nz = self.nr, self.nz
         out["er"] = self._tensor(v.er, nr * (nz + 1), t.float64)
         out["ez"] = self._tensor(v.ez, (nr + 1) * nz, t.float64)
@@ -277,10 +281,14 @@ class Pic:
             n = len(sp["cell"])
             if n > v["cap"][s]:
                 raise PicError(PIC_E_STATE, "set_state")
+            real = np.float32 if v["real_dtype"] == t.float32 else np.float64
             for k in FIELDS:
-                src = np.ascontiguousarray(sp[k])
                 if k == "id":
-                    src = src.astype(np.uint32).view(np.int32)
+                    src = np.ascontiguousarray(sp[k]).astype(np.uint32).view(np.int32)
+                elif k == "cell":
+                    src = np.ascontiguousarray(sp[k], dtype=np.int32)
+                else:
+                    src = np.ascontiguousarray(sp[k], dtype=real)
                 v["species"][s][k][:n].copy_(t.from_numpy(src))
             ns.append(n)
         for name, arr in (("er", er), ("ez", ez), ("h", h)):

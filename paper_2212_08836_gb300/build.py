@@ -26,6 +26,7 @@ UNITS = {
     "load_diag.cu": ["--fmad=false"],
     "pic_api.cu": ["--fmad=false"],
     "sort_noalloc.cu": [],
+    "push_fp32.cu": ["--use_fast_math"],
 }
 
 

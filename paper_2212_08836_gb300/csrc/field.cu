@@ -32,6 +32,25 @@ __global__ void k_half(long long n1, long long n2, const double *er0, const doub
   }
 }
 
+// half-step field plus the mixed form's normalised accelerations per species
+__global__ void k_half_alpha(long long n1, long long n2, const double *er0, const double *ez0,
+                             const double *er1, const double *ez1, double *erh, double *ezh,
+                             AlphaOut A) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n1) {
+    double e = 0.5 * (er0[t] + er1[t]);
+    erh[t] = e;
+    A.ar[0][t] = (float)(A.sr[0] * e);
+    A.ar[1][t] = (float)(A.sr[1] * e);
+  } else if (t < n1 + n2) {
+    long long u = t - n1;
+    double e = 0.5 * (ez0[u] + ez1[u]);
+    ezh[u] = e;
+    A.az[0][u] = (float)(A.sz[0] * e);
+    A.az[1][u] = (float)(A.sz[1] * e);
+  }
+}
+
 // rhs(i,j) = 2 mu Vh H0 - dt * C^T L Et   (Et = E0 - dQ/(2 eps A), or the prescribed half value)
 __global__ void k_rhs(FieldOp F, const double *er0, const double *ez0, const double *h0,
                       const double *ir, const double *iz, double v0, double v1) {
@@ -219,6 +238,16 @@ cudaError_t launch_half_field(const Grid &g, const double *er0, const double *ez
   return cudaGetLastError();
 }
 
+cudaError_t launch_half_field_alpha(const Grid &g, const double *er0, const double *ez0,
+                                    const double *er1, const double *ez1, double *erh,
+                                    double *ezh, const AlphaOut &A, cudaStream_t s) {
+  long long n1 = (long long)g.nr * (g.nz + 1), n2 = (long long)(g.nr + 1) * g.nz;
+  long long n = n1 + n2;
+  k_half_alpha<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n1, n2, er0, ez0, er1, ez1, erh, ezh,
+                                                           A);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_field_solve(const FieldOp &F, const double *er0, const double *ez0,
                                const double *h0, const double *ir, const double *iz, double v0,
                                double v1, double *er1, double *ez1, double *h1, const double *er_it,
@@ -229,7 +258,8 @@ cudaError_t launch_field_solve(const FieldOp &F, const double *er0, const double
   k_rhs<<<(nc + 255) / 256, 256, 0, s>>>(F, er0, ez0, h0, ir, iz, v0, v1);
   dim3 grid((F.nz + TM - 1) / TM, (F.nr + TM - 1) / TM);
   k_gemm<<<grid, 256, 0, s>>>(F.nr, F.nz, F.nz, F.rhs, F.Q, F.hat);
-  int mb = 16;
+  // few modes per block so that many blocks stage their columns in parallel
+  int mb = 2;
   while (mb > 1 && (size_t)3 * F.nr * mb * sizeof(double) > 200 * 1024) mb >>= 1;
   size_t smem = (size_t)3 * F.nr * mb * sizeof(double);
   static bool attr_set = false;
@@ -237,7 +267,7 @@ cudaError_t launch_field_solve(const FieldOp &F, const double *er0, const double
     cudaFuncSetAttribute(k_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
     attr_set = true;
   }
-  k_tridiag<<<(F.nz + mb - 1) / mb, 64, smem, s>>>(F, mb);
+  k_tridiag<<<(F.nz + mb - 1) / mb, 256, smem, s>>>(F, mb);
   k_gemm<<<grid, 256, 0, s>>>(F.nr, F.nz, F.nz, F.hat, F.QT, F.hhalf);
   long long ner = (long long)F.nr * (F.nz + 1), nez = (long long)(F.nr + 1) * F.nz;
   long long n = ner > nez ? ner : nez;

@@ -6,8 +6,10 @@
 namespace pic {
 namespace {
 
+template <typename T>
 __global__ void __launch_bounds__(256) k_load(Grid g, long long n, double n0, double vthe,
-                                              double vthi, uint64_t seed, Parts e, Parts i) {
+                                              double vthi, uint64_t seed, PartsT<T> e,
+                                              PartsT<T> i) {
   long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   double u[4];
@@ -20,17 +22,17 @@ __global__ void __launch_bounds__(256) k_load(Grid g, long long n, double n0, do
   int32_t cell = ic * g.nz + jc;
   double a = xi - (double)ic, b = eta - (double)jc;
   double w = n0 * (kTwoPi * (xi * g.dr)) * g.R * g.L / (double)n;
-  e.cell[p] = cell; e.a[p] = a; e.b[p] = b; e.w[p] = w; e.id[p] = (uint32_t)p;
-  i.cell[p] = cell; i.a[p] = a; i.b[p] = b; i.w[p] = w; i.id[p] = (uint32_t)p;
+  e.cell[p] = cell; e.a[p] = (T)a; e.b[p] = (T)b; e.w[p] = (T)w; e.id[p] = (uint32_t)p;
+  i.cell[p] = cell; i.a[p] = (T)a; i.b[p] = (T)b; i.w[p] = (T)w; i.id[p] = (uint32_t)p;
   double g1, g2, g3, g4;
   draw4(seed, kStreamLoadVe, (uint64_t)p, kLoadStep, 0, u);
   gauss2(u[0], u[1], g1, g2);
   gauss2(u[2], u[3], g3, g4);
-  e.vr[p] = vthe * g1; e.vt[p] = vthe * g2; e.vz[p] = vthe * g3;
+  e.vr[p] = (T)(vthe * g1); e.vt[p] = (T)(vthe * g2); e.vz[p] = (T)(vthe * g3);
   draw4(seed, kStreamLoadVi, (uint64_t)p, kLoadStep, 0, u);
   gauss2(u[0], u[1], g1, g2);
   gauss2(u[2], u[3], g3, g4);
-  i.vr[p] = vthi * g1; i.vt[p] = vthi * g2; i.vz[p] = vthi * g3;
+  i.vr[p] = (T)(vthi * g1); i.vt[p] = (T)(vthi * g2); i.vz[p] = (T)(vthi * g3);
 }
 
 __device__ __forceinline__ double wsum(double v) {
@@ -55,12 +57,13 @@ __device__ void block_add2(double x, double y, double *out) {
   }
 }
 
-__global__ void __launch_bounds__(256) k_kinetic(Parts p, long long n, double m, double q,
+template <typename T>
+__global__ void __launch_bounds__(256) k_kinetic(PartsT<T> p, long long n, double m, double q,
                                                  double *out2) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double k = 0.0, c = 0.0;
   if (t < n && p.cell[t] >= 0) {
-    double vr = p.vr[t], vt = p.vt[t], vz = p.vz[t], w = p.w[t];
+    double vr = (double)p.vr[t], vt = (double)p.vt[t], vz = (double)p.vz[t], w = (double)p.w[t];
     k = 0.5 * m * w * (vr * vr + vt * vt + vz * vz);
     c = q * w;
   }
@@ -98,7 +101,8 @@ __global__ void __launch_bounds__(256) k_field_energy(Grid g, double eps, double
   block_add2(W, 0.0, out);
 }
 
-__global__ void __launch_bounds__(256) k_node_charge(Grid g, Parts p, long long n, double q,
+template <typename T>
+__global__ void __launch_bounds__(256) k_node_charge(Grid g, PartsT<T> p, long long n, double q,
                                                      double *Q) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
@@ -106,7 +110,7 @@ __global__ void __launch_bounds__(256) k_node_charge(Grid g, Parts p, long long 
   if (c < 0) return;
   int nz = g.nz, nz1 = nz + 1;
   int ic = c / nz, jc = c - (c / nz) * nz;
-  double a = p.a[t], b = p.b[t], qw = q * p.w[t];
+  double a = (double)p.a[t], b = (double)p.b[t], qw = q * (double)p.w[t];
   atomicAdd(&Q[ic * nz1 + jc], qw * (1.0 - a) * (1.0 - b));
   atomicAdd(&Q[(ic + 1) * nz1 + jc], qw * a * (1.0 - b));
   atomicAdd(&Q[ic * nz1 + jc + 1], qw * (1.0 - a) * b);
@@ -115,18 +119,20 @@ __global__ void __launch_bounds__(256) k_node_charge(Grid g, Parts p, long long 
 
 }  // namespace
 
+template <typename T>
 cudaError_t launch_load(const Grid &g, long long n, double n0, double te_ev, double ti_ev,
-                        uint64_t seed, Parts e, Parts i, cudaStream_t s) {
+                        uint64_t seed, PartsT<T> e, PartsT<T> i, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   double vthe = sqrt(te_ev * kQE / kME), vthi = sqrt(ti_ev * kQE / kMAr);
-  k_load<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, n, n0, vthe, vthi, seed, e, i);
+  k_load<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, n, n0, vthe, vthi, seed, e, i);
   return cudaGetLastError();
 }
 
-cudaError_t launch_kinetic(const Parts &p, long long n, double m, double q, double *out2,
+template <typename T>
+cudaError_t launch_kinetic(const PartsT<T> &p, long long n, double m, double q, double *out2,
                            cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_kinetic<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, n, m, q, out2);
+  k_kinetic<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, n, m, q, out2);
   return cudaGetLastError();
 }
 
@@ -137,11 +143,23 @@ cudaError_t launch_field_energy(const Grid &g, double eps, double mu, const doub
   return cudaGetLastError();
 }
 
-cudaError_t launch_node_charge(const Grid &g, const Parts &p, long long n, double q, double *Q,
-                               cudaStream_t s) {
+template <typename T>
+cudaError_t launch_node_charge(const Grid &g, const PartsT<T> &p, long long n, double q,
+                               double *Q, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  k_node_charge<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, p, n, q, Q);
+  k_node_charge<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, p, n, q, Q);
   return cudaGetLastError();
 }
+
+#define PIC_INST(T)                                                                            \
+  template cudaError_t launch_load<T>(const Grid &, long long, double, double, double,          \
+                                      uint64_t, PartsT<T>, PartsT<T>, cudaStream_t);            \
+  template cudaError_t launch_kinetic<T>(const PartsT<T> &, long long, double, double,          \
+                                         double *, cudaStream_t);                                \
+  template cudaError_t launch_node_charge<T>(const Grid &, const PartsT<T> &, long long,        \
+                                             double, double *, cudaStream_t);
+PIC_INST(double)
+PIC_INST(float)
+#undef PIC_INST
 
 }  // namespace pic

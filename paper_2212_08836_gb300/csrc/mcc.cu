@@ -46,7 +46,8 @@ __device__ __forceinline__ double wsumd(double v) {
   return v;
 }
 
-__global__ void __launch_bounds__(256) k_mcc(MccLaunch M) {
+template <typename T>
+__global__ void __launch_bounds__(256) k_mcc(MccLaunchT<T> M) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long c[7] = {0, 0, 0, 0, 0, 0, 0};
   double de = 0.0;
@@ -54,11 +55,12 @@ __global__ void __launch_bounds__(256) k_mcc(MccLaunch M) {
     long long p = t;
     int32_t flag = 0;
     if (M.e.cell[p] >= 0) {
-      double u[4];
-      draw4(M.seed, kStreamMccE, M.e.id[p], M.step, 0, u);
-      if (u[0] < M.pnull_e) {
+      uint64_t c4[4] = {(uint64_t)M.e.id[p], M.step, 0, 0};
+      philox4x64(c4, M.seed, kStreamMccE);
+      if ((c4[0] >> 11) < M.thr_e) {
+        double u[4] = {u01(c4[0]), u01(c4[1]), u01(c4[2]), u01(c4[3])};
         c[0]++;
-        double vr = M.e.vr[p], vt = M.e.vt[p], vz = M.e.vz[p];
+        double vr = (double)M.e.vr[p], vt = (double)M.e.vt[p], vz = (double)M.e.vz[p];
         double v2 = vr * vr + vt * vt + vz * vz;
         double v = sqrt(v2);
         double eps = 0.5 * kME * v2 / kQE;
@@ -66,7 +68,7 @@ __global__ void __launch_bounds__(256) k_mcc(MccLaunch M) {
         double nu_ex = M.ng * sig_ex(eps) * v;
         double nu_iz = M.ng * sig_iz(eps) * v;
         double x = u[1] * M.numax_e;
-        double w = M.e.w[p];
+        double w = (double)M.e.w[p];
         double ke0 = 0.5 * kME * w * v2;
         bool hit = true;
         double nr_, nt_, nz_, v1;
@@ -90,11 +92,12 @@ __global__ void __launch_bounds__(256) k_mcc(MccLaunch M) {
           v1 = 0.0;
         }
         if (hit) {
-          double nvr = v1 * nr_, nvt = v1 * nt_, nvz = v1 * nz_;
+          T nvr = (T)(v1 * nr_), nvt = (T)(v1 * nt_), nvz = (T)(v1 * nz_);
           M.e.vr[p] = nvr;
           M.e.vt[p] = nvt;
           M.e.vz[p] = nvz;
-          de += 0.5 * kME * w * (nvr * nvr + nvt * nvt + nvz * nvz) - ke0;
+          double r2 = (double)nvr * (double)nvr + (double)nvt * (double)nvt + (double)nvz * (double)nvz;
+          de += 0.5 * kME * w * r2 - ke0;
         }
       }
     }
@@ -103,9 +106,10 @@ __global__ void __launch_bounds__(256) k_mcc(MccLaunch M) {
   if (t < M.ni) {
     long long p = t;
     if (M.i.cell[p] >= 0) {
-      double u[4];
-      draw4(M.seed, kStreamMccI, M.i.id[p], M.step, 0, u);
-      if (u[0] < M.pnull_i) {
+      uint64_t c4[4] = {(uint64_t)M.i.id[p], M.step, 0, 0};
+      philox4x64(c4, M.seed, kStreamMccI);
+      if ((c4[0] >> 11) < M.thr_i) {
+        double u[4] = {u01(c4[0]), u01(c4[1]), u01(c4[2]), u01(c4[3])};
         c[4]++;
         double u1[4];
         draw4(M.seed, kStreamMccI, M.i.id[p], M.step, 1, u1);
@@ -114,17 +118,19 @@ __global__ void __launch_bounds__(256) k_mcc(MccLaunch M) {
         gauss2(u1[0], u1[1], g3, g4);
         double vthg = sqrt(kKB * M.tg / kMAr);
         double wr = vthg * g1, wt = vthg * g2, wz = vthg * g3;
-        double vr = M.i.vr[p], vt = M.i.vt[p], vz = M.i.vz[p];
+        double vr = (double)M.i.vr[p], vt = (double)M.i.vt[p], vz = (double)M.i.vz[p];
         double dr_ = vr - wr, dt_ = vt - wt, dz_ = vz - wz;
         double g = sqrt(dr_ * dr_ + dt_ * dt_ + dz_ * dz_);
         if (g > M.gmax) c[6]++;
         if (u[1] * M.gmax < g) {
-          double w = M.i.w[p];
+          double w = (double)M.i.w[p];
           double ke0 = 0.5 * kMAr * w * (vr * vr + vt * vt + vz * vz);
-          M.i.vr[p] = wr;
-          M.i.vt[p] = wt;
-          M.i.vz[p] = wz;
-          de += 0.5 * kMAr * w * (wr * wr + wt * wt + wz * wz) - ke0;
+          T nr = (T)wr, nt = (T)wt, nz = (T)wz;
+          M.i.vr[p] = nr;
+          M.i.vt[p] = nt;
+          M.i.vz[p] = nz;
+          double r2 = (double)nr * (double)nr + (double)nt * (double)nt + (double)nz * (double)nz;
+          de += 0.5 * kMAr * w * r2 - ke0;
           c[5]++;
         }
       }
@@ -141,7 +147,8 @@ __global__ void __launch_bounds__(256) k_mcc(MccLaunch M) {
 }
 
 // new pairs for flagged electrons: electron at ne_new0 + k, ion at ni_new0 + k
-__global__ void __launch_bounds__(256) k_append(MccLaunch M, long long ne0, long long ni0,
+template <typename T>
+__global__ void __launch_bounds__(256) k_append(MccLaunchT<T> M, long long ne0, long long ni0,
                                                 uint32_t id_e0, uint32_t id_i0) {
   long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double de = 0.0;
@@ -150,15 +157,16 @@ __global__ void __launch_bounds__(256) k_append(MccLaunch M, long long ne0, long
     double u1[4], u2[4];
     draw4(M.seed, kStreamMccE, M.e.id[p], M.step, 1, u1);
     draw4(M.seed, kStreamMccE, M.e.id[p], M.step, 2, u2);
-    double vr = M.e.vr[p], vt = M.e.vt[p], vz = M.e.vz[p];
+    double vr = (double)M.e.vr[p], vt = (double)M.e.vt[p], vz = (double)M.e.vz[p];
     double v1 = sqrt(vr * vr + vt * vt + vz * vz);  // the parent's share: equal split
     double mr, mt, mz;
     iso_dir(u1[0], u1[1], mr, mt, mz);
     long long q = ne0 + k;
     int32_t cell = M.e.cell[p];
-    double a = M.e.a[p], b = M.e.b[p], w = M.e.w[p];
+    T a = M.e.a[p], b = M.e.b[p], w = M.e.w[p];
     M.e.cell[q] = cell; M.e.a[q] = a; M.e.b[q] = b; M.e.w[q] = w;
-    M.e.vr[q] = v1 * mr; M.e.vt[q] = v1 * mt; M.e.vz[q] = v1 * mz;
+    T er = (T)(v1 * mr), et = (T)(v1 * mt), ez = (T)(v1 * mz);
+    M.e.vr[q] = er; M.e.vt[q] = et; M.e.vz[q] = ez;
     M.e.id[q] = id_e0 + (uint32_t)k;
     double g1, g2, g3, g4;
     gauss2(u1[2], u1[3], g1, g2);
@@ -166,10 +174,13 @@ __global__ void __launch_bounds__(256) k_append(MccLaunch M, long long ne0, long
     double vthg = sqrt(kKB * M.tg / kMAr);
     long long s = ni0 + k;
     M.i.cell[s] = cell; M.i.a[s] = a; M.i.b[s] = b; M.i.w[s] = w;
-    double ir = vthg * g1, it = vthg * g2, iz = vthg * g3;
+    T ir = (T)(vthg * g1), it = (T)(vthg * g2), iz = (T)(vthg * g3);
     M.i.vr[s] = ir; M.i.vt[s] = it; M.i.vz[s] = iz;
     M.i.id[s] = id_i0 + (uint32_t)k;
-    de = 0.5 * kME * w * (v1 * v1) + 0.5 * kMAr * w * (ir * ir + it * it + iz * iz);
+    double wd = (double)w;
+    double e2 = (double)er * (double)er + (double)et * (double)et + (double)ez * (double)ez;
+    double i2 = (double)ir * (double)ir + (double)it * (double)it + (double)iz * (double)iz;
+    de = 0.5 * kME * wd * e2 + 0.5 * kMAr * wd * i2;
   }
   de = wsumd(de);
   if ((threadIdx.x & 31) == 0 && de != 0.0) atomicAdd(&M.cnt->de_coll, de);
@@ -177,18 +188,27 @@ __global__ void __launch_bounds__(256) k_append(MccLaunch M, long long ne0, long
 
 }  // namespace
 
-cudaError_t launch_mcc_collide(const MccLaunch &M, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_mcc_collide(const MccLaunchT<T> &M, cudaStream_t s) {
   long long n = M.ne > M.ni ? M.ne : M.ni;
   if (n <= 0) return cudaSuccess;
-  k_mcc<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(M);
+  k_mcc<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(M);
   return cudaGetLastError();
 }
 
-cudaError_t launch_mcc_append(const MccLaunch &M, long long ne0, long long ni0, uint32_t id_e0,
-                              uint32_t id_i0, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_mcc_append(const MccLaunchT<T> &M, long long ne0, long long ni0,
+                              uint32_t id_e0, uint32_t id_i0, cudaStream_t s) {
   if (M.ne <= 0) return cudaSuccess;
-  k_append<<<(unsigned)((M.ne + 255) / 256), 256, 0, s>>>(M, ne0, ni0, id_e0, id_i0);
+  k_append<T><<<(unsigned)((M.ne + 255) / 256), 256, 0, s>>>(M, ne0, ni0, id_e0, id_i0);
   return cudaGetLastError();
 }
+
+template cudaError_t launch_mcc_collide<double>(const MccLaunchT<double> &, cudaStream_t);
+template cudaError_t launch_mcc_collide<float>(const MccLaunchT<float> &, cudaStream_t);
+template cudaError_t launch_mcc_append<double>(const MccLaunchT<double> &, long long, long long,
+                                               uint32_t, uint32_t, cudaStream_t);
+template cudaError_t launch_mcc_append<float>(const MccLaunchT<float> &, long long, long long,
+                                              uint32_t, uint32_t, cudaStream_t);
 
 }  // namespace pic

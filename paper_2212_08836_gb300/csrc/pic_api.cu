@@ -22,8 +22,13 @@ struct pic_ctx {
   long long cap[2], n[2];
   uint32_t next_id[2];
   long long step;
-  Parts P[2][2];
+  Parts P[2][2];             // in the mixed form the real arrays hold float
   int cur[2];
+  int mixed;                 // 1: FP32 particle store and push (PIC_MIXED)
+  AlphaOut alpha;            // mixed form: normalised accelerations per species
+  int *queue, *qcount;       // mixed form: work queue of the general push path
+  int *q_cell;
+  float *q_real[6];
   double *er, *ez, *h;      // E^n, H^n
   double *er1, *ez1;        // Picard iterate E^{n+1,k}
   double *er2, *ez2, *h2;   // solver output
@@ -84,7 +89,7 @@ bool valid(const pic_config *c) {
   if (!(c->R > 0) || !(c->L > 0) || !(c->dt > 0)) return false;
   if (c->np_init < 0 || !(c->capacity_factor >= 1.0)) return false;
   if (!(c->picard_tol > 0) || c->picard_max < 1) return false;
-  if (c->precision != PIC_FP64) return false;
+  if (c->precision != PIC_FP64 && c->precision != PIC_MIXED) return false;
   if (c->mcc_on && (!(c->gas_pressure > 0) || !(c->gas_temp > 0))) return false;
   return true;
 }
@@ -100,19 +105,30 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
   Carver K{base, 0, cap, true};
   int nr = c->nr, nz = c->nz;
   long long pc = capacity(c);
+  size_t rs = c->precision == PIC_MIXED ? 4 : 8;
   size_t ner = (size_t)nr * (nz + 1), nez = (size_t)(nr + 1) * nz, nh = (size_t)nr * nz;
   for (int s = 0; s < 2; ++s)
     for (int b = 0; b < 2; ++b) {
       Parts &P = x->P[s][b];
       P.cell = (int32_t *)K.take(pc * 4);
-      P.a = (double *)K.take(pc * 8);
-      P.b = (double *)K.take(pc * 8);
-      P.vr = (double *)K.take(pc * 8);
-      P.vt = (double *)K.take(pc * 8);
-      P.vz = (double *)K.take(pc * 8);
-      P.w = (double *)K.take(pc * 8);
+      P.a = (double *)K.take(pc * rs);
+      P.b = (double *)K.take(pc * rs);
+      P.vr = (double *)K.take(pc * rs);
+      P.vt = (double *)K.take(pc * rs);
+      P.vz = (double *)K.take(pc * rs);
+      P.w = (double *)K.take(pc * rs);
       P.id = (uint32_t *)K.take(pc * 4);
     }
+  if (c->precision == PIC_MIXED) {
+    for (int s = 0; s < 2; ++s) {
+      x->alpha.ar[s] = (float *)K.take(ner * 4);
+      x->alpha.az[s] = (float *)K.take(nez * 4);
+    }
+    x->queue = (int *)K.take(pc * 4);
+    x->qcount = (int *)K.take(256);
+    x->q_cell = (int *)K.take(pc * 4);
+    for (int k = 0; k < 6; ++k) x->q_real[k] = (float *)K.take(pc * 4);
+  }
   x->er = (double *)K.take(ner * 8);
   x->ez = (double *)K.take(nez * 8);
   x->h = (double *)K.take(nh * 8);
@@ -153,6 +169,12 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
 int cuda_rc(cudaError_t e) { return e == cudaSuccess ? PIC_OK : PIC_E_CUDA; }
 
 Parts &cur(pic_ctx *x, int s) { return x->P[s][x->cur[s]]; }
+
+// the same arrays seen with the element type of the mixed form
+Parts32 as32(const Parts &p) {
+  return Parts32{p.cell, (float *)p.a, (float *)p.b, (float *)p.vr, (float *)p.vt,
+                 (float *)p.vz, (float *)p.w, p.id};
+}
 
 double volt_at(const pic_ctx *x, long long step) {
   double t = (double)step * x->cfg.dt;
@@ -205,7 +227,46 @@ int push_all(pic_ctx *x, const double *erh, const double *ezh, double *ir, doubl
     }
     L.counters = counters;
     L.ke_lost = kel;
-    cudaError_t e = launch_push_fp64(L, x->s);
+    cudaError_t e;
+    if (x->mixed) {
+      PushLaunch32 M;
+      M.g = x->g;
+      M.q = L.q;
+      M.m = L.m;
+      M.dt = L.dt;
+      M.cr = (float)(x->cfg.dt / x->g.dr);
+      M.cz = (float)(x->cfg.dt / x->g.dz);
+      M.icr = (float)(x->g.dr / x->cfg.dt);
+      M.icz = (float)(x->g.dz / x->cfg.dt);
+      M.inz = 1.0f / (float)x->g.nz;
+      M.queue = x->queue;
+      M.qcount = x->qcount;
+      M.q_cell = x->q_cell;
+      M.q_a = x->q_real[0];
+      M.q_b = x->q_real[1];
+      M.q_ur = x->q_real[2];
+      M.q_ut = x->q_real[3];
+      M.q_uz = x->q_real[4];
+      M.q_w = x->q_real[5];
+      M.wbt = (float)(L.wb * x->cfg.dt);
+      M.n = L.n;
+      M.p = as32(L.p);
+      M.ar = x->alpha.ar[s];
+      M.az = x->alpha.az[s];
+      M.qf = (float)L.q;
+      M.ir = ir;
+      M.iz = iz;
+      M.write = write;
+      M.wall_z0 = L.wall_z0;
+      M.wall_zl = L.wall_zl;
+      M.wall_r = L.wall_r;
+      M.counters = counters;
+      M.ke_lost = kel;
+      e = launch_push_fp32(M, x->s);
+      if (L.n > 0) x->launches += M.wbt == 0.f ? 1 : 0;  // fast + general kernels
+    } else {
+      e = launch_push_fp64(L, x->s);
+    }
     if (e != cudaSuccess) return PIC_E_CUDA;
     if (L.n > 0) {
       x->launches += 1;
@@ -277,6 +338,12 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
   x->eps = cfg->eps > 0 ? cfg->eps : kEps0;
   x->mu = cfg->mu > 0 ? cfg->mu : kMu0;
   x->cap[0] = x->cap[1] = capacity(cfg);
+  x->mixed = cfg->precision == PIC_MIXED ? 1 : 0;
+  for (int sp = 0; sp < 2; ++sp) {
+    double qm = sp == 0 ? -kQE / kME : kQE / kMAr;
+    x->alpha.sr[sp] = qm * cfg->dt * cfg->dt / x->g.dr;
+    x->alpha.sz[sp] = qm * cfg->dt * cfg->dt / x->g.dz;
+  }
   x->ng = cfg->mcc_on ? cfg->gas_pressure / (kKB * cfg->gas_temp) : 0.0;
 
   // MCC constants (host): nu_max over eps <= 1 keV (x 1.01), ion g_max
@@ -418,7 +485,15 @@ int pic_sort(pic_ctx *x) {
     S.cursor = x->cursor;
     S.total = x->total;
     S.scan_scratch = x->scan_scratch;
-    if (launch_sort(S, x->s) != cudaSuccess) return PIC_E_CUDA;
+    cudaError_t se;
+    if (x->mixed) {
+      SortLaunchT<float> S32{S.ncell, S.n, as32(S.src), as32(S.dst), S.counts, S.offs,
+                             S.cursor, S.total, S.scan_scratch};
+      se = launch_sort(S32, x->s);
+    } else {
+      se = launch_sort(S, x->s);
+    }
+    if (se != cudaSuccess) return PIC_E_CUDA;
     x->launches += S.n > 0 ? 5 : 3;
     long long tot = 0;
     if (cudaMemcpyAsync(&tot, x->total, 8, cudaMemcpyDeviceToHost, x->s) != cudaSuccess)
@@ -434,9 +509,12 @@ int pic_load_particles(pic_ctx *x) {
   if (!x) return PIC_E_CONFIG;
   long long n = x->cfg.np_init;
   if (n > x->cap[0] || n > x->cap[1] || n > 0xFFFFFFFFll) return PIC_E_CAPACITY;
-  if (launch_load(x->g, n, x->cfg.n0, x->cfg.te_ev, x->cfg.ti_ev, x->cfg.seed, cur(x, 0),
-                  cur(x, 1), x->s) != cudaSuccess)
-    return PIC_E_CUDA;
+  cudaError_t le =
+      x->mixed ? launch_load(x->g, n, x->cfg.n0, x->cfg.te_ev, x->cfg.ti_ev, x->cfg.seed,
+                             as32(cur(x, 0)), as32(cur(x, 1)), x->s)
+               : launch_load(x->g, n, x->cfg.n0, x->cfg.te_ev, x->cfg.ti_ev, x->cfg.seed,
+                             cur(x, 0), cur(x, 1), x->s);
+  if (le != cudaSuccess) return PIC_E_CUDA;
   if (n > 0) x->launches += 1;
   x->n[0] = x->n[1] = n;
   x->next_id[0] = x->next_id[1] = (uint32_t)n;
@@ -446,6 +524,13 @@ int pic_load_particles(pic_ctx *x) {
 int pic_push_deposit(pic_ctx *x, const double *erh, const double *ezh, double *ir, double *iz,
                      int write, unsigned long long *counters, double *kel) {
   if (!x || !erh || !ezh) return PIC_E_CONFIG;
+  if (x->mixed) {
+    // normalised accelerations of both species from the caller's E^{n+1/2}
+    if (launch_half_field_alpha(x->g, erh, ezh, erh, ezh, x->erh, x->ezh, x->alpha, x->s) !=
+        cudaSuccess)
+      return PIC_E_CUDA;
+    x->launches += 1;
+  }
   return push_all(x, erh, ezh, ir, iz, write, counters, kel, write ? x->wall : nullptr);
 }
 
@@ -474,6 +559,8 @@ int pic_mcc(pic_ctx *x, unsigned long long step, long long *counts, double *de_c
   M.pnull_e = x->pnull_e;
   M.pnull_i = x->pnull_i;
   M.gmax = x->gmax;
+  M.thr_e = (uint64_t)ceil(x->pnull_e * 9007199254740992.0);
+  M.thr_i = (uint64_t)ceil(x->pnull_i * 9007199254740992.0);
   M.ne = x->n[0];
   M.ni = x->n[1];
   M.e = cur(x, 0);
@@ -481,7 +568,10 @@ int pic_mcc(pic_ctx *x, unsigned long long step, long long *counts, double *de_c
   M.flag = x->flag;
   M.offs = x->offs;
   M.cnt = x->cnt;
-  if (e == cudaSuccess) e = launch_mcc_collide(M, x->s);
+  MccLaunchT<float> M32{M.seed, M.step, M.ng, M.tg, M.numax_e, M.pnull_e, M.pnull_i, M.gmax,
+                        M.thr_e, M.thr_i, M.ne, M.ni, as32(M.e), as32(M.i), M.flag, M.offs,
+                        M.cnt};
+  if (e == cudaSuccess) e = x->mixed ? launch_mcc_collide(M32, x->s) : launch_mcc_collide(M, x->s);
   if (e == cudaSuccess) e = scan_exclusive(x->flag, x->offs, M.ne, x->total, x->scan_scratch, x->s);
   x->launches += (M.ne > 0 || M.ni > 0 ? 1 : 0) + (M.ne > 0 ? 3 : 0);
   long long tot = 0;
@@ -496,7 +586,8 @@ int pic_mcc(pic_ctx *x, unsigned long long step, long long *counts, double *de_c
       rc = PIC_E_CAPACITY;
       capov = (unsigned long long)tot;
     } else {
-      e = launch_mcc_append(M, x->n[0], x->n[1], x->next_id[0], x->next_id[1], x->s);
+      e = x->mixed ? launch_mcc_append(M32, x->n[0], x->n[1], x->next_id[0], x->next_id[1], x->s)
+                   : launch_mcc_append(M, x->n[0], x->n[1], x->next_id[0], x->next_id[1], x->s);
       if (e != cudaSuccess) return PIC_E_CUDA;
       x->launches += 1;
       x->n[0] += tot;
@@ -543,8 +634,11 @@ int pic_step(pic_ctx *x, int nsteps, pic_step_stats *st) {
     double res = 0.0, src = 0.0;
     int k;
     for (k = 0; k < x->cfg.picard_max; ++k) {
-      if (launch_half_field(x->g, x->er, x->ez, x->er1, x->ez1, x->erh, x->ezh, s) != cudaSuccess)
-        return PIC_E_CUDA;
+      cudaError_t he =
+          x->mixed ? launch_half_field_alpha(x->g, x->er, x->ez, x->er1, x->ez1, x->erh, x->ezh,
+                                             x->alpha, s)
+                   : launch_half_field(x->g, x->er, x->ez, x->er1, x->ez1, x->erh, x->ezh, s);
+      if (he != cudaSuccess) return PIC_E_CUDA;
       x->launches += 1;
       if (cudaMemsetAsync(x->ir, 0, ner * 8, s) != cudaSuccess) return PIC_E_CUDA;
       if (cudaMemsetAsync(x->iz, 0, nez * 8, s) != cudaSuccess) return PIC_E_CUDA;
@@ -604,7 +698,7 @@ int pic_step(pic_ctx *x, int nsteps, pic_step_stats *st) {
     }
     int sr = pic_sort(x);
     if (sr) return sr;
-    unsigned long long pc[4];
+    unsigned long long pc[5];
     double kel = 0.0;
     if (cudaMemcpyAsync(pc, x->cnt->push, sizeof(pc), cudaMemcpyDeviceToHost, s) != cudaSuccess)
       return PIC_E_CUDA;
@@ -616,6 +710,7 @@ int pic_step(pic_ctx *x, int nsteps, pic_step_stats *st) {
     S.absorbed = (long long)pc[1];
     S.substeps = (long long)pc[2];
     S.fallbacks = (long long)pc[3];
+    S.push_flops = (long long)pc[4];
     S.ke_lost = kel;
     S.n[0] = x->n[0];
     S.n[1] = x->n[1];
@@ -630,9 +725,13 @@ int pic_step(pic_ctx *x, int nsteps, pic_step_stats *st) {
 int pic_diag(pic_ctx *x, pic_diag_out *out) {
   if (!x || !out) return PIC_E_CONFIG;
   cudaError_t e = cudaMemsetAsync(x->diag, 0, 8 * 8, x->s);
-  if (e == cudaSuccess) e = launch_kinetic(cur(x, 0), x->n[0], kME, -kQE, x->diag, x->s);
+  if (e == cudaSuccess)
+    e = x->mixed ? launch_kinetic(as32(cur(x, 0)), x->n[0], kME, -kQE, x->diag, x->s)
+                 : launch_kinetic(cur(x, 0), x->n[0], kME, -kQE, x->diag, x->s);
   x->launches += 3;
-  if (e == cudaSuccess) e = launch_kinetic(cur(x, 1), x->n[1], kMAr, kQE, x->diag + 2, x->s);
+  if (e == cudaSuccess)
+    e = x->mixed ? launch_kinetic(as32(cur(x, 1)), x->n[1], kMAr, kQE, x->diag + 2, x->s)
+                 : launch_kinetic(cur(x, 1), x->n[1], kMAr, kQE, x->diag + 2, x->s);
   if (e == cudaSuccess)
     e = launch_field_energy(x->g, x->eps, x->mu, x->er, x->ez, x->h, x->diag + 4, x->s);
   double h[8];
@@ -651,8 +750,14 @@ int pic_diag(pic_ctx *x, pic_diag_out *out) {
 
 int pic_node_charge(pic_ctx *x, double *q) {
   if (!x || !q) return PIC_E_CONFIG;
-  cudaError_t e = launch_node_charge(x->g, cur(x, 0), x->n[0], -kQE, q, x->s);
-  if (e == cudaSuccess) e = launch_node_charge(x->g, cur(x, 1), x->n[1], kQE, q, x->s);
+  cudaError_t e;
+  if (x->mixed) {
+    e = launch_node_charge(x->g, as32(cur(x, 0)), x->n[0], -kQE, q, x->s);
+    if (e == cudaSuccess) e = launch_node_charge(x->g, as32(cur(x, 1)), x->n[1], kQE, q, x->s);
+  } else {
+    e = launch_node_charge(x->g, cur(x, 0), x->n[0], -kQE, q, x->s);
+    if (e == cudaSuccess) e = launch_node_charge(x->g, cur(x, 1), x->n[1], kQE, q, x->s);
+  }
   return cuda_rc(e);
 }
 
@@ -661,12 +766,12 @@ int pic_get_view(pic_ctx *x, pic_view *v) {
   for (int s = 0; s < 2; ++s) {
     Parts &P = cur(x, s);
     v->cell[s] = P.cell;
-    v->a[s] = P.a;
-    v->b[s] = P.b;
-    v->vr[s] = P.vr;
-    v->vt[s] = P.vt;
-    v->vz[s] = P.vz;
-    v->w[s] = P.w;
+    v->a[s] = (void *)P.a;
+    v->b[s] = (void *)P.b;
+    v->vr[s] = (void *)P.vr;
+    v->vt[s] = (void *)P.vt;
+    v->vz[s] = (void *)P.vz;
+    v->w[s] = (void *)P.w;
     v->id[s] = P.id;
     v->n[s] = x->n[s];
     v->cap[s] = x->cap[s];
@@ -676,6 +781,7 @@ int pic_get_view(pic_ctx *x, pic_view *v) {
   v->ez = x->ez;
   v->h = x->h;
   v->step = x->step;
+  v->real_size = x->mixed ? 4 : 8;
   return PIC_OK;
 }
 

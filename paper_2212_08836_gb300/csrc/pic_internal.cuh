@@ -44,6 +44,7 @@ __device__ __forceinline__ void philox4x64(uint64_t c[4], uint64_t k0, uint64_t 
   }
 }
 
+// u01(x) < p  <=>  (x >> 11) < thr  with thr = ceil(p * 2^53) (integer test, no FP64)
 __device__ __forceinline__ double u01(uint64_t x) {
   return (double)(x >> 11) * (1.0 / 9007199254740992.0);
 }
@@ -67,22 +68,26 @@ struct Grid {
   double dr, dz, R, L;
 };
 
-// Particle structure of arrays of one species (FP64 form)
-struct Parts {
+// Particle structure of arrays of one species; T = double (plain FP64 form)
+// or float (mixed form: FP32 state in physical units)
+template <typename T>
+struct PartsT {
   int32_t *cell;
-  double *a, *b, *vr, *vt, *vz, *w;
+  T *a, *b, *vr, *vt, *vz, *w;
   uint32_t *id;
 };
+using Parts = PartsT<double>;
+using Parts32 = PartsT<float>;
 
 // Device counters written by the push / MCC kernels
 struct DevCounters {
-  unsigned long long push[4];  // substep errors, absorbed, substeps, fallbacks
+  unsigned long long push[5];  // substep errors, absorbed, substeps, fallbacks, FP64 flops
   unsigned long long mcc[8];
   double ke_lost;
   double de_coll;
   double norm[2];              // Picard: sum (E_new - E_it)^2, sum E_new^2
   double src;                  // drive-gap energy of the last solve
-  double pad[3];
+  double pad[2];
 };
 
 // Field operator (separable direct solve of the H_theta system)
@@ -121,19 +126,25 @@ cudaError_t launch_field_solve(const FieldOp &F, const double *er0, const double
 cudaError_t launch_half_field(const Grid &g, const double *er0, const double *ez0,
                               const double *er1, const double *ez1, double *erh, double *ezh,
                               cudaStream_t s);
+template <typename T>
 cudaError_t launch_load(const Grid &g, long long n, double n0, double te_ev, double ti_ev,
-                        uint64_t seed, Parts e, Parts i, cudaStream_t s);
+                        uint64_t seed, PartsT<T> e, PartsT<T> i, cudaStream_t s);
 
-struct MccLaunch {
+template <typename T>
+struct MccLaunchT {
   uint64_t seed, step;
   double ng, tg, numax_e, pnull_e, pnull_i, gmax;
+  uint64_t thr_e, thr_i;  // null-collision thresholds on the 53-bit integer draw
   long long ne, ni;
-  Parts e, i;
+  PartsT<T> e, i;
   int32_t *flag, *offs;   // per-electron ionization flags / exclusive scan
   DevCounters *cnt;
 };
-cudaError_t launch_mcc_collide(const MccLaunch &M, cudaStream_t s);
-cudaError_t launch_mcc_append(const MccLaunch &M, long long ne_new0, long long ni_new0,
+using MccLaunch = MccLaunchT<double>;
+template <typename T>
+cudaError_t launch_mcc_collide(const MccLaunchT<T> &M, cudaStream_t s);
+template <typename T>
+cudaError_t launch_mcc_append(const MccLaunchT<T> &M, long long ne_new0, long long ni_new0,
                               uint32_t id_e0, uint32_t id_i0, cudaStream_t s);
 
 // exclusive scan of n int32 values; total written to *total_dev (int64)
@@ -141,23 +152,61 @@ size_t scan_scratch_bytes(long long n);
 cudaError_t scan_exclusive(const int32_t *in, int32_t *out, long long n, long long *total_dev,
                            void *scratch, cudaStream_t s);
 
-struct SortLaunch {
+template <typename T>
+struct SortLaunchT {
   int ncell;
   long long n;
-  Parts src, dst;
+  PartsT<T> src, dst;
   int32_t *counts;   // ncell + 1
   int32_t *offs;     // ncell + 1
   int32_t *cursor;   // ncell
   long long *total;
   void *scan_scratch;
 };
-cudaError_t launch_sort(const SortLaunch &S, cudaStream_t s);
+using SortLaunch = SortLaunchT<double>;
+template <typename T>
+cudaError_t launch_sort(const SortLaunchT<T> &S, cudaStream_t s);
 
-cudaError_t launch_kinetic(const Parts &p, long long n, double m, double q, double *out2,
+template <typename T>
+cudaError_t launch_kinetic(const PartsT<T> &p, long long n, double m, double q, double *out2,
                            cudaStream_t s);
 cudaError_t launch_field_energy(const Grid &g, double eps, double mu, const double *er,
                                 const double *ez, const double *h, double *out, cudaStream_t s);
-cudaError_t launch_node_charge(const Grid &g, const Parts &p, long long n, double q, double *Q,
-                               cudaStream_t s);
+template <typename T>
+cudaError_t launch_node_charge(const Grid &g, const PartsT<T> &p, long long n, double q,
+                               double *Q, cudaStream_t s);
+
+// Mixed form: normalised per-species accelerations alpha = qm*E*dt^2/dx (float)
+struct AlphaOut {
+  float *ar[2], *az[2];   // per species: Er-edge and Ez-edge layouts
+  double sr[2], sz[2];    // scale factors qm*dt^2/dr, qm*dt^2/dz
+};
+cudaError_t launch_half_field_alpha(const Grid &g, const double *er0, const double *ez0,
+                                    const double *er1, const double *ez1, double *erh,
+                                    double *ezh, const AlphaOut &A, cudaStream_t s);
+
+struct PushLaunch32 {
+  Grid g;
+  double q, m, dt;
+  float cr, cz;          // dt/dr, dt/dz: velocity [m/s] -> cells per step
+  float icr, icz;        // dr/dt, dz/dt: cells per step -> velocity [m/s]
+  float wbt;             // qm*Bz*dt
+  long long n;
+  Parts32 p;
+  const float *ar, *az;  // normalised accelerations of this species
+  float qf;              // species charge [C] in FP32
+  double *ir, *iz;       // crossed charge [C] (FP64, atomics)
+  int write;
+  double *wall_z0, *wall_zl, *wall_r;
+  unsigned long long *counters;
+  double *ke_lost;
+  float inz;             // 1/nz
+  int *queue;            // scratch: indices of particles for the general path (capacity n)
+  int *qcount;           // scratch: queue length
+  int *q_cell;           // scratch: queued start state (cell, offsets, normalised v, weight)
+  float *q_a, *q_b, *q_ur, *q_ut, *q_uz, *q_w;
+};
+cudaError_t launch_push_fp32(const PushLaunch32 &L, cudaStream_t s);
+
 
 }  // namespace pic

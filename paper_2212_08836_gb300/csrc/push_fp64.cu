@@ -78,14 +78,20 @@ __device__ __forceinline__ void eval(const Consts &K, const Sub &s, double da, d
   o.vt1 = vt1;
 }
 
+// Algorithmic FP64 operation counts of the source (add, sub, mul, div each
+// count 1): one residual/Jacobian evaluation, one Newton update, the rest of
+// an accepted sub-step, and the per-sub-step set-up.
+constexpr unsigned kFlopEval = 68, kFlopNewton = 17, kFlopAccept = 30, kFlopSetup = 9;
+
 __device__ bool solve_interior(const Consts &K, const Sub &s, double dt, double &pda,
-                               double &pdb) {
+                               double &pdb, unsigned long long &flops) {
   double da = dt * s.vr / K.dr;
   double db = dt * s.vz / K.dz;
   if (s.pth != 0.0 && s.r + da * K.dr <= 0.0) da = -0.5 * s.r / K.dr;
   for (int it = 0; it < kNewtonMax; ++it) {
     Res o;
     eval(K, s, da, db, dt, o);
+    flops += kFlopEval + kFlopNewton;
     double det = o.f1a * o.f2b - o.f1b * o.f2a;
     if (!(det != 0.0) || !isfinite(det)) return false;
     double xa = (-o.f1 * o.f2b + o.f2 * o.f1b) / det;
@@ -108,13 +114,15 @@ __device__ bool solve_interior(const Consts &K, const Sub &s, double dt, double 
 
 // landing on a face normal to direction dir (0: xi, 1: eta) with fixed offset change X
 __device__ bool solve_landing(const Consts &K, const Sub &s, int dir, double X, double dt0,
-                              double oth0, double tscale, double &pdt, double &poth) {
+                              double oth0, double tscale, double &pdt, double &poth,
+                              unsigned long long &flops) {
   double dt = dt0, oth = oth0;
   for (int it = 0; it < kNewtonMax; ++it) {
     double da = dir == 0 ? X : oth;
     double db = dir == 0 ? oth : X;
     Res o;
     eval(K, s, da, db, dt, o);
+    flops += kFlopEval + kFlopNewton;
     double gF, gFo, gFt, gO, gOo, gOt;
     if (dir == 0) {
       gO = o.f1; gOo = o.f1b; gOt = o.f1t;
@@ -198,7 +206,7 @@ __global__ void __launch_bounds__(128) k_push_fp64(PushLaunch L) {
 
   int home = -1;
   double hr0 = 0.0, hr1 = 0.0, hz0 = 0.0, hz1 = 0.0;  // home-cell deposit
-  unsigned long long c_err = 0, c_abs = 0, c_sub = 0, c_fb = 0;
+  unsigned long long c_err = 0, c_abs = 0, c_sub = 0, c_fb = 0, c_flop = 0;
   double kel = 0.0;
 
   if (p < L.n) {
@@ -229,9 +237,10 @@ __global__ void __launch_bounds__(128) k_push_fp64(PushLaunch L) {
         s.r = ((double)ic + a) * K.dr;
         s.vr = vr; s.vt = vt; s.vz = vz;
         s.pth = s.r * vt + 0.5 * K.wb * s.r * s.r;
+        c_flop += kFlopSetup;
 
         double da, db;
-        if (!solve_interior(K, s, dtT, da, db)) {
+        if (!solve_interior(K, s, dtT, da, db, c_flop)) {
           dtT *= 0.5;
           c_fb++;
           continue;
@@ -266,7 +275,8 @@ __global__ void __launch_bounds__(128) k_push_fp64(PushLaunch L) {
             }
             double oth0 = doth * (g0 / dtT);
             double tdt = 0.0, toth = 0.0;
-            if (!(g0 > 0.0) || !solve_landing(K, s, dir, X, g0, oth0, dtT, tdt, toth)) continue;
+            if (!(g0 > 0.0) || !solve_landing(K, s, dir, X, g0, oth0, dtT, tdt, toth, c_flop))
+              continue;
             if (!(tdt > 0.0) || tdt > dtT) continue;
             double xo = (dir == 0 ? b : a) + toth;
             if (xo < 0.0 || xo > 1.0) continue;
@@ -295,6 +305,7 @@ __global__ void __launch_bounds__(128) k_push_fp64(PushLaunch L) {
         }
         Res o;
         eval(K, s, da, db, step_dt, o);
+        c_flop += kFlopEval + kFlopAccept;
         double am = a + 0.5 * da, bm = b + 0.5 * db;
         double nvr = vr + step_dt * (K.qm * (s.er0 + s.ger * bm) + o.C);
         double nvz = vz + step_dt * (K.qm * (s.ez0 + s.gez * am));
@@ -385,11 +396,13 @@ __global__ void __launch_bounds__(128) k_push_fp64(PushLaunch L) {
     c_abs = warp_sum_u64(c_abs);
     c_sub = warp_sum_u64(c_sub);
     c_fb = warp_sum_u64(c_fb);
+    c_flop = warp_sum_u64(c_flop);
     if (lane == 0) {
       if (c_err) atomicAdd(&L.counters[0], c_err);
       if (c_abs) atomicAdd(&L.counters[1], c_abs);
       if (c_sub) atomicAdd(&L.counters[2], c_sub);
       if (c_fb) atomicAdd(&L.counters[3], c_fb);
+      if (c_flop) atomicAdd(&L.counters[4], c_flop);
     }
   }
   if (L.ke_lost && kel != 0.0) atomicAdd(L.ke_lost, kel);

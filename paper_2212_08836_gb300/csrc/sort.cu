@@ -97,7 +97,8 @@ __global__ void __launch_bounds__(256) k_hist(const int32_t *cell, long long n, 
   if (c >= 0 && lane == leader) atomicAdd(&counts[c], __popc(peers));
 }
 
-__global__ void __launch_bounds__(256) k_scatter(SortLaunch S) {
+template <typename T>
+__global__ void __launch_bounds__(256) k_scatter(SortLaunchT<T> S) {
   long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   int c = p < S.n ? S.src.cell[p] : -1;
   if (c >= S.ncell) c = -1;
@@ -138,7 +139,8 @@ cudaError_t scan_exclusive(const int32_t *in, int32_t *out, long long n, long lo
   return cudaGetLastError();
 }
 
-cudaError_t launch_sort(const SortLaunch &S, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_sort(const SortLaunchT<T> &S, cudaStream_t s) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(S.counts, 0, sizeof(int32_t) * (S.ncell + 1), s)) != cudaSuccess)
     return e;
@@ -147,8 +149,11 @@ cudaError_t launch_sort(const SortLaunch &S, cudaStream_t s) {
   if ((e = scan_exclusive(S.counts, S.offs, S.ncell + 1, S.total, S.scan_scratch, s)) !=
       cudaSuccess)
     return e;
-  if (S.n > 0) k_scatter<<<(unsigned)((S.n + 255) / 256), 256, 0, s>>>(S);
+  if (S.n > 0) k_scatter<T><<<(unsigned)((S.n + 255) / 256), 256, 0, s>>>(S);
   return cudaGetLastError();
 }
+
+template cudaError_t launch_sort<double>(const SortLaunchT<double> &, cudaStream_t);
+template cudaError_t launch_sort<float>(const SortLaunchT<float> &, cudaStream_t);
 
 }  // namespace pic

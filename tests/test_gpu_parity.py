@@ -45,8 +45,25 @@ def by_id(sp):
     return {k: v[o] for k, v in sp.items()}
 
 
-def assert_state_close(gs, os_, rtol=1e-12, what=""):
-    assert np.array_equal(gs["cell"], os_["cell"]), what + " cell"
+def assert_state_close(gs, os_, rtol=1e-12, what="", nz=None):
+    """Same particles in the same state.  Positions are compared in global
+    logical coordinates: a particle that ends within roundoff of a face may
+    sit in either adjacent cell (counted, at most two per comparison)."""
+    if nz is None:
+        assert np.array_equal(gs["cell"], os_["cell"]), what + " cell"
+    else:
+        assert np.array_equal(gs["cell"] >= 0, os_["cell"] >= 0), what + " absorbed set"
+        bad = np.where(gs["cell"] != os_["cell"])[0]
+        info = [(int(gs["id"][k]), int(gs["cell"][k]), float(gs["a"][k]), float(gs["b"][k]),
+                 int(os_["cell"][k]), float(os_["a"][k]), float(os_["b"][k])) for k in bad[:5]]
+        assert len(bad) <= 2, what + " %d face-side flips %s" % (len(bad), info)
+        alive = gs["cell"] >= 0
+        for name, x_g, x_o in (("xi", gs["cell"] // nz + gs["a"], os_["cell"] // nz + os_["a"]),
+                               ("eta", gs["cell"] % nz + gs["b"], os_["cell"] % nz + os_["b"])):
+            np.testing.assert_allclose(x_g[alive], x_o[alive], rtol=0, atol=rtol * 64,
+                                       err_msg=what + name)
+        gs = {k: v[gs["cell"] == os_["cell"]] for k, v in gs.items()}
+        os_ = {k: v[os_["cell"] == os_["cell"]][:len(gs["cell"])] for k, v in os_.items()}
     for k in ("a", "b"):
         np.testing.assert_allclose(gs[k], os_[k], rtol=0, atol=rtol, err_msg=what + k)
     vs = max(np.max(np.abs(os_["vr"])), np.max(np.abs(os_["vz"])), 1e-300)
@@ -66,7 +83,7 @@ def test_push_deposit_parity(nr, nz, n, dt):
     pic.set_state([e, i])
     ir = torch.zeros(g.n_er, dtype=torch.float64, device=DEV)
     iz = torch.zeros(g.n_ez, dtype=torch.float64, device=DEV)
-    cnt = torch.zeros(4, dtype=torch.int64, device=DEV)
+    cnt = torch.zeros(5, dtype=torch.int64, device=DEV)
     kel = torch.zeros(1, dtype=torch.float64, device=DEV)
     pic.push_deposit(tgpu(er), tgpu(ez), ir, iz, write=True, counters=cnt, ke_lost=kel)
     ir_o, iz_o = np.zeros(g.n_er), np.zeros(g.n_ez)
@@ -82,7 +99,8 @@ def test_push_deposit_parity(nr, nz, n, dt):
     scale = max(np.max(np.abs(ir_o)), np.max(np.abs(iz_o)))
     assert np.max(np.abs(ir.cpu().numpy() - ir_o)) <= 1e-12 * scale
     assert np.max(np.abs(iz.cpu().numpy() - iz_o)) <= 1e-12 * scale
-    assert list(cnt.cpu().numpy()) == list(cnt_o)
+    assert list(cnt.cpu().numpy()[:4]) == list(cnt_o)
+    assert cnt.cpu().numpy()[4] > 100 * 2 * n  # algorithmic FP64 operations counted
     np.testing.assert_allclose(kel.item(), kel_o, rtol=1e-12)
     assert cnt_o[2] > 1.2 * 2 * n / 2  # crossings exercised
     for s in range(2):
@@ -252,7 +270,8 @@ def test_full_step_parity(mcc):
             got = by_id(pic.get_state(s))
             ref = by_id(sim.state(s))
             assert len(got["id"]) == len(ref["id"])
-            assert_state_close(got, ref, rtol=1e-11, what="step %d species %d " % (step, s))
+            assert_state_close(got, ref, rtol=1e-11, what="step %d species %d " % (step, s),
+                               nz=nz)
         assert st["absorbed"] == sto.counters[1]
         if mcc:
             assert st["mcc"][:7] == list(sto.mcc[:7])
