@@ -790,12 +790,25 @@ static void o_iso_dir(double u2, double u3, double *nr_, double *nt_, double *nz
   *nz_ = ct;
 }
 
+typedef struct {
+  int64_t p;
+  uint32_t id;
+  double v1;
+} o_iz;
+
+static int o_iz_cmp(const void *x, const void *y) {
+  uint32_t a = ((const o_iz *)x)->id, b = ((const o_iz *)y)->id;
+  return a < b ? -1 : (a > b ? 1 : 0);
+}
+
 /* Null-collision MCC (row a7), after Mertmann et al. 2011 / Vahedi & Surendra.
  * Electrons: elastic, excitation (11.5 eV), ionization (15.76 eV, equal split,
  * new e + Ar+ at the parent's position with its weight).  Ions: charge
  * exchange with constant cross section against a 300 K neutral Maxwellian.
- * pnull_* = 1 - exp(-numax_* dt), supplied by the caller.  New particles are
- * appended in parent order; their ids continue from *next_id_*.
+ * pnull_* = 1 - exp(-numax_* dt), supplied by the caller.  New pairs are
+ * appended in order of the parent's id (so ids do not depend on how the
+ * store happens to be ordered); their ids continue from *next_id_*.  If the
+ * capacity cannot take all pairs of this pass, none is appended (rc -5).
  * counts[8]: cand_e, el, ex, iz, cand_i, cx, gmax overflow, capacity overflow */
 int oracle_mcc(uint64_t seed, uint64_t step, double ng, double tg, double me, double mi,
                double numax_e, double pnull_e, double pnull_i, double gmax,
@@ -808,6 +821,8 @@ int oracle_mcc(uint64_t seed, uint64_t step, double ng, double tg, double me, do
   int64_t n_e0 = *ne, n_i0 = *ni;
   int rc = 0;
   double dE = 0.0;
+  o_iz *izl = (o_iz *)malloc(sizeof(o_iz) * (size_t)(n_e0 > 0 ? n_e0 : 1));
+  int64_t niz = 0;
   for (int64_t p = 0; p < n_e0; ++p) {
     if (ce[p] < 0) continue;
     double u[4];
@@ -844,35 +859,46 @@ int oracle_mcc(uint64_t seed, uint64_t step, double ng, double tg, double me, do
       double eps1 = 0.5 * (eps - 15.76);
       double v1 = sqrt(2.0 * eps1 * O_QE / me);
       vre[p] = v1 * nr_; vte[p] = v1 * nt_; vze[p] = v1 * nz_;
-      if (*ne >= cap_e || *ni >= cap_i) {
-        counts[7]++;
-        rc = -5;
-      } else {
-        double u1[4], u2[4];
-        o_draw4(seed, O_STREAM_MCC_E, ide[p], step, 1, u1);
-        o_draw4(seed, O_STREAM_MCC_E, ide[p], step, 2, u2);
-        int64_t q = *ne;
-        double mr, mt, mz;
-        o_iso_dir(u1[0], u1[1], &mr, &mt, &mz);
-        ce[q] = ce[p]; ae[q] = ae[p]; be[q] = be[p]; we[q] = we[p];
-        vre[q] = v1 * mr; vte[q] = v1 * mt; vze[q] = v1 * mz;
-        ide[q] = (*next_id_e)++;
-        *ne = q + 1;
-        double g1, g2, g3, g4;
-        o_gauss2(u1[2], u1[3], &g1, &g2);
-        o_gauss2(u2[0], u2[1], &g3, &g4);
-        int64_t s = *ni;
-        ci[s] = ce[p]; ai[s] = ae[p]; bi[s] = be[p]; wi[s] = we[p];
-        vri[s] = vthg * g1; vti[s] = vthg * g2; vzi[s] = vthg * g3;
-        idi[s] = (*next_id_i)++;
-        *ni = s + 1;
-        dE += 0.5 * me * we[p] * (v1 * v1) + 0.5 * mi * wi[s] * (vri[s] * vri[s] + vti[s] * vti[s] + vzi[s] * vzi[s]);
-      }
+      izl[niz].p = p;
+      izl[niz].id = ide[p];
+      izl[niz].v1 = v1;
+      niz++;
     } else {
       continue;
     }
     dE += 0.5 * me * we[p] * (vre[p] * vre[p] + vte[p] * vte[p] + vze[p] * vze[p]) - ke0;
   }
+  /* new pairs in order of the parent's id (independent of the storage order) */
+  qsort(izl, (size_t)niz, sizeof(o_iz), o_iz_cmp);
+  if (*ne + niz > cap_e || *ni + niz > cap_i) {
+    counts[7] += niz;
+    if (niz) rc = -5;
+  } else {
+    for (int64_t k = 0; k < niz; ++k) {
+      int64_t p = izl[k].p;
+      double v1 = izl[k].v1;
+      double u1[4], u2[4];
+      o_draw4(seed, O_STREAM_MCC_E, ide[p], step, 1, u1);
+      o_draw4(seed, O_STREAM_MCC_E, ide[p], step, 2, u2);
+      int64_t q = *ne;
+      double mr, mt, mz;
+      o_iso_dir(u1[0], u1[1], &mr, &mt, &mz);
+      ce[q] = ce[p]; ae[q] = ae[p]; be[q] = be[p]; we[q] = we[p];
+      vre[q] = v1 * mr; vte[q] = v1 * mt; vze[q] = v1 * mz;
+      ide[q] = (*next_id_e)++;
+      *ne = q + 1;
+      double g1, g2, g3, g4;
+      o_gauss2(u1[2], u1[3], &g1, &g2);
+      o_gauss2(u2[0], u2[1], &g3, &g4);
+      int64_t s = *ni;
+      ci[s] = ce[p]; ai[s] = ae[p]; bi[s] = be[p]; wi[s] = we[p];
+      vri[s] = vthg * g1; vti[s] = vthg * g2; vzi[s] = vthg * g3;
+      idi[s] = (*next_id_i)++;
+      *ni = s + 1;
+      dE += 0.5 * me * we[p] * (v1 * v1) + 0.5 * mi * wi[s] * (vri[s] * vri[s] + vti[s] * vti[s] + vzi[s] * vzi[s]);
+    }
+  }
+  free(izl);
   for (int64_t p = 0; p < n_i0; ++p) {
     if (ci[p] < 0) continue;
     double u[4];

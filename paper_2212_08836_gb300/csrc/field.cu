@@ -51,13 +51,30 @@ __global__ void k_half_alpha(long long n1, long long n2, const double *er0, cons
   }
 }
 
+__global__ void k_half_alpha64(long long n1, long long n2, const double *er0, const double *ez0,
+                               const double *er1, const double *ez1, double *erh, double *ezh,
+                               AlphaOut64 A) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n1) {
+    double e = 0.5 * (er0[t] + er1[t]);
+    erh[t] = e;
+    A.ar[0][t] = A.sr[0] * e;
+    A.ar[1][t] = A.sr[1] * e;
+  } else if (t < n1 + n2) {
+    long long u = t - n1;
+    double e = 0.5 * (ez0[u] + ez1[u]);
+    ezh[u] = e;
+    A.az[0][u] = A.sz[0] * e;
+    A.az[1][u] = A.sz[1] * e;
+  }
+}
+
 // rhs(i,j) = 2 mu Vh H0 - dt * C^T L Et   (Et = E0 - dQ/(2 eps A), or the prescribed half value)
-__global__ void k_rhs(FieldOp F, const double *er0, const double *ez0, const double *h0,
-                      const double *ir, const double *iz, double v0, double v1) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ double rhs_at(const FieldOp &F, const double *er0, const double *ez0,
+                                        const double *h0, const double *ir, const double *iz,
+                                        double v0, double v1, int i, int j) {
   int nr = F.nr, nz = F.nz, nz1 = nz + 1;
-  if (c >= nr * nz) return;
-  int i = c / nz, j = c - (c / nz) * nz;
+  int c = i * nz + j;
   double dr = F.dr, dz = F.dz, eps = F.eps;
   double s = kTwoPi * rhalf(dr, i);
   double ar = area_r(dr, dz, i);
@@ -70,7 +87,73 @@ __global__ void k_rhs(FieldOp F, const double *er0, const double *ez0, const dou
   else etr = ez0[(i + 1) * nz + j] - iz[(i + 1) * nz + j] / (2.0 * eps * area_z(dr, i + 1));
   double vh = kTwoPi * rhalf(dr, i) * dr * dz;
   double curl = (-s) * dr * etb + s * dr * ett + s * dz * etl + (-s) * dz * etr;
-  F.rhs[c] = 2.0 * F.mu * vh * h0[c] - F.dt * curl;
+  return 2.0 * F.mu * vh * h0[c] - F.dt * curl;
+}
+
+__global__ void k_rhs(FieldOp F, const double *er0, const double *ez0, const double *h0,
+                      const double *ir, const double *iz, double v0, double v1) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  int nz = F.nz;
+  if (F.half) {
+    // mirrored pairs (j, nz-1-j): S = sum into rhs[i*h + j], D = difference into hat-side buffer
+    int h = F.half;
+    if (c >= F.nr * h) return;
+    int i = c / h, j = c - (c / h) * h;
+    double x0 = rhs_at(F, er0, ez0, h0, ir, iz, v0, v1, i, j);
+    double x1 = rhs_at(F, er0, ez0, h0, ir, iz, v0, v1, i, nz - 1 - j);
+    F.rhs[i * h + j] = x0 + x1;
+    F.rhs[F.nr * h + i * h + j] = x0 - x1;
+    return;
+  }
+  if (c >= F.nr * nz) return;
+  int i = c / nz, j = c - (c / nz) * nz;
+  F.rhs[c] = rhs_at(F, er0, ez0, h0, ir, iz, v0, v1, i, j);
+}
+
+// Batched C_z[M x N] = A_z[M x K] * B_z[K x N] (z = blockIdx.z), row-major FP64 with
+// leading dimensions; 16x16 output tile per 64-thread block, 2x2 per thread, so that
+// the small transforms still spread over all SMs (the FP64 pipe is the limit).
+struct Gemm {
+  int M, N, K, lda, ldb, ldc;
+  const double *A[2], *B[2];
+  double *C[2];
+};
+constexpr int GT = 16, GK = 16;
+__global__ void __launch_bounds__(64) k_gemm16(Gemm G) {
+  __shared__ double As[GK][GT + 1];
+  __shared__ double Bs[GK][GT + 1];
+  const double *__restrict__ A = G.A[blockIdx.z];
+  const double *__restrict__ B = G.B[blockIdx.z];
+  double *__restrict__ Cm = G.C[blockIdx.z];
+  int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;
+  int row0 = blockIdx.y * GT, col0 = blockIdx.x * GT;
+  double acc00 = 0.0, acc01 = 0.0, acc10 = 0.0, acc11 = 0.0;
+  for (int k0 = 0; k0 < G.K; k0 += GK) {
+    for (int e = threadIdx.x; e < GT * GK; e += 64) {
+      int r = e / GK, kk = e - (e / GK) * GK;
+      int gr = row0 + r, gk = k0 + kk;
+      As[kk][r] = (gr < G.M && gk < G.K) ? A[(long long)gr * G.lda + gk] : 0.0;
+      int kb = e / GT, cc = e - (e / GT) * GT;
+      int gkb = k0 + kb, gc = col0 + cc;
+      Bs[kb][cc] = (gkb < G.K && gc < G.N) ? B[(long long)gkb * G.ldb + gc] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      double a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1];
+      double b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
+      acc00 += a0 * b0;
+      acc01 += a0 * b1;
+      acc10 += a1 * b0;
+      acc11 += a1 * b1;
+    }
+    __syncthreads();
+  }
+  int gr = row0 + ty * 2, gc = col0 + tx * 2;
+  if (gr < G.M && gc < G.N) Cm[(long long)gr * G.ldc + gc] = acc00;
+  if (gr < G.M && gc + 1 < G.N) Cm[(long long)gr * G.ldc + gc + 1] = acc01;
+  if (gr + 1 < G.M && gc < G.N) Cm[(long long)(gr + 1) * G.ldc + gc] = acc10;
+  if (gr + 1 < G.M && gc + 1 < G.N) Cm[(long long)(gr + 1) * G.ldc + gc + 1] = acc11;
 }
 
 // C[M x N] = A[M x K] * B[K x N], row-major FP64, 32x32 tile per block, 2x2 per thread
@@ -152,6 +235,16 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// H_half(i, j): direct, or recombined from the two half-size inverse transforms
+__device__ __forceinline__ double hhalf_at(const FieldOp &F, int i, int j) {
+  if (!F.half) return F.hhalf[i * F.nz + j];
+  int h = F.half;
+  const double *P = F.hhalf, *R = F.hhalf + F.nr * h;
+  if (j < h) return P[i * h + j] + R[i * h + j];
+  int jj = F.nz - 1 - j;
+  return P[i * h + jj] - R[i * h + jj];
+}
+
 // H1 = 2 H_half - H0; E1 from Ampere; Picard norms and drive-gap energy
 __global__ void __launch_bounds__(256) k_update(FieldOp F, const double *er0, const double *ez0,
                                                 const double *h0, const double *ir,
@@ -163,10 +256,10 @@ __global__ void __launch_bounds__(256) k_update(FieldOp F, const double *er0, co
   long long ner = (long long)nr * nz1, nez = (long long)(nr + 1) * nz, nh = (long long)nr * nz;
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double dn = 0.0, nn = 0.0, src = 0.0;
-  const double *hh = F.hhalf;
   double dr = F.dr, dz = F.dz, eps = F.eps, dt = F.dt;
   if (t < nh) {
-    h1[t] = 2.0 * hh[t] - h0[t];
+    int i = (int)(t / nz), j = (int)(t - (t / nz) * nz);
+    h1[t] = 2.0 * hhalf_at(F, i, j) - h0[t];
   }
   if (t < ner) {
     int i = (int)(t / nz1), j = (int)(t - (t / nz1) * nz1);
@@ -174,7 +267,7 @@ __global__ void __launch_bounds__(256) k_update(FieldOp F, const double *er0, co
       er1[t] = 0.0;
     } else {
       double s = kTwoPi * rhalf(dr, i);
-      double ch = -s * hh[i * nz + j] + s * hh[i * nz + j - 1];
+      double ch = -s * hhalf_at(F, i, j) + s * hhalf_at(F, i, j - 1);
       double e1 = er0[t] + (dt * ch - ir[t]) / (eps * area_r(dr, dz, i));
       er1[t] = e1;
       if (er_it) {
@@ -187,8 +280,8 @@ __global__ void __launch_bounds__(256) k_update(FieldOp F, const double *er0, co
   if (t < nez) {
     int i = (int)(t / nz), j = (int)(t - (t / nz) * nz);
     double ch = 0.0;
-    if (i <= nr - 1) ch += kTwoPi * rhalf(dr, i) * hh[i * nz + j];
-    if (i >= 1) ch += -kTwoPi * rhalf(dr, i - 1) * hh[(i - 1) * nz + j];
+    if (i <= nr - 1) ch += kTwoPi * rhalf(dr, i) * hhalf_at(F, i, j);
+    if (i >= 1) ch += -kTwoPi * rhalf(dr, i - 1) * hhalf_at(F, i - 1, j);
     if (i == nr) {
       ez1[t] = v1 / F.L;
       double eh = 0.5 * (v0 + v1) / F.L;
@@ -248,6 +341,16 @@ cudaError_t launch_half_field_alpha(const Grid &g, const double *er0, const doub
   return cudaGetLastError();
 }
 
+cudaError_t launch_half_field_alpha64(const Grid &g, const double *er0, const double *ez0,
+                                      const double *er1, const double *ez1, double *erh,
+                                      double *ezh, const AlphaOut64 &A, cudaStream_t s) {
+  long long n1 = (long long)g.nr * (g.nz + 1), n2 = (long long)(g.nr + 1) * g.nz;
+  long long n = n1 + n2;
+  k_half_alpha64<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n1, n2, er0, ez0, er1, ez1, erh,
+                                                             ezh, A);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_field_solve(const FieldOp &F, const double *er0, const double *ez0,
                                const double *h0, const double *ir, const double *iz, double v0,
                                double v1, double *er1, double *ez1, double *h1, const double *er_it,
@@ -257,7 +360,19 @@ cudaError_t launch_field_solve(const FieldOp &F, const double *er0, const double
   if ((e = cudaMemsetAsync(&cnt->norm[0], 0, 3 * sizeof(double), s)) != cudaSuccess) return e;
   k_rhs<<<(nc + 255) / 256, 256, 0, s>>>(F, er0, ez0, h0, ir, iz, v0, v1);
   dim3 grid((F.nz + TM - 1) / TM, (F.nr + TM - 1) / TM);
-  k_gemm<<<grid, 256, 0, s>>>(F.nr, F.nz, F.nz, F.rhs, F.Q, F.hat);
+  int h = F.half;
+  Gemm G;
+  dim3 g16((h + GT - 1) / GT, (F.nr + GT - 1) / GT, 2);
+  if (h) {
+    // hat[:, 0:h] = S * Qe, hat[:, h:nz] = D * Qo   (even / odd DCT modes)
+    G.M = F.nr; G.N = h; G.K = h; G.lda = h; G.ldb = h; G.ldc = F.nz;
+    G.A[0] = F.rhs; G.A[1] = F.rhs + F.nr * h;
+    G.B[0] = F.Q; G.B[1] = F.Q + h * h;
+    G.C[0] = F.hat; G.C[1] = F.hat + h;
+    k_gemm16<<<g16, 64, 0, s>>>(G);
+  } else {
+    k_gemm<<<grid, 256, 0, s>>>(F.nr, F.nz, F.nz, F.rhs, F.Q, F.hat);
+  }
   // few modes per block so that many blocks stage their columns in parallel
   int mb = 2;
   while (mb > 1 && (size_t)3 * F.nr * mb * sizeof(double) > 200 * 1024) mb >>= 1;
@@ -268,7 +383,16 @@ cudaError_t launch_field_solve(const FieldOp &F, const double *er0, const double
     attr_set = true;
   }
   k_tridiag<<<(F.nz + mb - 1) / mb, 256, smem, s>>>(F, mb);
-  k_gemm<<<grid, 256, 0, s>>>(F.nr, F.nz, F.nz, F.hat, F.QT, F.hhalf);
+  if (h) {
+    // P = hat_e * Qe^T, R = hat_o * Qo^T; H_half(j) = P + R, H_half(nz-1-j) = P - R
+    G.M = F.nr; G.N = h; G.K = h; G.lda = F.nz; G.ldb = h; G.ldc = h;
+    G.A[0] = F.hat; G.A[1] = F.hat + h;
+    G.B[0] = F.QT; G.B[1] = F.QT + h * h;
+    G.C[0] = F.hhalf; G.C[1] = F.hhalf + F.nr * h;
+    k_gemm16<<<g16, 64, 0, s>>>(G);
+  } else {
+    k_gemm<<<grid, 256, 0, s>>>(F.nr, F.nz, F.nz, F.hat, F.QT, F.hhalf);
+  }
   long long ner = (long long)F.nr * (F.nz + 1), nez = (long long)(F.nr + 1) * F.nz;
   long long n = ner > nez ? ner : nez;
   k_update<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(F, er0, ez0, h0, ir, iz, v0, v1, er1, ez1,

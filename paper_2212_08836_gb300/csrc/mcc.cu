@@ -5,7 +5,9 @@
 // exchange with a constant cross section against a 300 K neutral Maxwellian.
 // One thread per particle; Philox4x64-10 with counter (id, step, block, 0), so
 // the draws do not depend on the launch shape.  Ionizing electrons set a flag;
-// an exclusive scan of the flags gives the append slot in parent order.
+// the flagged parents are compacted and ordered by their id, and the new pairs
+// are appended in that order, so the ids they receive do not depend on how the
+// store happens to be ordered inside a cell.
 #include "pic_internal.cuh"
 
 namespace pic {
@@ -146,14 +148,61 @@ __global__ void __launch_bounds__(256) k_mcc(MccLaunchT<T> M) {
   if (lane == 0 && de != 0.0) atomicAdd(&M.cnt->de_coll, de);
 }
 
-// new pairs for flagged electrons: electron at ne_new0 + k, ion at ni_new0 + k
+// keys of the ionizing electrons, compacted by the exclusive scan of the flags
 template <typename T>
-__global__ void __launch_bounds__(256) k_append(MccLaunchT<T> M, long long ne0, long long ni0,
-                                                uint32_t id_e0, uint32_t id_i0) {
+__global__ void __launch_bounds__(256) k_iz_keys(MccLaunchT<T> M) {
   long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < M.ne && M.flag[p])
+    M.keys[M.offs[p]] = ((uint64_t)M.e.id[p] << 32) | (uint64_t)(uint32_t)p;
+}
+
+// one-block bitonic sort of up to kSortMax keys (padded with all-ones)
+constexpr int kSortMax = 4096;
+__global__ void __launch_bounds__(1024) k_sort_keys_block(uint64_t *keys, int n) {
+  __shared__ uint64_t sk[kSortMax];
+  int m = 1;
+  while (m < n) m <<= 1;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) sk[i] = i < n ? keys[i] : ~0ull;
+  __syncthreads();
+  for (int k = 2; k <= m; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        int l = i ^ j;
+        if (l > i) {
+          bool up = (i & k) == 0;
+          uint64_t x = sk[i], y = sk[l];
+          if ((x > y) == up) {
+            sk[i] = y;
+            sk[l] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) keys[i] = sk[i];
+}
+
+// large counts: rank of every key by counting smaller keys (keys are unique)
+__global__ void __launch_bounds__(256) k_sort_keys_rank(const uint64_t *keys, uint64_t *out,
+                                                        long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    uint64_t x = keys[i];
+    long long r = 0;
+    for (long long j = 0; j < n; ++j) r += keys[j] < x ? 1 : 0;
+    out[r] = x;
+  }
+}
+
+// pair k (in order of the parent's id): electron at ne0 + k, ion at ni0 + k
+template <typename T>
+__global__ void __launch_bounds__(256) k_append(MccLaunchT<T> M, const uint64_t *keys,
+                                                long long tot, long long ne0, long long ni0,
+                                                uint32_t id_e0, uint32_t id_i0) {
+  long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double de = 0.0;
-  if (p < M.ne && M.flag[p]) {
-    long long k = M.offs[p];
+  if (k < tot) {
+    long long p = (long long)(uint32_t)(keys[k] & 0xffffffffull);
     double u1[4], u2[4];
     draw4(M.seed, kStreamMccE, M.e.id[p], M.step, 1, u1);
     draw4(M.seed, kStreamMccE, M.e.id[p], M.step, 2, u2);
@@ -197,18 +246,27 @@ cudaError_t launch_mcc_collide(const MccLaunchT<T> &M, cudaStream_t s) {
 }
 
 template <typename T>
-cudaError_t launch_mcc_append(const MccLaunchT<T> &M, long long ne0, long long ni0,
-                              uint32_t id_e0, uint32_t id_i0, cudaStream_t s) {
-  if (M.ne <= 0) return cudaSuccess;
-  k_append<T><<<(unsigned)((M.ne + 255) / 256), 256, 0, s>>>(M, ne0, ni0, id_e0, id_i0);
+cudaError_t launch_mcc_append(const MccLaunchT<T> &M, long long tot, long long ne0,
+                              long long ni0, uint32_t id_e0, uint32_t id_i0, cudaStream_t s) {
+  if (tot <= 0 || M.ne <= 0) return cudaSuccess;
+  k_iz_keys<T><<<(unsigned)((M.ne + 255) / 256), 256, 0, s>>>(M);
+  const uint64_t *sorted = M.keys;
+  if (tot <= kSortMax) {
+    k_sort_keys_block<<<1, 1024, 0, s>>>(M.keys, (int)tot);
+  } else {
+    long long nb = (tot + 255) / 256;
+    k_sort_keys_rank<<<(unsigned)(nb < 152 * 8 ? nb : 152 * 8), 256, 0, s>>>(M.keys, M.keys2, tot);
+    sorted = M.keys2;
+  }
+  k_append<T><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(M, sorted, tot, ne0, ni0, id_e0, id_i0);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_mcc_collide<double>(const MccLaunchT<double> &, cudaStream_t);
 template cudaError_t launch_mcc_collide<float>(const MccLaunchT<float> &, cudaStream_t);
 template cudaError_t launch_mcc_append<double>(const MccLaunchT<double> &, long long, long long,
-                                               uint32_t, uint32_t, cudaStream_t);
+                                               long long, uint32_t, uint32_t, cudaStream_t);
 template cudaError_t launch_mcc_append<float>(const MccLaunchT<float> &, long long, long long,
-                                              uint32_t, uint32_t, cudaStream_t);
+                                              long long, uint32_t, uint32_t, cudaStream_t);
 
 }  // namespace pic

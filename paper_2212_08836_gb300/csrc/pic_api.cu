@@ -26,9 +26,11 @@ struct pic_ctx {
   int cur[2];
   int mixed;                 // 1: FP32 particle store and push (PIC_MIXED)
   AlphaOut alpha;            // mixed form: normalised accelerations per species
-  int *queue, *qcount;       // mixed form: work queue of the general push path
+  int *queue, *qcount;       // work queue of the general push path (both forms)
   int *q_cell;
-  float *q_real[6];
+  float *q_real[6];          // mixed form queue records
+  double *q_real64[6];       // FP64 form queue records
+  AlphaOut64 alpha64;        // FP64 form: normalised accelerations per species
   double *er, *ez, *h;      // E^n, H^n
   double *er1, *ez1;        // Picard iterate E^{n+1,k}
   double *er2, *ez2, *h2;   // solver output
@@ -38,6 +40,7 @@ struct pic_ctx {
   FieldOp F;
   DevCounters *cnt;
   int32_t *flag, *offs, *counts, *coffs, *cursor;
+  uint64_t *keys, *keys2;   // MCC: ionizing parents ordered by id
   long long *total;
   void *scan_scratch;
   double *diag;             // 8 doubles
@@ -119,15 +122,21 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
       P.w = (double *)K.take(pc * rs);
       P.id = (uint32_t *)K.take(pc * 4);
     }
+  x->queue = (int *)K.take(pc * 4);
+  x->qcount = (int *)K.take(256);
+  x->q_cell = (int *)K.take(pc * 4);
   if (c->precision == PIC_MIXED) {
     for (int s = 0; s < 2; ++s) {
       x->alpha.ar[s] = (float *)K.take(ner * 4);
       x->alpha.az[s] = (float *)K.take(nez * 4);
     }
-    x->queue = (int *)K.take(pc * 4);
-    x->qcount = (int *)K.take(256);
-    x->q_cell = (int *)K.take(pc * 4);
     for (int k = 0; k < 6; ++k) x->q_real[k] = (float *)K.take(pc * 4);
+  } else {
+    for (int s = 0; s < 2; ++s) {
+      x->alpha64.ar[s] = (double *)K.take(ner * 8);
+      x->alpha64.az[s] = (double *)K.take(nez * 8);
+    }
+    for (int k = 0; k < 6; ++k) x->q_real64[k] = (double *)K.take(pc * 8);
   }
   x->er = (double *)K.take(ner * 8);
   x->ez = (double *)K.take(nez * 8);
@@ -153,6 +162,8 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
   x->cnt = (DevCounters *)K.take(sizeof(DevCounters));
   x->flag = (int32_t *)K.take(pc * 4);
   x->offs = (int32_t *)K.take(pc * 4);
+  x->keys = (uint64_t *)K.take(pc * 8);
+  x->keys2 = (uint64_t *)K.take(pc * 8);
   int ncell = nr * nz;
   x->counts = (int32_t *)K.take((size_t)(ncell + 1) * 4);
   x->coffs = (int32_t *)K.take((size_t)(ncell + 1) * 4);
@@ -227,6 +238,21 @@ int push_all(pic_ctx *x, const double *erh, const double *ezh, double *ir, doubl
     }
     L.counters = counters;
     L.ke_lost = kel;
+    L.ar = x->alpha64.ar[s];
+    L.az = x->alpha64.az[s];
+    L.cr = x->cfg.dt / x->g.dr;
+    L.cz = x->cfg.dt / x->g.dz;
+    L.icr = x->g.dr / x->cfg.dt;
+    L.icz = x->g.dz / x->cfg.dt;
+    L.queue = x->queue;
+    L.qcount = x->qcount;
+    L.q_cell = x->q_cell;
+    L.q_a = x->q_real64[0];
+    L.q_b = x->q_real64[1];
+    L.q_vr = x->q_real64[2];
+    L.q_vt = x->q_real64[3];
+    L.q_vz = x->q_real64[4];
+    L.q_w = x->q_real64[5];
     cudaError_t e;
     if (x->mixed) {
       PushLaunch32 M;
@@ -266,6 +292,7 @@ int push_all(pic_ctx *x, const double *erh, const double *ezh, double *ir, doubl
       if (L.n > 0) x->launches += M.wbt == 0.f ? 1 : 0;  // fast + general kernels
     } else {
       e = launch_push_fp64(L, x->s);
+      if (L.n > 0) x->launches += L.wb == 0.0 ? 1 : 0;  // fast + general kernels
     }
     if (e != cudaSuccess) return PIC_E_CUDA;
     if (L.n > 0) {
@@ -341,8 +368,8 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
   x->mixed = cfg->precision == PIC_MIXED ? 1 : 0;
   for (int sp = 0; sp < 2; ++sp) {
     double qm = sp == 0 ? -kQE / kME : kQE / kMAr;
-    x->alpha.sr[sp] = qm * cfg->dt * cfg->dt / x->g.dr;
-    x->alpha.sz[sp] = qm * cfg->dt * cfg->dt / x->g.dz;
+    x->alpha.sr[sp] = x->alpha64.sr[sp] = qm * cfg->dt * cfg->dt / x->g.dr;
+    x->alpha.sz[sp] = x->alpha64.sz[sp] = qm * cfg->dt * cfg->dt / x->g.dz;
   }
   x->ng = cfg->mcc_on ? cfg->gas_pressure / (kKB * cfg->gas_temp) : 0.0;
 
@@ -376,14 +403,34 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
   F.L = cfg->L;
   double dr = F.dr, dz = F.dz, hdt2 = 0.5 * cfg->dt * cfg->dt;
   std::vector<double> Q((size_t)nz * nz), QT((size_t)nz * nz), lam(nz);
-  for (int m = 0; m < nz; ++m) {
+  F.half = (nz % 2 == 0) ? nz / 2 : 0;
+  const int hz = F.half;
+  auto qbasis = [&](int j, int m) {
     double cm = m == 0 ? sqrt(1.0 / nz) : sqrt(2.0 / nz);
+    return cm * cos(kPi * m * (j + 0.5) / nz);
+  };
+  // column of mode m in the transformed arrays
+  std::vector<int> col(nz);
+  for (int m = 0; m < nz; ++m) {
     lam[m] = 2.0 - 2.0 * cos(kPi * m / nz);
-    for (int j = 0; j < nz; ++j) {
-      double v = cm * cos(kPi * m * (j + 0.5) / nz);
-      Q[(size_t)j * nz + m] = v;
-      QT[(size_t)m * nz + j] = v;
-    }
+    col[m] = hz ? ((m % 2 == 0) ? m / 2 : hz + m / 2) : m;
+  }
+  if (hz) {
+    for (int j = 0; j < hz; ++j)
+      for (int k = 0; k < hz; ++k) {
+        double ve = qbasis(j, 2 * k), vo = qbasis(j, 2 * k + 1);
+        Q[(size_t)j * hz + k] = ve;                       // Qe
+        Q[(size_t)hz * hz + (size_t)j * hz + k] = vo;     // Qo
+        QT[(size_t)k * hz + j] = ve;                      // Qe^T
+        QT[(size_t)hz * hz + (size_t)k * hz + j] = vo;    // Qo^T
+      }
+  } else {
+    for (int m = 0; m < nz; ++m)
+      for (int j = 0; j < nz; ++j) {
+        double v = qbasis(j, m);
+        Q[(size_t)j * nz + m] = v;
+        QT[(size_t)m * nz + j] = v;
+      }
   }
   std::vector<double> mass(nr), kz(nr), kdiag(nr), eoff(nr, 0.0);
   auto rh = [&](int i) { return ((double)i + 0.5) * dr; };
@@ -401,15 +448,16 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
   }
   std::vector<double> lf((size_t)nr * nz), ci((size_t)nr * nz);
   for (int m = 0; m < nz; ++m) {
+    int cm = col[m];
     double c = mass[0] + kz[0] * lam[m] + kdiag[0];
-    lf[m] = 0.0;
-    ci[m] = 1.0 / c;
+    lf[cm] = 0.0;
+    ci[cm] = 1.0 / c;
     for (int i = 1; i < nr; ++i) {
       double d = mass[i] + kz[i] * lam[m] + kdiag[i];
       double l = eoff[i] / c;
       c = d - l * eoff[i];
-      lf[(size_t)i * nz + m] = l;
-      ci[(size_t)i * nz + m] = 1.0 / c;
+      lf[(size_t)i * nz + cm] = l;
+      ci[(size_t)i * nz + cm] = 1.0 / c;
     }
   }
   cudaError_t e = cudaSuccess;
@@ -524,13 +572,13 @@ int pic_load_particles(pic_ctx *x) {
 int pic_push_deposit(pic_ctx *x, const double *erh, const double *ezh, double *ir, double *iz,
                      int write, unsigned long long *counters, double *kel) {
   if (!x || !erh || !ezh) return PIC_E_CONFIG;
-  if (x->mixed) {
-    // normalised accelerations of both species from the caller's E^{n+1/2}
-    if (launch_half_field_alpha(x->g, erh, ezh, erh, ezh, x->erh, x->ezh, x->alpha, x->s) !=
-        cudaSuccess)
-      return PIC_E_CUDA;
-    x->launches += 1;
-  }
+  // normalised accelerations of both species from the caller's E^{n+1/2}
+  cudaError_t ae = x->mixed ? launch_half_field_alpha(x->g, erh, ezh, erh, ezh, x->erh, x->ezh,
+                                                      x->alpha, x->s)
+                            : launch_half_field_alpha64(x->g, erh, ezh, erh, ezh, x->erh,
+                                                        x->ezh, x->alpha64, x->s);
+  if (ae != cudaSuccess) return PIC_E_CUDA;
+  x->launches += 1;
   return push_all(x, erh, ezh, ir, iz, write, counters, kel, write ? x->wall : nullptr);
 }
 
@@ -568,9 +616,11 @@ int pic_mcc(pic_ctx *x, unsigned long long step, long long *counts, double *de_c
   M.flag = x->flag;
   M.offs = x->offs;
   M.cnt = x->cnt;
+  M.keys = x->keys;
+  M.keys2 = x->keys2;
   MccLaunchT<float> M32{M.seed, M.step, M.ng, M.tg, M.numax_e, M.pnull_e, M.pnull_i, M.gmax,
                         M.thr_e, M.thr_i, M.ne, M.ni, as32(M.e), as32(M.i), M.flag, M.offs,
-                        M.cnt};
+                        M.cnt, M.keys, M.keys2};
   if (e == cudaSuccess) e = x->mixed ? launch_mcc_collide(M32, x->s) : launch_mcc_collide(M, x->s);
   if (e == cudaSuccess) e = scan_exclusive(x->flag, x->offs, M.ne, x->total, x->scan_scratch, x->s);
   x->launches += (M.ne > 0 || M.ni > 0 ? 1 : 0) + (M.ne > 0 ? 3 : 0);
@@ -586,10 +636,10 @@ int pic_mcc(pic_ctx *x, unsigned long long step, long long *counts, double *de_c
       rc = PIC_E_CAPACITY;
       capov = (unsigned long long)tot;
     } else {
-      e = x->mixed ? launch_mcc_append(M32, x->n[0], x->n[1], x->next_id[0], x->next_id[1], x->s)
-                   : launch_mcc_append(M, x->n[0], x->n[1], x->next_id[0], x->next_id[1], x->s);
+      e = x->mixed ? launch_mcc_append(M32, tot, x->n[0], x->n[1], x->next_id[0], x->next_id[1], x->s)
+                   : launch_mcc_append(M, tot, x->n[0], x->n[1], x->next_id[0], x->next_id[1], x->s);
       if (e != cudaSuccess) return PIC_E_CUDA;
-      x->launches += 1;
+      x->launches += 3;
       x->n[0] += tot;
       x->n[1] += tot;
       x->next_id[0] += (uint32_t)tot;
@@ -637,7 +687,8 @@ int pic_step(pic_ctx *x, int nsteps, pic_step_stats *st) {
       cudaError_t he =
           x->mixed ? launch_half_field_alpha(x->g, x->er, x->ez, x->er1, x->ez1, x->erh, x->ezh,
                                              x->alpha, s)
-                   : launch_half_field(x->g, x->er, x->ez, x->er1, x->ez1, x->erh, x->ezh, s);
+                   : launch_half_field_alpha64(x->g, x->er, x->ez, x->er1, x->ez1, x->erh,
+                                               x->ezh, x->alpha64, s);
       if (he != cudaSuccess) return PIC_E_CUDA;
       x->launches += 1;
       if (cudaMemsetAsync(x->ir, 0, ner * 8, s) != cudaSuccess) return PIC_E_CUDA;

