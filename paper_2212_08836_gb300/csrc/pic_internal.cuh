@@ -24,11 +24,8 @@ constexpr uint64_t kStreamLoadPos = 0x20, kStreamLoadVe = 0x21, kStreamLoadVi = 
 constexpr uint64_t kStreamMccE = 0x10, kStreamMccI = 0x11;
 constexpr uint64_t kLoadStep = 0xFFFFFFFFFFFFFFFFull;
 
-// Sub-step solver limits (FP64 form)
+// at most this many sub-steps per particle and pass (PIC_E_SUBSTEP beyond)
 constexpr int kNsubMax = 64;
-constexpr int kNewtonMax = 30;
-constexpr double kTolX = 1e-14;
-constexpr double kTolT = 1e-14;
 
 // Philox4x64-10 (Salmon et al., SC'11): 64x64 -> 128-bit products via umul64hi.
 __device__ __forceinline__ void philox4x64(uint64_t c[4], uint64_t k0, uint64_t k1) {

@@ -1,0 +1,429 @@
+// General sub-step path of the CN mover + charge-conserving deposit (rows a2,
+// a3, a6; Sec. 2.1, Eqs. 3-4), shared by the FP64 and FP32 forms through the
+// scalar type T.  It serves the particles the fast kernels do not finish
+// (cell crossings, particles on faces, near the axis, optional external B_z).
+//
+// Normalised units: lengths in cells (r in units of dr, z in units of dz),
+// time in units of dt (tau in [0, 1]), velocities in cells per step
+// (u = v*dt/dx), accelerations alpha = (q/m)*E*dt^2/dx per species.  With
+// am = a + da/2, bm = b + db/2, rho = ic + a, one sub-step of length tau solves
+//   f1 = db - tau*uz - tau^2/2*alpha_z(am)                     = 0
+//   f2 = da - tau*ur - tau^2/2*(alpha_r(bm) + C(da))           = 0
+//   C  = ut_m^2/rho_m + wt*ut_m,  ut' = (P - wt*rho'^2/2)/rho'
+// (P = rho*ut + wt*rho^2/2, the exactly conserved CN canonical angular
+// momentum, wt = qm*Bz*dt) by Newton for (da, db) at given tau, or for
+// (tau, other offset) when the sub-step must end exactly on a face.
+#pragma once
+
+#include "pic_internal.cuh"
+
+namespace pic {
+
+template <typename T>
+struct Num;
+
+template <>
+struct Num<float> {
+  static constexpr float tol = 1e-6f;    // offsets [cells] and tau [steps]
+  static constexpr float ulpf = 4.8e-7f;  // a few ulp, relative
+  __device__ static __forceinline__ float rcp(float x) { return __fdividef(1.f, x); }
+  // exact float -> double by exponent re-biasing in integer registers (no FP64
+  // instruction; denormals are flushed in the FP32 unit anyway)
+  __device__ static __forceinline__ double to_double(float f) {
+    unsigned u = __float_as_uint(f);
+    unsigned e = (u >> 23) & 0xffu;
+    unsigned long long bits = ((unsigned long long)(u >> 31) << 63) |
+                              ((unsigned long long)(e + 896u) << 52) |
+                              ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double(e == 0u ? 0ull : bits);
+  }
+};
+
+template <>
+struct Num<double> {
+  static constexpr double tol = 1e-13;
+  static constexpr double ulpf = 1e-15;
+  __device__ static __forceinline__ double rcp(double x) { return 1.0 / x; }
+  __device__ static __forceinline__ double to_double(double f) { return f; }
+};
+
+constexpr int kNewtonMaxGen = 30;
+
+// stopping tests: the change of the r-offset is measured relative to r' close
+// to the axis (where r' is small), never below a few ulp of the unknown
+template <typename T>
+__device__ __forceinline__ T tol_r(T rho1, T da) {
+  T one = (T)1, zero = (T)0;
+  return fmax(Num<T>::tol * fmin(one, fmax(rho1, zero)), Num<T>::ulpf * fabs(da));
+}
+template <typename T>
+__device__ __forceinline__ T tol_x(T x) {
+  return fmax(Num<T>::tol, Num<T>::ulpf * fabs(x));
+}
+
+template <typename T>
+struct SubT {
+  T ar0, gar, az0, gaz;
+  T a, b, rho, ur, ut, uz, P;
+};
+
+template <typename T>
+struct ResT {
+  T f1, f2, f1a, f1t, f2a, f2b, f2t, A, az, ut1;
+};
+
+template <typename T>
+__device__ __forceinline__ void eval_gen(const SubT<T> &s, T wt, T da, T db, T tau, ResT<T> &o) {
+  const T h = (T)0.5, q = (T)0.25, zero = (T)0, one = (T)1, two = (T)2;
+  T rho1 = s.rho + da;
+  T rhom = s.rho + h * da;
+  T ut1, dut1;
+  if (rho1 > zero) {
+    T inv1 = Num<T>::rcp(rho1);
+    ut1 = (s.P - h * wt * rho1 * rho1) * inv1;
+    dut1 = -s.P * inv1 * inv1 - h * wt;
+  } else {
+    ut1 = s.ut;
+    dut1 = zero;
+  }
+  T utm = h * (s.ut + ut1);
+  T dutm = h * dut1;
+  T C, dC;
+  if (rhom > zero) {
+    T invm = Num<T>::rcp(rhom);
+    C = utm * utm * invm + wt * utm;
+    dC = two * utm * dutm * invm - h * utm * utm * invm * invm + wt * dutm;
+  } else {
+    C = wt * utm;
+    dC = wt * dutm;
+  }
+  T am = s.a + h * da;
+  T bm = s.b + h * db;
+  T az = s.az0 + s.gaz * am;
+  T A = s.ar0 + s.gar * bm + C;
+  T t2 = tau * tau;
+  o.f1 = db - tau * s.uz - h * t2 * az;
+  o.f2 = da - tau * s.ur - h * t2 * A;
+  o.f1a = -q * t2 * s.gaz;
+  o.f1t = -s.uz - tau * az;
+  o.f2a = one - h * t2 * dC;
+  o.f2b = -q * t2 * s.gar;
+  o.f2t = -s.ur - tau * A;
+  o.A = A;
+  o.az = az;
+  o.ut1 = ut1;
+}
+
+template <typename T>
+__device__ __forceinline__ bool interior_gen(const SubT<T> &s, T wt, T tau, T &pda, T &pdb,
+                                             unsigned &it_count) {
+  const T h = (T)0.5, zero = (T)0;
+  // predictor with the acceleration at the start point; the centrifugal term
+  // is left out when the angular step is not small (close to the axis)
+  T A0 = s.ar0 + s.gar * s.b + wt * s.ut;
+  if (s.rho > zero && tau * fabs(s.ut) < (T)0.25 * s.rho) A0 += s.ut * s.ut * Num<T>::rcp(s.rho);
+  T da = tau * (s.ur + h * tau * A0);
+  T db = tau * (s.uz + h * tau * (s.az0 + s.gaz * s.a));
+  if (s.P != zero && s.rho + da <= zero) da = -h * s.rho;
+  for (int it = 0; it < kNewtonMaxGen; ++it) {
+    ResT<T> o;
+    eval_gen(s, wt, da, db, tau, o);
+    it_count++;
+    // [f1a 1; f2a f2b] [xa; xb] = -[f1; f2]
+    T det = o.f1a * o.f2b - o.f2a;
+    if (!(det != zero) || !isfinite(det)) return false;
+    T idet = Num<T>::rcp(det);
+    T xa = (-o.f1 * o.f2b + o.f2) * idet;
+    T xb = (-o.f1a * o.f2 + o.f2a * o.f1) * idet;
+    T nda = da + xa, ndb = db + xb;
+    if (s.P != zero && s.rho + nda <= zero) nda = h * (da - s.rho);
+    T ca = fabs(nda - da), cb = fabs(ndb - db);
+    da = nda;
+    db = ndb;
+    if (!isfinite(da) || !isfinite(db)) return false;
+    if (ca <= tol_r<T>(s.rho + da, da) && cb <= tol_x<T>(db)) {
+      pda = da;
+      pdb = db;
+      return true;
+    }
+  }
+  return false;
+}
+
+template <typename T>
+__device__ __forceinline__ bool landing_gen(const SubT<T> &s, T wt, int dir, T X, T t0, T oth0,
+                                            T &ptau, T &poth, unsigned &it_count) {
+  const T h = (T)0.5, q = (T)0.25, zero = (T)0, one = (T)1;
+  T tau = t0, oth = oth0;
+  for (int it = 0; it < kNewtonMaxGen; ++it) {
+    T da = dir == 0 ? X : oth;
+    T db = dir == 0 ? oth : X;
+    ResT<T> o;
+    eval_gen(s, wt, da, db, tau, o);
+    it_count++;
+    T gF, gFo, gFt, gO, gOo, gOt;
+    if (dir == 0) {
+      gO = o.f1; gOo = one; gOt = o.f1t;
+      if (X != zero) {
+        gF = o.f2; gFo = o.f2b; gFt = o.f2t;
+      } else {  // return to the face the particle sits on: residual / tau
+        gF = -s.ur - h * tau * o.A;
+        gFo = -q * tau * s.gar;
+        gFt = -h * o.A;
+      }
+    } else {
+      gO = o.f2; gOo = o.f2a; gOt = o.f2t;
+      if (X != zero) {
+        gF = o.f1; gFo = o.f1a; gFt = o.f1t;
+      } else {
+        gF = -s.uz - h * tau * o.az;
+        gFo = -q * tau * s.gaz;
+        gFt = -h * o.az;
+      }
+    }
+    T det = gFo * gOt - gFt * gOo;
+    if (!(det != zero) || !isfinite(det)) return false;
+    T idet = Num<T>::rcp(det);
+    T xo = (-gF * gOt + gO * gFt) * idet;
+    T xt = (-gFo * gO + gOo * gF) * idet;
+    T noth = oth + xo, ntau = tau + xt;
+    if (dir == 1 && s.P != zero && s.rho + noth <= zero) noth = h * (oth - s.rho);
+    T co = fabs(noth - oth), ct = fabs(ntau - tau);
+    oth = noth;
+    tau = ntau;
+    if (!isfinite(oth) || !isfinite(tau)) return false;
+    T to = dir == 1 ? tol_r<T>(s.rho + oth, oth) : tol_x<T>(oth);
+    if (co <= to && ct <= tol_x<T>(tau)) {
+      ptau = tau;
+      poth = oth;
+      return true;
+    }
+  }
+  return false;
+}
+
+// particle on a face of its cell with its normal velocity pointing out moves to
+// the neighbour cell; r = 0 reflects; walls absorb (1: r = R, 2: z = L, 3: z = 0)
+template <typename T>
+__device__ __forceinline__ int transition_gen(int nr, int nz, int &ic, int &jc, T &a, T &b, T &ur,
+                                              T &uz) {
+  const T zero = (T)0, one = (T)1;
+  if (a == one && ur > zero) {
+    if (ic + 1 == nr) return 1;
+    ic += 1;
+    a = zero;
+  } else if (a == zero && ur < zero) {
+    if (ic == 0) ur = -ur;
+    else { ic -= 1; a = one; }
+  }
+  if (b == one && uz > zero) {
+    if (jc + 1 == nz) return 2;
+    jc += 1;
+    b = zero;
+  } else if (b == zero && uz < zero) {
+    if (jc == 0) return 3;
+    jc -= 1;
+    b = one;
+  }
+  return 0;
+}
+
+struct Tally {
+  unsigned err, abs, sub, fb, newton;
+};
+
+template <typename T>
+struct GenArgs {
+  int nr, nz;
+  const T *ar, *az;      // normalised accelerations of the species
+  T wt, icr, icz;        // qm*Bz*dt; dr/dt, dz/dt
+  double q, m;
+  T qf;                  // q in T
+  double *ir, *iz;       // crossed charge [C]
+  int write;
+  PartsT<T> p;
+  double *wall_z0, *wall_zl, *wall_r;
+  double *ke_lost;
+};
+
+// one particle from its start state (offsets a, b; normalised velocities)
+template <typename T>
+__device__ void push_general(const GenArgs<T> &L, long long p, int c0, T a, T b, T ur, T ut, T uz,
+                             const T w, Tally &Tl) {
+  const T zero = (T)0, one = (T)1, h = (T)0.5, two = (T)2;
+  const int nr = L.nr, nz = L.nz, nz1 = nz + 1;
+  const T wt = L.wt;
+  if (c0 < 0 || c0 >= nr * nz) return;
+  int ic = c0 / nz, jc = c0 - (c0 / nz) * nz;
+  T tau = one;
+  T tT = tau;
+  int nsub = 0;
+  int absorbed = transition_gen<T>(nr, nz, ic, jc, a, b, ur, uz);
+  while (tau > zero && !absorbed) {
+    if (++nsub > kNsubMax) {
+      Tl.err++;
+      break;
+    }
+    SubT<T> s;
+    s.ar0 = L.ar[ic * nz1 + jc];
+    s.gar = L.ar[ic * nz1 + jc + 1] - s.ar0;
+    s.az0 = L.az[ic * nz + jc];
+    s.gaz = L.az[(ic + 1) * nz + jc] - s.az0;
+    s.a = a; s.b = b;
+    s.rho = (T)ic + a;
+    s.ur = ur; s.ut = ut; s.uz = uz;
+    s.P = s.rho * ut + h * wt * s.rho * s.rho;
+    T da, db;
+    if (!interior_gen<T>(s, wt, tT, da, db, Tl.newton)) {
+      tT *= h;
+      Tl.fb++;
+      continue;
+    }
+    T a1 = a + da, b1 = b + db;
+    T step_t;
+    int land_dir = -1;
+    T land_face = zero;
+    if (a1 >= zero && a1 <= one && b1 >= zero && b1 <= one) {
+      step_t = tT;
+    } else {
+      T best_t = zero, best_oth = zero, best_face = zero;
+      int best_dir = -1;
+#pragma unroll 1
+      for (int dir = 0; dir < 2; ++dir) {
+        T x0 = dir == 0 ? a : b;
+        T x1 = dir == 0 ? a1 : b1;
+        T dx = dir == 0 ? da : db;
+        T doth = dir == 0 ? db : da;
+        T face;
+        if (x1 > one) face = one;
+        else if (x1 < zero) face = zero;
+        else continue;
+        T X = face - x0;
+        T v0 = dir == 0 ? ur : uz;
+        T g0;
+        if (X != zero) {
+          g0 = tT * (X / dx);
+        } else {  // quadratic model through the trial end point
+          T alpha = two * (dx - v0 * tT) / (tT * tT);
+          g0 = -two * v0 / alpha;
+        }
+        T oth0 = doth * (g0 / tT);
+        T tt = zero, toth = zero;
+        if (!(g0 > zero) || !landing_gen<T>(s, wt, dir, X, g0, oth0, tt, toth, Tl.newton)) continue;
+        if (!(tt > zero) || tt > tT) continue;
+        T xo = (dir == 0 ? b : a) + toth;
+        if (xo < zero || xo > one) continue;
+        if (best_dir < 0 || tt < best_t) {
+          best_dir = dir;
+          best_t = tt;
+          best_oth = toth;
+          best_face = face;
+        }
+      }
+      if (best_dir < 0) {
+        tT *= h;
+        Tl.fb++;
+        continue;
+      }
+      step_t = best_t;
+      land_dir = best_dir;
+      land_face = best_face;
+      if (best_dir == 0) {
+        da = best_face - a;
+        db = best_oth;
+      } else {
+        db = best_face - b;
+        da = best_oth;
+      }
+    }
+    ResT<T> o;
+    eval_gen<T>(s, wt, da, db, step_t, o);
+    T am = a + h * da, bm = b + h * db;
+    T nur = ur + step_t * o.A;
+    T nuz = uz + step_t * o.az;
+    T nut = o.ut1;
+    if (L.ir) {
+      T fr = L.qf * w * da, fz = L.qf * w * db;
+      atomicAdd(&L.ir[ic * nz1 + jc], Num<T>::to_double(fr * (one - bm)));
+      atomicAdd(&L.ir[ic * nz1 + jc + 1], Num<T>::to_double(fr * bm));
+      atomicAdd(&L.iz[ic * nz + jc], Num<T>::to_double(fz * (one - am)));
+      atomicAdd(&L.iz[(ic + 1) * nz + jc], Num<T>::to_double(fz * am));
+    }
+    if (land_dir == 0) {
+      a = land_face;
+      b = b + db;
+    } else if (land_dir == 1) {
+      b = land_face;
+      a = a + da;
+    } else {
+      a = a + da;
+      b = b + db;
+    }
+    a = fmin(fmax(a, zero), one);
+    b = fmin(fmax(b, zero), one);
+    ur = nur; ut = nut; uz = nuz;
+    tau = tau - step_t;
+    Tl.sub++;
+    absorbed = transition_gen<T>(nr, nz, ic, jc, a, b, ur, uz);
+    if (absorbed) break;
+    tT = tau;
+  }
+  T vr = ur * L.icr, vt = ut * L.icr, vz = uz * L.icz;
+  if (absorbed) {
+    Tl.abs++;
+    if (L.write) {
+      double qw = L.q * (double)w;
+      if (absorbed == 1 && L.wall_r) {
+        atomicAdd(&L.wall_r[jc], qw * (1.0 - (double)b));
+        atomicAdd(&L.wall_r[jc + 1], qw * (double)b);
+      } else if (absorbed == 2 && L.wall_zl) {
+        atomicAdd(&L.wall_zl[ic], qw * (1.0 - (double)a));
+        atomicAdd(&L.wall_zl[ic + 1], qw * (double)a);
+      } else if (absorbed == 3 && L.wall_z0) {
+        atomicAdd(&L.wall_z0[ic], qw * (1.0 - (double)a));
+        atomicAdd(&L.wall_z0[ic + 1], qw * (double)a);
+      }
+    }
+    if (L.ke_lost) {
+      double v2 = (double)vr * vr + (double)vt * vt + (double)vz * vz;
+      atomicAdd(L.ke_lost, 0.5 * L.m * (double)w * v2);
+    }
+  }
+  if (L.write) {
+    L.p.cell[p] = absorbed ? -1 : ic * nz + jc;
+    L.p.a[p] = a; L.p.b[p] = b;
+    L.p.vr[p] = vr; L.p.vt[p] = vt; L.p.vz[p] = vz;
+  }
+}
+
+__device__ __forceinline__ unsigned long long wsum_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// algorithmic operation counts of the general path: 75 per Newton iteration
+// (one residual/Jacobian evaluation and update), 93 per accepted sub-step
+constexpr unsigned kOpGenNewton = 75, kOpGenAccept = 93;
+
+// counters[0..4] += errors, absorbed, accepted sub-steps, fallbacks, operations
+__device__ __forceinline__ void flush_tally(unsigned long long *counters, const Tally &T, int lane,
+                                            unsigned fast_newton, unsigned fast_acc,
+                                            unsigned op_fast_newton, unsigned op_fast_acc) {
+  if (!counters) return;
+  unsigned long long e0 = wsum_u64(T.err), e1 = wsum_u64(T.abs), e2 = wsum_u64(T.sub),
+                     e3 = wsum_u64(T.fb), e4 = wsum_u64(T.newton), e5 = wsum_u64(fast_newton),
+                     e6 = wsum_u64(fast_acc);
+  if (lane == 0) {
+    if (e0) atomicAdd(&counters[0], e0);
+    if (e1) atomicAdd(&counters[1], e1);
+    if (e2 + e6) atomicAdd(&counters[2], e2 + e6);
+    if (e3) atomicAdd(&counters[3], e3);
+    unsigned long long fl = kOpGenNewton * e4 + kOpGenAccept * e2 +
+                            (unsigned long long)op_fast_newton * e5 +
+                            (unsigned long long)op_fast_acc * e6;
+    if (fl) atomicAdd(&counters[4], fl);
+  }
+}
+
+}  // namespace pic
