@@ -40,7 +40,7 @@ DFMA_PER_CYCLE = 304
 BYTES_PER_PUSH_FP64 = 52
 # ncu DRAM bytes (read + write) per push of the current FP64 kernel, from the
 # profile in profiles/ (None when the kernel changed after the capture)
-TRAFFIC_PER_PUSH = 54.07  # profiles/push_fp64_large_reactor.md: (222.16 + 4.63) MB / 4194304 pushes
+TRAFFIC_PER_PUSH = None  # re-measured per kernel change (profiles/)
 
 
 def peaks():
