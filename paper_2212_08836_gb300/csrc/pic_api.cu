@@ -28,8 +28,8 @@ struct pic_ctx {
   AlphaOut alpha;            // mixed form: normalised accelerations per species
   int *queue, *qcount;       // work queue of the general push path (both forms)
   int *q_cell;
-  float *q_real[6];          // mixed form queue records
-  double *q_real64[6];       // FP64 form queue records
+  float *q_real[8];          // mixed form queue records
+  double *q_real64[8];       // FP64 form queue records
   AlphaOut64 alpha64;        // FP64 form: normalised accelerations per species
   double *er, *ez, *h;      // E^n, H^n
   double *er1, *ez1;        // Picard iterate E^{n+1,k}
@@ -130,13 +130,13 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
       x->alpha.ar[s] = (float *)K.take(ner * 4);
       x->alpha.az[s] = (float *)K.take(nez * 4);
     }
-    for (int k = 0; k < 6; ++k) x->q_real[k] = (float *)K.take(pc * 4);
+    for (int k = 0; k < 8; ++k) x->q_real[k] = (float *)K.take(pc * 4);
   } else {
     for (int s = 0; s < 2; ++s) {
       x->alpha64.ar[s] = (double *)K.take(ner * 8);
       x->alpha64.az[s] = (double *)K.take(nez * 8);
     }
-    for (int k = 0; k < 6; ++k) x->q_real64[k] = (double *)K.take(pc * 8);
+    for (int k = 0; k < 8; ++k) x->q_real64[k] = (double *)K.take(pc * 8);
   }
   x->er = (double *)K.take(ner * 8);
   x->ez = (double *)K.take(nez * 8);
@@ -208,95 +208,88 @@ void prof_collect(pic_ctx *x) {
   x->pending_launches = 0;
 }
 
+template <typename T>
+void fill_push(pic_ctx *x, int s, double q, double m, const double *erh, const double *ezh,
+               double *ir, double *iz, int write, unsigned long long *counters, double *kel,
+               double *const ws[3], PushLaunchT<T> &L) {
+  (void)erh;
+  (void)ezh;
+  const double dt = x->cfg.dt;
+  L.g = x->g;
+  L.q = q;
+  L.m = m;
+  L.qf = (T)q;
+  L.cr = (T)(dt / x->g.dr);
+  L.cz = (T)(dt / x->g.dz);
+  L.icr = (T)(x->g.dr / dt);
+  L.icz = (T)(x->g.dz / dt);
+  L.wbt = (T)(q / m * x->cfg.bz * dt);
+  L.inz = 1.0f / (float)x->g.nz;
+  L.n = x->n[s];
+  L.ir = ir;
+  L.iz = iz;
+  L.write = write;
+  L.wall_z0 = ws[0];
+  L.wall_zl = ws[1];
+  L.wall_r = ws[2];
+  L.counters = counters;
+  L.ke_lost = kel;
+}
+
+template <typename T>
+void set_queue(pic_ctx *x, T *const rec[8], PushLaunchT<T> &L) {
+  L.queue = x->queue;
+  L.qcount = x->qcount;
+  L.q_cell = x->q_cell;
+  L.q_a = rec[0];
+  L.q_b = rec[1];
+  L.q_ur = rec[2];
+  L.q_ut = rec[3];
+  L.q_uz = rec[4];
+  L.q_w = rec[5];
+  L.q_da = rec[6];
+  L.q_db = rec[7];
+}
+
 int push_all(pic_ctx *x, const double *erh, const double *ezh, double *ir, double *iz, int write,
              unsigned long long *counters, double *kel, double *wall) {
   bool timed = x->prof && x->nev < 128;
   if (timed) cudaEventRecord(x->ev[2 * x->nev], x->s);
   for (int s = 0; s < 2; ++s) {
-    PushLaunch L;
-    L.g = x->g;
-    L.dt = x->cfg.dt;
-    L.q = s == 0 ? -kQE : kQE;
-    L.m = s == 0 ? kME : kMAr;
-    L.qm = L.q / L.m;
-    L.wb = L.qm * x->cfg.bz;
-    L.n = x->n[s];
-    L.p = cur(x, s);
-    L.er = erh;
-    L.ez = ezh;
-    L.ir = ir;
-    L.iz = iz;
-    L.write = write;
-    int nr = x->g.nr, nz = x->g.nz;
+    const double q = s == 0 ? -kQE : kQE, m = s == 0 ? kME : kMAr;
+    double *ws[3] = {nullptr, nullptr, nullptr};
     if (wall) {
-      double *ws = wall + (size_t)s * (2 * (nr + 1) + nz + 1);
-      L.wall_z0 = ws;
-      L.wall_zl = ws + (nr + 1);
-      L.wall_r = ws + 2 * (nr + 1);
-    } else {
-      L.wall_z0 = L.wall_zl = L.wall_r = nullptr;
+      int nr = x->g.nr, nz = x->g.nz;
+      double *w0 = wall + (size_t)s * (2 * (nr + 1) + nz + 1);
+      ws[0] = w0;
+      ws[1] = w0 + (nr + 1);
+      ws[2] = w0 + 2 * (nr + 1);
     }
-    L.counters = counters;
-    L.ke_lost = kel;
-    L.ar = x->alpha64.ar[s];
-    L.az = x->alpha64.az[s];
-    L.cr = x->cfg.dt / x->g.dr;
-    L.cz = x->cfg.dt / x->g.dz;
-    L.icr = x->g.dr / x->cfg.dt;
-    L.icz = x->g.dz / x->cfg.dt;
-    L.queue = x->queue;
-    L.qcount = x->qcount;
-    L.q_cell = x->q_cell;
-    L.q_a = x->q_real64[0];
-    L.q_b = x->q_real64[1];
-    L.q_vr = x->q_real64[2];
-    L.q_vt = x->q_real64[3];
-    L.q_vz = x->q_real64[4];
-    L.q_w = x->q_real64[5];
     cudaError_t e;
+    long long n = x->n[s];
+    bool fast;
     if (x->mixed) {
-      PushLaunch32 M;
-      M.g = x->g;
-      M.q = L.q;
-      M.m = L.m;
-      M.dt = L.dt;
-      M.cr = (float)(x->cfg.dt / x->g.dr);
-      M.cz = (float)(x->cfg.dt / x->g.dz);
-      M.icr = (float)(x->g.dr / x->cfg.dt);
-      M.icz = (float)(x->g.dz / x->cfg.dt);
-      M.inz = 1.0f / (float)x->g.nz;
-      M.queue = x->queue;
-      M.qcount = x->qcount;
-      M.q_cell = x->q_cell;
-      M.q_a = x->q_real[0];
-      M.q_b = x->q_real[1];
-      M.q_ur = x->q_real[2];
-      M.q_ut = x->q_real[3];
-      M.q_uz = x->q_real[4];
-      M.q_w = x->q_real[5];
-      M.wbt = (float)(L.wb * x->cfg.dt);
-      M.n = L.n;
-      M.p = as32(L.p);
-      M.ar = x->alpha.ar[s];
-      M.az = x->alpha.az[s];
-      M.qf = (float)L.q;
-      M.ir = ir;
-      M.iz = iz;
-      M.write = write;
-      M.wall_z0 = L.wall_z0;
-      M.wall_zl = L.wall_zl;
-      M.wall_r = L.wall_r;
-      M.counters = counters;
-      M.ke_lost = kel;
-      e = launch_push_fp32(M, x->s);
-      if (L.n > 0) x->launches += M.wbt == 0.f ? 1 : 0;  // fast + general kernels
+      PushLaunchT<float> L;
+      fill_push(x, s, q, m, erh, ezh, ir, iz, write, counters, kel, ws, L);
+      L.p = as32(cur(x, s));
+      L.ar = x->alpha.ar[s];
+      L.az = x->alpha.az[s];
+      set_queue(x, x->q_real, L);
+      fast = L.wbt == 0.f;
+      e = launch_push(L, x->s);
     } else {
-      e = launch_push_fp64(L, x->s);
-      if (L.n > 0) x->launches += L.wb == 0.0 ? 1 : 0;  // fast + general kernels
+      PushLaunchT<double> L;
+      fill_push(x, s, q, m, erh, ezh, ir, iz, write, counters, kel, ws, L);
+      L.p = cur(x, s);
+      L.ar = x->alpha64.ar[s];
+      L.az = x->alpha64.az[s];
+      set_queue(x, x->q_real64, L);
+      fast = L.wbt == 0.0;
+      e = launch_push(L, x->s);
     }
     if (e != cudaSuccess) return PIC_E_CUDA;
-    if (L.n > 0) {
-      x->launches += 1;
+    if (n > 0) {
+      x->launches += fast ? 2 : 1;  // fast + general kernels
       if (timed) x->pending_launches += 1;
     }
   }

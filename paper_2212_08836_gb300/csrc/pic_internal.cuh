@@ -103,27 +103,33 @@ struct FieldOp {
   double *hhalf;       // nr x nz: H^{n+1/2}
 };
 
-struct PushLaunch {
+// One mover + deposit pass over one species (rows a2, a3, a6) in the scalar
+// type T of the particle store: double (plain form) or float (mixed form).
+template <typename T>
+struct PushLaunchT {
   Grid g;
-  double dt, q, qm, wb, m;
+  double q, m;             // species charge [C] and mass [kg]
+  T qf;                    // q in T
+  T cr, cz, icr, icz;      // dt/dr, dt/dz (velocity -> cells per step) and inverses
+  T wbt;                   // qm*Bz*dt (0: no external B_z)
+  float inz;               // 1/nz (cell -> (i, j) split without an integer division)
   long long n;
-  Parts p;
-  const double *er, *ez;
-  double *ir, *iz;
-  int write;
+  PartsT<T> p;
+  const T *ar, *az;        // normalised accelerations qm*E*dt^2/dx of this species
+  double *ir, *iz;         // crossed charge [C] (FP64, atomics)
+  int write;               // commit pass: write the new state
   double *wall_z0, *wall_zl, *wall_r;
   unsigned long long *counters;
   double *ke_lost;
-  // fast path: normalised accelerations qm*E*dt^2/dx of this species and scalings
-  const double *ar, *az;
-  double cr, cz, icr, icz;   // dt/dr, dt/dz and inverses
-  int *queue, *qcount;       // scratch work queue for the general path (nullptr: all)
-  int *q_cell;
-  double *q_a, *q_b, *q_vr, *q_vt, *q_vz, *q_w;
+  int *queue, *qcount;     // scratch work queue for the general path (nullptr: all)
+  int *q_cell;             // queued start state: cell, offsets, normalised v, weight,
+  T *q_a, *q_b, *q_ur, *q_ut, *q_uz, *q_w;
+  T *q_da, *q_db;          // and the converged whole-step trial (NaN: none)
 };
+template <typename T>
+cudaError_t launch_push(const PushLaunchT<T> &L, cudaStream_t s);
 
 // launchers (return cudaError_t of the launch)
-cudaError_t launch_push_fp64(const PushLaunch &L, cudaStream_t s);
 cudaError_t launch_field_solve(const FieldOp &F, const double *er0, const double *ez0,
                                const double *h0, const double *ir, const double *iz, double v0,
                                double v1, double *er1, double *ez1, double *h1, const double *er_it,
@@ -201,28 +207,7 @@ cudaError_t launch_half_field_alpha(const Grid &g, const double *er0, const doub
                                     const double *er1, const double *ez1, double *erh,
                                     double *ezh, const AlphaOut &A, cudaStream_t s);
 
-struct PushLaunch32 {
-  Grid g;
-  double q, m, dt;
-  float cr, cz;          // dt/dr, dt/dz: velocity [m/s] -> cells per step
-  float icr, icz;        // dr/dt, dz/dt: cells per step -> velocity [m/s]
-  float wbt;             // qm*Bz*dt
-  long long n;
-  Parts32 p;
-  const float *ar, *az;  // normalised accelerations of this species
-  float qf;              // species charge [C] in FP32
-  double *ir, *iz;       // crossed charge [C] (FP64, atomics)
-  int write;
-  double *wall_z0, *wall_zl, *wall_r;
-  unsigned long long *counters;
-  double *ke_lost;
-  float inz;             // 1/nz
-  int *queue;            // scratch: indices of particles for the general path (capacity n)
-  int *qcount;           // scratch: queue length
-  int *q_cell;           // scratch: queued start state (cell, offsets, normalised v, weight)
-  float *q_a, *q_b, *q_ur, *q_ut, *q_uz, *q_w;
-};
-cudaError_t launch_push_fp32(const PushLaunch32 &L, cudaStream_t s);
+
 
 
 }  // namespace pic

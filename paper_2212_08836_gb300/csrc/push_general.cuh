@@ -26,7 +26,13 @@ template <>
 struct Num<float> {
   static constexpr float tol = 1e-6f;    // offsets [cells] and tau [steps]
   static constexpr float ulpf = 4.8e-7f;  // a few ulp, relative
+  // fast in-cell solve: estimated error below half an ulp of the displacement
+  static constexpr float fast_rel = 6e-8f, fast_abs = 1e-12f;
   __device__ static __forceinline__ float rcp(float x) { return __fdividef(1.f, x); }
+  // NaN test on the bits (independent of fast-math compilation)
+  __device__ static __forceinline__ bool nan_bits(float x) {
+    return (__float_as_uint(x) & 0x7fffffffu) > 0x7f800000u;
+  }
   // exact float -> double by exponent re-biasing in integer registers (no FP64
   // instruction; denormals are flushed in the FP32 unit anyway)
   __device__ static __forceinline__ double to_double(float f) {
@@ -43,7 +49,12 @@ template <>
 struct Num<double> {
   static constexpr double tol = 1e-13;
   static constexpr double ulpf = 1e-15;
+  static constexpr double fast_rel = 1e-16, fast_abs = 1e-20;
   __device__ static __forceinline__ double rcp(double x) { return 1.0 / x; }
+  __device__ static __forceinline__ bool nan_bits(double x) {
+    return ((unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull) >
+           0x7ff0000000000000ull;
+  }
   __device__ static __forceinline__ double to_double(double f) { return f; }
 };
 
@@ -246,10 +257,13 @@ struct GenArgs {
   double *ke_lost;
 };
 
-// one particle from its start state (offsets a, b; normalised velocities)
+// one particle from its start state (offsets a, b; normalised velocities);
+// (tr_da, tr_db): the converged interior solution of the whole step from a
+// start strictly inside the cell (NaN: none), which replaces the first
+// interior solve
 template <typename T>
 __device__ void push_general(const GenArgs<T> &L, long long p, int c0, T a, T b, T ur, T ut, T uz,
-                             const T w, Tally &Tl) {
+                             const T w, T tr_da, T tr_db, Tally &Tl) {
   const T zero = (T)0, one = (T)1, h = (T)0.5, two = (T)2;
   const int nr = L.nr, nz = L.nz, nz1 = nz + 1;
   const T wt = L.wt;
@@ -274,7 +288,10 @@ __device__ void push_general(const GenArgs<T> &L, long long p, int c0, T a, T b,
     s.ur = ur; s.ut = ut; s.uz = uz;
     s.P = s.rho * ut + h * wt * s.rho * s.rho;
     T da, db;
-    if (!interior_gen<T>(s, wt, tT, da, db, Tl.newton)) {
+    if (nsub == 1 && !Num<T>::nan_bits(tr_da)) {
+      da = tr_da;
+      db = tr_db;
+    } else if (!interior_gen<T>(s, wt, tT, da, db, Tl.newton)) {
       tT *= h;
       Tl.fb++;
       continue;
@@ -396,30 +413,28 @@ __device__ void push_general(const GenArgs<T> &L, long long p, int c0, T a, T b,
   }
 }
 
-__device__ __forceinline__ unsigned long long wsum_u64(unsigned long long v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
 // algorithmic operation counts of the general path: 75 per Newton iteration
 // (one residual/Jacobian evaluation and update), 93 per accepted sub-step
 constexpr unsigned kOpGenNewton = 75, kOpGenAccept = 93;
 
-// counters[0..4] += errors, absorbed, accepted sub-steps, fallbacks, operations
+// counters[0..4] += errors, absorbed, accepted sub-steps, fallbacks, operations;
+// per-thread counts are small, so the warp sums use the 32-bit redux unit
 __device__ __forceinline__ void flush_tally(unsigned long long *counters, const Tally &T, int lane,
                                             unsigned fast_newton, unsigned fast_acc,
                                             unsigned op_fast_newton, unsigned op_fast_acc) {
   if (!counters) return;
-  unsigned long long e0 = wsum_u64(T.err), e1 = wsum_u64(T.abs), e2 = wsum_u64(T.sub),
-                     e3 = wsum_u64(T.fb), e4 = wsum_u64(T.newton), e5 = wsum_u64(fast_newton),
-                     e6 = wsum_u64(fast_acc);
+  const unsigned full = 0xffffffffu;
+  unsigned e0 = __reduce_add_sync(full, T.err), e1 = __reduce_add_sync(full, T.abs),
+           e2 = __reduce_add_sync(full, T.sub), e3 = __reduce_add_sync(full, T.fb),
+           e4 = __reduce_add_sync(full, T.newton), e5 = __reduce_add_sync(full, fast_newton),
+           e6 = __reduce_add_sync(full, fast_acc);
   if (lane == 0) {
-    if (e0) atomicAdd(&counters[0], e0);
-    if (e1) atomicAdd(&counters[1], e1);
-    if (e2 + e6) atomicAdd(&counters[2], e2 + e6);
-    if (e3) atomicAdd(&counters[3], e3);
-    unsigned long long fl = kOpGenNewton * e4 + kOpGenAccept * e2 +
+    if (e0) atomicAdd(&counters[0], (unsigned long long)e0);
+    if (e1) atomicAdd(&counters[1], (unsigned long long)e1);
+    if (e2 + e6) atomicAdd(&counters[2], (unsigned long long)e2 + e6);
+    if (e3) atomicAdd(&counters[3], (unsigned long long)e3);
+    unsigned long long fl = (unsigned long long)kOpGenNewton * e4 +
+                            (unsigned long long)kOpGenAccept * e2 +
                             (unsigned long long)op_fast_newton * e5 +
                             (unsigned long long)op_fast_acc * e6;
     if (fl) atomicAdd(&counters[4], fl);

@@ -1,0 +1,345 @@
+// Mover + deposit kernels of rows a2, a3 and a6 (Sec. 2.1, Eqs. 3-4) for a
+// particle store of scalar type T (double: plain form, float: mixed form).
+//
+// Two phases, both in the normalised units of push_general.cuh:
+//   1. k_push_fast: particles that stay inside their cell over the whole step
+//      (the common case).  Without B_z the z-equation of the CN midpoint system
+//      is linear in the r-displacement, so the system reduces to one scalar
+//      equation g(d) = 0 for d = delta a, solved by Newton with an a-priori
+//      error estimate (one iteration is usually enough).  The home-cell
+//      deposits of a warp are summed with a transposed butterfly and added
+//      with one FP64 atomic per edge and run of lanes with the same cell.
+//      The kernel is persistent and prefetches the next particle's state while
+//      it works on the current one.
+//   2. k_push_general: the queued rest (crossings, particles on faces, near
+//      the axis, no convergence) through the general sub-step path, starting
+//      from the fast phase's converged whole-step trial where there is one.
+#pragma once
+
+#include "push_general.cuh"
+
+namespace pic {
+namespace {
+
+constexpr int kFastNewtonMax = 4;
+// algorithmic operations of the fast path: per Newton iteration, and per
+// accepted particle (set-up, deposit terms, velocity update)
+constexpr unsigned kOpFastNewton = 25, kOpFastAccept = 58;
+
+// ---------------------------------------------------------------------------
+// In-cell CN step without B_z.  With rho = ic + a, the unknowns (d, e) =
+// (delta a, delta b) over tau = 1 satisfy
+//   e = zb + gaz/4 * d,                  zb = uz + (az0 + gaz*a)/2
+//   g(d) = k1*d - K - C(d)/2 = 0,         k1 = 1 - gar*gaz/16,
+//   K = ur + (ar0 + gar*b)/2 + gar/4 * zb,
+//   C(d)/2 = ut^2 (2 rho + d) / (4 (rho + d)^2)
+// (C = ut_m^2 / rho_m with the CN-exact ut' = rho*ut/(rho + d)).  g' > 0 on
+// d > -rho, so the root is unique; Newton's error after a step s is about
+// |g''|/(2 g') s^2, with |g''| = ut^2 (4 rho + d) / (2 (rho + d)^4); the
+// iterate is accepted when twice that estimate is below half an ulp of d
+// (the CN velocity u' = 2d - u must not amplify an unconverged d).
+template <typename T>
+__device__ __forceinline__ bool fast_solve(T rho, T ut, T K, T k1, T &pd, unsigned &nit) {
+  const T zero = (T)0, q = (T)0.25, h = (T)0.5;
+  const T ut2 = ut * ut, r2 = rho + rho, r3 = r2 + rho, r4 = r2 + r2;
+  T d = K;
+#pragma unroll 1
+  for (int it = 0; it < kFastNewtonMax; ++it) {
+    T r1 = rho + d;
+    if (!(r1 > zero)) return false;
+    T x = Num<T>::rcp(r1);
+    T s2 = ut2 * x * x;
+    T g = k1 * d - K - q * s2 * (r2 + d);
+    T gp = k1 + q * s2 * (r3 + d) * x;
+    T ig = Num<T>::rcp(gp);
+    T st = -g * ig;
+    // twice the Newton error estimate of the updated iterate
+    T kap = h * s2 * x * x * (r4 + d) * ig;
+    d += st;
+    nit++;
+    if (kap * st * st <= fmax(Num<T>::fast_rel * fabs(d), Num<T>::fast_abs)) {
+      pd = d;
+      return isfinite(d);
+    }
+  }
+  return false;
+}
+
+// ---------------------------------------------------------------------------
+// Warp sums of the home-cell deposits.  v0, v1: charge through the r-faces
+// (i+1/2, j) and (i+1/2, j+1); v2, v3: through the z-faces (i, j+1/2) and
+// (i+1, j+1/2) of the lane's cell `key` (ascending over the lanes, -1: none).
+
+// lane l ends with the warp total of v[(l >> 3) & 3]
+template <typename T>
+__device__ __forceinline__ T bfly4(T v0, T v1, T v2, T v3, int lane) {
+  const unsigned full = 0xffffffffu;
+  const bool h16 = lane & 16, h8 = lane & 8;
+  T k0 = h16 ? v2 : v0, k1 = h16 ? v3 : v1;
+  T s0 = h16 ? v0 : v2, s1 = h16 ? v1 : v3;
+  k0 += __shfl_xor_sync(full, s0, 16);
+  k1 += __shfl_xor_sync(full, s1, 16);
+  T k = h8 ? k1 : k0, s = h8 ? k0 : k1;
+  k += __shfl_xor_sync(full, s, 8);
+  k += __shfl_xor_sync(full, k, 4);
+  k += __shfl_xor_sync(full, k, 2);
+  k += __shfl_xor_sync(full, k, 1);
+  return k;
+}
+
+// two runs (lanes below / from the second run's first lane): lane l ends with
+// the total of run (l >> 4) of v[(l >> 2) & 3]
+template <typename T>
+__device__ __forceinline__ T bfly8(T v0, T v1, T v2, T v3, bool second, int lane) {
+  const unsigned full = 0xffffffffu;
+  const T z = (T)0;
+  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+  const bool keep = h16 == second;
+  T k0 = keep ? v0 : z, k1 = keep ? v1 : z, k2 = keep ? v2 : z, k3 = keep ? v3 : z;
+  T s0 = keep ? z : v0, s1 = keep ? z : v1, s2 = keep ? z : v2, s3 = keep ? z : v3;
+  k0 += __shfl_xor_sync(full, s0, 16);
+  k1 += __shfl_xor_sync(full, s1, 16);
+  k2 += __shfl_xor_sync(full, s2, 16);
+  k3 += __shfl_xor_sync(full, s3, 16);
+  T m0 = h8 ? k2 : k0, m1 = h8 ? k3 : k1;
+  T t0 = h8 ? k0 : k2, t1 = h8 ? k1 : k3;
+  m0 += __shfl_xor_sync(full, t0, 8);
+  m1 += __shfl_xor_sync(full, t1, 8);
+  T k = h4 ? m1 : m0, s = h4 ? m0 : m1;
+  k += __shfl_xor_sync(full, s, 4);
+  k += __shfl_xor_sync(full, k, 2);
+  k += __shfl_xor_sync(full, k, 1);
+  return k;
+}
+
+__device__ __forceinline__ double *edge_ptr(int key, int j, int nz, double *ir, double *iz) {
+  int ic = key / nz, jc = key - ic * nz;
+  return j < 2 ? ir + ic * (nz + 1) + jc + j : iz + (ic + (j - 2)) * nz + jc;
+}
+
+template <typename T>
+__device__ __forceinline__ void warp_deposit(int key, T v0, T v1, T v2, T v3, int lane, int nz,
+                                             double *ir, double *iz) {
+  const unsigned full = 0xffffffffu;
+  int prev = __shfl_up_sync(full, key, 1);
+  unsigned heads = __ballot_sync(full, lane == 0 || prev != key);
+  int nrun = __popc(heads);
+  if (nrun == 1) {
+    T t = bfly4(v0, v1, v2, v3, lane);
+    if ((lane & 7) == 0 && key >= 0 && ir)
+      atomicAdd(edge_ptr(key, (lane >> 3) & 3, nz, ir, iz), Num<T>::to_double(t));
+  } else if (nrun == 2) {
+    int first2 = __ffs(heads & ~1u) - 1;
+    T t = bfly8(v0, v1, v2, v3, lane >= first2, lane);
+    int k = __shfl_sync(full, key, (lane & 16) ? 31 : 0);
+    if ((lane & 3) == 0 && k >= 0 && ir)
+      atomicAdd(edge_ptr(k, (lane >> 2) & 3, nz, ir, iz), Num<T>::to_double(t));
+  } else {
+    // segmented inclusive scan; the last lane of each run adds the run's totals
+    unsigned below = heads & ((2u << lane) - 1u);
+    int seg_start = 31 - __clz(below);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      T t0 = __shfl_up_sync(full, v0, o);
+      T t1 = __shfl_up_sync(full, v1, o);
+      T t2 = __shfl_up_sync(full, v2, o);
+      T t3 = __shfl_up_sync(full, v3, o);
+      if (lane - o >= seg_start) {
+        v0 += t0; v1 += t1; v2 += t2; v3 += t3;
+      }
+    }
+    int next = __shfl_down_sync(full, key, 1);
+    if ((lane == 31 || next != key) && key >= 0 && ir) {
+      atomicAdd(edge_ptr(key, 0, nz, ir, iz), Num<T>::to_double(v0));
+      atomicAdd(edge_ptr(key, 1, nz, ir, iz), Num<T>::to_double(v1));
+      atomicAdd(edge_ptr(key, 2, nz, ir, iz), Num<T>::to_double(v2));
+      atomicAdd(edge_ptr(key, 3, nz, ir, iz), Num<T>::to_double(v3));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <typename T>
+struct PState {
+  int c;
+  T a, b, vr, vt, vz, w;
+};
+
+template <typename T>
+__device__ __forceinline__ void load_state(const PartsT<T> &P, long long p, long long n,
+                                           PState<T> &s) {
+  if (p < n) {
+    s.c = P.cell[p];
+    s.a = P.a[p];
+    s.b = P.b[p];
+    s.vr = P.vr[p];
+    s.vt = P.vt[p];
+    s.vz = P.vz[p];
+    s.w = P.w[p];
+  } else {
+    s.c = -1;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_push_fast(PushLaunchT<T> L) {
+  const int lane = threadIdx.x & 31;
+  const int nz = L.g.nz, nz1 = nz + 1, ncell = L.g.nr * nz;
+  const T zero = (T)0, one = (T)1, h = (T)0.5, q = (T)0.25;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  unsigned n_newton = 0, n_acc = 0;
+  long long base = (long long)blockIdx.x * blockDim.x;
+  PState<T> cur;
+  load_state(L.p, base + threadIdx.x, L.n, cur);
+  for (; base < L.n; base += stride) {
+    const long long p = base + threadIdx.x;
+    PState<T> nxt;
+    load_state(L.p, p + stride, L.n, nxt);
+    const int c0 = cur.c;
+    const T a = cur.a, b = cur.b, w = cur.w;
+    T ur = zero, ut = zero, uz = zero;
+    T v0 = zero, v1 = zero, v2 = zero, v3 = zero;
+    bool queued = false, trial = false;
+    T d = zero, e = zero;
+    int key = -1;
+    if (c0 >= 0 && c0 < ncell) {
+      key = c0;
+      ur = cur.vr * L.cr;
+      ut = cur.vt * L.cr;
+      uz = cur.vz * L.cz;
+      // cell -> (ic, jc) without an integer division (c0 < 2^24 is exact in FP32)
+      int ic = __float2int_rz(__int2float_rn(c0) * L.inz);
+      int jc = c0 - ic * nz;
+      if (jc < 0) { ic -= 1; jc += nz; }
+      else if (jc >= nz) { ic += 1; jc -= nz; }
+      const T rho = (T)ic + a;
+      bool acc = false;
+      if (a > zero && a < one && b > zero && b < one && fabs(ut) < q * rho) {
+        const T ar0 = L.ar[ic * nz1 + jc];
+        const T gar = L.ar[ic * nz1 + jc + 1] - ar0;
+        const T az0 = L.az[ic * nz + jc];
+        const T gaz = L.az[(ic + 1) * nz + jc] - az0;
+        const T zb = uz + h * (az0 + gaz * a);
+        const T K = ur + h * (ar0 + gar * b) + q * gar * zb;
+        const T k1 = one - (T)0.0625 * gar * gaz;
+        if (k1 > h && fast_solve<T>(rho, ut, K, k1, d, n_newton)) {
+          trial = true;
+          e = zb + q * gaz * d;
+          const T a1 = a + d, b1 = b + e;
+          acc = a1 > zero && a1 < one && b1 > zero && b1 < one;
+          if (acc) {
+            n_acc++;
+            const T qw = L.qf * w;
+            const T fr = qw * d, fz = qw * e;
+            const T am = a + h * d, bm = b + h * e;
+            v0 = fr * (one - bm);
+            v1 = fr * bm;
+            v2 = fz * (one - am);
+            v3 = fz * am;
+            if (L.write) {
+              // CN velocity relations: the displacement is the mean of u and u'
+              L.p.a[p] = a1;
+              L.p.b[p] = b1;
+              L.p.vr[p] = (d + d - ur) * L.icr;
+              L.p.vz[p] = (e + e - uz) * L.icz;
+              L.p.vt[p] = rho * ut * Num<T>::rcp(rho + d) * L.icr;
+            }
+          }
+        }
+      }
+      queued = !acc;
+    }
+    warp_deposit<T>(key, v0, v1, v2, v3, lane, nz, L.ir, L.iz);
+    // queue the rest for the general path (warp-aggregated append)
+    const unsigned full = 0xffffffffu;
+    unsigned qm = __ballot_sync(full, queued);
+    if (qm) {
+      int leader = __ffs(qm) - 1;
+      int qb = 0;
+      if (lane == leader) qb = atomicAdd(L.qcount, __popc(qm));
+      qb = __shfl_sync(full, qb, leader);
+      if (queued) {
+        int k = qb + __popc(qm & ((1u << lane) - 1u));
+        L.queue[k] = (int)p;
+        L.q_cell[k] = c0;
+        L.q_a[k] = a;
+        L.q_b[k] = b;
+        L.q_ur[k] = ur;
+        L.q_ut[k] = ut;
+        L.q_uz[k] = uz;
+        L.q_w[k] = w;
+        L.q_da[k] = trial ? d : (T)NAN;
+        L.q_db[k] = e;
+      }
+    }
+    cur = nxt;
+  }
+  Tally T0 = {0, 0, 0, 0, 0};
+  flush_tally(L.counters, T0, lane, n_newton, n_acc, kOpFastNewton, kOpFastAccept);
+}
+
+// queued particles (or all of them when queue == nullptr)
+template <typename T>
+__global__ void __launch_bounds__(256) k_push_general(PushLaunchT<T> L) {
+  const int lane = threadIdx.x & 31;
+  GenArgs<T> G;
+  G.nr = L.g.nr; G.nz = L.g.nz; G.ar = L.ar; G.az = L.az;
+  G.wt = L.wbt; G.icr = L.icr; G.icz = L.icz;
+  G.q = L.q; G.m = L.m; G.qf = L.qf; G.ir = L.ir; G.iz = L.iz; G.write = L.write; G.p = L.p;
+  G.wall_z0 = L.wall_z0; G.wall_zl = L.wall_zl; G.wall_r = L.wall_r; G.ke_lost = L.ke_lost;
+  long long count = L.queue ? (long long)*L.qcount : L.n;
+  Tally tl = {0, 0, 0, 0, 0};
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < count;
+       k += (long long)gridDim.x * blockDim.x) {
+    if (L.queue) {
+      push_general<T>(G, L.queue[k], L.q_cell[k], L.q_a[k], L.q_b[k], L.q_ur[k], L.q_ut[k],
+                      L.q_uz[k], L.q_w[k], L.q_da[k], L.q_db[k], tl);
+    } else {
+      push_general<T>(G, k, L.p.cell[k], L.p.a[k], L.p.b[k], L.p.vr[k] * L.cr,
+                      L.p.vt[k] * L.cr, L.p.vz[k] * L.cz, L.p.w[k], (T)NAN, (T)NAN, tl);
+    }
+  }
+  flush_tally(L.counters, tl, lane, 0, 0, 0, 0);
+}
+
+// grid of the persistent fast kernel: resident blocks of 256 threads per SM x SMs
+template <typename T>
+long long fast_grid() {
+  static long long nb = 0;
+  if (nb == 0) {
+    int v = 0, dev = 0, nsm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_push_fast<T>, 256, 0) != cudaSuccess ||
+        v < 1)
+      v = 1;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+      nsm = 152;
+    nb = (long long)v * nsm;
+  }
+  return nb;
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_push(const PushLaunchT<T> &L, cudaStream_t s) {
+  if (L.n <= 0) return cudaSuccess;
+  const int bs = 256;
+  long long nb = (L.n + bs - 1) / bs;
+  if (L.wbt == (T)0 && L.queue) {
+    cudaError_t e = cudaMemsetAsync(L.qcount, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    long long nf = fast_grid<T>();
+    k_push_fast<T><<<(unsigned)(nb < nf ? nb : nf), bs, 0, s>>>(L);
+    // the queue holds the crossing / near-axis particles (a fraction of n)
+    long long ng = nb < 152 * 16 ? nb : 152 * 16;
+    k_push_general<T><<<(unsigned)ng, bs, 0, s>>>(L);
+  } else {
+    PushLaunchT<T> A = L;
+    A.queue = nullptr;
+    k_push_general<T><<<(unsigned)nb, bs, 0, s>>>(A);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace pic
