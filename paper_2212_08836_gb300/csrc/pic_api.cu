@@ -26,7 +26,7 @@ struct pic_ctx {
   int cur[2];
   int mixed;                 // 1: FP32 particle store and push (PIC_MIXED)
   AlphaOut alpha;            // mixed form: normalised accelerations per species
-  int *queue, *qcount;       // work queue of the general push path (both forms)
+  int *queue, *qblock;       // work queue of the general push path (both forms)
   int *q_cell;
   float *q_real[8];          // mixed form queue records
   double *q_real64[8];       // FP64 form queue records
@@ -122,21 +122,22 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
       P.w = (double *)K.take(pc * rs);
       P.id = (uint32_t *)K.take(pc * 4);
     }
-  x->queue = (int *)K.take(pc * 4);
-  x->qcount = (int *)K.take(256);
-  x->q_cell = (int *)K.take(pc * 4);
+  const size_t qc = pc + (size_t)kMaxFastBlocks * 256;  // queue entries
+  x->queue = (int *)K.take(qc * 4);
+  x->qblock = (int *)K.take((size_t)kMaxFastBlocks * 4);
+  x->q_cell = (int *)K.take(qc * 4);
   if (c->precision == PIC_MIXED) {
     for (int s = 0; s < 2; ++s) {
       x->alpha.ar[s] = (float *)K.take(ner * 4);
       x->alpha.az[s] = (float *)K.take(nez * 4);
     }
-    for (int k = 0; k < 8; ++k) x->q_real[k] = (float *)K.take(pc * 4);
+    for (int k = 0; k < 8; ++k) x->q_real[k] = (float *)K.take(qc * 4);
   } else {
     for (int s = 0; s < 2; ++s) {
       x->alpha64.ar[s] = (double *)K.take(ner * 8);
       x->alpha64.az[s] = (double *)K.take(nez * 8);
     }
-    for (int k = 0; k < 8; ++k) x->q_real64[k] = (double *)K.take(pc * 8);
+    for (int k = 0; k < 8; ++k) x->q_real64[k] = (double *)K.take(qc * 8);
   }
   x->er = (double *)K.take(ner * 8);
   x->ez = (double *)K.take(nez * 8);
@@ -239,7 +240,7 @@ void fill_push(pic_ctx *x, int s, double q, double m, const double *erh, const d
 template <typename T>
 void set_queue(pic_ctx *x, T *const rec[8], PushLaunchT<T> &L) {
   L.queue = x->queue;
-  L.qcount = x->qcount;
+  L.qblock = x->qblock;
   L.q_cell = x->q_cell;
   L.q_a = rec[0];
   L.q_b = rec[1];

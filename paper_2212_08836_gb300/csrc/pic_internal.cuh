@@ -121,11 +121,18 @@ struct PushLaunchT {
   double *wall_z0, *wall_zl, *wall_r;
   unsigned long long *counters;
   double *ke_lost;
-  int *queue, *qcount;     // scratch work queue for the general path (nullptr: all)
+  // work queue of the general path (queue == nullptr: all particles).  Block b
+  // of the fast kernel appends to entries [b*qseg, b*qseg + qblock[b]).
+  int *queue, *qblock;
+  long long qseg;
+  int qgrid;               // blocks of the fast kernel
   int *q_cell;             // queued start state: cell, offsets, normalised v, weight,
   T *q_a, *q_b, *q_ur, *q_ut, *q_uz, *q_w;
   T *q_da, *q_db;          // and the converged whole-step trial (NaN: none)
 };
+// most blocks of 256 threads resident on a GB300 (152 SMs x 8); the queue
+// holds up to capacity + kMaxFastBlocks*256 entries
+constexpr int kMaxFastBlocks = 152 * 8;
 template <typename T>
 cudaError_t launch_push(const PushLaunchT<T> &L, cudaStream_t s);
 

@@ -50,7 +50,17 @@ struct Num<double> {
   static constexpr double tol = 1e-13;
   static constexpr double ulpf = 1e-15;
   static constexpr double fast_rel = 1e-16, fast_abs = 1e-20;
-  __device__ static __forceinline__ double rcp(double x) { return 1.0 / x; }
+  // reciprocal: the hardware approximation (about 20 correct bits) refined by
+  // two Newton-Raphson steps y <- y + y (1 - x y) (Markstein, IBM J. Res.
+  // Dev. 34, 1990), each doubling the correct bits; for x > 0 and finite
+  __device__ static __forceinline__ double rcp(double x) {
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    double e = fma(-x, y, 1.0);
+    y = fma(y, e, y);
+    e = fma(-x, y, 1.0);
+    return fma(y, e, y);
+  }
   __device__ static __forceinline__ bool nan_bits(double x) {
     return ((unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull) >
            0x7ff0000000000000ull;
@@ -83,30 +93,42 @@ struct ResT {
   T f1, f2, f1a, f1t, f2a, f2b, f2t, A, az, ut1;
 };
 
-template <typename T>
+// kB = false: no external B_z (wt = 0, P = rho*ut).  Then, for rho' > 0,
+// C = ut_m^2/rho_m = ut^2 (2 rho + da) / (2 rho'^2), which needs one
+// reciprocal instead of two.
+template <typename T, bool kB>
 __device__ __forceinline__ void eval_gen(const SubT<T> &s, T wt, T da, T db, T tau, ResT<T> &o) {
   const T h = (T)0.5, q = (T)0.25, zero = (T)0, one = (T)1, two = (T)2;
   T rho1 = s.rho + da;
   T rhom = s.rho + h * da;
   T ut1, dut1;
-  if (rho1 > zero) {
-    T inv1 = Num<T>::rcp(rho1);
-    ut1 = (s.P - h * wt * rho1 * rho1) * inv1;
-    dut1 = -s.P * inv1 * inv1 - h * wt;
-  } else {
-    ut1 = s.ut;
-    dut1 = zero;
-  }
-  T utm = h * (s.ut + ut1);
-  T dutm = h * dut1;
   T C, dC;
-  if (rhom > zero) {
-    T invm = Num<T>::rcp(rhom);
-    C = utm * utm * invm + wt * utm;
-    dC = two * utm * dutm * invm - h * utm * utm * invm * invm + wt * dutm;
+  if (!kB && rho1 > zero) {
+    T inv1 = Num<T>::rcp(rho1);
+    T i2 = inv1 * inv1;
+    T ut2h = h * s.ut * s.ut * i2;
+    ut1 = s.P * inv1;
+    C = ut2h * (s.rho + s.rho + da);
+    dC = -ut2h * (s.rho + s.rho + s.rho + da) * inv1;
   } else {
-    C = wt * utm;
-    dC = wt * dutm;
+    if (rho1 > zero) {
+      T inv1 = Num<T>::rcp(rho1);
+      ut1 = (s.P - h * wt * rho1 * rho1) * inv1;
+      dut1 = -s.P * inv1 * inv1 - h * wt;
+    } else {
+      ut1 = s.ut;
+      dut1 = zero;
+    }
+    T utm = h * (s.ut + ut1);
+    T dutm = h * dut1;
+    if (rhom > zero) {
+      T invm = Num<T>::rcp(rhom);
+      C = utm * utm * invm + wt * utm;
+      dC = two * utm * dutm * invm - h * utm * utm * invm * invm + wt * dutm;
+    } else {
+      C = wt * utm;
+      dC = wt * dutm;
+    }
   }
   T am = s.a + h * da;
   T bm = s.b + h * db;
@@ -125,7 +147,7 @@ __device__ __forceinline__ void eval_gen(const SubT<T> &s, T wt, T da, T db, T t
   o.ut1 = ut1;
 }
 
-template <typename T>
+template <typename T, bool kB>
 __device__ __forceinline__ bool interior_gen(const SubT<T> &s, T wt, T tau, T &pda, T &pdb,
                                              unsigned &it_count) {
   const T h = (T)0.5, zero = (T)0;
@@ -138,7 +160,7 @@ __device__ __forceinline__ bool interior_gen(const SubT<T> &s, T wt, T tau, T &p
   if (s.P != zero && s.rho + da <= zero) da = -h * s.rho;
   for (int it = 0; it < kNewtonMaxGen; ++it) {
     ResT<T> o;
-    eval_gen(s, wt, da, db, tau, o);
+    eval_gen<T, kB>(s, wt, da, db, tau, o);
     it_count++;
     // [f1a 1; f2a f2b] [xa; xb] = -[f1; f2]
     T det = o.f1a * o.f2b - o.f2a;
@@ -161,7 +183,7 @@ __device__ __forceinline__ bool interior_gen(const SubT<T> &s, T wt, T tau, T &p
   return false;
 }
 
-template <typename T>
+template <typename T, bool kB>
 __device__ __forceinline__ bool landing_gen(const SubT<T> &s, T wt, int dir, T X, T t0, T oth0,
                                             T &ptau, T &poth, unsigned &it_count) {
   const T h = (T)0.5, q = (T)0.25, zero = (T)0, one = (T)1;
@@ -170,7 +192,7 @@ __device__ __forceinline__ bool landing_gen(const SubT<T> &s, T wt, int dir, T X
     T da = dir == 0 ? X : oth;
     T db = dir == 0 ? oth : X;
     ResT<T> o;
-    eval_gen(s, wt, da, db, tau, o);
+    eval_gen<T, kB>(s, wt, da, db, tau, o);
     it_count++;
     T gF, gFo, gFt, gO, gOo, gOt;
     if (dir == 0) {
@@ -261,7 +283,7 @@ struct GenArgs {
 // (tr_da, tr_db): the converged interior solution of the whole step from a
 // start strictly inside the cell (NaN: none), which replaces the first
 // interior solve
-template <typename T>
+template <typename T, bool kB>
 __device__ void push_general(const GenArgs<T> &L, long long p, int c0, T a, T b, T ur, T ut, T uz,
                              const T w, T tr_da, T tr_db, Tally &Tl) {
   const T zero = (T)0, one = (T)1, h = (T)0.5, two = (T)2;
@@ -291,7 +313,7 @@ __device__ void push_general(const GenArgs<T> &L, long long p, int c0, T a, T b,
     if (nsub == 1 && !Num<T>::nan_bits(tr_da)) {
       da = tr_da;
       db = tr_db;
-    } else if (!interior_gen<T>(s, wt, tT, da, db, Tl.newton)) {
+    } else if (!interior_gen<T, kB>(s, wt, tT, da, db, Tl.newton)) {
       tT *= h;
       Tl.fb++;
       continue;
@@ -326,7 +348,7 @@ __device__ void push_general(const GenArgs<T> &L, long long p, int c0, T a, T b,
         }
         T oth0 = doth * (g0 / tT);
         T tt = zero, toth = zero;
-        if (!(g0 > zero) || !landing_gen<T>(s, wt, dir, X, g0, oth0, tt, toth, Tl.newton)) continue;
+        if (!(g0 > zero) || !landing_gen<T, kB>(s, wt, dir, X, g0, oth0, tt, toth, Tl.newton)) continue;
         if (!(tt > zero) || tt > tT) continue;
         T xo = (dir == 0 ? b : a) + toth;
         if (xo < zero || xo > one) continue;
@@ -354,7 +376,7 @@ __device__ void push_general(const GenArgs<T> &L, long long p, int c0, T a, T b,
       }
     }
     ResT<T> o;
-    eval_gen<T>(s, wt, da, db, step_t, o);
+    eval_gen<T, kB>(s, wt, da, db, step_t, o);
     T am = a + h * da, bm = b + h * db;
     T nur = ur + step_t * o.A;
     T nuz = uz + step_t * o.az;
