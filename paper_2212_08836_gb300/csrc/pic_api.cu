@@ -27,9 +27,8 @@ struct pic_ctx {
   int mixed;                 // 1: FP32 particle store and push (PIC_MIXED)
   AlphaOut alpha;            // mixed form: normalised accelerations per species
   int *queue, *qblock;       // work queue of the general push path (both forms)
-  int *q_cell;
-  float *q_real[8];          // mixed form queue records
-  double *q_real64[8];       // FP64 form queue records
+  float *q_real[2];          // mixed form queue records (trial displacements)
+  double *q_real64[2];       // FP64 form queue records
   AlphaOut64 alpha64;        // FP64 form: normalised accelerations per species
   double *er, *ez, *h;      // E^n, H^n
   double *er1, *ez1;        // Picard iterate E^{n+1,k}
@@ -39,7 +38,9 @@ struct pic_ctx {
   double *wall;             // 2 species x (2(nr+1) + nz+1)
   FieldOp F;
   DevCounters *cnt;
-  int32_t *flag, *offs, *counts, *coffs, *cursor;
+  uint32_t *cand;           // MCC: null-collision candidates (per-block segments)
+  int *cblock;
+  int32_t *counts, *coffs, *cursor;
   uint64_t *keys, *keys2;   // MCC: ionizing parents ordered by id
   long long *total;
   void *scan_scratch;
@@ -125,19 +126,18 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
   const size_t qc = pc + (size_t)kMaxFastBlocks * 256;  // queue entries
   x->queue = (int *)K.take(qc * 4);
   x->qblock = (int *)K.take((size_t)kMaxFastBlocks * 4);
-  x->q_cell = (int *)K.take(qc * 4);
   if (c->precision == PIC_MIXED) {
     for (int s = 0; s < 2; ++s) {
       x->alpha.ar[s] = (float *)K.take(ner * 4);
       x->alpha.az[s] = (float *)K.take(nez * 4);
     }
-    for (int k = 0; k < 8; ++k) x->q_real[k] = (float *)K.take(qc * 4);
+    for (int k = 0; k < 2; ++k) x->q_real[k] = (float *)K.take(qc * 4);
   } else {
     for (int s = 0; s < 2; ++s) {
       x->alpha64.ar[s] = (double *)K.take(ner * 8);
       x->alpha64.az[s] = (double *)K.take(nez * 8);
     }
-    for (int k = 0; k < 8; ++k) x->q_real64[k] = (double *)K.take(qc * 8);
+    for (int k = 0; k < 2; ++k) x->q_real64[k] = (double *)K.take(qc * 8);
   }
   x->er = (double *)K.take(ner * 8);
   x->ez = (double *)K.take(nez * 8);
@@ -161,8 +161,8 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
   x->F.hat = (double *)K.take(nh * 8);
   x->F.hhalf = (double *)K.take(nh * 8);
   x->cnt = (DevCounters *)K.take(sizeof(DevCounters));
-  x->flag = (int32_t *)K.take(pc * 4);
-  x->offs = (int32_t *)K.take(pc * 4);
+  x->cand = (uint32_t *)K.take((2 * (size_t)pc + 2 * (size_t)kMaxFastBlocks * 256) * 4);
+  x->cblock = (int *)K.take((size_t)kMaxFastBlocks * 4);
   x->keys = (uint64_t *)K.take(pc * 8);
   x->keys2 = (uint64_t *)K.take(pc * 8);
   int ncell = nr * nz;
@@ -238,18 +238,11 @@ void fill_push(pic_ctx *x, int s, double q, double m, const double *erh, const d
 }
 
 template <typename T>
-void set_queue(pic_ctx *x, T *const rec[8], PushLaunchT<T> &L) {
+void set_queue(pic_ctx *x, T *const rec[2], PushLaunchT<T> &L) {
   L.queue = x->queue;
   L.qblock = x->qblock;
-  L.q_cell = x->q_cell;
-  L.q_a = rec[0];
-  L.q_b = rec[1];
-  L.q_ur = rec[2];
-  L.q_ut = rec[3];
-  L.q_uz = rec[4];
-  L.q_w = rec[5];
-  L.q_da = rec[6];
-  L.q_db = rec[7];
+  L.q_da = rec[0];
+  L.q_db = rec[1];
 }
 
 int push_all(pic_ctx *x, const double *erh, const double *ezh, double *ir, double *iz, int write,
@@ -592,6 +585,7 @@ int pic_mcc(pic_ctx *x, unsigned long long step, long long *counts, double *de_c
   if (!x) return PIC_E_CONFIG;
   cudaError_t e = cudaMemsetAsync(x->cnt->mcc, 0, sizeof(x->cnt->mcc), x->s);
   if (e == cudaSuccess) e = cudaMemsetAsync(&x->cnt->de_coll, 0, 8, x->s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(&x->cnt->iz_slots, 0, 8, x->s);
   MccLaunch M;
   M.seed = x->cfg.seed;
   M.step = step;
@@ -607,19 +601,20 @@ int pic_mcc(pic_ctx *x, unsigned long long step, long long *counts, double *de_c
   M.ni = x->n[1];
   M.e = cur(x, 0);
   M.i = cur(x, 1);
-  M.flag = x->flag;
-  M.offs = x->offs;
+  M.cand = x->cand;
+  M.cblock = x->cblock;
+  M.cseg = 0;
+  M.cgrid = 0;
   M.cnt = x->cnt;
   M.keys = x->keys;
   M.keys2 = x->keys2;
   MccLaunchT<float> M32{M.seed, M.step, M.ng, M.tg, M.numax_e, M.pnull_e, M.pnull_i, M.gmax,
-                        M.thr_e, M.thr_i, M.ne, M.ni, as32(M.e), as32(M.i), M.flag, M.offs,
-                        M.cnt, M.keys, M.keys2};
+                        M.thr_e, M.thr_i, M.ne, M.ni, as32(M.e), as32(M.i), M.cand, M.cblock,
+                        M.cseg, M.cgrid, M.cnt, M.keys, M.keys2};
   if (e == cudaSuccess) e = x->mixed ? launch_mcc_collide(M32, x->s) : launch_mcc_collide(M, x->s);
-  if (e == cudaSuccess) e = scan_exclusive(x->flag, x->offs, M.ne, x->total, x->scan_scratch, x->s);
-  x->launches += (M.ne > 0 || M.ni > 0 ? 1 : 0) + (M.ne > 0 ? 3 : 0);
+  x->launches += (M.ne > 0 || M.ni > 0 ? 2 : 0);
   long long tot = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&tot, x->total, 8, cudaMemcpyDeviceToHost, x->s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&tot, &x->cnt->iz_slots, 8, cudaMemcpyDeviceToHost, x->s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(x->s);
   if (e != cudaSuccess) return PIC_E_CUDA;
   int rc = PIC_OK;
@@ -633,7 +628,7 @@ int pic_mcc(pic_ctx *x, unsigned long long step, long long *counts, double *de_c
       e = x->mixed ? launch_mcc_append(M32, tot, x->n[0], x->n[1], x->next_id[0], x->next_id[1], x->s)
                    : launch_mcc_append(M, tot, x->n[0], x->n[1], x->next_id[0], x->next_id[1], x->s);
       if (e != cudaSuccess) return PIC_E_CUDA;
-      x->launches += 3;
+      x->launches += 2;
       x->n[0] += tot;
       x->n[1] += tot;
       x->next_id[0] += (uint32_t)tot;

@@ -84,7 +84,8 @@ struct DevCounters {
   double de_coll;
   double norm[2];              // Picard: sum (E_new - E_it)^2, sum E_new^2
   double src;                  // drive-gap energy of the last solve
-  double pad[2];
+  unsigned long long iz_slots; // MCC: ionization keys written
+  double pad[1];
 };
 
 // Field operator (separable direct solve of the H_theta system)
@@ -126,9 +127,9 @@ struct PushLaunchT {
   int *queue, *qblock;
   long long qseg;
   int qgrid;               // blocks of the fast kernel
-  int *q_cell;             // queued start state: cell, offsets, normalised v, weight,
-  T *q_a, *q_b, *q_ur, *q_ut, *q_uz, *q_w;
-  T *q_da, *q_db;          // and the converged whole-step trial (NaN: none)
+  T *q_da, *q_db;          // queued particle's converged whole-step trial (NaN: none);
+                           // its start state is re-read from the store, which the
+                           // fast kernel leaves untouched for queued particles
 };
 // most blocks of 256 threads resident on a GB300 (152 SMs x 8); the queue
 // holds up to capacity + kMaxFastBlocks*256 entries
@@ -155,11 +156,18 @@ struct MccLaunchT {
   uint64_t thr_e, thr_i;  // null-collision thresholds on the 53-bit integer draw
   long long ne, ni;
   PartsT<T> e, i;
-  int32_t *flag, *offs;   // per-electron ionization flags / exclusive scan
+  // null-collision candidates (slot, top bit set for ions) in per-block
+  // segments [b*cseg, b*cseg + cblock[b]) of the select kernel's cgrid blocks
+  uint32_t *cand;
+  int *cblock;
+  long long cseg;
+  int cgrid;
   DevCounters *cnt;
   uint64_t *keys, *keys2; // scratch: (parent id << 32 | slot) of ionizing electrons
 };
 using MccLaunch = MccLaunchT<double>;
+// selects the candidates, then collides them; the ionizing parents' keys go to
+// keys[0 .. cnt->iz_slots)
 template <typename T>
 cudaError_t launch_mcc_collide(const MccLaunchT<T> &M, cudaStream_t s);
 // orders the tot ionizing parents by id (keys), then appends the pairs in that order

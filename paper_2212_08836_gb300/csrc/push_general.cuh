@@ -261,8 +261,71 @@ __device__ __forceinline__ int transition_gen(int nr, int nz, int &ic, int &jc, 
   return 0;
 }
 
+constexpr int kFastNewtonMax = 4;
+// algorithmic operations of the fast path: per Newton iteration, and per
+// accepted particle (set-up, deposit terms, velocity update)
+constexpr unsigned kOpFastNewton = 25, kOpFastAccept = 58;
+
+// ---------------------------------------------------------------------------
+// In-cell CN step without B_z.  With rho = ic + a, the unknowns (d, e) =
+// (delta a, delta b) over tau = 1 satisfy
+//   e = zb + gaz/4 * d,                  zb = uz + (az0 + gaz*a)/2
+//   g(d) = k1*d - K - C(d)/2 = 0,         k1 = 1 - gar*gaz/16,
+//   K = ur + (ar0 + gar*b)/2 + gar/4 * zb,
+//   C(d)/2 = ut^2 (2 rho + d) / (4 (rho + d)^2)
+// (C = ut_m^2 / rho_m with the CN-exact ut' = rho*ut/(rho + d)).  g' > 0 on
+// d > -rho, so the root is unique; Newton's error after a step s is about
+// |g''|/(2 g') s^2, with |g''| = ut^2 (4 rho + d) / (2 (rho + d)^4); the
+// iterate is accepted when twice that estimate is below half an ulp of d
+// (the CN velocity u' = 2d - u must not amplify an unconverged d).
+template <typename T>
+__device__ __forceinline__ bool fast_solve(T rho, T ut, T K, T k1, T &pd, unsigned &nit) {
+  const T zero = (T)0, q = (T)0.25, h = (T)0.5;
+  const T ut2 = ut * ut, r2 = rho + rho, r3 = r2 + rho, r4 = r2 + r2;
+  T d = K;
+#pragma unroll 1
+  for (int it = 0; it < kFastNewtonMax; ++it) {
+    T r1 = rho + d;
+    if (!(r1 > zero)) return false;
+    T x = Num<T>::rcp(r1);
+    T s2 = ut2 * x * x;
+    T g = k1 * d - K - q * s2 * (r2 + d);
+    T gp = k1 + q * s2 * (r3 + d) * x;
+    T ig = Num<T>::rcp(gp);
+    T st = -g * ig;
+    // twice the Newton error estimate of the updated iterate
+    T kap = h * s2 * x * x * (r4 + d) * ig;
+    d += st;
+    nit++;
+    if (kap * st * st <= fmax(Num<T>::fast_rel * fabs(d), Num<T>::fast_abs)) {
+      pd = d;
+      return isfinite(d);
+    }
+  }
+  return false;
+}
+
+// Interior sub-step of length tau without B_z through the same scalar
+// reduction (tau-scaled coefficients; ut enters as tau*ut); false when the
+// reduction does not apply (close to the axis) or does not converge
+template <typename T>
+__device__ __forceinline__ bool scalar_interior(const SubT<T> &s, T tau, T &pda, T &pdb,
+                                                unsigned &nit) {
+  const T h = (T)0.5, q = (T)0.25, one = (T)1, zero = (T)0;
+  const T t2 = tau * tau, tut = tau * s.ut;
+  if (!(s.rho > zero) || !(fabs(tut) < q * s.rho)) return false;
+  const T zb = tau * s.uz + h * t2 * (s.az0 + s.gaz * s.a);
+  const T K = tau * s.ur + h * t2 * (s.ar0 + s.gar * s.b) + q * t2 * s.gar * zb;
+  const T k1 = one - (T)0.0625 * t2 * t2 * s.gar * s.gaz;
+  T d;
+  if (!(k1 > h) || !fast_solve<T>(s.rho, tut, K, k1, d, nit)) return false;
+  pda = d;
+  pdb = zb + q * t2 * s.gaz * d;
+  return true;
+}
+
 struct Tally {
-  unsigned err, abs, sub, fb, newton;
+  unsigned err, abs, sub, fb, newton, snewton;  // snewton: scalar Newton iterations
 };
 
 template <typename T>
@@ -313,7 +376,8 @@ __device__ void push_general(const GenArgs<T> &L, long long p, int c0, T a, T b,
     if (nsub == 1 && !Num<T>::nan_bits(tr_da)) {
       da = tr_da;
       db = tr_db;
-    } else if (!interior_gen<T, kB>(s, wt, tT, da, db, Tl.newton)) {
+    } else if (!(!kB && scalar_interior<T>(s, tT, da, db, Tl.snewton)) &&
+               !interior_gen<T, kB>(s, wt, tT, da, db, Tl.newton)) {
       tT *= h;
       Tl.fb++;
       continue;
@@ -442,13 +506,13 @@ constexpr unsigned kOpGenNewton = 75, kOpGenAccept = 93;
 // counters[0..4] += errors, absorbed, accepted sub-steps, fallbacks, operations;
 // per-thread counts are small, so the warp sums use the 32-bit redux unit
 __device__ __forceinline__ void flush_tally(unsigned long long *counters, const Tally &T, int lane,
-                                            unsigned fast_newton, unsigned fast_acc,
-                                            unsigned op_fast_newton, unsigned op_fast_acc) {
+                                            unsigned fast_newton, unsigned fast_acc) {
   if (!counters) return;
   const unsigned full = 0xffffffffu;
   unsigned e0 = __reduce_add_sync(full, T.err), e1 = __reduce_add_sync(full, T.abs),
            e2 = __reduce_add_sync(full, T.sub), e3 = __reduce_add_sync(full, T.fb),
-           e4 = __reduce_add_sync(full, T.newton), e5 = __reduce_add_sync(full, fast_newton),
+           e4 = __reduce_add_sync(full, T.newton),
+           e5 = __reduce_add_sync(full, fast_newton + T.snewton),
            e6 = __reduce_add_sync(full, fast_acc);
   if (lane == 0) {
     if (e0) atomicAdd(&counters[0], (unsigned long long)e0);
@@ -457,8 +521,8 @@ __device__ __forceinline__ void flush_tally(unsigned long long *counters, const 
     if (e3) atomicAdd(&counters[3], (unsigned long long)e3);
     unsigned long long fl = (unsigned long long)kOpGenNewton * e4 +
                             (unsigned long long)kOpGenAccept * e2 +
-                            (unsigned long long)op_fast_newton * e5 +
-                            (unsigned long long)op_fast_acc * e6;
+                            (unsigned long long)kOpFastNewton * e5 +
+                            (unsigned long long)kOpFastAccept * e6;
     if (fl) atomicAdd(&counters[4], fl);
   }
 }

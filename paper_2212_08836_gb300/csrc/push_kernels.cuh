@@ -17,53 +17,10 @@
 #pragma once
 
 #include "push_general.cuh"
+#include "seg_queue.cuh"
 
 namespace pic {
 namespace {
-
-constexpr int kFastNewtonMax = 4;
-// algorithmic operations of the fast path: per Newton iteration, and per
-// accepted particle (set-up, deposit terms, velocity update)
-constexpr unsigned kOpFastNewton = 25, kOpFastAccept = 58;
-
-// ---------------------------------------------------------------------------
-// In-cell CN step without B_z.  With rho = ic + a, the unknowns (d, e) =
-// (delta a, delta b) over tau = 1 satisfy
-//   e = zb + gaz/4 * d,                  zb = uz + (az0 + gaz*a)/2
-//   g(d) = k1*d - K - C(d)/2 = 0,         k1 = 1 - gar*gaz/16,
-//   K = ur + (ar0 + gar*b)/2 + gar/4 * zb,
-//   C(d)/2 = ut^2 (2 rho + d) / (4 (rho + d)^2)
-// (C = ut_m^2 / rho_m with the CN-exact ut' = rho*ut/(rho + d)).  g' > 0 on
-// d > -rho, so the root is unique; Newton's error after a step s is about
-// |g''|/(2 g') s^2, with |g''| = ut^2 (4 rho + d) / (2 (rho + d)^4); the
-// iterate is accepted when twice that estimate is below half an ulp of d
-// (the CN velocity u' = 2d - u must not amplify an unconverged d).
-template <typename T>
-__device__ __forceinline__ bool fast_solve(T rho, T ut, T K, T k1, T &pd, unsigned &nit) {
-  const T zero = (T)0, q = (T)0.25, h = (T)0.5;
-  const T ut2 = ut * ut, r2 = rho + rho, r3 = r2 + rho, r4 = r2 + r2;
-  T d = K;
-#pragma unroll 1
-  for (int it = 0; it < kFastNewtonMax; ++it) {
-    T r1 = rho + d;
-    if (!(r1 > zero)) return false;
-    T x = Num<T>::rcp(r1);
-    T s2 = ut2 * x * x;
-    T g = k1 * d - K - q * s2 * (r2 + d);
-    T gp = k1 + q * s2 * (r3 + d) * x;
-    T ig = Num<T>::rcp(gp);
-    T st = -g * ig;
-    // twice the Newton error estimate of the updated iterate
-    T kap = h * s2 * x * x * (r4 + d) * ig;
-    d += st;
-    nit++;
-    if (kap * st * st <= fmax(Num<T>::fast_rel * fabs(d), Num<T>::fast_abs)) {
-      pd = d;
-      return isfinite(d);
-    }
-  }
-  return false;
-}
 
 // ---------------------------------------------------------------------------
 // Warp sums of the home-cell deposits.  v0, v1: charge through the r-faces
@@ -187,7 +144,7 @@ __device__ __forceinline__ void load_state(const PartsT<T> &P, long long p, long
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_push_fast(PushLaunchT<T> L) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_push_fast(PushLaunchT<T> L) {
   const int lane = threadIdx.x & 31;
   const int nz = L.g.nz, nz1 = nz + 1, ncell = L.g.nr * nz;
   const T zero = (T)0, one = (T)1, h = (T)0.5, q = (T)0.25;
@@ -259,90 +216,39 @@ __global__ void __launch_bounds__(256) k_push_fast(PushLaunchT<T> L) {
     warp_deposit<T>(key, ic, jc, v0, v1, v2, v3, lane, nz, L.ir, L.iz);
     // queue the rest for the general path (warp-aggregated append to the
     // block's segment; the shared-memory counter keeps it off global atomics)
-    const unsigned full = 0xffffffffu;
-    unsigned qm = __ballot_sync(full, queued);
-    if (qm) {
-      int leader = __ffs(qm) - 1;
-      int qb = 0;
-      if (lane == leader) qb = atomicAdd(&s_qn, __popc(qm));
-      qb = __shfl_sync(full, qb, leader);
-      if (queued) {
-        long long k = qoff + qb + __popc(qm & ((1u << lane) - 1u));
-        L.queue[k] = (int)p;
-        L.q_cell[k] = c0;
-        L.q_a[k] = a;
-        L.q_b[k] = b;
-        L.q_ur[k] = ur;
-        L.q_ut[k] = ut;
-        L.q_uz[k] = uz;
-        L.q_w[k] = w;
-        L.q_da[k] = trial ? d : (T)NAN;
-        L.q_db[k] = e;
-      }
+    const long long k = seg_append(&s_qn, queued, lane, qoff);
+    if (queued) {
+      L.queue[k] = (int)p;
+      L.q_da[k] = trial ? d : (T)NAN;
+      L.q_db[k] = e;
     }
   }
   __syncthreads();
   if (threadIdx.x == 0) L.qblock[blockIdx.x] = s_qn;
-  Tally T0 = {0, 0, 0, 0, 0};
-  flush_tally(L.counters, T0, lane, n_newton, n_acc, kOpFastNewton, kOpFastAccept);
+  Tally T0 = {0, 0, 0, 0, 0, 0};
+  flush_tally(L.counters, T0, lane, n_newton, n_acc);
 }
 
 // queued particles (or all of them when queue == nullptr); blockDim 256
 template <typename T, bool kB>
 __global__ void __launch_bounds__(256) k_push_general(PushLaunchT<T> L) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   GenArgs<T> G;
   G.nr = L.g.nr; G.nz = L.g.nz; G.ar = L.ar; G.az = L.az;
   G.wt = L.wbt; G.icr = L.icr; G.icz = L.icz;
   G.q = L.q; G.m = L.m; G.qf = L.qf; G.ir = L.ir; G.iz = L.iz; G.write = L.write; G.p = L.p;
   G.wall_z0 = L.wall_z0; G.wall_zl = L.wall_zl; G.wall_r = L.wall_r; G.ke_lost = L.ke_lost;
-  Tally tl = {0, 0, 0, 0, 0};
+  Tally tl = {0, 0, 0, 0, 0, 0};
   const long long gstride = (long long)gridDim.x * blockDim.x;
   const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (L.queue) {
-    // exclusive prefix of the per-block segment lengths, in shared memory
-    constexpr int kPer = (kMaxFastBlocks + 255) / 256;
     __shared__ int s_pre[kMaxFastBlocks + 1];
-    __shared__ int s_w[8];
-    const int nblk = L.qgrid;
-    int loc[kPer], sum = 0;
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-      int idx = threadIdx.x * kPer + k;
-      loc[k] = idx < nblk ? L.qblock[idx] : 0;
-      sum += loc[k];
-    }
-    int incl = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      int t = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += t;
-    }
-    if (lane == 31) s_w[warp] = incl;
-    __syncthreads();
-    int wpre = 0;
-    for (int k = 0; k < warp; ++k) wpre += s_w[k];
-    int ex = wpre + incl - sum;
-#pragma unroll
-    for (int k = 0; k < kPer; ++k) {
-      int idx = threadIdx.x * kPer + k;
-      if (idx < nblk) s_pre[idx] = ex;
-      ex += loc[k];
-    }
-    if (threadIdx.x == 255) s_pre[nblk] = ex;
-    __syncthreads();
-    const int total = s_pre[nblk];
+    const int total = seg_prefix(L.qblock, L.qgrid, s_pre);
     for (long long q = gtid; q < total; q += gstride) {
-      // segment b with s_pre[b] <= q < s_pre[b + 1]
-      int lo = 0, hi = nblk;
-      while (hi - lo > 1) {
-        int mid = (lo + hi) >> 1;
-        if (s_pre[mid] <= (int)q) lo = mid;
-        else hi = mid;
-      }
-      long long k = (long long)lo * L.qseg + (q - s_pre[lo]);
-      push_general<T, kB>(G, L.queue[k], L.q_cell[k], L.q_a[k], L.q_b[k], L.q_ur[k], L.q_ut[k],
-                          L.q_uz[k], L.q_w[k], L.q_da[k], L.q_db[k], tl);
+      long long k = seg_entry(s_pre, L.qgrid, L.qseg, (int)q);
+      long long p = L.queue[k];
+      push_general<T, kB>(G, p, L.p.cell[p], L.p.a[p], L.p.b[p], L.p.vr[p] * L.cr,
+                          L.p.vt[p] * L.cr, L.p.vz[p] * L.cz, L.p.w[p], L.q_da[k], L.q_db[k], tl);
     }
   } else {
     for (long long k = gtid; k < L.n; k += gstride) {
@@ -350,23 +256,14 @@ __global__ void __launch_bounds__(256) k_push_general(PushLaunchT<T> L) {
                           L.p.vt[k] * L.cr, L.p.vz[k] * L.cz, L.p.w[k], (T)NAN, (T)NAN, tl);
     }
   }
-  flush_tally(L.counters, tl, lane, 0, 0, 0, 0);
+  flush_tally(L.counters, tl, lane, 0, 0);
 }
 
-// grid of the persistent fast kernel: resident blocks of 256 threads per SM x SMs
+// grid of the persistent fast kernel
 template <typename T>
 long long fast_grid() {
-  static long long nb = 0;
-  if (nb == 0) {
-    int v = 0, dev = 0, nsm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_push_fast<T>, 256, 0) != cudaSuccess ||
-        v < 1)
-      v = 1;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
-      nsm = 152;
-    nb = (long long)v * nsm;
-  }
+  static int nb = 0;
+  if (nb == 0) nb = persistent_grid(k_push_fast<T>);
   return nb;
 }
 
