@@ -147,6 +147,18 @@ __device__ __forceinline__ void eval_gen(const SubT<T> &s, T wt, T da, T db, T t
   o.ut1 = ut1;
 }
 
+// Early stop of the 2x2 Newton iterations, per unknown: with c the last
+// correction, cp the one before and t the tolerance, the contraction rate is
+// theta = c/cp; while theta < 1/2 the remaining error is below
+// theta/(1-theta) c <= 2 c^2/cp (a contraction-rate bound, as in the stopping
+// rule of simplified Newton iterations, Hairer & Wanner, Solving ODEs II,
+// IV.8).  Accepting when that bound is below 1 % of the tolerance saves the
+// confirming iteration without loosening the accuracy (no division needed).
+template <typename T>
+__device__ __forceinline__ bool contracted(T c, T cp, T t) {
+  return c == (T)0 || ((T)2 * c < cp && (T)200 * c * c <= cp * t);
+}
+
 template <typename T, bool kB>
 __device__ __forceinline__ bool interior_gen(const SubT<T> &s, T wt, T tau, T &pda, T &pdb,
                                              unsigned &it_count) {
@@ -158,6 +170,7 @@ __device__ __forceinline__ bool interior_gen(const SubT<T> &s, T wt, T tau, T &p
   T da = tau * (s.ur + h * tau * A0);
   T db = tau * (s.uz + h * tau * (s.az0 + s.gaz * s.a));
   if (s.P != zero && s.rho + da <= zero) da = -h * s.rho;
+  T pca = zero, pcb = zero;
   for (int it = 0; it < kNewtonMaxGen; ++it) {
     ResT<T> o;
     eval_gen<T, kB>(s, wt, da, db, tau, o);
@@ -174,11 +187,14 @@ __device__ __forceinline__ bool interior_gen(const SubT<T> &s, T wt, T tau, T &p
     da = nda;
     db = ndb;
     if (!isfinite(da) || !isfinite(db)) return false;
-    if (ca <= tol_r<T>(s.rho + da, da) && cb <= tol_x<T>(db)) {
+    const T ta = tol_r<T>(s.rho + da, da), tb = tol_x<T>(db);
+    if ((ca <= ta && cb <= tb) || (contracted(ca, pca, ta) && contracted(cb, pcb, tb))) {
       pda = da;
       pdb = db;
       return true;
     }
+    pca = ca;
+    pcb = cb;
   }
   return false;
 }
@@ -188,6 +204,7 @@ __device__ __forceinline__ bool landing_gen(const SubT<T> &s, T wt, int dir, T X
                                             T &ptau, T &poth, unsigned &it_count) {
   const T h = (T)0.5, q = (T)0.25, zero = (T)0, one = (T)1;
   T tau = t0, oth = oth0;
+  T pco = zero, pct = zero;
   for (int it = 0; it < kNewtonMaxGen; ++it) {
     T da = dir == 0 ? X : oth;
     T db = dir == 0 ? oth : X;
@@ -225,12 +242,14 @@ __device__ __forceinline__ bool landing_gen(const SubT<T> &s, T wt, int dir, T X
     oth = noth;
     tau = ntau;
     if (!isfinite(oth) || !isfinite(tau)) return false;
-    T to = dir == 1 ? tol_r<T>(s.rho + oth, oth) : tol_x<T>(oth);
-    if (co <= to && ct <= tol_x<T>(tau)) {
+    const T to = dir == 1 ? tol_r<T>(s.rho + oth, oth) : tol_x<T>(oth), tt = tol_x<T>(tau);
+    if ((co <= to && ct <= tt) || (contracted(co, pco, to) && contracted(ct, pct, tt))) {
       ptau = tau;
       poth = oth;
       return true;
     }
+    pco = co;
+    pct = ct;
   }
   return false;
 }
@@ -373,11 +392,16 @@ __device__ void push_general(const GenArgs<T> &L, long long p, int c0, T a, T b,
     s.ur = ur; s.ut = ut; s.uz = uz;
     s.P = s.rho * ut + h * wt * s.rho * s.rho;
     T da, db;
+    // tight: converged to half an ulp (scalar solves), so the CN velocity
+    // relation u' = 2 dx / tau - u may replace an evaluation
+    bool tight = true;
     if (nsub == 1 && !Num<T>::nan_bits(tr_da)) {
       da = tr_da;
       db = tr_db;
-    } else if (!(!kB && scalar_interior<T>(s, tT, da, db, Tl.snewton)) &&
-               !interior_gen<T, kB>(s, wt, tT, da, db, Tl.newton)) {
+    } else if (!kB && scalar_interior<T>(s, tT, da, db, Tl.snewton)) {
+    } else if (interior_gen<T, kB>(s, wt, tT, da, db, Tl.newton)) {
+      tight = false;
+    } else {
       tT *= h;
       Tl.fb++;
       continue;
@@ -405,12 +429,12 @@ __device__ void push_general(const GenArgs<T> &L, long long p, int c0, T a, T b,
         T v0 = dir == 0 ? ur : uz;
         T g0;
         if (X != zero) {
-          g0 = tT * (X / dx);
+          g0 = tT * X * Num<T>::rcp(dx);
         } else {  // quadratic model through the trial end point
-          T alpha = two * (dx - v0 * tT) / (tT * tT);
-          g0 = -two * v0 / alpha;
+          T alpha = two * (dx - v0 * tT) * (tT == one ? one : Num<T>::rcp(tT * tT));
+          g0 = -two * v0 * Num<T>::rcp(alpha);
         }
-        T oth0 = doth * (g0 / tT);
+        T oth0 = doth * (g0 * (tT == one ? one : Num<T>::rcp(tT)));
         T tt = zero, toth = zero;
         if (!(g0 > zero) || !landing_gen<T, kB>(s, wt, dir, X, g0, oth0, tt, toth, Tl.newton)) continue;
         if (!(tt > zero) || tt > tT) continue;
@@ -440,11 +464,19 @@ __device__ void push_general(const GenArgs<T> &L, long long p, int c0, T a, T b,
       }
     }
     ResT<T> o;
-    eval_gen<T, kB>(s, wt, da, db, step_t, o);
     T am = a + h * da, bm = b + h * db;
-    T nur = ur + step_t * o.A;
-    T nuz = uz + step_t * o.az;
-    T nut = o.ut1;
+    T nur, nuz, nut;
+    if (!kB && tight && land_dir < 0 && s.rho + da > zero) {
+      const T it = step_t == one ? one : Num<T>::rcp(step_t);
+      nur = two * da * it - ur;
+      nuz = two * db * it - uz;
+      nut = s.P * Num<T>::rcp(s.rho + da);
+    } else {
+      eval_gen<T, kB>(s, wt, da, db, step_t, o);
+      nur = ur + step_t * o.A;
+      nuz = uz + step_t * o.az;
+      nut = o.ut1;
+    }
     if (L.ir) {
       T fr = L.qf * w * da, fz = L.qf * w * db;
       atomicAdd(&L.ir[ic * nz1 + jc], Num<T>::to_double(fr * (one - bm)));

@@ -259,11 +259,17 @@ __global__ void __launch_bounds__(256) k_push_general(PushLaunchT<T> L) {
   flush_tally(L.counters, tl, lane, 0, 0);
 }
 
-// grid of the persistent fast kernel
+// grids of the persistent kernels (one wave of resident blocks)
 template <typename T>
 long long fast_grid() {
   static int nb = 0;
   if (nb == 0) nb = persistent_grid(k_push_fast<T>);
+  return nb;
+}
+template <typename T>
+long long general_grid() {
+  static int nb = 0;
+  if (nb == 0) nb = persistent_grid(k_push_general<T, false>);
   return nb;
 }
 
@@ -282,8 +288,11 @@ cudaError_t launch_push(const PushLaunchT<T> &L, cudaStream_t s) {
     A.qgrid = (int)nf;
     A.qseg = (nb + nf - 1) / nf * bs;  // particles one fast block visits, at most
     k_push_fast<T><<<(unsigned)nf, bs, 0, s>>>(A);
-    // the queue holds the crossing / near-axis particles (a fraction of n)
-    long long ng = nb < 152 * 16 ? nb : 152 * 16;
+    // the queue holds the crossing / near-axis particles (a fraction of n);
+    // one wave, so the per-block prefix of the segment counts is computed once
+    // per resident block
+    long long ng = general_grid<T>();
+    if (ng > nb) ng = nb;
     k_push_general<T, false><<<(unsigned)ng, bs, 0, s>>>(A);
   } else {
     PushLaunchT<T> A = L;
