@@ -70,24 +70,27 @@ __global__ void k_half_alpha64(long long n1, long long n2, const double *er0, co
 }
 
 // rhs(i,j) = 2 mu Vh H0 - dt * C^T L Et   (Et = E0 - dQ/(2 eps A), or the prescribed half value)
+enum { kT2ear = 0, kT2eaz = 1, kTear = 2, kTeaz = 3, kTs = 4, kTvh = 5 };
+__device__ __forceinline__ double tab(const FieldOp &F, int k, int i) {
+  return F.rtab[k * (F.nr + 1) + i];
+}
 __device__ __forceinline__ double rhs_at(const FieldOp &F, const double *er0, const double *ez0,
                                         const double *h0, const double *ir, const double *iz,
                                         double v0, double v1, int i, int j) {
   int nr = F.nr, nz = F.nz, nz1 = nz + 1;
   int c = i * nz + j;
-  double dr = F.dr, dz = F.dz, eps = F.eps;
-  double s = kTwoPi * rhalf(dr, i);
-  double ar = area_r(dr, dz, i);
+  double dr = F.dr, dz = F.dz;
+  double s = tab(F, kTs, i);
+  double r2 = tab(F, kT2ear, i);
   double etb = 0.0, ett = 0.0;
-  if (j != 0) etb = er0[i * nz1 + j] - ir[i * nz1 + j] / (2.0 * eps * ar);
-  if (j + 1 != nz) ett = er0[i * nz1 + j + 1] - ir[i * nz1 + j + 1] / (2.0 * eps * ar);
-  double etl = ez0[i * nz + j] - iz[i * nz + j] / (2.0 * eps * area_z(dr, i));
+  if (j != 0) etb = er0[i * nz1 + j] - ir[i * nz1 + j] * r2;
+  if (j + 1 != nz) ett = er0[i * nz1 + j + 1] - ir[i * nz1 + j + 1] * r2;
+  double etl = ez0[i * nz + j] - iz[i * nz + j] * tab(F, kT2eaz, i);
   double etr;
   if (i + 1 == nr) etr = 0.5 * (v0 + v1) / F.L;
-  else etr = ez0[(i + 1) * nz + j] - iz[(i + 1) * nz + j] / (2.0 * eps * area_z(dr, i + 1));
-  double vh = kTwoPi * rhalf(dr, i) * dr * dz;
+  else etr = ez0[(i + 1) * nz + j] - iz[(i + 1) * nz + j] * tab(F, kT2eaz, i + 1);
   double curl = (-s) * dr * etb + s * dr * ett + s * dz * etl + (-s) * dz * etr;
-  return 2.0 * F.mu * vh * h0[c] - F.dt * curl;
+  return 2.0 * F.mu * tab(F, kTvh, i) * h0[c] - F.dt * curl;
 }
 
 __global__ void k_rhs(FieldOp F, const double *er0, const double *ez0, const double *h0,
@@ -197,6 +200,119 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, const double 
     }
 }
 
+// ---------------------------------------------------------------------------
+// DCTs along z by FFT (Makhoul, IEEE Trans. ASSP 28, 1980): with the even
+// samples in order followed by the odd ones reversed, v = (x0, x2, ..., x3,
+// x1), the DCT-II is X[m] = Re(exp(-i pi m / 2N) V[m]) with V = DFT(v); two
+// real rows are transformed at once as the real and imaginary parts of one
+// complex sequence.  The N-point DFT is a mixed-radix (4, 2, 3) Stockham
+// autosort FFT in shared memory (Stockham 1966; index form of Govindaraju et
+// al., SC 2008).
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+
+// forward DFT (exp(-2 pi i jk / N)) of x; y is scratch; returns the buffer holding the result
+__device__ double2 *fft_fwd(const FieldOp &F, double2 *x, double2 *y) {
+  const int N = F.fft;
+  int Ns = 1;
+  for (int p = 0; p < F.nrad; ++p) {
+    const int R = F.rad[p], nb = N / R;
+    for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+      const int k = j % Ns;
+      const int ts = (N / (Ns * R)) * k;
+      double2 v0 = x[j], v1 = cmul(x[j + nb], F.tw[ts]);
+      const int d = (j / Ns) * Ns * R + k;
+      if (R == 2) {
+        y[d] = cadd(v0, v1);
+        y[d + Ns] = csub(v0, v1);
+      } else if (R == 4) {
+        double2 v2 = cmul(x[j + 2 * nb], F.tw[2 * ts]), v3 = cmul(x[j + 3 * nb], F.tw[3 * ts]);
+        double2 s02 = cadd(v0, v2), d02 = csub(v0, v2), s13 = cadd(v1, v3), d13 = csub(v1, v3);
+        y[d] = cadd(s02, s13);
+        y[d + Ns] = make_double2(d02.x + d13.y, d02.y - d13.x);      // d02 - i d13
+        y[d + 2 * Ns] = csub(s02, s13);
+        y[d + 3 * Ns] = make_double2(d02.x - d13.y, d02.y + d13.x);  // d02 + i d13
+      } else {  // R == 3
+        const double s3 = 0.86602540378443864676;  // sqrt(3)/2
+        double2 v2 = cmul(x[j + 2 * nb], F.tw[2 * ts]);
+        double2 t1 = cadd(v1, v2), dd = csub(v1, v2);
+        double2 t2 = make_double2(v0.x - 0.5 * t1.x, v0.y - 0.5 * t1.y);
+        double2 t3 = make_double2(s3 * dd.y, -s3 * dd.x);
+        y[d] = cadd(v0, t1);
+        y[d + Ns] = cadd(t2, t3);
+        y[d + 2 * Ns] = csub(t2, t3);
+      }
+    }
+    __syncthreads();
+    double2 *t = x;
+    x = y;
+    y = t;
+    Ns *= R;
+  }
+  return x;
+}
+
+__device__ __forceinline__ int dct_perm(int j, int N) { return (j & 1) ? N - 1 - (j >> 1) : (j >> 1); }
+
+// orthonormal DCT-II along z of rows 2b, 2b+1 of src into dst (nr x nz, natural modes)
+__global__ void __launch_bounds__(128) k_dct2(FieldOp F, const double *__restrict__ src,
+                                              double *__restrict__ dst) {
+  extern __shared__ double2 smc[];
+  const int N = F.fft;
+  double2 *a = smc, *b = smc + N;
+  const int r0 = 2 * blockIdx.x, r1 = r0 + 1;
+  const bool two = r1 < F.nr;
+  for (int j = threadIdx.x; j < N; j += blockDim.x)
+    a[dct_perm(j, N)] = make_double2(src[r0 * N + j], two ? src[r1 * N + j] : 0.0);
+  __syncthreads();
+  const double2 *Z = fft_fwd(F, a, b);
+  for (int m = threadIdx.x; m < N; m += blockDim.x) {
+    const double2 z = Z[m], zr = Z[m == 0 ? 0 : N - m];
+    const double2 w = F.pw[m];
+    const double c = m == 0 ? F.c0 : F.c1;
+    // V_A = (Z + conj Zr)/2, V_B = (Z - conj Zr)/(2i); X = Re(exp(-i pi m/2N) V)
+    const double xa = 0.5 * (w.x * (z.x + zr.x) + w.y * (z.y - zr.y));
+    const double xb = 0.5 * (w.x * (z.y + zr.y) - w.y * (z.x - zr.x));
+    dst[r0 * N + m] = c * xa;
+    if (two) dst[r1 * N + m] = c * xb;
+  }
+}
+
+// orthonormal DCT-III (inverse of k_dct2) of rows 2b, 2b+1
+__global__ void __launch_bounds__(128) k_dct3(FieldOp F, const double *__restrict__ src,
+                                              double *__restrict__ dst) {
+  extern __shared__ double2 smc[];
+  const int N = F.fft;
+  double2 *a = smc, *b = smc + N;
+  const int r0 = 2 * blockIdx.x, r1 = r0 + 1;
+  const bool two = r1 < F.nr;
+  const double i0 = 1.0 / F.c0, i1 = 1.0 / F.c1;
+  // Z = V_A + i V_B with V[m] = exp(i pi m/2N) (X[m] - i X[N-m]), X[N] = 0; the
+  // inverse DFT is taken as conj(DFT(conj Z)) / N, so conj Z is stored
+  for (int m = threadIdx.x; m < N; m += blockDim.x) {
+    const double sm = m == 0 ? i0 : i1;
+    const double pa = src[r0 * N + m] * sm, pb = two ? src[r1 * N + m] * sm : 0.0;
+    const double qa = m == 0 ? 0.0 : -src[r0 * N + N - m] * i1;
+    const double qb = (m == 0 || !two) ? 0.0 : -src[r1 * N + N - m] * i1;
+    const double2 w = F.pw[m];
+    const double2 va = make_double2(pa * w.x - qa * w.y, pa * w.y + qa * w.x);
+    const double2 vb = make_double2(pb * w.x - qb * w.y, pb * w.y + qb * w.x);
+    a[m] = make_double2(va.x - vb.y, -(va.y + vb.x));
+  }
+  __syncthreads();
+  const double2 *z = fft_fwd(F, a, b);
+  const double inv = 1.0 / (double)N;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    const double2 v = z[dct_perm(j, N)];
+    dst[r0 * N + j] = v.x * inv;
+    if (two) dst[r1 * N + j] = -v.y * inv;
+  }
+}
+
 // Thomas solve per DCT mode m along r; MB modes per block staged in shared memory
 __global__ void k_tridiag(FieldOp F, int mb) {
   extern __shared__ double sm[];
@@ -256,7 +372,7 @@ __global__ void __launch_bounds__(256) k_update(FieldOp F, const double *er0, co
   long long ner = (long long)nr * nz1, nez = (long long)(nr + 1) * nz, nh = (long long)nr * nz;
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double dn = 0.0, nn = 0.0, src = 0.0;
-  double dr = F.dr, dz = F.dz, eps = F.eps, dt = F.dt;
+  double dz = F.dz, dt = F.dt;
   if (t < nh) {
     int i = (int)(t / nz), j = (int)(t - (t / nz) * nz);
     h1[t] = 2.0 * hhalf_at(F, i, j) - h0[t];
@@ -266,9 +382,9 @@ __global__ void __launch_bounds__(256) k_update(FieldOp F, const double *er0, co
     if (j == 0 || j == nz) {
       er1[t] = 0.0;
     } else {
-      double s = kTwoPi * rhalf(dr, i);
+      double s = tab(F, kTs, i);
       double ch = -s * hhalf_at(F, i, j) + s * hhalf_at(F, i, j - 1);
-      double e1 = er0[t] + (dt * ch - ir[t]) / (eps * area_r(dr, dz, i));
+      double e1 = er0[t] + (dt * ch - ir[t]) * tab(F, kTear, i);
       er1[t] = e1;
       if (er_it) {
         double d = e1 - er_it[t];
@@ -280,14 +396,14 @@ __global__ void __launch_bounds__(256) k_update(FieldOp F, const double *er0, co
   if (t < nez) {
     int i = (int)(t / nz), j = (int)(t - (t / nz) * nz);
     double ch = 0.0;
-    if (i <= nr - 1) ch += kTwoPi * rhalf(dr, i) * hhalf_at(F, i, j);
-    if (i >= 1) ch += -kTwoPi * rhalf(dr, i - 1) * hhalf_at(F, i - 1, j);
+    if (i <= nr - 1) ch += tab(F, kTs, i) * hhalf_at(F, i, j);
+    if (i >= 1) ch += -tab(F, kTs, i - 1) * hhalf_at(F, i - 1, j);
     if (i == nr) {
       ez1[t] = v1 / F.L;
       double eh = 0.5 * (v0 + v1) / F.L;
       src += eh * dz * (iz[t] - dt * ch);
     } else {
-      double e1 = ez0[t] + (dt * ch - iz[t]) / (eps * area_z(dr, i));
+      double e1 = ez0[t] + (dt * ch - iz[t]) * tab(F, kTeaz, i);
       ez1[t] = e1;
       if (ez_it) {
         double d = e1 - ez_it[t];
@@ -363,7 +479,17 @@ cudaError_t launch_field_solve(const FieldOp &F, const double *er0, const double
   int h = F.half;
   Gemm G;
   dim3 g16((h + GT - 1) / GT, (F.nr + GT - 1) / GT, 2);
-  if (h) {
+  const unsigned npair = (unsigned)((F.nr + 1) / 2);
+  const size_t fsm = (size_t)2 * F.fft * sizeof(double2);
+  static bool fattr = false;
+  if (F.fft && !fattr) {
+    cudaFuncSetAttribute(k_dct2, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024);
+    cudaFuncSetAttribute(k_dct3, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024);
+    fattr = true;
+  }
+  if (F.fft) {
+    k_dct2<<<npair, 128, fsm, s>>>(F, F.rhs, F.hat);
+  } else if (h) {
     // hat[:, 0:h] = S * Qe, hat[:, h:nz] = D * Qo   (even / odd DCT modes)
     G.M = F.nr; G.N = h; G.K = h; G.lda = h; G.ldb = h; G.ldc = F.nz;
     G.A[0] = F.rhs; G.A[1] = F.rhs + F.nr * h;
@@ -373,8 +499,9 @@ cudaError_t launch_field_solve(const FieldOp &F, const double *er0, const double
   } else {
     k_gemm<<<grid, 256, 0, s>>>(F.nr, F.nz, F.nz, F.rhs, F.Q, F.hat);
   }
-  // few modes per block so that many blocks stage their columns in parallel
-  int mb = 2;
+  // a full warp of modes per block: an FP64 warp instruction costs the same
+  // pipe time whatever the number of active lanes
+  int mb = 32;
   while (mb > 1 && (size_t)3 * F.nr * mb * sizeof(double) > 200 * 1024) mb >>= 1;
   size_t smem = (size_t)3 * F.nr * mb * sizeof(double);
   static bool attr_set = false;
@@ -383,7 +510,9 @@ cudaError_t launch_field_solve(const FieldOp &F, const double *er0, const double
     attr_set = true;
   }
   k_tridiag<<<(F.nz + mb - 1) / mb, 256, smem, s>>>(F, mb);
-  if (h) {
+  if (F.fft) {
+    k_dct3<<<npair, 128, fsm, s>>>(F, F.hat, F.hhalf);
+  } else if (h) {
     // P = hat_e * Qe^T, R = hat_o * Qo^T; H_half(j) = P + R, H_half(nz-1-j) = P - R
     G.M = F.nr; G.N = h; G.K = h; G.lda = F.nz; G.ldb = h; G.ldc = h;
     G.A[0] = F.hat; G.A[1] = F.hat + h;

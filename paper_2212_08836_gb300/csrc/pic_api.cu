@@ -160,6 +160,9 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
   x->F.rhs = (double *)K.take(nh * 8);
   x->F.hat = (double *)K.take(nh * 8);
   x->F.hhalf = (double *)K.take(nh * 8);
+  x->F.tw = (const double2 *)K.take((size_t)nz * 16);
+  x->F.pw = (const double2 *)K.take((size_t)nz * 16);
+  x->F.rtab = (const double *)K.take((size_t)6 * (nr + 1) * 8);
   x->cnt = (DevCounters *)K.take(sizeof(DevCounters));
   x->cand = (uint32_t *)K.take((2 * (size_t)pc + 2 * (size_t)kMaxFastBlocks * 256) * 4);
   x->cblock = (int *)K.take((size_t)kMaxFastBlocks * 4);
@@ -390,7 +393,24 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
   F.L = cfg->L;
   double dr = F.dr, dz = F.dz, hdt2 = 0.5 * cfg->dt * cfg->dt;
   std::vector<double> Q((size_t)nz * nz), QT((size_t)nz * nz), lam(nz);
-  F.half = (nz % 2 == 0) ? nz / 2 : 0;
+  // FFT path when nz = 4^a 2^b 3^c is even (at most 4096); else the GEMM path
+  F.fft = 0;
+  F.nrad = 0;
+  if (nz % 2 == 0 && nz <= 4096) {
+    int n = nz, k = 0;
+    int rad[16];
+    while (n % 4 == 0 && k < 16) { rad[k++] = 4; n /= 4; }
+    while (n % 2 == 0 && k < 16) { rad[k++] = 2; n /= 2; }
+    while (n % 3 == 0 && k < 16) { rad[k++] = 3; n /= 3; }
+    if (n == 1) {
+      F.fft = nz;
+      F.nrad = k;
+      for (int q = 0; q < k; ++q) F.rad[q] = rad[q];
+    }
+  }
+  F.half = (!F.fft && nz % 2 == 0) ? nz / 2 : 0;
+  F.c0 = sqrt(1.0 / nz);
+  F.c1 = sqrt(2.0 / nz);
   const int hz = F.half;
   auto qbasis = [&](int j, int m) {
     double cm = m == 0 ? sqrt(1.0 / nz) : sqrt(2.0 / nz);
@@ -447,10 +467,33 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
       ci[(size_t)i * nz + cm] = 1.0 / c;
     }
   }
+  // twiddles, DCT phases and per-row reciprocal tables
+  std::vector<double> tw((size_t)2 * nz), pw((size_t)2 * nz), rt((size_t)6 * (nr + 1), 0.0);
+  for (int k = 0; k < nz; ++k) {
+    double t = -kTwoPi * (double)k / nz;
+    tw[2 * k] = cos(t);
+    tw[2 * k + 1] = sin(t);
+    double u = kPi * (double)k / (2.0 * nz);
+    pw[2 * k] = cos(u);
+    pw[2 * k + 1] = sin(u);
+  }
+  for (int i = 0; i <= nr; ++i) {
+    double ari = kTwoPi * rh(i) * dz;
+    double azi = az(i);
+    rt[0 * (nr + 1) + i] = 1.0 / (2.0 * x->eps * ari);
+    rt[1 * (nr + 1) + i] = 1.0 / (2.0 * x->eps * azi);
+    rt[2 * (nr + 1) + i] = 1.0 / (x->eps * ari);
+    rt[3 * (nr + 1) + i] = 1.0 / (x->eps * azi);
+    rt[4 * (nr + 1) + i] = kTwoPi * rh(i);
+    rt[5 * (nr + 1) + i] = kTwoPi * rh(i) * dr * dz;
+  }
   cudaError_t e = cudaSuccess;
   auto up = [&](const void *dst, const void *src, size_t b) {
     if (e == cudaSuccess) e = cudaMemcpyAsync((void *)dst, src, b, cudaMemcpyHostToDevice, x->s);
   };
+  up(F.tw, tw.data(), tw.size() * 8);
+  up(F.pw, pw.data(), pw.size() * 8);
+  up(F.rtab, rt.data(), rt.size() * 8);
   up(F.Q, Q.data(), Q.size() * 8);
   up(F.QT, QT.data(), QT.size() * 8);
   up(F.lfac, lf.data(), lf.size() * 8);

@@ -102,6 +102,16 @@ struct FieldOp {
   double *rhs;         // nr x nz scratch
   double *hat;         // nr x nz scratch
   double *hhalf;       // nr x nz: H^{n+1/2}
+  // FFT path (fft = nz = 2^a 3^b, nz even): the DCTs along z by an nz-point
+  // complex FFT per pair of rows (natural mode order, half = 0)
+  int fft;
+  int nrad, rad[16];   // radices (4, 2, 3) of the mixed-radix Stockham passes
+  const double2 *tw;   // tw[k] = exp(-2 pi i k / nz)
+  const double2 *pw;   // pw[m] = (cos, sin)(pi m / (2 nz))
+  double c0, c1;       // DCT-II normalisation sqrt(1/nz), sqrt(2/nz)
+  // per-row tables (nr + 1 entries each): 1/(2 eps A_r), 1/(2 eps A_z),
+  // 1/(eps A_r), 1/(eps A_z), 2 pi r_{i+1/2}, V_H
+  const double *rtab;
 };
 
 // One mover + deposit pass over one species (rows a2, a3, a6) in the scalar
