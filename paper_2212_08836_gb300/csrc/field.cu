@@ -313,35 +313,59 @@ __global__ void __launch_bounds__(128) k_dct3(FieldOp F, const double *__restric
   }
 }
 
-// Thomas solve per DCT mode m along r; MB modes per block staged in shared memory
-__global__ void k_tridiag(FieldOp F, int mb) {
-  extern __shared__ double sm[];
-  int nr = F.nr, nz = F.nz;
-  int m0 = blockIdx.x * mb;
-  double *x = sm;                 // nr x mb
-  double *l = sm + nr * mb;       // nr x mb
-  double *ci = sm + 2 * nr * mb;  // nr x mb
-  for (int e = threadIdx.x; e < nr * mb; e += blockDim.x) {
-    int i = e / mb, k = e - (e / mb) * mb;
-    int m = m0 + k;
-    bool ok = m < nz;
-    x[e] = ok ? F.hat[i * nz + m] : 0.0;
-    l[e] = ok ? F.lfac[i * nz + m] : 0.0;
-    ci[e] = ok ? F.cinv[i * nz + m] : 0.0;
+// Tridiagonal solve along r per DCT mode by cyclic reduction (Hockney, J. ACM
+// 12, 1965): the forward levels s = 1, 2, 4, ... fold rows i = 2sk + 2s - 1
+// into d_i += alpha d_{i-s} + gamma d_{i+s}; the back levels solve rows
+// j = 2sk + s - 1 as x_j = d_j/b_j - (a_j/b_j) x_{j-s} - (c_j/b_j) x_{j+s}.  The
+// operator does not change between solves, so every coefficient is
+// precomputed; per solve the dependency chain is 2 log2(n2) levels instead of
+// the 2 nr steps of the Thomas algorithm.  One warp per mode, mb modes per
+// block staged in shared memory (coalesced along the modes).
+__global__ void k_cr(FieldOp F) {
+  extern __shared__ double sd[];
+  const int n2 = F.n2, nr = F.nr, nz = F.nz;
+  const int mb = blockDim.x >> 5;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * mb;
+  for (int e = threadIdx.x; e < n2 * mb; e += blockDim.x) {
+    const int i = e / mb, k = e - i * mb, m = m0 + k;
+    sd[k * n2 + i] = (i < nr && m < nz) ? F.hat[i * nz + m] : 0.0;
   }
   __syncthreads();
-  int k = threadIdx.x;
-  if (k < mb && m0 + k < nz) {
-    for (int i = 1; i < nr; ++i) x[i * mb + k] -= l[i * mb + k] * x[(i - 1) * mb + k];
-    x[(nr - 1) * mb + k] *= ci[(nr - 1) * mb + k];
-    for (int i = nr - 2; i >= 0; --i)
-      x[i * mb + k] = (x[i * mb + k] - F.eoff[i + 1] * x[(i + 1) * mb + k]) * ci[i * mb + k];
+  const int m = m0 + w;
+  if (m < nz) {
+    double *d = sd + w * n2;
+    const double *co = F.crc + (size_t)m * 5 * n2;
+    const double *fa = co, *fg = co + n2, *bp = co + 2 * n2, *bq = co + 3 * n2, *br = co + 4 * n2;
+    int off = 0;
+    for (int s = 1; s < n2; s <<= 1) {
+      const int cnt = n2 / (2 * s);
+      for (int k = lane; k < cnt; k += 32) {
+        const int i = 2 * s * k + 2 * s - 1;
+        double v = d[i] + fa[off + k] * d[i - s];
+        if (i + s < n2) v += fg[off + k] * d[i + s];
+        d[i] = v;
+      }
+      off += cnt;
+      __syncwarp();
+    }
+    off = 0;
+    for (int s = n2; s >= 1; s >>= 1) {
+      const int cnt = n2 >= 2 * s ? n2 / (2 * s) : 1;
+      for (int k = lane; k < cnt; k += 32) {
+        const int j = 2 * s * k + s - 1;
+        const double xl = j - s >= 0 ? d[j - s] : 0.0;
+        const double xr = j + s < n2 ? d[j + s] : 0.0;
+        d[j] = br[off + k] * d[j] - bp[off + k] * xl - bq[off + k] * xr;
+      }
+      off += cnt;
+      __syncwarp();
+    }
   }
   __syncthreads();
   for (int e = threadIdx.x; e < nr * mb; e += blockDim.x) {
-    int i = e / mb, kk = e - (e / mb) * mb;
-    int m = m0 + kk;
-    if (m < nz) F.hat[i * nz + m] = x[e];
+    const int i = e / mb, k = e - i * mb, mm = m0 + k;
+    if (mm < nz) F.hat[i * nz + mm] = sd[k * n2 + i];
   }
 }
 
@@ -499,17 +523,15 @@ cudaError_t launch_field_solve(const FieldOp &F, const double *er0, const double
   } else {
     k_gemm<<<grid, 256, 0, s>>>(F.nr, F.nz, F.nz, F.rhs, F.Q, F.hat);
   }
-  // a full warp of modes per block: an FP64 warp instruction costs the same
-  // pipe time whatever the number of active lanes
-  int mb = 32;
-  while (mb > 1 && (size_t)3 * F.nr * mb * sizeof(double) > 200 * 1024) mb >>= 1;
-  size_t smem = (size_t)3 * F.nr * mb * sizeof(double);
+  // modes per block: up to 8 (one warp each) within the shared-memory budget
+  int mb = 8;
+  while (mb > 1 && (size_t)F.n2 * mb * sizeof(double) > 160 * 1024) mb >>= 1;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaFuncSetAttribute(k_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    cudaFuncSetAttribute(k_cr, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
-  k_tridiag<<<(F.nz + mb - 1) / mb, 256, smem, s>>>(F, mb);
+  k_cr<<<(F.nz + mb - 1) / mb, 32 * mb, (size_t)F.n2 * mb * sizeof(double), s>>>(F);
   if (F.fft) {
     k_dct3<<<npair, 128, fsm, s>>>(F, F.hat, F.hhalf);
   } else if (h) {

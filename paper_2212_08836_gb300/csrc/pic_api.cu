@@ -154,9 +154,10 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
   x->wall = (double *)K.take((size_t)2 * (2 * (nr + 1) + nz + 1) * 8);
   x->F.Q = (double *)K.take((size_t)nz * nz * 8);
   x->F.QT = (double *)K.take((size_t)nz * nz * 8);
-  x->F.lfac = (double *)K.take(nh * 8);
-  x->F.cinv = (double *)K.take(nh * 8);
-  x->F.eoff = (double *)K.take((size_t)nr * 8);
+  int n2 = 1;
+  while (n2 < nr) n2 *= 2;
+  x->F.n2 = n2;
+  x->F.crc = (const double *)K.take((size_t)5 * n2 * nz * 8);
   x->F.rhs = (double *)K.take(nh * 8);
   x->F.hat = (double *)K.take(nh * 8);
   x->F.hhalf = (double *)K.take(nh * 8);
@@ -453,18 +454,45 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
     kdiag[i] = hdt2 * d;
     if (i >= 1) eoff[i] = hdt2 * wz_i * (-kTwoPi * rh(i - 1)) * s;
   }
-  std::vector<double> lf((size_t)nr * nz), ci((size_t)nr * nz);
+  // cyclic-reduction coefficients of each column (rows padded to n2 with identity)
+  const int n2 = F.n2;
+  std::vector<double> cr((size_t)5 * n2 * nz, 0.0);
+  std::vector<double> A(n2), B(n2), Cc(n2);
   for (int m = 0; m < nz; ++m) {
-    int cm = col[m];
-    double c = mass[0] + kz[0] * lam[m] + kdiag[0];
-    lf[cm] = 0.0;
-    ci[cm] = 1.0 / c;
-    for (int i = 1; i < nr; ++i) {
-      double d = mass[i] + kz[i] * lam[m] + kdiag[i];
-      double l = eoff[i] / c;
-      c = d - l * eoff[i];
-      lf[(size_t)i * nz + cm] = l;
-      ci[(size_t)i * nz + cm] = 1.0 / c;
+    double *co = cr.data() + (size_t)col[m] * 5 * n2;
+    for (int i = 0; i < n2; ++i) {
+      bool in = i < nr;
+      A[i] = in && i >= 1 ? eoff[i] : 0.0;
+      Cc[i] = in && i + 1 < nr ? eoff[i + 1] : 0.0;
+      B[i] = in ? mass[i] + kz[i] * lam[m] + kdiag[i] : 1.0;
+    }
+    int off = 0;
+    for (int s = 1; s < n2; s *= 2) {
+      const int cnt = n2 / (2 * s);
+      for (int k = 0; k < cnt; ++k) {
+        const int i = 2 * s * k + 2 * s - 1;
+        const bool up = i + s < n2;
+        const double al = -A[i] / B[i - s];
+        const double ga = up ? -Cc[i] / B[i + s] : 0.0;
+        co[off + k] = al;
+        co[n2 + off + k] = ga;
+        const double nb = B[i] + al * Cc[i - s] + (up ? ga * A[i + s] : 0.0);
+        A[i] = al * A[i - s];
+        Cc[i] = up ? ga * Cc[i + s] : 0.0;
+        B[i] = nb;
+      }
+      off += cnt;
+    }
+    off = 0;
+    for (int s = n2; s >= 1; s /= 2) {
+      const int cnt = n2 >= 2 * s ? n2 / (2 * s) : 1;
+      for (int k = 0; k < cnt; ++k) {
+        const int j = 2 * s * k + s - 1;
+        co[2 * n2 + off + k] = A[j] / B[j];
+        co[3 * n2 + off + k] = Cc[j] / B[j];
+        co[4 * n2 + off + k] = 1.0 / B[j];
+      }
+      off += cnt;
     }
   }
   // twiddles, DCT phases and per-row reciprocal tables
@@ -496,9 +524,7 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
   up(F.rtab, rt.data(), rt.size() * 8);
   up(F.Q, Q.data(), Q.size() * 8);
   up(F.QT, QT.data(), QT.size() * 8);
-  up(F.lfac, lf.data(), lf.size() * 8);
-  up(F.cinv, ci.data(), ci.size() * 8);
-  up(F.eoff, eoff.data(), eoff.size() * 8);
+  up(F.crc, cr.data(), cr.size() * 8);
   size_t ner = (size_t)nr * (nz + 1), nez = (size_t)(nr + 1) * nz, nh = (size_t)nr * nz;
   if (e == cudaSuccess) e = cudaMemsetAsync(x->er, 0, ner * 8, x->s);
   if (e == cudaSuccess) e = cudaMemsetAsync(x->ez, 0, nez * 8, x->s);

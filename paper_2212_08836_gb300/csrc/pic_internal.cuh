@@ -96,9 +96,12 @@ struct FieldOp {
   const double *Q;     // split: Qe[j*h+k] = Q(j, 2k), then Qo[j*h+k] = Q(j, 2k+1), j,k < h
                        // else the nz x nz DCT-II basis Q[j*nz+m]
   const double *QT;    // split: Qe^T, Qo^T (h x h each); else the transpose of Q
-  const double *lfac;  // nr x nz: Thomas multipliers l[i*nz+c] (i >= 1), column c of mode m
-  const double *cinv;  // nr x nz: 1 / pivots (split: c = m/2 for even m, h + m/2 for odd m)
-  const double *eoff;  // nr: off-diagonal e_i (coupling i-1, i), e_0 = 0
+  // cyclic reduction of the tridiagonal system of column c (split: c = m/2 for
+  // even m, h + m/2 for odd m; else c = m), padded to n2 = 2^k >= nr rows:
+  // crc[c*5*n2 + ...] = forward multipliers (alpha, gamma), then the
+  // back-substitution factors (a/b, c/b, 1/b) level by level
+  int n2;
+  const double *crc;
   double *rhs;         // nr x nz scratch
   double *hat;         // nr x nz scratch
   double *hhalf;       // nr x nz: H^{n+1/2}
