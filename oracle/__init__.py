@@ -5,7 +5,7 @@ Plain serial C (``oracle.c``) behind ctypes.  Only ``tests/``,
 legs of ``bench.py`` may import this package; the product path never does.
 It shares no code with ``paper_2212_08836_gb300`` (no headers, constants or
 helpers): both sides are written from the paper (arXiv:2212.08836, Sec. 2.1,
-Eqs. 2-4) and the discretisation readings listed in the design doc.
+Eqs. 2-4) and the same readings of its discretisation.
 
 Every function is pinned by ``tests/test_oracle_*.py`` against closed forms,
 invariants or independent library routines; see the docstrings for which.

@@ -6,7 +6,8 @@
  * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
  * cpu_baseline leg of bench.py may load this library.  It shares no code,
  * header or constant table with the CUDA path; both are written from the
- * paper's equations and the discretisation readings listed in the design doc.
+ * paper's equations and the same readings of its discretisation (uniform
+ * r-z mesh, integral Yee form, linear shapes, lumped gap drive).
  *
  * Plain, serial, slow on purpose.  Compile with -ffp-contract=off so that no
  * multiply-add is fused (the GPU FP64 parity build uses --fmad=false).

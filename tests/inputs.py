@@ -1,7 +1,8 @@
 """Seeded synthetic inputs shared by the oracle pins and the GPU parity tests.
 
 Holds none of the method's arithmetic: only numpy random draws shaped like the
-particle store and the Yee field arrays (layout: see DESIGN.md, "Data layout").
+particle store (cell index, offsets in the cell, velocities, weight, id) and the
+Yee field arrays (E_r on nr x (nz+1) edges, E_z on (nr+1) x nz edges).
 """
 import numpy as np
 
