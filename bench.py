@@ -364,6 +364,34 @@ def run_ours(args):
                                  "peak_tflops": fp32_peak,
                                  "peak_kind": "FP32: 128 lanes x 152 SMs x 2 x max SM clock"}}}
         wall["mixed"] = tm / args.steps * 1e-3 * steps_per_cycle
+    # ---- learned Picard start (mixed form): trained on the discharge's own fields
+    if "guess" in forms:
+        from paper_2212_08836_gb300 import guess as GS
+        cfgg = P.large_reactor(seed=1 + rank, precision=P.PIC_MIXED, capacity_factor=2.5)
+        if args.np:
+            cfgg["np_init"] = args.np
+        pic = P.Pic(cfgg, device=dev)
+        pic.load_particles()
+        pic.step(args.guess_warmup)
+        X, T = GS.collect(pic, args.guess_samples)
+        net = P.Cnn(cfgg["nr"], cfgg["nz"], batch=8, device=dev)
+        t0 = time.perf_counter()
+        loss, val, zero = GS.train(net, X, T, args.guess_epochs)
+        t_train = time.perf_counter() - t0
+        del X, T
+        rs = GS.run_starts(pic, net, args.guess_steps)
+        line["learned_guess"] = {
+            "workload": "mixed form, 256x384 reactor after %d steps (%d samples, %d Adam steps "
+                        "of batch 8, %.0f s)" % (args.guess_warmup, args.guess_samples,
+                                                 args.guess_epochs, t_train),
+            "network": "5 x conv3x3, 14-64-64-64-64-2, BF16 weights/activations, FP32 accumulate, "
+                       "%d parameters" % net.num_params,
+            "heldout_loss": val, "heldout_loss_no_correction": zero,
+            "starts": rs, "tol": cfgg["picard_tol"]}
+        wall["mixed_learned_start"] = rs["cnn"]["ms_per_step"] * 1e-3 * steps_per_cycle
+        wall["mixed_plain_start_same_state"] = rs["plain"]["ms_per_step"] * 1e-3 * steps_per_cycle
+        pic.close()
+        net.close()
     line["wall_s_per_rf_cycle"] = wall
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -389,8 +417,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--np", type=int, default=0, help="macro-particles per species (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--forms", default="plain,mixed",
-                    help="comma list of plain (FP64) and mixed (FP32 push) forms to time")
+    ap.add_argument("--forms", default="plain,mixed,guess",
+                    help="comma list of plain (FP64), mixed (FP32 push) and guess (mixed form "
+                         "with the learned Picard start) to time")
+    ap.add_argument("--guess-warmup", type=int, default=400)
+    ap.add_argument("--guess-samples", type=int, default=600)
+    ap.add_argument("--guess-epochs", type=int, default=1500)
+    ap.add_argument("--guess-steps", type=int, default=100)
     args = ap.parse_args()
     args.steps_e2e = args.steps
     if args.impl == "reference":

@@ -95,6 +95,9 @@ typedef struct pic_step_stats {
   long long pushes;           /* particle pushes performed by the step (all passes) */
   long long launches;         /* kernels launched by the step */
   long long push_flops;       /* algorithmic FP64 operations of the commit pass */
+  int guess;                  /* Picard start used by the last step (PIC_GUESS_* of pic_guess.h) */
+  int guess_pad;
+  double first_res;           /* Picard residual after the first iteration of the last step */
 } pic_step_stats;
 
 /* Device pointers and sizes of the context's arrays (for parity tests,

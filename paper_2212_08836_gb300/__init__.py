@@ -47,13 +47,19 @@ class StepStats(C.Structure):
     _fields_ = [("picard_iters", _I), ("converged", _I), ("last_res", _D), ("src_energy", _D),
                 ("ke_lost", _D), ("de_coll", _D), ("substep_err", _LL), ("absorbed", _LL),
                 ("substeps", _LL), ("fallbacks", _LL), ("mcc", _LL * 8), ("n", _LL * 2),
-                ("pushes", _LL), ("launches", _LL), ("push_flops", _LL)]
+                ("pushes", _LL), ("launches", _LL), ("push_flops", _LL), ("guess", _I),
+                ("guess_pad", _I), ("first_res", _D)]
 
     def as_dict(self):
-        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("mcc", "n")}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("mcc", "n", "guess_pad")}
         d["mcc"] = list(self.mcc)
         d["n"] = list(self.n)
         return d
+
+
+class CnnConfig(C.Structure):
+    _fields_ = [("nr", _I), ("nz", _I), ("width", _I), ("depth", _I), ("batch", _I),
+                ("seed", C.c_ulonglong)]
 
 
 class View(C.Structure):
@@ -93,6 +99,20 @@ def _load_lib():
     L.pic_sort_cells_noalloc.argtypes = [_I, _I, _LL] + [_P] * 16 + [_P, _P]
     L.pic_profile.argtypes = [_P, _I]
     L.pic_profile_read.argtypes = [_P, _P, _P]
+    L.pic_cnn_workspace_size.argtypes = [C.POINTER(CnnConfig)]
+    L.pic_cnn_workspace_size.restype = C.c_size_t
+    L.pic_cnn_init.argtypes = [C.POINTER(CnnConfig), _P, C.c_size_t, _P, C.POINTER(_P)]
+    L.pic_cnn_destroy.argtypes = [_P]
+    L.pic_cnn_destroy.restype = None
+    L.pic_cnn_num_params.argtypes = [_P]
+    L.pic_cnn_num_params.restype = _LL
+    L.pic_cnn_get_params.argtypes = [_P, _P]
+    L.pic_cnn_set_params.argtypes = [_P, _P]
+    L.pic_cnn_forward.argtypes = [_P, _P, _I, _P]
+    L.pic_cnn_loss_grad.argtypes = [_P, _P, _P, _I, _P, _P]
+    L.pic_cnn_train_step.argtypes = [_P, _P, _P, _I, C.c_float, _P]
+    L.pic_set_guess.argtypes = [_P, _I, _P]
+    L.pic_guess_sample.argtypes = [_P, _P, _P, C.POINTER(_I)]
     return L
 
 
@@ -104,6 +124,10 @@ def lib():
     if _lib is None:
         _lib = _load_lib()
     return _lib
+
+
+PIC_GUESS_PLAIN, PIC_GUESS_EXTRAP, PIC_GUESS_CNN = 0, 1, 2
+CNN_IN, CNN_OUT = 14, 2
 
 
 class PicError(RuntimeError):
@@ -317,3 +341,98 @@ class Pic:
 def drive_voltage(cfg, step):
     t = step * cfg["dt"]
     return cfg["volt"] * math.sin(6.283185307179586 * cfg["freq"] * t)
+
+
+class Cnn:
+    """The learned Picard start (include/pic_guess.h): a stack of 3x3
+    convolutions on the (nr+1) x (nz+1) grid, BF16 tensor-core kernels with
+    FP32 accumulation.  Owns a torch uint8 workspace on ``device``."""
+
+    def __init__(self, nr, nz, depth=5, width=64, batch=8, seed=0, device="cuda:0", stream=None):
+        import torch
+
+        self.torch = torch
+        self.device = torch.device(device)
+        self.nr, self.nz, self.depth, self.width, self.batch = nr, nz, depth, width, batch
+        self._c = CnnConfig(nr=nr, nz=nz, width=width, depth=depth, batch=batch, seed=seed)
+        nb = lib().pic_cnn_workspace_size(C.byref(self._c))
+        if nb == 0:
+            raise PicError(PIC_E_CONFIG, "pic_cnn_workspace_size")
+        self.ws = torch.empty(int(nb), dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = _P()
+        _check(lib().pic_cnn_init(C.byref(self._c), self.ws.data_ptr(), int(nb),
+                                  self.stream.cuda_stream, C.byref(h)), "pic_cnn_init")
+        self._h = h
+        self.num_params = int(lib().pic_cnn_num_params(h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pic_cnn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def shape(self):
+        return (self.nr + 1, self.nz + 1)
+
+    def get_params(self):
+        import numpy as np
+        out = np.empty(self.num_params, dtype=np.float32)
+        _check(lib().pic_cnn_get_params(self._h, out.ctypes.data), "pic_cnn_get_params")
+        return out
+
+    def set_params(self, v):
+        import numpy as np
+        v = np.ascontiguousarray(v, dtype=np.float32)
+        assert v.size == self.num_params
+        _check(lib().pic_cnn_set_params(self._h, v.ctypes.data), "pic_cnn_set_params")
+
+    def forward(self, x):
+        """x: float32 device tensor [B, 14, nr+1, nz+1] -> [B, 2, nr+1, nz+1]."""
+        x = x.contiguous()
+        y = self.torch.empty((x.shape[0], CNN_OUT) + self.shape, dtype=self.torch.float32,
+                             device=self.device)
+        _check(lib().pic_cnn_forward(self._h, x.data_ptr(), int(x.shape[0]), y.data_ptr()),
+               "pic_cnn_forward")
+        return y
+
+    def loss_grad(self, x, t, grad=True):
+        import numpy as np
+        x, t = x.contiguous(), t.contiguous()
+        loss = C.c_double(0.0)
+        g = np.empty(self.num_params, dtype=np.float32) if grad else None
+        _check(lib().pic_cnn_loss_grad(self._h, x.data_ptr(), t.data_ptr(), int(x.shape[0]),
+                                       C.byref(loss), g.ctypes.data if grad else None),
+               "pic_cnn_loss_grad")
+        return loss.value, g
+
+    def train_step(self, x, t, lr):
+        x, t = x.contiguous(), t.contiguous()
+        loss = C.c_double(0.0)
+        _check(lib().pic_cnn_train_step(self._h, x.data_ptr(), t.data_ptr(), int(x.shape[0]),
+                                        float(lr), C.byref(loss)), "pic_cnn_train_step")
+        return loss.value
+
+
+def set_guess(pic, mode, cnn=None):
+    """Picard start of the following steps of ``pic`` (PIC_GUESS_*)."""
+    _check(lib().pic_set_guess(pic._h, int(mode), cnn._h if cnn is not None else None),
+           "pic_set_guess")
+
+
+def guess_sample(pic):
+    """(inputs [14, nr+1, nz+1], target [2, nr+1, nz+1]) of the last step, or None."""
+    import torch
+    H, W = pic.nr + 1, pic.nz + 1
+    x = torch.empty((CNN_IN, H, W), dtype=torch.float32, device=pic.device)
+    t = torch.empty((CNN_OUT, H, W), dtype=torch.float32, device=pic.device)
+    valid = _I(0)
+    _check(lib().pic_guess_sample(pic._h, x.data_ptr(), t.data_ptr(), C.byref(valid)),
+           "pic_guess_sample")
+    return (x, t) if valid.value else None

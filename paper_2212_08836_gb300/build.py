@@ -28,6 +28,8 @@ UNITS = {
     "pic_api.cu": ["--fmad=false"],
     "sort_noalloc.cu": [],
     "push_fp32.cu": ["--use_fast_math"],
+    "cnn.cu": [],
+    "guess.cu": ["--fmad=false"],
 }
 
 

@@ -8,9 +8,17 @@
 
 #include <vector>
 
+#include "../../include/pic_guess.h"
 #include "pic_internal.cuh"
 
 using namespace pic;
+
+namespace pic {
+int cnn_forward_async(pic_cnn *x, const float *xin, const float **y_posmajor, int *cp);
+int cnn_grid(const pic_cnn *x, int *nr, int *nz);
+cudaStream_t cnn_stream(const pic_cnn *x);
+int cnn_layers(const pic_cnn *x);
+}  // namespace pic
 
 struct pic_ctx {
   pic_config cfg;
@@ -53,6 +61,21 @@ struct pic_ctx {
   cudaEvent_t ev[2 * 128];
   double push_ms;
   long long push_launches, pending_launches;
+  // Picard start (pic_guess.h): field history E^{n-1..n-3} (rotated pointers),
+  // last crossed charge, extrapolation G, inputs / target of the learned guess
+  int guess_mode;
+  pic_cnn *cnn;
+  int hist_n;               // field levels known, E^n included (at most 4)
+  double *hr[3], *hz[3];
+  double *jr, *jz;
+  double *ger, *gez;
+  double *gsums, *gsd;      // 4 sums, s_d
+  int *gbad;
+  float *gx, *gt;           // inputs of the current / last step and its target
+  int sample_valid, feat_now;
+  cudaStream_t gstream;     // stream of the network
+  cudaEvent_t gev[2];
+  int gev_made, cnn_layers;
 };
 
 namespace {
@@ -165,6 +188,22 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
   x->F.pw = (const double2 *)K.take((size_t)nz * 16);
   x->F.rtab = (const double *)K.take((size_t)6 * (nr + 1) * 8);
   x->cnt = (DevCounters *)K.take(sizeof(DevCounters));
+  for (int k = 0; k < 3; ++k) {
+    x->hr[k] = (double *)K.take(ner * 8);
+    x->hz[k] = (double *)K.take(nez * 8);
+  }
+  x->jr = (double *)K.take(ner * 8);
+  x->jz = (double *)K.take(nez * 8);
+  x->ger = (double *)K.take(ner * 8);
+  x->gez = (double *)K.take(nez * 8);
+  x->gsums = (double *)K.take(8 * 8);
+  x->gsd = x->gsums + 4;
+  x->gbad = (int *)K.take(256);
+  {
+    size_t P = (size_t)(nr + 1) * (nz + 1);
+    x->gx = (float *)K.take(P * PIC_CNN_IN * 4);
+    x->gt = (float *)K.take(P * PIC_CNN_OUT * 4);
+  }
   x->cand = (uint32_t *)K.take((2 * (size_t)pc + 2 * (size_t)kMaxFastBlocks * 256) * 4);
   x->cblock = (int *)K.take((size_t)kMaxFastBlocks * 4);
   x->keys = (uint64_t *)K.take(pc * 8);
@@ -542,6 +581,11 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
 
 void pic_destroy(pic_ctx *ctx) {
   if (!ctx) return;
+  if (ctx->gev_made) {
+    cudaStreamSynchronize(ctx->s);
+    cudaEventDestroy(ctx->gev[0]);
+    cudaEventDestroy(ctx->gev[1]);
+  }
   if (ctx->prof) {
     cudaStreamSynchronize(ctx->s);
     for (int k = 0; k < 2 * 128; ++k) cudaEventDestroy(ctx->ev[k]);
@@ -622,6 +666,8 @@ int pic_load_particles(pic_ctx *x) {
   if (n > 0) x->launches += 1;
   x->n[0] = x->n[1] = n;
   x->next_id[0] = x->next_id[1] = (uint32_t)n;
+  x->hist_n = 1;
+  x->sample_valid = 0;
   return pic_sort(x);
 }
 
@@ -719,6 +765,123 @@ int pic_mcc(pic_ctx *x, unsigned long long step, long long *counts, double *de_c
   return rc;
 }
 
+namespace {
+
+GuessArgs guess_args(pic_ctx *x) {
+  GuessArgs A;
+  A.nr = x->g.nr;
+  A.nz = x->g.nz;
+  A.e[0] = FieldPair{x->er, x->ez};
+  for (int k = 0; k < 3; ++k) A.e[k + 1] = FieldPair{x->hr[k], x->hz[k]};
+  A.h = x->h;
+  A.jr = x->jr;
+  A.jz = x->jz;
+  A.sums = x->gsums;
+  A.sd = x->gsd;
+  A.ger = x->ger;
+  A.gez = x->gez;
+  A.x = x->gx;
+  return A;
+}
+
+// plain start E^{n+1,0} = E^n with the drive value on r = R
+int plain_start(pic_ctx *x, double v1) {
+  const int nr = x->g.nr, nz = x->g.nz;
+  const size_t ner = (size_t)nr * (nz + 1), nez = (size_t)(nr + 1) * nz;
+  cudaError_t e = cudaMemcpyAsync(x->er1, x->er, ner * 8, cudaMemcpyDeviceToDevice, x->s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(x->ez1, x->ez, nez * 8, cudaMemcpyDeviceToDevice, x->s);
+  if (e == cudaSuccess) {
+    k_fill<<<(nz + 127) / 128, 128, 0, x->s>>>(x->ez1 + (size_t)nr * nz, nz, v1 / x->cfg.L);
+    e = cudaGetLastError();
+    x->launches += 1;
+  }
+  return e == cudaSuccess ? PIC_OK : PIC_E_CUDA;
+}
+
+// extrapolated or learned start; *used = the start placed in er1/ez1
+// (PIC_GUESS_PLAIN: nothing was placed, the caller falls back)
+int guess_start(pic_ctx *x, double v1, int *used) {
+  *used = PIC_GUESS_PLAIN;
+  GuessArgs A = guess_args(x);
+  if (launch_guess_inputs(A, x->s) != cudaSuccess) return PIC_E_CUDA;
+  x->launches += 2;
+  x->feat_now = 1;
+  const float *y = nullptr;
+  int cp = 0;
+  if (x->guess_mode == PIC_GUESS_CNN) {
+    // the network runs on its own stream, ordered after the inputs and before the start
+    if (cudaEventRecord(x->gev[0], x->s) != cudaSuccess) return PIC_E_CUDA;
+    if (cudaStreamWaitEvent(x->gstream, x->gev[0], 0) != cudaSuccess) return PIC_E_CUDA;
+    if (cnn_forward_async(x->cnn, x->gx, &y, &cp)) return PIC_E_CUDA;
+    if (cudaEventRecord(x->gev[1], x->gstream) != cudaSuccess) return PIC_E_CUDA;
+    if (cudaStreamWaitEvent(x->s, x->gev[1], 0) != cudaSuccess) return PIC_E_CUDA;
+    x->launches += 2 + 2 * x->cnn_layers;
+  }
+  int bad = 0;
+  if (cudaMemsetAsync(x->gbad, 0, sizeof(int), x->s) != cudaSuccess) return PIC_E_CUDA;
+  if (launch_guess_apply(A, y, cp, v1 / x->cfg.L, x->er1, x->ez1, x->gbad, x->s) != cudaSuccess)
+    return PIC_E_CUDA;
+  x->launches += 1;
+  if (cudaMemcpyAsync(&bad, x->gbad, sizeof(int), cudaMemcpyDeviceToHost, x->s) != cudaSuccess)
+    return PIC_E_CUDA;
+  if (cudaStreamSynchronize(x->s) != cudaSuccess) return PIC_E_CUDA;
+  if (!bad) *used = x->guess_mode;
+  return PIC_OK;
+}
+
+// the nonlinear iteration of Sec. 2.1 from the start in er1/ez1: push + deposit
+// with E^{n+1/2,k}, implicit field solve, relative-change test
+int picard(pic_ctx *x, double v0, double v1, pic_step_stats &S, bool &conv, int &k, double &res,
+           double &src, double &first) {
+  const int nr = x->g.nr, nz = x->g.nz;
+  const size_t ner = (size_t)nr * (nz + 1), nez = (size_t)(nr + 1) * nz;
+  cudaStream_t s = x->s;
+  conv = false;
+  res = 0.0;
+  src = 0.0;
+  first = 0.0;
+  for (k = 0; k < x->cfg.picard_max; ++k) {
+    cudaError_t he =
+        x->mixed ? launch_half_field_alpha(x->g, x->er, x->ez, x->er1, x->ez1, x->erh, x->ezh,
+                                           x->alpha, s)
+                 : launch_half_field_alpha64(x->g, x->er, x->ez, x->er1, x->ez1, x->erh, x->ezh,
+                                             x->alpha64, s);
+    if (he != cudaSuccess) return PIC_E_CUDA;
+    x->launches += 1;
+    if (cudaMemsetAsync(x->ir, 0, ner * 8, s) != cudaSuccess) return PIC_E_CUDA;
+    if (cudaMemsetAsync(x->iz, 0, nez * 8, s) != cudaSuccess) return PIC_E_CUDA;
+    int r = push_all(x, x->erh, x->ezh, x->ir, x->iz, 0, nullptr, nullptr, nullptr);
+    if (r) return r;
+    S.pushes += x->n[0] + x->n[1];
+    if (launch_field_solve(x->F, x->er, x->ez, x->h, x->ir, x->iz, v0, v1, x->er2, x->ez2, x->h2,
+                           x->er1, x->ez1, x->cnt, s) != cudaSuccess)
+      return PIC_E_CUDA;
+    x->launches += 5;
+    double hn[3];
+    if (cudaMemcpyAsync(hn, x->cnt->norm, 3 * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return PIC_E_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return PIC_E_CUDA;
+    if (x->prof) prof_collect(x);
+    res = sqrt(hn[0]) / fmax(sqrt(hn[1]), 1e-30);
+    if (k == 0) first = res;
+    src = hn[2];
+    double *t;
+    t = x->er1; x->er1 = x->er2; x->er2 = t;
+    t = x->ez1; x->ez1 = x->ez2; x->ez2 = t;
+    if (!isfinite(res)) {
+      S.picard_iters = k + 1;
+      return PIC_E_NAN;
+    }
+    if (res < x->cfg.picard_tol) {
+      conv = true;
+      break;
+    }
+  }
+  return PIC_OK;
+}
+
+}  // namespace
+
 int pic_step(pic_ctx *x, int nsteps, pic_step_stats *st) {
   if (!x || nsteps < 0) return PIC_E_CONFIG;
   int nr = x->g.nr, nz = x->g.nz;
@@ -730,53 +893,31 @@ int pic_step(pic_ctx *x, int nsteps, pic_step_stats *st) {
     long long l0 = x->launches;
     double v0 = volt_at(x, x->step), v1 = volt_at(x, x->step + 1);
     cudaStream_t s = x->s;
-    cudaError_t e = cudaMemcpyAsync(x->er1, x->er, ner * 8, cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(x->ez1, x->ez, nez * 8, cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess) {
-      k_fill<<<(nz + 127) / 128, 128, 0, s>>>(x->ez1 + (size_t)nr * nz, nz, v1 / x->cfg.L);
-      e = cudaGetLastError();
-      x->launches += 1;
+    int used = PIC_GUESS_PLAIN;
+    x->feat_now = 0;
+    if (x->guess_mode != PIC_GUESS_PLAIN && x->hist_n >= 4) {
+      int gr = guess_start(x, v1, &used);
+      if (gr) return gr;
     }
-    if (e != cudaSuccess) return PIC_E_CUDA;
+    if (used == PIC_GUESS_PLAIN) {
+      int pr = plain_start(x, v1);
+      if (pr) return pr;
+    }
     bool conv = false;
-    double res = 0.0, src = 0.0;
-    int k;
-    for (k = 0; k < x->cfg.picard_max; ++k) {
-      cudaError_t he =
-          x->mixed ? launch_half_field_alpha(x->g, x->er, x->ez, x->er1, x->ez1, x->erh, x->ezh,
-                                             x->alpha, s)
-                   : launch_half_field_alpha64(x->g, x->er, x->ez, x->er1, x->ez1, x->erh,
-                                               x->ezh, x->alpha64, s);
-      if (he != cudaSuccess) return PIC_E_CUDA;
-      x->launches += 1;
-      if (cudaMemsetAsync(x->ir, 0, ner * 8, s) != cudaSuccess) return PIC_E_CUDA;
-      if (cudaMemsetAsync(x->iz, 0, nez * 8, s) != cudaSuccess) return PIC_E_CUDA;
-      int r = push_all(x, x->erh, x->ezh, x->ir, x->iz, 0, nullptr, nullptr, nullptr);
-      if (r) return r;
-      S.pushes += x->n[0] + x->n[1];
-      if (launch_field_solve(x->F, x->er, x->ez, x->h, x->ir, x->iz, v0, v1, x->er2, x->ez2, x->h2,
-                             x->er1, x->ez1, x->cnt, s) != cudaSuccess)
-        return PIC_E_CUDA;
-      x->launches += 5;
-      double hn[3];
-      if (cudaMemcpyAsync(hn, x->cnt->norm, 3 * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-        return PIC_E_CUDA;
-      if (cudaStreamSynchronize(s) != cudaSuccess) return PIC_E_CUDA;
-      if (x->prof) prof_collect(x);
-      res = sqrt(hn[0]) / fmax(sqrt(hn[1]), 1e-30);
-      src = hn[2];
-      double *t;
-      t = x->er1; x->er1 = x->er2; x->er2 = t;
-      t = x->ez1; x->ez1 = x->ez2; x->ez2 = t;
-      if (!isfinite(res)) {
-        S.picard_iters = k + 1;
-        if (st) *st = S;
-        return PIC_E_NAN;
-      }
-      if (res < x->cfg.picard_tol) {
-        conv = true;
-        break;
-      }
+    double res = 0.0, src = 0.0, first = 0.0;
+    int k = 0;
+    int pr = picard(x, v0, v1, S, conv, k, res, src, first);
+    if (!conv && used != PIC_GUESS_PLAIN && (pr == PIC_OK || pr == PIC_E_NAN)) {
+      // the plain start remains the fallback: redo the iteration from E^n
+      used = PIC_GUESS_PLAIN;
+      pr = plain_start(x, v1);
+      if (!pr) pr = picard(x, v0, v1, S, conv, k, res, src, first);
+    }
+    S.guess = used;
+    S.first_res = first;
+    if (pr) {
+      if (st) *st = S;
+      return pr;
     }
     S.picard_iters = conv ? k + 1 : k;
     S.last_res = res;
@@ -799,6 +940,22 @@ int pic_step(pic_ctx *x, int nsteps, pic_step_stats *st) {
     t = x->er; x->er = x->er1; x->er1 = t;
     t = x->ez; x->ez = x->ez1; x->ez1 = t;
     t = x->h; x->h = x->h2; x->h2 = t;
+    if (x->guess_mode != PIC_GUESS_PLAIN) {
+      // training target of this step, then E^n joins the history (its buffer
+      // is now er1/ez1) and the committed crossed charge is kept
+      if (x->feat_now) {
+        GuessArgs A = guess_args(x);
+        if (launch_guess_target(A, x->er, x->ez, x->gt, s) != cudaSuccess) return PIC_E_CUDA;
+        x->launches += 1;
+        x->sample_valid = 1;
+      }
+      t = x->hr[2]; x->hr[2] = x->hr[1]; x->hr[1] = x->hr[0]; x->hr[0] = x->er1; x->er1 = t;
+      t = x->hz[2]; x->hz[2] = x->hz[1]; x->hz[1] = x->hz[0]; x->hz[0] = x->ez1; x->ez1 = t;
+      if (cudaMemcpyAsync(x->jr, x->ir, ner * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+          cudaMemcpyAsync(x->jz, x->iz, nez * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return PIC_E_CUDA;
+      if (x->hist_n < 4) x->hist_n += 1;
+    }
     S.src_energy = src;
     if (x->cfg.mcc_on) {
       int mr = pic_mcc(x, (unsigned long long)x->step, S.mcc, &S.de_coll);
@@ -917,3 +1074,43 @@ int pic_mcc_constants(pic_ctx *x, double *numax_e, double *gmax, double *pnull_e
 }
 
 }  // extern "C"
+
+int pic_set_guess(pic_ctx *x, int mode, pic_cnn *cnn) {
+  if (!x || mode < PIC_GUESS_PLAIN || mode > PIC_GUESS_CNN) return PIC_E_CONFIG;
+  if (mode == PIC_GUESS_CNN) {
+    int nr = 0, nz = 0;
+    if (!cnn || cnn_grid(cnn, &nr, &nz) || nr != x->g.nr || nz != x->g.nz) return PIC_E_CONFIG;
+    if (!x->gev_made) {
+      if (cudaEventCreateWithFlags(&x->gev[0], cudaEventDisableTiming) != cudaSuccess)
+        return PIC_E_CUDA;
+      if (cudaEventCreateWithFlags(&x->gev[1], cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventDestroy(x->gev[0]);
+        return PIC_E_CUDA;
+      }
+      x->gev_made = 1;
+    }
+    x->gstream = cnn_stream(cnn);
+    x->cnn_layers = cnn_layers(cnn);
+  }
+  if (x->guess_mode == PIC_GUESS_PLAIN && mode != PIC_GUESS_PLAIN) {
+    // the history restarts from the current field
+    x->hist_n = 1;
+    x->sample_valid = 0;
+  }
+  x->guess_mode = mode;
+  x->cnn = mode == PIC_GUESS_CNN ? cnn : nullptr;
+  return PIC_OK;
+}
+
+int pic_guess_sample(pic_ctx *x, float *x_dev, float *t_dev, int *valid) {
+  if (!x || !valid) return PIC_E_CONFIG;
+  *valid = x->sample_valid;
+  if (!x->sample_valid) return PIC_OK;
+  const size_t P = (size_t)(x->g.nr + 1) * (x->g.nz + 1);
+  cudaError_t e = cudaSuccess;
+  if (x_dev) e = cudaMemcpyAsync(x_dev, x->gx, P * PIC_CNN_IN * 4, cudaMemcpyDeviceToDevice, x->s);
+  if (e == cudaSuccess && t_dev)
+    e = cudaMemcpyAsync(t_dev, x->gt, P * PIC_CNN_OUT * 4, cudaMemcpyDeviceToDevice, x->s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(x->s);
+  return e == cudaSuccess ? PIC_OK : PIC_E_CUDA;
+}

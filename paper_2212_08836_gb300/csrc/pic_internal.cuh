@@ -144,6 +144,26 @@ struct PushLaunchT {
                            // its start state is re-read from the store, which the
                            // fast kernel leaves untouched for queued particles
 };
+// Picard start of a step (guess.cu)
+struct FieldPair {
+  const double *r, *z;  // E_r (nr x (nz+1)), E_z ((nr+1) x nz)
+};
+struct GuessArgs {
+  int nr, nz;
+  FieldPair e[4];       // E^n, E^{n-1}, E^{n-2}, E^{n-3}
+  const double *h;      // H^n
+  const double *jr, *jz;  // charge crossed in the last step
+  double *sums;         // scratch: 4 sums of squares
+  double *sd;           // s_d (device scalar)
+  double *ger, *gez;    // G = 3E^n - 3E^{n-1} + E^{n-2}
+  float *x;             // inputs [14][nr+1][nz+1]
+};
+cudaError_t launch_guess_inputs(const GuessArgs &A, cudaStream_t s);
+cudaError_t launch_guess_apply(const GuessArgs &A, const float *y, int cp, double ez_edge,
+                               double *er1, double *ez1, int *bad, cudaStream_t s);
+cudaError_t launch_guess_target(const GuessArgs &A, const double *er_next, const double *ez_next,
+                                float *tg, cudaStream_t s);
+
 // most blocks of 256 threads resident on a GB300 (152 SMs x 8); the queue
 // holds up to capacity + kMaxFastBlocks*256 entries
 constexpr int kMaxFastBlocks = 152 * 8;
