@@ -190,13 +190,17 @@ def measure(P, torch, dev, cfg, args, dist, D, do_e2e, sample_clocks, local):
     for _ in range(args.steps):
         _, st = pic.step(1)
         k = st["picard_iters"]
-        n_commit = st["pushes"] // (k + 1)
+        # passes: k Picard passes, plus the commit push unless the converged
+        # pass already wrote the state (out of place: every field)
+        n_commit = st["pushes"] // (k + (0 if st["spec_final"] else 1))
         r["pushes"] += st["pushes"]
         r["launches"] += st["launches"]
         r["iters"].append(k)
         r["flops"] += st["push_flops"]
         r["commit_pushes"] += n_commit
         rb, wb = (28, 24) if cfg["precision"] == P.PIC_MIXED else (52, 48)
+        if st["spec_final"]:
+            wb += 8  # cell and id (4 B each) written too
         r["bytes"] += st["pushes"] * rb + n_commit * wb
     ev1.record(stream)
     barrier()

@@ -96,7 +96,7 @@ typedef struct pic_step_stats {
   long long launches;         /* kernels launched by the step */
   long long push_flops;       /* algorithmic FP64 operations of the commit pass */
   int guess;                  /* Picard start used by the last step (PIC_GUESS_* of pic_guess.h) */
-  int guess_pad;
+  int spec_final;             /* 1: the converged pass wrote the new state (no separate commit push) */
   double first_res;           /* Picard residual after the first iteration of the last step */
 } pic_step_stats;
 

@@ -48,10 +48,10 @@ class StepStats(C.Structure):
                 ("ke_lost", _D), ("de_coll", _D), ("substep_err", _LL), ("absorbed", _LL),
                 ("substeps", _LL), ("fallbacks", _LL), ("mcc", _LL * 8), ("n", _LL * 2),
                 ("pushes", _LL), ("launches", _LL), ("push_flops", _LL), ("guess", _I),
-                ("guess_pad", _I), ("first_res", _D)]
+                ("spec_final", _I), ("first_res", _D)]
 
     def as_dict(self):
-        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("mcc", "n", "guess_pad")}
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("mcc", "n")}
         d["mcc"] = list(self.mcc)
         d["n"] = list(self.n)
         return d

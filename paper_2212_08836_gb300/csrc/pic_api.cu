@@ -44,6 +44,8 @@ struct pic_ctx {
   double *erh, *ezh;        // E^{n+1/2,k}
   double *ir, *iz;          // crossed charge of the pass
   double *wall;             // 2 species x (2(nr+1) + nz+1)
+  double *wall_spec;        // wall tallies of a speculative final pass
+  double rho_prev;          // last Picard contraction r_k / r_{k-1} observed
   FieldOp F;
   DevCounters *cnt;
   uint32_t *cand;           // MCC: null-collision candidates (per-block segments)
@@ -175,6 +177,7 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
   x->ir = (double *)K.take(ner * 8);
   x->iz = (double *)K.take(nez * 8);
   x->wall = (double *)K.take((size_t)2 * (2 * (nr + 1) + nz + 1) * 8);
+  x->wall_spec = (double *)K.take((size_t)2 * (2 * (nr + 1) + nz + 1) * 8);
   x->F.Q = (double *)K.take((size_t)nz * nz * 8);
   x->F.QT = (double *)K.take((size_t)nz * nz * 8);
   int n2 = 1;
@@ -288,8 +291,10 @@ void set_queue(pic_ctx *x, T *const rec[2], PushLaunchT<T> &L) {
   L.q_db = rec[1];
 }
 
+// oop: write the new state into the second buffer of the store (speculative
+// final pass), every field; else (write) in place
 int push_all(pic_ctx *x, const double *erh, const double *ezh, double *ir, double *iz, int write,
-             unsigned long long *counters, double *kel, double *wall) {
+             unsigned long long *counters, double *kel, double *wall, int oop = 0) {
   bool timed = x->prof && x->nev < 128;
   if (timed) cudaEventRecord(x->ev[2 * x->nev], x->s);
   for (int s = 0; s < 2; ++s) {
@@ -309,6 +314,8 @@ int push_all(pic_ctx *x, const double *erh, const double *ezh, double *ir, doubl
       PushLaunchT<float> L;
       fill_push(x, s, q, m, erh, ezh, ir, iz, write, counters, kel, ws, L);
       L.p = as32(cur(x, s));
+      L.dst = oop ? as32(x->P[s][x->cur[s] ^ 1]) : L.p;
+      L.oop = oop;
       L.ar = x->alpha.ar[s];
       L.az = x->alpha.az[s];
       set_queue(x, x->q_real, L);
@@ -318,6 +325,8 @@ int push_all(pic_ctx *x, const double *erh, const double *ezh, double *ir, doubl
       PushLaunchT<double> L;
       fill_push(x, s, q, m, erh, ezh, ir, iz, write, counters, kel, ws, L);
       L.p = cur(x, s);
+      L.dst = oop ? x->P[s][x->cur[s] ^ 1] : L.p;
+      L.oop = oop;
       L.ar = x->alpha64.ar[s];
       L.az = x->alpha64.az[s];
       set_queue(x, x->q_real64, L);
@@ -831,15 +840,26 @@ int guess_start(pic_ctx *x, double v1, int *used) {
 
 // the nonlinear iteration of Sec. 2.1 from the start in er1/ez1: push + deposit
 // with E^{n+1/2,k}, implicit field solve, relative-change test
+//
+// Speculative final pass: the commit push of a converged step repeats the last
+// pass with the same E^{n+1/2}, so when the contraction of the last two
+// residuals predicts that the next pass converges, that pass already writes
+// the new particle state into the second buffer of the store (every field;
+// wall tallies into scratch).  If it converges the buffers are swapped and
+// the commit push is skipped (*spec = 1); if not, the iteration goes on.
 int picard(pic_ctx *x, double v0, double v1, pic_step_stats &S, bool &conv, int &k, double &res,
-           double &src, double &first) {
+           double &src, double &first, int &spec_ok) {
   const int nr = x->g.nr, nz = x->g.nz;
   const size_t ner = (size_t)nr * (nz + 1), nez = (size_t)(nr + 1) * nz;
+  const size_t nwall = (size_t)2 * (2 * (nr + 1) + nz + 1);
   cudaStream_t s = x->s;
   conv = false;
   res = 0.0;
   src = 0.0;
   first = 0.0;
+  spec_ok = 0;
+  bool spec = false;
+  double rprev = 0.0;
   for (k = 0; k < x->cfg.picard_max; ++k) {
     cudaError_t he =
         x->mixed ? launch_half_field_alpha(x->g, x->er, x->ez, x->er1, x->ez1, x->erh, x->ezh,
@@ -850,7 +870,17 @@ int picard(pic_ctx *x, double v0, double v1, pic_step_stats &S, bool &conv, int 
     x->launches += 1;
     if (cudaMemsetAsync(x->ir, 0, ner * 8, s) != cudaSuccess) return PIC_E_CUDA;
     if (cudaMemsetAsync(x->iz, 0, nez * 8, s) != cudaSuccess) return PIC_E_CUDA;
-    int r = push_all(x, x->erh, x->ezh, x->ir, x->iz, 0, nullptr, nullptr, nullptr);
+    int r;
+    if (spec) {
+      if (cudaMemsetAsync(x->cnt->push, 0, sizeof(x->cnt->push), s) != cudaSuccess ||
+          cudaMemsetAsync(&x->cnt->ke_lost, 0, 8, s) != cudaSuccess ||
+          cudaMemsetAsync(x->wall_spec, 0, nwall * 8, s) != cudaSuccess)
+        return PIC_E_CUDA;
+      r = push_all(x, x->erh, x->ezh, x->ir, x->iz, 1, x->cnt->push, &x->cnt->ke_lost,
+                   x->wall_spec, 1);
+    } else {
+      r = push_all(x, x->erh, x->ezh, x->ir, x->iz, 0, nullptr, nullptr, nullptr);
+    }
     if (r) return r;
     S.pushes += x->n[0] + x->n[1];
     if (launch_field_solve(x->F, x->er, x->ez, x->h, x->ir, x->iz, v0, v1, x->er2, x->ez2, x->h2,
@@ -872,12 +902,23 @@ int picard(pic_ctx *x, double v0, double v1, pic_step_stats &S, bool &conv, int 
       S.picard_iters = k + 1;
       return PIC_E_NAN;
     }
+    if (k > 0 && rprev > 0.0) x->rho_prev = res / rprev;
     if (res < x->cfg.picard_tol) {
       conv = true;
+      spec_ok = spec ? 1 : 0;
       break;
     }
+    // next residual predicted from the contraction (the previous step's for k = 0)
+    const double rho = k > 0 ? res / rprev : x->rho_prev;
+    spec = rho > 0.0 && rho < 1.0 && res * rho < x->cfg.picard_tol;
+    rprev = res;
   }
   return PIC_OK;
+}
+
+__global__ void k_addto(double *dst, const double *src, int n) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) dst[t] += src[t];
 }
 
 }  // namespace
@@ -905,16 +946,17 @@ int pic_step(pic_ctx *x, int nsteps, pic_step_stats *st) {
     }
     bool conv = false;
     double res = 0.0, src = 0.0, first = 0.0;
-    int k = 0;
-    int pr = picard(x, v0, v1, S, conv, k, res, src, first);
+    int k = 0, spec = 0;
+    int pr = picard(x, v0, v1, S, conv, k, res, src, first, spec);
     if (!conv && used != PIC_GUESS_PLAIN && (pr == PIC_OK || pr == PIC_E_NAN)) {
       // the plain start remains the fallback: redo the iteration from E^n
       used = PIC_GUESS_PLAIN;
       pr = plain_start(x, v1);
-      if (!pr) pr = picard(x, v0, v1, S, conv, k, res, src, first);
+      if (!pr) pr = picard(x, v0, v1, S, conv, k, res, src, first, spec);
     }
     S.guess = used;
     S.first_res = first;
+    S.spec_final = spec;
     if (pr) {
       if (st) *st = S;
       return pr;
@@ -928,14 +970,25 @@ int pic_step(pic_ctx *x, int nsteps, pic_step_stats *st) {
       if (st) *st = S;
       return PIC_E_NOCONV;
     }
-    // commit: the half field of the last iteration fed the last solve
-    if (cudaMemsetAsync(x->ir, 0, ner * 8, s) != cudaSuccess) return PIC_E_CUDA;
-    if (cudaMemsetAsync(x->iz, 0, nez * 8, s) != cudaSuccess) return PIC_E_CUDA;
-    if (cudaMemsetAsync(x->cnt->push, 0, sizeof(x->cnt->push), s) != cudaSuccess) return PIC_E_CUDA;
-    if (cudaMemsetAsync(&x->cnt->ke_lost, 0, 8, s) != cudaSuccess) return PIC_E_CUDA;
-    int r = push_all(x, x->erh, x->ezh, x->ir, x->iz, 1, x->cnt->push, &x->cnt->ke_lost, x->wall);
-    if (r) return r;
-    S.pushes += x->n[0] + x->n[1];
+    if (spec) {
+      // the converged pass already wrote the new state into the second buffer
+      x->cur[0] ^= 1;
+      x->cur[1] ^= 1;
+      const int nwall = 2 * (2 * (nr + 1) + nz + 1);
+      k_addto<<<(nwall + 255) / 256, 256, 0, s>>>(x->wall, x->wall_spec, nwall);
+      if (cudaGetLastError() != cudaSuccess) return PIC_E_CUDA;
+      x->launches += 1;
+    } else {
+      // commit: the half field of the last iteration fed the last solve
+      if (cudaMemsetAsync(x->ir, 0, ner * 8, s) != cudaSuccess) return PIC_E_CUDA;
+      if (cudaMemsetAsync(x->iz, 0, nez * 8, s) != cudaSuccess) return PIC_E_CUDA;
+      if (cudaMemsetAsync(x->cnt->push, 0, sizeof(x->cnt->push), s) != cudaSuccess)
+        return PIC_E_CUDA;
+      if (cudaMemsetAsync(&x->cnt->ke_lost, 0, 8, s) != cudaSuccess) return PIC_E_CUDA;
+      int r = push_all(x, x->erh, x->ezh, x->ir, x->iz, 1, x->cnt->push, &x->cnt->ke_lost, x->wall);
+      if (r) return r;
+      S.pushes += x->n[0] + x->n[1];
+    }
     double *t;
     t = x->er; x->er = x->er1; x->er1 = t;
     t = x->ez; x->ez = x->ez1; x->ez1 = t;

@@ -131,7 +131,9 @@ struct PushLaunchT {
   PartsT<T> p;
   const T *ar, *az;        // normalised accelerations qm*E*dt^2/dx of this species
   double *ir, *iz;         // crossed charge [C] (FP64, atomics)
-  int write;               // commit pass: write the new state
+  int write;               // write the new state (commit or speculative pass)
+  int oop;                 // out of place: write every field into dst (in place: p)
+  PartsT<T> dst;
   double *wall_z0, *wall_zl, *wall_r;
   unsigned long long *counters;
   double *ke_lost;

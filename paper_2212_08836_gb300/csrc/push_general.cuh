@@ -355,8 +355,8 @@ struct GenArgs {
   double q, m;
   T qf;                  // q in T
   double *ir, *iz;       // crossed charge [C]
-  int write;
-  PartsT<T> p;
+  int write, oop;        // write the new state; out of place into dst
+  PartsT<T> p, dst;
   double *wall_z0, *wall_zl, *wall_r;
   double *ke_lost;
 };
@@ -371,7 +371,10 @@ __device__ void push_general(const GenArgs<T> &L, long long p, int c0, T a, T b,
   const T zero = (T)0, one = (T)1, h = (T)0.5, two = (T)2;
   const int nr = L.nr, nz = L.nz, nz1 = nz + 1;
   const T wt = L.wt;
-  if (c0 < 0 || c0 >= nr * nz) return;
+  if (c0 < 0 || c0 >= nr * nz) {
+    if (L.write && L.oop) L.dst.cell[p] = c0;  // absorbed earlier: stays out of the store
+    return;
+  }
   int ic = c0 / nz, jc = c0 - (c0 / nz) * nz;
   T tau = one;
   T tT = tau;
@@ -525,9 +528,13 @@ __device__ void push_general(const GenArgs<T> &L, long long p, int c0, T a, T b,
     }
   }
   if (L.write) {
-    L.p.cell[p] = absorbed ? -1 : ic * nz + jc;
-    L.p.a[p] = a; L.p.b[p] = b;
-    L.p.vr[p] = vr; L.p.vt[p] = vt; L.p.vz[p] = vz;
+    L.dst.cell[p] = absorbed ? -1 : ic * nz + jc;
+    L.dst.a[p] = a; L.dst.b[p] = b;
+    L.dst.vr[p] = vr; L.dst.vt[p] = vt; L.dst.vz[p] = vz;
+    if (L.oop) {
+      L.dst.w[p] = w;
+      L.dst.id[p] = L.p.id[p];
+    }
   }
 }
 

@@ -202,16 +202,23 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_push_fast(PushL
             v3 = fz * am;
             if (L.write) {
               // CN velocity relations: the displacement is the mean of u and u'
-              L.p.a[p] = a1;
-              L.p.b[p] = b1;
-              L.p.vr[p] = (d + d - ur) * L.icr;
-              L.p.vz[p] = (e + e - uz) * L.icz;
-              L.p.vt[p] = rho * ut * Num<T>::rcp(rho + d) * L.icr;
+              L.dst.a[p] = a1;
+              L.dst.b[p] = b1;
+              L.dst.vr[p] = (d + d - ur) * L.icr;
+              L.dst.vz[p] = (e + e - uz) * L.icz;
+              L.dst.vt[p] = rho * ut * Num<T>::rcp(rho + d) * L.icr;
+              if (L.oop) {
+                L.dst.cell[p] = c0;
+                L.dst.w[p] = w;
+                L.dst.id[p] = L.p.id[p];
+              }
             }
           }
         }
       }
       queued = !acc;
+    } else if (L.write && L.oop && p < L.n) {
+      L.dst.cell[p] = c0;  // not pushed (absorbed earlier): stays out of the store
     }
     warp_deposit<T>(key, ic, jc, v0, v1, v2, v3, lane, nz, L.ir, L.iz);
     // queue the rest for the general path (warp-aggregated append to the
@@ -237,6 +244,7 @@ __global__ void __launch_bounds__(256) k_push_general(PushLaunchT<T> L) {
   G.nr = L.g.nr; G.nz = L.g.nz; G.ar = L.ar; G.az = L.az;
   G.wt = L.wbt; G.icr = L.icr; G.icz = L.icz;
   G.q = L.q; G.m = L.m; G.qf = L.qf; G.ir = L.ir; G.iz = L.iz; G.write = L.write; G.p = L.p;
+  G.oop = L.oop; G.dst = L.dst;
   G.wall_z0 = L.wall_z0; G.wall_zl = L.wall_zl; G.wall_r = L.wall_r; G.ke_lost = L.ke_lost;
   Tally tl = {0, 0, 0, 0, 0, 0};
   const long long gstride = (long long)gridDim.x * blockDim.x;
