@@ -40,7 +40,7 @@ DFMA_PER_CYCLE = 304
 BYTES_PER_PUSH_FP64 = 52
 # ncu DRAM bytes (read + write) per push of the current FP64 kernel, from the
 # profile in profiles/ (None when the kernel changed after the capture)
-TRAFFIC_PER_PUSH = None  # re-measured per kernel change (profiles/)
+TRAFFIC_PER_PUSH = 83.0  # DRAM bytes per push of the FP64 push kernels: ncu dram__bytes_read + write, 4M/species case
 
 
 def peaks():
