@@ -112,6 +112,12 @@ def _load_lib():
     L.pic_cnn_loss_grad.argtypes = [_P, _P, _P, _I, _P, _P]
     L.pic_cnn_train_step.argtypes = [_P, _P, _P, _I, C.c_float, _P]
     L.pic_set_guess.argtypes = [_P, _I, _P]
+    L.pic_set_graphs.argtypes = [_P, _I]
+    L.pic_ensemble_create.argtypes = [_P, _I, C.POINTER(_P)]
+    L.pic_ensemble_destroy.argtypes = [_P]
+    L.pic_ensemble_destroy.restype = None
+    L.pic_ensemble_step.argtypes = [_P, _I, _P]
+    L.pic_ensemble_tune.argtypes = [_P, _I, C.POINTER(C.c_float), C.POINTER(_D)]
     L.pic_guess_sample.argtypes = [_P, _P, _P, C.POINTER(_I)]
     return L
 
@@ -436,3 +442,45 @@ def guess_sample(pic):
     _check(lib().pic_guess_sample(pic._h, x.data_ptr(), t.data_ptr(), C.byref(valid)),
            "pic_guess_sample")
     return (x, t) if valid.value else None
+
+
+def set_graphs(pic, on=True):
+    """Replay the Picard passes of ``pic`` from captured CUDA graphs."""
+    _check(lib().pic_set_graphs(pic._h, 1 if on else 0), "pic_set_graphs")
+
+
+class Ensemble:
+    """Independent discharges (``Pic`` members, each on its own stream) stepped
+    side by side (include/pic_ensemble.h).  Does not own the members."""
+
+    def __init__(self, members):
+        self.members = list(members)
+        arr = (_P * len(self.members))(*[m._h for m in self.members])
+        h = _P()
+        _check(lib().pic_ensemble_create(arr, len(self.members), C.byref(h)),
+               "pic_ensemble_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pic_ensemble_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n=1, check=True):
+        st = (StepStats * len(self.members))()
+        rc = lib().pic_ensemble_step(self._h, int(n), st)
+        if check:
+            _check(rc, "pic_ensemble_step")
+        return rc, [s.as_dict() for s in st]
+
+    def tune(self, rounds=3):
+        f = C.c_float(0.0)
+        ms = (_D * 3)()
+        _check(lib().pic_ensemble_tune(self._h, int(rounds), C.byref(f), ms), "pic_ensemble_tune")
+        return float(f.value), list(ms)

@@ -95,6 +95,10 @@ __device__ __forceinline__ double rhs_at(const FieldOp &F, const double *er0, co
 
 __global__ void k_rhs(FieldOp F, const double *er0, const double *ez0, const double *h0,
                       const double *ir, const double *iz, double v0, double v1) {
+  if (F.vd) {
+    v0 = F.vd[0];
+    v1 = F.vd[1];
+  }
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   int nz = F.nz;
   if (F.half) {
@@ -392,6 +396,10 @@ __global__ void __launch_bounds__(256) k_update(FieldOp F, const double *er0, co
                                                 double *er1, double *ez1, double *h1,
                                                 const double *er_it, const double *ez_it,
                                                 DevCounters *cnt) {
+  if (F.vd) {
+    v0 = F.vd[0];
+    v1 = F.vd[1];
+  }
   int nr = F.nr, nz = F.nz, nz1 = nz + 1;
   long long ner = (long long)nr * nz1, nez = (long long)(nr + 1) * nz, nh = (long long)nr * nz;
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;

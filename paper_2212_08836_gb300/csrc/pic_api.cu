@@ -6,8 +6,10 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <chrono>
 #include <vector>
 
+#include "../../include/pic_ensemble.h"
 #include "../../include/pic_guess.h"
 #include "pic_internal.cuh"
 
@@ -75,6 +77,21 @@ struct pic_ctx {
   int *gbad;
   float *gx, *gt;           // inputs of the current / last step and its target
   int sample_valid, feat_now;
+  // graph-stable launches: particle counts and drive voltages on the device,
+  // Picard passes captured once per buffer configuration and replayed
+  long long *n_dev;
+  double *vdev;
+  double *hn;               // pinned host: Picard norms of the last pass
+  int graphs;               // 1: passes replayed from captured graphs
+  int capturing;            // a pass is being captured (no timing events)
+  long long passes;         // passes enqueued (the first one is never captured)
+  int fgrid[2], ggrid[2];   // tuned push grids (fast / general, per form: index 0)
+  struct GraphEntry {
+    const void *key[12];
+    cudaGraphExec_t exec;
+    long long nlaunch;      // kernels in the graph
+  } gcache[64];
+  int ngraph;
   cudaStream_t gstream;     // stream of the network
   cudaEvent_t gev[2];
   int gev_made, cnn_layers;
@@ -202,6 +219,8 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
   x->gsums = (double *)K.take(8 * 8);
   x->gsd = x->gsums + 4;
   x->gbad = (int *)K.take(256);
+  x->n_dev = (long long *)K.take(256);
+  x->vdev = (double *)K.take(256);
   {
     size_t P = (size_t)(nr + 1) * (nz + 1);
     x->gx = (float *)K.take(P * PIC_CNN_IN * 4);
@@ -273,6 +292,10 @@ void fill_push(pic_ctx *x, int s, double q, double m, const double *erh, const d
   L.wbt = (T)(q / m * x->cfg.bz * dt);
   L.inz = 1.0f / (float)x->g.nz;
   L.n = x->n[s];
+  L.n_dev = x->n_dev + s;
+  L.cap = x->cap[s];
+  L.fgrid = x->fgrid[0];
+  L.ggrid = x->ggrid[0];
   L.ir = ir;
   L.iz = iz;
   L.write = write;
@@ -295,7 +318,7 @@ void set_queue(pic_ctx *x, T *const rec[2], PushLaunchT<T> &L) {
 // final pass), every field; else (write) in place
 int push_all(pic_ctx *x, const double *erh, const double *ezh, double *ir, double *iz, int write,
              unsigned long long *counters, double *kel, double *wall, int oop = 0) {
-  bool timed = x->prof && x->nev < 128;
+  bool timed = x->prof && x->nev < 128 && !x->capturing;
   if (timed) cudaEventRecord(x->ev[2 * x->nev], x->s);
   for (int s = 0; s < 2; ++s) {
     const double q = s == 0 ? -kQE : kQE, m = s == 0 ? kME : kMAr;
@@ -579,17 +602,24 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
   if (e == cudaSuccess) e = cudaMemsetAsync(x->h, 0, nh * 8, x->s);
   if (e == cudaSuccess) e = cudaMemsetAsync(x->wall, 0, (size_t)2 * (2 * (nr + 1) + nz + 1) * 8, x->s);
   if (e == cudaSuccess) e = cudaMemsetAsync(x->cnt, 0, sizeof(DevCounters), x->s);
+  if (e == cudaSuccess) e = cudaHostAlloc((void **)&x->hn, 64, cudaHostAllocDefault);
   if (e == cudaSuccess) e = cudaStreamSynchronize(x->s);
   if (e != cudaSuccess) {
+    if (x->hn) cudaFreeHost(x->hn);
     free(x);
     return PIC_E_CUDA;
   }
+  x->F.vd = x->vdev;
+  x->hist_n = 1;
   *out = x;
   return PIC_OK;
 }
 
 void pic_destroy(pic_ctx *ctx) {
   if (!ctx) return;
+  if (ctx->ngraph || ctx->hn) cudaStreamSynchronize(ctx->s);
+  for (int k = 0; k < ctx->ngraph; ++k) cudaGraphExecDestroy(ctx->gcache[k].exec);
+  if (ctx->hn) cudaFreeHost(ctx->hn);
   if (ctx->gev_made) {
     cudaStreamSynchronize(ctx->s);
     cudaEventDestroy(ctx->gev[0]);
@@ -690,6 +720,8 @@ int pic_push_deposit(pic_ctx *x, const double *erh, const double *ezh, double *i
                                                         x->ezh, x->alpha64, x->s);
   if (ae != cudaSuccess) return PIC_E_CUDA;
   x->launches += 1;
+  if (cudaMemcpyAsync(x->n_dev, x->n, 16, cudaMemcpyHostToDevice, x->s) != cudaSuccess)
+    return PIC_E_CUDA;
   return push_all(x, erh, ezh, ir, iz, write, counters, kel, write ? x->wall : nullptr);
 }
 
@@ -697,7 +729,9 @@ int pic_field_solve(pic_ctx *x, const double *er0, const double *ez0, const doub
                     const double *ir, const double *iz, double v0, double v1, double *er1,
                     double *ez1, double *h1, double *src) {
   if (!x || !er0 || !ez0 || !h0 || !ir || !iz || !er1 || !ez1 || !h1) return PIC_E_CONFIG;
-  cudaError_t e = launch_field_solve(x->F, er0, ez0, h0, ir, iz, v0, v1, er1, ez1, h1, nullptr,
+  FieldOp F = x->F;
+  F.vd = nullptr;  // the caller's voltages
+  cudaError_t e = launch_field_solve(F, er0, ez0, h0, ir, iz, v0, v1, er1, ez1, h1, nullptr,
                                      nullptr, x->cnt, x->s);
   x->launches += 5;
   if (e == cudaSuccess && src)
@@ -793,6 +827,15 @@ GuessArgs guess_args(pic_ctx *x) {
   return A;
 }
 
+// counts and drive voltages of the coming step on the device
+int upload_step(pic_ctx *x, double v0, double v1) {
+  // pageable sources: the call returns once they are staged, so the stack is safe
+  const double st[2] = {v0, v1};
+  if (cudaMemcpyAsync(x->vdev, st, 16, cudaMemcpyHostToDevice, x->s) != cudaSuccess) return 1;
+  if (cudaMemcpyAsync(x->n_dev, x->n, 16, cudaMemcpyHostToDevice, x->s) != cudaSuccess) return 1;
+  return 0;
+}
+
 // plain start E^{n+1,0} = E^n with the drive value on r = R
 int plain_start(pic_ctx *x, double v1) {
   const int nr = x->g.nr, nz = x->g.nz;
@@ -847,12 +890,117 @@ int guess_start(pic_ctx *x, double v1, int *used) {
 // the new particle state into the second buffer of the store (every field;
 // wall tallies into scratch).  If it converges the buffers are swapped and
 // the commit push is skipped (*spec = 1); if not, the iteration goes on.
-int picard(pic_ctx *x, double v0, double v1, pic_step_stats &S, bool &conv, int &k, double &res,
-           double &src, double &first, int &spec_ok) {
+// one Picard pass: E^{n+1/2,k}, push + deposit (speculative: writing the new
+// state out of place), field solve, norms copied to pinned host memory
+int enqueue_pass(pic_ctx *x, bool spec) {
   const int nr = x->g.nr, nz = x->g.nz;
   const size_t ner = (size_t)nr * (nz + 1), nez = (size_t)(nr + 1) * nz;
   const size_t nwall = (size_t)2 * (2 * (nr + 1) + nz + 1);
   cudaStream_t s = x->s;
+  cudaError_t he =
+      x->mixed ? launch_half_field_alpha(x->g, x->er, x->ez, x->er1, x->ez1, x->erh, x->ezh,
+                                         x->alpha, s)
+               : launch_half_field_alpha64(x->g, x->er, x->ez, x->er1, x->ez1, x->erh, x->ezh,
+                                           x->alpha64, s);
+  if (he != cudaSuccess) return PIC_E_CUDA;
+  x->launches += 1;
+  if (cudaMemsetAsync(x->ir, 0, ner * 8, s) != cudaSuccess) return PIC_E_CUDA;
+  if (cudaMemsetAsync(x->iz, 0, nez * 8, s) != cudaSuccess) return PIC_E_CUDA;
+  int r;
+  if (spec) {
+    if (cudaMemsetAsync(x->cnt->push, 0, sizeof(x->cnt->push), s) != cudaSuccess ||
+        cudaMemsetAsync(&x->cnt->ke_lost, 0, 8, s) != cudaSuccess ||
+        cudaMemsetAsync(x->wall_spec, 0, nwall * 8, s) != cudaSuccess)
+      return PIC_E_CUDA;
+    r = push_all(x, x->erh, x->ezh, x->ir, x->iz, 1, x->cnt->push, &x->cnt->ke_lost,
+                 x->wall_spec, 1);
+  } else {
+    r = push_all(x, x->erh, x->ezh, x->ir, x->iz, 0, nullptr, nullptr, nullptr);
+  }
+  if (r) return r;
+  if (launch_field_solve(x->F, x->er, x->ez, x->h, x->ir, x->iz, 0.0, 0.0, x->er2, x->ez2, x->h2,
+                         x->er1, x->ez1, x->cnt, s) != cudaSuccess)
+    return PIC_E_CUDA;
+  x->launches += 5;
+  if (cudaMemcpyAsync(x->hn, x->cnt->norm, 3 * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return PIC_E_CUDA;
+  return PIC_OK;
+}
+
+// the pass for the current buffers, replayed from a graph captured the first
+// time this buffer configuration occurs (counts and voltages are read on the
+// device, grids depend only on capacities)
+int launch_pass(pic_ctx *x, bool spec) {
+  // the first pass runs uncaptured (one-time set-up of launch shapes)
+  if (!x->graphs || x->passes++ == 0) return enqueue_pass(x, spec);
+  const void *key[12] = {x->er, x->ez, x->h, x->er1, x->ez1, x->er2, x->ez2, x->h2,
+                         (const void *)(uintptr_t)x->cur[0], (const void *)(uintptr_t)x->cur[1],
+                         (const void *)(uintptr_t)(spec ? 1 : 0), x->erh};
+  for (int k = 0; k < x->ngraph; ++k)
+    if (!memcmp(x->gcache[k].key, key, sizeof(key))) {
+      x->launches += x->gcache[k].nlaunch;
+      return cudaGraphLaunch(x->gcache[k].exec, x->s) == cudaSuccess ? PIC_OK : PIC_E_CUDA;
+    }
+  if (x->ngraph == 64) return enqueue_pass(x, spec);
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(x->s, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return PIC_E_CUDA;
+  long long l0 = x->launches;
+  x->capturing = 1;
+  int r = enqueue_pass(x, spec);
+  x->capturing = 0;
+  cudaError_t e = cudaStreamEndCapture(x->s, &g);
+  if (r) {
+    if (g) cudaGraphDestroy(g);
+    return r;
+  }
+  if (e != cudaSuccess) return PIC_E_CUDA;
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return PIC_E_CUDA;
+  pic_ctx::GraphEntry &E = x->gcache[x->ngraph++];
+  memcpy(E.key, key, sizeof(key));
+  E.exec = ex;
+  E.nlaunch = x->launches - l0;
+  return cudaGraphLaunch(ex, x->s) == cudaSuccess ? PIC_OK : PIC_E_CUDA;
+}
+
+// after the pass has completed: residual, buffer swap, convergence and the
+// speculation decision for the next pass
+void finish_pass(pic_ctx *x, int k, double &rprev, double &res, double &src, double &first,
+                 bool &conv, bool &spec, int &spec_ok) {
+  const double *hn = x->hn;
+  res = sqrt(hn[0]) / fmax(sqrt(hn[1]), 1e-30);
+  if (k == 0) first = res;
+  src = hn[2];
+  double *t;
+  t = x->er1; x->er1 = x->er2; x->er2 = t;
+  t = x->ez1; x->ez1 = x->ez2; x->ez2 = t;
+  if (k > 0 && rprev > 0.0) x->rho_prev = res / rprev;
+  if (res < x->cfg.picard_tol) {
+    conv = true;
+    spec_ok = spec ? 1 : 0;
+    return;
+  }
+  const double rho = k > 0 ? res / rprev : x->rho_prev;
+  spec = rho > 0.0 && rho < 1.0 && res * rho < x->cfg.picard_tol;
+  rprev = res;
+}
+
+// the nonlinear iteration of Sec. 2.1 from the start in er1/ez1: push + deposit
+// with E^{n+1/2,k}, implicit field solve, relative-change test
+//
+// Speculative final pass: the commit push of a converged step repeats the last
+// pass with the same E^{n+1/2}, so when the contraction of the last two
+// residuals predicts that the next pass converges, that pass already writes
+// the new particle state into the second buffer of the store (every field;
+// wall tallies into scratch).  If it converges the buffers are swapped and
+// the commit push is skipped (*spec = 1); if not, the iteration goes on.
+int picard(pic_ctx *x, double v0, double v1, pic_step_stats &S, bool &conv, int &k, double &res,
+           double &src, double &first, int &spec_ok) {
+  (void)v0;
+  (void)v1;
   conv = false;
   res = 0.0;
   src = 0.0;
@@ -861,57 +1009,17 @@ int picard(pic_ctx *x, double v0, double v1, pic_step_stats &S, bool &conv, int 
   bool spec = false;
   double rprev = 0.0;
   for (k = 0; k < x->cfg.picard_max; ++k) {
-    cudaError_t he =
-        x->mixed ? launch_half_field_alpha(x->g, x->er, x->ez, x->er1, x->ez1, x->erh, x->ezh,
-                                           x->alpha, s)
-                 : launch_half_field_alpha64(x->g, x->er, x->ez, x->er1, x->ez1, x->erh, x->ezh,
-                                             x->alpha64, s);
-    if (he != cudaSuccess) return PIC_E_CUDA;
-    x->launches += 1;
-    if (cudaMemsetAsync(x->ir, 0, ner * 8, s) != cudaSuccess) return PIC_E_CUDA;
-    if (cudaMemsetAsync(x->iz, 0, nez * 8, s) != cudaSuccess) return PIC_E_CUDA;
-    int r;
-    if (spec) {
-      if (cudaMemsetAsync(x->cnt->push, 0, sizeof(x->cnt->push), s) != cudaSuccess ||
-          cudaMemsetAsync(&x->cnt->ke_lost, 0, 8, s) != cudaSuccess ||
-          cudaMemsetAsync(x->wall_spec, 0, nwall * 8, s) != cudaSuccess)
-        return PIC_E_CUDA;
-      r = push_all(x, x->erh, x->ezh, x->ir, x->iz, 1, x->cnt->push, &x->cnt->ke_lost,
-                   x->wall_spec, 1);
-    } else {
-      r = push_all(x, x->erh, x->ezh, x->ir, x->iz, 0, nullptr, nullptr, nullptr);
-    }
+    int r = launch_pass(x, spec);
     if (r) return r;
     S.pushes += x->n[0] + x->n[1];
-    if (launch_field_solve(x->F, x->er, x->ez, x->h, x->ir, x->iz, v0, v1, x->er2, x->ez2, x->h2,
-                           x->er1, x->ez1, x->cnt, s) != cudaSuccess)
-      return PIC_E_CUDA;
-    x->launches += 5;
-    double hn[3];
-    if (cudaMemcpyAsync(hn, x->cnt->norm, 3 * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-      return PIC_E_CUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return PIC_E_CUDA;
+    if (cudaStreamSynchronize(x->s) != cudaSuccess) return PIC_E_CUDA;
     if (x->prof) prof_collect(x);
-    res = sqrt(hn[0]) / fmax(sqrt(hn[1]), 1e-30);
-    if (k == 0) first = res;
-    src = hn[2];
-    double *t;
-    t = x->er1; x->er1 = x->er2; x->er2 = t;
-    t = x->ez1; x->ez1 = x->ez2; x->ez2 = t;
+    finish_pass(x, k, rprev, res, src, first, conv, spec, spec_ok);
     if (!isfinite(res)) {
       S.picard_iters = k + 1;
       return PIC_E_NAN;
     }
-    if (k > 0 && rprev > 0.0) x->rho_prev = res / rprev;
-    if (res < x->cfg.picard_tol) {
-      conv = true;
-      spec_ok = spec ? 1 : 0;
-      break;
-    }
-    // next residual predicted from the contraction (the previous step's for k = 0)
-    const double rho = k > 0 ? res / rprev : x->rho_prev;
-    spec = rho > 0.0 && rho < 1.0 && res * rho < x->cfg.picard_tol;
-    rprev = res;
+    if (conv) break;
   }
   return PIC_OK;
 }
@@ -923,120 +1031,148 @@ __global__ void k_addto(double *dst, const double *src, int n) {
 
 }  // namespace
 
-int pic_step(pic_ctx *x, int nsteps, pic_step_stats *st) {
-  if (!x || nsteps < 0) return PIC_E_CONFIG;
-  int nr = x->g.nr, nz = x->g.nz;
-  size_t ner = (size_t)nr * (nz + 1), nez = (size_t)(nr + 1) * nz;
-  int rc = PIC_OK;
-  for (int it = 0; it < nsteps; ++it) {
-    pic_step_stats S;
-    memset(&S, 0, sizeof(S));
-    long long l0 = x->launches;
-    double v0 = volt_at(x, x->step), v1 = volt_at(x, x->step + 1);
-    cudaStream_t s = x->s;
-    int used = PIC_GUESS_PLAIN;
-    x->feat_now = 0;
-    if (x->guess_mode != PIC_GUESS_PLAIN && x->hist_n >= 4) {
-      int gr = guess_start(x, v1, &used);
-      if (gr) return gr;
-    }
-    if (used == PIC_GUESS_PLAIN) {
-      int pr = plain_start(x, v1);
-      if (pr) return pr;
-    }
-    bool conv = false;
-    double res = 0.0, src = 0.0, first = 0.0;
-    int k = 0, spec = 0;
-    int pr = picard(x, v0, v1, S, conv, k, res, src, first, spec);
-    if (!conv && used != PIC_GUESS_PLAIN && (pr == PIC_OK || pr == PIC_E_NAN)) {
-      // the plain start remains the fallback: redo the iteration from E^n
-      used = PIC_GUESS_PLAIN;
-      pr = plain_start(x, v1);
-      if (!pr) pr = picard(x, v0, v1, S, conv, k, res, src, first, spec);
-    }
-    S.guess = used;
-    S.first_res = first;
-    S.spec_final = spec;
-    if (pr) {
-      if (st) *st = S;
-      return pr;
-    }
-    S.picard_iters = conv ? k + 1 : k;
-    S.last_res = res;
-    S.converged = conv ? 1 : 0;
-    if (!conv) {
-      S.n[0] = x->n[0];
-      S.n[1] = x->n[1];
-      if (st) *st = S;
-      return PIC_E_NOCONV;
-    }
-    if (spec) {
-      // the converged pass already wrote the new state into the second buffer
-      x->cur[0] ^= 1;
-      x->cur[1] ^= 1;
-      const int nwall = 2 * (2 * (nr + 1) + nz + 1);
-      k_addto<<<(nwall + 255) / 256, 256, 0, s>>>(x->wall, x->wall_spec, nwall);
-      if (cudaGetLastError() != cudaSuccess) return PIC_E_CUDA;
-      x->launches += 1;
-    } else {
-      // commit: the half field of the last iteration fed the last solve
-      if (cudaMemsetAsync(x->ir, 0, ner * 8, s) != cudaSuccess) return PIC_E_CUDA;
-      if (cudaMemsetAsync(x->iz, 0, nez * 8, s) != cudaSuccess) return PIC_E_CUDA;
-      if (cudaMemsetAsync(x->cnt->push, 0, sizeof(x->cnt->push), s) != cudaSuccess)
-        return PIC_E_CUDA;
-      if (cudaMemsetAsync(&x->cnt->ke_lost, 0, 8, s) != cudaSuccess) return PIC_E_CUDA;
-      int r = push_all(x, x->erh, x->ezh, x->ir, x->iz, 1, x->cnt->push, &x->cnt->ke_lost, x->wall);
-      if (r) return r;
-      S.pushes += x->n[0] + x->n[1];
-    }
-    double *t;
-    t = x->er; x->er = x->er1; x->er1 = t;
-    t = x->ez; x->ez = x->ez1; x->ez1 = t;
-    t = x->h; x->h = x->h2; x->h2 = t;
-    if (x->guess_mode != PIC_GUESS_PLAIN) {
-      // training target of this step, then E^n joins the history (its buffer
-      // is now er1/ez1) and the committed crossed charge is kept
-      if (x->feat_now) {
-        GuessArgs A = guess_args(x);
-        if (launch_guess_target(A, x->er, x->ez, x->gt, s) != cudaSuccess) return PIC_E_CUDA;
-        x->launches += 1;
-        x->sample_valid = 1;
-      }
-      t = x->hr[2]; x->hr[2] = x->hr[1]; x->hr[1] = x->hr[0]; x->hr[0] = x->er1; x->er1 = t;
-      t = x->hz[2]; x->hz[2] = x->hz[1]; x->hz[1] = x->hz[0]; x->hz[0] = x->ez1; x->ez1 = t;
-      if (cudaMemcpyAsync(x->jr, x->ir, ner * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
-          cudaMemcpyAsync(x->jz, x->iz, nez * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-        return PIC_E_CUDA;
-      if (x->hist_n < 4) x->hist_n += 1;
-    }
-    S.src_energy = src;
-    if (x->cfg.mcc_on) {
-      int mr = pic_mcc(x, (unsigned long long)x->step, S.mcc, &S.de_coll);
-      if (mr && mr != PIC_E_CAPACITY) return mr;
-      if (mr) rc = mr;
-    }
-    int sr = pic_sort(x);
-    if (sr) return sr;
-    unsigned long long pc[5];
-    double kel = 0.0;
-    if (cudaMemcpyAsync(pc, x->cnt->push, sizeof(pc), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-      return PIC_E_CUDA;
-    if (cudaMemcpyAsync(&kel, &x->cnt->ke_lost, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-      return PIC_E_CUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return PIC_E_CUDA;
-    if (x->prof) prof_collect(x);
-    S.substep_err = (long long)pc[0];
-    S.absorbed = (long long)pc[1];
-    S.substeps = (long long)pc[2];
-    S.fallbacks = (long long)pc[3];
-    S.push_flops = (long long)pc[4];
-    S.ke_lost = kel;
+namespace {
+
+// state of one step between its phases (shared by pic_step and the ensemble)
+struct StepState {
+  pic_step_stats S;
+  long long l0;
+  double v0, v1;
+  int used;          // Picard start
+  bool conv, spec;   // converged; the next pass is speculative
+  int k, spec_ok;
+  double res, src, first, rprev;
+};
+
+// upload counts and voltages, choose and place the Picard start
+int step_begin(pic_ctx *x, StepState &T) {
+  memset(&T, 0, sizeof(T));
+  T.l0 = x->launches;
+  T.v0 = volt_at(x, x->step);
+  T.v1 = volt_at(x, x->step + 1);
+  if (upload_step(x, T.v0, T.v1)) return PIC_E_CUDA;
+  T.used = PIC_GUESS_PLAIN;
+  x->feat_now = 0;
+  if (x->guess_mode != PIC_GUESS_PLAIN && x->hist_n >= 4) {
+    int gr = guess_start(x, T.v1, &T.used);
+    if (gr) return gr;
+  }
+  if (T.used == PIC_GUESS_PLAIN) return plain_start(x, T.v1);
+  return PIC_OK;
+}
+
+// commit (or adopt the speculative pass), field rotation, guess history, MCC,
+// sort and statistics; *rc collects non-fatal codes
+int step_end(pic_ctx *x, StepState &T, int *rc) {
+  pic_step_stats &S = T.S;
+  const int nr = x->g.nr, nz = x->g.nz;
+  const size_t ner = (size_t)nr * (nz + 1), nez = (size_t)(nr + 1) * nz;
+  cudaStream_t s = x->s;
+  S.guess = T.used;
+  S.first_res = T.first;
+  S.spec_final = T.spec_ok;
+  S.picard_iters = T.conv ? T.k + 1 : T.k;
+  S.last_res = T.res;
+  S.converged = T.conv ? 1 : 0;
+  if (!T.conv) {
     S.n[0] = x->n[0];
     S.n[1] = x->n[1];
-    S.launches = x->launches - l0;
-    x->step += 1;
-    if (st) *st = S;
-    if (S.substep_err && !rc) rc = PIC_E_SUBSTEP;
+    return PIC_E_NOCONV;
+  }
+  if (T.spec_ok) {
+    // the converged pass already wrote the new state into the second buffer
+    x->cur[0] ^= 1;
+    x->cur[1] ^= 1;
+    const int nwall = 2 * (2 * (nr + 1) + nz + 1);
+    k_addto<<<(nwall + 255) / 256, 256, 0, s>>>(x->wall, x->wall_spec, nwall);
+    if (cudaGetLastError() != cudaSuccess) return PIC_E_CUDA;
+    x->launches += 1;
+  } else {
+    // commit: the half field of the last iteration fed the last solve
+    if (cudaMemsetAsync(x->ir, 0, ner * 8, s) != cudaSuccess) return PIC_E_CUDA;
+    if (cudaMemsetAsync(x->iz, 0, nez * 8, s) != cudaSuccess) return PIC_E_CUDA;
+    if (cudaMemsetAsync(x->cnt->push, 0, sizeof(x->cnt->push), s) != cudaSuccess)
+      return PIC_E_CUDA;
+    if (cudaMemsetAsync(&x->cnt->ke_lost, 0, 8, s) != cudaSuccess) return PIC_E_CUDA;
+    int r = push_all(x, x->erh, x->ezh, x->ir, x->iz, 1, x->cnt->push, &x->cnt->ke_lost, x->wall);
+    if (r) return r;
+    S.pushes += x->n[0] + x->n[1];
+  }
+  double *t;
+  t = x->er; x->er = x->er1; x->er1 = t;
+  t = x->ez; x->ez = x->ez1; x->ez1 = t;
+  t = x->h; x->h = x->h2; x->h2 = t;
+  if (x->guess_mode != PIC_GUESS_PLAIN) {
+    // training target of this step, then E^n joins the history (its buffer
+    // is now er1/ez1) and the committed crossed charge is kept
+    if (x->feat_now) {
+      GuessArgs A = guess_args(x);
+      if (launch_guess_target(A, x->er, x->ez, x->gt, s) != cudaSuccess) return PIC_E_CUDA;
+      x->launches += 1;
+      x->sample_valid = 1;
+    }
+    t = x->hr[2]; x->hr[2] = x->hr[1]; x->hr[1] = x->hr[0]; x->hr[0] = x->er1; x->er1 = t;
+    t = x->hz[2]; x->hz[2] = x->hz[1]; x->hz[1] = x->hz[0]; x->hz[0] = x->ez1; x->ez1 = t;
+    if (cudaMemcpyAsync(x->jr, x->ir, ner * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(x->jz, x->iz, nez * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return PIC_E_CUDA;
+    if (x->hist_n < 4) x->hist_n += 1;
+  }
+  S.src_energy = T.src;
+  if (x->cfg.mcc_on) {
+    int mr = pic_mcc(x, (unsigned long long)x->step, S.mcc, &S.de_coll);
+    if (mr && mr != PIC_E_CAPACITY) return mr;
+    if (mr) *rc = mr;
+  }
+  int sr = pic_sort(x);
+  if (sr) return sr;
+  unsigned long long pc[5];
+  double kel = 0.0;
+  if (cudaMemcpyAsync(pc, x->cnt->push, sizeof(pc), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return PIC_E_CUDA;
+  if (cudaMemcpyAsync(&kel, &x->cnt->ke_lost, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return PIC_E_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return PIC_E_CUDA;
+  if (x->prof) prof_collect(x);
+  S.substep_err = (long long)pc[0];
+  S.absorbed = (long long)pc[1];
+  S.substeps = (long long)pc[2];
+  S.fallbacks = (long long)pc[3];
+  S.push_flops = (long long)pc[4];
+  S.ke_lost = kel;
+  S.n[0] = x->n[0];
+  S.n[1] = x->n[1];
+  S.launches = x->launches - T.l0;
+  x->step += 1;
+  if (S.substep_err && !*rc) *rc = PIC_E_SUBSTEP;
+  return PIC_OK;
+}
+
+}  // namespace
+
+int pic_step(pic_ctx *x, int nsteps, pic_step_stats *st) {
+  if (!x || nsteps < 0) return PIC_E_CONFIG;
+  int rc = PIC_OK;
+  for (int it = 0; it < nsteps; ++it) {
+    StepState T;
+    int r = step_begin(x, T);
+    if (r) return r;
+    int pr = picard(x, T.v0, T.v1, T.S, T.conv, T.k, T.res, T.src, T.first, T.spec_ok);
+    if (!T.conv && T.used != PIC_GUESS_PLAIN && (pr == PIC_OK || pr == PIC_E_NAN)) {
+      // the plain start remains the fallback: redo the iteration from E^n
+      T.used = PIC_GUESS_PLAIN;
+      pr = plain_start(x, T.v1);
+      if (!pr) pr = picard(x, T.v0, T.v1, T.S, T.conv, T.k, T.res, T.src, T.first, T.spec_ok);
+    }
+    if (pr) {
+      T.S.guess = T.used;
+      T.S.first_res = T.first;
+      if (st) *st = T.S;
+      return pr;
+    }
+    r = step_end(x, T, &rc);
+    if (st) *st = T.S;
+    if (r) return r;
   }
   return rc;
 }
@@ -1166,4 +1302,157 @@ int pic_guess_sample(pic_ctx *x, float *x_dev, float *t_dev, int *valid) {
     e = cudaMemcpyAsync(t_dev, x->gt, P * PIC_CNN_OUT * 4, cudaMemcpyDeviceToDevice, x->s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(x->s);
   return e == cudaSuccess ? PIC_OK : PIC_E_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// ensembles (include/pic_ensemble.h)
+
+struct pic_ensemble {
+  int n;
+  pic_ctx *m[PIC_ENSEMBLE_MAX];
+};
+
+namespace {
+
+void drop_graphs(pic_ctx *x) {
+  if (x->ngraph) cudaStreamSynchronize(x->s);
+  for (int k = 0; k < x->ngraph; ++k) cudaGraphExecDestroy(x->gcache[k].exec);
+  x->ngraph = 0;
+}
+
+}  // namespace
+
+int pic_set_graphs(pic_ctx *x, int on) {
+  if (!x) return PIC_E_CONFIG;
+  x->graphs = on ? 1 : 0;
+  return PIC_OK;
+}
+
+int pic_ensemble_create(pic_ctx *const *members, int n, pic_ensemble **out) {
+  if (!out) return PIC_E_CONFIG;
+  *out = nullptr;
+  if (!members || n < 1 || n > PIC_ENSEMBLE_MAX) return PIC_E_CONFIG;
+  for (int i = 0; i < n; ++i) {
+    if (!members[i]) return PIC_E_CONFIG;
+    for (int j = 0; j < i; ++j)
+      if (members[j] == members[i]) return PIC_E_CONFIG;
+  }
+  pic_ensemble *E = (pic_ensemble *)calloc(1, sizeof(pic_ensemble));
+  if (!E) return PIC_E_CONFIG;
+  E->n = n;
+  for (int i = 0; i < n; ++i) {
+    E->m[i] = members[i];
+    members[i]->graphs = 1;
+  }
+  *out = E;
+  return PIC_OK;
+}
+
+void pic_ensemble_destroy(pic_ensemble *E) { free(E); }
+
+int pic_ensemble_step(pic_ensemble *E, int nsteps, pic_step_stats *st) {
+  if (!E || nsteps < 0) return PIC_E_CONFIG;
+  const int n = E->n;
+  int rc = PIC_OK;
+  std::vector<StepState> T(n);
+  std::vector<char> active(n);
+  for (int it = 0; it < nsteps; ++it) {
+    for (int i = 0; i < n; ++i) {
+      int r = step_begin(E->m[i], T[i]);
+      if (r) return r;
+      active[i] = 1;
+    }
+    // rounds: one Picard pass of every unconverged member, then one wait
+    int nact = n;
+    while (nact) {
+      for (int i = 0; i < n; ++i) {
+        if (!active[i]) continue;
+        pic_ctx *x = E->m[i];
+        int r = launch_pass(x, T[i].spec);
+        if (r) return r;
+        T[i].S.pushes += x->n[0] + x->n[1];
+      }
+      for (int i = 0; i < n; ++i) {
+        if (!active[i]) continue;
+        pic_ctx *x = E->m[i];
+        if (cudaStreamSynchronize(x->s) != cudaSuccess) return PIC_E_CUDA;
+        StepState &S = T[i];
+        finish_pass(x, S.k, S.rprev, S.res, S.src, S.first, S.conv, S.spec, S.spec_ok);
+        if (!isfinite(S.res)) return PIC_E_NAN;
+        if (S.conv) {
+          active[i] = 0;
+          --nact;
+          continue;
+        }
+        if (++S.k < x->cfg.picard_max) continue;
+        if (S.used != PIC_GUESS_PLAIN) {
+          // the plain start remains the fallback
+          S.used = PIC_GUESS_PLAIN;
+          S.k = 0;
+          S.spec = false;
+          S.rprev = 0.0;
+          int r = plain_start(x, S.v1);
+          if (r) return r;
+        } else {
+          active[i] = 0;  // not converged: step_end reports PIC_E_NOCONV
+          --nact;
+        }
+      }
+    }
+    for (int i = 0; i < n; ++i) {
+      int r = step_end(E->m[i], T[i], &rc);
+      if (st) st[i] = T[i].S;
+      if (r) return r;
+    }
+  }
+  return rc;
+}
+
+int pic_ensemble_tune(pic_ensemble *E, int rounds, float *frac_out, double *ms_out) {
+  if (!E || rounds < 1) return PIC_E_CONFIG;
+  const float fr[3] = {1.0f, 0.5f, 0.25f};
+  double best = 1e300;
+  int bi = 0;
+  for (int c = 0; c < 3; ++c) {
+    for (int i = 0; i < E->n; ++i) {
+      pic_ctx *x = E->m[i];
+      drop_graphs(x);
+      int wf = x->mixed ? push_wave_fp32(0) : push_wave_fp64(0);
+      int wg = x->mixed ? push_wave_fp32(1) : push_wave_fp64(1);
+      x->fgrid[0] = fr[c] < 1.0f ? (int)(wf * fr[c]) > 0 ? (int)(wf * fr[c]) : 1 : 0;
+      x->ggrid[0] = fr[c] < 1.0f ? (int)(wg * fr[c]) > 0 ? (int)(wg * fr[c]) : 1 : 0;
+      if (upload_step(x, volt_at(x, x->step), volt_at(x, x->step + 1))) return PIC_E_CUDA;
+      int r = plain_start(x, volt_at(x, x->step + 1));
+      if (r) return r;
+    }
+    double tbest = 1e300;
+    for (int rep = 0; rep < rounds + 1; ++rep) {
+      for (int i = 0; i < E->n; ++i)
+        if (cudaStreamSynchronize(E->m[i]->s) != cudaSuccess) return PIC_E_CUDA;
+      auto t0 = std::chrono::steady_clock::now();
+      for (int i = 0; i < E->n; ++i) {
+        int r = enqueue_pass(E->m[i], false);
+        if (r) return r;
+      }
+      for (int i = 0; i < E->n; ++i)
+        if (cudaStreamSynchronize(E->m[i]->s) != cudaSuccess) return PIC_E_CUDA;
+      double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+                      .count();
+      if (rep > 0 && ms < tbest) tbest = ms;  // the first round warms up
+    }
+    if (ms_out) ms_out[c] = tbest;
+    if (tbest < best) {
+      best = tbest;
+      bi = c;
+    }
+  }
+  for (int i = 0; i < E->n; ++i) {
+    pic_ctx *x = E->m[i];
+    int wf = x->mixed ? push_wave_fp32(0) : push_wave_fp64(0);
+    int wg = x->mixed ? push_wave_fp32(1) : push_wave_fp64(1);
+    x->fgrid[0] = bi ? (int)(wf * fr[bi]) : 0;
+    x->ggrid[0] = bi ? (int)(wg * fr[bi]) : 0;
+  }
+  if (frac_out) *frac_out = fr[bi];
+  return PIC_OK;
 }

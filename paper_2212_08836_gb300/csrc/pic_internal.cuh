@@ -115,6 +115,9 @@ struct FieldOp {
   // per-row tables (nr + 1 entries each): 1/(2 eps A_r), 1/(2 eps A_z),
   // 1/(eps A_r), 1/(eps A_z), 2 pi r_{i+1/2}, V_H
   const double *rtab;
+  // drive voltages V(t^n), V(t^{n+1}) read on the device (vd != nullptr) so
+  // that a captured solve stays valid from step to step; else the arguments
+  const double *vd;
 };
 
 // One mover + deposit pass over one species (rows a2, a3, a6) in the scalar
@@ -128,6 +131,8 @@ struct PushLaunchT {
   T wbt;                   // qm*Bz*dt (0: no external B_z)
   float inz;               // 1/nz (cell -> (i, j) split without an integer division)
   long long n;
+  const long long *n_dev;  // particle count on the device (graph-stable launches), or nullptr
+  long long cap;           // store capacity (bounds the queue segments when n_dev is used)
   PartsT<T> p;
   const T *ar, *az;        // normalised accelerations qm*E*dt^2/dx of this species
   double *ir, *iz;         // crossed charge [C] (FP64, atomics)
@@ -142,6 +147,7 @@ struct PushLaunchT {
   int *queue, *qblock;
   long long qseg;
   int qgrid;               // blocks of the fast kernel
+  int fgrid, ggrid;        // tuned grids of the fast / general kernels (0: one wave)
   T *q_da, *q_db;          // queued particle's converged whole-step trial (NaN: none);
                            // its start state is re-read from the store, which the
                            // fast kernel leaves untouched for queued particles
@@ -171,6 +177,9 @@ cudaError_t launch_guess_target(const GuessArgs &A, const double *er_next, const
 constexpr int kMaxFastBlocks = 152 * 8;
 template <typename T>
 cudaError_t launch_push(const PushLaunchT<T> &L, cudaStream_t s);
+// one resident wave of the persistent push kernels (blocks of 256 threads)
+int push_wave_fp64(int general);
+int push_wave_fp32(int general);
 
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_field_solve(const FieldOp &F, const double *er0, const double *ez0,

@@ -9,4 +9,7 @@
 
 namespace pic {
 template cudaError_t launch_push<float>(const PushLaunchT<float> &L, cudaStream_t s);
+int push_wave_fp32(int general) {
+  return (int)(general ? general_grid<float>() : fast_grid<float>());
+}
 }  // namespace pic

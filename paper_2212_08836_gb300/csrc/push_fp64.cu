@@ -7,4 +7,7 @@
 
 namespace pic {
 template cudaError_t launch_push<double>(const PushLaunchT<double> &L, cudaStream_t s);
+int push_wave_fp64(int general) {
+  return (int)(general ? general_grid<double>() : fast_grid<double>());
+}
 }  // namespace pic

@@ -154,11 +154,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_push_fast(PushL
   if (threadIdx.x == 0) s_qn = 0;
   __syncthreads();
   const long long qoff = (long long)blockIdx.x * L.qseg;
+  const long long n = L.n_dev ? *L.n_dev : L.n;
   long long base = (long long)blockIdx.x * blockDim.x;
-  for (; base < L.n; base += stride) {
+  for (; base < n; base += stride) {
     const long long p = base + threadIdx.x;
     PState<T> cur;
-    load_state(L.p, p, L.n, cur);
+    load_state(L.p, p, n, cur);
     const int c0 = cur.c;
     const T a = cur.a, b = cur.b, w = cur.w;
     T ur = zero, ut = zero, uz = zero;
@@ -217,7 +218,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_push_fast(PushL
         }
       }
       queued = !acc;
-    } else if (L.write && L.oop && p < L.n) {
+    } else if (L.write && L.oop && p < n) {
       L.dst.cell[p] = c0;  // not pushed (absorbed earlier): stays out of the store
     }
     warp_deposit<T>(key, ic, jc, v0, v1, v2, v3, lane, nz, L.ir, L.iz);
@@ -259,7 +260,8 @@ __global__ void __launch_bounds__(256) k_push_general(PushLaunchT<T> L) {
                           L.p.vt[p] * L.cr, L.p.vz[p] * L.cz, L.p.w[p], L.q_da[k], L.q_db[k], tl);
     }
   } else {
-    for (long long k = gtid; k < L.n; k += gstride) {
+    const long long n = L.n_dev ? *L.n_dev : L.n;
+    for (long long k = gtid; k < n; k += gstride) {
       push_general<T, kB>(G, k, L.p.cell[k], L.p.a[k], L.p.b[k], L.p.vr[k] * L.cr,
                           L.p.vt[k] * L.cr, L.p.vz[k] * L.cz, L.p.w[k], (T)NAN, (T)NAN, tl);
     }
@@ -285,11 +287,14 @@ long long general_grid() {
 
 template <typename T>
 cudaError_t launch_push(const PushLaunchT<T> &L, cudaStream_t s) {
-  if (L.n <= 0) return cudaSuccess;
+  // with the count on the device the grids depend only on the capacity, so a
+  // captured launch stays valid while the count changes
+  const long long nsz = L.n_dev ? L.cap : L.n;
+  if (nsz <= 0) return cudaSuccess;
   const int bs = 256;
-  long long nb = (L.n + bs - 1) / bs;
+  long long nb = (nsz + bs - 1) / bs;
   if (L.wbt == (T)0 && L.queue) {
-    long long nf = fast_grid<T>();
+    long long nf = L.fgrid > 0 ? L.fgrid : fast_grid<T>();
     if (nf > kMaxFastBlocks) nf = kMaxFastBlocks;
     if (nf > nb) nf = nb;
     PushLaunchT<T> A = L;
@@ -299,7 +304,7 @@ cudaError_t launch_push(const PushLaunchT<T> &L, cudaStream_t s) {
     // the queue holds the crossing / near-axis particles (a fraction of n);
     // one wave, so the per-block prefix of the segment counts is computed once
     // per resident block
-    long long ng = general_grid<T>();
+    long long ng = L.ggrid > 0 ? L.ggrid : general_grid<T>();
     if (ng > nb) ng = nb;
     k_push_general<T, false><<<(unsigned)ng, bs, 0, s>>>(A);
   } else {
