@@ -263,6 +263,78 @@ def measure(P, torch, dev, cfg, args, dist, D, do_e2e, sample_clocks, local):
     return r
 
 
+def ensemble_configs(P, rank):
+    """16 discharges spanning 64x96..256x384 grids, 1M..16M macro-particles per
+    species, 1-10 Pa, 40-100 MHz, 100-300 V, seeds 100-115 (mixed form)."""
+    cfgs = []
+    order_p = [3, 11, 6, 14, 0, 9, 5, 12, 2, 15, 7, 10, 1, 13, 4, 8]
+    order_f = [9, 2, 13, 5, 15, 0, 7, 11, 4, 14, 1, 8, 12, 3, 10, 6]
+    order_v = [6, 14, 1, 10, 3, 12, 8, 0, 15, 5, 11, 2, 13, 7, 4, 9]
+    for i in range(16):
+        u = i / 15.0
+        nr = int(round((64 + u * 192) / 8.0)) * 8
+        nz = nr * 3 // 2
+        f = 40e6 + order_f[i] / 15.0 * 60e6
+        cfgs.append(P.large_reactor(
+            nr=nr, nz=nz, np_init=int(round((1 + 15 * u) * (1 << 20))),
+            gas_pressure=1.0 + order_p[i] / 15.0 * 9.0, freq=f, dt=1.0 / (400 * f),
+            volt=100.0 + order_v[i] / 15.0 * 200.0, seed=100 + i + 16 * rank,
+            precision=P.PIC_MIXED, capacity_factor=1.5))
+    return cfgs
+
+
+def run_ensemble_form(P, torch, dev, args, rank):
+    cfgs = ensemble_configs(P, rank)
+    mem = []
+    for c in cfgs:
+        pic = P.Pic(c, device=dev, stream=torch.cuda.Stream(device=dev))
+        pic.load_particles()
+        mem.append(pic)
+    torch.cuda.synchronize(dev)
+    E = P.Ensemble(mem)
+    E.step(args.warmup)
+    frac, ms_round = E.tune(rounds=3)
+    E.step(1)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    _, st = E.step(1)
+    pushes = sum(s["pushes"] for s in st)
+    for _ in range(args.steps - 1):
+        _, st = E.step(1)
+        pushes += sum(s["pushes"] for s in st)
+    torch.cuda.synchronize(dev)
+    t_ens = time.perf_counter() - t0
+    # the same discharges one after another (kernel-by-kernel launches, one
+    # wave of the push kernels: the single-run configuration)
+    t_seq, p_seq = 0.0, 0
+    for pic in mem:
+        P.set_graphs(pic, False)
+        pic.step(1)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            _, s1 = pic.step(1)
+            p_seq += s1["pushes"]
+        torch.cuda.synchronize(dev)
+        t_seq += time.perf_counter() - t0
+    npart = sum(c["np_init"] for c in cfgs)
+    out = {"members": len(cfgs), "steps": args.steps,
+           "workload": "16 discharges, grids %dx%d..%dx%d, %.0fM..%.0fM macro-particles/species "
+                       "(%.0fM in all), 1-10 Pa, 40-100 MHz, 100-300 V, seeds 100-115, mixed form"
+                       % (cfgs[0]["nr"], cfgs[0]["nz"], cfgs[-1]["nr"], cfgs[-1]["nz"],
+                          cfgs[0]["np_init"] / 2 ** 20, cfgs[-1]["np_init"] / 2 ** 20,
+                          2 * npart / 2 ** 20),
+           "value": pushes / t_ens, "unit": UNIT, "ms_per_step": t_ens * 1e3 / args.steps,
+           "sequential_value": p_seq / t_seq, "sequential_ms_per_step": t_seq * 1e3 / args.steps,
+           "speedup_vs_sequential": (pushes / t_ens) / (p_seq / t_seq),
+           "tuner": {"push_grid_fraction": frac, "ms_per_round": ms_round},
+           "timing": "host clock around whole ensemble steps (device synchronised)"}
+    E.close()
+    for pic in mem:
+        pic.close()
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -398,6 +470,11 @@ def run_ours(args):
         net.close()
     line["wall_s_per_rf_cycle"] = wall
 
+    # ---- batched ensemble of 16 uneven discharges (mixed form) vs the same
+    # discharges stepped one after another
+    if "ensemble" in forms:
+        line["ensemble"] = run_ensemble_form(P, torch, dev, args, rank)
+
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, secs, npush = cpu_oracle_rate(args.cpu_sample, steps=1)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -421,9 +498,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--np", type=int, default=0, help="macro-particles per species (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--forms", default="plain,mixed,guess",
-                    help="comma list of plain (FP64), mixed (FP32 push) and guess (mixed form "
-                         "with the learned Picard start) to time")
+    ap.add_argument("--forms", default="plain,mixed,guess,ensemble",
+                    help="comma list of plain (FP64), mixed (FP32 push), guess (mixed form "
+                         "with the learned Picard start) and ensemble (16 uneven discharges) "
+                         "to time")
     ap.add_argument("--guess-warmup", type=int, default=400)
     ap.add_argument("--guess-samples", type=int, default=600)
     ap.add_argument("--guess-epochs", type=int, default=1500)
