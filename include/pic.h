@@ -55,6 +55,11 @@ extern "C" {
 #define PIC_MIXED 1        /* FP32 particle state, push and deposit; FP64 field solve,
                               Picard norms, current accumulation and diagnostics */
 
+#define PIC_FIELD_EM 0     /* electromagnetic field model (Eqs. 1-2, CN; the default) */
+#define PIC_FIELD_ES 1     /* electrostatic model (Eq. 8): E = -grad phi, Gauss's law on
+                              the nodes with the charge advanced by continuity (Eq. 3);
+                              H = 0 */
+
 typedef struct pic_ctx pic_ctx; /* opaque; host memory owned by the library */
 
 /* Problem definition, copied at pic_init.  Zero eps/mu select vacuum values. */
@@ -76,6 +81,7 @@ typedef struct pic_config {
   double eps, mu;             /* permittivity / permeability; 0 -> eps0 / mu0 */
   unsigned long long seed;    /* RNG key word (Philox4x64-10) */
   int precision;              /* PIC_FP64 or PIC_MIXED */
+  int field_model;            /* PIC_FIELD_EM or PIC_FIELD_ES */
 } pic_config;
 
 /* Per-step statistics (host struct). */
@@ -166,6 +172,16 @@ int pic_step(pic_ctx *ctx, int nsteps, pic_step_stats *stats);
 int pic_push_deposit(pic_ctx *ctx, const double *er_half_dev, const double *ez_half_dev,
                      double *ir_dev, double *iz_dev, int write,
                      unsigned long long *counters_dev, double *ke_lost_dev);
+
+/* Electrostatic model, Eq. 8 on the same mesh: the potential on the nodes
+ * with phi = phi0 on the powered plate z = 0, 0 on z = L and phi0 (1 - z/L)
+ * across the drive gap at r = R, Gauss's law eps div E = Q on the interior
+ * nodes (i < nr, 0 < j < nz) in the flux form of the electromagnetic scheme.
+ * Q_dev: node charges [(nr+1) x (nz+1)] (device, only interior nodes used);
+ * outputs E_r, E_z in the Yee layouts (device, not aliasing Q).  Solved
+ * directly (DST-I along z, cyclic reduction along r).  Asynchronous.
+ * Errors: PIC_E_CONFIG, PIC_E_CUDA. */
+int pic_es_solve(pic_ctx *ctx, const double *Q_dev, double phi0, double *er_dev, double *ez_dev);
 
 /* Row a4, Eqs. 1-2 in CN form: one implicit field solve.  Inputs E^n, H^n,
  * crossed charges, drive voltages V^n (v0) and V^{n+1} (v1); outputs E^{n+1},

@@ -40,7 +40,8 @@ class Config(C.Structure):
                 ("volt", _D), ("gas_pressure", _D), ("gas_temp", _D), ("n0", _D),
                 ("te_ev", _D), ("ti_ev", _D), ("np_init", _LL), ("capacity_factor", _D),
                 ("picard_tol", _D), ("picard_max", _I), ("mcc_on", _I), ("bz", _D),
-                ("eps", _D), ("mu", _D), ("seed", C.c_ulonglong), ("precision", _I)]
+                ("eps", _D), ("mu", _D), ("seed", C.c_ulonglong), ("precision", _I),
+                ("field_model", _I)]
 
 
 class StepStats(C.Structure):
@@ -113,6 +114,7 @@ def _load_lib():
     L.pic_cnn_train_step.argtypes = [_P, _P, _P, _I, C.c_float, _P]
     L.pic_set_guess.argtypes = [_P, _I, _P]
     L.pic_set_graphs.argtypes = [_P, _I]
+    L.pic_es_solve.argtypes = [_P, _P, _D, _P, _P]
     L.pic_ensemble_create.argtypes = [_P, _I, C.POINTER(_P)]
     L.pic_ensemble_destroy.argtypes = [_P]
     L.pic_ensemble_destroy.restype = None
@@ -133,6 +135,7 @@ def lib():
 
 
 PIC_GUESS_PLAIN, PIC_GUESS_EXTRAP, PIC_GUESS_CNN = 0, 1, 2
+PIC_FIELD_EM, PIC_FIELD_ES = 0, 1
 CNN_IN, CNN_OUT = 14, 2
 
 
@@ -157,7 +160,7 @@ def small_reactor(**kw):
     cfg = dict(nr=32, nz=64, R=0.1, L=0.03, dt=1.0 / (200 * f), freq=f, volt=100.0,
                gas_pressure=2.0, gas_temp=300.0, n0=1e15, te_ev=3.0, ti_ev=0.026,
                np_init=40000, capacity_factor=1.5, picard_tol=1e-8, picard_max=50, mcc_on=1,
-               bz=0.0, eps=0.0, mu=0.0, seed=0, precision=PIC_FP64)
+               bz=0.0, eps=0.0, mu=0.0, seed=0, precision=PIC_FP64, field_model=0)
     cfg.update(kw)
     return cfg
 
@@ -170,7 +173,7 @@ def large_reactor(**kw):
     cfg = dict(nr=256, nz=384, R=0.3, L=0.03, dt=1.0 / (400 * f), freq=f, volt=200.0,
                gas_pressure=2.0, gas_temp=300.0, n0=1e15, te_ev=3.0, ti_ev=0.026,
                np_init=16 * 1024 * 1024, capacity_factor=1.25, picard_tol=1e-8, picard_max=50,
-               mcc_on=1, bz=0.0, eps=0.0, mu=0.0, seed=1, precision=PIC_FP64)
+               mcc_on=1, bz=0.0, eps=0.0, mu=0.0, seed=1, precision=PIC_FP64, field_model=0)
     cfg.update(kw)
     return cfg
 
@@ -227,6 +230,11 @@ class Pic:
                                       counters.data_ptr() if counters is not None else None,
                                       ke_lost.data_ptr() if ke_lost is not None else None),
                "pic_push_deposit")
+
+    def es_solve(self, Q, phi0, er, ez):
+        """Electrostatic fields (Eq. 8) of node charges Q (device tensors)."""
+        _check(lib().pic_es_solve(self._h, Q.data_ptr(), float(phi0), er.data_ptr(),
+                                  ez.data_ptr()), "pic_es_solve")
 
     def field_solve(self, er0, ez0, h0, ir, iz, v0, v1, er1, ez1, h1, src=None):
         _check(lib().pic_field_solve(self._h, er0.data_ptr(), ez0.data_ptr(), h0.data_ptr(),

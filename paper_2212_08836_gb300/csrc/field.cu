@@ -8,19 +8,12 @@
 // Laplacian along z, so a DCT-II along z diagonalises it into nz independent
 // SPD tridiagonal systems along r.  Solve = DCT (FP64 GEMM), Thomas per mode,
 // inverse DCT; then H1 = 2 H_half - H0 and E1 explicitly from Ampere.
+#include <string.h>
+
 #include "pic_internal.cuh"
 
 namespace pic {
 namespace {
-
-__device__ __forceinline__ double rhalf(double dr, int i) { return ((double)i + 0.5) * dr; }
-__device__ __forceinline__ double area_r(double dr, double dz, int i) {
-  return kTwoPi * rhalf(dr, i) * dz;
-}
-__device__ __forceinline__ double area_z(double dr, int i) {
-  if (i == 0) return kPi * (0.5 * dr) * (0.5 * dr);
-  return kTwoPi * ((double)i * dr) * dr;
-}
 
 __global__ void k_half(long long n1, long long n2, const double *er0, const double *ez0,
                        const double *er1, const double *ez1, double *erh, double *ezh) {
@@ -468,6 +461,91 @@ __global__ void __launch_bounds__(256) k_update(FieldOp F, const double *er0, co
   }
 }
 
+// ---------------------------------------------------------------------------
+// electrostatic model (Eq. 8)
+
+__device__ __forceinline__ double es_phi0(const EsOp &E, double phi0) {
+  return E.vd ? E.vd[1] : phi0;
+}
+
+// node potential with the Dirichlet values on the plates and across the gap
+__device__ __forceinline__ double es_node(const EsOp &E, double phi0, int i, int j) {
+  if (j == 0) return phi0;
+  if (j == E.nz) return 0.0;
+  if (i == E.nr) return phi0 * (1.0 - (double)j / E.nz);
+  return E.phi[i * E.M + j - 1];
+}
+
+// rhs of the interior nodes: Q^{n+1} (= Qn - div I) plus the boundary values
+__global__ void __launch_bounds__(256) k_es_rhs(EsOp E, const double *Q, const double *ir,
+                                                const double *iz, double phi0) {
+  phi0 = es_phi0(E, phi0);
+  const int nr = E.nr, nz = E.nz, M = E.M;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nr * M) return;
+  const int i = t / M, j = t - (t / M) * M + 1;
+  double q = Q[i * (nz + 1) + j];
+  if (ir) {
+    // continuity on the node: Q^{n+1} = Q^n - (outward crossed charge)
+    double out = ir[i * (nz + 1) + j] + iz[i * nz + j] - iz[i * nz + j - 1];
+    if (i >= 1) out -= ir[(i - 1) * (nz + 1) + j];
+    q -= out;
+  }
+  const double cR = E.tab[i], cZ = E.tab[2 * nr + i];
+  if (i == nr - 1) q += cR * phi0 * (1.0 - (double)j / nz);
+  if (j == 1) q += cZ * phi0;
+  E.rhs[t] = q;
+}
+
+__global__ void __launch_bounds__(256) k_es_field(EsOp E, double phi0, double *er1, double *ez1,
+                                                  const double *er_it, const double *ez_it,
+                                                  DevCounters *cnt) {
+  phi0 = es_phi0(E, phi0);
+  const int nr = E.nr, nz = E.nz, nz1 = nz + 1;
+  const long long ner = (long long)nr * nz1, nez = (long long)(nr + 1) * nz;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double dn = 0.0, nn = 0.0;
+  if (t < ner) {
+    const int i = (int)(t / nz1), j = (int)(t - (t / nz1) * nz1);
+    double e = -(es_node(E, phi0, i + 1, j) - es_node(E, phi0, i, j)) / E.dr;
+    er1[t] = e;
+    if (er_it && j != 0 && j != nz) {
+      double d = e - er_it[t];
+      dn += d * d;
+      nn += e * e;
+    }
+  }
+  if (t < nez) {
+    const int i = (int)(t / nz), j = (int)(t - (t / nz) * nz);
+    double e = -(es_node(E, phi0, i, j + 1) - es_node(E, phi0, i, j)) / E.dz;
+    ez1[t] = e;
+    if (ez_it && i < nr) {
+      double d = e - ez_it[t];
+      dn += d * d;
+      nn += e * e;
+    }
+  }
+  if (!cnt) return;
+  __shared__ double red[2][8];
+  dn = warp_sum(dn);
+  nn = warp_sum(nn);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    red[0][w] = dn;
+    red[1][w] = nn;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      a += red[0][k];
+      b += red[1][k];
+    }
+    if (a != 0.0) atomicAdd(&cnt->norm[0], a);
+    if (b != 0.0) atomicAdd(&cnt->norm[1], b);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_half_field(const Grid &g, const double *er0, const double *ez0,
@@ -556,6 +634,40 @@ cudaError_t launch_field_solve(const FieldOp &F, const double *er0, const double
   long long n = ner > nez ? ner : nez;
   k_update<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(F, er0, ez0, h0, ir, iz, v0, v1, er1, ez1,
                                                        h1, er_it, ez_it, cnt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_es_solve(const EsOp &E, const double *Q, const double *ir, const double *iz,
+                            double phi0, double *er1, double *ez1, const double *er_it,
+                            const double *ez_it, DevCounters *cnt, cudaStream_t s) {
+  cudaError_t e;
+  if (cnt && (e = cudaMemsetAsync(&cnt->norm[0], 0, 3 * sizeof(double), s)) != cudaSuccess)
+    return e;
+  const int nc = E.nr * E.M;
+  k_es_rhs<<<(nc + 255) / 256, 256, 0, s>>>(E, Q, ir, iz, phi0);
+  dim3 grid((E.M + TM - 1) / TM, (E.nr + TM - 1) / TM);
+  k_gemm<<<grid, 256, 0, s>>>(E.nr, E.M, E.M, E.rhs, E.S, E.hat);
+  // the tridiagonal solves of the modes: the cyclic-reduction kernel on an
+  // operator view with M columns
+  FieldOp V;
+  memset(&V, 0, sizeof(V));
+  V.nr = E.nr;
+  V.nz = E.M;
+  V.n2 = E.n2;
+  V.crc = E.crc;
+  V.hat = E.hat;
+  int mb = 8;
+  while (mb > 1 && (size_t)E.n2 * mb * sizeof(double) > 160 * 1024) mb >>= 1;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_cr, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  k_cr<<<(E.M + mb - 1) / mb, 32 * mb, (size_t)E.n2 * mb * sizeof(double), s>>>(V);
+  k_gemm<<<grid, 256, 0, s>>>(E.nr, E.M, E.M, E.hat, E.S, E.phi);
+  long long ner = (long long)E.nr * (E.nz + 1), nez = (long long)(E.nr + 1) * E.nz;
+  long long n = ner > nez ? ner : nez;
+  k_es_field<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(E, phi0, er1, ez1, er_it, ez_it, cnt);
   return cudaGetLastError();
 }
 

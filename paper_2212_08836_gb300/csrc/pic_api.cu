@@ -49,6 +49,8 @@ struct pic_ctx {
   double *wall_spec;        // wall tallies of a speculative final pass
   double rho_prev;          // last Picard contraction r_k / r_{k-1} observed
   FieldOp F;
+  EsOp es;                  // electrostatic model (field_model == PIC_FIELD_ES)
+  double *qn;               // node charge at the start of the step (ES model)
   DevCounters *cnt;
   uint32_t *cand;           // MCC: null-collision candidates (per-block segments)
   int *cblock;
@@ -101,6 +103,41 @@ namespace {
 
 const double kSigmaCx = 5e-19;
 
+// cyclic-reduction coefficients (the layout k_cr reads) of the tridiagonal
+// matrix with sub-diagonal A[i] (coupling i-1), diagonal B, super-diagonal C,
+// padded to n2 rows with identity; A, B, C are overwritten
+void cr_coeffs(int n2, std::vector<double> &A, std::vector<double> &B, std::vector<double> &Cc,
+               double *co) {
+  int off = 0;
+  for (int s = 1; s < n2; s *= 2) {
+    const int cnt = n2 / (2 * s);
+    for (int k = 0; k < cnt; ++k) {
+      const int i = 2 * s * k + 2 * s - 1;
+      const bool up = i + s < n2;
+      const double al = -A[i] / B[i - s];
+      const double ga = up ? -Cc[i] / B[i + s] : 0.0;
+      co[off + k] = al;
+      co[n2 + off + k] = ga;
+      const double nb = B[i] + al * Cc[i - s] + (up ? ga * A[i + s] : 0.0);
+      A[i] = al * A[i - s];
+      Cc[i] = up ? ga * Cc[i + s] : 0.0;
+      B[i] = nb;
+    }
+    off += cnt;
+  }
+  off = 0;
+  for (int s = n2; s >= 1; s /= 2) {
+    const int cnt = n2 >= 2 * s ? n2 / (2 * s) : 1;
+    for (int k = 0; k < cnt; ++k) {
+      const int j = 2 * s * k + s - 1;
+      co[2 * n2 + off + k] = A[j] / B[j];
+      co[3 * n2 + off + k] = Cc[j] / B[j];
+      co[4 * n2 + off + k] = 1.0 / B[j];
+    }
+    off += cnt;
+  }
+}
+
 double h_sig_el(double eps) {
   double x = eps / 12.0;
   return 1.5e-19 * x / (1.0 + x * x) + 1e-20;
@@ -136,6 +173,7 @@ bool valid(const pic_config *c) {
   if (c->np_init < 0 || !(c->capacity_factor >= 1.0)) return false;
   if (!(c->picard_tol > 0) || c->picard_max < 1) return false;
   if (c->precision != PIC_FP64 && c->precision != PIC_MIXED) return false;
+  if (c->field_model != PIC_FIELD_EM && c->field_model != PIC_FIELD_ES) return false;
   if (c->mcc_on && (!(c->gas_pressure > 0) || !(c->gas_temp > 0))) return false;
   return true;
 }
@@ -204,6 +242,22 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
   x->F.rhs = (double *)K.take(nh * 8);
   x->F.hat = (double *)K.take(nh * 8);
   x->F.hhalf = (double *)K.take(nh * 8);
+  {
+    const int M = nz - 1, n2e = x->F.n2;
+    x->es.nr = nr;
+    x->es.nz = nz;
+    x->es.M = M;
+    x->es.n2 = n2e;
+    x->es.dr = c->R / nr;
+    x->es.dz = c->L / nz;
+    x->es.S = (const double *)K.take((size_t)M * M * 8);
+    x->es.crc = (const double *)K.take((size_t)5 * n2e * M * 8);
+    x->es.tab = (const double *)K.take((size_t)3 * nr * 8);
+    x->es.rhs = (double *)K.take((size_t)nr * M * 8);
+    x->es.hat = (double *)K.take((size_t)nr * M * 8);
+    x->es.phi = (double *)K.take((size_t)nr * M * 8);
+    x->qn = (double *)K.take((size_t)(nr + 1) * (nz + 1) * 8);
+  }
   x->F.tw = (const double2 *)K.take((size_t)nz * 16);
   x->F.pw = (const double2 *)K.take((size_t)nz * 16);
   x->F.rtab = (const double *)K.take((size_t)6 * (nr + 1) * 8);
@@ -537,34 +591,27 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
       Cc[i] = in && i + 1 < nr ? eoff[i + 1] : 0.0;
       B[i] = in ? mass[i] + kz[i] * lam[m] + kdiag[i] : 1.0;
     }
-    int off = 0;
-    for (int s = 1; s < n2; s *= 2) {
-      const int cnt = n2 / (2 * s);
-      for (int k = 0; k < cnt; ++k) {
-        const int i = 2 * s * k + 2 * s - 1;
-        const bool up = i + s < n2;
-        const double al = -A[i] / B[i - s];
-        const double ga = up ? -Cc[i] / B[i + s] : 0.0;
-        co[off + k] = al;
-        co[n2 + off + k] = ga;
-        const double nb = B[i] + al * Cc[i - s] + (up ? ga * A[i + s] : 0.0);
-        A[i] = al * A[i - s];
-        Cc[i] = up ? ga * Cc[i + s] : 0.0;
-        B[i] = nb;
-      }
-      off += cnt;
+    cr_coeffs(n2, A, B, Cc, co);
+  }
+  // electrostatic model: DST-I basis, per-row coefficients, mode coefficients
+  const int M = nz - 1;
+  std::vector<double> Sd((size_t)M * M), et((size_t)3 * nr), ecr((size_t)5 * n2 * M, 0.0);
+  for (int j = 1; j <= M; ++j)
+    for (int m = 1; m <= M; ++m) Sd[(size_t)(j - 1) * M + (m - 1)] = sqrt(2.0 / nz) * sin(kPi * j * m / nz);
+  for (int i = 0; i < nr; ++i) {
+    et[i] = x->eps * (kTwoPi * rh(i) * dz) / dr;                        // cR: face i+1/2
+    et[nr + i] = i >= 1 ? x->eps * (kTwoPi * rh(i - 1) * dz) / dr : 0.0;  // cL: face i-1/2
+    et[2 * nr + i] = x->eps * az(i) / dz;                               // cZ
+  }
+  for (int m = 1; m <= M; ++m) {
+    const double lm = 2.0 - 2.0 * cos(kPi * m / nz);
+    for (int i = 0; i < n2; ++i) {
+      bool in = i < nr;
+      A[i] = in && i >= 1 ? -et[nr + i] : 0.0;
+      Cc[i] = in && i + 1 < nr ? -et[i] : 0.0;
+      B[i] = in ? et[i] + et[nr + i] + et[2 * nr + i] * lm : 1.0;
     }
-    off = 0;
-    for (int s = n2; s >= 1; s /= 2) {
-      const int cnt = n2 >= 2 * s ? n2 / (2 * s) : 1;
-      for (int k = 0; k < cnt; ++k) {
-        const int j = 2 * s * k + s - 1;
-        co[2 * n2 + off + k] = A[j] / B[j];
-        co[3 * n2 + off + k] = Cc[j] / B[j];
-        co[4 * n2 + off + k] = 1.0 / B[j];
-      }
-      off += cnt;
-    }
+    cr_coeffs(n2, A, B, Cc, ecr.data() + (size_t)(m - 1) * 5 * n2);
   }
   // twiddles, DCT phases and per-row reciprocal tables
   std::vector<double> tw((size_t)2 * nz), pw((size_t)2 * nz), rt((size_t)6 * (nr + 1), 0.0);
@@ -596,10 +643,14 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
   up(F.Q, Q.data(), Q.size() * 8);
   up(F.QT, QT.data(), QT.size() * 8);
   up(F.crc, cr.data(), cr.size() * 8);
+  up(x->es.S, Sd.data(), Sd.size() * 8);
+  up(x->es.tab, et.data(), et.size() * 8);
+  up(x->es.crc, ecr.data(), ecr.size() * 8);
   size_t ner = (size_t)nr * (nz + 1), nez = (size_t)(nr + 1) * nz, nh = (size_t)nr * nz;
   if (e == cudaSuccess) e = cudaMemsetAsync(x->er, 0, ner * 8, x->s);
   if (e == cudaSuccess) e = cudaMemsetAsync(x->ez, 0, nez * 8, x->s);
   if (e == cudaSuccess) e = cudaMemsetAsync(x->h, 0, nh * 8, x->s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(x->h2, 0, nh * 8, x->s);
   if (e == cudaSuccess) e = cudaMemsetAsync(x->wall, 0, (size_t)2 * (2 * (nr + 1) + nz + 1) * 8, x->s);
   if (e == cudaSuccess) e = cudaMemsetAsync(x->cnt, 0, sizeof(DevCounters), x->s);
   if (e == cudaSuccess) e = cudaHostAlloc((void **)&x->hn, 64, cudaHostAllocDefault);
@@ -610,6 +661,7 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
     return PIC_E_CUDA;
   }
   x->F.vd = x->vdev;
+  x->es.vd = x->vdev;
   x->hist_n = 1;
   *out = x;
   return PIC_OK;
@@ -736,6 +788,16 @@ int pic_field_solve(pic_ctx *x, const double *er0, const double *ez0, const doub
   x->launches += 5;
   if (e == cudaSuccess && src)
     e = cudaMemcpyAsync(src, &x->cnt->src, 8, cudaMemcpyDeviceToDevice, x->s);
+  return cuda_rc(e);
+}
+
+int pic_es_solve(pic_ctx *x, const double *Q, double phi0, double *er, double *ez) {
+  if (!x || !Q || !er || !ez) return PIC_E_CONFIG;
+  EsOp E = x->es;
+  E.vd = nullptr;  // the caller's potential
+  cudaError_t e = launch_es_solve(E, Q, nullptr, nullptr, phi0, er, ez, nullptr, nullptr, nullptr,
+                                  x->s);
+  x->launches += 5;
   return cuda_rc(e);
 }
 
@@ -918,10 +980,18 @@ int enqueue_pass(pic_ctx *x, bool spec) {
     r = push_all(x, x->erh, x->ezh, x->ir, x->iz, 0, nullptr, nullptr, nullptr);
   }
   if (r) return r;
-  if (launch_field_solve(x->F, x->er, x->ez, x->h, x->ir, x->iz, 0.0, 0.0, x->er2, x->ez2, x->h2,
-                         x->er1, x->ez1, x->cnt, s) != cudaSuccess)
-    return PIC_E_CUDA;
-  x->launches += 5;
+  if (x->cfg.field_model == PIC_FIELD_ES) {
+    // Q^{n+1} = Q^n - div I, E^{n+1} = -grad phi^{n+1}; H stays zero
+    if (launch_es_solve(x->es, x->qn, x->ir, x->iz, 0.0, x->er2, x->ez2, x->er1, x->ez1, x->cnt,
+                        s) != cudaSuccess)
+      return PIC_E_CUDA;
+    x->launches += 5;
+  } else {
+    if (launch_field_solve(x->F, x->er, x->ez, x->h, x->ir, x->iz, 0.0, 0.0, x->er2, x->ez2,
+                           x->h2, x->er1, x->ez1, x->cnt, s) != cudaSuccess)
+      return PIC_E_CUDA;
+    x->launches += 5;
+  }
   if (cudaMemcpyAsync(x->hn, x->cnt->norm, 3 * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return PIC_E_CUDA;
   return PIC_OK;
@@ -1051,6 +1121,18 @@ int step_begin(pic_ctx *x, StepState &T) {
   T.v0 = volt_at(x, x->step);
   T.v1 = volt_at(x, x->step + 1);
   if (upload_step(x, T.v0, T.v1)) return PIC_E_CUDA;
+  if (x->cfg.field_model == PIC_FIELD_ES) {
+    // node charge of the start of the step (continuity advances it in the passes)
+    const size_t nn = (size_t)(x->g.nr + 1) * (x->g.nz + 1);
+    if (cudaMemsetAsync(x->qn, 0, nn * 8, x->s) != cudaSuccess) return PIC_E_CUDA;
+    for (int sp = 0; sp < 2; ++sp) {
+      const double q = sp == 0 ? -kQE : kQE;
+      cudaError_t e = x->mixed ? launch_node_charge(x->g, as32(cur(x, sp)), x->n[sp], q, x->qn, x->s)
+                               : launch_node_charge(x->g, cur(x, sp), x->n[sp], q, x->qn, x->s);
+      if (e != cudaSuccess) return PIC_E_CUDA;
+    }
+    x->launches += 2;
+  }
   T.used = PIC_GUESS_PLAIN;
   x->feat_now = 0;
   if (x->guess_mode != PIC_GUESS_PLAIN && x->hist_n >= 4) {

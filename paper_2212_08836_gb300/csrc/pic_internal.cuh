@@ -152,6 +152,24 @@ struct PushLaunchT {
                            // its start state is re-read from the store, which the
                            // fast kernel leaves untouched for queued particles
 };
+// Electrostatic field model (Eq. 8) on the same mesh: potential on the
+// nodes, Gauss's law on the interior nodes (i < nr, 0 < j < nz), separable:
+// orthonormal DST-I along z (GEMM), cyclic reduction along r (field.cu)
+struct EsOp {
+  int nr, nz, M, n2;       // M = nz - 1 interior nodes along z; n2 = 2^k >= nr
+  double dr, dz;
+  const double *S;         // M x M: sqrt(2/nz) sin(pi j m / nz), j, m = 1..M
+  const double *crc;       // cyclic-reduction coefficients of mode m in column m - 1
+  const double *tab;       // 3 x nr: eps A_r(i)/dr, eps A_r(i-1)/dr, eps A_z(i)/dz
+  double *rhs, *hat, *phi; // nr x M scratch
+  const double *vd;        // phi0 = vd[1] (V(t^{n+1})) if vd, else the argument
+};
+// E (Yee layouts) of the node charges Q (Q = Qn - div I if ir is given);
+// Picard norms against er_it / ez_it into cnt when cnt is given
+cudaError_t launch_es_solve(const EsOp &E, const double *Q, const double *ir, const double *iz,
+                            double phi0, double *er1, double *ez1, const double *er_it,
+                            const double *ez_it, DevCounters *cnt, cudaStream_t s);
+
 // Picard start of a step (guess.cu)
 struct FieldPair {
   const double *r, *z;  // E_r (nr x (nz+1)), E_z ((nr+1) x nz)
