@@ -440,6 +440,18 @@ def run_ours(args):
                                  "peak_tflops": fp32_peak,
                                  "peak_kind": "FP32: 128 lanes x 152 SMs x 2 x max SM clock"}}}
         wall["mixed"] = tm / args.steps * 1e-3 * steps_per_cycle
+    # ---- electrostatic field model (Eq. 8) on the same reactor, mixed form
+    if "es" in forms:
+        cfge = P.large_reactor(seed=1 + rank, precision=P.PIC_MIXED, field_model=P.PIC_FIELD_ES)
+        if args.np:
+            cfge["np_init"] = args.np
+        re_ = measure(P, torch, dev, cfge, args, dist, D, False, False, local)
+        te, tote = maxsum(re_["t_ms"], re_["pushes"])
+        line["es_form"] = {"value": tote / (te * 1e-3), "unit": UNIT, "ms_per_step": te / args.steps,
+                           "picard_iters": re_["iters"], "gpu_launches": re_["launches"],
+                           "field_model": "electrostatic (Eq. 8), mixed-precision push"}
+        wall["mixed_es"] = te / args.steps * 1e-3 * steps_per_cycle
+
     # ---- learned Picard start (mixed form): trained on the discharge's own fields
     if "guess" in forms:
         from paper_2212_08836_gb300 import guess as GS
@@ -498,8 +510,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--np", type=int, default=0, help="macro-particles per species (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--forms", default="plain,mixed,guess,ensemble",
-                    help="comma list of plain (FP64), mixed (FP32 push), guess (mixed form "
+    ap.add_argument("--forms", default="plain,mixed,es,guess,ensemble",
+                    help="comma list of plain (FP64), mixed (FP32 push), es (electrostatic "
+                         "model), guess (mixed form "
                          "with the learned Picard start) and ensemble (16 uneven discharges) "
                          "to time")
     ap.add_argument("--guess-warmup", type=int, default=400)
