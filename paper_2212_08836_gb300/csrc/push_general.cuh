@@ -29,6 +29,11 @@ struct Num<float> {
   // fast in-cell solve: estimated error below half an ulp of the displacement
   static constexpr float fast_rel = 6e-8f, fast_abs = 1e-12f;
   __device__ static __forceinline__ float rcp(float x) { return __fdividef(1.f, x); }
+  // 0 < x < 1 on the bits (positive floats order like their bit patterns)
+  __device__ static __forceinline__ bool in01(float x) {
+    const int b = __float_as_int(x);
+    return b > 0 && b < 0x3F800000;
+  }
   // NaN test on the bits (independent of fast-math compilation)
   __device__ static __forceinline__ bool nan_bits(float x) {
     return (__float_as_uint(x) & 0x7fffffffu) > 0x7f800000u;
@@ -60,6 +65,11 @@ struct Num<double> {
     y = fma(y, e, y);
     e = fma(-x, y, 1.0);
     return fma(y, e, y);
+  }
+  // 0 < x < 1 with integer compares (no FP64 instruction); exact, NaN excluded
+  __device__ static __forceinline__ bool in01(double x) {
+    const long long b = __double_as_longlong(x);
+    return b > 0 && b < 0x3FF0000000000000LL;
   }
   __device__ static __forceinline__ bool nan_bits(double x) {
     return ((unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull) >

@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_push_fast(PushL
       else if (jc >= nz) { ic += 1; jc -= nz; }
       const T rho = (T)ic + a;
       bool acc = false;
-      if (a > zero && a < one && b > zero && b < one && fabs(ut) < q * rho) {
+      if (Num<T>::in01(a) && Num<T>::in01(b) && fabs(ut) < q * rho) {
         const T ar0 = L.ar[ic * nz1 + jc];
         const T gar = L.ar[ic * nz1 + jc + 1] - ar0;
         const T az0 = L.az[ic * nz + jc];
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_push_fast(PushL
           trial = true;
           e = zb + q * gaz * d;
           const T a1 = a + d, b1 = b + e;
-          acc = a1 > zero && a1 < one && b1 > zero && b1 < one;
+          acc = Num<T>::in01(a1) && Num<T>::in01(b1);
           if (acc) {
             n_acc++;
             const T qw = L.qf * w;
