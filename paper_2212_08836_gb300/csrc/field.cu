@@ -461,6 +461,37 @@ __global__ void __launch_bounds__(256) k_update(FieldOp F, const double *er0, co
   }
 }
 
+// orthonormal DST-I of rows 2b, 2b+1 of src (nr x M, M = N - 1) into dst, by the
+// 2N-point FFT of the odd extensions y_j = x_j, y_{2N-j} = -x_j, y_0 = y_N = 0:
+// DFT(y)_m = -2i X_m, so with z = y_A + i y_B, X_A = -Im Z / 2, X_B = Re Z / 2
+__global__ void __launch_bounds__(128) k_dst1(FieldOp V, int nrows, int M,
+                                              const double *__restrict__ src,
+                                              double *__restrict__ dst) {
+  extern __shared__ double2 smd[];
+  const int N2 = V.fft, N = N2 / 2;
+  double2 *a = smd, *b = smd + N2;
+  const int r0 = 2 * blockIdx.x, r1 = r0 + 1;
+  const bool two = r1 < nrows;
+  for (int j = threadIdx.x; j < N2; j += blockDim.x) {
+    double2 v = make_double2(0.0, 0.0);
+    if (j >= 1 && j <= M) {
+      v = make_double2(src[r0 * M + j - 1], two ? src[r1 * M + j - 1] : 0.0);
+    } else if (j > N) {
+      const int k = N2 - j;
+      v = make_double2(-src[r0 * M + k - 1], two ? -src[r1 * M + k - 1] : 0.0);
+    }
+    a[j] = v;
+  }
+  __syncthreads();
+  const double2 *Z = fft_fwd(V, a, b);
+  const double sc = 0.5 * sqrt(2.0 / N);
+  for (int m = threadIdx.x; m < M; m += blockDim.x) {
+    const double2 z = Z[m + 1];
+    dst[r0 * M + m] = -z.y * sc;
+    if (two) dst[r1 * M + m] = z.x * sc;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // electrostatic model (Eq. 8)
 
@@ -495,6 +526,17 @@ __global__ void __launch_bounds__(256) k_es_rhs(EsOp E, const double *Q, const d
   if (i == nr - 1) q += cR * phi0 * (1.0 - (double)j / nz);
   if (j == 1) q += cZ * phi0;
   E.rhs[t] = q;
+}
+
+__global__ void __launch_bounds__(256) k_es_advance(EsOp E, double *Q, const double *ir,
+                                                    const double *iz) {
+  const int nr = E.nr, nz = E.nz, M = E.M;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nr * M) return;
+  const int i = t / M, j = t - (t / M) * M + 1;
+  double out = ir[i * (nz + 1) + j] + iz[i * nz + j] - iz[i * nz + j - 1];
+  if (i >= 1) out -= ir[(i - 1) * (nz + 1) + j];
+  Q[i * (nz + 1) + j] -= out;
 }
 
 __global__ void __launch_bounds__(256) k_es_field(EsOp E, double phi0, double *er1, double *ez1,
@@ -637,6 +679,13 @@ cudaError_t launch_field_solve(const FieldOp &F, const double *er0, const double
   return cudaGetLastError();
 }
 
+cudaError_t launch_es_advance(const EsOp &E, double *Q, const double *ir, const double *iz,
+                              cudaStream_t s) {
+  const int nc = E.nr * E.M;
+  k_es_advance<<<(nc + 255) / 256, 256, 0, s>>>(E, Q, ir, iz);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_es_solve(const EsOp &E, const double *Q, const double *ir, const double *iz,
                             double phi0, double *er1, double *ez1, const double *er_it,
                             const double *ez_it, DevCounters *cnt, cudaStream_t s) {
@@ -646,7 +695,23 @@ cudaError_t launch_es_solve(const EsOp &E, const double *Q, const double *ir, co
   const int nc = E.nr * E.M;
   k_es_rhs<<<(nc + 255) / 256, 256, 0, s>>>(E, Q, ir, iz, phi0);
   dim3 grid((E.M + TM - 1) / TM, (E.nr + TM - 1) / TM);
-  k_gemm<<<grid, 256, 0, s>>>(E.nr, E.M, E.M, E.rhs, E.S, E.hat);
+  FieldOp D;  // FFT plan of the DST
+  memset(&D, 0, sizeof(D));
+  D.fft = E.fft2;
+  D.nrad = E.nrad;
+  for (int k = 0; k < 16; ++k) D.rad[k] = E.rad[k];
+  D.tw = E.tw2;
+  const unsigned npair = (unsigned)((E.nr + 1) / 2);
+  const size_t dsm = (size_t)2 * E.fft2 * sizeof(double2);
+  static bool dattr = false;
+  if (E.fft2 && !dattr) {
+    cudaFuncSetAttribute(k_dst1, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    dattr = true;
+  }
+  if (E.fft2)
+    k_dst1<<<npair, 128, dsm, s>>>(D, E.nr, E.M, E.rhs, E.hat);
+  else
+    k_gemm<<<grid, 256, 0, s>>>(E.nr, E.M, E.M, E.rhs, E.S, E.hat);
   // the tridiagonal solves of the modes: the cyclic-reduction kernel on an
   // operator view with M columns
   FieldOp V;
@@ -664,7 +729,10 @@ cudaError_t launch_es_solve(const EsOp &E, const double *Q, const double *ir, co
     attr = true;
   }
   k_cr<<<(E.M + mb - 1) / mb, 32 * mb, (size_t)E.n2 * mb * sizeof(double), s>>>(V);
-  k_gemm<<<grid, 256, 0, s>>>(E.nr, E.M, E.M, E.hat, E.S, E.phi);
+  if (E.fft2)
+    k_dst1<<<npair, 128, dsm, s>>>(D, E.nr, E.M, E.hat, E.phi);
+  else
+    k_gemm<<<grid, 256, 0, s>>>(E.nr, E.M, E.M, E.hat, E.S, E.phi);
   long long ner = (long long)E.nr * (E.nz + 1), nez = (long long)(E.nr + 1) * E.nz;
   long long n = ner > nez ? ner : nez;
   k_es_field<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(E, phi0, er1, ez1, er_it, ez_it, cnt);

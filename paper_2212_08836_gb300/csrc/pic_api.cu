@@ -51,6 +51,7 @@ struct pic_ctx {
   FieldOp F;
   EsOp es;                  // electrostatic model (field_model == PIC_FIELD_ES)
   double *qn;               // node charge at the start of the step (ES model)
+  int qn_valid;             // qn carried from the last step (else rebuilt from particles)
   DevCounters *cnt;
   uint32_t *cand;           // MCC: null-collision candidates (per-block segments)
   int *cblock;
@@ -257,6 +258,7 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
     x->es.hat = (double *)K.take((size_t)nr * M * 8);
     x->es.phi = (double *)K.take((size_t)nr * M * 8);
     x->qn = (double *)K.take((size_t)(nr + 1) * (nz + 1) * 8);
+    x->es.tw2 = (const double2 *)K.take((size_t)2 * nz * 16);
   }
   x->F.tw = (const double2 *)K.take((size_t)nz * 16);
   x->F.pw = (const double2 *)K.take((size_t)nz * 16);
@@ -603,6 +605,27 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
     et[nr + i] = i >= 1 ? x->eps * (kTwoPi * rh(i - 1) * dz) / dr : 0.0;  // cL: face i-1/2
     et[2 * nr + i] = x->eps * az(i) / dz;                               // cZ
   }
+  // FFT plan of the DST-I (2 nz points) when 2 nz = 4^a 2^b 3^c <= 8192
+  x->es.fft2 = 0;
+  x->es.nrad = 0;
+  std::vector<double> tw2((size_t)4 * nz);
+  {
+    int n = 2 * nz, k = 0;
+    int rad[16];
+    while (n % 4 == 0 && k < 16) { rad[k++] = 4; n /= 4; }
+    while (n % 2 == 0 && k < 16) { rad[k++] = 2; n /= 2; }
+    while (n % 3 == 0 && k < 16) { rad[k++] = 3; n /= 3; }
+    if (n == 1 && 2 * nz <= 8192) {
+      x->es.fft2 = 2 * nz;
+      x->es.nrad = k;
+      for (int q = 0; q < k; ++q) x->es.rad[q] = rad[q];
+    }
+    for (int q = 0; q < 2 * nz; ++q) {
+      double t = -kTwoPi * (double)q / (2.0 * nz);
+      tw2[2 * q] = cos(t);
+      tw2[2 * q + 1] = sin(t);
+    }
+  }
   for (int m = 1; m <= M; ++m) {
     const double lm = 2.0 - 2.0 * cos(kPi * m / nz);
     for (int i = 0; i < n2; ++i) {
@@ -646,6 +669,7 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
   up(x->es.S, Sd.data(), Sd.size() * 8);
   up(x->es.tab, et.data(), et.size() * 8);
   up(x->es.crc, ecr.data(), ecr.size() * 8);
+  up(x->es.tw2, tw2.data(), tw2.size() * 8);
   size_t ner = (size_t)nr * (nz + 1), nez = (size_t)(nr + 1) * nz, nh = (size_t)nr * nz;
   if (e == cudaSuccess) e = cudaMemsetAsync(x->er, 0, ner * 8, x->s);
   if (e == cudaSuccess) e = cudaMemsetAsync(x->ez, 0, nez * 8, x->s);
@@ -759,6 +783,7 @@ int pic_load_particles(pic_ctx *x) {
   x->next_id[0] = x->next_id[1] = (uint32_t)n;
   x->hist_n = 1;
   x->sample_valid = 0;
+  x->qn_valid = 0;
   return pic_sort(x);
 }
 
@@ -1121,8 +1146,8 @@ int step_begin(pic_ctx *x, StepState &T) {
   T.v0 = volt_at(x, x->step);
   T.v1 = volt_at(x, x->step + 1);
   if (upload_step(x, T.v0, T.v1)) return PIC_E_CUDA;
-  if (x->cfg.field_model == PIC_FIELD_ES) {
-    // node charge of the start of the step (continuity advances it in the passes)
+  if (x->cfg.field_model == PIC_FIELD_ES && !x->qn_valid) {
+    // node charge of the particles, once; the steps then carry it by continuity
     const size_t nn = (size_t)(x->g.nr + 1) * (x->g.nz + 1);
     if (cudaMemsetAsync(x->qn, 0, nn * 8, x->s) != cudaSuccess) return PIC_E_CUDA;
     for (int sp = 0; sp < 2; ++sp) {
@@ -1132,6 +1157,7 @@ int step_begin(pic_ctx *x, StepState &T) {
       if (e != cudaSuccess) return PIC_E_CUDA;
     }
     x->launches += 2;
+    x->qn_valid = 1;
   }
   T.used = PIC_GUESS_PLAIN;
   x->feat_now = 0;
@@ -1179,6 +1205,11 @@ int step_end(pic_ctx *x, StepState &T, int *rc) {
     int r = push_all(x, x->erh, x->ezh, x->ir, x->iz, 1, x->cnt->push, &x->cnt->ke_lost, x->wall);
     if (r) return r;
     S.pushes += x->n[0] + x->n[1];
+  }
+  if (x->cfg.field_model == PIC_FIELD_ES) {
+    // Q^{n+1} = Q^n - div I of the committed step (ionization pairs are neutral)
+    if (launch_es_advance(x->es, x->qn, x->ir, x->iz, s) != cudaSuccess) return PIC_E_CUDA;
+    x->launches += 1;
   }
   double *t;
   t = x->er; x->er = x->er1; x->er1 = t;
@@ -1331,6 +1362,7 @@ int pic_set_counts(pic_ctx *x, long long ne, long long ni, uint32_t nide, uint32
   x->next_id[0] = nide;
   x->next_id[1] = nidi;
   x->step = step;
+  x->qn_valid = 0;
   return PIC_OK;
 }
 

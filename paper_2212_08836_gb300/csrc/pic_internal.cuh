@@ -163,9 +163,16 @@ struct EsOp {
   const double *tab;       // 3 x nr: eps A_r(i)/dr, eps A_r(i-1)/dr, eps A_z(i)/dz
   double *rhs, *hat, *phi; // nr x M scratch
   const double *vd;        // phi0 = vd[1] (V(t^{n+1})) if vd, else the argument
+  // FFT path (fft2 = 2 nz = 2^a 3^b): the DST-I of two rows as one 2nz-point
+  // complex FFT of their odd extensions; else the GEMM with S
+  int fft2, nrad, rad[16];
+  const double2 *tw2;      // exp(-2 pi i k / (2 nz))
 };
 // E (Yee layouts) of the node charges Q (Q = Qn - div I if ir is given);
 // Picard norms against er_it / ez_it into cnt when cnt is given
+// Q -= div I on the interior nodes (the charge carried to the next step)
+cudaError_t launch_es_advance(const EsOp &E, double *Q, const double *ir, const double *iz,
+                              cudaStream_t s);
 cudaError_t launch_es_solve(const EsOp &E, const double *Q, const double *ir, const double *iz,
                             double phi0, double *er1, double *ez1, const double *er_it,
                             const double *ez_it, DevCounters *cnt, cudaStream_t s);
