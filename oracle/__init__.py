@@ -71,7 +71,7 @@ class Cfg(C.Structure):
                 ("dt", _D), ("freq", _D), ("volt", _D), ("eps", _D), ("mu", _D), ("bz", _D),
                 ("tol", _D), ("kmax", _I), ("mcc_on", _I), ("ng", _D), ("tg", _D),
                 ("numax_e", _D), ("pnull_e", _D), ("pnull_i", _D), ("gmax", _D),
-                ("seed", _U)]
+                ("seed", _U), ("cblock", _D)]
 
 
 class Stats(C.Structure):
@@ -105,7 +105,7 @@ def _declare(L):
     L.oracle_sort.argtypes = [_I, _L] + [_P] * 8
     L.oracle_sort.restype = _L
     L.oracle_step.argtypes = [C.POINTER(Cfg), _P, _U, C.POINTER(Species), _I, _P, _P, _P, _P,
-                              _P, _P, C.POINTER(Stats)]
+                              _P, _P, C.POINTER(Stats), _P]
     L.oracle_step.restype = _I
 
 
@@ -296,13 +296,18 @@ class Sim:
 
     def __init__(self, grid: Grid, dt, *, freq=0.0, volt=0.0, tol=1e-8, kmax=50, bz=0.0,
                  mcc_on=False, ng=0.0, tg=300.0, seed=0, eps=EPS0, mu=MU0, numax=None,
-                 gmax=None, cap=None, species=None, charges=(-QE, QE), masses=(ME, M_AR)):
+                 gmax=None, cap=None, species=None, charges=(-QE, QE), masses=(ME, M_AR),
+                 cblock=0.0):
+        """cblock: blocking capacitor [F] in series with the generator (Eq. 6),
+        0 = the electrode follows V(t); its state is self.circ = [q^n, phi^n]."""
         self.grid = grid
         self.cfg = Cfg()
         c = self.cfg
         c.nr, c.nz, c.dr, c.dz, c.R, c.L = grid.nr, grid.nz, grid.dr, grid.dz, grid.R, grid.L
         c.dt, c.freq, c.volt, c.eps, c.mu, c.bz = dt, freq, volt, eps, mu, bz
         c.tol, c.kmax, c.mcc_on, c.ng, c.tg, c.seed = tol, kmax, 1 if mcc_on else 0, ng, tg, seed
+        c.cblock = cblock
+        self.circ = np.zeros(2)
         if mcc_on:
             me, mi = masses
             nu_e = numax_e(ng, me) if numax is None else numax
@@ -347,7 +352,7 @@ class Sim:
         st = Stats()
         rc = lib().oracle_step(C.byref(self.cfg), self.field._h, self.step_index, T, len(self.sp),
                                _p(self.er), _p(self.ez), _p(self.h), _p(self.wall_z0),
-                               _p(self.wall_zl), _p(self.wall_r), C.byref(st))
+                               _p(self.wall_zl), _p(self.wall_r), C.byref(st), _p(self.circ))
         for s, d in enumerate(self.sp):
             d["n"] = T[s].n
             d["next_id"] = T[s].next_id

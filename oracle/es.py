@@ -84,3 +84,137 @@ def solve(nr, nz, dr, dz, Q, phi0, eps=EPS0):
     phi[:nr, 1:nz] = x.reshape(nr, M)
     er, ez = fields(phi, dr, dz)
     return phi, er, ez
+
+
+def electrode_charge_flow(nr, nz, dr, dz, ez_new, ez_old, iz, eps=EPS0):
+    """dt times the reactor-side current of Eq. 6: the displacement current
+    plus the crossed charge through the dual faces of the first row of E_z
+    edges above the powered plate (i < nr, j = 1/2), i.e. the integral over
+    the electrode in Eq. 6 on the integral-form mesh."""
+    _, az = _areas(nr, nz, dr, dz)
+    s = 0.0
+    for i in range(nr):
+        s += eps * az[i] * (ez_new[i * nz] - (ez_old[i * nz] if ez_old is not None else 0.0))
+        if iz is not None:
+            s += iz[i * nz]
+    return s
+
+
+def circuit_potential(nr, nz, dr, dz, Q, ez_old, iz, v1, qn, cblock, eps=EPS0):
+    """Electrode potential phi^{n+1} of Eq. 6 with a blocking capacitor cblock
+    between the generator V^{n+1} = v1 and the electrode: the reactor-side
+    charge flow must equal C (V^{n+1} - phi^{n+1}) - q^n.  The field is affine
+    in phi^{n+1}; a solve at v1 and the unit-potential solve fix it."""
+    _, _, eza = solve(nr, nz, dr, dz, Q, v1, eps)
+    _, _, ezu = solve(nr, nz, dr, dz, np.zeros((nr + 1) * (nz + 1)), 1.0, eps)
+    dq = electrode_charge_flow(nr, nz, dr, dz, eza, ez_old, iz, eps)
+    gu = electrode_charge_flow(nr, nz, dr, dz, ezu, None, None, eps)
+    return v1 - (qn + dq) / (cblock + gu)
+
+
+def divergence_out(nr, nz, ir, iz):
+    """Charge leaving each interior node (i < nr, 0 < j < nz) through the dual
+    faces of its edges during the step, (nr+1) x (nz+1) (zero elsewhere)."""
+    ir = np.asarray(ir).reshape(nr, nz + 1)
+    iz = np.asarray(iz).reshape(nr + 1, nz)
+    out = np.zeros((nr + 1, nz + 1))
+    for i in range(nr):
+        for j in range(1, nz):
+            o = ir[i, j] + iz[i, j] - iz[i, j - 1]
+            if i >= 1:
+                o -= ir[i - 1, j]
+            out[i, j] = o
+    return out.ravel()
+
+
+class Sim:
+    """Whole-step oracle of the electrostatic model without collisions: the
+    Picard iteration of the push + deposit (Eqs. 3-4, the oracle's mover)
+    and the Eq. 8 solve for the node charge Q^{n+1,k} = Q^n - div I^k
+    (continuity, Q^n from the particles), the commit push with the half field
+    of the last iteration, and the sort.  With cblock > 0 the electrode
+    potential of every iteration solves Eq. 6 (state self.circ = [q^n, phi^n]);
+    otherwise it is V(t) = volt sin(2 pi freq t)."""
+
+    def __init__(self, grid, dt, *, freq=0.0, volt=0.0, tol=1e-8, kmax=50, eps=EPS0,
+                 cblock=0.0, species=(), charges=None, masses=None, cap=None):
+        import oracle as O
+        self.O = O
+        self.g, self.dt, self.freq, self.volt = grid, dt, freq, volt
+        self.tol, self.kmax, self.eps, self.cblock = tol, kmax, eps, cblock
+        charges = charges or (-O.QE, O.QE)
+        masses = masses or (O.ME, O.M_AR)
+        self.er, self.ez, _ = grid.zeros_fields()
+        self.circ = np.zeros(2)
+        self.step_index = 0
+        self.wall = [np.zeros(2 * (grid.nr + 1)), np.zeros(2 * (grid.nr + 1)),
+                     np.zeros(2 * (grid.nz + 1))]
+        self.sp = []
+        for s, arrs in enumerate(species):
+            n = len(arrs["cell"])
+            capn = cap if cap is not None else max(1, int(n * 1.5) + 16)
+            d = O.empty_species(capn)
+            for k in O.FIELDS:
+                d[k][:n] = arrs[k]
+            self.sp.append({"arr": d, "n": n, "q": charges[s], "m": masses[s]})
+
+    def _view(self, d):
+        return {k: d["arr"][k][: d["n"]] for k in self.O.FIELDS}
+
+    def state(self, s):
+        return {k: v.copy() for k, v in self._view(self.sp[s]).items()}
+
+    def volt_at(self, step):
+        return self.volt * np.sin(2.0 * np.pi * self.freq * step * self.dt)
+
+    def step(self):
+        """Returns (rc, stats dict); rc = -3 when the iteration does not converge."""
+        O, g = self.O, self.g
+        nr, nz = g.nr, g.nz
+        v1 = self.volt_at(self.step_index + 1)
+        Qn = np.zeros(g.n_node)
+        for d in self.sp:
+            O.node_charge(g, d["q"], self._view(d), Qn)
+        er1, ez1 = self.er.copy(), self.ez.copy()
+        if not self.cblock > 0.0:
+            ez1[nr * nz:] = v1 / g.L
+        phi1 = v1
+        conv, res, k = False, 0.0, 0
+        for k in range(self.kmax):
+            erh, ezh = 0.5 * (self.er + er1), 0.5 * (self.ez + ez1)
+            ir, iz = np.zeros(g.n_er), np.zeros(g.n_ez)
+            for d in self.sp:
+                O.push(g, self.dt, d["q"], d["m"], self._view(d), erh, ezh, ir=ir, iz=iz)
+            Q1 = Qn - divergence_out(nr, nz, ir, iz)
+            if self.cblock > 0.0:
+                phi1 = circuit_potential(nr, nz, g.dr, g.dz, Q1, self.ez, iz, v1, self.circ[0],
+                                         self.cblock, self.eps)
+            _, ern, ezn = solve(nr, nz, g.dr, g.dz, Q1, phi1, self.eps)
+            mr = np.ones((nr, nz + 1), bool)
+            mr[:, 0] = mr[:, nz] = False
+            dr_ = (ern - er1)[mr.ravel()]
+            dz_ = (ezn - ez1)[: nr * nz]
+            num = np.sqrt(np.sum(dr_ * dr_) + np.sum(dz_ * dz_))
+            den = np.sqrt(np.sum(ern[mr.ravel()] ** 2) + np.sum(ezn[: nr * nz] ** 2))
+            res = num / max(den, 1e-30)
+            er1, ez1 = ern, ezn
+            if res < self.tol:
+                conv = True
+                break
+        st = {"picard_iters": k + 1 if conv else k, "last_res": res, "converged": conv,
+              "absorbed": 0, "ke_lost": 0.0, "phi": phi1, "ir": ir, "iz": iz}
+        if not conv:
+            return -3, st
+        for s, d in enumerate(self.sp):
+            walls = tuple(w[s * (len(w) // 2):(s + 1) * (len(w) // 2)] for w in self.wall)
+            _, _, cnt, kel = O.push(g, self.dt, d["q"], d["m"], self._view(d), erh, ezh,
+                                    write=True, walls=walls)
+            st["absorbed"] += int(cnt[1])
+            st["ke_lost"] += kel
+        for d in self.sp:
+            d["n"] = O.sort(g, d["arr"], d["n"])
+        self.er, self.ez = er1, ez1
+        if self.cblock > 0.0:
+            self.circ[:] = (self.cblock * (v1 - phi1), phi1)
+        self.step_index += 1
+        return 0, st

@@ -977,6 +977,7 @@ typedef struct {
   int mcc_on;
   double ng, tg, numax_e, pnull_e, pnull_i, gmax;
   uint64_t seed;
+  double cblock;       /* blocking capacitor [F] between generator and electrode (Eq. 6); 0 = none */
 } orc_cfg;
 
 typedef struct {
@@ -990,9 +991,45 @@ typedef struct {
   int64_t mcc[8];
 } orc_stats;
 
+/* Eq. 6 solved for the electrode potential phi^{n+1} of one Picard iteration.
+ * The reactor-side current is the displacement current plus the crossed
+ * charge through the dual faces of the first row of E_z edges above the
+ * powered plate (i < nr, j = 1/2): the integral over the electrode in Eq. 6
+ * on the integral-form mesh.  It must equal the capacitor current
+ * (C (V^{n+1} - phi^{n+1}) - q^n) / dt.  The field solve is affine in the
+ * electrode potential at n+1, so a solve at phi = V^{n+1} and the response to
+ * a unit potential (no charge, no fields at n) give phi^{n+1} directly. */
+static double o_circuit(const orc_cfg *cfg, void *field, const double *er, const double *ez,
+                        const double *h, const double *ir, const double *iz, double phi_n,
+                        double v1, double qn) {
+  int nr = cfg->nr, nz = cfg->nz;
+  size_t ner = (size_t)nr * (nz + 1), nez = (size_t)(nr + 1) * nz, nh = (size_t)nr * nz;
+  og_grid g = {nr, nz, cfg->dr, cfg->dz};
+  double *era = (double *)malloc(sizeof(double) * ner), *eza = (double *)malloc(sizeof(double) * nez);
+  double *ha = (double *)malloc(sizeof(double) * nh);
+  double *zr = (double *)calloc(ner, sizeof(double)), *zz = (double *)calloc(nez, sizeof(double));
+  double *zh = (double *)calloc(nh, sizeof(double));
+  double *eru = (double *)malloc(sizeof(double) * ner), *ezu = (double *)malloc(sizeof(double) * nez);
+  double *hu = (double *)malloc(sizeof(double) * nh);
+  double src;
+  oracle_field_solve(field, er, ez, h, ir, iz, phi_n, v1, cfg->L, era, eza, ha, &src);
+  oracle_field_solve(field, zr, zz, zh, zr, zz, 0.0, 1.0, cfg->L, eru, ezu, hu, &src);
+  double dq = 0.0, gu = 0.0;
+  for (int i = 0; i < nr; ++i) {
+    double ea = cfg->eps * o_area_z(&g, i);
+    dq += ea * (eza[i * nz] - ez[i * nz]) + iz[i * nz];
+    gu += ea * ezu[i * nz];
+  }
+  free(era); free(eza); free(ha); free(zr); free(zz); free(zh); free(eru); free(ezu); free(hu);
+  /* C (V - phi) - q^n = dq + (phi - V) gu */
+  return v1 - (qn + dq) / (cfg->cblock + gu);
+}
+
+/* circ (nullable; used when cfg->cblock > 0): {capacitor charge q^n,
+ * electrode potential phi^n} in, the values at n+1 out after a converged step. */
 int oracle_step(const orc_cfg *cfg, void *field, uint64_t step, orc_species *sp, int nspec,
                 double *er, double *ez, double *h, double *wall_z0, double *wall_zl,
-                double *wall_r, orc_stats *st) {
+                double *wall_r, orc_stats *st, double *circ) {
   int nr = cfg->nr, nz = cfg->nz;
   size_t ner = (size_t)nr * (nz + 1), nez = (size_t)(nr + 1) * nz, nh = (size_t)nr * nz;
   double *er1 = (double *)malloc(sizeof(double) * ner), *ez1 = (double *)malloc(sizeof(double) * nez);
@@ -1004,10 +1041,15 @@ int oracle_step(const orc_cfg *cfg, void *field, uint64_t step, orc_species *sp,
   double v0 = cfg->volt * sin(O_TWO_PI * cfg->freq * t0);
   double v1 = cfg->volt * sin(O_TWO_PI * cfg->freq * t1);
   memset(st, 0, sizeof(*st));
-  /* initial iterate E^{n+1,0} = E^n (unknown edges), prescribed edges at n+1 */
+  const int circ_on = cfg->cblock > 0.0 && circ != NULL;
+  double phi0 = v0, phi1 = v1; /* electrode potential at n and n+1 */
+  if (circ_on) phi0 = circ[1];
+  /* initial iterate E^{n+1,0} = E^n (unknown edges); without a capacitor the
+   * prescribed gap edges take V^{n+1}, with one they keep phi^n */
   memcpy(er1, er, sizeof(double) * ner);
   memcpy(ez1, ez, sizeof(double) * nez);
-  for (int j = 0; j < nz; ++j) ez1[nr * nz + j] = v1 / cfg->L;
+  if (!circ_on)
+    for (int j = 0; j < nz; ++j) ez1[nr * nz + j] = v1 / cfg->L;
   int conv = 0;
   double src = 0.0, res = 0.0;
   int k;
@@ -1020,7 +1062,8 @@ int oracle_step(const orc_cfg *cfg, void *field, uint64_t step, orc_species *sp,
       oracle_push(nr, nz, cfg->dr, cfg->dz, cfg->dt, sp[s].q, sp[s].m, cfg->bz, sp[s].n, sp[s].cell,
                   sp[s].a, sp[s].b, sp[s].vr, sp[s].vt, sp[s].vz, sp[s].w, erh, ezh, ir, iz, 0,
                   NULL, NULL, NULL, NULL, NULL);
-    oracle_field_solve(field, er, ez, h, ir, iz, v0, v1, cfg->L, ern, ezn, h1, &src);
+    if (circ_on) phi1 = o_circuit(cfg, field, er, ez, h, ir, iz, phi0, v1, circ[0]);
+    oracle_field_solve(field, er, ez, h, ir, iz, phi0, phi1, cfg->L, ern, ezn, h1, &src);
     double dn = 0.0, nn = 0.0;
     for (int i = 0; i < nr; ++i)
       for (int j = 1; j < nz; ++j) {
@@ -1061,6 +1104,10 @@ int oracle_step(const orc_cfg *cfg, void *field, uint64_t step, orc_species *sp,
     memcpy(ez, ez1, sizeof(double) * nez);
     memcpy(h, h1, sizeof(double) * nh);
     st->src_energy = src;
+    if (circ_on) {
+      circ[0] = cfg->cblock * (v1 - phi1);
+      circ[1] = phi1;
+    }
     if (cfg->mcc_on && nspec == 2) {
       int mr = oracle_mcc(cfg->seed, step, cfg->ng, cfg->tg, sp[0].m, sp[1].m, cfg->numax_e,
                           cfg->pnull_e, cfg->pnull_i, cfg->gmax, &sp[0].n, sp[0].cap, sp[0].cell,
