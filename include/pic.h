@@ -82,6 +82,10 @@ typedef struct pic_config {
   unsigned long long seed;    /* RNG key word (Philox4x64-10) */
   int precision;              /* PIC_FP64 or PIC_MIXED */
   int field_model;            /* PIC_FIELD_EM or PIC_FIELD_ES */
+  double cblock;              /* blocking capacitor [F] between the generator V(t) and the
+                                 powered electrode (Eq. 6); 0 = none (the electrode is at V(t)) */
+  int ions_fixed;             /* 1: ions stay at their positions (no push, deposit or sort), as in
+                                 the dispersion test of Sec. 3.1; requires mcc_on = 0 */
 } pic_config;
 
 /* Per-step statistics (host struct). */
@@ -104,6 +108,8 @@ typedef struct pic_step_stats {
   int guess;                  /* Picard start used by the last step (PIC_GUESS_* of pic_guess.h) */
   int spec_final;             /* 1: the converged pass wrote the new state (no separate commit push) */
   double first_res;           /* Picard residual after the first iteration of the last step */
+  double v_electrode;         /* powered-electrode potential phi^{n+1} after the last step [V] */
+  double q_cap;               /* blocking-capacitor charge q^{n+1} after the last step [C] */
 } pic_step_stats;
 
 /* Device pointers and sizes of the context's arrays (for parity tests,
@@ -182,6 +188,41 @@ int pic_push_deposit(pic_ctx *ctx, const double *er_half_dev, const double *ez_h
  * directly (DST-I along z, cyclic reduction along r).  Asynchronous.
  * Errors: PIC_E_CONFIG, PIC_E_CUDA. */
 int pic_es_solve(pic_ctx *ctx, const double *Q_dev, double phi0, double *er_dev, double *ez_dev);
+
+/* Blocking capacitor (Eq. 6, cfg.cblock > 0).  Each Picard iteration solves
+ * for the electrode potential phi^{n+1} that makes the reactor-side current
+ * (displacement current plus crossed charge through the dual faces of the
+ * first row of E_z edges above the powered plate, i < nr) equal to the
+ * capacitor current (C (V^{n+1} - phi^{n+1}) - q^n) / dt.  The field solve is
+ * affine in phi^{n+1}, so the equation is solved exactly from the solve at
+ * V^{n+1} and a unit response computed at pic_init (EM) or known in closed
+ * form (ES: the vacuum potential 1 - z/L).  The potential then drives the gap
+ * (EM) or the plate and gap Dirichlet values (ES).  The state starts at
+ * q = 0, phi = V(t) at pic_init and pic_load_particles.
+ * pic_circuit_get: q^n [C] and phi^n [V] (host, nullable); without a
+ * capacitor q = 0 and phi = V(t^n).  Synchronises.
+ * pic_circuit_set: sets them (e.g. to resume a run).  Synchronises.
+ * Errors: PIC_E_CONFIG (set without a capacitor), PIC_E_CUDA. */
+int pic_circuit_get(pic_ctx *ctx, double *q, double *phi);
+int pic_circuit_set(pic_ctx *ctx, double q, double phi);
+
+/* Generator waveform V(t) = sum_k amp[k] sin(2 pi freq[k] t + phase[k]),
+ * t = step * dt, k < n (n <= 64), replacing volt * sin(2 pi freq t) from the
+ * next step on (the sawtooth excitation of Sec. 3.1 is n harmonics with
+ * amp = A/k); n = 0 restores the configured sine.  Errors: PIC_E_CONFIG. */
+int pic_set_drive(pic_ctx *ctx, int n, const double *amp, const double *freq,
+                  const double *phase);
+
+/* Fourier-Bessel coefficients (App. A, Eq. A2) of the context's field E^n
+ * along r at one axial row: c_m = int r f F_m dr / int r F_m^2 dr with
+ * F_m = J_alpha(chi_{alpha,m} r / R), chi_{alpha,m} the m-th zero of J_alpha,
+ * m = 1..nmodes (nmodes <= 64).  alpha = 0: f = E_z on the edges
+ * (i, row + 1/2), i = 0..nr (0 <= row < nz), integrals by the trapezoid rule
+ * on the nodes; alpha = 1: f = E_r on the edges (i + 1/2, row), i < nr
+ * (0 <= row <= nz), midpoint rule.  coef_dev: nmodes doubles (device).
+ * Asynchronous, one kernel; a call with a new (alpha, nmodes) first builds
+ * the basis on the host and synchronises.  Errors: PIC_E_CONFIG, PIC_E_CUDA. */
+int pic_fourier_bessel(pic_ctx *ctx, int alpha, int row, int nmodes, double *coef_dev);
 
 /* Row a4, Eqs. 1-2 in CN form: one implicit field solve.  Inputs E^n, H^n,
  * crossed charges, drive voltages V^n (v0) and V^{n+1} (v1); outputs E^{n+1},

@@ -32,7 +32,9 @@ extern "C" {
 typedef struct pic_ensemble pic_ensemble;
 
 /* Replays the Picard passes of ctx from captured CUDA graphs (on = 1) or
- * launches them kernel by kernel (on = 0, the default). */
+ * launches them kernel by kernel (on = 0, the default).  Capture needs a
+ * created stream: a context on the legacy default stream (stream 0) always
+ * launches kernel by kernel. */
 int pic_set_graphs(pic_ctx *ctx, int on);
 
 /* n members (1..PIC_ENSEMBLE_MAX), distinct, each ready to step; turns graph

@@ -137,9 +137,13 @@ class Sim:
     otherwise it is V(t) = volt sin(2 pi freq t)."""
 
     def __init__(self, grid, dt, *, freq=0.0, volt=0.0, tol=1e-8, kmax=50, eps=EPS0,
-                 cblock=0.0, species=(), charges=None, masses=None, cap=None):
+                 cblock=0.0, species=(), charges=None, masses=None, cap=None, drive=None,
+                 fixed=()):
+        """drive: optional V(t) replacing volt sin(2 pi freq t); fixed: indices of
+        species that stay in place (not pushed, deposited or sorted)."""
         import oracle as O
         self.O = O
+        self.drive, self.fixed = drive, tuple(fixed)
         self.g, self.dt, self.freq, self.volt = grid, dt, freq, volt
         self.tol, self.kmax, self.eps, self.cblock = tol, kmax, eps, cblock
         charges = charges or (-O.QE, O.QE)
@@ -165,6 +169,8 @@ class Sim:
         return {k: v.copy() for k, v in self._view(self.sp[s]).items()}
 
     def volt_at(self, step):
+        if self.drive is not None:
+            return self.drive(step * self.dt)
         return self.volt * np.sin(2.0 * np.pi * self.freq * step * self.dt)
 
     def step(self):
@@ -183,8 +189,9 @@ class Sim:
         for k in range(self.kmax):
             erh, ezh = 0.5 * (self.er + er1), 0.5 * (self.ez + ez1)
             ir, iz = np.zeros(g.n_er), np.zeros(g.n_ez)
-            for d in self.sp:
-                O.push(g, self.dt, d["q"], d["m"], self._view(d), erh, ezh, ir=ir, iz=iz)
+            for s, d in enumerate(self.sp):
+                if s not in self.fixed:
+                    O.push(g, self.dt, d["q"], d["m"], self._view(d), erh, ezh, ir=ir, iz=iz)
             Q1 = Qn - divergence_out(nr, nz, ir, iz)
             if self.cblock > 0.0:
                 phi1 = circuit_potential(nr, nz, g.dr, g.dz, Q1, self.ez, iz, v1, self.circ[0],
@@ -206,13 +213,16 @@ class Sim:
         if not conv:
             return -3, st
         for s, d in enumerate(self.sp):
+            if s in self.fixed:
+                continue
             walls = tuple(w[s * (len(w) // 2):(s + 1) * (len(w) // 2)] for w in self.wall)
             _, _, cnt, kel = O.push(g, self.dt, d["q"], d["m"], self._view(d), erh, ezh,
                                     write=True, walls=walls)
             st["absorbed"] += int(cnt[1])
             st["ke_lost"] += kel
-        for d in self.sp:
-            d["n"] = O.sort(g, d["arr"], d["n"])
+        for s, d in enumerate(self.sp):
+            if s not in self.fixed:
+                d["n"] = O.sort(g, d["arr"], d["n"])
         self.er, self.ez = er1, ez1
         if self.cblock > 0.0:
             self.circ[:] = (self.cblock * (v1 - phi1), phi1)

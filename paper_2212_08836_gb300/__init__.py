@@ -41,7 +41,7 @@ class Config(C.Structure):
                 ("te_ev", _D), ("ti_ev", _D), ("np_init", _LL), ("capacity_factor", _D),
                 ("picard_tol", _D), ("picard_max", _I), ("mcc_on", _I), ("bz", _D),
                 ("eps", _D), ("mu", _D), ("seed", C.c_ulonglong), ("precision", _I),
-                ("field_model", _I)]
+                ("field_model", _I), ("cblock", _D), ("ions_fixed", _I)]
 
 
 class StepStats(C.Structure):
@@ -49,7 +49,7 @@ class StepStats(C.Structure):
                 ("ke_lost", _D), ("de_coll", _D), ("substep_err", _LL), ("absorbed", _LL),
                 ("substeps", _LL), ("fallbacks", _LL), ("mcc", _LL * 8), ("n", _LL * 2),
                 ("pushes", _LL), ("launches", _LL), ("push_flops", _LL), ("guess", _I),
-                ("spec_final", _I), ("first_res", _D)]
+                ("spec_final", _I), ("first_res", _D), ("v_electrode", _D), ("q_cap", _D)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("mcc", "n")}
@@ -115,6 +115,10 @@ def _load_lib():
     L.pic_set_guess.argtypes = [_P, _I, _P]
     L.pic_set_graphs.argtypes = [_P, _I]
     L.pic_es_solve.argtypes = [_P, _P, _D, _P, _P]
+    L.pic_circuit_get.argtypes = [_P, _P, _P]
+    L.pic_circuit_set.argtypes = [_P, _D, _D]
+    L.pic_set_drive.argtypes = [_P, _I, _P, _P, _P]
+    L.pic_fourier_bessel.argtypes = [_P, _I, _I, _I, _P]
     L.pic_ensemble_create.argtypes = [_P, _I, C.POINTER(_P)]
     L.pic_ensemble_destroy.argtypes = [_P]
     L.pic_ensemble_destroy.restype = None
@@ -160,7 +164,8 @@ def small_reactor(**kw):
     cfg = dict(nr=32, nz=64, R=0.1, L=0.03, dt=1.0 / (200 * f), freq=f, volt=100.0,
                gas_pressure=2.0, gas_temp=300.0, n0=1e15, te_ev=3.0, ti_ev=0.026,
                np_init=40000, capacity_factor=1.5, picard_tol=1e-8, picard_max=50, mcc_on=1,
-               bz=0.0, eps=0.0, mu=0.0, seed=0, precision=PIC_FP64, field_model=0)
+               bz=0.0, eps=0.0, mu=0.0, seed=0, precision=PIC_FP64, field_model=0, cblock=0.0,
+               ions_fixed=0)
     cfg.update(kw)
     return cfg
 
@@ -173,7 +178,8 @@ def large_reactor(**kw):
     cfg = dict(nr=256, nz=384, R=0.3, L=0.03, dt=1.0 / (400 * f), freq=f, volt=200.0,
                gas_pressure=2.0, gas_temp=300.0, n0=1e15, te_ev=3.0, ti_ev=0.026,
                np_init=16 * 1024 * 1024, capacity_factor=1.25, picard_tol=1e-8, picard_max=50,
-               mcc_on=1, bz=0.0, eps=0.0, mu=0.0, seed=1, precision=PIC_FP64, field_model=0)
+               mcc_on=1, bz=0.0, eps=0.0, mu=0.0, seed=1, precision=PIC_FP64, field_model=0,
+               cblock=0.0, ions_fixed=0)
     cfg.update(kw)
     return cfg
 
@@ -242,6 +248,32 @@ class Pic:
                                      er1.data_ptr(), ez1.data_ptr(), h1.data_ptr(),
                                      src.data_ptr() if src is not None else None),
                "pic_field_solve")
+
+    def circuit(self):
+        """(q^n, phi^n): blocking-capacitor charge and electrode potential."""
+        q, phi = _D(0.0), _D(0.0)
+        _check(lib().pic_circuit_get(self._h, C.addressof(q), C.addressof(phi)), "pic_circuit_get")
+        return q.value, phi.value
+
+    def set_circuit(self, q, phi):
+        _check(lib().pic_circuit_set(self._h, float(q), float(phi)), "pic_circuit_set")
+
+    def set_drive(self, amp=(), freq=(), phase=()):
+        """V(t) = sum_k amp[k] sin(2 pi freq[k] t + phase[k]); empty restores the sine."""
+        n = len(amp)
+        A, Fq, Ph = (_D * max(n, 1))(*amp), (_D * max(n, 1))(*freq), (_D * max(n, 1))(*phase)
+        _check(lib().pic_set_drive(self._h, n, C.addressof(A), C.addressof(Fq), C.addressof(Ph)),
+               "pic_set_drive")
+
+    def fourier_bessel(self, alpha, row, nmodes, out=None):
+        """Fourier-Bessel coefficients (Eq. A2) of E_z (alpha 0) or E_r (alpha 1) at
+        one axial row of E^n, into the device tensor ``out`` (allocated if None)."""
+        t = self.torch
+        if out is None:
+            out = t.empty(nmodes, dtype=t.float64, device=self.device)
+        _check(lib().pic_fourier_bessel(self._h, int(alpha), int(row), int(nmodes),
+                                        out.data_ptr()), "pic_fourier_bessel")
+        return out
 
     def mcc(self, step):
         counts = (_LL * 8)()

@@ -92,6 +92,7 @@ __global__ void k_rhs(FieldOp F, const double *er0, const double *ez0, const dou
     v0 = F.vd[0];
     v1 = F.vd[1];
   }
+  if (F.cc.st) v0 = F.cc.st[2];  // the electrode potential phi^n
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   int nz = F.nz;
   if (F.half) {
@@ -382,7 +383,19 @@ __device__ __forceinline__ double hhalf_at(const FieldOp &F, int i, int j) {
   return P[i * h + jj] - R[i * h + jj];
 }
 
-// H1 = 2 H_half - H0; E1 from Ampere; Picard norms and drive-gap energy
+// H^{n+1/2} with the circuit's correction: the solve ran with the electrode
+// at V^{n+1}; the actual potential differs by dl, whose response is hu / 2
+__device__ __forceinline__ double hh_at(const FieldOp &F, double dl, int i, int j) {
+  double v = hhalf_at(F, i, j);
+  if (F.cc.st) v += dl * (0.5 * F.cc.hu[i * F.nz + j]);
+  return v;
+}
+
+// H1 = 2 H_half - H0; E1 from Ampere; Picard norms and drive-gap energy.
+// With the blocking capacitor, Eq. 6 fixes the electrode potential first:
+// Ampere's law summed over the first row of E_z edges (i < nr) telescopes, so
+// dt x the reactor-side current is dt 2 pi r_{nr-1/2} H^{n+1/2}(nr-1/2, 1/2),
+// affine in the potential; every thread evaluates the same expression.
 __global__ void __launch_bounds__(256) k_update(FieldOp F, const double *er0, const double *ez0,
                                                 const double *h0, const double *ir,
                                                 const double *iz, double v0, double v1,
@@ -398,9 +411,22 @@ __global__ void __launch_bounds__(256) k_update(FieldOp F, const double *er0, co
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double dn = 0.0, nn = 0.0, src = 0.0;
   double dz = F.dz, dt = F.dt;
+  double dl = 0.0;
+  if (F.cc.st) {
+    v0 = F.cc.st[2];
+    const double s = dt * tab(F, kTs, nr - 1);
+    const double q0 = s * hhalf_at(F, nr - 1, 0);          // electrode at V^{n+1}
+    const double gu = s * (0.5 * F.cc.hu[(nr - 1) * nz]);   // per unit potential
+    dl = -(F.cc.st[0] + q0) / (F.cc.C + gu);
+    if (t == 0) {
+      F.cc.st[1] = dl;
+      F.cc.st[3] = q0 + gu * dl;
+    }
+    v1 += dl;
+  }
   if (t < nh) {
     int i = (int)(t / nz), j = (int)(t - (t / nz) * nz);
-    h1[t] = 2.0 * hhalf_at(F, i, j) - h0[t];
+    h1[t] = 2.0 * hh_at(F, dl, i, j) - h0[t];
   }
   if (t < ner) {
     int i = (int)(t / nz1), j = (int)(t - (t / nz1) * nz1);
@@ -408,7 +434,7 @@ __global__ void __launch_bounds__(256) k_update(FieldOp F, const double *er0, co
       er1[t] = 0.0;
     } else {
       double s = tab(F, kTs, i);
-      double ch = -s * hhalf_at(F, i, j) + s * hhalf_at(F, i, j - 1);
+      double ch = -s * hh_at(F, dl, i, j) + s * hh_at(F, dl, i, j - 1);
       double e1 = er0[t] + (dt * ch - ir[t]) * tab(F, kTear, i);
       er1[t] = e1;
       if (er_it) {
@@ -421,8 +447,8 @@ __global__ void __launch_bounds__(256) k_update(FieldOp F, const double *er0, co
   if (t < nez) {
     int i = (int)(t / nz), j = (int)(t - (t / nz) * nz);
     double ch = 0.0;
-    if (i <= nr - 1) ch += tab(F, kTs, i) * hhalf_at(F, i, j);
-    if (i >= 1) ch += -tab(F, kTs, i - 1) * hhalf_at(F, i - 1, j);
+    if (i <= nr - 1) ch += tab(F, kTs, i) * hh_at(F, dl, i, j);
+    if (i >= 1) ch += -tab(F, kTs, i - 1) * hh_at(F, dl, i - 1, j);
     if (i == nr) {
       ez1[t] = v1 / F.L;
       double eh = 0.5 * (v0 + v1) / F.L;
@@ -499,12 +525,46 @@ __device__ __forceinline__ double es_phi0(const EsOp &E, double phi0) {
   return E.vd ? E.vd[1] : phi0;
 }
 
-// node potential with the Dirichlet values on the plates and across the gap
-__device__ __forceinline__ double es_node(const EsOp &E, double phi0, int i, int j) {
+// node potential with the Dirichlet values on the plates and across the gap;
+// dl: the circuit's correction of the electrode potential (phi0 includes it),
+// whose response is the vacuum solution dl (1 - z/L)
+__device__ __forceinline__ double es_node(const EsOp &E, double phi0, double dl, int i, int j) {
   if (j == 0) return phi0;
   if (j == E.nz) return 0.0;
   if (i == E.nr) return phi0 * (1.0 - (double)j / E.nz);
-  return E.phi[i * E.M + j - 1];
+  return E.phi[i * E.M + j - 1] + dl * (1.0 - (double)j / E.nz);
+}
+
+// Eq. 6 with the blocking capacitor: dt x the reactor-side current through the
+// dual faces of the first row of E_z edges (i < nr), displacement plus crossed
+// charge, for the solve at V^{n+1}; the response per unit potential is the
+// closed-form vacuum value cr.  One block, fixed summation order.
+__global__ void __launch_bounds__(256) k_es_circuit(EsOp E, const double *iz, double phi0) {
+  phi0 = es_phi0(E, phi0);
+  const int nr = E.nr, nz = E.nz;
+  double v = 0.0;
+  for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+    const double ea = E.tab[2 * nr + i];  // eps A_z(i) / dz
+    const double ez1 = (phi0 - E.phi[i * E.M]) / E.dz;
+    v += ea * E.dz * (ez1 - E.ez0[i * nz]) + iz[i * nz];
+  }
+  __shared__ double red[8];
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double q0 = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) q0 += red[k];
+    const double dl = -(E.cc.st[0] + q0) / (E.cc.C + E.cc.cr);
+    E.cc.st[1] = dl;
+    E.cc.st[3] = q0 + E.cc.cr * dl;
+  }
+}
+
+__global__ void k_circuit_commit(Circuit c, const double *vd) {
+  const double phi1 = vd[1] + c.st[1];
+  c.st[0] = c.C * (vd[1] - phi1);
+  c.st[2] = phi1;
 }
 
 // rhs of the interior nodes: Q^{n+1} (= Qn - div I) plus the boundary values
@@ -543,13 +603,18 @@ __global__ void __launch_bounds__(256) k_es_field(EsOp E, double phi0, double *e
                                                   const double *er_it, const double *ez_it,
                                                   DevCounters *cnt) {
   phi0 = es_phi0(E, phi0);
+  double dl = 0.0;
+  if (E.cc.st) {
+    dl = E.cc.st[1];
+    phi0 += dl;
+  }
   const int nr = E.nr, nz = E.nz, nz1 = nz + 1;
   const long long ner = (long long)nr * nz1, nez = (long long)(nr + 1) * nz;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double dn = 0.0, nn = 0.0;
   if (t < ner) {
     const int i = (int)(t / nz1), j = (int)(t - (t / nz1) * nz1);
-    double e = -(es_node(E, phi0, i + 1, j) - es_node(E, phi0, i, j)) / E.dr;
+    double e = -(es_node(E, phi0, dl, i + 1, j) - es_node(E, phi0, dl, i, j)) / E.dr;
     er1[t] = e;
     if (er_it && j != 0 && j != nz) {
       double d = e - er_it[t];
@@ -559,7 +624,7 @@ __global__ void __launch_bounds__(256) k_es_field(EsOp E, double phi0, double *e
   }
   if (t < nez) {
     const int i = (int)(t / nz), j = (int)(t - (t / nz) * nz);
-    double e = -(es_node(E, phi0, i, j + 1) - es_node(E, phi0, i, j)) / E.dz;
+    double e = -(es_node(E, phi0, dl, i, j + 1) - es_node(E, phi0, dl, i, j)) / E.dz;
     ez1[t] = e;
     if (ez_it && i < nr) {
       double d = e - ez_it[t];
@@ -679,6 +744,11 @@ cudaError_t launch_field_solve(const FieldOp &F, const double *er0, const double
   return cudaGetLastError();
 }
 
+cudaError_t launch_circuit_commit(const Circuit &c, const double *vd, cudaStream_t s) {
+  k_circuit_commit<<<1, 1, 0, s>>>(c, vd);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_es_advance(const EsOp &E, double *Q, const double *ir, const double *iz,
                               cudaStream_t s) {
   const int nc = E.nr * E.M;
@@ -733,6 +803,7 @@ cudaError_t launch_es_solve(const EsOp &E, const double *Q, const double *ir, co
     k_dst1<<<npair, 128, dsm, s>>>(D, E.nr, E.M, E.hat, E.phi);
   else
     k_gemm<<<grid, 256, 0, s>>>(E.nr, E.M, E.M, E.hat, E.S, E.phi);
+  if (E.cc.st) k_es_circuit<<<1, 256, 0, s>>>(E, iz, phi0);
   long long ner = (long long)E.nr * (E.nz + 1), nez = (long long)(E.nr + 1) * E.nz;
   long long n = ner > nez ? ner : nez;
   k_es_field<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(E, phi0, er1, ez1, er_it, ez_it, cnt);

@@ -117,7 +117,31 @@ __global__ void __launch_bounds__(256) k_node_charge(Grid g, PartsT<T> p, long l
   atomicAdd(&Q[(ic + 1) * nz1 + jc + 1], qw * a * b);
 }
 
+// Fourier-Bessel coefficients (App. A, Eq. A2): block m sums basis row m
+// against the field samples f[k * stride], k < n, in a fixed order
+__global__ void __launch_bounds__(128) k_fourier_bessel(const double *__restrict__ basis,
+                                                        const double *__restrict__ f,
+                                                        int stride, int n,
+                                                        double *__restrict__ coef) {
+  const int m = blockIdx.x;
+  double v = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x)
+    v += basis[(size_t)m * n + k] * f[(size_t)k * stride];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __shared__ double red[4];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) coef[m] = (red[0] + red[1]) + (red[2] + red[3]);
+}
+
 }  // namespace
+
+cudaError_t launch_fourier_bessel(const double *basis, const double *f, int stride, int n,
+                                  int nmodes, double *coef, cudaStream_t s) {
+  k_fourier_bessel<<<nmodes, 128, 0, s>>>(basis, f, stride, n, coef);
+  return cudaGetLastError();
+}
 
 template <typename T>
 cudaError_t launch_load(const Grid &g, long long n, double n0, double te_ev, double ti_ev,

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <chrono>
+#include <cmath>
 #include <vector>
 
 #include "../../include/pic_ensemble.h"
@@ -83,7 +84,15 @@ struct pic_ctx {
   // graph-stable launches: particle counts and drive voltages on the device,
   // Picard passes captured once per buffer configuration and replayed
   long long *n_dev;
-  double *vdev;
+  double *vdev;             // [0..1] V^n, V^{n+1}; [4..7] blocking-capacitor state (Circuit)
+  double *hu;               // EM unit response of the circuit (nr x nz)
+  int circ_on;
+  // generator waveform: sum of harmonics when nharm > 0 (else volt sin(2 pi f t))
+  int nharm;
+  double hamp[64], hfreq[64], hph[64];
+  // Fourier-Bessel basis (App. A) for (fb_alpha, fb_m), 64 x (nr + 1) doubles
+  double *fbb;
+  int fb_alpha, fb_m;
   double *hn;               // pinned host: Picard norms of the last pass
   int graphs;               // 1: passes replayed from captured graphs
   int capturing;            // a pass is being captured (no timing events)
@@ -176,6 +185,9 @@ bool valid(const pic_config *c) {
   if (c->precision != PIC_FP64 && c->precision != PIC_MIXED) return false;
   if (c->field_model != PIC_FIELD_EM && c->field_model != PIC_FIELD_ES) return false;
   if (c->mcc_on && (!(c->gas_pressure > 0) || !(c->gas_temp > 0))) return false;
+  if (!(c->cblock >= 0.0) || !isfinite(c->cblock)) return false;
+  if (c->ions_fixed != 0 && c->ions_fixed != 1) return false;
+  if (c->ions_fixed && c->mcc_on) return false;
   return true;
 }
 
@@ -277,6 +289,8 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
   x->gbad = (int *)K.take(256);
   x->n_dev = (long long *)K.take(256);
   x->vdev = (double *)K.take(256);
+  x->hu = (double *)K.take((size_t)nr * nz * 8);
+  x->fbb = (double *)K.take((size_t)64 * (nr + 1) * 8);
   {
     size_t P = (size_t)(nr + 1) * (nz + 1);
     x->gx = (float *)K.take(P * PIC_CNN_IN * 4);
@@ -311,7 +325,19 @@ Parts32 as32(const Parts &p) {
 
 double volt_at(const pic_ctx *x, long long step) {
   double t = (double)step * x->cfg.dt;
+  if (x->nharm > 0) {
+    double v = 0.0;
+    for (int k = 0; k < x->nharm; ++k) v += x->hamp[k] * sin(kTwoPi * x->hfreq[k] * t + x->hph[k]);
+    return v;
+  }
   return x->cfg.volt * sin(kTwoPi * x->cfg.freq * t);
+}
+
+// circuit state {q, 0, phi, 0} with q = 0 and the electrode at V(t^n)
+cudaError_t circuit_reset(pic_ctx *x) {
+  // pageable source: the call returns once it is staged
+  const double st[4] = {0.0, 0.0, volt_at(x, x->step), 0.0};
+  return cudaMemcpyAsync(x->vdev + 4, st, sizeof(st), cudaMemcpyHostToDevice, x->s);
 }
 
 __global__ void k_fill(double *p, int n, double v) {
@@ -376,7 +402,8 @@ int push_all(pic_ctx *x, const double *erh, const double *ezh, double *ir, doubl
              unsigned long long *counters, double *kel, double *wall, int oop = 0) {
   bool timed = x->prof && x->nev < 128 && !x->capturing;
   if (timed) cudaEventRecord(x->ev[2 * x->nev], x->s);
-  for (int s = 0; s < 2; ++s) {
+  const int nsp = x->cfg.ions_fixed ? 1 : 2;
+  for (int s = 0; s < nsp; ++s) {
     const double q = s == 0 ? -kQE : kQE, m = s == 0 ? kME : kMAr;
     double *ws[3] = {nullptr, nullptr, nullptr};
     if (wall) {
@@ -687,6 +714,30 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
   x->F.vd = x->vdev;
   x->es.vd = x->vdev;
   x->hist_n = 1;
+  x->fb_alpha = -1;
+  if (cfg->cblock > 0.0) {
+    // unit response: H^{n+1} of a unit electrode potential at n+1 with no
+    // fields at n and no charge (fields, H and the crossed charge are zero here)
+    FieldOp U = x->F;
+    U.vd = nullptr;
+    if (e == cudaSuccess) e = cudaMemsetAsync(x->ir, 0, ner * 8, x->s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(x->iz, 0, nez * 8, x->s);
+    if (e == cudaSuccess)
+      e = launch_field_solve(U, x->er, x->ez, x->h, x->ir, x->iz, 0.0, 1.0, x->er2, x->ez2, x->hu,
+                             nullptr, nullptr, x->cnt, x->s);
+    double cr = 0.0;
+    for (int i = 0; i < nr; ++i) cr += x->eps * az(i);
+    x->circ_on = 1;
+    x->F.cc = Circuit{x->vdev + 4, x->hu, cfg->cblock, 0.0};
+    x->es.cc = Circuit{x->vdev + 4, nullptr, cfg->cblock, cr / cfg->L};
+    x->es.ez0 = nullptr;
+    if (e == cudaSuccess) e = circuit_reset(x);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(x->s);
+    if (e != cudaSuccess) {
+      pic_destroy(x);
+      return PIC_E_CUDA;
+    }
+  }
   *out = x;
   return PIC_OK;
 }
@@ -737,7 +788,7 @@ int pic_profile_read(pic_ctx *x, double *push_ms, long long *push_launches) {
 
 int pic_sort(pic_ctx *x) {
   if (!x) return PIC_E_CONFIG;
-  for (int s = 0; s < 2; ++s) {
+  for (int s = 0; s < (x->cfg.ions_fixed ? 1 : 2); ++s) {
     SortLaunch S;
     S.ncell = x->g.nr * x->g.nz;
     S.n = x->n[s];
@@ -784,7 +835,95 @@ int pic_load_particles(pic_ctx *x) {
   x->hist_n = 1;
   x->sample_valid = 0;
   x->qn_valid = 0;
+  if (x->circ_on && circuit_reset(x) != cudaSuccess) return PIC_E_CUDA;
   return pic_sort(x);
+}
+
+int pic_set_drive(pic_ctx *x, int n, const double *amp, const double *freq, const double *phase) {
+  if (!x || n < 0 || n > 64 || (n > 0 && (!amp || !freq || !phase))) return PIC_E_CONFIG;
+  for (int k = 0; k < n; ++k)
+    if (!isfinite(amp[k]) || !isfinite(freq[k]) || !isfinite(phase[k])) return PIC_E_CONFIG;
+  for (int k = 0; k < n; ++k) {
+    x->hamp[k] = amp[k];
+    x->hfreq[k] = freq[k];
+    x->hph[k] = phase[k];
+  }
+  x->nharm = n;
+  return PIC_OK;
+}
+
+// m-th positive zero of J_alpha (alpha = 0, 1): McMahon's asymptotic start,
+// then Newton with J_0' = -J_1, J_1' = J_0 - J_1 / x
+double bessel_zero(int alpha, int m) {
+  const double b = (m + 0.5 * alpha - 0.25) * kPi;
+  const double mu = 4.0 * alpha * alpha;
+  double x = b - (mu - 1.0) / (8.0 * b);
+  for (int it = 0; it < 50; ++it) {
+    const double j = std::cyl_bessel_j((double)alpha, x);
+    const double d = alpha == 0 ? -std::cyl_bessel_j(1.0, x)
+                                : std::cyl_bessel_j(0.0, x) - j / x;
+    const double step = j / d;
+    x -= step;
+    if (fabs(step) < 1e-15 * x) break;
+  }
+  return x;
+}
+
+int pic_fourier_bessel(pic_ctx *x, int alpha, int row, int nmodes, double *coef) {
+  if (!x || !coef || (alpha != 0 && alpha != 1) || nmodes < 1 || nmodes > 64) return PIC_E_CONFIG;
+  const int nr = x->g.nr, nz = x->g.nz;
+  if (alpha == 0 ? (row < 0 || row >= nz) : (row < 0 || row > nz)) return PIC_E_CONFIG;
+  const int n = alpha == 0 ? nr + 1 : nr;
+  if (x->fb_alpha != alpha || x->fb_m != nmodes) {
+    // basis[m][k] = w_k r_k F_m(r_k) / sum_k w_k r_k F_m(r_k)^2 (Eq. A2 by the
+    // trapezoid rule on nodes, alpha = 0, or the midpoint rule, alpha = 1)
+    const double R = x->cfg.R, dr = R / nr;
+    std::vector<double> B((size_t)nmodes * n);
+    for (int m = 0; m < nmodes; ++m) {
+      const double chi = bessel_zero(alpha, m + 1);
+      double den = 0.0;
+      for (int k = 0; k < n; ++k) {
+        const double r = alpha == 0 ? k * dr : (k + 0.5) * dr;
+        const double w = alpha == 0 && (k == 0 || k == nr) ? 0.5 * dr : dr;
+        const double F = std::cyl_bessel_j((double)alpha, chi * r / R);
+        B[(size_t)m * n + k] = w * r * F;
+        den += w * r * F * F;
+      }
+      for (int k = 0; k < n; ++k) B[(size_t)m * n + k] /= den;
+    }
+    if (cudaMemcpyAsync(x->fbb, B.data(), B.size() * 8, cudaMemcpyHostToDevice, x->s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(x->s) != cudaSuccess)
+      return PIC_E_CUDA;
+    x->fb_alpha = alpha;
+    x->fb_m = nmodes;
+  }
+  const double *f = alpha == 0 ? x->ez + row : x->er + row;
+  const int stride = alpha == 0 ? nz : nz + 1;
+  cudaError_t e = launch_fourier_bessel(x->fbb, f, stride, n, nmodes, coef, x->s);
+  x->launches += 1;
+  return cuda_rc(e);
+}
+
+int pic_circuit_get(pic_ctx *x, double *q, double *phi) {
+  if (!x) return PIC_E_CONFIG;
+  double st[4] = {0.0, 0.0, volt_at(x, x->step), 0.0};
+  if (x->circ_on) {
+    if (cudaMemcpyAsync(st, x->vdev + 4, sizeof(st), cudaMemcpyDeviceToHost, x->s) != cudaSuccess)
+      return PIC_E_CUDA;
+    if (cudaStreamSynchronize(x->s) != cudaSuccess) return PIC_E_CUDA;
+  }
+  if (q) *q = st[0];
+  if (phi) *phi = st[2];
+  return PIC_OK;
+}
+
+int pic_circuit_set(pic_ctx *x, double q, double phi) {
+  if (!x || !x->circ_on || !isfinite(q) || !isfinite(phi)) return PIC_E_CONFIG;
+  const double st[4] = {q, 0.0, phi, 0.0};
+  if (cudaMemcpyAsync(x->vdev + 4, st, sizeof(st), cudaMemcpyHostToDevice, x->s) != cudaSuccess)
+    return PIC_E_CUDA;
+  return cudaStreamSynchronize(x->s) == cudaSuccess ? PIC_OK : PIC_E_CUDA;
 }
 
 int pic_push_deposit(pic_ctx *x, const double *erh, const double *ezh, double *ir, double *iz,
@@ -808,6 +947,7 @@ int pic_field_solve(pic_ctx *x, const double *er0, const double *ez0, const doub
   if (!x || !er0 || !ez0 || !h0 || !ir || !iz || !er1 || !ez1 || !h1) return PIC_E_CONFIG;
   FieldOp F = x->F;
   F.vd = nullptr;  // the caller's voltages
+  F.cc = Circuit{};
   cudaError_t e = launch_field_solve(F, er0, ez0, h0, ir, iz, v0, v1, er1, ez1, h1, nullptr,
                                      nullptr, x->cnt, x->s);
   x->launches += 5;
@@ -820,6 +960,7 @@ int pic_es_solve(pic_ctx *x, const double *Q, double phi0, double *er, double *e
   if (!x || !Q || !er || !ez) return PIC_E_CONFIG;
   EsOp E = x->es;
   E.vd = nullptr;  // the caller's potential
+  E.cc = Circuit{};
   cudaError_t e = launch_es_solve(E, Q, nullptr, nullptr, phi0, er, ez, nullptr, nullptr, nullptr,
                                   x->s);
   x->launches += 5;
@@ -929,7 +1070,8 @@ int plain_start(pic_ctx *x, double v1) {
   const size_t ner = (size_t)nr * (nz + 1), nez = (size_t)(nr + 1) * nz;
   cudaError_t e = cudaMemcpyAsync(x->er1, x->er, ner * 8, cudaMemcpyDeviceToDevice, x->s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(x->ez1, x->ez, nez * 8, cudaMemcpyDeviceToDevice, x->s);
-  if (e == cudaSuccess) {
+  // with the blocking capacitor the gap keeps phi^n / L (the start is E^n)
+  if (e == cudaSuccess && !x->circ_on) {
     k_fill<<<(nz + 127) / 128, 128, 0, x->s>>>(x->ez1 + (size_t)nr * nz, nz, v1 / x->cfg.L);
     e = cudaGetLastError();
     x->launches += 1;
@@ -961,6 +1103,13 @@ int guess_start(pic_ctx *x, double v1, int *used) {
   if (launch_guess_apply(A, y, cp, v1 / x->cfg.L, x->er1, x->ez1, x->gbad, x->s) != cudaSuccess)
     return PIC_E_CUDA;
   x->launches += 1;
+  if (x->circ_on) {
+    // the gap edges keep phi^n / L, as in the plain start
+    const size_t g0 = (size_t)x->g.nr * x->g.nz;
+    if (cudaMemcpyAsync(x->ez1 + g0, x->ez + g0, (size_t)x->g.nz * 8, cudaMemcpyDeviceToDevice,
+                        x->s) != cudaSuccess)
+      return PIC_E_CUDA;
+  }
   if (cudaMemcpyAsync(&bad, x->gbad, sizeof(int), cudaMemcpyDeviceToHost, x->s) != cudaSuccess)
     return PIC_E_CUDA;
   if (cudaStreamSynchronize(x->s) != cudaSuccess) return PIC_E_CUDA;
@@ -1007,10 +1156,12 @@ int enqueue_pass(pic_ctx *x, bool spec) {
   if (r) return r;
   if (x->cfg.field_model == PIC_FIELD_ES) {
     // Q^{n+1} = Q^n - div I, E^{n+1} = -grad phi^{n+1}; H stays zero
-    if (launch_es_solve(x->es, x->qn, x->ir, x->iz, 0.0, x->er2, x->ez2, x->er1, x->ez1, x->cnt,
+    EsOp E = x->es;
+    E.ez0 = x->ez;
+    if (launch_es_solve(E, x->qn, x->ir, x->iz, 0.0, x->er2, x->ez2, x->er1, x->ez1, x->cnt,
                         s) != cudaSuccess)
       return PIC_E_CUDA;
-    x->launches += 5;
+    x->launches += x->circ_on ? 6 : 5;
   } else {
     if (launch_field_solve(x->F, x->er, x->ez, x->h, x->ir, x->iz, 0.0, 0.0, x->er2, x->ez2,
                            x->h2, x->er1, x->ez1, x->cnt, s) != cudaSuccess)
@@ -1026,8 +1177,9 @@ int enqueue_pass(pic_ctx *x, bool spec) {
 // time this buffer configuration occurs (counts and voltages are read on the
 // device, grids depend only on capacities)
 int launch_pass(pic_ctx *x, bool spec) {
-  // the first pass runs uncaptured (one-time set-up of launch shapes)
-  if (!x->graphs || x->passes++ == 0) return enqueue_pass(x, spec);
+  // the first pass runs uncaptured (one-time set-up of launch shapes); the
+  // legacy default stream cannot be captured, so its passes are never replayed
+  if (!x->graphs || x->s == nullptr || x->passes++ == 0) return enqueue_pass(x, spec);
   const void *key[12] = {x->er, x->ez, x->h, x->er1, x->ez1, x->er2, x->ez2, x->h2,
                          (const void *)(uintptr_t)x->cur[0], (const void *)(uintptr_t)x->cur[1],
                          (const void *)(uintptr_t)(spec ? 1 : 0), x->erh};
@@ -1190,7 +1342,7 @@ int step_end(pic_ctx *x, StepState &T, int *rc) {
   if (T.spec_ok) {
     // the converged pass already wrote the new state into the second buffer
     x->cur[0] ^= 1;
-    x->cur[1] ^= 1;
+    if (!x->cfg.ions_fixed) x->cur[1] ^= 1;
     const int nwall = 2 * (2 * (nr + 1) + nz + 1);
     k_addto<<<(nwall + 255) / 256, 256, 0, s>>>(x->wall, x->wall_spec, nwall);
     if (cudaGetLastError() != cudaSuccess) return PIC_E_CUDA;
@@ -1205,6 +1357,10 @@ int step_end(pic_ctx *x, StepState &T, int *rc) {
     int r = push_all(x, x->erh, x->ezh, x->ir, x->iz, 1, x->cnt->push, &x->cnt->ke_lost, x->wall);
     if (r) return r;
     S.pushes += x->n[0] + x->n[1];
+  }
+  if (x->circ_on) {
+    if (launch_circuit_commit(x->F.cc, x->vdev, s) != cudaSuccess) return PIC_E_CUDA;
+    x->launches += 1;
   }
   if (x->cfg.field_model == PIC_FIELD_ES) {
     // Q^{n+1} = Q^n - div I of the committed step (ionization pairs are neutral)
@@ -1241,6 +1397,10 @@ int step_end(pic_ctx *x, StepState &T, int *rc) {
   if (sr) return sr;
   unsigned long long pc[5];
   double kel = 0.0;
+  double cst[4] = {0.0, 0.0, T.v1, 0.0};
+  if (x->circ_on &&
+      cudaMemcpyAsync(cst, x->vdev + 4, sizeof(cst), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return PIC_E_CUDA;
   if (cudaMemcpyAsync(pc, x->cnt->push, sizeof(pc), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return PIC_E_CUDA;
   if (cudaMemcpyAsync(&kel, &x->cnt->ke_lost, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
@@ -1253,6 +1413,8 @@ int step_end(pic_ctx *x, StepState &T, int *rc) {
   S.fallbacks = (long long)pc[3];
   S.push_flops = (long long)pc[4];
   S.ke_lost = kel;
+  S.q_cap = cst[0];
+  S.v_electrode = cst[2];
   S.n[0] = x->n[0];
   S.n[1] = x->n[1];
   S.launches = x->launches - T.l0;

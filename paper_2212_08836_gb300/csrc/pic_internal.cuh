@@ -89,6 +89,18 @@ struct DevCounters {
 };
 
 // Field operator (separable direct solve of the H_theta system)
+// Blocking capacitor between the generator and the powered electrode (Eq. 6),
+// state on the device so that captured passes stay valid:
+//   st[0] = capacitor charge q^n, st[1] = phi^{n+1} - V^{n+1} found by the latest
+//   field solve, st[2] = electrode potential phi^n, st[3] = dt x the electrode
+//   current of the latest solve.  st == nullptr: the electrode follows V(t).
+struct Circuit {
+  double *st;
+  const double *hu;  // EM: H^{n+1} response to a unit electrode potential at n+1 (nr x nz)
+  double C;          // capacitance [F]
+  double cr;         // ES: eps sum_{i<nr} A_z(i) / L, the vacuum response of the plate flow
+};
+
 struct FieldOp {
   int nr, nz;
   int half;            // nz/2 when nz is even: even/odd split of the DCT (else 0)
@@ -118,6 +130,7 @@ struct FieldOp {
   // drive voltages V(t^n), V(t^{n+1}) read on the device (vd != nullptr) so
   // that a captured solve stays valid from step to step; else the arguments
   const double *vd;
+  Circuit cc;
 };
 
 // One mover + deposit pass over one species (rows a2, a3, a6) in the scalar
@@ -167,10 +180,18 @@ struct EsOp {
   // complex FFT of their odd extensions; else the GEMM with S
   int fft2, nrad, rad[16];
   const double2 *tw2;      // exp(-2 pi i k / (2 nz))
+  Circuit cc;
+  const double *ez0;       // E_z^n (the plate flow of Eq. 6 with the circuit)
 };
 // E (Yee layouts) of the node charges Q (Q = Qn - div I if ir is given);
 // Picard norms against er_it / ez_it into cnt when cnt is given
 // Q -= div I on the interior nodes (the charge carried to the next step)
+// c[m] = sum_k basis[m n + k] f[k stride], m < nmodes (one block per mode)
+cudaError_t launch_fourier_bessel(const double *basis, const double *f, int stride, int n,
+                                  int nmodes, double *coef, cudaStream_t s);
+// end of a converged step with the circuit: q^{n+1} = C (V^{n+1} - phi^{n+1}),
+// phi^n <- phi^{n+1}
+cudaError_t launch_circuit_commit(const Circuit &c, const double *vd, cudaStream_t s);
 cudaError_t launch_es_advance(const EsOp &E, double *Q, const double *ir, const double *iz,
                               cudaStream_t s);
 cudaError_t launch_es_solve(const EsOp &E, const double *Q, const double *ir, const double *iz,
