@@ -206,6 +206,12 @@ int pic_es_solve(pic_ctx *ctx, const double *Q_dev, double phi0, double *er_dev,
 int pic_circuit_get(pic_ctx *ctx, double *q, double *phi);
 int pic_circuit_set(pic_ctx *ctx, double q, double phi);
 
+/* Picard tolerance and iteration limit of the following steps (the values
+ * of pic_config at pic_init).  A caller may relax them for a step that ends
+ * in PIC_E_NOCONV (the state is then still at step n) and retry it.
+ * Errors: PIC_E_CONFIG (tol <= 0 or not finite, kmax < 1). */
+int pic_set_picard(pic_ctx *ctx, double tol, int kmax);
+
 /* Generator waveform V(t) = sum_k amp[k] sin(2 pi freq[k] t + phase[k]),
  * t = step * dt, k < n (n <= 64), replacing volt * sin(2 pi freq t) from the
  * next step on (the sawtooth excitation of Sec. 3.1 is n harmonics with

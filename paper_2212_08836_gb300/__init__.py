@@ -118,6 +118,7 @@ def _load_lib():
     L.pic_circuit_get.argtypes = [_P, _P, _P]
     L.pic_circuit_set.argtypes = [_P, _D, _D]
     L.pic_set_drive.argtypes = [_P, _I, _P, _P, _P]
+    L.pic_set_picard.argtypes = [_P, _D, _I]
     L.pic_fourier_bessel.argtypes = [_P, _I, _I, _I, _P]
     L.pic_ensemble_create.argtypes = [_P, _I, C.POINTER(_P)]
     L.pic_ensemble_destroy.argtypes = [_P]
@@ -257,6 +258,10 @@ class Pic:
 
     def set_circuit(self, q, phi):
         _check(lib().pic_circuit_set(self._h, float(q), float(phi)), "pic_circuit_set")
+
+    def set_picard(self, tol, kmax):
+        """Picard tolerance and iteration limit of the following steps."""
+        _check(lib().pic_set_picard(self._h, float(tol), int(kmax)), "pic_set_picard")
 
     def set_drive(self, amp=(), freq=(), phase=()):
         """V(t) = sum_k amp[k] sin(2 pi freq[k] t + phase[k]); empty restores the sine."""

@@ -839,6 +839,13 @@ int pic_load_particles(pic_ctx *x) {
   return pic_sort(x);
 }
 
+int pic_set_picard(pic_ctx *x, double tol, int kmax) {
+  if (!x || !(tol > 0.0) || !isfinite(tol) || kmax < 1) return PIC_E_CONFIG;
+  x->cfg.picard_tol = tol;
+  x->cfg.picard_max = kmax;
+  return PIC_OK;
+}
+
 int pic_set_drive(pic_ctx *x, int n, const double *amp, const double *freq, const double *phase) {
   if (!x || n < 0 || n > 64 || (n > 0 && (!amp || !freq || !phase))) return PIC_E_CONFIG;
   for (int k = 0; k < n; ++k)

@@ -53,7 +53,7 @@ def slab_plasma(nr, nz, R, L, n0, ppc, s, te_ev, seed):
 
 
 def run(model="es", nr=64, nz=128, R=0.1, L=0.03, n0=1e16, ppc=64, sheath=1.8e-3, f=106e6,
-        amp=1.0, nharm=20, obs_cycles=64, z_sample=1e-3, nmodes=10, dt=1e-10, mu=0.0,
+        amp=10.0, nharm=20, obs_cycles=64, z_sample=1e-3, nmodes=10, dt=1e-10, mu=0.0,
         te_ev=3.0, seed=0, device="cuda:0", precision=PIC_FP64, tol=1e-7):
     import torch
     fm = PIC_FIELD_ES if model == "es" else PIC_FIELD_EM
@@ -76,11 +76,20 @@ def run(model="es", nr=64, nz=128, R=0.1, L=0.03, n0=1e16, ppc=64, sheath=1.8e-3
     dz = L / nz
     row = int(round(z_sample / dz - 0.5))
     coef = torch.empty((n_obs, nmodes), dtype=torch.float64, device=device)
-    iters, sub_err = [], []
+    iters, sub_err, relaxed = [], [], []
     t0 = time.time()
     for k in range(n_obs):
         # a particle at the sub-step cap is reported (PIC_E_SUBSTEP) and kept
         rc, st = pic.step(1, check=False)
+        t = tol
+        while rc == -3 and t < 1e-3:
+            # the iteration stalls at a small residual (a few particles switch
+            # between sub-step paths): retry the step with a looser tolerance
+            t *= 10.0
+            pic.set_picard(t, 100)
+            rc, st = pic.step(1, check=False)
+            pic.set_picard(tol, 100)
+            relaxed.append((k, t))
         if rc not in (0, -4):
             raise RuntimeError("pic_step failed with %d at step %d (iterations %d, residual %.3g)"
                                % (rc, k, st["picard_iters"], st["last_res"]))
@@ -97,7 +106,8 @@ def run(model="es", nr=64, nz=128, R=0.1, L=0.03, n0=1e16, ppc=64, sheath=1.8e-3
     return {"freqs": freqs, "spectrum": spec.T, "sheath": sheath, "n0": n0, "R": R, "L": L,
             "dz": dz, "row": row, "z_sample": (row + 0.5) * dz, "steps": n_obs, "wall_s": wall,
             "model": model, "mu": mu, "picard_iters_mean": float(np.mean(iters)),
-            "substep_errors": np.array(sub_err, dtype=np.int64).reshape(-1, 2), "coef": c}
+            "substep_errors": np.array(sub_err, dtype=np.int64).reshape(-1, 2), "coef": c,
+            "relaxed": np.array(relaxed, dtype=np.float64).reshape(-1, 2)}
 
 
 def main():
@@ -112,7 +122,8 @@ def main():
     np.savez(a.out, **{k: np.asarray(v) for k, v in r.items()})
     ne = int(r["substep_errors"][:, 1].sum())
     print("model %s: %d steps in %.1f s, %.2f Picard iterations/step, sub-step cap reached %d "
-          "times" % (r["model"], r["steps"], r["wall_s"], r["picard_iters_mean"], ne))
+          "times, %d steps retried with a looser tolerance" %
+          (r["model"], r["steps"], r["wall_s"], r["picard_iters_mean"], ne, len(r["relaxed"])))
 
 
 if __name__ == "__main__":
