@@ -40,7 +40,8 @@ DFMA_PER_CYCLE = 304
 BYTES_PER_PUSH_FP64 = 52
 # ncu DRAM bytes (read + write) per push of the current FP64 kernel, from the
 # profile in profiles/ (None when the kernel changed after the capture)
-TRAFFIC_PER_PUSH = 83.0  # DRAM bytes per push of the FP64 push kernels: ncu dram__bytes_read + write, 4M/species case
+TRAFFIC_PER_PUSH = 82.4  # DRAM bytes per push of the FP64 push kernels: ncu dram__bytes_read + write, 4M/species case
+TRAFFIC_PER_PUSH_FP32 = 45.0  # the same for the FP32 push kernels of the mixed form
 
 
 def peaks():
@@ -180,7 +181,7 @@ def measure(P, torch, dev, cfg, args, dist, D, do_e2e, sample_clocks, local):
     pic.profile(True)
     barrier()
     r = {"pushes": 0, "launches": 0, "iters": [], "flops": 0, "commit_pushes": 0,
-         "bytes": 0}
+         "bytes": 0, "substep_cap": 0}
     clk = ClockSampler(local) if sample_clocks else None
     if clk:
         clk.__enter__()
@@ -198,6 +199,7 @@ def measure(P, torch, dev, cfg, args, dist, D, do_e2e, sample_clocks, local):
         r["iters"].append(k)
         r["flops"] += st["push_flops"]
         r["commit_pushes"] += n_commit
+        r["substep_cap"] += st["substep_err"]
         rb, wb = (28, 24) if cfg["precision"] == P.PIC_MIXED else (52, 48)
         if st["spec_final"]:
             wb += 8  # cell and id (4 B each) written too
@@ -403,7 +405,8 @@ def run_ours(args):
                                    % cfg["np_init"],
                        "l2": "inputs larger than L2 (particle store ~1.9 GB)",
                        "parallelism": "replicas" if ws > 1 else "single GPU",
-                       "picard_iters": r["iters"]},
+                       "picard_iters": r["iters"],
+                       "substep_cap_hits": r["substep_cap"]},
             "clocks": r.get("clocks"),
             "gpu_launches": r["launches"],
             "roofline": roof}
@@ -431,7 +434,8 @@ def run_ours(args):
             "dtype": "f32 particles / f64 fields", "picard_iters": rm["iters"],
             "gpu_launches": rm["launches"],
             "roofline": {"bound": "hbm", "achieved": hbm_m, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                         "frac": hbm_m / pk["hbm_gbs"], "traffic": None,
+                         "frac": hbm_m / pk["hbm_gbs"],
+                         "traffic": TRAFFIC_PER_PUSH_FP32 * ppl if TRAFFIC_PER_PUSH_FP32 else None,
                          "kernel": "k_push_fp32 (mover+deposit, FP32)", "peak_kind": pk_kind,
                          "bytes_per_push": "28 read (+24 written in the commit pass)",
                          "avg_launch_ms": alm, "launches": rm["push_launches"],

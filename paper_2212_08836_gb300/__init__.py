@@ -225,9 +225,13 @@ class Pic:
         _check(lib().pic_load_particles(self._h), "pic_load_particles")
 
     def step(self, n=1, check=True):
+        """Advances n steps; returns (status, statistics of the last step).
+        check: raise on every error except PIC_E_SUBSTEP, which the library
+        reports after completing the step (a particle stopped at the sub-step
+        cap, counted in ``substep_err``); the status is returned either way."""
         st = StepStats()
         rc = lib().pic_step(self._h, int(n), C.byref(st))
-        if check:
+        if check and rc != PIC_E_SUBSTEP:
             _check(rc, "pic_step")
         return rc, st.as_dict()
 
@@ -520,7 +524,7 @@ class Ensemble:
     def step(self, n=1, check=True):
         st = (StepStats * len(self.members))()
         rc = lib().pic_ensemble_step(self._h, int(n), st)
-        if check:
+        if check and rc != PIC_E_SUBSTEP:  # non-fatal, as in Pic.step
             _check(rc, "pic_ensemble_step")
         return rc, [s.as_dict() for s in st]
 
