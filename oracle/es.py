@@ -23,10 +23,23 @@ import numpy as np
 EPS0 = 8.8541878128e-12
 
 
-def _areas(nr, nz, dr, dz):
-    ar = 2.0 * np.pi * (np.arange(nr) + 0.5) * dr * dz           # faces (i+1/2), i < nr
-    az = 2.0 * np.pi * np.arange(nr + 1) * dr * dr                # node rings
-    az[0] = np.pi * (0.5 * dr) ** 2
+def radii(nr, dr, xa=0):
+    """Node radii r_i, cell centres r_{i+1/2} and cell widths of the mesh:
+    uniform (xa = 0), or mapped with r = 2 dr sqrt(xa xi) for xi <= xa and
+    dr (xi + xa) beyond, linear within each cell (Sec. 2.1)."""
+    i = np.arange(nr + 1, dtype=np.float64)
+    rn = np.where(i < xa, 2.0 * dr * np.sqrt(xa * i), (i + xa) * dr)
+    rc = 0.5 * (rn[:-1] + rn[1:])
+    return rn, rc, np.diff(rn)
+
+
+def _areas(nr, nz, dr, dz, xa=0):
+    rn, rc, _ = radii(nr, dr, xa)
+    ar = 2.0 * np.pi * rc * dz                                    # faces (i+1/2), i < nr
+    az = np.empty(nr + 1)
+    az[0] = np.pi * rc[0] ** 2                                    # axis disc
+    az[1:nr] = np.pi * (rc[1:] ** 2 - rc[:-1] ** 2)               # rings between centres
+    az[nr] = np.pi * (rn[nr] ** 2 - rc[nr - 1] ** 2)
     return ar, az
 
 
@@ -38,19 +51,21 @@ def boundary_phi(nr, nz, phi0):
     return phi
 
 
-def fields(phi, dr, dz):
+def fields(phi, dr, dz, xa=0):
     """Yee-layout E_r (nr x (nz+1)) and E_z ((nr+1) x nz) of node potentials."""
-    er = -(phi[1:, :] - phi[:-1, :]) / dr
+    _, _, w = radii(phi.shape[0] - 1, dr, xa)
+    er = -(phi[1:, :] - phi[:-1, :]) / w[:, None]
     ez = -(phi[:, 1:] - phi[:, :-1]) / dz
     return er.ravel(), ez.ravel()
 
 
-def solve(nr, nz, dr, dz, Q, phi0, eps=EPS0):
+def solve(nr, nz, dr, dz, Q, phi0, eps=EPS0, xa=0):
     """Potential and fields for node charges Q ((nr+1) x (nz+1), only interior
     nodes used) and powered-plate potential phi0."""
     import scipy.sparse as sp
     import scipy.sparse.linalg as spla
-    ar, az = _areas(nr, nz, dr, dz)
+    ar, az = _areas(nr, nz, dr, dz, xa)
+    wr = radii(nr, dr, xa)[2]
     Q = np.asarray(Q, dtype=np.float64).reshape(nr + 1, nz + 1)
     phi = boundary_phi(nr, nz, phi0)
     M = nz - 1
@@ -61,9 +76,9 @@ def solve(nr, nz, dr, dz, Q, phi0, eps=EPS0):
         for j in range(1, nz):
             k = idx(i, j)
             # eps * sum of outward fluxes of -grad phi = Q  ->  coefficients of phi
-            terms = [(i + 1, j, eps * ar[i] / dr)]
+            terms = [(i + 1, j, eps * ar[i] / wr[i])]
             if i >= 1:
-                terms.append((i - 1, j, eps * ar[i - 1] / dr))
+                terms.append((i - 1, j, eps * ar[i - 1] / wr[i - 1]))
             terms.append((i, j + 1, eps * az[i] / dz))
             terms.append((i, j - 1, eps * az[i] / dz))
             diag = 0.0
@@ -82,16 +97,16 @@ def solve(nr, nz, dr, dz, Q, phi0, eps=EPS0):
     A = sp.csr_matrix((vals, (rows, cols)), shape=(nr * M, nr * M))
     x = spla.spsolve(A.tocsc(), rhs)
     phi[:nr, 1:nz] = x.reshape(nr, M)
-    er, ez = fields(phi, dr, dz)
+    er, ez = fields(phi, dr, dz, xa)
     return phi, er, ez
 
 
-def electrode_charge_flow(nr, nz, dr, dz, ez_new, ez_old, iz, eps=EPS0):
+def electrode_charge_flow(nr, nz, dr, dz, ez_new, ez_old, iz, eps=EPS0, xa=0):
     """dt times the reactor-side current of Eq. 6: the displacement current
     plus the crossed charge through the dual faces of the first row of E_z
     edges above the powered plate (i < nr, j = 1/2), i.e. the integral over
     the electrode in Eq. 6 on the integral-form mesh."""
-    _, az = _areas(nr, nz, dr, dz)
+    _, az = _areas(nr, nz, dr, dz, xa)
     s = 0.0
     for i in range(nr):
         s += eps * az[i] * (ez_new[i * nz] - (ez_old[i * nz] if ez_old is not None else 0.0))
@@ -100,15 +115,15 @@ def electrode_charge_flow(nr, nz, dr, dz, ez_new, ez_old, iz, eps=EPS0):
     return s
 
 
-def circuit_potential(nr, nz, dr, dz, Q, ez_old, iz, v1, qn, cblock, eps=EPS0):
+def circuit_potential(nr, nz, dr, dz, Q, ez_old, iz, v1, qn, cblock, eps=EPS0, xa=0):
     """Electrode potential phi^{n+1} of Eq. 6 with a blocking capacitor cblock
     between the generator V^{n+1} = v1 and the electrode: the reactor-side
     charge flow must equal C (V^{n+1} - phi^{n+1}) - q^n.  The field is affine
     in phi^{n+1}; a solve at v1 and the unit-potential solve fix it."""
-    _, _, eza = solve(nr, nz, dr, dz, Q, v1, eps)
-    _, _, ezu = solve(nr, nz, dr, dz, np.zeros((nr + 1) * (nz + 1)), 1.0, eps)
-    dq = electrode_charge_flow(nr, nz, dr, dz, eza, ez_old, iz, eps)
-    gu = electrode_charge_flow(nr, nz, dr, dz, ezu, None, None, eps)
+    _, _, eza = solve(nr, nz, dr, dz, Q, v1, eps, xa)
+    _, _, ezu = solve(nr, nz, dr, dz, np.zeros((nr + 1) * (nz + 1)), 1.0, eps, xa)
+    dq = electrode_charge_flow(nr, nz, dr, dz, eza, ez_old, iz, eps, xa)
+    gu = electrode_charge_flow(nr, nz, dr, dz, ezu, None, None, eps, xa)
     return v1 - (qn + dq) / (cblock + gu)
 
 
@@ -195,8 +210,8 @@ class Sim:
             Q1 = Qn - divergence_out(nr, nz, ir, iz)
             if self.cblock > 0.0:
                 phi1 = circuit_potential(nr, nz, g.dr, g.dz, Q1, self.ez, iz, v1, self.circ[0],
-                                         self.cblock, self.eps)
-            _, ern, ezn = solve(nr, nz, g.dr, g.dz, Q1, phi1, self.eps)
+                                         self.cblock, self.eps, g.xa)
+            _, ern, ezn = solve(nr, nz, g.dr, g.dz, Q1, phi1, self.eps, g.xa)
             mr = np.ones((nr, nz + 1), bool)
             mr[:, 0] = mr[:, nz] = False
             dr_ = (ern - er1)[mr.ravel()]

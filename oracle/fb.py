@@ -13,24 +13,27 @@ import numpy as np
 from scipy import special as sp
 
 
-def basis_points(nr, R, alpha):
+def basis_points(nr, R, alpha, xa=0):
     """Sample radii and quadrature weights of int_0^R dr (.) for a field with
-    Bessel order alpha (0: nodes, trapezoid; 1: half nodes, midpoint)."""
-    dr = R / nr
+    Bessel order alpha (0: nodes, trapezoid; 1: cell centres, midpoint), on
+    the uniform mesh or the mapped one (xa > 0, r = 2 dr sqrt(xa xi) for
+    xi <= xa, dr (xi + xa) beyond, dr = R / (nr + xa))."""
+    dr = R / (nr + xa)
+    i = np.arange(nr + 1, dtype=np.float64)
+    rn = np.where(i < xa, 2.0 * dr * np.sqrt(xa * i), (i + xa) * dr)
+    h = np.diff(rn)
     if alpha == 0:
-        r = np.arange(nr + 1) * dr
-        w = np.full(nr + 1, dr)
-        w[0] = w[-1] = 0.5 * dr
-    else:
-        r = (np.arange(nr) + 0.5) * dr
-        w = np.full(nr, dr)
-    return r, w
+        w = np.zeros(nr + 1)
+        w[:-1] += 0.5 * h
+        w[1:] += 0.5 * h
+        return rn, w
+    return 0.5 * (rn[:-1] + rn[1:]), h
 
 
-def coefficients(f, nr, R, alpha, nmodes):
-    """c_m, m = 1..nmodes, of f sampled at basis_points(nr, R, alpha):
+def coefficients(f, nr, R, alpha, nmodes, xa=0):
+    """c_m, m = 1..nmodes, of f sampled at basis_points(nr, R, alpha, xa):
     c_m = int r f F_m dr / int r F_m^2 dr, F_m = J_alpha(chi_{alpha,m} r / R)."""
-    r, w = basis_points(nr, R, alpha)
+    r, w = basis_points(nr, R, alpha, xa)
     chi = sp.jn_zeros(alpha, nmodes)
     F = sp.jv(alpha, np.outer(chi, r) / R)
     num = F @ (w * r * np.asarray(f, dtype=np.float64))

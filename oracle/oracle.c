@@ -12,7 +12,8 @@
  * Plain, serial, slow on purpose.  Compile with -ffp-contract=off so that no
  * multiply-add is fused (the GPU FP64 parity build uses --fmad=false).
  *
- * Conventions (uniform logical mesh, Sec. 2.1 with r = xi*dr, z = eta*dz):
+ * Conventions (mesh uniform in the logical coordinates, Sec. 2.1: z = eta*dz,
+ * r = xi*dr, or the mapped r(xi) of o_rnode with xa > 0):
  *   nodes (i,j), i=0..nr, j=0..nz;  cells (i,j) i<nr, j<nz
  *   Er edge (i+1/2, j): Er[i*(nz+1)+j], i<nr, j<=nz      (Yee, Eq. 2)
  *   Ez edge (i, j+1/2): Ez[i*nz+j],     i<=nr, j<nz
@@ -96,29 +97,57 @@ static void o_gauss2(double ua, double ub, double *g1, double *g2) {
 /* ------------------------------------------------------------- geometry */
 typedef struct {
   int nr, nz;
-  double dr, dz;
+  double dr, dz; /* dr: radial spacing of the uniformly spaced part of the mesh */
+  int xa;        /* mapped mesh: the first xa cells have r proportional to sqrt(xi) */
 } og_grid;
 
-static double o_rhalf(const og_grid *g, int i) { return ((double)i + 0.5) * g->dr; }
-static double o_rnode(const og_grid *g, int i) { return (double)i * g->dr; }
-/* dual-face areas of Yee edges (integral form of Ampere, Eq. 2) */
+/* Radial mapping (Sec. 2.1, the mapped mesh): r(xi) = 2 dr sqrt(xa xi) for
+ * xi <= xa and dr (xi + xa) beyond, continuous with its slope at xi = xa, so
+ * that r J_r = 2 dr^2 xa near the axis; xa = 0 is the uniform mesh r = xi dr.
+ * Within a cell r is linear in xi (J_r constant per cell). */
+static double o_rnode(const og_grid *g, int i) {
+  if (i < g->xa) return 2.0 * g->dr * sqrt((double)g->xa * (double)i);
+  return ((double)i + (double)g->xa) * g->dr;
+}
+/* cell width J_r and r at the cell centre */
+static double o_drc(const og_grid *g, int i) {
+  return i < g->xa ? o_rnode(g, i + 1) - o_rnode(g, i) : g->dr;
+}
+static double o_rhalf(const og_grid *g, int i) {
+  if (i < g->xa) return 0.5 * (o_rnode(g, i) + o_rnode(g, i + 1));
+  return ((double)i + 0.5 + (double)g->xa) * g->dr;
+}
+/* r at the inner face of cell i in units of its width */
+static double o_rho0(const og_grid *g, int i) {
+  return i < g->xa ? o_rnode(g, i) / o_drc(g, i) : (double)(i + g->xa);
+}
+/* dual-face areas of Yee edges (integral form of Ampere, Eq. 2): E_r edge
+ * (i+1/2, j): the cylinder 2 pi r_{i+1/2} dz; E_z edge (i, j+1/2): the ring
+ * between the neighbouring cell centres */
 static double o_area_r(const og_grid *g, int i) { return O_TWO_PI * o_rhalf(g, i) * g->dz; }
 static double o_area_z(const og_grid *g, int i) {
-  if (i == 0) return O_PI * (0.5 * g->dr) * (0.5 * g->dr);
+  if (i == 0) return O_PI * o_rhalf(g, 0) * o_rhalf(g, 0);
+  if (i <= g->xa) {
+    double ro = o_rhalf(g, i), ri = o_rhalf(g, i - 1);
+    return O_PI * (ro * ro - ri * ri);
+  }
   return O_TWO_PI * o_rnode(g, i) * g->dr;
 }
 /* primal-cell volume carrying H_theta */
-static double o_vol_h(const og_grid *g, int i) { return O_TWO_PI * o_rhalf(g, i) * g->dr * g->dz; }
+static double o_vol_h(const og_grid *g, int i) {
+  return O_TWO_PI * o_rhalf(g, i) * o_drc(g, i) * g->dz;
+}
 
 /* ------------------------------------------------------------ particles */
 /* Particle loading (a1): pair loading at identical positions, uniform in the
  * logical coordinates, weight proportional to r*J_r (Sec. 2.1), Maxwellian
  * velocities.  Electron p and ion p share position and weight, so the initial
  * node charge vanishes and E = 0, H = 0 is a Gauss-consistent start. */
-void oracle_load(int nr, int nz, double dr, double dz, double R, double L, double n0,
+void oracle_load(int nr, int nz, double dr, double dz, int xa, double R, double L, double n0,
                  int64_t n, double te_ev, double ti_ev, double me, double mi, uint64_t seed,
                  int32_t *cell, double *a, double *b, double *vre, double *vte, double *vze,
                  double *vri, double *vti, double *vzi, double *w, uint32_t *id) {
+  og_grid g = {nr, nz, dr, dz, xa};
   double vthe = sqrt(te_ev * O_QE / me);
   double vthi = sqrt(ti_ev * O_QE / mi);
   for (int64_t p = 0; p < n; ++p) {
@@ -133,7 +162,13 @@ void oracle_load(int nr, int nz, double dr, double dz, double R, double L, doubl
     cell[p] = ic * nz + jc;
     a[p] = xi - (double)ic;
     b[p] = eta - (double)jc;
-    w[p] = n0 * (O_TWO_PI * (xi * dr)) * R * L / (double)n;
+    if (xa == 0) {
+      w[p] = n0 * (O_TWO_PI * (xi * dr)) * R * L / (double)n;
+    } else {  /* w proportional to r J_r */
+      double Jr = o_drc(&g, ic);
+      double r = (o_rho0(&g, ic) + a[p]) * Jr;
+      w[p] = n0 * (O_TWO_PI * r) * (Jr * (double)nr) * L / (double)n;
+    }
     id[p] = (uint32_t)p;
     double g1, g2, g3, g4;
     o_draw4(seed, O_STREAM_LOAD_VE, (uint64_t)p, O_LOAD_STEP, 0, u);
@@ -145,7 +180,7 @@ void oracle_load(int nr, int nz, double dr, double dz, double R, double L, doubl
     o_gauss2(u[2], u[3], &g3, &g4);
     vri[p] = vthi * g1; vti[p] = vthi * g2; vzi[p] = vthi * g3;
   }
-  (void)dz;
+  (void)R;
 }
 
 /* ---------------------------------------------------------------- mover */
@@ -309,6 +344,7 @@ static int o_solve_landing(const o_sub *s, int dir, double X, double dt0, double
 typedef struct {
   int nr, nz;
   double dr, dz;
+  og_grid g;             /* the mesh (radial mapping) */
   const double *er, *ez;
   double *ir, *iz;       /* may be NULL */
   double q, qm, wb;
@@ -377,12 +413,12 @@ static int o_push_one(o_push *P, int *pic, int *pjc, double *pa, double *pb, dou
     s.ger = P->er[ic * (P->nz + 1) + jc + 1] - s.er0;
     s.ez0 = P->ez[ic * P->nz + jc];
     s.gez = P->ez[(ic + 1) * P->nz + jc] - s.ez0;
-    s.dr = P->dr;
+    s.dr = o_drc(&P->g, ic);
     s.dz = P->dz;
     s.qm = P->qm;
     s.wb = P->wb;
     s.a = a; s.b = b;
-    s.r = ((double)ic + a) * P->dr;
+    s.r = (o_rho0(&P->g, ic) + a) * s.dr;
     s.vr = vr; s.vt = vt; s.vz = vz;
     s.pth = s.r * vt + 0.5 * P->wb * s.r * s.r;
 
@@ -414,7 +450,7 @@ static int o_push_one(o_push *P, int *pic, int *pjc, double *pa, double *pb, dou
         else continue;
         double X = face - x0;
         double v0 = dir == 0 ? vr : vz;
-        double h = dir == 0 ? P->dr : P->dz;
+        double h = dir == 0 ? s.dr : P->dz;
         double g0;
         if (X != 0.0) {
           g0 = dtT * (X / dx);
@@ -500,7 +536,8 @@ static int o_push_one(o_push *P, int *pic, int *pjc, double *pa, double *pb, dou
 /* Push + deposit of one species (rows a2/a3, and a6 when write != 0).
  * er/ez hold E^{n+1/2}; ir/iz accumulate (caller zeroes).  counters[6]:
  * substep errors, absorbed, substeps, fallbacks (and ke_lost in kelost). */
-void oracle_push(int nr, int nz, double dr, double dz, double dt, double q, double m, double bz,
+void oracle_push(int nr, int nz, double dr, double dz, int xa, double dt, double q, double m,
+                 double bz,
                  int64_t n, int32_t *cell, double *a, double *b, double *vr, double *vt,
                  double *vz, const double *w, const double *er, const double *ez, double *ir,
                  double *iz, int write, double *wall_z0, double *wall_zl, double *wall_r,
@@ -508,6 +545,7 @@ void oracle_push(int nr, int nz, double dr, double dz, double dt, double q, doub
   o_push P;
   memset(&P, 0, sizeof(P));
   P.nr = nr; P.nz = nz; P.dr = dr; P.dz = dz;
+  P.g.nr = nr; P.g.nz = nz; P.g.dr = dr; P.g.dz = dz; P.g.xa = xa;
   P.er = er; P.ez = ez; P.ir = ir; P.iz = iz;
   P.q = q; P.qm = q / m; P.wb = (q / m) * bz; P.m = m;
   P.wall_z0 = wall_z0; P.wall_zl = wall_zl; P.wall_r = wall_r;
@@ -547,24 +585,26 @@ void oracle_node_charge(int nr, int nz, double q, int64_t n, const int32_t *cell
 
 /* --------------------------------------------------------- field solve */
 /* Implicit CN Maxwell solve of Eq. 2 (TM: Er, Ez, H_theta; H_theta is the
- * primary unknown).  Integral (finite-volume) Yee form on the uniform mesh:
+ * primary unknown).  Integral (finite-volume) Yee form on the (mapped) mesh:
  *   Faraday: mu*Vh*(H1-H0) = -dt * C^T L E_half
  *   Ampere:  eps*A*(E1-E0) = dt * C H_half - dQ          (unknown edges)
  * Eliminating E gives (2 mu Vh + dt^2/2 C^T W C) H_half = rhs, W = L/(eps A),
  * solved here by banded Cholesky.  Prescribed edges: Er = 0 on the plates
  * z=0, z=L; Ez(R, z) = V(t)/L on the r = R gap. */
 typedef struct {
-  int nr, nz, n, bw;
+  int nr, nz, n, bw, xa;
   double dr, dz, dt, eps, mu;
   double *Lb; /* lower band of the Cholesky factor, n*(bw+1) */
 } o_field;
 
 static double *o_band(o_field *F, int i, int j) { return &F->Lb[(size_t)i * (F->bw + 1) + (j - i + F->bw)]; }
 
-void *oracle_field_create(int nr, int nz, double dr, double dz, double dt, double eps, double mu) {
+void *oracle_field_create(int nr, int nz, double dr, double dz, int xa, double dt, double eps,
+                          double mu) {
   o_field *F = (o_field *)calloc(1, sizeof(o_field));
-  og_grid g = {nr, nz, dr, dz};
+  og_grid g = {nr, nz, dr, dz, xa};
   F->nr = nr; F->nz = nz; F->dr = dr; F->dz = dz; F->dt = dt; F->eps = eps; F->mu = mu;
+  F->xa = xa;
   F->n = nr * nz;
   F->bw = nz;
   F->Lb = (double *)calloc((size_t)F->n * (F->bw + 1), sizeof(double));
@@ -579,7 +619,7 @@ void *oracle_field_create(int nr, int nz, double dr, double dz, double dt, doubl
   /* unknown Er edges (i+1/2, j), j = 1..nz-1, between cells (i,j-1) [C=+2pi r] and (i,j) [C=-2pi r] */
   for (int i = 0; i < nr; ++i)
     for (int j = 1; j < nz; ++j) {
-      double W = dr / (eps * o_area_r(&g, i));
+      double W = o_drc(&g, i) / (eps * o_area_r(&g, i));
       double s_lo = O_TWO_PI * o_rhalf(&g, i);
       double s_hi = -O_TWO_PI * o_rhalf(&g, i);
       int clo = i * nz + (j - 1), chi = i * nz + j;
@@ -651,7 +691,7 @@ void oracle_field_solve(void *p, const double *er0, const double *ez0, const dou
                         double *er1, double *ez1, double *h1, double *src) {
   o_field *F = (o_field *)p;
   int nr = F->nr, nz = F->nz;
-  og_grid g = {nr, nz, F->dr, F->dz};
+  og_grid g = {nr, nz, F->dr, F->dz, F->xa};
   double dt = F->dt, eps = F->eps, mu = F->mu;
   double *x = (double *)malloc(sizeof(double) * (size_t)F->n);
   for (int i = 0; i < nr; ++i)
@@ -663,8 +703,8 @@ void oracle_field_solve(void *p, const double *er0, const double *ez0, const dou
       if (j == 0 || j == nz) et = 0.0;
       else et = er0[i * (nz + 1) + j] - ir[i * (nz + 1) + j] / (2.0 * eps * o_area_r(&g, i));
       double s = O_TWO_PI * o_rhalf(&g, i);
-      if (j <= nz - 1) x[i * nz + j] -= dt * (-s) * F->dr * et;
-      if (j >= 1) x[i * nz + (j - 1)] -= dt * (s) * F->dr * et;
+      if (j <= nz - 1) x[i * nz + j] -= dt * (-s) * o_drc(&g, i) * et;
+      if (j >= 1) x[i * nz + (j - 1)] -= dt * (s) * o_drc(&g, i) * et;
     }
   for (int i = 0; i <= nr; ++i)
     for (int j = 0; j < nz; ++j) {
@@ -704,14 +744,14 @@ void oracle_field_solve(void *p, const double *er0, const double *ez0, const dou
 }
 
 /* field energy over unknown edges and H cells */
-double oracle_field_energy(int nr, int nz, double dr, double dz, double eps, double mu,
+double oracle_field_energy(int nr, int nz, double dr, double dz, int xa, double eps, double mu,
                            const double *er, const double *ez, const double *h) {
-  og_grid g = {nr, nz, dr, dz};
+  og_grid g = {nr, nz, dr, dz, xa};
   double W = 0.0;
   for (int i = 0; i < nr; ++i)
     for (int j = 1; j < nz; ++j) {
       double e = er[i * (nz + 1) + j];
-      W += 0.5 * eps * e * e * o_area_r(&g, i) * dr;
+      W += 0.5 * eps * e * e * o_area_r(&g, i) * o_drc(&g, i);
     }
   for (int i = 0; i < nr; ++i)
     for (int j = 0; j < nz; ++j) {
@@ -727,9 +767,10 @@ double oracle_field_energy(int nr, int nz, double dr, double dz, double eps, dou
 }
 
 /* Gauss residual eps*div E - Q at interior nodes i=0..nr-1, j=1..nz-1 (others 0) */
-void oracle_gauss_residual(int nr, int nz, double dr, double dz, double eps, const double *er,
+void oracle_gauss_residual(int nr, int nz, double dr, double dz, int xa, double eps,
+                           const double *er,
                            const double *ez, const double *Q, double *G) {
-  og_grid g = {nr, nz, dr, dz};
+  og_grid g = {nr, nz, dr, dz, xa};
   for (int i = 0; i <= nr; ++i)
     for (int j = 0; j <= nz; ++j) G[i * (nz + 1) + j] = 0.0;
   for (int i = 0; i < nr; ++i)
@@ -978,6 +1019,7 @@ typedef struct {
   double ng, tg, numax_e, pnull_e, pnull_i, gmax;
   uint64_t seed;
   double cblock;       /* blocking capacitor [F] between generator and electrode (Eq. 6); 0 = none */
+  int xa;              /* mapped mesh: cells near the axis with r proportional to sqrt(xi) */
 } orc_cfg;
 
 typedef struct {
@@ -1004,7 +1046,7 @@ static double o_circuit(const orc_cfg *cfg, void *field, const double *er, const
                         double v1, double qn) {
   int nr = cfg->nr, nz = cfg->nz;
   size_t ner = (size_t)nr * (nz + 1), nez = (size_t)(nr + 1) * nz, nh = (size_t)nr * nz;
-  og_grid g = {nr, nz, cfg->dr, cfg->dz};
+  og_grid g = {nr, nz, cfg->dr, cfg->dz, cfg->xa};
   double *era = (double *)malloc(sizeof(double) * ner), *eza = (double *)malloc(sizeof(double) * nez);
   double *ha = (double *)malloc(sizeof(double) * nh);
   double *zr = (double *)calloc(ner, sizeof(double)), *zz = (double *)calloc(nez, sizeof(double));
@@ -1059,7 +1101,7 @@ int oracle_step(const orc_cfg *cfg, void *field, uint64_t step, orc_species *sp,
     memset(ir, 0, sizeof(double) * ner);
     memset(iz, 0, sizeof(double) * nez);
     for (int s = 0; s < nspec; ++s)
-      oracle_push(nr, nz, cfg->dr, cfg->dz, cfg->dt, sp[s].q, sp[s].m, cfg->bz, sp[s].n, sp[s].cell,
+      oracle_push(nr, nz, cfg->dr, cfg->dz, cfg->xa, cfg->dt, sp[s].q, sp[s].m, cfg->bz, sp[s].n, sp[s].cell,
                   sp[s].a, sp[s].b, sp[s].vr, sp[s].vt, sp[s].vz, sp[s].w, erh, ezh, ir, iz, 0,
                   NULL, NULL, NULL, NULL, NULL);
     if (circ_on) phi1 = o_circuit(cfg, field, er, ez, h, ir, iz, phi0, v1, circ[0]);
@@ -1095,7 +1137,7 @@ int oracle_step(const orc_cfg *cfg, void *field, uint64_t step, orc_species *sp,
     memset(ir, 0, sizeof(double) * ner);
     memset(iz, 0, sizeof(double) * nez);
     for (int s = 0; s < nspec; ++s)
-      oracle_push(nr, nz, cfg->dr, cfg->dz, cfg->dt, sp[s].q, sp[s].m, cfg->bz, sp[s].n, sp[s].cell,
+      oracle_push(nr, nz, cfg->dr, cfg->dz, cfg->xa, cfg->dt, sp[s].q, sp[s].m, cfg->bz, sp[s].n, sp[s].cell,
                   sp[s].a, sp[s].b, sp[s].vr, sp[s].vt, sp[s].vz, sp[s].w, erh, ezh, ir, iz, 1,
                   wall_z0 ? wall_z0 + (size_t)s * (nr + 1) : NULL,
                   wall_zl ? wall_zl + (size_t)s * (nr + 1) : NULL,
