@@ -86,6 +86,10 @@ typedef struct pic_config {
                                  powered electrode (Eq. 6); 0 = none (the electrode is at V(t)) */
   int ions_fixed;             /* 1: ions stay at their positions (no push, deposit or sort), as in
                                  the dispersion test of Sec. 3.1; requires mcc_on = 0 */
+  int axis_cells;             /* mapped radial mesh (Sec. 2.1), 0..16 (< nr): the first
+                                 axis_cells cells have r = 2 dr sqrt(xa xi), the rest
+                                 r = dr (xi + xa), dr = R / (nr + xa), r linear in xi inside
+                                 each cell; 0 = uniform mesh r = xi R / nr */
 } pic_config;
 
 /* Per-step statistics (host struct). */

@@ -33,8 +33,14 @@ __global__ void k_half_alpha(long long n1, long long n2, const double *er0, cons
   if (t < n1) {
     double e = 0.5 * (er0[t] + er1[t]);
     erh[t] = e;
-    A.ar[0][t] = (float)(A.sr[0] * e);
-    A.ar[1][t] = (float)(A.sr[1] * e);
+    const long long i = t / A.nz1;
+    if (i < A.xa) {  // mapped mesh: the row's own width
+      A.ar[0][t] = (float)(A.srx[0][i] * e);
+      A.ar[1][t] = (float)(A.srx[1][i] * e);
+    } else {
+      A.ar[0][t] = (float)(A.sr[0] * e);
+      A.ar[1][t] = (float)(A.sr[1] * e);
+    }
   } else if (t < n1 + n2) {
     long long u = t - n1;
     double e = 0.5 * (ez0[u] + ez1[u]);
@@ -51,8 +57,14 @@ __global__ void k_half_alpha64(long long n1, long long n2, const double *er0, co
   if (t < n1) {
     double e = 0.5 * (er0[t] + er1[t]);
     erh[t] = e;
-    A.ar[0][t] = A.sr[0] * e;
-    A.ar[1][t] = A.sr[1] * e;
+    const long long i = t / A.nz1;
+    if (i < A.xa) {
+      A.ar[0][t] = A.srx[0][i] * e;
+      A.ar[1][t] = A.srx[1][i] * e;
+    } else {
+      A.ar[0][t] = A.sr[0] * e;
+      A.ar[1][t] = A.sr[1] * e;
+    }
   } else if (t < n1 + n2) {
     long long u = t - n1;
     double e = 0.5 * (ez0[u] + ez1[u]);
@@ -63,7 +75,7 @@ __global__ void k_half_alpha64(long long n1, long long n2, const double *er0, co
 }
 
 // rhs(i,j) = 2 mu Vh H0 - dt * C^T L Et   (Et = E0 - dQ/(2 eps A), or the prescribed half value)
-enum { kT2ear = 0, kT2eaz = 1, kTear = 2, kTeaz = 3, kTs = 4, kTvh = 5 };
+enum { kT2ear = 0, kT2eaz = 1, kTear = 2, kTeaz = 3, kTs = 4, kTvh = 5, kTw = 6 };
 __device__ __forceinline__ double tab(const FieldOp &F, int k, int i) {
   return F.rtab[k * (F.nr + 1) + i];
 }
@@ -72,7 +84,7 @@ __device__ __forceinline__ double rhs_at(const FieldOp &F, const double *er0, co
                                         double v0, double v1, int i, int j) {
   int nr = F.nr, nz = F.nz, nz1 = nz + 1;
   int c = i * nz + j;
-  double dr = F.dr, dz = F.dz;
+  double dr = tab(F, kTw, i), dz = F.dz;  // E_r edge length: the cell width
   double s = tab(F, kTs, i);
   double r2 = tab(F, kT2ear, i);
   double etb = 0.0, ett = 0.0;
@@ -614,7 +626,7 @@ __global__ void __launch_bounds__(256) k_es_field(EsOp E, double phi0, double *e
   double dn = 0.0, nn = 0.0;
   if (t < ner) {
     const int i = (int)(t / nz1), j = (int)(t - (t / nz1) * nz1);
-    double e = -(es_node(E, phi0, dl, i + 1, j) - es_node(E, phi0, dl, i, j)) / E.dr;
+    double e = -(es_node(E, phi0, dl, i + 1, j) - es_node(E, phi0, dl, i, j)) / E.tab[3 * nr + i];
     er1[t] = e;
     if (er_it && j != 0 && j != nz) {
       double d = e - er_it[t];

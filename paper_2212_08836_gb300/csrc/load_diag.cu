@@ -21,7 +21,14 @@ __global__ void __launch_bounds__(256) k_load(Grid g, long long n, double n0, do
   if (jc > g.nz - 1) jc = g.nz - 1;
   int32_t cell = ic * g.nz + jc;
   double a = xi - (double)ic, b = eta - (double)jc;
-  double w = n0 * (kTwoPi * (xi * g.dr)) * g.R * g.L / (double)n;
+  double w;
+  if (g.xa == 0) {
+    w = n0 * (kTwoPi * (xi * g.dr)) * g.R * g.L / (double)n;
+  } else {  // mapped mesh: w proportional to r J_r, J_r the cell width
+    const double jr = g_width(g, ic);
+    const double r = (g_rho0(g, ic) + a) * jr;
+    w = n0 * (kTwoPi * r) * (jr * (double)g.nr) * g.L / (double)n;
+  }
   e.cell[p] = cell; e.a[p] = (T)a; e.b[p] = (T)b; e.w[p] = (T)w; e.id[p] = (uint32_t)p;
   i.cell[p] = cell; i.a[p] = (T)a; i.b[p] = (T)b; i.w[p] = (T)w; i.id[p] = (uint32_t)p;
   double g1, g2, g3, g4;
@@ -77,26 +84,25 @@ __global__ void __launch_bounds__(256) k_field_energy(Grid g, double eps, double
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   long long ner = (long long)nr * nz1, nez = (long long)(nr + 1) * nz, nh = (long long)nr * nz;
   double W = 0.0;
-  double dr = g.dr, dz = g.dz;
+  double dz = g.dz;
   if (t < ner) {
     int i = (int)(t / nz1), j = (int)(t - (t / nz1) * nz1);
     if (j != 0 && j != nz) {
       double e = er[t];
-      W += 0.5 * eps * e * e * (kTwoPi * (((double)i + 0.5) * dr) * dz) * dr;
+      W += 0.5 * eps * e * e * (kTwoPi * g_rcentre(g, i) * dz) * g_width(g, i);
     }
   }
   if (t < nez) {
     int i = (int)(t / nz);
     if (i < nr) {
       double e = ez[t];
-      double A = i == 0 ? kPi * (0.5 * dr) * (0.5 * dr) : kTwoPi * ((double)i * dr) * dr;
-      W += 0.5 * eps * e * e * A * dz;
+      W += 0.5 * eps * e * e * g_area_z(g, i) * dz;
     }
   }
   if (t < nh) {
     int i = (int)(t / nz);
     double hh = h[t];
-    W += 0.5 * mu * hh * hh * (kTwoPi * (((double)i + 0.5) * dr) * dr * dz);
+    W += 0.5 * mu * hh * hh * (kTwoPi * g_rcentre(g, i) * g_width(g, i) * dz);
   }
   block_add2(W, 0.0, out);
 }

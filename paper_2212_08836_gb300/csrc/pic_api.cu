@@ -86,6 +86,8 @@ struct pic_ctx {
   long long *n_dev;
   double *vdev;             // [0..1] V^n, V^{n+1}; [4..7] blocking-capacitor state (Circuit)
   double *hu;               // EM unit response of the circuit (nr x nz)
+  double *rmap64;           // mapped mesh: radial scales of the first cells (RadialMapT)
+  float *rmap32;
   int circ_on;
   // generator waveform: sum of harmonics when nharm > 0 (else volt sin(2 pi f t))
   int nharm;
@@ -187,6 +189,7 @@ bool valid(const pic_config *c) {
   if (c->mcc_on && (!(c->gas_pressure > 0) || !(c->gas_temp > 0))) return false;
   if (!(c->cblock >= 0.0) || !isfinite(c->cblock)) return false;
   if (c->ions_fixed != 0 && c->ions_fixed != 1) return false;
+  if (c->axis_cells < 0 || c->axis_cells > kMaxAxisCells || c->axis_cells >= c->nr) return false;
   if (c->ions_fixed && c->mcc_on) return false;
   return true;
 }
@@ -261,11 +264,11 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
     x->es.nz = nz;
     x->es.M = M;
     x->es.n2 = n2e;
-    x->es.dr = c->R / nr;
+    x->es.dr = c->R / (nr + c->axis_cells);
     x->es.dz = c->L / nz;
     x->es.S = (const double *)K.take((size_t)M * M * 8);
     x->es.crc = (const double *)K.take((size_t)5 * n2e * M * 8);
-    x->es.tab = (const double *)K.take((size_t)3 * nr * 8);
+    x->es.tab = (const double *)K.take((size_t)4 * nr * 8);
     x->es.rhs = (double *)K.take((size_t)nr * M * 8);
     x->es.hat = (double *)K.take((size_t)nr * M * 8);
     x->es.phi = (double *)K.take((size_t)nr * M * 8);
@@ -274,7 +277,7 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
   }
   x->F.tw = (const double2 *)K.take((size_t)nz * 16);
   x->F.pw = (const double2 *)K.take((size_t)nz * 16);
-  x->F.rtab = (const double *)K.take((size_t)6 * (nr + 1) * 8);
+  x->F.rtab = (const double *)K.take((size_t)7 * (nr + 1) * 8);
   x->cnt = (DevCounters *)K.take(sizeof(DevCounters));
   for (int k = 0; k < 3; ++k) {
     x->hr[k] = (double *)K.take(ner * 8);
@@ -290,6 +293,8 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
   x->n_dev = (long long *)K.take(256);
   x->vdev = (double *)K.take(256);
   x->hu = (double *)K.take((size_t)nr * nz * 8);
+  x->rmap64 = (double *)K.take((size_t)3 * kMaxAxisCells * 8);
+  x->rmap32 = (float *)K.take((size_t)3 * kMaxAxisCells * 4);
   x->fbb = (double *)K.take((size_t)64 * (nr + 1) * 8);
   {
     size_t P = (size_t)(nr + 1) * (nz + 1);
@@ -371,6 +376,13 @@ void fill_push(pic_ctx *x, int s, double q, double m, const double *erh, const d
   L.cz = (T)(dt / x->g.dz);
   L.icr = (T)(x->g.dr / dt);
   L.icz = (T)(x->g.dz / dt);
+  L.rm.xa = x->g.xa;
+  L.rm.cr = L.cr;
+  L.rm.icr = L.icr;
+  const T *tb = (const T *)(sizeof(T) == 8 ? (const void *)x->rmap64 : (const void *)x->rmap32);
+  L.rm.rho0x = tb;
+  L.rm.crx = tb + kMaxAxisCells;
+  L.rm.icrx = tb + 2 * kMaxAxisCells;
   L.wbt = (T)(q / m * x->cfg.bz * dt);
   L.inz = 1.0f / (float)x->g.nz;
   L.n = x->n[s];
@@ -505,7 +517,8 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
   x->g.nz = nz;
   x->g.R = cfg->R;
   x->g.L = cfg->L;
-  x->g.dr = cfg->R / nr;
+  x->g.xa = cfg->axis_cells;
+  x->g.dr = cfg->R / (nr + cfg->axis_cells);
   x->g.dz = cfg->L / nz;
   x->eps = cfg->eps > 0 ? cfg->eps : kEps0;
   x->mu = cfg->mu > 0 ? cfg->mu : kMu0;
@@ -515,7 +528,11 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
     double qm = sp == 0 ? -kQE / kME : kQE / kMAr;
     x->alpha.sr[sp] = x->alpha64.sr[sp] = qm * cfg->dt * cfg->dt / x->g.dr;
     x->alpha.sz[sp] = x->alpha64.sz[sp] = qm * cfg->dt * cfg->dt / x->g.dz;
+    for (int i = 0; i < x->g.xa; ++i)
+      x->alpha.srx[sp][i] = x->alpha64.srx[sp][i] = qm * cfg->dt * cfg->dt / g_width(x->g, i);
   }
+  x->alpha.xa = x->alpha64.xa = x->g.xa;
+  x->alpha.nz1 = x->alpha64.nz1 = nz + 1;
   x->ng = cfg->mcc_on ? cfg->gas_pressure / (kKB * cfg->gas_temp) : 0.0;
 
   // MCC constants (host): nu_max over eps <= 1 keV (x 1.01), ion g_max
@@ -595,13 +612,17 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
       }
   }
   std::vector<double> mass(nr), kz(nr), kdiag(nr), eoff(nr, 0.0);
-  auto rh = [&](int i) { return ((double)i + 0.5) * dr; };
-  auto az = [&](int i) { return i == 0 ? kPi * (0.5 * dr) * (0.5 * dr) : kTwoPi * ((double)i * dr) * dr; };
+  // radial geometry of the (mapped) mesh: cell-centre radius, cell width and
+  // E_z dual-face area per row
+  const Grid &G = x->g;
+  auto rh = [&](int i) { return g_rcentre(G, i); };
+  auto wr = [&](int i) { return g_width(G, i); };
+  auto az = [&](int i) { return g_area_z(G, i); };
   for (int i = 0; i < nr; ++i) {
-    mass[i] = 2.0 * x->mu * (kTwoPi * rh(i) * dr * dz);
+    mass[i] = 2.0 * x->mu * (kTwoPi * rh(i) * wr(i) * dz);
     double ar = kTwoPi * rh(i) * dz;
     double s = kTwoPi * rh(i);
-    kz[i] = hdt2 * (dr / (x->eps * ar)) * s * s;
+    kz[i] = hdt2 * (wr(i) / (x->eps * ar)) * s * s;
     double wz_i = dz / (x->eps * az(i));
     double d = wz_i * s * s;
     if (i + 1 <= nr - 1) d += (dz / (x->eps * az(i + 1))) * s * s;
@@ -624,13 +645,14 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
   }
   // electrostatic model: DST-I basis, per-row coefficients, mode coefficients
   const int M = nz - 1;
-  std::vector<double> Sd((size_t)M * M), et((size_t)3 * nr), ecr((size_t)5 * n2 * M, 0.0);
+  std::vector<double> Sd((size_t)M * M), et((size_t)4 * nr), ecr((size_t)5 * n2 * M, 0.0);
   for (int j = 1; j <= M; ++j)
     for (int m = 1; m <= M; ++m) Sd[(size_t)(j - 1) * M + (m - 1)] = sqrt(2.0 / nz) * sin(kPi * j * m / nz);
   for (int i = 0; i < nr; ++i) {
-    et[i] = x->eps * (kTwoPi * rh(i) * dz) / dr;                        // cR: face i+1/2
-    et[nr + i] = i >= 1 ? x->eps * (kTwoPi * rh(i - 1) * dz) / dr : 0.0;  // cL: face i-1/2
-    et[2 * nr + i] = x->eps * az(i) / dz;                               // cZ
+    et[i] = x->eps * (kTwoPi * rh(i) * dz) / wr(i);                            // cR: face i+1/2
+    et[nr + i] = i >= 1 ? x->eps * (kTwoPi * rh(i - 1) * dz) / wr(i - 1) : 0.0;  // cL: face i-1/2
+    et[2 * nr + i] = x->eps * az(i) / dz;                                      // cZ
+    et[3 * nr + i] = wr(i);                                                    // E_r edge length
   }
   // FFT plan of the DST-I (2 nz points) when 2 nz = 4^a 2^b 3^c <= 8192
   x->es.fft2 = 0;
@@ -664,7 +686,7 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
     cr_coeffs(n2, A, B, Cc, ecr.data() + (size_t)(m - 1) * 5 * n2);
   }
   // twiddles, DCT phases and per-row reciprocal tables
-  std::vector<double> tw((size_t)2 * nz), pw((size_t)2 * nz), rt((size_t)6 * (nr + 1), 0.0);
+  std::vector<double> tw((size_t)2 * nz), pw((size_t)2 * nz), rt((size_t)7 * (nr + 1), 0.0);
   for (int k = 0; k < nz; ++k) {
     double t = -kTwoPi * (double)k / nz;
     tw[2 * k] = cos(t);
@@ -681,7 +703,8 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
     rt[2 * (nr + 1) + i] = 1.0 / (x->eps * ari);
     rt[3 * (nr + 1) + i] = 1.0 / (x->eps * azi);
     rt[4 * (nr + 1) + i] = kTwoPi * rh(i);
-    rt[5 * (nr + 1) + i] = kTwoPi * rh(i) * dr * dz;
+    rt[5 * (nr + 1) + i] = kTwoPi * rh(i) * wr(i) * dz;
+    rt[6 * (nr + 1) + i] = wr(i);
   }
   cudaError_t e = cudaSuccess;
   auto up = [&](const void *dst, const void *src, size_t b) {
@@ -697,6 +720,19 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
   up(x->es.tab, et.data(), et.size() * 8);
   up(x->es.crc, ecr.data(), ecr.size() * 8);
   up(x->es.tw2, tw2.data(), tw2.size() * 8);
+  // radial scales of the mapped cells: inner-face radius / w, dt / w, w / dt
+  std::vector<double> rm64((size_t)3 * kMaxAxisCells, 0.0);
+  std::vector<float> rm32((size_t)3 * kMaxAxisCells, 0.f);
+  for (int i = 0; i < x->g.xa; ++i) {
+    const double w = g_width(x->g, i);
+    rm64[i] = g_rho0(x->g, i);
+    rm64[kMaxAxisCells + i] = cfg->dt / w;
+    rm64[2 * kMaxAxisCells + i] = w / cfg->dt;
+    for (int k = 0; k < 3; ++k)
+      rm32[k * kMaxAxisCells + i] = (float)rm64[k * kMaxAxisCells + i];
+  }
+  up(x->rmap64, rm64.data(), rm64.size() * 8);
+  up(x->rmap32, rm32.data(), rm32.size() * 4);
   size_t ner = (size_t)nr * (nz + 1), nez = (size_t)(nr + 1) * nz, nh = (size_t)nr * nz;
   if (e == cudaSuccess) e = cudaMemsetAsync(x->er, 0, ner * 8, x->s);
   if (e == cudaSuccess) e = cudaMemsetAsync(x->ez, 0, nez * 8, x->s);
@@ -884,14 +920,22 @@ int pic_fourier_bessel(pic_ctx *x, int alpha, int row, int nmodes, double *coef)
   if (x->fb_alpha != alpha || x->fb_m != nmodes) {
     // basis[m][k] = w_k r_k F_m(r_k) / sum_k w_k r_k F_m(r_k)^2 (Eq. A2 by the
     // trapezoid rule on nodes, alpha = 0, or the midpoint rule, alpha = 1)
-    const double R = x->cfg.R, dr = R / nr;
+    const double R = x->cfg.R;
+    const Grid &G = x->g;
     std::vector<double> B((size_t)nmodes * n);
     for (int m = 0; m < nmodes; ++m) {
       const double chi = bessel_zero(alpha, m + 1);
       double den = 0.0;
       for (int k = 0; k < n; ++k) {
-        const double r = alpha == 0 ? k * dr : (k + 0.5) * dr;
-        const double w = alpha == 0 && (k == 0 || k == nr) ? 0.5 * dr : dr;
+        // nodes with trapezoid weights, or cell centres with the cell widths
+        double r, w;
+        if (alpha == 0) {
+          r = g_rnode(G, k);
+          w = 0.5 * ((k > 0 ? g_width(G, k - 1) : 0.0) + (k < nr ? g_width(G, k) : 0.0));
+        } else {
+          r = 0.5 * (g_rnode(G, k) + g_rnode(G, k + 1));
+          w = g_width(G, k);
+        }
         const double F = std::cyl_bessel_j((double)alpha, chi * r / R);
         B[(size_t)m * n + k] = w * r * F;
         den += w * r * F * F;

@@ -60,10 +60,43 @@ __device__ __forceinline__ void gauss2(double ua, double ub, double &g1, double 
   g2 = rho * sin(ang);
 }
 
+// Mesh: uniform in the logical coordinates (xi, eta).  Radial mapping of the
+// mapped mesh (Sec. 2.1): r(xi) = 2 dr sqrt(xa xi) in the first xa cells and
+// dr (xi + xa) beyond (continuous with its slope; r J_r finite at the axis),
+// linear in xi within each cell; xa = 0 is the uniform mesh r = xi dr.
+constexpr int kMaxAxisCells = 16;
 struct Grid {
   int nr, nz;
-  double dr, dz, R, L;
+  double dr, dz, R, L;  // dr: spacing of the uniformly spaced part
+  int xa;               // cells with r proportional to sqrt(xi)
 };
+
+// node radius r_i, cell width J_r, cell-centre radius, and the inner-face
+// radius of a cell in units of its width
+__host__ __device__ inline double g_rnode(const Grid &g, int i) {
+  if (i < g.xa) return 2.0 * g.dr * sqrt((double)g.xa * (double)i);
+  return ((double)i + (double)g.xa) * g.dr;
+}
+__host__ __device__ inline double g_width(const Grid &g, int i) {
+  return i < g.xa ? g_rnode(g, i + 1) - g_rnode(g, i) : g.dr;
+}
+__host__ __device__ inline double g_rcentre(const Grid &g, int i) {
+  if (i < g.xa) return 0.5 * (g_rnode(g, i) + g_rnode(g, i + 1));
+  return ((double)i + 0.5 + (double)g.xa) * g.dr;
+}
+__host__ __device__ inline double g_rho0(const Grid &g, int i) {
+  return i < g.xa ? g_rnode(g, i) / g_width(g, i) : (double)(i + g.xa);
+}
+// dual-face area of the E_z edge at node i: the ring between the
+// neighbouring cell centres (the disc of radius r_{1/2} on the axis)
+__host__ __device__ inline double g_area_z(const Grid &g, int i) {
+  if (i == 0) return kPi * g_rcentre(g, 0) * g_rcentre(g, 0);
+  if (i <= g.xa) {
+    const double ro = g_rcentre(g, i), ri = g_rcentre(g, i - 1);
+    return kPi * (ro * ro - ri * ri);
+  }
+  return kTwoPi * g_rnode(g, i) * g.dr;
+}
 
 // Particle structure of arrays of one species; T = double (plain FP64 form)
 // or float (mixed form: FP32 state in physical units)
@@ -125,12 +158,26 @@ struct FieldOp {
   const double2 *pw;   // pw[m] = (cos, sin)(pi m / (2 nz))
   double c0, c1;       // DCT-II normalisation sqrt(1/nz), sqrt(2/nz)
   // per-row tables (nr + 1 entries each): 1/(2 eps A_r), 1/(2 eps A_z),
-  // 1/(eps A_r), 1/(eps A_z), 2 pi r_{i+1/2}, V_H
+  // 1/(eps A_r), 1/(eps A_z), 2 pi r_{i+1/2}, V_H, cell width w_i
   const double *rtab;
   // drive voltages V(t^n), V(t^{n+1}) read on the device (vd != nullptr) so
   // that a captured solve stays valid from step to step; else the arguments
   const double *vd;
   Circuit cc;
+};
+
+// Radial scales of a cell in the push's normalised units: lengths in units of
+// the cell's width w.  Cells ic < xa of the mapped mesh have their own width
+// (tables in device memory: inner-face radius / w, dt / w, w / dt); beyond,
+// w = dr, the inner-face radius is (ic + xa) dr and the scalars apply.
+template <typename T>
+struct RadialMapT {
+  int xa;
+  T cr, icr;
+  const T *rho0x, *crx, *icrx;
+  __device__ __forceinline__ T rho0(int ic) const { return ic < xa ? rho0x[ic] : (T)(ic + xa); }
+  __device__ __forceinline__ T crr(int ic) const { return ic < xa ? crx[ic] : cr; }
+  __device__ __forceinline__ T icrr(int ic) const { return ic < xa ? icrx[ic] : icr; }
 };
 
 // One mover + deposit pass over one species (rows a2, a3, a6) in the scalar
@@ -141,6 +188,7 @@ struct PushLaunchT {
   double q, m;             // species charge [C] and mass [kg]
   T qf;                    // q in T
   T cr, cz, icr, icz;      // dt/dr, dt/dz (velocity -> cells per step) and inverses
+  RadialMapT<T> rm;        // per-cell radial scales (mapped mesh)
   T wbt;                   // qm*Bz*dt (0: no external B_z)
   float inz;               // 1/nz (cell -> (i, j) split without an integer division)
   long long n;
@@ -173,7 +221,8 @@ struct EsOp {
   double dr, dz;
   const double *S;         // M x M: sqrt(2/nz) sin(pi j m / nz), j, m = 1..M
   const double *crc;       // cyclic-reduction coefficients of mode m in column m - 1
-  const double *tab;       // 3 x nr: eps A_r(i)/dr, eps A_r(i-1)/dr, eps A_z(i)/dz
+  const double *tab;       // 4 x nr: eps A_r(i)/w_i, eps A_r(i-1)/w_{i-1}, eps A_z(i)/dz,
+                           // w_i (cell widths)
   double *rhs, *hat, *phi; // nr x M scratch
   const double *vd;        // phi0 = vd[1] (V(t^{n+1})) if vd, else the argument
   // FFT path (fft2 = 2 nz = 2^a 3^b): the DST-I of two rows as one 2nz-point
@@ -298,6 +347,8 @@ cudaError_t launch_node_charge(const Grid &g, const PartsT<T> &p, long long n, d
 struct AlphaOut64 {
   double *ar[2], *az[2];
   double sr[2], sz[2];
+  int xa, nz1;                        // mapped mesh: rows i < xa scale by their width
+  double srx[2][kMaxAxisCells];       // qm*dt^2/w_i, i < xa
 };
 cudaError_t launch_half_field_alpha64(const Grid &g, const double *er0, const double *ez0,
                                       const double *er1, const double *ez1, double *erh,
@@ -307,6 +358,8 @@ cudaError_t launch_half_field_alpha64(const Grid &g, const double *er0, const do
 struct AlphaOut {
   float *ar[2], *az[2];   // per species: Er-edge and Ez-edge layouts
   double sr[2], sz[2];    // scale factors qm*dt^2/dr, qm*dt^2/dz
+  int xa, nz1;
+  double srx[2][kMaxAxisCells];
 };
 cudaError_t launch_half_field_alpha(const Grid &g, const double *er0, const double *ez0,
                                     const double *er1, const double *ez1, double *erh,

@@ -361,7 +361,8 @@ template <typename T>
 struct GenArgs {
   int nr, nz;
   const T *ar, *az;      // normalised accelerations of the species
-  T wt, icr, icz;        // qm*Bz*dt; dr/dt, dz/dt
+  T wt, icr, icz, cz;    // qm*Bz*dt; dr/dt, dz/dt; dt/dz
+  RadialMapT<T> rm;      // per-cell radial scales (mapped mesh)
   double q, m;
   T qf;                  // q in T
   double *ir, *iz;       // crossed charge [C]
@@ -371,13 +372,25 @@ struct GenArgs {
   double *ke_lost;
 };
 
-// one particle from its start state (offsets a, b; normalised velocities);
+// radial face crossing on a mapped mesh: the normalised radial and azimuthal
+// velocities follow the new cell's width
+template <typename T>
+__device__ __forceinline__ void rescale_radial(const RadialMapT<T> &rm, int ic_old, int ic_new,
+                                               T &ur, T &ut) {
+  if (ic_new != ic_old && (ic_old < rm.xa || ic_new < rm.xa)) {
+    const T f = rm.icrr(ic_old) * rm.crr(ic_new);
+    ur *= f;
+    ut *= f;
+  }
+}
+
+// one particle from its start state (offsets a, b; physical velocities);
 // (tr_da, tr_db): the converged interior solution of the whole step from a
 // start strictly inside the cell (NaN: none), which replaces the first
 // interior solve
 template <typename T, bool kB>
-__device__ void push_general(const GenArgs<T> &L, long long p, int c0, T a, T b, T ur, T ut, T uz,
-                             const T w, T tr_da, T tr_db, Tally &Tl) {
+__device__ void push_general(const GenArgs<T> &L, long long p, int c0, T a, T b, T vr0, T vt0,
+                             T vz0, const T w, T tr_da, T tr_db, Tally &Tl) {
   const T zero = (T)0, one = (T)1, h = (T)0.5, two = (T)2;
   const int nr = L.nr, nz = L.nz, nz1 = nz + 1;
   const T wt = L.wt;
@@ -386,10 +399,14 @@ __device__ void push_general(const GenArgs<T> &L, long long p, int c0, T a, T b,
     return;
   }
   int ic = c0 / nz, jc = c0 - (c0 / nz) * nz;
+  const T cr0 = L.rm.crr(ic);
+  T ur = vr0 * cr0, ut = vt0 * cr0, uz = vz0 * L.cz;
   T tau = one;
   T tT = tau;
   int nsub = 0;
+  int ic_prev = ic;
   int absorbed = transition_gen<T>(nr, nz, ic, jc, a, b, ur, uz);
+  rescale_radial<T>(L.rm, ic_prev, ic, ur, ut);
   while (tau > zero && !absorbed) {
     if (++nsub > kNsubMax) {
       Tl.err++;
@@ -401,7 +418,7 @@ __device__ void push_general(const GenArgs<T> &L, long long p, int c0, T a, T b,
     s.az0 = L.az[ic * nz + jc];
     s.gaz = L.az[(ic + 1) * nz + jc] - s.az0;
     s.a = a; s.b = b;
-    s.rho = (T)ic + a;
+    s.rho = L.rm.rho0(ic) + a;
     s.ur = ur; s.ut = ut; s.uz = uz;
     s.P = s.rho * ut + h * wt * s.rho * s.rho;
     T da, db;
@@ -512,11 +529,14 @@ __device__ void push_general(const GenArgs<T> &L, long long p, int c0, T a, T b,
     ur = nur; ut = nut; uz = nuz;
     tau = tau - step_t;
     Tl.sub++;
+    ic_prev = ic;
     absorbed = transition_gen<T>(nr, nz, ic, jc, a, b, ur, uz);
     if (absorbed) break;
+    rescale_radial<T>(L.rm, ic_prev, ic, ur, ut);
     tT = tau;
   }
-  T vr = ur * L.icr, vt = ut * L.icr, vz = uz * L.icz;
+  const T icr = L.rm.icrr(ic);
+  T vr = ur * icr, vt = ut * icr, vz = uz * L.icz;
   if (absorbed) {
     Tl.abs++;
     if (L.write) {

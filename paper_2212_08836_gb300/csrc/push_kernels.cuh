@@ -169,15 +169,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_push_fast(PushL
     int key = -1, ic = 0, jc = 0;
     if (c0 >= 0 && c0 < ncell) {
       key = c0;
-      ur = cur.vr * L.cr;
-      ut = cur.vt * L.cr;
-      uz = cur.vz * L.cz;
       // cell -> (ic, jc) without an integer division (c0 < 2^24 is exact in FP32)
       ic = __float2int_rz(__int2float_rn(c0) * L.inz);
       jc = c0 - ic * nz;
       if (jc < 0) { ic -= 1; jc += nz; }
       else if (jc >= nz) { ic += 1; jc -= nz; }
-      const T rho = (T)ic + a;
+      const T crr = L.rm.crr(ic);
+      ur = cur.vr * crr;
+      ut = cur.vt * crr;
+      uz = cur.vz * L.cz;
+      const T rho = L.rm.rho0(ic) + a;
       bool acc = false;
       if (Num<T>::in01(a) && Num<T>::in01(b) && fabs(ut) < q * rho) {
         const T ar0 = L.ar[ic * nz1 + jc];
@@ -205,9 +206,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_push_fast(PushL
               // CN velocity relations: the displacement is the mean of u and u'
               L.dst.a[p] = a1;
               L.dst.b[p] = b1;
-              L.dst.vr[p] = (d + d - ur) * L.icr;
+              const T icr = L.rm.icrr(ic);
+              L.dst.vr[p] = (d + d - ur) * icr;
               L.dst.vz[p] = (e + e - uz) * L.icz;
-              L.dst.vt[p] = rho * ut * Num<T>::rcp(rho + d) * L.icr;
+              L.dst.vt[p] = rho * ut * Num<T>::rcp(rho + d) * icr;
               if (L.oop) {
                 L.dst.cell[p] = c0;
                 L.dst.w[p] = w;
@@ -243,7 +245,7 @@ __global__ void __launch_bounds__(256) k_push_general(PushLaunchT<T> L) {
   const int lane = threadIdx.x & 31;
   GenArgs<T> G;
   G.nr = L.g.nr; G.nz = L.g.nz; G.ar = L.ar; G.az = L.az;
-  G.wt = L.wbt; G.icr = L.icr; G.icz = L.icz;
+  G.wt = L.wbt; G.icr = L.icr; G.icz = L.icz; G.cz = L.cz; G.rm = L.rm;
   G.q = L.q; G.m = L.m; G.qf = L.qf; G.ir = L.ir; G.iz = L.iz; G.write = L.write; G.p = L.p;
   G.oop = L.oop; G.dst = L.dst;
   G.wall_z0 = L.wall_z0; G.wall_zl = L.wall_zl; G.wall_r = L.wall_r; G.ke_lost = L.ke_lost;
@@ -256,14 +258,14 @@ __global__ void __launch_bounds__(256) k_push_general(PushLaunchT<T> L) {
     for (long long q = gtid; q < total; q += gstride) {
       long long k = seg_entry(s_pre, L.qgrid, L.qseg, (int)q);
       long long p = L.queue[k];
-      push_general<T, kB>(G, p, L.p.cell[p], L.p.a[p], L.p.b[p], L.p.vr[p] * L.cr,
-                          L.p.vt[p] * L.cr, L.p.vz[p] * L.cz, L.p.w[p], L.q_da[k], L.q_db[k], tl);
+      push_general<T, kB>(G, p, L.p.cell[p], L.p.a[p], L.p.b[p], L.p.vr[p], L.p.vt[p],
+                          L.p.vz[p], L.p.w[p], L.q_da[k], L.q_db[k], tl);
     }
   } else {
     const long long n = L.n_dev ? *L.n_dev : L.n;
     for (long long k = gtid; k < n; k += gstride) {
-      push_general<T, kB>(G, k, L.p.cell[k], L.p.a[k], L.p.b[k], L.p.vr[k] * L.cr,
-                          L.p.vt[k] * L.cr, L.p.vz[k] * L.cz, L.p.w[k], (T)NAN, (T)NAN, tl);
+      push_general<T, kB>(G, k, L.p.cell[k], L.p.a[k], L.p.b[k], L.p.vr[k], L.p.vt[k],
+                          L.p.vz[k], L.p.w[k], (T)NAN, (T)NAN, tl);
     }
   }
   flush_tally(L.counters, tl, lane, 0, 0);

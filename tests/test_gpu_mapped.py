@@ -1,0 +1,164 @@
+"""Mapped radial mesh (Sec. 2.1: r proportional to sqrt(xi) in the first
+cells near the axis) on the GPU against the FP64 oracle: push + deposit,
+field solve, loading, whole steps of both field models, the mixed form, and
+Fourier-Bessel sampling on the mapped nodes."""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import es as ES
+from oracle import fb as FB
+from tests import inputs
+from tests.test_gpu_parity import assert_state_close, by_id
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+QE, ME, M_AR = O.QE, O.ME, O.M_AR
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as G
+    G.build()
+
+
+def P():
+    import paper_2212_08836_gb300 as M
+    return M
+
+
+def tgpu(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(DEV)
+
+
+def make_pic(nr, nz, R, L, dt, cap, xa, **kw):
+    M = P()
+    cfg = M.small_reactor(nr=nr, nz=nz, R=R, L=L, dt=dt, np_init=cap, capacity_factor=1.0,
+                          mcc_on=0, axis_cells=xa)
+    cfg.update(kw)
+    return M.Pic(cfg, device=DEV)
+
+
+def near_axis_particles(nr, nz, n, seed, vth, xa):
+    """Half of them in the mapped cells (ic < xa), some exactly on faces."""
+    rng = np.random.default_rng(seed + 7)
+    ic = np.where(rng.random(n) < 0.5, rng.integers(0, xa, size=n), rng.integers(0, nr, size=n))
+    jc = rng.integers(0, nz, size=n)
+    sp = inputs.particles(nr, nz, n, seed, vth, cells=ic * nz + jc, edge_frac=0.02)
+    o = np.argsort(sp["cell"], kind="stable")
+    return {k: v[o] for k, v in sp.items()}
+
+
+@pytest.mark.parametrize("nr,nz,xa,precision", [(16, 24, 3, 0), (32, 64, 6, 0), (16, 24, 4, 1)])
+def test_push_deposit_parity(nr, nz, xa, precision):
+    n, dt = 8000, 1e-9
+    g = O.Grid(nr, nz, 0.05, 0.03, xa=xa)
+    e = near_axis_particles(nr, nz, n, 1, 8e5, xa)
+    i = near_axis_particles(nr, nz, n, 2, 3e3, xa)
+    er, ez = inputs.smooth_fields(nr, nz, 3, 3e3)
+    pic = make_pic(nr, nz, 0.05, 0.03, dt, n, xa, precision=precision)
+    pic.set_state([e, i])
+    ir = torch.zeros(g.n_er, dtype=torch.float64, device=DEV)
+    iz = torch.zeros(g.n_ez, dtype=torch.float64, device=DEV)
+    cnt = torch.zeros(5, dtype=torch.int64, device=DEV)
+    pic.push_deposit(tgpu(er), tgpu(ez), ir, iz, write=True, counters=cnt)
+    ir_o, iz_o = np.zeros(g.n_er), np.zeros(g.n_ez)
+    cnt_o = np.zeros(4, dtype=np.int64)
+    states = []
+    for sp, q, m in ((e, -QE, ME), (i, QE, M_AR)):
+        s = {k: v.copy() for k, v in sp.items()}
+        _, _, c, _ = O.push(g, dt, q, m, s, er, ez, write=True, ir=ir_o, iz=iz_o)
+        cnt_o += c
+        states.append(s)
+    assert cnt_o[2] > 1.2 * n  # crossings, many of them between mapped cells
+    scale = max(np.max(np.abs(ir_o)), np.max(np.abs(iz_o)))
+    tol = 1e-12 if precision == 0 else 2e-5
+    assert np.max(np.abs(ir.cpu().numpy() - ir_o)) <= tol * scale
+    assert np.max(np.abs(iz.cpu().numpy() - iz_o)) <= tol * scale
+    if precision == 0:
+        assert list(cnt.cpu().numpy()[:4]) == list(cnt_o)
+        for s in range(2):
+            assert_state_close(pic.get_state(s), states[s], what="species %d " % s)
+
+
+def test_field_solve_parity():
+    nr, nz, R, L, dt, xa = 32, 64, 0.1, 0.03, 1.0 / (200 * 60e6), 5
+    g = O.Grid(nr, nz, R, L, xa=xa)
+    rng = np.random.default_rng(5)
+    er0 = rng.normal(size=g.n_er) * 100
+    er0.reshape(nr, nz + 1)[:, [0, -1]] = 0.0
+    ez0 = rng.normal(size=g.n_ez) * 100
+    h0 = rng.normal(size=g.n_h) * 0.1
+    ir = rng.normal(size=g.n_er) * 1e-12
+    iz = rng.normal(size=g.n_ez) * 1e-12
+    v0, v1 = 37.0, -12.0
+    ez0.reshape(nr + 1, nz)[-1, :] = v0 / L
+    er1, ez1, h1, src = O.FieldSolver(g, dt).solve(er0, ez0, h0, ir, iz, v0, v1)
+    pic = make_pic(nr, nz, R, L, dt, 16, xa)
+    out = [torch.empty(k, dtype=torch.float64, device=DEV) for k in (g.n_er, g.n_ez, g.n_h)]
+    s_dev = torch.zeros(1, dtype=torch.float64, device=DEV)
+    pic.field_solve(tgpu(er0), tgpu(ez0), tgpu(h0), tgpu(ir), tgpu(iz), v0, v1, *out, src=s_dev)
+    torch.cuda.synchronize()
+    for got, ref in zip(out, (er1, ez1, h1)):
+        assert np.max(np.abs(got.cpu().numpy() - ref)) <= 1e-10 * np.max(np.abs(ref))
+    np.testing.assert_allclose(s_dev.item(), src, rtol=1e-9)
+
+
+def test_load_parity():
+    M = P()
+    cfg = M.small_reactor(np_init=20000, axis_cells=4)
+    pic = M.Pic(cfg, device=DEV)
+    pic.load_particles()
+    g = O.Grid(cfg["nr"], cfg["nz"], cfg["R"], cfg["L"], xa=4)
+    e, i = O.load(g, 20000, cfg["n0"], cfg["te_ev"], cfg["ti_ev"], cfg["seed"])
+    for s, ref in enumerate((e, i)):
+        got, ref = by_id(pic.get_state(s)), by_id(ref)
+        for k in ("cell", "a", "b", "id"):
+            np.testing.assert_array_equal(got[k], ref[k])
+        np.testing.assert_allclose(got["w"], ref["w"], rtol=1e-14)
+
+
+@pytest.mark.parametrize("field_model", [0, 1])
+def test_step_parity(field_model):
+    M = P()
+    n, xa = 30000, 4
+    cfg = M.small_reactor(np_init=n, capacity_factor=1.5, mcc_on=0, picard_tol=1e-10,
+                          volt=300.0, axis_cells=xa, field_model=field_model)
+    g = O.Grid(cfg["nr"], cfg["nz"], cfg["R"], cfg["L"], xa=xa)
+    e, i = O.load(g, n, 1e15, 8.0, 0.026, 21)
+    pic = M.Pic(cfg, device=DEV)
+    pic.set_state([e, i])
+    if field_model == 1:
+        sim = ES.Sim(g, cfg["dt"], freq=cfg["freq"], volt=cfg["volt"], tol=1e-10,
+                     species=[e, i], cap=int(1.5 * n))
+    else:
+        sim = O.Sim(g, cfg["dt"], freq=cfg["freq"], volt=cfg["volt"], tol=1e-10,
+                    kmax=cfg["picard_max"], species=[e, i], cap=int(1.5 * n))
+    for step in range(3):
+        rc, st = pic.step(1)
+        rco, sto = sim.step()
+        assert rc == 0 and rco == 0
+        its = sto["picard_iters"] if isinstance(sto, dict) else sto.picard_iters
+        assert st["picard_iters"] == its
+        er, ez, _ = pic.fields()
+        for got, ref in ((er, sim.er), (ez, sim.ez)):
+            assert np.max(np.abs(got - ref)) <= 1e-9 * np.max(np.abs(ref)), step
+        for s in range(2):
+            assert_state_close(by_id(pic.get_state(s)), by_id(sim.state(s)), rtol=1e-10,
+                               what="step %d species %d " % (step, s), nz=cfg["nz"])
+
+
+@pytest.mark.parametrize("alpha,row", [(0, 3), (1, 7)])
+def test_fourier_bessel_on_mapped_nodes(alpha, row):
+    M = P()
+    cfg = M.small_reactor(np_init=20000, mcc_on=0, volt=150.0, axis_cells=5)
+    pic = M.Pic(cfg, device=DEV)
+    pic.load_particles()
+    pic.step(2)
+    er, ez, _ = pic.fields()
+    nr, nz = cfg["nr"], cfg["nz"]
+    f = ez.reshape(nr + 1, nz)[:, row] if alpha == 0 else er.reshape(nr, nz + 1)[:, row]
+    ref = FB.coefficients(f, nr, cfg["R"], alpha, 16, xa=5)
+    got = pic.fourier_bessel(alpha, row, 16).cpu().numpy()
+    assert np.max(np.abs(got - ref)) <= 1e-11 * np.max(np.abs(ref))
