@@ -127,6 +127,9 @@ typedef struct pic_view {
   double *er, *ez, *h;        /* E^n, H^n */
   long long step;             /* index n of the next step */
   int real_size;              /* bytes per element of a..w: 8 or 4 */
+  double *wall;               /* charge [C] absorbed at the walls since pic_init, per species s
+                                 at wall + s*(2(nr+1) + nz+1): nodes of z = 0 (nr+1), of z = L
+                                 (nr+1), of r = R (nz+1) */
 } pic_view;
 
 /* Conservation diagnostics (row a9), host struct filled by pic_diag. */

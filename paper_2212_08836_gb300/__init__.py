@@ -67,7 +67,7 @@ class View(C.Structure):
     _fields_ = [("cell", _P * 2), ("a", _P * 2), ("b", _P * 2), ("vr", _P * 2), ("vt", _P * 2),
                 ("vz", _P * 2), ("w", _P * 2), ("id", _P * 2), ("n", _LL * 2), ("cap", _LL * 2),
                 ("next_id", C.c_uint32 * 2), ("er", _P), ("ez", _P), ("h", _P), ("step", _LL),
-                ("real_size", _I)]
+                ("real_size", _I), ("wall", _P)]
 
 
 class DiagOut(C.Structure):
@@ -349,7 +349,18 @@ class Pic:
         out["er"] = self._tensor(v.er, nr * (nz + 1), t.float64)
         out["ez"] = self._tensor(v.ez, (nr + 1) * nz, t.float64)
         out["h"] = self._tensor(v.h, nr * nz, t.float64)
+        out["wall"] = self._tensor(v.wall, 2 * (2 * (nr + 1) + nz + 1), t.float64)
         return out
+
+    def wall_charge(self):
+        """Charge absorbed at the walls since pic_init (host copy): per species
+        a dict of the z = 0, z = L and r = R node tallies [C]."""
+        self.torch.cuda.synchronize(self.device)
+        w = self.view()["wall"].cpu().numpy()
+        nr, nz = self.nr, self.nz
+        blk = 2 * (nr + 1) + nz + 1
+        return [{"z0": w[s * blk:s * blk + nr + 1], "zl": w[s * blk + nr + 1:s * blk + 2 * (nr + 1)],
+                 "r": w[s * blk + 2 * (nr + 1):(s + 1) * blk]} for s in range(2)]
 
     def set_state(self, species, er=None, ez=None, h=None, next_ids=None, step=0):
         """Copy host (numpy) species dicts and fields into the context."""

@@ -1563,6 +1563,7 @@ int pic_get_view(pic_ctx *x, pic_view *v) {
   v->h = x->h;
   v->step = x->step;
   v->real_size = x->mixed ? 4 : 8;
+  v->wall = x->wall;
   return PIC_OK;
 }
 
