@@ -95,7 +95,8 @@ struct pic_ctx {
   // Fourier-Bessel basis (App. A) for (fb_alpha, fb_m), 64 x (nr + 1) doubles
   double *fbb;
   int fb_alpha, fb_m;
-  double *hn;               // pinned host: Picard norms of the last pass
+  double *hn;               // pinned host read-back slots (kHn* below): Picard norms,
+                            // sort totals, step counters
   int graphs;               // 1: passes replayed from captured graphs
   int capturing;            // a pass is being captured (no timing events)
   long long passes;         // passes enqueued (the first one is never captured)
@@ -114,6 +115,20 @@ struct pic_ctx {
 namespace {
 
 const double kSigmaCx = 5e-19;
+
+// 8-byte slots of the pinned read-back buffer pic_ctx::hn: device values are
+// copied there asynchronously and read after one wait per phase
+enum {
+  kHnNorm = 0,    // 3: Picard norms and drive energy of the last pass
+  kHnTotal = 4,   // 2: particles kept by the sort, per species
+  kHnPush = 8,    // 5: push counters of the commit pass
+  kHnKel = 13,    // absorbed kinetic energy
+  kHnCirc = 14,   // 4: circuit state
+  kHnMcc = 18,    // 8: collision counts
+  kHnDe = 26,     // collision energy change
+  kHnIz = 27,     // ionization pairs of the MCC pass
+  kHnSlots = 32
+};
 
 // cyclic-reduction coefficients (the layout k_cr reads) of the tridiagonal
 // matrix with sub-diagonal A[i] (coupling i-1), diagonal B, super-diagonal C,
@@ -309,7 +324,7 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
   x->counts = (int32_t *)K.take((size_t)(ncell + 1) * 4);
   x->coffs = (int32_t *)K.take((size_t)(ncell + 1) * 4);
   x->cursor = (int32_t *)K.take((size_t)ncell * 4);
-  x->total = (long long *)K.take(8);
+  x->total = (long long *)K.take(16);  // one slot per species
   long long sn = pc > ncell + 1 ? pc : ncell + 1;
   x->scan_scratch = K.take(scan_scratch_bytes(sn));
   x->diag = (double *)K.take(8 * 8);
@@ -740,7 +755,7 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
   if (e == cudaSuccess) e = cudaMemsetAsync(x->h2, 0, nh * 8, x->s);
   if (e == cudaSuccess) e = cudaMemsetAsync(x->wall, 0, (size_t)2 * (2 * (nr + 1) + nz + 1) * 8, x->s);
   if (e == cudaSuccess) e = cudaMemsetAsync(x->cnt, 0, sizeof(DevCounters), x->s);
-  if (e == cudaSuccess) e = cudaHostAlloc((void **)&x->hn, 64, cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaHostAlloc((void **)&x->hn, 8 * kHnSlots, cudaHostAllocDefault);
   if (e == cudaSuccess) e = cudaStreamSynchronize(x->s);
   if (e != cudaSuccess) {
     if (x->hn) cudaFreeHost(x->hn);
@@ -822,8 +837,11 @@ int pic_profile_read(pic_ctx *x, double *push_ms, long long *push_launches) {
   return PIC_OK;
 }
 
-int pic_sort(pic_ctx *x) {
-  if (!x) return PIC_E_CONFIG;
+namespace {
+
+// enqueue the sort of both species (each one's kept count into its pinned
+// slot); sort_finish reads the counts after the caller's wait
+int sort_enqueue(pic_ctx *x) {
   for (int s = 0; s < (x->cfg.ions_fixed ? 1 : 2); ++s) {
     SortLaunch S;
     S.ncell = x->g.nr * x->g.nz;
@@ -833,7 +851,7 @@ int pic_sort(pic_ctx *x) {
     S.counts = x->counts;
     S.offs = x->coffs;
     S.cursor = x->cursor;
-    S.total = x->total;
+    S.total = x->total + s;
     S.scan_scratch = x->scan_scratch;
     cudaError_t se;
     if (x->mixed) {
@@ -845,13 +863,27 @@ int pic_sort(pic_ctx *x) {
     }
     if (se != cudaSuccess) return PIC_E_CUDA;
     x->launches += S.n > 0 ? 5 : 3;
-    long long tot = 0;
-    if (cudaMemcpyAsync(&tot, x->total, 8, cudaMemcpyDeviceToHost, x->s) != cudaSuccess)
+    if (cudaMemcpyAsync(x->hn + kHnTotal + s, x->total + s, 8, cudaMemcpyDeviceToHost, x->s) !=
+        cudaSuccess)
       return PIC_E_CUDA;
-    if (cudaStreamSynchronize(x->s) != cudaSuccess) return PIC_E_CUDA;
-    x->n[s] = tot;
     x->cur[s] ^= 1;
   }
+  return PIC_OK;
+}
+
+void sort_finish(pic_ctx *x) {
+  for (int s = 0; s < (x->cfg.ions_fixed ? 1 : 2); ++s)
+    memcpy(&x->n[s], x->hn + kHnTotal + s, 8);
+}
+
+}  // namespace
+
+int pic_sort(pic_ctx *x) {
+  if (!x) return PIC_E_CONFIG;
+  int r = sort_enqueue(x);
+  if (r) return r;
+  if (cudaStreamSynchronize(x->s) != cudaSuccess) return PIC_E_CUDA;
+  sort_finish(x);
   return PIC_OK;
 }
 
@@ -1050,10 +1082,22 @@ int pic_mcc(pic_ctx *x, unsigned long long step, long long *counts, double *de_c
                         M.cseg, M.cgrid, M.cnt, M.keys, M.keys2};
   if (e == cudaSuccess) e = x->mixed ? launch_mcc_collide(M32, x->s) : launch_mcc_collide(M, x->s);
   x->launches += (M.ne > 0 || M.ni > 0 ? 2 : 0);
-  long long tot = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&tot, &x->cnt->iz_slots, 8, cudaMemcpyDeviceToHost, x->s);
+  // the process counts are final after the collisions: read them with the
+  // number of ionizations in one wait (pinned slots)
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(x->hn + kHnIz, &x->cnt->iz_slots, 8, cudaMemcpyDeviceToHost, x->s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(x->hn + kHnMcc, x->cnt->mcc, 64, cudaMemcpyDeviceToHost, x->s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(x->hn + kHnDe, &x->cnt->de_coll, 8, cudaMemcpyDeviceToHost, x->s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(x->s);
   if (e != cudaSuccess) return PIC_E_CUDA;
+  long long tot = 0;
+  unsigned long long hc[8];
+  double de = 0.0;
+  memcpy(&tot, x->hn + kHnIz, 8);
+  memcpy(hc, x->hn + kHnMcc, 64);
+  memcpy(&de, x->hn + kHnDe, 8);
   int rc = PIC_OK;
   unsigned long long capov = 0;
   if (tot > 0) {
@@ -1073,12 +1117,6 @@ int pic_mcc(pic_ctx *x, unsigned long long step, long long *counts, double *de_c
     }
   }
   if (counts || de_coll) {
-    unsigned long long hc[8];
-    double de = 0.0;
-    e = cudaMemcpyAsync(hc, x->cnt->mcc, sizeof(hc), cudaMemcpyDeviceToHost, x->s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&de, &x->cnt->de_coll, 8, cudaMemcpyDeviceToHost, x->s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(x->s);
-    if (e != cudaSuccess) return PIC_E_CUDA;
     hc[7] = capov;
     if (counts)
       for (int k = 0; k < 8; ++k) counts[k] = (long long)hc[k];
@@ -1444,19 +1482,24 @@ int step_end(pic_ctx *x, StepState &T, int *rc) {
     if (mr && mr != PIC_E_CAPACITY) return mr;
     if (mr) *rc = mr;
   }
-  int sr = pic_sort(x);
+  // step counters and the sort's counts: one wait
+  if (x->circ_on &&
+      cudaMemcpyAsync(x->hn + kHnCirc, x->vdev + 4, 32, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return PIC_E_CUDA;
+  if (cudaMemcpyAsync(x->hn + kHnPush, x->cnt->push, 40, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return PIC_E_CUDA;
+  if (cudaMemcpyAsync(x->hn + kHnKel, &x->cnt->ke_lost, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return PIC_E_CUDA;
+  int sr = sort_enqueue(x);
   if (sr) return sr;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return PIC_E_CUDA;
+  sort_finish(x);
   unsigned long long pc[5];
   double kel = 0.0;
   double cst[4] = {0.0, 0.0, T.v1, 0.0};
-  if (x->circ_on &&
-      cudaMemcpyAsync(cst, x->vdev + 4, sizeof(cst), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-    return PIC_E_CUDA;
-  if (cudaMemcpyAsync(pc, x->cnt->push, sizeof(pc), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-    return PIC_E_CUDA;
-  if (cudaMemcpyAsync(&kel, &x->cnt->ke_lost, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-    return PIC_E_CUDA;
-  if (cudaStreamSynchronize(s) != cudaSuccess) return PIC_E_CUDA;
+  memcpy(pc, x->hn + kHnPush, 40);
+  memcpy(&kel, x->hn + kHnKel, 8);
+  if (x->circ_on) memcpy(cst, x->hn + kHnCirc, 32);
   if (x->prof) prof_collect(x);
   S.substep_err = (long long)pc[0];
   S.absorbed = (long long)pc[1];
