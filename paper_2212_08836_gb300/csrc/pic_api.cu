@@ -1050,8 +1050,20 @@ int pic_es_solve(pic_ctx *x, const double *Q, double phi0, double *er, double *e
   return cuda_rc(e);
 }
 
+namespace {
+int mcc_run(pic_ctx *x, unsigned long long step, long long *counts, double *de_coll);
+}  // namespace
+
 int pic_mcc(pic_ctx *x, unsigned long long step, long long *counts, double *de_coll) {
   if (!x) return PIC_E_CONFIG;
+  return mcc_run(x, step, counts, de_coll);
+}
+
+namespace {
+// one MCC pass; de_coll (nullable) is read after the appended pairs are
+// counted in, which costs a wait: the step instead copies the pinned slot
+// kHnDe with its other counters (de_coll = nullptr here)
+int mcc_run(pic_ctx *x, unsigned long long step, long long *counts, double *de_coll) {
   cudaError_t e = cudaMemsetAsync(x->cnt->mcc, 0, sizeof(x->cnt->mcc), x->s);
   if (e == cudaSuccess) e = cudaMemsetAsync(&x->cnt->de_coll, 0, 8, x->s);
   if (e == cudaSuccess) e = cudaMemsetAsync(&x->cnt->iz_slots, 0, 8, x->s);
@@ -1088,16 +1100,12 @@ int pic_mcc(pic_ctx *x, unsigned long long step, long long *counts, double *de_c
     e = cudaMemcpyAsync(x->hn + kHnIz, &x->cnt->iz_slots, 8, cudaMemcpyDeviceToHost, x->s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(x->hn + kHnMcc, x->cnt->mcc, 64, cudaMemcpyDeviceToHost, x->s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(x->hn + kHnDe, &x->cnt->de_coll, 8, cudaMemcpyDeviceToHost, x->s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(x->s);
   if (e != cudaSuccess) return PIC_E_CUDA;
   long long tot = 0;
   unsigned long long hc[8];
-  double de = 0.0;
   memcpy(&tot, x->hn + kHnIz, 8);
   memcpy(hc, x->hn + kHnMcc, 64);
-  memcpy(&de, x->hn + kHnDe, 8);
   int rc = PIC_OK;
   unsigned long long capov = 0;
   if (tot > 0) {
@@ -1116,14 +1124,20 @@ int pic_mcc(pic_ctx *x, unsigned long long step, long long *counts, double *de_c
       x->next_id[1] += (uint32_t)tot;
     }
   }
-  if (counts || de_coll) {
-    hc[7] = capov;
-    if (counts)
-      for (int k = 0; k < 8; ++k) counts[k] = (long long)hc[k];
-    if (de_coll) *de_coll = de;
+  hc[7] = capov;
+  if (counts)
+    for (int k = 0; k < 8; ++k) counts[k] = (long long)hc[k];
+  if (de_coll) {
+    // the appended pairs' energy is in de_coll after the append
+    if (cudaMemcpyAsync(x->hn + kHnDe, &x->cnt->de_coll, 8, cudaMemcpyDeviceToHost, x->s) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(x->s) != cudaSuccess)
+      return PIC_E_CUDA;
+    memcpy(de_coll, x->hn + kHnDe, 8);
   }
   return rc;
 }
+}  // namespace
 
 namespace {
 
@@ -1478,7 +1492,7 @@ int step_end(pic_ctx *x, StepState &T, int *rc) {
   }
   S.src_energy = T.src;
   if (x->cfg.mcc_on) {
-    int mr = pic_mcc(x, (unsigned long long)x->step, S.mcc, &S.de_coll);
+    int mr = mcc_run(x, (unsigned long long)x->step, S.mcc, nullptr);
     if (mr && mr != PIC_E_CAPACITY) return mr;
     if (mr) *rc = mr;
   }
@@ -1490,6 +1504,9 @@ int step_end(pic_ctx *x, StepState &T, int *rc) {
     return PIC_E_CUDA;
   if (cudaMemcpyAsync(x->hn + kHnKel, &x->cnt->ke_lost, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return PIC_E_CUDA;
+  if (x->cfg.mcc_on &&
+      cudaMemcpyAsync(x->hn + kHnDe, &x->cnt->de_coll, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return PIC_E_CUDA;
   int sr = sort_enqueue(x);
   if (sr) return sr;
   if (cudaStreamSynchronize(s) != cudaSuccess) return PIC_E_CUDA;
@@ -1500,6 +1517,7 @@ int step_end(pic_ctx *x, StepState &T, int *rc) {
   memcpy(pc, x->hn + kHnPush, 40);
   memcpy(&kel, x->hn + kHnKel, 8);
   if (x->circ_on) memcpy(cst, x->hn + kHnCirc, 32);
+  if (x->cfg.mcc_on) memcpy(&S.de_coll, x->hn + kHnDe, 8);
   if (x->prof) prof_collect(x);
   S.substep_err = (long long)pc[0];
   S.absorbed = (long long)pc[1];
