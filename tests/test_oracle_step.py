@@ -5,7 +5,9 @@ Gauss residual at interior nodes constant to roundoff over full steps (with
 drive, wall losses and ionization); total particle + field energy is
 conserved to the nonlinear tolerance and the error shrinks with it; a cold
 plasma oscillates at the CN frequency (2/dt)*atan(w_pe*dt/2); a step that
-fails to converge leaves the state untouched.
+fails to converge leaves the state untouched; on a tiny grid the Picard step
+equals the fixed point found by Newton with a finite-difference Jacobian on
+the full nonlinear system (brute force).
 """
 import numpy as np
 import pytest
@@ -147,3 +149,77 @@ def test_noconv_leaves_state_unchanged():
         np.testing.assert_array_equal(before[k], after[k])
     np.testing.assert_array_equal(er, sim.er)
     assert sim.step_index == 0
+
+
+def test_picard_step_equals_newton_brute_force_on_a_tiny_grid():
+    """The implicit step is the fixed point E = G(E) of push + field solve
+    (Sec. 2.1).  On a 3x4 grid with 8 strongly weighted electrons (so that the
+    field couples back), Newton with a finite-difference Jacobian on the full
+    nonlinear system, no Picard, reaches the same E^{n+1} and particle state as
+    the oracle's Picard step."""
+    nr, nz = 3, 4
+    g = O.Grid(nr, nz, 0.01, 0.01)
+    dt, f, V = 2e-10, 60e6, 30.0
+    rng = np.random.default_rng(11)
+    n = 8
+    sp = O.empty_species(n)
+    ic, jc = rng.integers(0, nr, n), rng.integers(0, nz, n)
+    sp["cell"][:] = ic * nz + jc
+    sp["a"][:] = 0.3 + 0.4 * rng.random(n)
+    sp["b"][:] = 0.3 + 0.4 * rng.random(n)
+    sp["vr"][:], sp["vt"][:], sp["vz"][:] = rng.normal(size=(3, n)) * 2e5
+    sp["w"][:] = 3e7
+    sp["id"][:] = np.arange(n)
+    ions = {k: v.copy() for k, v in sp.items()}
+    ions["vr"][:] = ions["vt"][:] = ions["vz"][:] = 0.0
+    sim = O.Sim(g, dt, freq=f, volt=V, tol=1e-14, kmax=200, species=[sp, ions])
+    er0, ez0, h0 = sim.er.copy(), sim.ez.copy(), sim.h.copy()
+    F = O.FieldSolver(g, dt)
+    v1 = V * np.sin(2 * np.pi * f * dt)
+    mr = np.ones((nr, nz + 1), bool)
+    mr[:, [0, nz]] = False
+    ur = np.flatnonzero(mr.ravel())            # unknown E_r edges
+    uz = np.arange(nr * nz)                     # unknown E_z edges (i < nr)
+
+    def fields(x):
+        er, ez = np.zeros(g.n_er), np.zeros(g.n_ez)
+        er[ur], ez[uz] = x[:len(ur)], x[len(ur):]
+        ez[nr * nz:] = v1 / g.L
+        return er, ez
+
+    def G(x):
+        er1, ez1 = fields(x)
+        ir, iz = np.zeros(g.n_er), np.zeros(g.n_ez)
+        for s, (q, m) in enumerate(((-QE, ME), (QE, M_AR))):
+            O.push(g, dt, q, m, sim.state(s), 0.5 * (er0 + er1), 0.5 * (ez0 + ez1), ir=ir, iz=iz)
+        ern, ezn, _, _ = F.solve(er0, ez0, h0, ir, iz, 0.0, v1)
+        return np.concatenate([ern[ur], ezn[uz]])
+
+    x = G(np.concatenate([er0[ur], ez0[uz]]))
+    for _ in range(20):
+        r = x - G(x)
+        if np.linalg.norm(r) <= 1e-14 * np.linalg.norm(x):
+            break
+        J = np.eye(len(x))
+        for k in range(len(x)):
+            hk = 1e-6 * max(abs(x[k]), 1e-3 * np.max(np.abs(x)))
+            e = np.zeros(len(x))
+            e[k] = hk
+            J[:, k] -= (G(x + e) - G(x - e)) / (2 * hk)
+        x = x - np.linalg.solve(J, r)
+    assert np.linalg.norm(x - G(x)) <= 1e-12 * np.linalg.norm(x)
+    rc, st = sim.step()
+    assert rc == 0 and st.picard_iters > 2  # the coupling is strong enough to iterate
+    ern, ezn = fields(x)
+    scale = np.max(np.abs(x))
+    assert np.max(np.abs(sim.er[ur] - ern[ur])) <= 1e-10 * scale
+    assert np.max(np.abs(sim.ez[uz] - ezn[uz])) <= 1e-10 * scale
+    # the committed particles follow the Newton half field
+    ref = O.empty_species(n)
+    for k in O.FIELDS:
+        ref[k][:] = sp[k]
+    O.push(g, dt, -QE, ME, ref, 0.5 * (er0 + ern), 0.5 * (ez0 + ezn), write=True)
+    got = sim.state(0)
+    o = np.argsort(got["id"])
+    for k in ("a", "b", "vr", "vz"):
+        np.testing.assert_allclose(got[k][o], ref[k], rtol=1e-9, atol=1e-12 * np.max(np.abs(ref[k])))
