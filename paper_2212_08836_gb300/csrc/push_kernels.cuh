@@ -156,10 +156,20 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_push_fast(PushL
   const long long qoff = (long long)blockIdx.x * L.qseg;
   const long long n = L.n_dev ? *L.n_dev : L.n;
   long long base = (long long)blockIdx.x * blockDim.x;
+  // FP32 form: the next tile's state is loaded while this one is pushed (the
+  // kernel is issue-bound; the FP64 form is bound by its FP64 pipe instead)
+  constexpr bool kPrefetch = sizeof(T) == 4;
+  PState<T> nxt;
+  if (kPrefetch) load_state(L.p, base + threadIdx.x, n, nxt);
   for (; base < n; base += stride) {
     const long long p = base + threadIdx.x;
     PState<T> cur;
-    load_state(L.p, p, n, cur);
+    if (kPrefetch) {
+      cur = nxt;
+      load_state(L.p, base + stride + threadIdx.x, n, nxt);
+    } else {
+      load_state(L.p, p, n, cur);
+    }
     const int c0 = cur.c;
     const T a = cur.a, b = cur.b, w = cur.w;
     T ur = zero, ut = zero, uz = zero;
@@ -255,11 +265,36 @@ __global__ void __launch_bounds__(256) k_push_general(PushLaunchT<T> L) {
   if (L.queue) {
     __shared__ int s_pre[kMaxFastBlocks + 1];
     const int total = seg_prefix(L.qblock, L.qgrid, s_pre);
-    for (long long q = gtid; q < total; q += gstride) {
-      long long k = seg_entry(s_pre, L.qgrid, L.qseg, (int)q);
-      long long p = L.queue[k];
-      push_general<T, kB>(G, p, L.p.cell[p], L.p.a[p], L.p.b[p], L.p.vr[p], L.p.vt[p],
-                          L.p.vz[p], L.p.w[p], L.q_da[k], L.q_db[k], tl);
+    if (sizeof(T) == 4) {
+      // FP32 form: the next entry's start state (a scattered re-read from the
+      // store) is loaded while this one is pushed
+      struct Ent {
+        long long p;
+        PState<T> s;
+        T da, db;
+      };
+      auto fetch = [&](long long q, Ent &en) {
+        const long long k = seg_entry(s_pre, L.qgrid, L.qseg, (int)q);
+        en.p = L.queue[k];
+        en.da = L.q_da[k];
+        en.db = L.q_db[k];
+        load_state(L.p, en.p, en.p + 1, en.s);
+      };
+      Ent nx;
+      if (gtid < total) fetch(gtid, nx);
+      for (long long q = gtid; q < total; q += gstride) {
+        const Ent cu = nx;
+        if (q + gstride < total) fetch(q + gstride, nx);
+        push_general<T, kB>(G, cu.p, cu.s.c, cu.s.a, cu.s.b, cu.s.vr, cu.s.vt, cu.s.vz, cu.s.w,
+                            cu.da, cu.db, tl);
+      }
+    } else {
+      for (long long q = gtid; q < total; q += gstride) {
+        long long k = seg_entry(s_pre, L.qgrid, L.qseg, (int)q);
+        long long p = L.queue[k];
+        push_general<T, kB>(G, p, L.p.cell[p], L.p.a[p], L.p.b[p], L.p.vr[p], L.p.vt[p],
+                            L.p.vz[p], L.p.w[p], L.q_da[k], L.q_db[k], tl);
+      }
     }
   } else {
     const long long n = L.n_dev ? *L.n_dev : L.n;
