@@ -50,6 +50,7 @@ extern "C" {
 #define PIC_E_NAN -6       /* non-finite field or residual */
 #define PIC_E_STATE -7     /* state arrays inconsistent (counts beyond capacity) */
 #define PIC_E_WORKSPACE -8 /* workspace missing, too small or misaligned */
+#define PIC_E_IO -9        /* checkpoint file could not be written or read, or is malformed */
 
 #define PIC_FP64 0         /* plain method: FP64 particles, push and deposit */
 #define PIC_MIXED 1        /* FP32 particle state, push and deposit; FP64 field solve,
@@ -266,6 +267,22 @@ int pic_node_charge(pic_ctx *ctx, double *q_dev);
 
 /* Device pointers, counts and capacities of the context's state. */
 int pic_get_view(pic_ctx *ctx, pic_view *out);
+
+/* Checkpoint and resume.  pic_save writes the complete state of the method
+ * at step n to a file: both species (counts, next ids, every particle field
+ * in the context's precision), E^n, H^n, the wall tallies, the step index,
+ * the blocking-capacitor state, the generator waveform set by pic_set_drive,
+ * the carried node charge of the electrostatic model and the last Picard
+ * contraction (the speculation hint), behind a header with the mesh and
+ * model.  pic_load restores them into a context created with the same nr,
+ * nz, precision and field model; the learned-start history restarts (the
+ * first steps use the plain start).  A run resumed from a checkpoint takes
+ * the same steps as the uninterrupted one (the collision random numbers
+ * depend only on particle ids and the step index).  Both synchronise.
+ * Errors: PIC_E_IO (file), PIC_E_STATE (mesh, model or precision differ, or
+ * counts beyond the capacity), PIC_E_CUDA. */
+int pic_save(pic_ctx *ctx, const char *path);
+int pic_load(pic_ctx *ctx, const char *path);
 
 /* Set particle counts / next ids / step index after the caller wrote state
  * through pic_get_view.  Errors: PIC_E_STATE (count beyond capacity). */

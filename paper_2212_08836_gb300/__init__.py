@@ -26,6 +26,7 @@ PIC_E_CAPACITY = -5
 PIC_E_NAN = -6
 PIC_E_STATE = -7
 PIC_E_WORKSPACE = -8
+PIC_E_IO = -9
 PIC_FP64 = 0
 PIC_MIXED = 1
 
@@ -119,6 +120,8 @@ def _load_lib():
     L.pic_circuit_set.argtypes = [_P, _D, _D]
     L.pic_set_drive.argtypes = [_P, _I, _P, _P, _P]
     L.pic_set_picard.argtypes = [_P, _D, _I]
+    L.pic_save.argtypes = [_P, C.c_char_p]
+    L.pic_load.argtypes = [_P, C.c_char_p]
     L.pic_fourier_bessel.argtypes = [_P, _I, _I, _I, _P]
     L.pic_ensemble_create.argtypes = [_P, _I, C.POINTER(_P)]
     L.pic_ensemble_destroy.argtypes = [_P]
@@ -262,6 +265,14 @@ class Pic:
 
     def set_circuit(self, q, phi):
         _check(lib().pic_circuit_set(self._h, float(q), float(phi)), "pic_circuit_set")
+
+    def save(self, path):
+        """Checkpoint of the complete state at the current step."""
+        _check(lib().pic_save(self._h, os.fsencode(path)), "pic_save")
+
+    def load(self, path):
+        """Resume from a checkpoint written by save (same mesh, model, precision)."""
+        _check(lib().pic_load(self._h, os.fsencode(path)), "pic_load")
 
     def set_picard(self, tol, kmax):
         """Picard tolerance and iteration limit of the following steps."""

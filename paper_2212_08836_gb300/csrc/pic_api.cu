@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <chrono>
+#include <cstdio>
 #include <cmath>
 #include <vector>
 
@@ -494,6 +495,7 @@ const char *pic_strerror(int code) {
     case PIC_E_NAN: return "non-finite field or residual";
     case PIC_E_STATE: return "inconsistent state";
     case PIC_E_WORKSPACE: return "workspace missing, too small or misaligned";
+    case PIC_E_IO: return "checkpoint file could not be written or read";
     default: return "unknown status";
   }
 }
@@ -1625,6 +1627,136 @@ int pic_get_view(pic_ctx *x, pic_view *v) {
   v->step = x->step;
   v->real_size = x->mixed ? 4 : 8;
   v->wall = x->wall;
+  return PIC_OK;
+}
+
+namespace {
+
+// checkpoint header (little-endian host layout, version 1)
+struct CkptHeader {
+  char magic[8];
+  int32_t version, nr, nz, precision, field_model, real_size, circ_on, qn_valid, nharm, xa;
+  long long n[2], step;
+  uint32_t next_id[2];
+  double circ[4], rho_prev;
+  double hamp[64], hfreq[64], hph[64];
+};
+const char kCkptMagic[8] = {'P', 'I', 'C', 'C', 'K', 'P', 'T', '1'};
+
+// the device arrays of a checkpoint, in file order
+extern "C++" template <typename F>
+int ckpt_arrays(pic_ctx *x, const long long n[2], F &&f) {
+  const int nr = x->g.nr, nz = x->g.nz;
+  const size_t rs = x->mixed ? 4 : 8;
+  for (int s = 0; s < 2; ++s) {
+    Parts &P = cur(x, s);
+    void *arr[8] = {P.cell, P.a, P.b, P.vr, P.vt, P.vz, P.w, P.id};
+    for (int k = 0; k < 8; ++k) {
+      const size_t es = (k == 0 || k == 7) ? 4 : rs;
+      if (int r = f(arr[k], (size_t)n[s] * es)) return r;
+    }
+  }
+  if (int r = f(x->er, (size_t)nr * (nz + 1) * 8)) return r;
+  if (int r = f(x->ez, (size_t)(nr + 1) * nz * 8)) return r;
+  if (int r = f(x->h, (size_t)nr * nz * 8)) return r;
+  if (int r = f(x->wall, (size_t)2 * (2 * (nr + 1) + nz + 1) * 8)) return r;
+  if (x->cfg.field_model == PIC_FIELD_ES)
+    if (int r = f(x->qn, (size_t)(nr + 1) * (nz + 1) * 8)) return r;
+  return PIC_OK;
+}
+
+}  // namespace
+
+int pic_save(pic_ctx *x, const char *path) {
+  if (!x || !path) return PIC_E_CONFIG;
+  CkptHeader H;
+  memset(&H, 0, sizeof(H));
+  memcpy(H.magic, kCkptMagic, 8);
+  H.version = 1;
+  H.nr = x->g.nr;
+  H.nz = x->g.nz;
+  H.precision = x->cfg.precision;
+  H.field_model = x->cfg.field_model;
+  H.real_size = x->mixed ? 4 : 8;
+  H.circ_on = x->circ_on;
+  H.qn_valid = x->qn_valid;
+  H.nharm = x->nharm;
+  H.xa = x->g.xa;
+  H.n[0] = x->n[0];
+  H.n[1] = x->n[1];
+  H.step = x->step;
+  H.next_id[0] = x->next_id[0];
+  H.next_id[1] = x->next_id[1];
+  H.rho_prev = x->rho_prev;
+  for (int k = 0; k < 64; ++k) {
+    H.hamp[k] = x->hamp[k];
+    H.hfreq[k] = x->hfreq[k];
+    H.hph[k] = x->hph[k];
+  }
+  if (cudaStreamSynchronize(x->s) != cudaSuccess) return PIC_E_CUDA;
+  if (x->circ_on && cudaMemcpy(H.circ, x->vdev + 4, 32, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return PIC_E_CUDA;
+  FILE *fp = fopen(path, "wb");
+  if (!fp) return PIC_E_IO;
+  int rc = fwrite(&H, sizeof(H), 1, fp) == 1 ? PIC_OK : PIC_E_IO;
+  std::vector<char> buf;
+  if (!rc)
+    rc = ckpt_arrays(x, H.n, [&](void *dev, size_t bytes) {
+      if (!bytes) return PIC_OK;
+      buf.resize(bytes);
+      if (cudaMemcpy(buf.data(), dev, bytes, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return PIC_E_CUDA;
+      return fwrite(buf.data(), 1, bytes, fp) == bytes ? PIC_OK : PIC_E_IO;
+    });
+  if (fclose(fp) != 0 && !rc) rc = PIC_E_IO;
+  return rc;
+}
+
+int pic_load(pic_ctx *x, const char *path) {
+  if (!x || !path) return PIC_E_CONFIG;
+  FILE *fp = fopen(path, "rb");
+  if (!fp) return PIC_E_IO;
+  CkptHeader H;
+  int rc = fread(&H, sizeof(H), 1, fp) == 1 ? PIC_OK : PIC_E_IO;
+  if (!rc && (memcmp(H.magic, kCkptMagic, 8) != 0 || H.version != 1 || H.nharm < 0 ||
+              H.nharm > 64))
+    rc = PIC_E_IO;
+  if (!rc && (H.nr != x->g.nr || H.nz != x->g.nz || H.precision != x->cfg.precision ||
+              H.field_model != x->cfg.field_model || H.xa != x->g.xa ||
+              H.real_size != (x->mixed ? 4 : 8) || H.n[0] < 0 || H.n[1] < 0 ||
+              H.n[0] > x->cap[0] || H.n[1] > x->cap[1] || H.step < 0 ||
+              (H.circ_on != 0) != (x->circ_on != 0)))
+    rc = PIC_E_STATE;
+  std::vector<char> buf;
+  if (!rc && cudaStreamSynchronize(x->s) != cudaSuccess) rc = PIC_E_CUDA;
+  if (!rc)
+    rc = ckpt_arrays(x, H.n, [&](void *dev, size_t bytes) {
+      if (!bytes) return PIC_OK;
+      buf.resize(bytes);
+      if (fread(buf.data(), 1, bytes, fp) != bytes) return PIC_E_IO;
+      return cudaMemcpy(dev, buf.data(), bytes, cudaMemcpyHostToDevice) == cudaSuccess
+                 ? PIC_OK
+                 : PIC_E_CUDA;
+    });
+  fclose(fp);
+  if (rc) return rc;
+  if (x->circ_on && cudaMemcpy(x->vdev + 4, H.circ, 32, cudaMemcpyHostToDevice) != cudaSuccess)
+    return PIC_E_CUDA;
+  x->n[0] = H.n[0];
+  x->n[1] = H.n[1];
+  x->next_id[0] = H.next_id[0];
+  x->next_id[1] = H.next_id[1];
+  x->step = H.step;
+  x->rho_prev = H.rho_prev;
+  x->qn_valid = H.qn_valid;
+  x->nharm = H.nharm;
+  for (int k = 0; k < 64; ++k) {
+    x->hamp[k] = H.hamp[k];
+    x->hfreq[k] = H.hfreq[k];
+    x->hph[k] = H.hph[k];
+  }
+  x->hist_n = 1;
+  x->sample_valid = 0;
   return PIC_OK;
 }
 

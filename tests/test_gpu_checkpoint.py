@@ -1,0 +1,80 @@
+"""Checkpoint and resume (pic_save / pic_load): a run resumed from a
+checkpoint takes the same steps as the uninterrupted run, for the FP64 and
+mixed forms, the electrostatic model and the blocking capacitor, up to the
+order of the FP64 atomic additions of the deposit; mismatched contexts and
+unreadable files are refused."""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__ as G
+    G.build()
+
+
+def P():
+    import paper_2212_08836_gb300 as M
+    return M
+
+
+def by_id(sp):
+    o = np.argsort(sp["id"], kind="stable")
+    return {k: v[o] for k, v in sp.items()}
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(precision=1), dict(field_model=1, cblock=3e-11),
+                                dict(cblock=3e-11, axis_cells=3)])
+def test_resumed_run_matches_the_uninterrupted_one(kw, tmp_path):
+    M = P()
+    cfg = M.small_reactor(np_init=20000, mcc_on=1, volt=200.0, gas_pressure=10.0,
+                          picard_tol=1e-8 if kw.get("precision", 0) == 0 else 1e-5, **kw)
+    path = str(tmp_path / "ckpt.bin")
+    a = M.Pic(cfg, device=DEV)
+    a.load_particles()
+    a.step(3)
+    a.save(path)
+    for _ in range(3):
+        a.step(1)
+    b = M.Pic(cfg, device=DEV)
+    b.load(path)
+    for _ in range(3):
+        b.step(1)
+    fa, fb = a.fields(), b.fields()
+    ftol = 1e-10 if kw.get("precision", 0) == 0 else 1e-5
+    for x, y in zip(fa, fb):
+        assert np.max(np.abs(x - y)) <= ftol * max(np.max(np.abs(x)), 1e-300)
+    assert a.circuit() == pytest.approx(b.circuit(), rel=1e-9, abs=1e-30)
+    for s in range(2):
+        ga, gb = by_id(a.get_state(s)), by_id(b.get_state(s))
+        assert np.array_equal(ga["id"], gb["id"])  # same ionizations, same new ids
+        assert np.mean(ga["cell"] == gb["cell"]) > 0.999
+        for k in ("vr", "vz"):
+            d = np.abs(ga[k].astype(np.float64) - gb[k])
+            assert np.quantile(d, 0.999) <= 1e-6 * np.max(np.abs(ga[k]))
+
+
+def test_refused_checkpoints(tmp_path):
+    M = P()
+    path = str(tmp_path / "c.bin")
+    a = M.Pic(M.small_reactor(np_init=5000), device=DEV)
+    a.load_particles()
+    a.save(path)
+    other = M.Pic(M.small_reactor(np_init=5000, nz=48), device=DEV)
+    with pytest.raises(M.PicError) as e:
+        other.load(path)
+    assert e.value.code == M.PIC_E_STATE
+    with pytest.raises(M.PicError) as e:
+        other.load(str(tmp_path / "missing.bin"))
+    assert e.value.code == M.PIC_E_IO
+    with open(path, "r+b") as f:
+        f.write(b"XXXX")
+    with pytest.raises(M.PicError) as e:
+        a.load(path)
+    assert e.value.code == M.PIC_E_IO
