@@ -265,6 +265,14 @@ int pic_diag(pic_ctx *ctx, pic_diag_out *out);
  * ((nr+1)*(nz+1) doubles, caller zeroes).  Asynchronous. */
 int pic_node_charge(pic_ctx *ctx, double *q_dev);
 
+/* Row a9: Gauss residual of the state, eps div_h E^n - Q^n on the interior
+ * nodes (i < nr, 0 < j < nz) in the flux form of the integral mesh, Q^n the
+ * S1 x S1 node charge of both species; zero on the other nodes.  The
+ * charge-conserving scheme keeps it at its initial value (zero for the pair
+ * loading) to rounding.  res_dev: (nr+1)*(nz+1) doubles (device).
+ * Asynchronous.  Errors: PIC_E_CONFIG, PIC_E_CUDA. */
+int pic_gauss_residual(pic_ctx *ctx, double *res_dev);
+
 /* Device pointers, counts and capacities of the context's state. */
 int pic_get_view(pic_ctx *ctx, pic_view *out);
 

@@ -120,6 +120,7 @@ def _load_lib():
     L.pic_circuit_set.argtypes = [_P, _D, _D]
     L.pic_set_drive.argtypes = [_P, _I, _P, _P, _P]
     L.pic_set_picard.argtypes = [_P, _D, _I]
+    L.pic_gauss_residual.argtypes = [_P, _P]
     L.pic_save.argtypes = [_P, C.c_char_p]
     L.pic_load.argtypes = [_P, C.c_char_p]
     L.pic_fourier_bessel.argtypes = [_P, _I, _I, _I, _P]
@@ -315,6 +316,13 @@ class Pic:
         q = t.zeros((self.nr + 1) * (self.nz + 1), dtype=t.float64, device=self.device)
         _check(lib().pic_node_charge(self._h, q.data_ptr()), "pic_node_charge")
         return q
+
+    def gauss_residual(self):
+        """eps div_h E - Q on the interior nodes (device tensor, zero elsewhere)."""
+        t = self.torch
+        r = t.empty((self.nr + 1) * (self.nz + 1), dtype=t.float64, device=self.device)
+        _check(lib().pic_gauss_residual(self._h, r.data_ptr()), "pic_gauss_residual")
+        return r
 
     def mcc_constants(self):
         v = [_D(0.0) for _ in range(4)]

@@ -123,6 +123,25 @@ __global__ void __launch_bounds__(256) k_node_charge(Grid g, PartsT<T> p, long l
   atomicAdd(&Q[(ic + 1) * nz1 + jc + 1], qw * a * b);
 }
 
+// Gauss residual eps div_h E - Q on the interior nodes (i < nr, 0 < j < nz),
+// in the flux form of the integral mesh; zero elsewhere.  Q holds the node
+// charge on entry and the residual on exit.
+__global__ void __launch_bounds__(256) k_gauss_residual(Grid g, double eps, const double *er,
+                                                        const double *ez, double *Q) {
+  const int nz = g.nz, nz1 = nz + 1;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)(g.nr + 1) * nz1) return;
+  const int i = (int)(t / nz1), j = (int)(t - (t / nz1) * nz1);
+  if (i >= g.nr || j == 0 || j == nz) {
+    Q[t] = 0.0;
+    return;
+  }
+  double flux = kTwoPi * g_rcentre(g, i) * g.dz * er[i * nz1 + j];
+  if (i >= 1) flux -= kTwoPi * g_rcentre(g, i - 1) * g.dz * er[(i - 1) * nz1 + j];
+  flux += g_area_z(g, i) * (ez[i * nz + j] - ez[i * nz + j - 1]);
+  Q[t] = eps * flux - Q[t];
+}
+
 // Fourier-Bessel coefficients (App. A, Eq. A2): block m sums basis row m
 // against the field samples f[k * stride], k < n, in a fixed order
 __global__ void __launch_bounds__(128) k_fourier_bessel(const double *__restrict__ basis,
@@ -142,6 +161,13 @@ __global__ void __launch_bounds__(128) k_fourier_bessel(const double *__restrict
 }
 
 }  // namespace
+
+cudaError_t launch_gauss_residual(const Grid &g, double eps, const double *er, const double *ez,
+                                  double *Q, cudaStream_t s) {
+  const long long n = (long long)(g.nr + 1) * (g.nz + 1);
+  k_gauss_residual<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, eps, er, ez, Q);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_fourier_bessel(const double *basis, const double *f, int stride, int n,
                                   int nmodes, double *coef, cudaStream_t s) {

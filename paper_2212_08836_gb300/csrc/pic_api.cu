@@ -1605,6 +1605,16 @@ int pic_node_charge(pic_ctx *x, double *q) {
   return cuda_rc(e);
 }
 
+int pic_gauss_residual(pic_ctx *x, double *res) {
+  if (!x || !res) return PIC_E_CONFIG;
+  const size_t nn = (size_t)(x->g.nr + 1) * (x->g.nz + 1);
+  if (cudaMemsetAsync(res, 0, nn * 8, x->s) != cudaSuccess) return PIC_E_CUDA;
+  int r = pic_node_charge(x, res);
+  if (r) return r;
+  x->launches += 3;
+  return cuda_rc(launch_gauss_residual(x->g, x->eps, x->er, x->ez, res, x->s));
+}
+
 int pic_get_view(pic_ctx *x, pic_view *v) {
   if (!x || !v) return PIC_E_CONFIG;
   for (int s = 0; s < 2; ++s) {
