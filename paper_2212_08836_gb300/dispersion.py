@@ -110,6 +110,68 @@ def run(model="es", nr=64, nz=128, R=0.1, L=0.03, n0=1e16, ppc=64, sheath=1.8e-3
             "relaxed": np.array(relaxed, dtype=np.float64).reshape(-1, 2)}
 
 
+def bessel_zero0(m):
+    """m-th positive zero of J_0 (scipy)."""
+    from scipy import special as sp
+    return float(sp.jn_zeros(0, m)[m - 1])
+
+
+def ring(model="es", mode="symmetric", m=1, nr=64, nz=128, R=0.1, L=0.03, n0=1e16, ppc=64,
+         sheath=1.8e-3, u0=5e4, steps=800, z_sample=1e-3, dt=1e-10, mu=0.0, te_ev=3.0, seed=0,
+         device="cuda:0", precision=PIC_FP64, tol=1e-7):
+    """Free oscillation of one surface mode: the electrons of the loaded slab
+    get the axial velocity u0 J_0(chi_{0,m} r / R), uniform in z (symmetric
+    mode: the slab moves between the two sheaths, the plasma series resonance
+    at k -> 0) or of opposite sign in the two halves of the gap (antisymmetric
+    mode); the ringing of the Fourier-Bessel coefficient c_m of E_z in the
+    powered sheath gives the mode's frequency at k = chi_{0,m} / R (the
+    perturbed potential vanishes on the side wall, so both symmetries use the
+    zeros of J_0).  Returns the frequency from the FFT peak (parabolic
+    interpolation on a 16x zero-padded spectrum) and the time series."""
+    import torch
+    fm = PIC_FIELD_ES if model == "es" else PIC_FIELD_EM
+    cfg = small_reactor(nr=nr, nz=nz, R=R, L=L, dt=dt, freq=1e6, volt=0.0, n0=n0,
+                        te_ev=te_ev, np_init=int(ppc * nr * nz), capacity_factor=1.0, mcc_on=0,
+                        ions_fixed=1, field_model=fm, precision=precision, mu=mu, seed=seed,
+                        picard_tol=tol, picard_max=100)
+    pic = Pic(cfg, device=device, stream=torch.cuda.Stream(device=device))
+    sp = slab_plasma(nr, nz, R, L, n0, ppc, sheath, te_ev, seed)
+    e = sp[0]
+    chi = bessel_zero0(m)
+    from scipy import special as ss
+    xi = e["cell"] // nz + e["a"]   # r / dr on the uniform mesh
+    eta = e["cell"] % nz + e["b"]
+    prof = ss.j0(chi * xi / nr)     # J_0(chi r / R)
+    sign = np.ones_like(eta) if mode == "symmetric" else np.where(eta < 0.5 * nz, -1.0, 1.0)
+    e["vz"] = e["vz"] + u0 * prof * sign
+    pic.set_state(sp)
+    er = torch.zeros(nr * (nz + 1), dtype=torch.float64, device=device)
+    ez = torch.zeros((nr + 1) * nz, dtype=torch.float64, device=device)
+    pic.es_solve(pic.node_charge(), 0.0, er, ez)
+    torch.cuda.synchronize(device)
+    pic.set_state(sp, er=er.cpu().numpy(), ez=ez.cpu().numpy())
+    row = int(round(z_sample / (L / nz) - 0.5))
+    coef = torch.empty((steps, m), dtype=torch.float64, device=device)
+    iters = []
+    for k in range(steps):
+        rc, st = pic.step(1, check=False)
+        if rc not in (0, -4):
+            raise RuntimeError("pic_step failed with %d at step %d" % (rc, k))
+        iters.append(st["picard_iters"])
+        pic.fourier_bessel(0, row, m, out=coef[k])
+    c = coef[:, m - 1].cpu().numpy()
+    c = c - c.mean()
+    pad = 16 * len(c)
+    P = np.abs(np.fft.rfft(c * np.hanning(len(c)), n=pad)) ** 2
+    f = np.fft.rfftfreq(pad, dt)
+    k0 = int(np.argmax(P[1:])) + 1
+    if 1 <= k0 < len(P) - 1:
+        a, b, cc = np.log(P[k0 - 1]), np.log(P[k0]), np.log(P[k0 + 1])
+        k0 = k0 + 0.5 * (a - cc) / (a - 2 * b + cc)
+    return {"freq": float(k0 * (f[1] - f[0])), "series": c, "k": chi / R, "model": model,
+            "mode": mode, "m": m, "picard_iters_mean": float(np.mean(iters))}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", required=True)
