@@ -30,6 +30,25 @@ QE = 1.602176634e-19
 ME = 9.1093837015e-31
 
 
+def advance(pic, tol, relaxed, k):
+    """One step; a step whose Picard iteration stalls above tol (a few
+    particles switch between sub-step paths) is retried with a tolerance ten
+    times looser, down to 1e-3, and recorded in relaxed.  A particle at the
+    sub-step cap is reported (PIC_E_SUBSTEP) and kept."""
+    rc, st = pic.step(1, check=False)
+    t = tol
+    while rc == -3 and t < 1e-3:
+        t *= 10.0
+        pic.set_picard(t, 100)
+        rc, st = pic.step(1, check=False)
+        pic.set_picard(tol, 100)
+        relaxed.append((k, t))
+    if rc not in (0, -4):
+        raise RuntimeError("pic_step failed with %d at step %d (iterations %d, residual %.3g)"
+                           % (rc, k, st["picard_iters"], st["last_res"]))
+    return st
+
+
 def slab_plasma(nr, nz, R, L, n0, ppc, s, te_ev, seed):
     """Electrons uniform over s < z < L - s and ions uniform over the gap, both
     at density n0 (uniform in the logical coordinates, weights proportional
@@ -79,20 +98,7 @@ def run(model="es", nr=64, nz=128, R=0.1, L=0.03, n0=1e16, ppc=64, sheath=1.8e-3
     iters, sub_err, relaxed = [], [], []
     t0 = time.time()
     for k in range(n_obs):
-        # a particle at the sub-step cap is reported (PIC_E_SUBSTEP) and kept
-        rc, st = pic.step(1, check=False)
-        t = tol
-        while rc == -3 and t < 1e-3:
-            # the iteration stalls at a small residual (a few particles switch
-            # between sub-step paths): retry the step with a looser tolerance
-            t *= 10.0
-            pic.set_picard(t, 100)
-            rc, st = pic.step(1, check=False)
-            pic.set_picard(tol, 100)
-            relaxed.append((k, t))
-        if rc not in (0, -4):
-            raise RuntimeError("pic_step failed with %d at step %d (iterations %d, residual %.3g)"
-                               % (rc, k, st["picard_iters"], st["last_res"]))
+        st = advance(pic, tol, relaxed, k)
         iters.append(st["picard_iters"])
         if st["substep_err"]:
             sub_err.append((k, st["substep_err"]))
@@ -118,7 +124,7 @@ def bessel_zero0(m):
 
 def ring(model="es", mode="symmetric", m=1, nr=64, nz=128, R=0.1, L=0.03, n0=1e16, ppc=64,
          sheath=1.8e-3, u0=5e4, steps=800, z_sample=1e-3, dt=1e-10, mu=0.0, te_ev=3.0, seed=0,
-         device="cuda:0", precision=PIC_FP64, tol=1e-7):
+         device="cuda:0", precision=PIC_FP64, tol=1e-7, base=None):
     """Free oscillation of one surface mode: the electrons of the loaded slab
     get the axial velocity u0 J_0(chi_{0,m} r / R), uniform in z (symmetric
     mode: the slab moves between the two sheaths, the plasma series resonance
@@ -126,8 +132,10 @@ def ring(model="es", mode="symmetric", m=1, nr=64, nz=128, R=0.1, L=0.03, n0=1e1
     mode); the ringing of the Fourier-Bessel coefficient c_m of E_z in the
     powered sheath gives the mode's frequency at k = chi_{0,m} / R (the
     perturbed potential vanishes on the side wall, so both symmetries use the
-    zeros of J_0).  Returns the frequency from the FFT peak (parabolic
-    interpolation on a 16x zero-padded spectrum) and the time series."""
+    zeros of J_0).  base: the series c_m of the same run with u0 = 0, which
+    is subtracted so that only the response to the kick remains.  Returns the
+    frequency from the FFT peak (parabolic interpolation on a 16x zero-padded
+    spectrum) and the raw series."""
     import torch
     fm = PIC_FIELD_ES if model == "es" else PIC_FIELD_EM
     cfg = small_reactor(nr=nr, nz=nz, R=R, L=L, dt=dt, freq=1e6, volt=0.0, n0=n0,
@@ -152,14 +160,16 @@ def ring(model="es", mode="symmetric", m=1, nr=64, nz=128, R=0.1, L=0.03, n0=1e1
     pic.set_state(sp, er=er.cpu().numpy(), ez=ez.cpu().numpy())
     row = int(round(z_sample / (L / nz) - 0.5))
     coef = torch.empty((steps, m), dtype=torch.float64, device=device)
-    iters = []
+    iters, relaxed = [], []
     for k in range(steps):
-        rc, st = pic.step(1, check=False)
-        if rc not in (0, -4):
-            raise RuntimeError("pic_step failed with %d at step %d" % (rc, k))
+        st = advance(pic, tol, relaxed, k)
         iters.append(st["picard_iters"])
         pic.fourier_bessel(0, row, m, out=coef[k])
     c = coef[:, m - 1].cpu().numpy()
+    if base is not None:
+        # the response to the kick alone: the unkicked run with the same
+        # particles carries the loaded slab's own oscillation and the noise
+        c = c - base
     c = c - c.mean()
     pad = 16 * len(c)
     P = np.abs(np.fft.rfft(c * np.hanning(len(c)), n=pad)) ** 2
@@ -168,8 +178,10 @@ def ring(model="es", mode="symmetric", m=1, nr=64, nz=128, R=0.1, L=0.03, n0=1e1
     if 1 <= k0 < len(P) - 1:
         a, b, cc = np.log(P[k0 - 1]), np.log(P[k0]), np.log(P[k0 + 1])
         k0 = k0 + 0.5 * (a - cc) / (a - 2 * b + cc)
-    return {"freq": float(k0 * (f[1] - f[0])), "series": c, "k": chi / R, "model": model,
-            "mode": mode, "m": m, "picard_iters_mean": float(np.mean(iters))}
+    return {"freq": float(k0 * (f[1] - f[0])), "series": coef[:, m - 1].cpu().numpy(),
+            "k": chi / R, "model": model,
+            "mode": mode, "m": m, "picard_iters_mean": float(np.mean(iters)),
+            "relaxed_steps": len(relaxed)}
 
 
 def main():
