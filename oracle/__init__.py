@@ -71,7 +71,7 @@ class Cfg(C.Structure):
                 ("dt", _D), ("freq", _D), ("volt", _D), ("eps", _D), ("mu", _D), ("bz", _D),
                 ("tol", _D), ("kmax", _I), ("mcc_on", _I), ("ng", _D), ("tg", _D),
                 ("numax_e", _D), ("pnull_e", _D), ("pnull_i", _D), ("gmax", _D),
-                ("seed", _U), ("cblock", _D), ("xa", _I)]
+                ("seed", _U), ("cblock", _D), ("xa", _I), ("wave", _I)]
 
 
 class Stats(C.Structure):
@@ -85,7 +85,7 @@ def _declare(L):
     L.oracle_load.argtypes = [_I, _I, _D, _D, _I, _D, _D, _D, _L, _D, _D, _D, _D, _U] + [_P] * 11
     L.oracle_push.argtypes = [_I, _I, _D, _D, _I, _D, _D, _D, _D, _L] + [_P] * 11 + [_I] + [_P] * 5
     L.oracle_node_charge.argtypes = [_I, _I, _D, _L, _P, _P, _P, _P, _P]
-    L.oracle_field_create.argtypes = [_I, _I, _D, _D, _I, _D, _D, _D]
+    L.oracle_field_create.argtypes = [_I, _I, _D, _D, _I, _D, _D, _D, _I]
     L.oracle_field_create.restype = _P
     L.oracle_field_destroy.argtypes = [_P]
     L.oracle_field_solve.argtypes = [_P, _P, _P, _P, _P, _P, _D, _D, _D, _P, _P, _P, _P]
@@ -238,10 +238,12 @@ def gauss_residual(grid: Grid, er, ez, Q, eps=EPS0):
 class FieldSolver:
     """Implicit CN Maxwell solve (row a4) by banded Cholesky of the H system."""
 
-    def __init__(self, grid: Grid, dt, eps=EPS0, mu=MU0):
+    def __init__(self, grid: Grid, dt, eps=EPS0, mu=MU0, wave=False):
+        """wave: the r = R boundary is the matched wave port (incoming wave
+        E_in = V/(2L)) instead of the prescribed gap field V/L."""
         self.grid, self.dt, self.eps, self.mu = grid, dt, eps, mu
         self._h = lib().oracle_field_create(grid.nr, grid.nz, grid.dr, grid.dz, grid.xa, dt, eps,
-                                            mu)
+                                            mu, 1 if wave else 0)
         if not self._h:
             raise RuntimeError("oracle field matrix not positive definite")
 
@@ -309,7 +311,7 @@ class Sim:
     def __init__(self, grid: Grid, dt, *, freq=0.0, volt=0.0, tol=1e-8, kmax=50, bz=0.0,
                  mcc_on=False, ng=0.0, tg=300.0, seed=0, eps=EPS0, mu=MU0, numax=None,
                  gmax=None, cap=None, species=None, charges=(-QE, QE), masses=(ME, M_AR),
-                 cblock=0.0):
+                 cblock=0.0, wave=False):
         """cblock: blocking capacitor [F] in series with the generator (Eq. 6),
         0 = the electrode follows V(t); its state is self.circ = [q^n, phi^n]."""
         self.grid = grid
@@ -320,6 +322,7 @@ class Sim:
         c.tol, c.kmax, c.mcc_on, c.ng, c.tg, c.seed = tol, kmax, 1 if mcc_on else 0, ng, tg, seed
         c.cblock = cblock
         c.xa = grid.xa
+        c.wave = 1 if wave else 0
         self.circ = np.zeros(2)
         if mcc_on:
             me, mi = masses
@@ -330,7 +333,7 @@ class Sim:
             c.numax_e, c.gmax = nu_e, g_max
             c.pnull_e = -np.expm1(-nu_e * dt)
             c.pnull_i = -np.expm1(-nu_i * dt)
-        self.field = FieldSolver(grid, dt, eps, mu)
+        self.field = FieldSolver(grid, dt, eps, mu, wave)
         self.er, self.ez, self.h = grid.zeros_fields()
         self.wall_z0 = np.zeros(2 * (grid.nr + 1))
         self.wall_zl = np.zeros(2 * (grid.nr + 1))

@@ -593,18 +593,30 @@ void oracle_node_charge(int nr, int nz, double q, int64_t n, const int32_t *cell
  * z=0, z=L; Ez(R, z) = V(t)/L on the r = R gap. */
 typedef struct {
   int nr, nz, n, bw, xa;
+  int wave;   /* 1: the r = R boundary is the matched port of o_wave_port */
   double dr, dz, dt, eps, mu;
   double *Lb; /* lower band of the Cholesky factor, n*(bw+1) */
 } o_field;
 
+/* Wave port on r = R (Eq. 5 read for our side feed): instead of a prescribed
+ * gap field, the boundary edges obey the first-order absorbing condition of
+ * an outgoing TEM-like wave with an incoming one,
+ *   E_z(R) + eta H_theta(R) = 2 E_in(t),   eta = sqrt(mu/eps),
+ * CN-centred, with H_theta(R) taken at the outermost H node r_{nr-1/2} and
+ * E_in = V(t) / (2L), so that a slow drive gives the gap voltage V(t) (the
+ * open-circuit doubling of the incident wave).  Outgoing waves leave through
+ * it.  In the H system this adds dt 2 pi r_{nr-1/2} dz eta to the diagonal of
+ * the outermost row. */
+
 static double *o_band(o_field *F, int i, int j) { return &F->Lb[(size_t)i * (F->bw + 1) + (j - i + F->bw)]; }
 
 void *oracle_field_create(int nr, int nz, double dr, double dz, int xa, double dt, double eps,
-                          double mu) {
+                          double mu, int wave) {
   o_field *F = (o_field *)calloc(1, sizeof(o_field));
   og_grid g = {nr, nz, dr, dz, xa};
   F->nr = nr; F->nz = nz; F->dr = dr; F->dz = dz; F->dt = dt; F->eps = eps; F->mu = mu;
   F->xa = xa;
+  F->wave = wave;
   F->n = nr * nz;
   F->bw = nz;
   F->Lb = (double *)calloc((size_t)F->n * (F->bw + 1), sizeof(double));
@@ -641,6 +653,13 @@ void *oracle_field_create(int nr, int nz, double dr, double dz, int xa, double d
         *o_band(F, cr, cl) += hdt2 * W * s_l * s_r;
       }
     }
+  if (wave) {
+    double eta = sqrt(mu / eps);
+    for (int j = 0; j < nz; ++j) {
+      int c = (nr - 1) * nz + j;
+      *o_band(F, c, c) += dt * O_TWO_PI * o_rhalf(&g, nr - 1) * dz * eta;
+    }
+  }
   /* in-place banded Cholesky A = L L^T */
   int n = F->n, bw = F->bw;
   for (int i = 0; i < n; ++i) {
@@ -709,6 +728,8 @@ void oracle_field_solve(void *p, const double *er0, const double *ez0, const dou
   for (int i = 0; i <= nr; ++i)
     for (int j = 0; j < nz; ++j) {
       double et;
+      /* gap: E_z^{n+1/2}; wave port: its source part 2 E_in^{n+1/2}, the same
+       * value (the -eta H part sits in the matrix) */
       if (i == nr) et = 0.5 * (v0 + v1) / L;
       else et = ez0[i * nz + j] - iz[i * nz + j] / (2.0 * eps * o_area_z(&g, i));
       if (i <= nr - 1) x[i * nz + j] -= dt * (O_TWO_PI * o_rhalf(&g, i)) * F->dz * et;
@@ -732,8 +753,14 @@ void oracle_field_solve(void *p, const double *er0, const double *ez0, const dou
       if (i <= nr - 1) ch += O_TWO_PI * o_rhalf(&g, i) * x[i * nz + j];
       if (i >= 1) ch += -O_TWO_PI * o_rhalf(&g, i - 1) * x[(i - 1) * nz + j];
       if (i == nr) {
-        ez1[e] = v1 / L;
-        double eh = 0.5 * (v0 + v1) / L;
+        double eh;
+        if (F->wave) {  /* E_z^{n+1/2}(R) = 2 E_in^{n+1/2} - eta H^{n+1/2} */
+          eh = 0.5 * (v0 + v1) / L - sqrt(F->mu / eps) * x[(nr - 1) * nz + j];
+          ez1[e] = 2.0 * eh - ez0[e];
+        } else {
+          eh = 0.5 * (v0 + v1) / L;
+          ez1[e] = v1 / L;
+        }
         srcE += eh * F->dz * (iz[e] - dt * ch);
       } else {
         ez1[e] = ez0[e] + (dt * ch - iz[e]) / (eps * o_area_z(&g, i));
@@ -1020,6 +1047,7 @@ typedef struct {
   uint64_t seed;
   double cblock;       /* blocking capacitor [F] between generator and electrode (Eq. 6); 0 = none */
   int xa;              /* mapped mesh: cells near the axis with r proportional to sqrt(xi) */
+  int wave;            /* 1: wave port on r = R (the field object must be created with it) */
 } orc_cfg;
 
 typedef struct {
@@ -1086,11 +1114,11 @@ int oracle_step(const orc_cfg *cfg, void *field, uint64_t step, orc_species *sp,
   const int circ_on = cfg->cblock > 0.0 && circ != NULL;
   double phi0 = v0, phi1 = v1; /* electrode potential at n and n+1 */
   if (circ_on) phi0 = circ[1];
-  /* initial iterate E^{n+1,0} = E^n (unknown edges); without a capacitor the
-   * prescribed gap edges take V^{n+1}, with one they keep phi^n */
+  /* initial iterate E^{n+1,0} = E^n (unknown edges); without a capacitor or
+   * wave port the prescribed gap edges take V^{n+1}, else they keep E^n's */
   memcpy(er1, er, sizeof(double) * ner);
   memcpy(ez1, ez, sizeof(double) * nez);
-  if (!circ_on)
+  if (!circ_on && !cfg->wave)
     for (int j = 0; j < nz; ++j) ez1[nr * nz + j] = v1 / cfg->L;
   int conv = 0;
   double src = 0.0, res = 0.0;
