@@ -61,6 +61,12 @@ extern "C" {
                               the nodes with the charge advanced by continuity (Eq. 3);
                               H = 0 */
 
+#define PIC_FEED_GAP 0      /* r = R carries the prescribed gap field V(t)/L (the default) */
+#define PIC_FEED_WAVE 1     /* r = R is a wave port (Eq. 5 read for the side feed): the first-order
+                               absorbing condition E_z + eta H_theta = 2 E_in with the incoming
+                               wave E_in = V(t)/(2L), eta = sqrt(mu/eps); outgoing waves leave,
+                               a slow drive gives the gap voltage V(t).  EM model only. */
+
 typedef struct pic_ctx pic_ctx; /* opaque; host memory owned by the library */
 
 /* Problem definition, copied at pic_init.  Zero eps/mu select vacuum values. */
@@ -87,6 +93,7 @@ typedef struct pic_config {
                                  powered electrode (Eq. 6); 0 = none (the electrode is at V(t)) */
   int ions_fixed;             /* 1: ions stay at their positions (no push, deposit or sort), as in
                                  the dispersion test of Sec. 3.1; requires mcc_on = 0 */
+  int feed;                   /* PIC_FEED_GAP or PIC_FEED_WAVE (EM model, no capacitor) */
   int axis_cells;             /* mapped radial mesh (Sec. 2.1), 0..16 (< nr): the first
                                  axis_cells cells have r = 2 dr sqrt(xa xi), the rest
                                  r = dr (xi + xa), dr = R / (nr + xa), r linear in xi inside

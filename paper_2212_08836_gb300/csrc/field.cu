@@ -462,8 +462,14 @@ __global__ void __launch_bounds__(256) k_update(FieldOp F, const double *er0, co
     if (i <= nr - 1) ch += tab(F, kTs, i) * hh_at(F, dl, i, j);
     if (i >= 1) ch += -tab(F, kTs, i - 1) * hh_at(F, dl, i - 1, j);
     if (i == nr) {
-      ez1[t] = v1 / F.L;
-      double eh = 0.5 * (v0 + v1) / F.L;
+      double eh;
+      if (F.wave) {  // wave port: the boundary field follows H at the outermost node
+        eh = 0.5 * (v0 + v1) / F.L - F.eta * hh_at(F, dl, nr - 1, j);
+        ez1[t] = 2.0 * eh - ez0[t];
+      } else {
+        eh = 0.5 * (v0 + v1) / F.L;
+        ez1[t] = v1 / F.L;
+      }
       src += eh * dz * (iz[t] - dt * ch);
     } else {
       double e1 = ez0[t] + (dt * ch - iz[t]) * tab(F, kTeaz, i);

@@ -206,6 +206,9 @@ bool valid(const pic_config *c) {
   if (!(c->cblock >= 0.0) || !isfinite(c->cblock)) return false;
   if (c->ions_fixed != 0 && c->ions_fixed != 1) return false;
   if (c->axis_cells < 0 || c->axis_cells > kMaxAxisCells || c->axis_cells >= c->nr) return false;
+  if (c->feed != PIC_FEED_GAP && c->feed != PIC_FEED_WAVE) return false;
+  if (c->feed == PIC_FEED_WAVE && (c->field_model != PIC_FIELD_EM || c->cblock > 0.0))
+    return false;
   if (c->ions_fixed && c->mcc_on) return false;
   return true;
 }
@@ -646,6 +649,11 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
     kdiag[i] = hdt2 * d;
     if (i >= 1) eoff[i] = hdt2 * wz_i * (-kTwoPi * rh(i - 1)) * s;
   }
+  // wave port: the boundary field -eta H of the outermost H row enters its
+  // Faraday equation (dt 2 pi r_{nr-1/2} dz eta on the diagonal)
+  F.wave = cfg->feed == PIC_FEED_WAVE ? 1 : 0;
+  F.eta = sqrt(x->mu / x->eps);
+  if (F.wave) kdiag[nr - 1] += cfg->dt * kTwoPi * rh(nr - 1) * dz * F.eta;
   // cyclic-reduction coefficients of each column (rows padded to n2 with identity)
   const int n2 = F.n2;
   std::vector<double> cr((size_t)5 * n2 * nz, 0.0);
@@ -1175,8 +1183,8 @@ int plain_start(pic_ctx *x, double v1) {
   const size_t ner = (size_t)nr * (nz + 1), nez = (size_t)(nr + 1) * nz;
   cudaError_t e = cudaMemcpyAsync(x->er1, x->er, ner * 8, cudaMemcpyDeviceToDevice, x->s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(x->ez1, x->ez, nez * 8, cudaMemcpyDeviceToDevice, x->s);
-  // with the blocking capacitor the gap keeps phi^n / L (the start is E^n)
-  if (e == cudaSuccess && !x->circ_on) {
+  // with the blocking capacitor or the wave port the gap edges keep E^n's
+  if (e == cudaSuccess && !x->circ_on && !x->F.wave) {
     k_fill<<<(nz + 127) / 128, 128, 0, x->s>>>(x->ez1 + (size_t)nr * nz, nz, v1 / x->cfg.L);
     e = cudaGetLastError();
     x->launches += 1;
@@ -1208,8 +1216,8 @@ int guess_start(pic_ctx *x, double v1, int *used) {
   if (launch_guess_apply(A, y, cp, v1 / x->cfg.L, x->er1, x->ez1, x->gbad, x->s) != cudaSuccess)
     return PIC_E_CUDA;
   x->launches += 1;
-  if (x->circ_on) {
-    // the gap edges keep phi^n / L, as in the plain start
+  if (x->circ_on || x->F.wave) {
+    // the gap edges keep E^n's, as in the plain start
     const size_t g0 = (size_t)x->g.nr * x->g.nz;
     if (cudaMemcpyAsync(x->ez1 + g0, x->ez + g0, (size_t)x->g.nz * 8, cudaMemcpyDeviceToDevice,
                         x->s) != cudaSuccess)

@@ -164,6 +164,9 @@ struct FieldOp {
   // that a captured solve stays valid from step to step; else the arguments
   const double *vd;
   Circuit cc;
+  // wave port on r = R: E_z^{n+1/2}(R) = 2 E_in^{n+1/2} - eta H^{n+1/2}(nr-1/2)
+  int wave;
+  double eta;
 };
 
 // Radial scales of a cell in the push's normalised units: lengths in units of
