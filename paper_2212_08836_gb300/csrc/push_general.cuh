@@ -38,6 +38,31 @@ struct Num<float> {
   __device__ static __forceinline__ bool nan_bits(float x) {
     return (__float_as_uint(x) & 0x7fffffffu) > 0x7f800000u;
   }
+  // order tests on the bits (see Num<double>)
+  __device__ static __forceinline__ float absb(float x) {
+    return __uint_as_float(__float_as_uint(x) & 0x7fffffffu);
+  }
+  __device__ static __forceinline__ bool lt_abs(float x, float y) {
+    return (__float_as_uint(x) & 0x7fffffffu) < __float_as_uint(y);
+  }
+  __device__ static __forceinline__ bool gt(float x, float c) {
+    return __float_as_int(x) > __float_as_int(c);
+  }
+  __device__ static __forceinline__ bool le(float x, float y) {
+    return __float_as_uint(x) <= __float_as_uint(y);
+  }
+  __device__ static __forceinline__ bool lt(float x, float y) {
+    return __float_as_uint(x) < __float_as_uint(y);
+  }
+  __device__ static __forceinline__ float minb(float x, float y) {
+    return __uint_as_float(min(__float_as_uint(x), __float_as_uint(y)));
+  }
+  __device__ static __forceinline__ float maxb(float x, float y) {
+    return __uint_as_float(max(__float_as_uint(x), __float_as_uint(y)));
+  }
+  __device__ static __forceinline__ bool finite(float x) {
+    return (__float_as_uint(x) & 0x7f800000u) != 0x7f800000u;
+  }
   // exact float -> double by exponent re-biasing in integer registers (no FP64
   // instruction; denormals are flushed in the FP32 unit anyway)
   __device__ static __forceinline__ double to_double(float f) {
@@ -75,6 +100,42 @@ struct Num<double> {
     return ((unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull) >
            0x7ff0000000000000ull;
   }
+  // Order tests on the bits, so that the decisions take no FP64 instruction
+  // (non-negative IEEE numbers order like their bit patterns):
+  // |x|; |x| < y for y >= 0 (false for NaN x); x > c for c > 0 (true for a
+  // positive NaN, which the callers reject later by finite()); x <= y for
+  // x, y >= 0 (false for NaN x); max of x, y >= 0; finiteness
+  __device__ static __forceinline__ double absb(double x) {
+    return __longlong_as_double(__double_as_longlong(x) & 0x7fffffffffffffffLL);
+  }
+  __device__ static __forceinline__ bool lt_abs(double x, double y) {
+    return ((unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull) <
+           (unsigned long long)__double_as_longlong(y);
+  }
+  __device__ static __forceinline__ bool gt(double x, double c) {
+    return __double_as_longlong(x) > __double_as_longlong(c);
+  }
+  __device__ static __forceinline__ bool le(double x, double y) {
+    return (unsigned long long)__double_as_longlong(x) <=
+           (unsigned long long)__double_as_longlong(y);
+  }
+  __device__ static __forceinline__ bool lt(double x, double y) {
+    return (unsigned long long)__double_as_longlong(x) <
+           (unsigned long long)__double_as_longlong(y);
+  }
+  __device__ static __forceinline__ double minb(double x, double y) {
+    const unsigned long long a = (unsigned long long)__double_as_longlong(x),
+                             b = (unsigned long long)__double_as_longlong(y);
+    return __longlong_as_double((long long)(a < b ? a : b));
+  }
+  __device__ static __forceinline__ double maxb(double x, double y) {
+    const unsigned long long a = (unsigned long long)__double_as_longlong(x),
+                             b = (unsigned long long)__double_as_longlong(y);
+    return __longlong_as_double((long long)(a > b ? a : b));
+  }
+  __device__ static __forceinline__ bool finite(double x) {
+    return (__double_as_longlong(x) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
+  }
   __device__ static __forceinline__ double to_double(double f) { return f; }
 };
 
@@ -82,14 +143,15 @@ constexpr int kNewtonMaxGen = 30;
 
 // stopping tests: the change of the r-offset is measured relative to r' close
 // to the axis (where r' is small), never below a few ulp of the unknown
+// (the min / max of non-negative values on their bits)
 template <typename T>
 __device__ __forceinline__ T tol_r(T rho1, T da) {
-  T one = (T)1, zero = (T)0;
-  return fmax(Num<T>::tol * fmin(one, fmax(rho1, zero)), Num<T>::ulpf * fabs(da));
+  const T r = Num<T>::gt(rho1, (T)0) ? Num<T>::minb(rho1, (T)1) : (T)0;
+  return Num<T>::maxb(Num<T>::tol * r, Num<T>::ulpf * Num<T>::absb(da));
 }
 template <typename T>
 __device__ __forceinline__ T tol_x(T x) {
-  return fmax(Num<T>::tol, Num<T>::ulpf * fabs(x));
+  return Num<T>::maxb((T)Num<T>::tol, Num<T>::ulpf * Num<T>::absb(x));
 }
 
 template <typename T>
@@ -164,9 +226,10 @@ __device__ __forceinline__ void eval_gen(const SubT<T> &s, T wt, T da, T db, T t
 // rule of simplified Newton iterations, Hairer & Wanner, Solving ODEs II,
 // IV.8).  Accepting when that bound is below 1 % of the tolerance saves the
 // confirming iteration without loosening the accuracy (no division needed).
+// (c, cp, t >= 0: compared on their bits)
 template <typename T>
 __device__ __forceinline__ bool contracted(T c, T cp, T t) {
-  return c == (T)0 || ((T)2 * c < cp && (T)200 * c * c <= cp * t);
+  return Num<T>::le(c, (T)0) || (Num<T>::lt((T)2 * c, cp) && Num<T>::le((T)200 * c * c, cp * t));
 }
 
 template <typename T, bool kB>
@@ -193,12 +256,13 @@ __device__ __forceinline__ bool interior_gen(const SubT<T> &s, T wt, T tau, T &p
     T xb = (-o.f1a * o.f2 + o.f2a * o.f1) * idet;
     T nda = da + xa, ndb = db + xb;
     if (s.P != zero && s.rho + nda <= zero) nda = h * (da - s.rho);
-    T ca = fabs(nda - da), cb = fabs(ndb - db);
+    T ca = Num<T>::absb(nda - da), cb = Num<T>::absb(ndb - db);
     da = nda;
     db = ndb;
     if (!isfinite(da) || !isfinite(db)) return false;
     const T ta = tol_r<T>(s.rho + da, da), tb = tol_x<T>(db);
-    if ((ca <= ta && cb <= tb) || (contracted(ca, pca, ta) && contracted(cb, pcb, tb))) {
+    if ((Num<T>::le(ca, ta) && Num<T>::le(cb, tb)) ||
+        (contracted(ca, pca, ta) && contracted(cb, pcb, tb))) {
       pda = da;
       pdb = db;
       return true;
@@ -248,12 +312,13 @@ __device__ __forceinline__ bool landing_gen(const SubT<T> &s, T wt, int dir, T X
     T xt = (-gFo * gO + gOo * gF) * idet;
     T noth = oth + xo, ntau = tau + xt;
     if (dir == 1 && s.P != zero && s.rho + noth <= zero) noth = h * (oth - s.rho);
-    T co = fabs(noth - oth), ct = fabs(ntau - tau);
+    T co = Num<T>::absb(noth - oth), ct = Num<T>::absb(ntau - tau);
     oth = noth;
     tau = ntau;
     if (!isfinite(oth) || !isfinite(tau)) return false;
     const T to = dir == 1 ? tol_r<T>(s.rho + oth, oth) : tol_x<T>(oth), tt = tol_x<T>(tau);
-    if ((co <= to && ct <= tt) || (contracted(co, pco, to) && contracted(ct, pct, tt))) {
+    if ((Num<T>::le(co, to) && Num<T>::le(ct, tt)) ||
+        (contracted(co, pco, to) && contracted(ct, pct, tt))) {
       ptau = tau;
       poth = oth;
       return true;
@@ -315,7 +380,7 @@ __device__ __forceinline__ bool fast_solve(T rho, T ut, T K, T k1, T &pd, unsign
 #pragma unroll 1
   for (int it = 0; it < kFastNewtonMax; ++it) {
     T r1 = rho + d;
-    if (!(r1 > zero)) return false;
+    if (!Num<T>::gt(r1, zero)) return false;
     T x = Num<T>::rcp(r1);
     T s2 = ut2 * x * x;
     T g = k1 * d - K - q * s2 * (r2 + d);
@@ -326,9 +391,10 @@ __device__ __forceinline__ bool fast_solve(T rho, T ut, T K, T k1, T &pd, unsign
     T kap = h * s2 * x * x * (r4 + d) * ig;
     d += st;
     nit++;
-    if (kap * st * st <= fmax(Num<T>::fast_rel * fabs(d), Num<T>::fast_abs)) {
+    if (Num<T>::le(kap * st * st, Num<T>::maxb(Num<T>::fast_rel * Num<T>::absb(d),
+                                                (T)Num<T>::fast_abs))) {
       pd = d;
-      return isfinite(d);
+      return Num<T>::finite(d);
     }
   }
   return false;

@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_push_fast(PushL
       uz = cur.vz * L.cz;
       const T rho = L.rm.rho0(ic) + a;
       bool acc = false;
-      if (Num<T>::in01(a) && Num<T>::in01(b) && fabs(ut) < q * rho) {
+      if (Num<T>::in01(a) && Num<T>::in01(b) && Num<T>::lt_abs(ut, q * rho)) {
         const T ar0 = L.ar[ic * nz1 + jc];
         const T gar = L.ar[ic * nz1 + jc + 1] - ar0;
         const T az0 = L.az[ic * nz + jc];
@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_push_fast(PushL
         const T zb = uz + h * (az0 + gaz * a);
         const T K = ur + h * (ar0 + gar * b) + q * gar * zb;
         const T k1 = one - (T)0.0625 * gar * gaz;
-        if (k1 > h && fast_solve<T>(rho, ut, K, k1, d, n_newton)) {
+        if (Num<T>::gt(k1, h) && fast_solve<T>(rho, ut, K, k1, d, n_newton)) {
           trial = true;
           e = zb + q * gaz * d;
           const T a1 = a + d, b1 = b + e;
