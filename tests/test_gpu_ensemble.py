@@ -23,7 +23,9 @@ def P():
 
 CFGS = [dict(nr=16, nz=24, np_init=8000, seed=3, volt=150.0),
         dict(nr=32, nz=64, np_init=40000, seed=4, freq=80e6, dt=1.0 / (200 * 80e6)),
-        dict(nr=24, nz=48, np_init=20000, seed=5, gas_pressure=5.0, precision=1)]
+        # the FP32 form at a tolerance well above its rounding floor, where the
+        # iteration count does not depend on the order of the deposit's atomics
+        dict(nr=24, nz=48, np_init=20000, seed=5, gas_pressure=5.0, precision=1, picard_tol=1e-6)]
 
 
 def make(c):
