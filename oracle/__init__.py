@@ -71,7 +71,8 @@ class Cfg(C.Structure):
                 ("dt", _D), ("freq", _D), ("volt", _D), ("eps", _D), ("mu", _D), ("bz", _D),
                 ("tol", _D), ("kmax", _I), ("mcc_on", _I), ("ng", _D), ("tg", _D),
                 ("numax_e", _D), ("pnull_e", _D), ("pnull_i", _D), ("gmax", _D),
-                ("seed", _U), ("cblock", _D), ("xa", _I), ("wave", _I)]
+                ("seed", _U), ("cblock", _D), ("xa", _I), ("wave", _I), ("nd", _I),
+                ("erd", _D)]
 
 
 class Stats(C.Structure):
@@ -82,16 +83,18 @@ class Stats(C.Structure):
 
 def _declare(L):
     L.oracle_philox4x64.argtypes = [_P, _P, _P]
-    L.oracle_load.argtypes = [_I, _I, _D, _D, _I, _D, _D, _D, _L, _D, _D, _D, _D, _U] + [_P] * 11
-    L.oracle_push.argtypes = [_I, _I, _D, _D, _I, _D, _D, _D, _D, _L] + [_P] * 11 + [_I] + [_P] * 5
+    L.oracle_load.argtypes = ([_I, _I, _D, _D, _I, _I, _D, _D, _D, _D, _L, _D, _D, _D, _D, _U]
+                              + [_P] * 11)
+    L.oracle_push.argtypes = ([_I, _I, _D, _D, _I, _I, _D, _D, _D, _D, _D, _L] + [_P] * 11 + [_I]
+                              + [_P] * 5)
     L.oracle_node_charge.argtypes = [_I, _I, _D, _L, _P, _P, _P, _P, _P]
-    L.oracle_field_create.argtypes = [_I, _I, _D, _D, _I, _D, _D, _D, _I]
+    L.oracle_field_create.argtypes = [_I, _I, _D, _D, _I, _I, _D, _D, _D, _D, _I]
     L.oracle_field_create.restype = _P
     L.oracle_field_destroy.argtypes = [_P]
     L.oracle_field_solve.argtypes = [_P, _P, _P, _P, _P, _P, _D, _D, _D, _P, _P, _P, _P]
-    L.oracle_field_energy.argtypes = [_I, _I, _D, _D, _I, _D, _D, _P, _P, _P]
+    L.oracle_field_energy.argtypes = [_I, _I, _D, _D, _I, _I, _D, _D, _D, _P, _P, _P]
     L.oracle_field_energy.restype = _D
-    L.oracle_gauss_residual.argtypes = [_I, _I, _D, _D, _I, _D, _P, _P, _P, _P]
+    L.oracle_gauss_residual.argtypes = [_I, _I, _D, _D, _I, _I, _D, _D, _P, _P, _P, _P]
     L.oracle_kinetic_energy.argtypes = [_D, _L, _P, _P, _P, _P, _P]
     L.oracle_kinetic_energy.restype = _D
     for f in ("oracle_sigma_el", "oracle_sigma_ex", "oracle_sigma_iz"):
@@ -133,9 +136,12 @@ class Grid:
     mapped mesh with r proportional to sqrt(xi) near the axis), linear in xi
     within each cell; xa = 0 is the uniform mesh r = xi dr."""
 
-    def __init__(self, nr, nz, R, L, xa=0):
+    def __init__(self, nr, nz, R, L, xa=0, nd=0, erd=1.0):
+        """nd > 0: the outer nd cells are a dielectric ring of relative
+        permittivity erd; particles move inside it and stick at its face."""
         self.nr, self.nz, self.R, self.L = int(nr), int(nz), float(R), float(L)
         self.xa = int(xa)
+        self.nd, self.erd = int(nd), float(erd)
         self.dr = self.R / (self.nr + self.xa)
         self.dz = self.L / self.nz
 
@@ -176,8 +182,8 @@ def load(grid: Grid, n, n0, te_ev, ti_ev, seed, me=ME, mi=M_AR):
     """Pair loading (a1): returns (electrons, ions) dicts of numpy arrays."""
     e = empty_species(n)
     i = empty_species(n)
-    lib().oracle_load(grid.nr, grid.nz, grid.dr, grid.dz, grid.xa, grid.R, grid.L, n0, n, te_ev,
-                      ti_ev,
+    lib().oracle_load(grid.nr, grid.nz, grid.dr, grid.dz, grid.xa, grid.nd, grid.erd, grid.R,
+                      grid.L, n0, n, te_ev, ti_ev,
                       me, mi, seed, _p(e["cell"]), _p(e["a"]), _p(e["b"]), _p(e["vr"]),
                       _p(e["vt"]), _p(e["vz"]), _p(i["vr"]), _p(i["vt"]), _p(i["vz"]),
                       _p(e["w"]), _p(e["id"]))
@@ -201,7 +207,8 @@ def push(grid: Grid, dt, q, m, sp, er_half, ez_half, write=False, bz=0.0, ir=Non
     kel = np.zeros(1)
     wz0, wzl, wr = walls if walls is not None else (None, None, None)
     n = len(sp["cell"])
-    lib().oracle_push(grid.nr, grid.nz, grid.dr, grid.dz, grid.xa, dt, q, m, bz, n,
+    lib().oracle_push(grid.nr, grid.nz, grid.dr, grid.dz, grid.xa, grid.nd, grid.erd, dt, q, m,
+                      bz, n,
                       _p(sp["cell"]),
                       _p(sp["a"]), _p(sp["b"]), _p(sp["vr"]), _p(sp["vt"]), _p(sp["vz"]),
                       _p(sp["w"]), _p(np.ascontiguousarray(er_half, dtype=np.float64)),
@@ -224,13 +231,15 @@ def kinetic_energy(m, sp):
 
 
 def field_energy(grid: Grid, er, ez, h, eps=EPS0, mu=MU0):
-    return lib().oracle_field_energy(grid.nr, grid.nz, grid.dr, grid.dz, grid.xa, eps, mu, _p(er),
+    return lib().oracle_field_energy(grid.nr, grid.nz, grid.dr, grid.dz, grid.xa, grid.nd,
+                                     grid.erd, eps, mu, _p(er),
                                      _p(ez), _p(h))
 
 
 def gauss_residual(grid: Grid, er, ez, Q, eps=EPS0):
     G = np.zeros(grid.n_node)
-    lib().oracle_gauss_residual(grid.nr, grid.nz, grid.dr, grid.dz, grid.xa, eps, _p(er), _p(ez),
+    lib().oracle_gauss_residual(grid.nr, grid.nz, grid.dr, grid.dz, grid.xa, grid.nd, grid.erd,
+                                eps, _p(er), _p(ez),
                                 _p(Q), _p(G))
     return G
 
@@ -242,8 +251,8 @@ class FieldSolver:
         """wave: the r = R boundary is the matched wave port (incoming wave
         E_in = V/(2L)) instead of the prescribed gap field V/L."""
         self.grid, self.dt, self.eps, self.mu = grid, dt, eps, mu
-        self._h = lib().oracle_field_create(grid.nr, grid.nz, grid.dr, grid.dz, grid.xa, dt, eps,
-                                            mu, 1 if wave else 0)
+        self._h = lib().oracle_field_create(grid.nr, grid.nz, grid.dr, grid.dz, grid.xa, grid.nd,
+                                            grid.erd, dt, eps, mu, 1 if wave else 0)
         if not self._h:
             raise RuntimeError("oracle field matrix not positive definite")
 
@@ -323,6 +332,7 @@ class Sim:
         c.cblock = cblock
         c.xa = grid.xa
         c.wave = 1 if wave else 0
+        c.nd, c.erd = grid.nd, grid.erd
         self.circ = np.zeros(2)
         if mcc_on:
             me, mi = masses

@@ -33,13 +33,18 @@ def radii(nr, dr, xa=0):
     return rn, rc, np.diff(rn)
 
 
-def _areas(nr, nz, dr, dz, xa=0):
+def _areas(nr, nz, dr, dz, xa=0, nd=0, erd=1.0):
+    """Dual-face areas weighted by the relative permittivity of the cells they
+    cross (the outer nd cells form a dielectric ring of permittivity erd)."""
     rn, rc, _ = radii(nr, dr, xa)
-    ar = 2.0 * np.pi * rc * dz                                    # faces (i+1/2), i < nr
+    f = np.where(np.arange(nr) >= nr - nd, erd, 1.0)              # per cell
+    ar = 2.0 * np.pi * rc * dz * f                                # faces (i+1/2), i < nr
     az = np.empty(nr + 1)
-    az[0] = np.pi * rc[0] ** 2                                    # axis disc
-    az[1:nr] = np.pi * (rc[1:] ** 2 - rc[:-1] ** 2)               # rings between centres
-    az[nr] = np.pi * (rn[nr] ** 2 - rc[nr - 1] ** 2)
+    az[0] = np.pi * rc[0] ** 2 * f[0]                             # axis disc
+    inner = np.pi * (rn[1:nr] ** 2 - rc[:-1] ** 2) * f[:-1]       # half ring in cell i-1
+    outer = np.pi * (rc[1:] ** 2 - rn[1:nr] ** 2) * f[1:]         # half ring in cell i
+    az[1:nr] = inner + outer
+    az[nr] = np.pi * (rn[nr] ** 2 - rc[nr - 1] ** 2) * f[nr - 1]
     return ar, az
 
 
@@ -59,12 +64,12 @@ def fields(phi, dr, dz, xa=0):
     return er.ravel(), ez.ravel()
 
 
-def solve(nr, nz, dr, dz, Q, phi0, eps=EPS0, xa=0):
+def solve(nr, nz, dr, dz, Q, phi0, eps=EPS0, xa=0, nd=0, erd=1.0):
     """Potential and fields for node charges Q ((nr+1) x (nz+1), only interior
     nodes used) and powered-plate potential phi0."""
     import scipy.sparse as sp
     import scipy.sparse.linalg as spla
-    ar, az = _areas(nr, nz, dr, dz, xa)
+    ar, az = _areas(nr, nz, dr, dz, xa, nd, erd)
     wr = radii(nr, dr, xa)[2]
     Q = np.asarray(Q, dtype=np.float64).reshape(nr + 1, nz + 1)
     phi = boundary_phi(nr, nz, phi0)
@@ -101,12 +106,12 @@ def solve(nr, nz, dr, dz, Q, phi0, eps=EPS0, xa=0):
     return phi, er, ez
 
 
-def electrode_charge_flow(nr, nz, dr, dz, ez_new, ez_old, iz, eps=EPS0, xa=0):
+def electrode_charge_flow(nr, nz, dr, dz, ez_new, ez_old, iz, eps=EPS0, xa=0, nd=0, erd=1.0):
     """dt times the reactor-side current of Eq. 6: the displacement current
     plus the crossed charge through the dual faces of the first row of E_z
     edges above the powered plate (i < nr, j = 1/2), i.e. the integral over
     the electrode in Eq. 6 on the integral-form mesh."""
-    _, az = _areas(nr, nz, dr, dz, xa)
+    _, az = _areas(nr, nz, dr, dz, xa, nd, erd)
     s = 0.0
     for i in range(nr):
         s += eps * az[i] * (ez_new[i * nz] - (ez_old[i * nz] if ez_old is not None else 0.0))
@@ -115,15 +120,16 @@ def electrode_charge_flow(nr, nz, dr, dz, ez_new, ez_old, iz, eps=EPS0, xa=0):
     return s
 
 
-def circuit_potential(nr, nz, dr, dz, Q, ez_old, iz, v1, qn, cblock, eps=EPS0, xa=0):
+def circuit_potential(nr, nz, dr, dz, Q, ez_old, iz, v1, qn, cblock, eps=EPS0, xa=0, nd=0,
+                      erd=1.0):
     """Electrode potential phi^{n+1} of Eq. 6 with a blocking capacitor cblock
     between the generator V^{n+1} = v1 and the electrode: the reactor-side
     charge flow must equal C (V^{n+1} - phi^{n+1}) - q^n.  The field is affine
     in phi^{n+1}; a solve at v1 and the unit-potential solve fix it."""
-    _, _, eza = solve(nr, nz, dr, dz, Q, v1, eps, xa)
-    _, _, ezu = solve(nr, nz, dr, dz, np.zeros((nr + 1) * (nz + 1)), 1.0, eps, xa)
-    dq = electrode_charge_flow(nr, nz, dr, dz, eza, ez_old, iz, eps, xa)
-    gu = electrode_charge_flow(nr, nz, dr, dz, ezu, None, None, eps, xa)
+    _, _, eza = solve(nr, nz, dr, dz, Q, v1, eps, xa, nd, erd)
+    _, _, ezu = solve(nr, nz, dr, dz, np.zeros((nr + 1) * (nz + 1)), 1.0, eps, xa, nd, erd)
+    dq = electrode_charge_flow(nr, nz, dr, dz, eza, ez_old, iz, eps, xa, nd, erd)
+    gu = electrode_charge_flow(nr, nz, dr, dz, ezu, None, None, eps, xa, nd, erd)
     return v1 - (qn + dq) / (cblock + gu)
 
 
@@ -210,8 +216,8 @@ class Sim:
             Q1 = Qn - divergence_out(nr, nz, ir, iz)
             if self.cblock > 0.0:
                 phi1 = circuit_potential(nr, nz, g.dr, g.dz, Q1, self.ez, iz, v1, self.circ[0],
-                                         self.cblock, self.eps, g.xa)
-            _, ern, ezn = solve(nr, nz, g.dr, g.dz, Q1, phi1, self.eps, g.xa)
+                                         self.cblock, self.eps, g.xa, g.nd, g.erd)
+            _, ern, ezn = solve(nr, nz, g.dr, g.dz, Q1, phi1, self.eps, g.xa, g.nd, g.erd)
             mr = np.ones((nr, nz + 1), bool)
             mr[:, 0] = mr[:, nz] = False
             dr_ = (ern - er1)[mr.ravel()]

@@ -99,6 +99,8 @@ typedef struct {
   int nr, nz;
   double dr, dz; /* dr: radial spacing of the uniformly spaced part of the mesh */
   int xa;        /* mapped mesh: the first xa cells have r proportional to sqrt(xi) */
+  int nd;        /* dielectric ring: the outer nd cells (relative permittivity erd) */
+  double erd;
 } og_grid;
 
 /* Radial mapping (Sec. 2.1, the mapped mesh): r(xi) = 2 dr sqrt(xa xi) for
@@ -133,6 +135,21 @@ static double o_area_z(const og_grid *g, int i) {
   }
   return O_TWO_PI * o_rnode(g, i) * g->dr;
 }
+/* Dielectric ring (the feed region at the periphery, Sec. 2.1's dielectric
+ * port read for the side feed): the outer nd cells have relative
+ * permittivity erd.  The integral form weights each dual face by the
+ * permittivity of the cells it crosses: eps A for the E_r faces of ring rows,
+ * the two halves of the ring's inner boundary node separately. */
+static double o_aeff_r(const og_grid *g, int i) {
+  return (g->nd > 0 && i >= g->nr - g->nd) ? g->erd * o_area_r(g, i) : o_area_r(g, i);
+}
+static double o_aeff_z(const og_grid *g, int i) {
+  const int i0 = g->nr - g->nd;
+  if (g->nd == 0 || i < i0) return o_area_z(g, i);
+  if (i > i0) return g->erd * o_area_z(g, i);
+  const double ri = o_rnode(g, i), rm = o_rhalf(g, i - 1), rp = o_rhalf(g, i);
+  return O_PI * (ri * ri - rm * rm) + g->erd * O_PI * (rp * rp - ri * ri);
+}
 /* primal-cell volume carrying H_theta */
 static double o_vol_h(const og_grid *g, int i) {
   return O_TWO_PI * o_rhalf(g, i) * o_drc(g, i) * g->dz;
@@ -143,31 +160,33 @@ static double o_vol_h(const og_grid *g, int i) {
  * logical coordinates, weight proportional to r*J_r (Sec. 2.1), Maxwellian
  * velocities.  Electron p and ion p share position and weight, so the initial
  * node charge vanishes and E = 0, H = 0 is a Gauss-consistent start. */
-void oracle_load(int nr, int nz, double dr, double dz, int xa, double R, double L, double n0,
+void oracle_load(int nr, int nz, double dr, double dz, int xa, int nd, double erd, double R,
+                 double L, double n0,
                  int64_t n, double te_ev, double ti_ev, double me, double mi, uint64_t seed,
                  int32_t *cell, double *a, double *b, double *vre, double *vte, double *vze,
                  double *vri, double *vti, double *vzi, double *w, uint32_t *id) {
-  og_grid g = {nr, nz, dr, dz, xa};
+  og_grid g = {nr, nz, dr, dz, xa, nd, erd};
+  const int np_r = nr - nd; /* particles live inside the ring */
   double vthe = sqrt(te_ev * O_QE / me);
   double vthi = sqrt(ti_ev * O_QE / mi);
   for (int64_t p = 0; p < n; ++p) {
     double u[4];
     o_draw4(seed, O_STREAM_LOAD_POS, (uint64_t)p, O_LOAD_STEP, 0, u);
-    double xi = (double)nr * u[0];
+    double xi = (double)np_r * u[0];
     double eta = (double)nz * u[1];
     int ic = (int)floor(xi);
     int jc = (int)floor(eta);
-    if (ic > nr - 1) ic = nr - 1;
+    if (ic > np_r - 1) ic = np_r - 1;
     if (jc > nz - 1) jc = nz - 1;
     cell[p] = ic * nz + jc;
     a[p] = xi - (double)ic;
     b[p] = eta - (double)jc;
-    if (xa == 0) {
+    if (xa == 0 && nd == 0) {
       w[p] = n0 * (O_TWO_PI * (xi * dr)) * R * L / (double)n;
     } else {  /* w proportional to r J_r */
       double Jr = o_drc(&g, ic);
       double r = (o_rho0(&g, ic) + a[p]) * Jr;
-      w[p] = n0 * (O_TWO_PI * r) * (Jr * (double)nr) * L / (double)n;
+      w[p] = n0 * (O_TWO_PI * r) * (Jr * (double)np_r) * L / (double)n;
     }
     id[p] = (uint32_t)p;
     double g1, g2, g3, g4;
@@ -536,16 +555,18 @@ static int o_push_one(o_push *P, int *pic, int *pjc, double *pa, double *pb, dou
 /* Push + deposit of one species (rows a2/a3, and a6 when write != 0).
  * er/ez hold E^{n+1/2}; ir/iz accumulate (caller zeroes).  counters[6]:
  * substep errors, absorbed, substeps, fallbacks (and ke_lost in kelost). */
-void oracle_push(int nr, int nz, double dr, double dz, int xa, double dt, double q, double m,
-                 double bz,
+void oracle_push(int nr, int nz, double dr, double dz, int xa, int nd, double erd, double dt,
+                 double q, double m, double bz,
                  int64_t n, int32_t *cell, double *a, double *b, double *vr, double *vt,
                  double *vz, const double *w, const double *er, const double *ez, double *ir,
                  double *iz, int write, double *wall_z0, double *wall_zl, double *wall_r,
                  int64_t *counters, double *kelost) {
   o_push P;
   memset(&P, 0, sizeof(P));
-  P.nr = nr; P.nz = nz; P.dr = dr; P.dz = dz;
-  P.g.nr = nr; P.g.nz = nz; P.g.dr = dr; P.g.dz = dz; P.g.xa = xa;
+  /* particles move inside the dielectric ring: its inner face r_{nr-nd} is
+   * their outer wall, where they stop and their charge stays (sticking) */
+  P.nr = nr - nd; P.nz = nz; P.dr = dr; P.dz = dz;
+  P.g.nr = nr; P.g.nz = nz; P.g.dr = dr; P.g.dz = dz; P.g.xa = xa; P.g.nd = nd; P.g.erd = erd;
   P.er = er; P.ez = ez; P.ir = ir; P.iz = iz;
   P.q = q; P.qm = q / m; P.wb = (q / m) * bz; P.m = m;
   P.wall_z0 = wall_z0; P.wall_zl = wall_zl; P.wall_r = wall_r;
@@ -592,7 +613,8 @@ void oracle_node_charge(int nr, int nz, double q, int64_t n, const int32_t *cell
  * solved here by banded Cholesky.  Prescribed edges: Er = 0 on the plates
  * z=0, z=L; Ez(R, z) = V(t)/L on the r = R gap. */
 typedef struct {
-  int nr, nz, n, bw, xa;
+  int nr, nz, n, bw, xa, nd;
+  double erd;
   int wave;   /* 1: the r = R boundary is the matched port of o_wave_port */
   double dr, dz, dt, eps, mu;
   double *Lb; /* lower band of the Cholesky factor, n*(bw+1) */
@@ -610,12 +632,14 @@ typedef struct {
 
 static double *o_band(o_field *F, int i, int j) { return &F->Lb[(size_t)i * (F->bw + 1) + (j - i + F->bw)]; }
 
-void *oracle_field_create(int nr, int nz, double dr, double dz, int xa, double dt, double eps,
-                          double mu, int wave) {
+void *oracle_field_create(int nr, int nz, double dr, double dz, int xa, int nd, double erd,
+                          double dt, double eps, double mu, int wave) {
   o_field *F = (o_field *)calloc(1, sizeof(o_field));
-  og_grid g = {nr, nz, dr, dz, xa};
+  og_grid g = {nr, nz, dr, dz, xa, nd, erd};
   F->nr = nr; F->nz = nz; F->dr = dr; F->dz = dz; F->dt = dt; F->eps = eps; F->mu = mu;
   F->xa = xa;
+  F->nd = nd;
+  F->erd = erd;
   F->wave = wave;
   F->n = nr * nz;
   F->bw = nz;
@@ -631,7 +655,7 @@ void *oracle_field_create(int nr, int nz, double dr, double dz, int xa, double d
   /* unknown Er edges (i+1/2, j), j = 1..nz-1, between cells (i,j-1) [C=+2pi r] and (i,j) [C=-2pi r] */
   for (int i = 0; i < nr; ++i)
     for (int j = 1; j < nz; ++j) {
-      double W = o_drc(&g, i) / (eps * o_area_r(&g, i));
+      double W = o_drc(&g, i) / (eps * o_aeff_r(&g, i));
       double s_lo = O_TWO_PI * o_rhalf(&g, i);
       double s_hi = -O_TWO_PI * o_rhalf(&g, i);
       int clo = i * nz + (j - 1), chi = i * nz + j;
@@ -642,7 +666,7 @@ void *oracle_field_create(int nr, int nz, double dr, double dz, int xa, double d
   /* unknown Ez edges (i, j+1/2), i = 0..nr-1, cells (i-1,j) [C=-2pi r_{i-1/2}] and (i,j) [C=+2pi r_{i+1/2}] */
   for (int i = 0; i < nr; ++i)
     for (int j = 0; j < nz; ++j) {
-      double W = dz / (eps * o_area_z(&g, i));
+      double W = dz / (eps * o_aeff_z(&g, i));
       double s_r = O_TWO_PI * o_rhalf(&g, i);
       int cr = i * nz + j;
       *o_band(F, cr, cr) += hdt2 * W * s_r * s_r;
@@ -710,7 +734,7 @@ void oracle_field_solve(void *p, const double *er0, const double *ez0, const dou
                         double *er1, double *ez1, double *h1, double *src) {
   o_field *F = (o_field *)p;
   int nr = F->nr, nz = F->nz;
-  og_grid g = {nr, nz, F->dr, F->dz, F->xa};
+  og_grid g = {nr, nz, F->dr, F->dz, F->xa, F->nd, F->erd};
   double dt = F->dt, eps = F->eps, mu = F->mu;
   double *x = (double *)malloc(sizeof(double) * (size_t)F->n);
   for (int i = 0; i < nr; ++i)
@@ -720,7 +744,7 @@ void oracle_field_solve(void *p, const double *er0, const double *ez0, const dou
     for (int j = 0; j <= nz; ++j) {
       double et;
       if (j == 0 || j == nz) et = 0.0;
-      else et = er0[i * (nz + 1) + j] - ir[i * (nz + 1) + j] / (2.0 * eps * o_area_r(&g, i));
+      else et = er0[i * (nz + 1) + j] - ir[i * (nz + 1) + j] / (2.0 * eps * o_aeff_r(&g, i));
       double s = O_TWO_PI * o_rhalf(&g, i);
       if (j <= nz - 1) x[i * nz + j] -= dt * (-s) * o_drc(&g, i) * et;
       if (j >= 1) x[i * nz + (j - 1)] -= dt * (s) * o_drc(&g, i) * et;
@@ -731,7 +755,7 @@ void oracle_field_solve(void *p, const double *er0, const double *ez0, const dou
       /* gap: E_z^{n+1/2}; wave port: its source part 2 E_in^{n+1/2}, the same
        * value (the -eta H part sits in the matrix) */
       if (i == nr) et = 0.5 * (v0 + v1) / L;
-      else et = ez0[i * nz + j] - iz[i * nz + j] / (2.0 * eps * o_area_z(&g, i));
+      else et = ez0[i * nz + j] - iz[i * nz + j] / (2.0 * eps * o_aeff_z(&g, i));
       if (i <= nr - 1) x[i * nz + j] -= dt * (O_TWO_PI * o_rhalf(&g, i)) * F->dz * et;
       if (i >= 1) x[(i - 1) * nz + j] -= dt * (-O_TWO_PI * o_rhalf(&g, i - 1)) * F->dz * et;
     }
@@ -744,7 +768,7 @@ void oracle_field_solve(void *p, const double *er0, const double *ez0, const dou
       if (j == 0 || j == nz) { er1[e] = 0.0; continue; }
       double s = O_TWO_PI * o_rhalf(&g, i);
       double ch = -s * x[i * nz + j] + s * x[i * nz + j - 1];
-      er1[e] = er0[e] + (dt * ch - ir[e]) / (eps * o_area_r(&g, i));
+      er1[e] = er0[e] + (dt * ch - ir[e]) / (eps * o_aeff_r(&g, i));
     }
   for (int i = 0; i <= nr; ++i)
     for (int j = 0; j < nz; ++j) {
@@ -763,7 +787,7 @@ void oracle_field_solve(void *p, const double *er0, const double *ez0, const dou
         }
         srcE += eh * F->dz * (iz[e] - dt * ch);
       } else {
-        ez1[e] = ez0[e] + (dt * ch - iz[e]) / (eps * o_area_z(&g, i));
+        ez1[e] = ez0[e] + (dt * ch - iz[e]) / (eps * o_aeff_z(&g, i));
       }
     }
   if (src) *src = srcE;
@@ -771,19 +795,20 @@ void oracle_field_solve(void *p, const double *er0, const double *ez0, const dou
 }
 
 /* field energy over unknown edges and H cells */
-double oracle_field_energy(int nr, int nz, double dr, double dz, int xa, double eps, double mu,
+double oracle_field_energy(int nr, int nz, double dr, double dz, int xa, int nd, double erd,
+                           double eps, double mu,
                            const double *er, const double *ez, const double *h) {
-  og_grid g = {nr, nz, dr, dz, xa};
+  og_grid g = {nr, nz, dr, dz, xa, nd, erd};
   double W = 0.0;
   for (int i = 0; i < nr; ++i)
     for (int j = 1; j < nz; ++j) {
       double e = er[i * (nz + 1) + j];
-      W += 0.5 * eps * e * e * o_area_r(&g, i) * o_drc(&g, i);
+      W += 0.5 * eps * e * e * o_aeff_r(&g, i) * o_drc(&g, i);
     }
   for (int i = 0; i < nr; ++i)
     for (int j = 0; j < nz; ++j) {
       double e = ez[i * nz + j];
-      W += 0.5 * eps * e * e * o_area_z(&g, i) * dz;
+      W += 0.5 * eps * e * e * o_aeff_z(&g, i) * dz;
     }
   for (int i = 0; i < nr; ++i)
     for (int j = 0; j < nz; ++j) {
@@ -794,17 +819,18 @@ double oracle_field_energy(int nr, int nz, double dr, double dz, int xa, double 
 }
 
 /* Gauss residual eps*div E - Q at interior nodes i=0..nr-1, j=1..nz-1 (others 0) */
-void oracle_gauss_residual(int nr, int nz, double dr, double dz, int xa, double eps,
+void oracle_gauss_residual(int nr, int nz, double dr, double dz, int xa, int nd, double erd,
+                           double eps,
                            const double *er,
                            const double *ez, const double *Q, double *G) {
-  og_grid g = {nr, nz, dr, dz, xa};
+  og_grid g = {nr, nz, dr, dz, xa, nd, erd};
   for (int i = 0; i <= nr; ++i)
     for (int j = 0; j <= nz; ++j) G[i * (nz + 1) + j] = 0.0;
   for (int i = 0; i < nr; ++i)
     for (int j = 1; j < nz; ++j) {
-      double flux = o_area_r(&g, i) * er[i * (nz + 1) + j];
-      if (i >= 1) flux -= o_area_r(&g, i - 1) * er[(i - 1) * (nz + 1) + j];
-      flux += o_area_z(&g, i) * (ez[i * nz + j] - ez[i * nz + j - 1]);
+      double flux = o_aeff_r(&g, i) * er[i * (nz + 1) + j];
+      if (i >= 1) flux -= o_aeff_r(&g, i - 1) * er[(i - 1) * (nz + 1) + j];
+      flux += o_aeff_z(&g, i) * (ez[i * nz + j] - ez[i * nz + j - 1]);
       G[i * (nz + 1) + j] = eps * flux - Q[i * (nz + 1) + j];
     }
 }
@@ -1048,6 +1074,8 @@ typedef struct {
   double cblock;       /* blocking capacitor [F] between generator and electrode (Eq. 6); 0 = none */
   int xa;              /* mapped mesh: cells near the axis with r proportional to sqrt(xi) */
   int wave;            /* 1: wave port on r = R (the field object must be created with it) */
+  int nd;              /* dielectric ring: outer cells, relative permittivity erd */
+  double erd;
 } orc_cfg;
 
 typedef struct {
@@ -1074,7 +1102,7 @@ static double o_circuit(const orc_cfg *cfg, void *field, const double *er, const
                         double v1, double qn) {
   int nr = cfg->nr, nz = cfg->nz;
   size_t ner = (size_t)nr * (nz + 1), nez = (size_t)(nr + 1) * nz, nh = (size_t)nr * nz;
-  og_grid g = {nr, nz, cfg->dr, cfg->dz, cfg->xa};
+  og_grid g = {nr, nz, cfg->dr, cfg->dz, cfg->xa, cfg->nd, cfg->erd};
   double *era = (double *)malloc(sizeof(double) * ner), *eza = (double *)malloc(sizeof(double) * nez);
   double *ha = (double *)malloc(sizeof(double) * nh);
   double *zr = (double *)calloc(ner, sizeof(double)), *zz = (double *)calloc(nez, sizeof(double));
@@ -1086,7 +1114,7 @@ static double o_circuit(const orc_cfg *cfg, void *field, const double *er, const
   oracle_field_solve(field, zr, zz, zh, zr, zz, 0.0, 1.0, cfg->L, eru, ezu, hu, &src);
   double dq = 0.0, gu = 0.0;
   for (int i = 0; i < nr; ++i) {
-    double ea = cfg->eps * o_area_z(&g, i);
+    double ea = cfg->eps * o_aeff_z(&g, i);
     dq += ea * (eza[i * nz] - ez[i * nz]) + iz[i * nz];
     gu += ea * ezu[i * nz];
   }
@@ -1129,7 +1157,7 @@ int oracle_step(const orc_cfg *cfg, void *field, uint64_t step, orc_species *sp,
     memset(ir, 0, sizeof(double) * ner);
     memset(iz, 0, sizeof(double) * nez);
     for (int s = 0; s < nspec; ++s)
-      oracle_push(nr, nz, cfg->dr, cfg->dz, cfg->xa, cfg->dt, sp[s].q, sp[s].m, cfg->bz, sp[s].n, sp[s].cell,
+      oracle_push(nr, nz, cfg->dr, cfg->dz, cfg->xa, cfg->nd, cfg->erd, cfg->dt, sp[s].q, sp[s].m, cfg->bz, sp[s].n, sp[s].cell,
                   sp[s].a, sp[s].b, sp[s].vr, sp[s].vt, sp[s].vz, sp[s].w, erh, ezh, ir, iz, 0,
                   NULL, NULL, NULL, NULL, NULL);
     if (circ_on) phi1 = o_circuit(cfg, field, er, ez, h, ir, iz, phi0, v1, circ[0]);
@@ -1165,7 +1193,7 @@ int oracle_step(const orc_cfg *cfg, void *field, uint64_t step, orc_species *sp,
     memset(ir, 0, sizeof(double) * ner);
     memset(iz, 0, sizeof(double) * nez);
     for (int s = 0; s < nspec; ++s)
-      oracle_push(nr, nz, cfg->dr, cfg->dz, cfg->xa, cfg->dt, sp[s].q, sp[s].m, cfg->bz, sp[s].n, sp[s].cell,
+      oracle_push(nr, nz, cfg->dr, cfg->dz, cfg->xa, cfg->nd, cfg->erd, cfg->dt, sp[s].q, sp[s].m, cfg->bz, sp[s].n, sp[s].cell,
                   sp[s].a, sp[s].b, sp[s].vr, sp[s].vt, sp[s].vz, sp[s].w, erh, ezh, ir, iz, 1,
                   wall_z0 ? wall_z0 + (size_t)s * (nr + 1) : NULL,
                   wall_zl ? wall_zl + (size_t)s * (nr + 1) : NULL,
