@@ -94,6 +94,10 @@ typedef struct pic_config {
   int ions_fixed;             /* 1: ions stay at their positions (no push, deposit or sort), as in
                                  the dispersion test of Sec. 3.1; requires mcc_on = 0 */
   int feed;                   /* PIC_FEED_GAP or PIC_FEED_WAVE (EM model, no capacitor) */
+  int ring_cells;             /* dielectric ring: the outer ring_cells cells (r > R_d) are filled
+                                 with a dielectric of relative permittivity eps_ring; particles
+                                 move in r < R_d and stick at the ring face (0 = none) */
+  double eps_ring;            /* relative permittivity of the ring (>= 1; e.g. 3.8 for quartz) */
   int axis_cells;             /* mapped radial mesh (Sec. 2.1), 0..16 (< nr): the first
                                  axis_cells cells have r = 2 dr sqrt(xa xi), the rest
                                  r = dr (xi + xa), dr = R / (nr + xa), r linear in xi inside

@@ -45,7 +45,7 @@ class Config(C.Structure):
                 ("picard_tol", _D), ("picard_max", _I), ("mcc_on", _I), ("bz", _D),
                 ("eps", _D), ("mu", _D), ("seed", C.c_ulonglong), ("precision", _I),
                 ("field_model", _I), ("cblock", _D), ("ions_fixed", _I), ("feed", _I),
-                ("axis_cells", _I)]
+                ("ring_cells", _I), ("eps_ring", _D), ("axis_cells", _I)]
 
 
 class StepStats(C.Structure):
@@ -173,7 +173,7 @@ def small_reactor(**kw):
                gas_pressure=2.0, gas_temp=300.0, n0=1e15, te_ev=3.0, ti_ev=0.026,
                np_init=40000, capacity_factor=1.5, picard_tol=1e-8, picard_max=50, mcc_on=1,
                bz=0.0, eps=0.0, mu=0.0, seed=0, precision=PIC_FP64, field_model=0, cblock=0.0,
-               ions_fixed=0, feed=0, axis_cells=0)
+               ions_fixed=0, feed=0, ring_cells=0, eps_ring=1.0, axis_cells=0)
     cfg.update(kw)
     return cfg
 
@@ -187,7 +187,7 @@ def large_reactor(**kw):
                gas_pressure=2.0, gas_temp=300.0, n0=1e15, te_ev=3.0, ti_ev=0.026,
                np_init=16 * 1024 * 1024, capacity_factor=1.25, picard_tol=1e-8, picard_max=50,
                mcc_on=1, bz=0.0, eps=0.0, mu=0.0, seed=1, precision=PIC_FP64, field_model=0,
-               cblock=0.0, ions_fixed=0, feed=0, axis_cells=0)
+               cblock=0.0, ions_fixed=0, feed=0, ring_cells=0, eps_ring=1.0, axis_cells=0)
     cfg.update(kw)
     return cfg
 

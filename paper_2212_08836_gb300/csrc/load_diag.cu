@@ -22,7 +22,7 @@ __global__ void __launch_bounds__(256) k_load(Grid g, long long n, double n0, do
   int32_t cell = ic * g.nz + jc;
   double a = xi - (double)ic, b = eta - (double)jc;
   double w;
-  if (g.xa == 0) {
+  if (g.xa == 0 && g.nd == 0) {
     w = n0 * (kTwoPi * (xi * g.dr)) * g.R * g.L / (double)n;
   } else {  // mapped mesh: w proportional to r J_r, J_r the cell width
     const double jr = g_width(g, ic);
@@ -89,14 +89,14 @@ __global__ void __launch_bounds__(256) k_field_energy(Grid g, double eps, double
     int i = (int)(t / nz1), j = (int)(t - (t / nz1) * nz1);
     if (j != 0 && j != nz) {
       double e = er[t];
-      W += 0.5 * eps * e * e * (kTwoPi * g_rcentre(g, i) * dz) * g_width(g, i);
+      W += 0.5 * eps * e * e * g_aeff_r(g, i) * g_width(g, i);
     }
   }
   if (t < nez) {
     int i = (int)(t / nz);
     if (i < nr) {
       double e = ez[t];
-      W += 0.5 * eps * e * e * g_area_z(g, i) * dz;
+      W += 0.5 * eps * e * e * g_aeff_z(g, i) * dz;
     }
   }
   if (t < nh) {
@@ -136,9 +136,9 @@ __global__ void __launch_bounds__(256) k_gauss_residual(Grid g, double eps, cons
     Q[t] = 0.0;
     return;
   }
-  double flux = kTwoPi * g_rcentre(g, i) * g.dz * er[i * nz1 + j];
-  if (i >= 1) flux -= kTwoPi * g_rcentre(g, i - 1) * g.dz * er[(i - 1) * nz1 + j];
-  flux += g_area_z(g, i) * (ez[i * nz + j] - ez[i * nz + j - 1]);
+  double flux = g_aeff_r(g, i) * er[i * nz1 + j];
+  if (i >= 1) flux -= g_aeff_r(g, i - 1) * er[(i - 1) * nz1 + j];
+  flux += g_aeff_z(g, i) * (ez[i * nz + j] - ez[i * nz + j - 1]);
   Q[t] = eps * flux - Q[t];
 }
 

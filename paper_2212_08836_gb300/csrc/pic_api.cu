@@ -207,6 +207,9 @@ bool valid(const pic_config *c) {
   if (c->ions_fixed != 0 && c->ions_fixed != 1) return false;
   if (c->axis_cells < 0 || c->axis_cells > kMaxAxisCells || c->axis_cells >= c->nr) return false;
   if (c->feed != PIC_FEED_GAP && c->feed != PIC_FEED_WAVE) return false;
+  if (c->ring_cells < 0 || (c->ring_cells > 0 && (!(c->eps_ring >= 1.0) || !isfinite(c->eps_ring) ||
+                                                  c->ring_cells + c->axis_cells > c->nr - 2)))
+    return false;
   if (c->feed == PIC_FEED_WAVE && (c->field_model != PIC_FIELD_EM || c->cblock > 0.0))
     return false;
   if (c->ions_fixed && c->mcc_on) return false;
@@ -388,6 +391,7 @@ void fill_push(pic_ctx *x, int s, double q, double m, const double *erh, const d
   (void)ezh;
   const double dt = x->cfg.dt;
   L.g = x->g;
+  L.g.nr = x->g.nr - x->g.nd;  // particles move inside the dielectric ring
   L.q = q;
   L.m = m;
   L.qf = (T)q;
@@ -538,6 +542,8 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
   x->g.R = cfg->R;
   x->g.L = cfg->L;
   x->g.xa = cfg->axis_cells;
+  x->g.nd = cfg->ring_cells;
+  x->g.erd = cfg->ring_cells > 0 ? cfg->eps_ring : 1.0;
   x->g.dr = cfg->R / (nr + cfg->axis_cells);
   x->g.dz = cfg->L / nz;
   x->eps = cfg->eps > 0 ? cfg->eps : kEps0;
@@ -637,10 +643,11 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
   const Grid &G = x->g;
   auto rh = [&](int i) { return g_rcentre(G, i); };
   auto wr = [&](int i) { return g_width(G, i); };
-  auto az = [&](int i) { return g_area_z(G, i); };
+  auto az = [&](int i) { return g_aeff_z(G, i); };     // permittivity-weighted
+  auto are = [&](int i) { return g_aeff_r(G, i); };
   for (int i = 0; i < nr; ++i) {
     mass[i] = 2.0 * x->mu * (kTwoPi * rh(i) * wr(i) * dz);
-    double ar = kTwoPi * rh(i) * dz;
+    double ar = are(i);
     double s = kTwoPi * rh(i);
     kz[i] = hdt2 * (wr(i) / (x->eps * ar)) * s * s;
     double wz_i = dz / (x->eps * az(i));
@@ -674,8 +681,8 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
   for (int j = 1; j <= M; ++j)
     for (int m = 1; m <= M; ++m) Sd[(size_t)(j - 1) * M + (m - 1)] = sqrt(2.0 / nz) * sin(kPi * j * m / nz);
   for (int i = 0; i < nr; ++i) {
-    et[i] = x->eps * (kTwoPi * rh(i) * dz) / wr(i);                            // cR: face i+1/2
-    et[nr + i] = i >= 1 ? x->eps * (kTwoPi * rh(i - 1) * dz) / wr(i - 1) : 0.0;  // cL: face i-1/2
+    et[i] = x->eps * are(i) / wr(i);                                           // cR: face i+1/2
+    et[nr + i] = i >= 1 ? x->eps * are(i - 1) / wr(i - 1) : 0.0;                 // cL: face i-1/2
     et[2 * nr + i] = x->eps * az(i) / dz;                                      // cZ
     et[3 * nr + i] = wr(i);                                                    // E_r edge length
   }
@@ -721,7 +728,7 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
     pw[2 * k + 1] = sin(u);
   }
   for (int i = 0; i <= nr; ++i) {
-    double ari = kTwoPi * rh(i) * dz;
+    double ari = i < nr ? are(i) : kTwoPi * rh(i) * dz;
     double azi = az(i);
     rt[0 * (nr + 1) + i] = 1.0 / (2.0 * x->eps * ari);
     rt[1 * (nr + 1) + i] = 1.0 / (2.0 * x->eps * azi);
@@ -901,10 +908,12 @@ int pic_load_particles(pic_ctx *x) {
   if (!x) return PIC_E_CONFIG;
   long long n = x->cfg.np_init;
   if (n > x->cap[0] || n > x->cap[1] || n > 0xFFFFFFFFll) return PIC_E_CAPACITY;
+  Grid gp = x->g;
+  gp.nr = x->g.nr - x->g.nd;  // the plasma region inside the dielectric ring
   cudaError_t le =
-      x->mixed ? launch_load(x->g, n, x->cfg.n0, x->cfg.te_ev, x->cfg.ti_ev, x->cfg.seed,
+      x->mixed ? launch_load(gp, n, x->cfg.n0, x->cfg.te_ev, x->cfg.ti_ev, x->cfg.seed,
                              as32(cur(x, 0)), as32(cur(x, 1)), x->s)
-               : launch_load(x->g, n, x->cfg.n0, x->cfg.te_ev, x->cfg.ti_ev, x->cfg.seed,
+               : launch_load(gp, n, x->cfg.n0, x->cfg.te_ev, x->cfg.ti_ev, x->cfg.seed,
                              cur(x, 0), cur(x, 1), x->s);
   if (le != cudaSuccess) return PIC_E_CUDA;
   if (n > 0) x->launches += 1;

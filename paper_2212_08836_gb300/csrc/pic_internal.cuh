@@ -69,6 +69,8 @@ struct Grid {
   int nr, nz;
   double dr, dz, R, L;  // dr: spacing of the uniformly spaced part
   int xa;               // cells with r proportional to sqrt(xi)
+  int nd;               // dielectric ring: the outer nd cells, relative permittivity erd
+  double erd;
 };
 
 // node radius r_i, cell width J_r, cell-centre radius, and the inner-face
@@ -96,6 +98,19 @@ __host__ __device__ inline double g_area_z(const Grid &g, int i) {
     return kPi * (ro * ro - ri * ri);
   }
   return kTwoPi * g_rnode(g, i) * g.dr;
+}
+// dual-face areas weighted by the relative permittivity of the cells they
+// cross (the dielectric ring; the ring's inner boundary node by halves)
+__host__ __device__ inline double g_aeff_r(const Grid &g, int i) {
+  const double a = kTwoPi * g_rcentre(g, i) * g.dz;
+  return (g.nd > 0 && i >= g.nr - g.nd) ? g.erd * a : a;
+}
+__host__ __device__ inline double g_aeff_z(const Grid &g, int i) {
+  const int i0 = g.nr - g.nd;
+  if (g.nd == 0 || i < i0) return g_area_z(g, i);
+  if (i > i0) return g.erd * g_area_z(g, i);
+  const double ri = g_rnode(g, i), rm = g_rcentre(g, i - 1), rp = g_rcentre(g, i);
+  return kPi * (ri * ri - rm * rm) + g.erd * kPi * (rp * rp - ri * ri);
 }
 
 // Particle structure of arrays of one species; T = double (plain FP64 form)
