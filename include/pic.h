@@ -278,7 +278,8 @@ int pic_node_charge(pic_ctx *ctx, double *q_dev);
 
 /* Row a9: Gauss residual of the state, eps div_h E^n - Q^n on the interior
  * nodes (i < nr, 0 < j < nz) in the flux form of the integral mesh, Q^n the
- * S1 x S1 node charge of both species; zero on the other nodes.  The
+ * S1 x S1 node charge of both species plus, with the dielectric ring, the
+ * charge stuck on the ring's face; zero on the other nodes.  The
  * charge-conserving scheme keeps it at its initial value (zero for the pair
  * loading) to rounding.  res_dev: (nr+1)*(nz+1) doubles (device).
  * Asynchronous.  Errors: PIC_E_CONFIG, PIC_E_CUDA. */

@@ -202,6 +202,10 @@ class Sim:
         Qn = np.zeros(g.n_node)
         for d in self.sp:
             O.node_charge(g, d["q"], self._view(d), Qn)
+        if g.nd > 0:
+            # the charge stuck on the dielectric ring's face stays in Gauss's law
+            wr = self.wall[2]
+            Qn.reshape(nr + 1, nz + 1)[nr - g.nd, :] += wr[: nz + 1] + wr[nz + 1:]
         er1, ez1 = self.er.copy(), self.ez.copy()
         if not self.cblock > 0.0:
             ez1[nr * nz:] = v1 / g.L

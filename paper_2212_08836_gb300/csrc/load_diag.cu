@@ -127,7 +127,8 @@ __global__ void __launch_bounds__(256) k_node_charge(Grid g, PartsT<T> p, long l
 // in the flux form of the integral mesh; zero elsewhere.  Q holds the node
 // charge on entry and the residual on exit.
 __global__ void __launch_bounds__(256) k_gauss_residual(Grid g, double eps, const double *er,
-                                                        const double *ez, double *Q) {
+                                                        const double *ez, const double *wall,
+                                                        double *Q) {
   const int nz = g.nz, nz1 = nz + 1;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)(g.nr + 1) * nz1) return;
@@ -135,6 +136,11 @@ __global__ void __launch_bounds__(256) k_gauss_residual(Grid g, double eps, cons
   if (i >= g.nr || j == 0 || j == nz) {
     Q[t] = 0.0;
     return;
+  }
+  if (g.nd > 0 && i == g.nr - g.nd && wall) {
+    // the charge stuck on the dielectric ring's face (the r-wall tallies)
+    const int blk = 2 * (g.nr + 1) + nz1;
+    Q[t] += wall[2 * (g.nr + 1) + j] + wall[blk + 2 * (g.nr + 1) + j];
   }
   double flux = g_aeff_r(g, i) * er[i * nz1 + j];
   if (i >= 1) flux -= g_aeff_r(g, i - 1) * er[(i - 1) * nz1 + j];
@@ -163,9 +169,9 @@ __global__ void __launch_bounds__(128) k_fourier_bessel(const double *__restrict
 }  // namespace
 
 cudaError_t launch_gauss_residual(const Grid &g, double eps, const double *er, const double *ez,
-                                  double *Q, cudaStream_t s) {
+                                  const double *wall, double *Q, cudaStream_t s) {
   const long long n = (long long)(g.nr + 1) * (g.nz + 1);
-  k_gauss_residual<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, eps, er, ez, Q);
+  k_gauss_residual<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, eps, er, ez, wall, Q);
   return cudaGetLastError();
 }
 

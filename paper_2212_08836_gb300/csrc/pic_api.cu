@@ -1629,7 +1629,7 @@ int pic_gauss_residual(pic_ctx *x, double *res) {
   int r = pic_node_charge(x, res);
   if (r) return r;
   x->launches += 3;
-  return cuda_rc(launch_gauss_residual(x->g, x->eps, x->er, x->ez, res, x->s));
+  return cuda_rc(launch_gauss_residual(x->g, x->eps, x->er, x->ez, x->wall, res, x->s));
 }
 
 int pic_get_view(pic_ctx *x, pic_view *v) {

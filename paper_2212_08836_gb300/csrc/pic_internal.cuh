@@ -253,9 +253,10 @@ struct EsOp {
 // E (Yee layouts) of the node charges Q (Q = Qn - div I if ir is given);
 // Picard norms against er_it / ez_it into cnt when cnt is given
 // Q -= div I on the interior nodes (the charge carried to the next step)
-// Q <- eps div_h E - Q on the interior nodes (zero elsewhere)
+// Q <- eps div_h E - Q on the interior nodes (zero elsewhere); with the
+// dielectric ring the charge stuck on its face (wall: the wall tallies) joins Q
 cudaError_t launch_gauss_residual(const Grid &g, double eps, const double *er, const double *ez,
-                                  double *Q, cudaStream_t s);
+                                  const double *wall, double *Q, cudaStream_t s);
 // c[m] = sum_k basis[m n + k] f[k stride], m < nmodes (one block per mode)
 cudaError_t launch_fourier_bessel(const double *basis, const double *f, int stride, int n,
                                   int nmodes, double *coef, cudaStream_t s);

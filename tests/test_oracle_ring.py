@@ -107,3 +107,22 @@ def test_loading_fills_the_plasma_region_only():
     assert ic.max() == g.nr - ND - 1
     Rd = g.r_nodes()[g.nr - ND]
     assert np.sum(e["w"]) == pytest.approx(n0 * np.pi * Rd ** 2 * g.L, rel=0.01)
+
+
+def test_es_step_keeps_the_stuck_charge_in_gauss_law():
+    """Electrons stick at the ring face; the electrostatic step's field obeys
+    Gauss's law with the moved particles plus the charge stuck on the face."""
+    g = grid(nr=12, nz=16)
+    e, i = O.load(g, 4000, 1e15, 30.0, 0.026, 9)
+    s = ES.Sim(g, 2e-10, volt=0.0, tol=1e-12, species=[e, i])
+    for _ in range(3):
+        rc, st = s.step()
+        assert rc == 0
+    stuck = s.wall[2][: g.nz + 1] + s.wall[2][g.nz + 1:]
+    assert np.sum(np.abs(stuck)) > 0
+    Q = np.zeros(g.n_node)
+    for sp in range(2):
+        O.node_charge(g, (-QE, O.QE)[sp], s.state(sp), Q)
+    Q.reshape(g.nr + 1, g.nz + 1)[g.nr - ND, :] += stuck
+    G = O.gauss_residual(g, s.er, s.ez, Q).reshape(g.nr + 1, g.nz + 1)
+    assert np.max(np.abs(G)) <= 1e-9 * np.max(np.abs(Q))
