@@ -88,10 +88,12 @@ def _declare(L):
     L.oracle_push.argtypes = ([_I, _I, _D, _D, _I, _I, _D, _D, _D, _D, _D, _L] + [_P] * 11 + [_I]
                               + [_P] * 5)
     L.oracle_node_charge.argtypes = [_I, _I, _D, _L, _P, _P, _P, _P, _P]
-    L.oracle_field_create.argtypes = [_I, _I, _D, _D, _I, _I, _D, _D, _D, _D, _I]
+    L.oracle_field_create.argtypes = [_I, _I, _D, _D, _I, _I, _D, _D, _D, _D, _D, _I]
     L.oracle_field_create.restype = _P
     L.oracle_field_destroy.argtypes = [_P]
     L.oracle_field_solve.argtypes = [_P, _P, _P, _P, _P, _P, _D, _D, _D, _P, _P, _P, _P]
+    L.oracle_conduction_charge.argtypes = [_P, _P, _P, _P, _P, _P]
+    L.oracle_conduction_charge.restype = _D
     L.oracle_field_energy.argtypes = [_I, _I, _D, _D, _I, _I, _D, _D, _D, _P, _P, _P]
     L.oracle_field_energy.restype = _D
     L.oracle_gauss_residual.argtypes = [_I, _I, _D, _D, _I, _I, _D, _D, _P, _P, _P, _P]
@@ -136,12 +138,13 @@ class Grid:
     mapped mesh with r proportional to sqrt(xi) near the axis), linear in xi
     within each cell; xa = 0 is the uniform mesh r = xi dr."""
 
-    def __init__(self, nr, nz, R, L, xa=0, nd=0, erd=1.0):
-        """nd > 0: the outer nd cells are a dielectric ring of relative
-        permittivity erd; particles move inside it and stick at its face."""
+    def __init__(self, nr, nz, R, L, xa=0, nd=0, erd=1.0, sgd=0.0):
+        """nd > 0: the outer nd cells are a ring of relative permittivity erd
+        and conductivity sgd [S/m]; particles move inside it and stick at its
+        face.  A large sgd models a metal (electromagnetic model only)."""
         self.nr, self.nz, self.R, self.L = int(nr), int(nz), float(R), float(L)
         self.xa = int(xa)
-        self.nd, self.erd = int(nd), float(erd)
+        self.nd, self.erd, self.sgd = int(nd), float(erd), float(sgd)
         self.dr = self.R / (self.nr + self.xa)
         self.dz = self.L / self.nz
 
@@ -252,7 +255,7 @@ class FieldSolver:
         E_in = V/(2L)) instead of the prescribed gap field V/L."""
         self.grid, self.dt, self.eps, self.mu = grid, dt, eps, mu
         self._h = lib().oracle_field_create(grid.nr, grid.nz, grid.dr, grid.dz, grid.xa, grid.nd,
-                                            grid.erd, dt, eps, mu, 1 if wave else 0)
+                                            grid.erd, grid.sgd, dt, eps, mu, 1 if wave else 0)
         if not self._h:
             raise RuntimeError("oracle field matrix not positive definite")
 
@@ -268,6 +271,13 @@ class FieldSolver:
         lib().oracle_field_solve(self._h, _p(er0), _p(ez0), _p(h0), _p(ir), _p(iz), v0, v1, g.L,
                                  _p(er1), _p(ez1), _p(h1), _p(src))
         return er1, ez1, h1, float(src[0])
+
+    def conduction(self, er0, ez0, er1, ez1, qc):
+        """Subtract from the node array qc the charge the ring's conduction
+        current carries over the step from (er0, ez0) to (er1, ez1); returns
+        the Ohmic energy of the step."""
+        return lib().oracle_conduction_charge(self._h, _p(er0), _p(ez0), _p(er1), _p(ez1),
+                                              _p(qc))
 
 
 def sigma_el(eps):
@@ -348,6 +358,8 @@ class Sim:
         self.wall_z0 = np.zeros(2 * (grid.nr + 1))
         self.wall_zl = np.zeros(2 * (grid.nr + 1))
         self.wall_r = np.zeros(2 * (grid.nz + 1))
+        self.qcond = np.zeros(grid.n_node)  # charge moved by the ring's conduction current
+        self.ohmic = 0.0                     # Ohmic energy dissipated in the ring
         self.step_index = 0
         self.sp = []
         species = species or []
@@ -376,6 +388,8 @@ class Sim:
     def step(self):
         T = self._species_table()
         st = Stats()
+        if self.grid.sgd > 0.0:
+            er0, ez0 = self.er.copy(), self.ez.copy()
         rc = lib().oracle_step(C.byref(self.cfg), self.field._h, self.step_index, T, len(self.sp),
                                _p(self.er), _p(self.ez), _p(self.h), _p(self.wall_z0),
                                _p(self.wall_zl), _p(self.wall_r), C.byref(st), _p(self.circ))
@@ -384,4 +398,6 @@ class Sim:
             d["next_id"] = T[s].next_id
         if rc in (0, -4, -5):
             self.step_index += 1
+            if self.grid.sgd > 0.0:
+                self.ohmic += self.field.conduction(er0, ez0, self.er, self.ez, self.qcond)
         return rc, st

@@ -163,6 +163,9 @@ class Sim:
         """drive: optional V(t) replacing volt sin(2 pi freq t); fixed: indices of
         species that stay in place (not pushed, deposited or sorted)."""
         import oracle as O
+        if getattr(grid, "sgd", 0.0) > 0.0:
+            # Sec. 2.1: electrostatic runs model metals by a large permittivity
+            raise ValueError("a conducting ring needs the electromagnetic model")
         self.O = O
         self.drive, self.fixed = drive, tuple(fixed)
         self.g, self.dt, self.freq, self.volt = grid, dt, freq, volt

@@ -101,6 +101,7 @@ typedef struct {
   int xa;        /* mapped mesh: the first xa cells have r proportional to sqrt(xi) */
   int nd;        /* dielectric ring: the outer nd cells (relative permittivity erd) */
   double erd;
+  double sgd;    /* conductivity of the ring's cells [S/m] (0: a pure dielectric) */
 } og_grid;
 
 /* Radial mapping (Sec. 2.1, the mapped mesh): r(xi) = 2 dr sqrt(xa xi) for
@@ -149,6 +150,19 @@ static double o_aeff_z(const og_grid *g, int i) {
   if (i > i0) return g->erd * o_area_z(g, i);
   const double ri = o_rnode(g, i), rm = o_rhalf(g, i - 1), rp = o_rhalf(g, i);
   return O_PI * (ri * ri - rm * rm) + g->erd * O_PI * (rp * rp - ri * ri);
+}
+/* Conducting ring (Eq. 2's sigma E term; Sec. 2.1 models metals in EM runs
+ * by a large conductivity): the ring's cells carry conductivity sgd, and each
+ * dual face conducts sgd times the part of its area inside the ring. */
+static double o_asig_r(const og_grid *g, int i) {
+  return (g->nd > 0 && i >= g->nr - g->nd) ? g->sgd * o_area_r(g, i) : 0.0;
+}
+static double o_asig_z(const og_grid *g, int i) {
+  const int i0 = g->nr - g->nd;
+  if (g->nd == 0 || g->sgd == 0.0 || i < i0) return 0.0;
+  if (i > i0) return g->sgd * o_area_z(g, i);
+  const double ri = o_rnode(g, i), rp = o_rhalf(g, i);
+  return g->sgd * O_PI * (rp * rp - ri * ri);
 }
 /* primal-cell volume carrying H_theta */
 static double o_vol_h(const og_grid *g, int i) {
@@ -608,13 +622,16 @@ void oracle_node_charge(int nr, int nz, double q, int64_t n, const int32_t *cell
 /* Implicit CN Maxwell solve of Eq. 2 (TM: Er, Ez, H_theta; H_theta is the
  * primary unknown).  Integral (finite-volume) Yee form on the (mapped) mesh:
  *   Faraday: mu*Vh*(H1-H0) = -dt * C^T L E_half
- *   Ampere:  eps*A*(E1-E0) = dt * C H_half - dQ          (unknown edges)
- * Eliminating E gives (2 mu Vh + dt^2/2 C^T W C) H_half = rhs, W = L/(eps A),
+ *   Ampere:  eps*A*(E1-E0) + dt*S*E_half = dt * C H_half - dQ   (unknown edges)
+ * with S the conducting part of the face (sigma A, zero outside a conducting
+ * ring).  Per edge, with D = eps A + dt S/2:
+ *   E_half = (eps A E0 - dQ/2)/D + dt C H_half / (2D),
+ * so eliminating E gives (2 mu Vh + dt^2/2 C^T W C) H_half = rhs, W = L/D,
  * solved here by banded Cholesky.  Prescribed edges: Er = 0 on the plates
  * z=0, z=L; Ez(R, z) = V(t)/L on the r = R gap. */
 typedef struct {
   int nr, nz, n, bw, xa, nd;
-  double erd;
+  double erd, sgd;
   int wave;   /* 1: the r = R boundary is the matched port of o_wave_port */
   double dr, dz, dt, eps, mu;
   double *Lb; /* lower band of the Cholesky factor, n*(bw+1) */
@@ -630,16 +647,25 @@ typedef struct {
  * it.  In the H system this adds dt 2 pi r_{nr-1/2} dz eta to the diagonal of
  * the outermost row. */
 
+/* D = eps A_eff + dt S / 2 of the E_r edges of row i and the E_z edges of node i */
+static double o_dnr(const og_grid *g, double eps, double dt, int i) {
+  return eps * o_aeff_r(g, i) + 0.5 * dt * o_asig_r(g, i);
+}
+static double o_dnz(const og_grid *g, double eps, double dt, int i) {
+  return eps * o_aeff_z(g, i) + 0.5 * dt * o_asig_z(g, i);
+}
+
 static double *o_band(o_field *F, int i, int j) { return &F->Lb[(size_t)i * (F->bw + 1) + (j - i + F->bw)]; }
 
 void *oracle_field_create(int nr, int nz, double dr, double dz, int xa, int nd, double erd,
-                          double dt, double eps, double mu, int wave) {
+                          double sgd, double dt, double eps, double mu, int wave) {
   o_field *F = (o_field *)calloc(1, sizeof(o_field));
-  og_grid g = {nr, nz, dr, dz, xa, nd, erd};
+  og_grid g = {nr, nz, dr, dz, xa, nd, erd, sgd};
   F->nr = nr; F->nz = nz; F->dr = dr; F->dz = dz; F->dt = dt; F->eps = eps; F->mu = mu;
   F->xa = xa;
   F->nd = nd;
   F->erd = erd;
+  F->sgd = sgd;
   F->wave = wave;
   F->n = nr * nz;
   F->bw = nz;
@@ -655,7 +681,7 @@ void *oracle_field_create(int nr, int nz, double dr, double dz, int xa, int nd, 
   /* unknown Er edges (i+1/2, j), j = 1..nz-1, between cells (i,j-1) [C=+2pi r] and (i,j) [C=-2pi r] */
   for (int i = 0; i < nr; ++i)
     for (int j = 1; j < nz; ++j) {
-      double W = o_drc(&g, i) / (eps * o_aeff_r(&g, i));
+      double W = o_drc(&g, i) / o_dnr(&g, eps, dt, i);
       double s_lo = O_TWO_PI * o_rhalf(&g, i);
       double s_hi = -O_TWO_PI * o_rhalf(&g, i);
       int clo = i * nz + (j - 1), chi = i * nz + j;
@@ -666,7 +692,7 @@ void *oracle_field_create(int nr, int nz, double dr, double dz, int xa, int nd, 
   /* unknown Ez edges (i, j+1/2), i = 0..nr-1, cells (i-1,j) [C=-2pi r_{i-1/2}] and (i,j) [C=+2pi r_{i+1/2}] */
   for (int i = 0; i < nr; ++i)
     for (int j = 0; j < nz; ++j) {
-      double W = dz / (eps * o_aeff_z(&g, i));
+      double W = dz / o_dnz(&g, eps, dt, i);
       double s_r = O_TWO_PI * o_rhalf(&g, i);
       int cr = i * nz + j;
       *o_band(F, cr, cr) += hdt2 * W * s_r * s_r;
@@ -734,17 +760,18 @@ void oracle_field_solve(void *p, const double *er0, const double *ez0, const dou
                         double *er1, double *ez1, double *h1, double *src) {
   o_field *F = (o_field *)p;
   int nr = F->nr, nz = F->nz;
-  og_grid g = {nr, nz, F->dr, F->dz, F->xa, F->nd, F->erd};
+  og_grid g = {nr, nz, F->dr, F->dz, F->xa, F->nd, F->erd, F->sgd};
   double dt = F->dt, eps = F->eps, mu = F->mu;
   double *x = (double *)malloc(sizeof(double) * (size_t)F->n);
   for (int i = 0; i < nr; ++i)
     for (int j = 0; j < nz; ++j) x[i * nz + j] = 2.0 * mu * o_vol_h(&g, i) * h0[i * nz + j];
-  /* - dt * C^T L Et over all edges; Et = E^n - dQ/(2 eps A) (unknown) or E^{n+1/2} (prescribed) */
+  /* - dt * C^T L Et over all edges; Et = (eps A E^n - dQ/2)/D (unknown) or E^{n+1/2} (prescribed) */
   for (int i = 0; i < nr; ++i)
     for (int j = 0; j <= nz; ++j) {
       double et;
       if (j == 0 || j == nz) et = 0.0;
-      else et = er0[i * (nz + 1) + j] - ir[i * (nz + 1) + j] / (2.0 * eps * o_aeff_r(&g, i));
+      else et = (eps * o_aeff_r(&g, i) * er0[i * (nz + 1) + j] - 0.5 * ir[i * (nz + 1) + j]) /
+                o_dnr(&g, eps, dt, i);
       double s = O_TWO_PI * o_rhalf(&g, i);
       if (j <= nz - 1) x[i * nz + j] -= dt * (-s) * o_drc(&g, i) * et;
       if (j >= 1) x[i * nz + (j - 1)] -= dt * (s) * o_drc(&g, i) * et;
@@ -755,7 +782,8 @@ void oracle_field_solve(void *p, const double *er0, const double *ez0, const dou
       /* gap: E_z^{n+1/2}; wave port: its source part 2 E_in^{n+1/2}, the same
        * value (the -eta H part sits in the matrix) */
       if (i == nr) et = 0.5 * (v0 + v1) / L;
-      else et = ez0[i * nz + j] - iz[i * nz + j] / (2.0 * eps * o_aeff_z(&g, i));
+      else et = (eps * o_aeff_z(&g, i) * ez0[i * nz + j] - 0.5 * iz[i * nz + j]) /
+                o_dnz(&g, eps, dt, i);
       if (i <= nr - 1) x[i * nz + j] -= dt * (O_TWO_PI * o_rhalf(&g, i)) * F->dz * et;
       if (i >= 1) x[(i - 1) * nz + j] -= dt * (-O_TWO_PI * o_rhalf(&g, i - 1)) * F->dz * et;
     }
@@ -768,7 +796,9 @@ void oracle_field_solve(void *p, const double *er0, const double *ez0, const dou
       if (j == 0 || j == nz) { er1[e] = 0.0; continue; }
       double s = O_TWO_PI * o_rhalf(&g, i);
       double ch = -s * x[i * nz + j] + s * x[i * nz + j - 1];
-      er1[e] = er0[e] + (dt * ch - ir[e]) / (eps * o_aeff_r(&g, i));
+      /* Ampere with E_half: (eps A + dt S/2) E1 = (eps A - dt S/2) E0 + dt C H - dQ */
+      er1[e] = ((eps * o_aeff_r(&g, i) - 0.5 * dt * o_asig_r(&g, i)) * er0[e] + dt * ch - ir[e]) /
+               o_dnr(&g, eps, dt, i);
     }
   for (int i = 0; i <= nr; ++i)
     for (int j = 0; j < nz; ++j) {
@@ -787,11 +817,42 @@ void oracle_field_solve(void *p, const double *er0, const double *ez0, const dou
         }
         srcE += eh * F->dz * (iz[e] - dt * ch);
       } else {
-        ez1[e] = ez0[e] + (dt * ch - iz[e]) / (eps * o_aeff_z(&g, i));
+        ez1[e] = ((eps * o_aeff_z(&g, i) - 0.5 * dt * o_asig_z(&g, i)) * ez0[e] + dt * ch - iz[e]) /
+                 o_dnz(&g, eps, dt, i);
       }
     }
   if (src) *src = srcE;
   free(x);
+}
+
+/* Charge carried by the conduction current of a conducting ring over one step
+ * (Eq. 2's sigma E at the half step): each unknown edge moves dt S E_half from
+ * the node at its lower end to the node at its upper end.  Subtracted from qc
+ * (nodes, (nr+1) x (nz+1)), so that Gauss's law holds with qc added to the
+ * particle and wall charge.  Returns the Ohmic energy dt sum S L E_half^2. */
+double oracle_conduction_charge(void *p, const double *er0, const double *ez0, const double *er1,
+                                const double *ez1, double *qc) {
+  o_field *F = (o_field *)p;
+  int nr = F->nr, nz = F->nz;
+  og_grid g = {nr, nz, F->dr, F->dz, F->xa, F->nd, F->erd, F->sgd};
+  double dt = F->dt, heat = 0.0;
+  for (int i = 0; i < nr; ++i)
+    for (int j = 1; j < nz; ++j) {
+      int e = i * (nz + 1) + j;
+      double q = dt * o_asig_r(&g, i) * 0.5 * (er0[e] + er1[e]);
+      qc[i * (nz + 1) + j] -= q;
+      qc[(i + 1) * (nz + 1) + j] += q;
+      heat += q * 0.5 * (er0[e] + er1[e]) * o_drc(&g, i);
+    }
+  for (int i = 0; i < nr; ++i)
+    for (int j = 0; j < nz; ++j) {
+      int e = i * nz + j;
+      double q = dt * o_asig_z(&g, i) * 0.5 * (ez0[e] + ez1[e]);
+      qc[i * (nz + 1) + j] -= q;
+      qc[i * (nz + 1) + j + 1] += q;
+      heat += q * 0.5 * (ez0[e] + ez1[e]) * F->dz;
+    }
+  return heat;
 }
 
 /* field energy over unknown edges and H cells */
@@ -1091,7 +1152,8 @@ typedef struct {
 
 /* Eq. 6 solved for the electrode potential phi^{n+1} of one Picard iteration.
  * The reactor-side current is the displacement current plus the crossed
- * charge through the dual faces of the first row of E_z edges above the
+ * charge (and, in a conducting ring, the conduction current at the half step)
+ * through the dual faces of the first row of E_z edges above the
  * powered plate (i < nr, j = 1/2): the integral over the electrode in Eq. 6
  * on the integral-form mesh.  It must equal the capacitor current
  * (C (V^{n+1} - phi^{n+1}) - q^n) / dt.  The field solve is affine in the
@@ -1102,7 +1164,7 @@ static double o_circuit(const orc_cfg *cfg, void *field, const double *er, const
                         double v1, double qn) {
   int nr = cfg->nr, nz = cfg->nz;
   size_t ner = (size_t)nr * (nz + 1), nez = (size_t)(nr + 1) * nz, nh = (size_t)nr * nz;
-  og_grid g = {nr, nz, cfg->dr, cfg->dz, cfg->xa, cfg->nd, cfg->erd};
+  og_grid g = {nr, nz, cfg->dr, cfg->dz, cfg->xa, cfg->nd, cfg->erd, ((o_field *)field)->sgd};
   double *era = (double *)malloc(sizeof(double) * ner), *eza = (double *)malloc(sizeof(double) * nez);
   double *ha = (double *)malloc(sizeof(double) * nh);
   double *zr = (double *)calloc(ner, sizeof(double)), *zz = (double *)calloc(nez, sizeof(double));
@@ -1114,9 +1176,9 @@ static double o_circuit(const orc_cfg *cfg, void *field, const double *er, const
   oracle_field_solve(field, zr, zz, zh, zr, zz, 0.0, 1.0, cfg->L, eru, ezu, hu, &src);
   double dq = 0.0, gu = 0.0;
   for (int i = 0; i < nr; ++i) {
-    double ea = cfg->eps * o_aeff_z(&g, i);
-    dq += ea * (eza[i * nz] - ez[i * nz]) + iz[i * nz];
-    gu += ea * ezu[i * nz];
+    double ea = cfg->eps * o_aeff_z(&g, i), hs = 0.5 * cfg->dt * o_asig_z(&g, i);
+    dq += ea * (eza[i * nz] - ez[i * nz]) + iz[i * nz] + hs * (eza[i * nz] + ez[i * nz]);
+    gu += (ea + hs) * ezu[i * nz];
   }
   free(era); free(eza); free(ha); free(zr); free(zz); free(zh); free(eru); free(ezu); free(hu);
   /* C (V - phi) - q^n = dq + (phi - V) gu */
