@@ -102,6 +102,10 @@ typedef struct pic_config {
                                  axis_cells cells have r = 2 dr sqrt(xa xi), the rest
                                  r = dr (xi + xa), dr = R / (nr + xa), r linear in xi inside
                                  each cell; 0 = uniform mesh r = xi R / nr */
+  double sigma_ring;          /* conductivity of the ring's cells [S/m] (Eq. 2's sigma E, taken
+                                 at the half step); a large value models a metal (Sec. 2.1).
+                                 Needs ring_cells > 0 and the EM model (an electrostatic run
+                                 models a metal by a large eps_ring); 0 = none */
 } pic_config;
 
 /* Per-step statistics (host struct). */
@@ -142,6 +146,9 @@ typedef struct pic_view {
   double *wall;               /* charge [C] absorbed at the walls since pic_init, per species s
                                  at wall + s*(2(nr+1) + nz+1): nodes of z = 0 (nr+1), of z = L
                                  (nr+1), of r = R (nz+1) */
+  double *qcond;              /* charge [C] the conducting ring's current moved since pic_init,
+                                 per node (nr+1) x (nz+1); Gauss's law holds with it added to
+                                 the particle and wall charge (zero without sigma_ring) */
 } pic_view;
 
 /* Conservation diagnostics (row a9), host struct filled by pic_diag. */

@@ -45,7 +45,8 @@ class Config(C.Structure):
                 ("picard_tol", _D), ("picard_max", _I), ("mcc_on", _I), ("bz", _D),
                 ("eps", _D), ("mu", _D), ("seed", C.c_ulonglong), ("precision", _I),
                 ("field_model", _I), ("cblock", _D), ("ions_fixed", _I), ("feed", _I),
-                ("ring_cells", _I), ("eps_ring", _D), ("axis_cells", _I)]
+                ("ring_cells", _I), ("eps_ring", _D), ("axis_cells", _I),
+                ("sigma_ring", _D)]
 
 
 class StepStats(C.Structure):
@@ -71,7 +72,7 @@ class View(C.Structure):
     _fields_ = [("cell", _P * 2), ("a", _P * 2), ("b", _P * 2), ("vr", _P * 2), ("vt", _P * 2),
                 ("vz", _P * 2), ("w", _P * 2), ("id", _P * 2), ("n", _LL * 2), ("cap", _LL * 2),
                 ("next_id", C.c_uint32 * 2), ("er", _P), ("ez", _P), ("h", _P), ("step", _LL),
-                ("real_size", _I), ("wall", _P)]
+                ("real_size", _I), ("wall", _P), ("qcond", _P)]
 
 
 class DiagOut(C.Structure):
@@ -173,7 +174,8 @@ def small_reactor(**kw):
                gas_pressure=2.0, gas_temp=300.0, n0=1e15, te_ev=3.0, ti_ev=0.026,
                np_init=40000, capacity_factor=1.5, picard_tol=1e-8, picard_max=50, mcc_on=1,
                bz=0.0, eps=0.0, mu=0.0, seed=0, precision=PIC_FP64, field_model=0, cblock=0.0,
-               ions_fixed=0, feed=0, ring_cells=0, eps_ring=1.0, axis_cells=0)
+               ions_fixed=0, feed=0, ring_cells=0, eps_ring=1.0, axis_cells=0,
+               sigma_ring=0.0)
     cfg.update(kw)
     return cfg
 
@@ -187,7 +189,8 @@ def large_reactor(**kw):
                gas_pressure=2.0, gas_temp=300.0, n0=1e15, te_ev=3.0, ti_ev=0.026,
                np_init=16 * 1024 * 1024, capacity_factor=1.25, picard_tol=1e-8, picard_max=50,
                mcc_on=1, bz=0.0, eps=0.0, mu=0.0, seed=1, precision=PIC_FP64, field_model=0,
-               cblock=0.0, ions_fixed=0, feed=0, ring_cells=0, eps_ring=1.0, axis_cells=0)
+               cblock=0.0, ions_fixed=0, feed=0, ring_cells=0, eps_ring=1.0, axis_cells=0,
+               sigma_ring=0.0)
     cfg.update(kw)
     return cfg
 
@@ -372,6 +375,7 @@ class Pic:
         out["ez"] = self._tensor(v.ez, (nr + 1) * nz, t.float64)
         out["h"] = self._tensor(v.h, nr * nz, t.float64)
         out["wall"] = self._tensor(v.wall, 2 * (2 * (nr + 1) + nz + 1), t.float64)
+        out["qcond"] = self._tensor(v.qcond, (nr + 1) * (nz + 1), t.float64)
         return out
 
     def wall_charge(self):

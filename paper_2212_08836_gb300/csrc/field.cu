@@ -74,8 +74,13 @@ __global__ void k_half_alpha64(long long n1, long long n2, const double *er0, co
   }
 }
 
-// rhs(i,j) = 2 mu Vh H0 - dt * C^T L Et   (Et = E0 - dQ/(2 eps A), or the prescribed half value)
-enum { kT2ear = 0, kT2eaz = 1, kTear = 2, kTeaz = 3, kTs = 4, kTvh = 5, kTw = 6 };
+// rhs(i,j) = 2 mu Vh H0 - dt * C^T L Et   (Et = (eps A E0 - dQ/2)/D, or the prescribed half value)
+// per-row tables: 1/(2D), 1/D of the E_r and E_z edges with D = eps A + dt S/2
+// (S: conducting part of the face, zero outside a conducting ring), 2 pi r_{i+1/2},
+// the H cell volume, the cell width, and eps A/D of the E_r and E_z edges (1
+// outside a conducting ring)
+enum { kT2ear = 0, kT2eaz = 1, kTear = 2, kTeaz = 3, kTs = 4, kTvh = 5, kTw = 6, kTgr = 7,
+       kTgz = 8, kTabs = 9 };
 __device__ __forceinline__ double tab(const FieldOp &F, int k, int i) {
   return F.rtab[k * (F.nr + 1) + i];
 }
@@ -88,12 +93,13 @@ __device__ __forceinline__ double rhs_at(const FieldOp &F, const double *er0, co
   double s = tab(F, kTs, i);
   double r2 = tab(F, kT2ear, i);
   double etb = 0.0, ett = 0.0;
-  if (j != 0) etb = er0[i * nz1 + j] - ir[i * nz1 + j] * r2;
-  if (j + 1 != nz) ett = er0[i * nz1 + j + 1] - ir[i * nz1 + j + 1] * r2;
-  double etl = ez0[i * nz + j] - iz[i * nz + j] * tab(F, kT2eaz, i);
+  double gr = tab(F, kTgr, i);
+  if (j != 0) etb = er0[i * nz1 + j] * gr - ir[i * nz1 + j] * r2;
+  if (j + 1 != nz) ett = er0[i * nz1 + j + 1] * gr - ir[i * nz1 + j + 1] * r2;
+  double etl = ez0[i * nz + j] * tab(F, kTgz, i) - iz[i * nz + j] * tab(F, kT2eaz, i);
   double etr;
   if (i + 1 == nr) etr = 0.5 * (v0 + v1) / F.L;
-  else etr = ez0[(i + 1) * nz + j] - iz[(i + 1) * nz + j] * tab(F, kT2eaz, i + 1);
+  else etr = ez0[(i + 1) * nz + j] * tab(F, kTgz, i + 1) - iz[(i + 1) * nz + j] * tab(F, kT2eaz, i + 1);
   double curl = (-s) * dr * etb + s * dr * ett + s * dz * etl + (-s) * dz * etr;
   return 2.0 * F.mu * tab(F, kTvh, i) * h0[c] - F.dt * curl;
 }
@@ -447,7 +453,8 @@ __global__ void __launch_bounds__(256) k_update(FieldOp F, const double *er0, co
     } else {
       double s = tab(F, kTs, i);
       double ch = -s * hh_at(F, dl, i, j) + s * hh_at(F, dl, i, j - 1);
-      double e1 = er0[t] + (dt * ch - ir[t]) * tab(F, kTear, i);
+      // (eps A + dt S/2) E1 = (eps A - dt S/2) E0 + dt C H - dQ
+      double e1 = er0[t] * (2.0 * tab(F, kTgr, i) - 1.0) + (dt * ch - ir[t]) * tab(F, kTear, i);
       er1[t] = e1;
       if (er_it) {
         double d = e1 - er_it[t];
@@ -472,7 +479,7 @@ __global__ void __launch_bounds__(256) k_update(FieldOp F, const double *er0, co
       }
       src += eh * dz * (iz[t] - dt * ch);
     } else {
-      double e1 = ez0[t] + (dt * ch - iz[t]) * tab(F, kTeaz, i);
+      double e1 = ez0[t] * (2.0 * tab(F, kTgz, i) - 1.0) + (dt * ch - iz[t]) * tab(F, kTeaz, i);
       ez1[t] = e1;
       if (ez_it) {
         double d = e1 - ez_it[t];

@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(256) k_node_charge(Grid g, PartsT<T> p, long l
 // charge on entry and the residual on exit.
 __global__ void __launch_bounds__(256) k_gauss_residual(Grid g, double eps, const double *er,
                                                         const double *ez, const double *wall,
-                                                        double *Q) {
+                                                        const double *qc, double *Q) {
   const int nz = g.nz, nz1 = nz + 1;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)(g.nr + 1) * nz1) return;
@@ -142,6 +142,7 @@ __global__ void __launch_bounds__(256) k_gauss_residual(Grid g, double eps, cons
     const int blk = 2 * (g.nr + 1) + nz1;
     Q[t] += wall[2 * (g.nr + 1) + j] + wall[blk + 2 * (g.nr + 1) + j];
   }
+  if (qc) Q[t] += qc[t];
   double flux = g_aeff_r(g, i) * er[i * nz1 + j];
   if (i >= 1) flux -= g_aeff_r(g, i - 1) * er[(i - 1) * nz1 + j];
   flux += g_aeff_z(g, i) * (ez[i * nz + j] - ez[i * nz + j - 1]);
@@ -169,9 +170,39 @@ __global__ void __launch_bounds__(128) k_fourier_bessel(const double *__restrict
 }  // namespace
 
 cudaError_t launch_gauss_residual(const Grid &g, double eps, const double *er, const double *ez,
-                                  const double *wall, double *Q, cudaStream_t s) {
+                                  const double *wall, const double *qc, double *Q, cudaStream_t s) {
   const long long n = (long long)(g.nr + 1) * (g.nz + 1);
-  k_gauss_residual<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, eps, er, ez, wall, Q);
+  k_gauss_residual<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, eps, er, ez, wall, qc, Q);
+  return cudaGetLastError();
+}
+
+// Conduction tally of a conducting ring: node (i, j) loses dt S E^{n+1/2} through
+// each unknown edge that starts at it and gains it through each that ends at it
+__global__ void __launch_bounds__(256) k_conduction(Grid g, double dt, const double *er0,
+                                                    const double *ez0, const double *er1,
+                                                    const double *ez1, double *qc) {
+  const int nr = g.nr, nz = g.nz, nz1 = nz + 1;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)(nr + 1) * nz1) return;
+  const int i = (int)(t / nz1), j = (int)(t - (t / nz1) * nz1);
+  const double h = 0.5 * dt;
+  double d = 0.0;
+  if (j >= 1 && j <= nz - 1) {
+    if (i < nr) d -= h * g_asig_r(g, i) * (er0[i * nz1 + j] + er1[i * nz1 + j]);
+    if (i >= 1) d += h * g_asig_r(g, i - 1) * (er0[(i - 1) * nz1 + j] + er1[(i - 1) * nz1 + j]);
+  }
+  if (i < nr) {
+    const double sz = h * g_asig_z(g, i);
+    if (j < nz) d -= sz * (ez0[i * nz + j] + ez1[i * nz + j]);
+    if (j >= 1) d += sz * (ez0[i * nz + j - 1] + ez1[i * nz + j - 1]);
+  }
+  qc[t] += d;
+}
+
+cudaError_t launch_conduction(const Grid &g, double dt, const double *er0, const double *ez0,
+                              const double *er1, const double *ez1, double *qc, cudaStream_t s) {
+  const long long n = (long long)(g.nr + 1) * (g.nz + 1);
+  k_conduction<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(g, dt, er0, ez0, er1, ez1, qc);
   return cudaGetLastError();
 }
 

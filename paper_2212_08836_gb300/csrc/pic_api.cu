@@ -87,6 +87,7 @@ struct pic_ctx {
   long long *n_dev;
   double *vdev;             // [0..1] V^n, V^{n+1}; [4..7] blocking-capacitor state (Circuit)
   double *hu;               // EM unit response of the circuit (nr x nz)
+  double *qc;               // charge moved by the conducting ring's current (nodes)
   double *rmap64;           // mapped mesh: radial scales of the first cells (RadialMapT)
   float *rmap32;
   int circ_on;
@@ -212,6 +213,8 @@ bool valid(const pic_config *c) {
     return false;
   if (c->feed == PIC_FEED_WAVE && (c->field_model != PIC_FIELD_EM || c->cblock > 0.0))
     return false;
+  if (!(c->sigma_ring >= 0.0) || !isfinite(c->sigma_ring)) return false;
+  if (c->sigma_ring > 0.0 && (c->ring_cells == 0 || c->field_model != PIC_FIELD_EM)) return false;
   if (c->ions_fixed && c->mcc_on) return false;
   return true;
 }
@@ -271,6 +274,7 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
   x->iz = (double *)K.take(nez * 8);
   x->wall = (double *)K.take((size_t)2 * (2 * (nr + 1) + nz + 1) * 8);
   x->wall_spec = (double *)K.take((size_t)2 * (2 * (nr + 1) + nz + 1) * 8);
+  x->qc = (double *)K.take((size_t)(nr + 1) * (nz + 1) * 8);
   x->F.Q = (double *)K.take((size_t)nz * nz * 8);
   x->F.QT = (double *)K.take((size_t)nz * nz * 8);
   int n2 = 1;
@@ -299,7 +303,7 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
   }
   x->F.tw = (const double2 *)K.take((size_t)nz * 16);
   x->F.pw = (const double2 *)K.take((size_t)nz * 16);
-  x->F.rtab = (const double *)K.take((size_t)7 * (nr + 1) * 8);
+  x->F.rtab = (const double *)K.take((size_t)9 * (nr + 1) * 8);
   x->cnt = (DevCounters *)K.take(sizeof(DevCounters));
   for (int k = 0; k < 3; ++k) {
     x->hr[k] = (double *)K.take(ner * 8);
@@ -544,6 +548,7 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
   x->g.xa = cfg->axis_cells;
   x->g.nd = cfg->ring_cells;
   x->g.erd = cfg->ring_cells > 0 ? cfg->eps_ring : 1.0;
+  x->g.sgd = cfg->ring_cells > 0 ? cfg->sigma_ring : 0.0;
   x->g.dr = cfg->R / (nr + cfg->axis_cells);
   x->g.dz = cfg->L / nz;
   x->eps = cfg->eps > 0 ? cfg->eps : kEps0;
@@ -645,14 +650,16 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
   auto wr = [&](int i) { return g_width(G, i); };
   auto az = [&](int i) { return g_aeff_z(G, i); };     // permittivity-weighted
   auto are = [&](int i) { return g_aeff_r(G, i); };
+  // D = eps A + dt S / 2 per edge (S: the conducting part, Eq. 2's sigma E at the half step)
+  auto dnr = [&](int i) { return x->eps * are(i) + 0.5 * cfg->dt * g_asig_r(G, i); };
+  auto dnz = [&](int i) { return x->eps * az(i) + 0.5 * cfg->dt * g_asig_z(G, i); };
   for (int i = 0; i < nr; ++i) {
     mass[i] = 2.0 * x->mu * (kTwoPi * rh(i) * wr(i) * dz);
-    double ar = are(i);
     double s = kTwoPi * rh(i);
-    kz[i] = hdt2 * (wr(i) / (x->eps * ar)) * s * s;
-    double wz_i = dz / (x->eps * az(i));
+    kz[i] = hdt2 * (wr(i) / dnr(i)) * s * s;
+    double wz_i = dz / dnz(i);
     double d = wz_i * s * s;
-    if (i + 1 <= nr - 1) d += (dz / (x->eps * az(i + 1))) * s * s;
+    if (i + 1 <= nr - 1) d += (dz / dnz(i + 1)) * s * s;
     kdiag[i] = hdt2 * d;
     if (i >= 1) eoff[i] = hdt2 * wz_i * (-kTwoPi * rh(i - 1)) * s;
   }
@@ -718,7 +725,7 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
     cr_coeffs(n2, A, B, Cc, ecr.data() + (size_t)(m - 1) * 5 * n2);
   }
   // twiddles, DCT phases and per-row reciprocal tables
-  std::vector<double> tw((size_t)2 * nz), pw((size_t)2 * nz), rt((size_t)7 * (nr + 1), 0.0);
+  std::vector<double> tw((size_t)2 * nz), pw((size_t)2 * nz), rt((size_t)9 * (nr + 1), 0.0);
   for (int k = 0; k < nz; ++k) {
     double t = -kTwoPi * (double)k / nz;
     tw[2 * k] = cos(t);
@@ -728,15 +735,20 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
     pw[2 * k + 1] = sin(u);
   }
   for (int i = 0; i <= nr; ++i) {
-    double ari = i < nr ? are(i) : kTwoPi * rh(i) * dz;
-    double azi = az(i);
-    rt[0 * (nr + 1) + i] = 1.0 / (2.0 * x->eps * ari);
-    rt[1 * (nr + 1) + i] = 1.0 / (2.0 * x->eps * azi);
-    rt[2 * (nr + 1) + i] = 1.0 / (x->eps * ari);
-    rt[3 * (nr + 1) + i] = 1.0 / (x->eps * azi);
+    // the E_r row nr and the E_z node nr are prescribed: only their finite
+    // placeholders matter
+    double ear = x->eps * (i < nr ? are(i) : kTwoPi * rh(i) * dz);
+    double eaz = x->eps * az(i);
+    double dr_ = i < nr ? dnr(i) : ear, dz_ = i < nr ? dnz(i) : eaz;
+    rt[0 * (nr + 1) + i] = 1.0 / (2.0 * dr_);
+    rt[1 * (nr + 1) + i] = 1.0 / (2.0 * dz_);
+    rt[2 * (nr + 1) + i] = 1.0 / dr_;
+    rt[3 * (nr + 1) + i] = 1.0 / dz_;
     rt[4 * (nr + 1) + i] = kTwoPi * rh(i);
     rt[5 * (nr + 1) + i] = kTwoPi * rh(i) * wr(i) * dz;
     rt[6 * (nr + 1) + i] = wr(i);
+    rt[7 * (nr + 1) + i] = dr_ == ear ? 1.0 : ear / dr_;
+    rt[8 * (nr + 1) + i] = dz_ == eaz ? 1.0 : eaz / dz_;
   }
   cudaError_t e = cudaSuccess;
   auto up = [&](const void *dst, const void *src, size_t b) {
@@ -771,6 +783,7 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
   if (e == cudaSuccess) e = cudaMemsetAsync(x->h, 0, nh * 8, x->s);
   if (e == cudaSuccess) e = cudaMemsetAsync(x->h2, 0, nh * 8, x->s);
   if (e == cudaSuccess) e = cudaMemsetAsync(x->wall, 0, (size_t)2 * (2 * (nr + 1) + nz + 1) * 8, x->s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(x->qc, 0, (size_t)(nr + 1) * (nz + 1) * 8, x->s);
   if (e == cudaSuccess) e = cudaMemsetAsync(x->cnt, 0, sizeof(DevCounters), x->s);
   if (e == cudaSuccess) e = cudaHostAlloc((void **)&x->hn, 8 * kHnSlots, cudaHostAllocDefault);
   if (e == cudaSuccess) e = cudaStreamSynchronize(x->s);
@@ -1484,6 +1497,12 @@ int step_end(pic_ctx *x, StepState &T, int *rc) {
     if (launch_circuit_commit(x->F.cc, x->vdev, s) != cudaSuccess) return PIC_E_CUDA;
     x->launches += 1;
   }
+  if (x->g.sgd > 0.0) {
+    // charge moved by the conducting ring's current over the committed step
+    if (launch_conduction(x->g, x->cfg.dt, x->er, x->ez, x->er1, x->ez1, x->qc, s) != cudaSuccess)
+      return PIC_E_CUDA;
+    x->launches += 1;
+  }
   if (x->cfg.field_model == PIC_FIELD_ES) {
     // Q^{n+1} = Q^n - div I of the committed step (ionization pairs are neutral)
     if (launch_es_advance(x->es, x->qn, x->ir, x->iz, s) != cudaSuccess) return PIC_E_CUDA;
@@ -1629,7 +1648,8 @@ int pic_gauss_residual(pic_ctx *x, double *res) {
   int r = pic_node_charge(x, res);
   if (r) return r;
   x->launches += 3;
-  return cuda_rc(launch_gauss_residual(x->g, x->eps, x->er, x->ez, x->wall, res, x->s));
+  return cuda_rc(launch_gauss_residual(x->g, x->eps, x->er, x->ez, x->wall,
+                                       x->g.sgd > 0.0 ? x->qc : nullptr, res, x->s));
 }
 
 int pic_get_view(pic_ctx *x, pic_view *v) {
@@ -1654,6 +1674,7 @@ int pic_get_view(pic_ctx *x, pic_view *v) {
   v->step = x->step;
   v->real_size = x->mixed ? 4 : 8;
   v->wall = x->wall;
+  v->qcond = x->qc;
   return PIC_OK;
 }
 
@@ -1689,6 +1710,8 @@ int ckpt_arrays(pic_ctx *x, const long long n[2], F &&f) {
   if (int r = f(x->wall, (size_t)2 * (2 * (nr + 1) + nz + 1) * 8)) return r;
   if (x->cfg.field_model == PIC_FIELD_ES)
     if (int r = f(x->qn, (size_t)(nr + 1) * (nz + 1) * 8)) return r;
+  if (x->g.sgd > 0.0)
+    if (int r = f(x->qc, (size_t)(nr + 1) * (nz + 1) * 8)) return r;
   return PIC_OK;
 }
 

@@ -71,6 +71,7 @@ struct Grid {
   int xa;               // cells with r proportional to sqrt(xi)
   int nd;               // dielectric ring: the outer nd cells, relative permittivity erd
   double erd;
+  double sgd;           // conductivity of the ring's cells [S/m] (0: a pure dielectric)
 };
 
 // node radius r_i, cell width J_r, cell-centre radius, and the inner-face
@@ -111,6 +112,18 @@ __host__ __device__ inline double g_aeff_z(const Grid &g, int i) {
   if (i > i0) return g.erd * g_area_z(g, i);
   const double ri = g_rnode(g, i), rm = g_rcentre(g, i - 1), rp = g_rcentre(g, i);
   return kPi * (ri * ri - rm * rm) + g.erd * kPi * (rp * rp - ri * ri);
+}
+// conducting part of the same dual faces (Eq. 2's sigma E in the ring): the
+// ring's conductivity times the face area inside the ring
+__host__ __device__ inline double g_asig_r(const Grid &g, int i) {
+  return (g.nd > 0 && i >= g.nr - g.nd) ? g.sgd * (kTwoPi * g_rcentre(g, i) * g.dz) : 0.0;
+}
+__host__ __device__ inline double g_asig_z(const Grid &g, int i) {
+  const int i0 = g.nr - g.nd;
+  if (g.nd == 0 || g.sgd == 0.0 || i < i0) return 0.0;
+  if (i > i0) return g.sgd * g_area_z(g, i);
+  const double ri = g_rnode(g, i), rp = g_rcentre(g, i);
+  return g.sgd * kPi * (rp * rp - ri * ri);
 }
 
 // Particle structure of arrays of one species; T = double (plain FP64 form)
@@ -254,9 +267,14 @@ struct EsOp {
 // Picard norms against er_it / ez_it into cnt when cnt is given
 // Q -= div I on the interior nodes (the charge carried to the next step)
 // Q <- eps div_h E - Q on the interior nodes (zero elsewhere); with the
-// dielectric ring the charge stuck on its face (wall: the wall tallies) joins Q
+// dielectric ring the charge stuck on its face (wall: the wall tallies) joins Q,
+// and with a conducting ring the charge its conduction current moved (qc)
 cudaError_t launch_gauss_residual(const Grid &g, double eps, const double *er, const double *ez,
-                                  const double *wall, double *Q, cudaStream_t s);
+                                  const double *wall, const double *qc, double *Q, cudaStream_t s);
+// qc -= the charge the conducting ring's current moves over one step, dt S E^{n+1/2}
+// per edge from its lower to its upper node (E^n in er0/ez0, E^{n+1} in er1/ez1)
+cudaError_t launch_conduction(const Grid &g, double dt, const double *er0, const double *ez0,
+                              const double *er1, const double *ez1, double *qc, cudaStream_t s);
 // c[m] = sum_k basis[m n + k] f[k stride], m < nmodes (one block per mode)
 cudaError_t launch_fourier_bessel(const double *basis, const double *f, int stride, int n,
                                   int nmodes, double *coef, cudaStream_t s);
