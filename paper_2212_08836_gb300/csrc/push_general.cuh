@@ -16,6 +16,7 @@
 #pragma once
 
 #include "pic_internal.cuh"
+#include "swfp.cuh"
 
 namespace pic {
 
@@ -29,6 +30,10 @@ struct Num<float> {
   // fast in-cell solve: estimated error below half an ulp of the displacement
   static constexpr float fast_rel = 6e-8f, fast_abs = 1e-12f;
   __device__ static __forceinline__ float rcp(float x) { return __fdividef(1.f, x); }
+  // a product that feeds no addition (the FP64 form moves these off its FP64 pipe)
+  __device__ static __forceinline__ float mul(float x, float y) { return x * y; }
+  // 2x for finite x >= 0
+  __device__ static __forceinline__ float twice(float x) { return x + x; }
   // 0 < x < 1 on the bits (positive floats order like their bit patterns)
   __device__ static __forceinline__ bool in01(float x) {
     const int b = __float_as_int(x);
@@ -137,6 +142,16 @@ struct Num<double> {
     return (__double_as_longlong(x) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
   }
   __device__ static __forceinline__ double to_double(double f) { return f; }
+  // a product that feeds no addition: the correctly rounded integer-pipe
+  // multiply (bit-identical to the FP64 pipe's, which stays free for the rest)
+  __device__ static __forceinline__ double mul(double x, double y) { return sw_dmul(x, y); }
+  // 2x for finite x >= 0, exactly, on the bits: a zero or subnormal doubles its
+  // significand field (which carries into the exponent field when it becomes
+  // normal), a normal number takes one more in its exponent field
+  __device__ static __forceinline__ double twice(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return __longlong_as_double((long long)((b >> 52) == 0 ? b << 1 : b + (1ull << 52)));
+  }
 };
 
 constexpr int kNewtonMaxGen = 30;
@@ -368,33 +383,38 @@ constexpr unsigned kOpFastNewton = 25, kOpFastAccept = 58;
 //   K = ur + (ar0 + gar*b)/2 + gar/4 * zb,
 //   C(d)/2 = ut^2 (2 rho + d) / (4 (rho + d)^2)
 // (C = ut_m^2 / rho_m with the CN-exact ut' = rho*ut/(rho + d)).  g' > 0 on
-// d > -rho, so the root is unique; Newton's error after a step s is about
-// |g''|/(2 g') s^2, with |g''| = ut^2 (4 rho + d) / (2 (rho + d)^4); the
-// iterate is accepted when twice that estimate is below half an ulp of d
-// (the CN velocity u' = 2d - u must not amplify an unconverged d).
+// d > -rho, so the root is unique.  Newton runs on the cleared forms, with
+// r1 = rho + d:
+//   G  = g r1^2  = (k1 d - K) r1^2 - ut^2 (2 rho + d) / 4,
+//   G' = g' r1^3 = k1 r1^3 + ut^2 (3 rho + d) / 4,
+// so that a step s = -g/g' = -G r1 / G' takes one reciprocal.  Newton's error
+// after the step is about |g''|/(2 g') s^2 with |g''| = ut^2 (4 rho + d) /
+// (2 r1^4), i.e. ut^2 (4 rho + d) s^2 / (4 r1 G'); the iterate is accepted when
+// twice that estimate is below half an ulp of d (the CN velocity u' = 2d - u
+// must not amplify an unconverged d), tested without a division.
 template <typename T>
 __device__ __forceinline__ bool fast_solve(T rho, T ut, T K, T k1, T &pd, unsigned &nit) {
-  const T zero = (T)0, q = (T)0.25, h = (T)0.5;
-  const T ut2 = ut * ut, r2 = rho + rho, r3 = r2 + rho, r4 = r2 + r2;
+  typedef Num<T> N;
+  const T zero = (T)0;
+  // rho >= 0 and the squares are non-negative: the doublings are exact bit edits
+  const T qut2 = N::mul(N::mul(ut, ut), (T)0.25), hut2 = N::twice(qut2);
+  const T r2 = N::twice(rho), r3 = r2 + rho, r4 = N::twice(r2);
   T d = K;
 #pragma unroll 1
   for (int it = 0; it < kFastNewtonMax; ++it) {
-    T r1 = rho + d;
-    if (!Num<T>::gt(r1, zero)) return false;
-    T x = Num<T>::rcp(r1);
-    T s2 = ut2 * x * x;
-    T g = k1 * d - K - q * s2 * (r2 + d);
-    T gp = k1 + q * s2 * (r3 + d) * x;
-    T ig = Num<T>::rcp(gp);
-    T st = -g * ig;
-    // twice the Newton error estimate of the updated iterate
-    T kap = h * s2 * x * x * (r4 + d) * ig;
+    const T r1 = rho + d;
+    if (!N::gt(r1, zero)) return false;
+    const T R2 = N::mul(r1, r1);
+    const T G = N::mul(k1 * d - K, R2) - qut2 * (r2 + d);
+    const T Gp = k1 * N::mul(R2, r1) + N::mul(qut2, r3 + d);
+    const T st = -N::mul(N::mul(G, r1), N::rcp(Gp));
+    const T lhs = N::mul(N::mul(hut2, r4 + d), N::mul(st, st));
     d += st;
     nit++;
-    if (Num<T>::le(kap * st * st, Num<T>::maxb(Num<T>::fast_rel * Num<T>::absb(d),
-                                                (T)Num<T>::fast_abs))) {
+    const T tol = N::maxb(N::mul(N::fast_rel, N::absb(d)), (T)N::fast_abs);
+    if (N::le(lhs, N::mul(N::mul(tol, r1), Gp))) {
       pd = d;
-      return Num<T>::finite(d);
+      return N::finite(d);
     }
   }
   return false;

@@ -184,42 +184,45 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_push_fast(PushL
       jc = c0 - ic * nz;
       if (jc < 0) { ic -= 1; jc += nz; }
       else if (jc >= nz) { ic += 1; jc -= nz; }
+      // products that feed no addition go through Num<T>::mul (the FP64 form
+      // computes them on the integer pipes)
+      typedef Num<T> N;
       const T crr = L.rm.crr(ic);
-      ur = cur.vr * crr;
-      ut = cur.vt * crr;
-      uz = cur.vz * L.cz;
+      ur = N::mul(cur.vr, crr);
+      ut = N::mul(cur.vt, crr);
+      uz = N::mul(cur.vz, L.cz);
       const T rho = L.rm.rho0(ic) + a;
       bool acc = false;
-      if (Num<T>::in01(a) && Num<T>::in01(b) && Num<T>::lt_abs(ut, q * rho)) {
+      if (N::in01(a) && N::in01(b) && N::lt_abs(ut, N::mul(q, rho))) {
         const T ar0 = L.ar[ic * nz1 + jc];
         const T gar = L.ar[ic * nz1 + jc + 1] - ar0;
         const T az0 = L.az[ic * nz + jc];
         const T gaz = L.az[(ic + 1) * nz + jc] - az0;
         const T zb = uz + h * (az0 + gaz * a);
-        const T K = ur + h * (ar0 + gar * b) + q * gar * zb;
-        const T k1 = one - (T)0.0625 * gar * gaz;
+        const T K = ur + h * (ar0 + gar * b) + N::mul(q, gar) * zb;
+        const T k1 = one - N::mul((T)0.0625, gar) * gaz;
         if (Num<T>::gt(k1, h) && fast_solve<T>(rho, ut, K, k1, d, n_newton)) {
           trial = true;
-          e = zb + q * gaz * d;
+          e = zb + N::mul(q, gaz) * d;
           const T a1 = a + d, b1 = b + e;
           acc = Num<T>::in01(a1) && Num<T>::in01(b1);
           if (acc) {
             n_acc++;
-            const T qw = L.qf * w;
-            const T fr = qw * d, fz = qw * e;
+            const T qw = N::mul(L.qf, w);
+            const T fr = N::mul(qw, d), fz = N::mul(qw, e);
             const T am = a + h * d, bm = b + h * e;
-            v0 = fr * (one - bm);
-            v1 = fr * bm;
-            v2 = fz * (one - am);
-            v3 = fz * am;
+            v1 = N::mul(fr, bm);
+            v0 = fr - v1;
+            v3 = N::mul(fz, am);
+            v2 = fz - v3;
             if (L.write) {
               // CN velocity relations: the displacement is the mean of u and u'
               L.dst.a[p] = a1;
               L.dst.b[p] = b1;
               const T icr = L.rm.icrr(ic);
-              L.dst.vr[p] = (d + d - ur) * icr;
-              L.dst.vz[p] = (e + e - uz) * L.icz;
-              L.dst.vt[p] = rho * ut * Num<T>::rcp(rho + d) * icr;
+              L.dst.vr[p] = N::mul((T)2 * d - ur, icr);
+              L.dst.vz[p] = N::mul((T)2 * e - uz, L.icz);
+              L.dst.vt[p] = N::mul(N::mul(N::mul(rho, ut), N::rcp(rho + d)), icr);
               if (L.oop) {
                 L.dst.cell[p] = c0;
                 L.dst.w[p] = w;
