@@ -355,6 +355,17 @@ int pic_sort_cells_noalloc(int nr, int nz, long long n, const int32_t *cell_dev,
                            double *vz_out_dev, double *w_out_dev, uint32_t *id_out_dev,
                            void *stream, long long *n_out);
 
+/* Self-check of the binary64 multiply the FP64 mover computes on the integer
+ * pipes for products that feed no addition (IEEE 754 round to nearest, ties to
+ * even, in 64-bit integer arithmetic; operands or results outside the normal
+ * range take the hardware multiply).  The paper has no counterpart: it lets a
+ * test compare out[i] = x[i] * y[i] bit for bit with any IEEE binary64
+ * multiply.  x_dev, y_dev, out_dev: device arrays of n doubles (caller-owned);
+ * runs on `stream` (NULL: the legacy default stream) and synchronises it.
+ * Errors: PIC_E_CONFIG (n < 0, a null array with n > 0), PIC_E_CUDA. */
+int pic_check_dmul(const double *x_dev, const double *y_dev, double *out_dev, long long n,
+                   void *stream);
+
 #ifdef __cplusplus
 }
 #endif

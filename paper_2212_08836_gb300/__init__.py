@@ -103,6 +103,7 @@ def _load_lib():
     L.pic_set_counts.argtypes = [_P, _LL, _LL, C.c_uint32, C.c_uint32, _LL]
     L.pic_mcc_constants.argtypes = [_P, _P, _P, _P, _P]
     L.pic_sort_cells_noalloc.argtypes = [_I, _I, _LL] + [_P] * 16 + [_P, _P]
+    L.pic_check_dmul.argtypes = [_P, _P, _P, _LL, _P]
     L.pic_profile.argtypes = [_P, _I]
     L.pic_profile_read.argtypes = [_P, _P, _P]
     L.pic_cnn_workspace_size.argtypes = [C.POINTER(CnnConfig)]
@@ -428,6 +429,17 @@ class Pic:
         v = self.view()
         self.torch.cuda.synchronize(self.device)
         return tuple(v[k].cpu().numpy().copy() for k in ("er", "ez", "h"))
+
+
+def check_dmul(x, y):
+    """x * y elementwise through the integer-pipe binary64 multiply of the FP64
+    mover (pic_check_dmul); x, y: float64 CUDA tensors of one shape."""
+    import torch
+    x, y = x.contiguous(), y.contiguous()
+    out = torch.empty_like(x)
+    _check(lib().pic_check_dmul(x.data_ptr(), y.data_ptr(), out.data_ptr(), x.numel(),
+                                torch.cuda.current_stream(x.device).cuda_stream), "pic_check_dmul")
+    return out
 
 
 def drive_voltage(cfg, step):

@@ -256,3 +256,28 @@ PIC_INST(float)
 #undef PIC_INST
 
 }  // namespace pic
+
+// ---------------------------------------------------------------------------
+// self-check of the integer-pipe binary64 multiply (pic_check_dmul)
+#include "swfp.cuh"
+namespace pic {
+namespace {
+__global__ void __launch_bounds__(256) k_check_dmul(const double *x, const double *y, double *o,
+                                                    long long n) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    o[i] = sw_dmul(x[i], y[i]);
+}
+}  // namespace
+}  // namespace pic
+
+extern "C" int pic_check_dmul(const double *x, const double *y, double *out, long long n,
+                              void *stream) {
+  if (n < 0 || (n > 0 && (!x || !y || !out))) return PIC_E_CONFIG;
+  if (n == 0) return PIC_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long nb = (n + 255) / 256;
+  pic::k_check_dmul<<<(unsigned)(nb < 152 * 16 ? nb : 152 * 16), 256, 0, s>>>(x, y, out, n);
+  if (cudaGetLastError() != cudaSuccess) return PIC_E_CUDA;
+  return cudaStreamSynchronize(s) == cudaSuccess ? PIC_OK : PIC_E_CUDA;
+}
