@@ -246,7 +246,7 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
     }
   const size_t qc = pc + (size_t)kMaxFastBlocks * 256;  // queue entries
   x->queue = (int *)K.take(qc * 4);
-  x->qblock = (int *)K.take((size_t)kMaxFastBlocks * 4);
+  x->qblock = (int *)K.take((size_t)2 * kMaxFastBlocks * 4);  // front and back counts
   if (c->precision == PIC_MIXED) {
     for (int s = 0; s < 2; ++s) {
       x->alpha.ar[s] = (float *)K.take(ner * 4);

@@ -235,7 +235,10 @@ struct PushLaunchT {
   unsigned long long *counters;
   double *ke_lost;
   // work queue of the general path (queue == nullptr: all particles).  Block b
-  // of the fast kernel appends to entries [b*qseg, b*qseg + qblock[b]).
+  // of the fast kernel appends the particles whose whole-step trial leaves the
+  // cell through a z-face only to entries [b*qseg, b*qseg + qblock[b]) and the
+  // rest from the back of its segment, qblock[qgrid + b] of them, so that the
+  // general kernel's warps take those two kinds one after the other.
   int *queue, *qblock;
   long long qseg;
   int qgrid;               // blocks of the fast kernel

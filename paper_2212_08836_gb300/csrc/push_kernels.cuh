@@ -150,8 +150,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_push_fast(PushL
   const T zero = (T)0, one = (T)1, h = (T)0.5, q = (T)0.25;
   const long long stride = (long long)gridDim.x * blockDim.x;
   unsigned n_newton = 0, n_acc = 0;
-  __shared__ int s_qn;  // entries this block appended to its queue segment
-  if (threadIdx.x == 0) s_qn = 0;
+  // entries this block appended to its queue segment: [0] z-face-only
+  // crossings of the trial from the front, [1] the rest from the back
+  __shared__ int s_qn[2];
+  if (threadIdx.x < 2) s_qn[threadIdx.x] = 0;
   __syncthreads();
   const long long qoff = (long long)blockIdx.x * L.qseg;
   const long long n = L.n_dev ? *L.n_dev : L.n;
@@ -174,7 +176,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_push_fast(PushL
     const T a = cur.a, b = cur.b, w = cur.w;
     T ur = zero, ut = zero, uz = zero;
     T v0 = zero, v1 = zero, v2 = zero, v3 = zero;
-    bool queued = false, trial = false;
+    bool queued = false, trial = false, zcross = false;
     T d = zero, e = zero;
     int key = -1, ic = 0, jc = 0;
     if (c0 >= 0 && c0 < ncell) {
@@ -206,6 +208,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_push_fast(PushL
           e = zb + N::mul(q, gaz) * d;
           const T a1 = a + d, b1 = b + e;
           acc = Num<T>::in01(a1) && Num<T>::in01(b1);
+          zcross = Num<T>::in01(a1) && !Num<T>::in01(b1);
           if (acc) {
             n_acc++;
             const T qw = N::mul(L.qf, w);
@@ -239,7 +242,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_push_fast(PushL
     warp_deposit<T>(key, ic, jc, v0, v1, v2, v3, lane, nz, L.ir, L.iz);
     // queue the rest for the general path (warp-aggregated append to the
     // block's segment; the shared-memory counter keeps it off global atomics)
-    const long long k = seg_append(&s_qn, queued, lane, qoff);
+    // two kinds in the FP64 form only: there the general kernel is bound by its
+    // FP64 pipe, which spends a whole warp slot on each instruction of a
+    // divergent warp (the FP32 form is issue-bound and gains nothing from it)
+    const bool front = sizeof(T) == 8 ? zcross : true;
+    const long long kf = seg_append(&s_qn[0], queued && front, lane, qoff);
+    const long long kb = sizeof(T) == 8 ? seg_append(&s_qn[1], queued && !front, lane, 0) : 0;
+    const long long k = front ? kf : qoff + L.qseg - 1 - kb;
     if (queued) {
       L.queue[k] = (int)p;
       L.q_da[k] = trial ? d : (T)NAN;
@@ -247,7 +256,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_push_fast(PushL
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0) L.qblock[blockIdx.x] = s_qn;
+  if (threadIdx.x == 0) {
+    L.qblock[blockIdx.x] = s_qn[0];
+    L.qblock[L.qgrid + blockIdx.x] = s_qn[1];
+  }
   Tally T0 = {0, 0, 0, 0, 0, 0};
   flush_tally(L.counters, T0, lane, n_newton, n_acc);
 }
@@ -266,8 +278,14 @@ __global__ void __launch_bounds__(256) k_push_general(PushLaunchT<T> L) {
   const long long gstride = (long long)gridDim.x * blockDim.x;
   const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (L.queue) {
-    __shared__ int s_pre[kMaxFastBlocks + 1];
-    const int total = seg_prefix(L.qblock, L.qgrid, s_pre);
+    // the z-face-only crossings first, then the rest (uniform warps)
+    __shared__ int s_pre[kMaxFastBlocks + 1], s_preb[kMaxFastBlocks + 1];
+    const int total_f = seg_prefix(L.qblock, L.qgrid, s_pre);
+    const int total = total_f + seg_prefix(L.qblock + L.qgrid, L.qgrid, s_preb);
+    auto entry = [&](long long q) {
+      return q < total_f ? seg_entry(s_pre, L.qgrid, L.qseg, (int)q)
+                         : seg_entry_back(s_preb, L.qgrid, L.qseg, (int)(q - total_f));
+    };
     if (sizeof(T) == 4) {
       // FP32 form: the next entry's start state (a scattered re-read from the
       // store) is loaded while this one is pushed
@@ -277,7 +295,7 @@ __global__ void __launch_bounds__(256) k_push_general(PushLaunchT<T> L) {
         T da, db;
       };
       auto fetch = [&](long long q, Ent &en) {
-        const long long k = seg_entry(s_pre, L.qgrid, L.qseg, (int)q);
+        const long long k = entry(q);
         en.p = L.queue[k];
         en.da = L.q_da[k];
         en.db = L.q_db[k];
@@ -293,7 +311,7 @@ __global__ void __launch_bounds__(256) k_push_general(PushLaunchT<T> L) {
       }
     } else {
       for (long long q = gtid; q < total; q += gstride) {
-        long long k = seg_entry(s_pre, L.qgrid, L.qseg, (int)q);
+        long long k = entry(q);
         long long p = L.queue[k];
         push_general<T, kB>(G, p, L.p.cell[p], L.p.a[p], L.p.b[p], L.p.vr[p], L.p.vt[p],
                             L.p.vz[p], L.p.w[p], L.q_da[k], L.q_db[k], tl);

@@ -69,6 +69,18 @@ __device__ __forceinline__ long long seg_entry(const int *s_pre, int nblk, long 
   return (long long)lo * seg + (q - s_pre[lo]);
 }
 
+// the same for entries appended from the back of each segment (the r-th entry
+// of segment b sits at b*seg + seg - 1 - r)
+__device__ __forceinline__ long long seg_entry_back(const int *s_pre, int nblk, long long seg, int q) {
+  int lo = 0, hi = nblk;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (s_pre[mid] <= q) lo = mid;
+    else hi = mid;
+  }
+  return (long long)lo * seg + seg - 1 - (q - s_pre[lo]);
+}
+
 // blocks of 256 threads of a persistent kernel: resident blocks per SM x SMs
 // (at most kMaxFastBlocks)
 template <typename K>
