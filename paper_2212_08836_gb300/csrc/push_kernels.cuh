@@ -144,7 +144,7 @@ __device__ __forceinline__ void load_state(const PartsT<T> &P, long long p, long
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 1) k_push_fast(PushLaunchT<T> L) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_push_fast(PushLaunchT<T> L) {
   const int lane = threadIdx.x & 31;
   const int nz = L.g.nz, nz1 = nz + 1, ncell = L.g.nr * nz;
   const T zero = (T)0, one = (T)1, h = (T)0.5, q = (T)0.25;
