@@ -106,6 +106,24 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def replica_seed(seed, rank):
+    """Seed of the replica on `rank`: N > 1 runs N independent discharges
+    (replicas only: the path needs no exchange between GPUs)."""
+    return seed + rank
+
+
+def reduce_replicas(D, t_ms, pushes, device):
+    """Whole-job figures of the replicas: the slowest rank's time and the pushes
+    of all ranks (value = all pushes / that time)."""
+    import torch
+
+    tt = torch.tensor([float(t_ms)], dtype=torch.float64, device=device)
+    D.all_reduce(tt, op=D.ReduceOp.MAX)
+    nn = torch.tensor([float(pushes)], dtype=torch.float64, device=device)
+    D.all_reduce(nn)
+    return tt.item(), nn.item()
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -356,18 +374,12 @@ def run_ours(args):
     sm_max = pk.get("sm_max_mhz", 2070.0)
 
     def maxsum(t, n):
-        if not dist:
-            return t, n
-        tt = torch.tensor([t], dtype=torch.float64, device=dev)
-        D.all_reduce(tt, op=D.ReduceOp.MAX)
-        nn = torch.tensor([n], dtype=torch.float64, device=dev)
-        D.all_reduce(nn)
-        return tt.item(), nn.item()
+        return reduce_replicas(D, t, n, dev) if dist else (t, n)
 
     forms = args.forms.split(",")
     if "plain" not in forms:
         # profiling aid: only the mixed form (no headline line is printed)
-        cfgm = P.large_reactor(seed=1 + rank, precision=P.PIC_MIXED)
+        cfgm = P.large_reactor(seed=replica_seed(1, rank), precision=P.PIC_MIXED)
         if args.np:
             cfgm["np_init"] = args.np
         rm = measure(P, torch, dev, cfgm, args, dist, D, False, False, local)
@@ -376,7 +388,7 @@ def run_ours(args):
                               "push_ms_per_launch": rm["push_ms"] / max(rm["push_launches"], 1)}))
         return 0
     # ---- plain FP64 method on the 256 x 384 reactor (the headline workload)
-    cfg = P.large_reactor(seed=1 + rank)
+    cfg = P.large_reactor(seed=replica_seed(1, rank))
     if args.np:
         cfg["np_init"] = args.np
     r = measure(P, torch, dev, cfg, args, dist, D, not args.no_e2e, True, local)
@@ -419,7 +431,7 @@ def run_ours(args):
 
     # ---- mixed-precision form on the same reactor (FP32 push/deposit)
     if "mixed" in forms:
-        cfgm = P.large_reactor(seed=1 + rank, precision=P.PIC_MIXED)
+        cfgm = P.large_reactor(seed=replica_seed(1, rank), precision=P.PIC_MIXED)
         if args.np:
             cfgm["np_init"] = args.np
         rm = measure(P, torch, dev, cfgm, args, dist, D, False, False, local)
@@ -446,7 +458,7 @@ def run_ours(args):
         wall["mixed"] = tm / args.steps * 1e-3 * steps_per_cycle
     # ---- electrostatic field model (Eq. 8) on the same reactor, mixed form
     if "es" in forms:
-        cfge = P.large_reactor(seed=1 + rank, precision=P.PIC_MIXED, field_model=P.PIC_FIELD_ES)
+        cfge = P.large_reactor(seed=replica_seed(1, rank), precision=P.PIC_MIXED, field_model=P.PIC_FIELD_ES)
         if args.np:
             cfge["np_init"] = args.np
         re_ = measure(P, torch, dev, cfge, args, dist, D, False, False, local)
@@ -459,7 +471,7 @@ def run_ours(args):
     # ---- learned Picard start (mixed form): trained on the discharge's own fields
     if "guess" in forms:
         from paper_2212_08836_gb300 import guess as GS
-        cfgg = P.large_reactor(seed=1 + rank, precision=P.PIC_MIXED, capacity_factor=2.5)
+        cfgg = P.large_reactor(seed=replica_seed(1, rank), precision=P.PIC_MIXED, capacity_factor=2.5)
         if args.np:
             cfgg["np_init"] = args.np
         pic = P.Pic(cfgg, device=dev)
