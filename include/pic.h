@@ -299,15 +299,18 @@ int pic_get_view(pic_ctx *ctx, pic_view *out);
  * at step n to a file: both species (counts, next ids, every particle field
  * in the context's precision), E^n, H^n, the wall tallies, the step index,
  * the blocking-capacitor state, the generator waveform set by pic_set_drive,
- * the carried node charge of the electrostatic model and the last Picard
- * contraction (the speculation hint), behind a header with the mesh and
- * model.  pic_load restores them into a context created with the same nr,
- * nz, precision and field model; the learned-start history restarts (the
+ * the carried node charge of the electrostatic model, the conducting ring's
+ * conduction tally and the last Picard contraction (the speculation hint),
+ * behind a header with the mesh and model.  pic_load restores them into a
+ * context created with the same nr, nz, axis_cells, ring_cells, precision and
+ * field model, with or without sigma_ring as the saving one, and with the
+ * blocking capacitor on or off as there; the learned-start history restarts (the
  * first steps use the plain start).  A run resumed from a checkpoint takes
  * the same steps as the uninterrupted one (the collision random numbers
  * depend only on particle ids and the step index).  Both synchronise.
- * Errors: PIC_E_IO (file), PIC_E_STATE (mesh, model or precision differ, or
- * counts beyond the capacity), PIC_E_CUDA. */
+ * Errors: PIC_E_IO (file, or a checkpoint of another format version),
+ * PIC_E_STATE (mesh, ring, model or precision differ, or counts beyond the
+ * capacity), PIC_E_CUDA. */
 int pic_save(pic_ctx *ctx, const char *path);
 int pic_load(pic_ctx *ctx, const char *path);
 

@@ -1688,6 +1688,7 @@ struct CkptHeader {
   uint32_t next_id[2];
   double circ[4], rho_prev;
   double hamp[64], hfreq[64], hph[64];
+  int32_t ring_cells, conducting;  // the ring's extent and whether it carries a conduction tally
 };
 const char kCkptMagic[8] = {'P', 'I', 'C', 'C', 'K', 'P', 'T', '1'};
 
@@ -1722,7 +1723,7 @@ int pic_save(pic_ctx *x, const char *path) {
   CkptHeader H;
   memset(&H, 0, sizeof(H));
   memcpy(H.magic, kCkptMagic, 8);
-  H.version = 1;
+  H.version = 2;
   H.nr = x->g.nr;
   H.nz = x->g.nz;
   H.precision = x->cfg.precision;
@@ -1732,6 +1733,8 @@ int pic_save(pic_ctx *x, const char *path) {
   H.qn_valid = x->qn_valid;
   H.nharm = x->nharm;
   H.xa = x->g.xa;
+  H.ring_cells = x->g.nd;
+  H.conducting = x->g.sgd > 0.0 ? 1 : 0;
   H.n[0] = x->n[0];
   H.n[1] = x->n[1];
   H.step = x->step;
@@ -1768,11 +1771,12 @@ int pic_load(pic_ctx *x, const char *path) {
   if (!fp) return PIC_E_IO;
   CkptHeader H;
   int rc = fread(&H, sizeof(H), 1, fp) == 1 ? PIC_OK : PIC_E_IO;
-  if (!rc && (memcmp(H.magic, kCkptMagic, 8) != 0 || H.version != 1 || H.nharm < 0 ||
+  if (!rc && (memcmp(H.magic, kCkptMagic, 8) != 0 || H.version != 2 || H.nharm < 0 ||
               H.nharm > 64))
     rc = PIC_E_IO;
   if (!rc && (H.nr != x->g.nr || H.nz != x->g.nz || H.precision != x->cfg.precision ||
               H.field_model != x->cfg.field_model || H.xa != x->g.xa ||
+              H.ring_cells != x->g.nd || H.conducting != (x->g.sgd > 0.0 ? 1 : 0) ||
               H.real_size != (x->mixed ? 4 : 8) || H.n[0] < 0 || H.n[1] < 0 ||
               H.n[0] > x->cap[0] || H.n[1] > x->cap[1] || H.step < 0 ||
               (H.circ_on != 0) != (x->circ_on != 0)))

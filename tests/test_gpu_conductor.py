@@ -111,6 +111,12 @@ def test_checkpoint_keeps_the_conduction_tally(tmp_path):
     # continued runs agree up to the order of the deposit's atomic additions
     qa, qb = a.view()["qcond"].cpu().numpy(), b.view()["qcond"].cpu().numpy()
     assert np.max(np.abs(qb - qa)) <= 1e-12 * np.max(np.abs(qa))
+    # a context without the conducting ring, or with another ring, refuses it
+    for other in (dict(sigma_ring=0.0), dict(ring_cells=ND + 1)):
+        c = M.Pic(dict(cfg, **other), device=DEV)
+        with pytest.raises(M.PicError) as e:
+            c.load(path)
+        assert e.value.code == M.PIC_E_STATE
 
 
 @pytest.mark.parametrize("kw", [dict(sigma_ring=1.0),                                   # no ring
