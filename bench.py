@@ -303,6 +303,66 @@ def ensemble_configs(P, rank):
     return cfgs
 
 
+def run_developed_form(P, torch, dev, args, rank, cycles=5):
+    """FP64 push rate on a developed discharge: the 256 x 384 reactor after
+    `cycles` RF cycles (sheaths, sheath-accelerated electrons, more face
+    crossings than the Maxwellian start), developed with the mixed form and
+    handed to the FP64 form through host arrays; then args.steps timed steps."""
+    from paper_2212_08836_gb300.dispersion import advance
+
+    seed = replica_seed(1, rank)
+    cfgm = P.large_reactor(seed=seed, precision=P.PIC_MIXED, capacity_factor=3.0)
+    if args.np:
+        cfgm["np_init"] = args.np
+    n_dev = int(round(cycles / (cfgm["freq"] * cfgm["dt"])))
+    pic = P.Pic(cfgm, device=dev)
+    pic.load_particles()
+    relaxed = []
+    t0 = time.perf_counter()
+    try:
+        for k in range(n_dev):
+            advance(pic, cfgm["picard_tol"], relaxed, k)
+    except RuntimeError as e:
+        pic.close()
+        return {"failed": str(e)}
+    t_develop = time.perf_counter() - t0
+    species = [pic.get_state(s) for s in range(2)]
+    er, ez, h = pic.fields()
+    v = pic.view()
+    step, next_ids = v["step"], list(v["next_id"])
+    pic.close()
+    cfg = P.large_reactor(seed=seed, capacity_factor=3.0)
+    if args.np:
+        cfg["np_init"] = args.np
+    p64 = P.Pic(cfg, device=dev)
+    p64.set_state(species, er, ez, h, next_ids=next_ids, step=step)
+    for _ in range(args.warmup):
+        p64.step(1, check=False)
+    stream = p64.stream
+    torch.cuda.synchronize(dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    pushes, iters, subs, rcs = 0, [], 0, []
+    for _ in range(args.steps):
+        rc, st = p64.step(1, check=False)
+        rcs.append(rc)
+        pushes += st["pushes"]
+        iters.append(st["picard_iters"])
+        subs += st["substeps"]
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    t_ms = ev0.elapsed_time(ev1)
+    n = st["n"]
+    p64.close()
+    return {"workload": "256x384 reactor after %d RF cycles (%d steps of the mixed form, %.1f s), "
+                        "then the FP64 form" % (cycles, n_dev, t_develop),
+            "value": pushes / (t_ms * 1e-3), "unit": UNIT, "ms_per_step": t_ms / args.steps,
+            "picard_iters": iters, "n": n, "step_status": rcs,
+            "accepted_substeps_per_particle_commit": subs / max(args.steps * (n[0] + n[1]), 1),
+            "develop_steps_relaxed": len(relaxed)}
+
+
 def run_ensemble_form(P, torch, dev, args, rank):
     cfgs = ensemble_configs(P, rank)
     mem = []
@@ -498,6 +558,10 @@ def run_ours(args):
         net.close()
     line["wall_s_per_rf_cycle"] = wall
 
+    # ---- FP64 form on a developed discharge (5 RF cycles)
+    if "developed" in forms:
+        line["developed_state"] = run_developed_form(P, torch, dev, args, rank)
+
     # ---- batched ensemble of 16 uneven discharges (mixed form) vs the same
     # discharges stepped one after another
     if "ensemble" in forms:
@@ -526,11 +590,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--np", type=int, default=0, help="macro-particles per species (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--forms", default="plain,mixed,es,guess,ensemble",
+    ap.add_argument("--forms", default="plain,mixed,es,guess,developed,ensemble",
                     help="comma list of plain (FP64), mixed (FP32 push), es (electrostatic "
                          "model), guess (mixed form "
-                         "with the learned Picard start) and ensemble (16 uneven discharges) "
-                         "to time")
+                         "with the learned Picard start), developed (the FP64 form after 5 RF "
+                         "cycles) and ensemble (16 uneven discharges) to time")
     ap.add_argument("--guess-warmup", type=int, default=400)
     ap.add_argument("--guess-samples", type=int, default=600)
     ap.add_argument("--guess-epochs", type=int, default=1500)
