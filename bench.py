@@ -232,45 +232,25 @@ def measure(P, torch, dev, cfg, args, dist, D, do_e2e, sample_clocks, local):
     pic.profile(False)
     r["e2e_ms"] = None
     if do_e2e:
-        v = pic.view()
-        host = []
-        for s in range(2):
-            host.append({k: torch.empty_like(v["species"][s][k], device="cpu").pin_memory()
-                         for k in P.FIELDS})
-        hf = {k: torch.empty_like(v[k], device="cpu").pin_memory() for k in ("er", "ez", "h")}
-        for s in range(2):
-            for k in P.FIELDS:
-                host[s][k].copy_(v["species"][s][k])
-        for k in hf:
-            hf[k].copy_(v[k])
+        # the whole state lives in pinned host memory between steps: every
+        # step uploads it through the C ABI (pic_state_upload), steps, and
+        # reads the new state back (pic_state_download)
+        hs = pic.host_state(pinned=True)
+        pic.state_download(hs)
+        rs = pic.view()["species"][0]["a"].element_size()
         barrier()
         e2e_pushes = h2d = d2h = 0
         ev2 = torch.cuda.Event(enable_timing=True)
         ev3 = torch.cuda.Event(enable_timing=True)
+        nf = sum(hs[k].numel() * 8 for k in ("er", "ez", "h"))
         ev2.record(stream)
         for _ in range(args.steps):
-            v = pic.view()
-            with torch.cuda.stream(stream):
-                for s in range(2):
-                    n = v["n"][s]
-                    for k in P.FIELDS:
-                        v["species"][s][k][:n].copy_(host[s][k][:n], non_blocking=True)
-                        h2d += host[s][k][:n].numel() * host[s][k].element_size()
-                for k in hf:
-                    v[k].copy_(hf[k], non_blocking=True)
-                    h2d += hf[k].numel() * hf[k].element_size()
+            h2d += sum(hs["n"]) * (8 + 6 * rs) + nf
+            pic.state_upload(hs)
             _, st = pic.step(1)
             e2e_pushes += st["pushes"]
-            v = pic.view()
-            with torch.cuda.stream(stream):
-                for s in range(2):
-                    n = v["n"][s]
-                    for k in P.FIELDS:
-                        host[s][k][:n].copy_(v["species"][s][k][:n], non_blocking=True)
-                        d2h += host[s][k][:n].numel() * host[s][k].element_size()
-                for k in hf:
-                    hf[k].copy_(v[k], non_blocking=True)
-                    d2h += hf[k].numel() * hf[k].element_size()
+            pic.state_download(hs)
+            d2h += sum(hs["n"]) * (8 + 6 * rs) + nf
         ev3.record(stream)
         barrier()
         r["e2e_ms"] = ev2.elapsed_time(ev3)

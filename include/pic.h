@@ -314,6 +314,39 @@ int pic_get_view(pic_ctx *ctx, pic_view *out);
 int pic_save(pic_ctx *ctx, const char *path);
 int pic_load(pic_ctx *ctx, const char *path);
 
+/* The state of the method in caller-owned HOST memory: per species a
+ * structure of arrays in the layout of pic_view (a..w in the context's
+ * precision, pic_view.real_size bytes each; cell int32; id uint32), the
+ * counts, next ids and step index, and optionally E^n, H^n in the Yee layouts
+ * of pic_view.  Pinned host memory (cudaHostAlloc / cudaHostRegister) moves at
+ * the host link's speed; pageable memory works, slower. */
+typedef struct pic_host_state {
+  long long n[2];             /* macro-particles per species (download: capacity of the arrays in,
+                                 count out) */
+  uint32_t next_id[2];
+  long long step;             /* index n of the next step */
+  int32_t *cell[2];
+  void *a[2], *b[2], *vr[2], *vt[2], *vz[2], *w[2];
+  uint32_t *id[2];
+  double *er, *ez, *h;        /* nullable: fields not copied */
+} pic_host_state;
+
+/* Host -> device: copies the species arrays (and the fields given) into the
+ * context and sets counts, next ids and step index as pic_set_counts does.
+ * One cudaMemcpyAsync per array on the context's stream, so it returns before
+ * the copies finish: the host memory must stay valid until the stream reaches
+ * them (any later synchronising call, e.g. pic_state_download).
+ * Errors: PIC_E_CONFIG (null ctx or state, a null array with n > 0),
+ * PIC_E_STATE (n beyond capacity, negative counts or step), PIC_E_CUDA. */
+int pic_state_upload(pic_ctx *ctx, const pic_host_state *in);
+
+/* Device -> host: writes the counts, next ids and step index into *out and
+ * copies the species arrays (and the fields where out->er/ez/h are given).
+ * On entry out->n[s] is the capacity of the host arrays of species s.
+ * Synchronises the stream.  Errors: PIC_E_CONFIG, PIC_E_STATE (host arrays
+ * smaller than the counts; nothing is copied), PIC_E_CUDA. */
+int pic_state_download(pic_ctx *ctx, pic_host_state *out);
+
 /* Set particle counts / next ids / step index after the caller wrote state
  * through pic_get_view.  Errors: PIC_E_STATE (count beyond capacity). */
 int pic_set_counts(pic_ctx *ctx, long long ne, long long ni, uint32_t next_id_e,

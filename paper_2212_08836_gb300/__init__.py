@@ -68,6 +68,12 @@ class CnnConfig(C.Structure):
                 ("seed", C.c_ulonglong)]
 
 
+class HostState(C.Structure):
+    _fields_ = [("n", _LL * 2), ("next_id", C.c_uint32 * 2), ("step", _LL),
+                ("cell", _P * 2), ("a", _P * 2), ("b", _P * 2), ("vr", _P * 2), ("vt", _P * 2),
+                ("vz", _P * 2), ("w", _P * 2), ("id", _P * 2), ("er", _P), ("ez", _P), ("h", _P)]
+
+
 class View(C.Structure):
     _fields_ = [("cell", _P * 2), ("a", _P * 2), ("b", _P * 2), ("vr", _P * 2), ("vt", _P * 2),
                 ("vz", _P * 2), ("w", _P * 2), ("id", _P * 2), ("n", _LL * 2), ("cap", _LL * 2),
@@ -104,6 +110,8 @@ def _load_lib():
     L.pic_mcc_constants.argtypes = [_P, _P, _P, _P, _P]
     L.pic_sort_cells_noalloc.argtypes = [_I, _I, _LL] + [_P] * 16 + [_P, _P]
     L.pic_check_dmul.argtypes = [_P, _P, _P, _LL, _P]
+    L.pic_state_upload.argtypes = [_P, C.POINTER(HostState)]
+    L.pic_state_download.argtypes = [_P, C.POINTER(HostState)]
     L.pic_profile.argtypes = [_P, _I]
     L.pic_profile_read.argtypes = [_P, _P, _P]
     L.pic_cnn_workspace_size.argtypes = [C.POINTER(CnnConfig)]
@@ -416,6 +424,53 @@ class Pic:
         self.torch.cuda.synchronize(self.device)
         _check(lib().pic_set_counts(self._h, ns[0], ns[1], next_ids[0], next_ids[1], step),
                "pic_set_counts")
+
+    def host_state(self, pinned=True):
+        """Host buffers for the whole state (capacity-sized species arrays in
+        the context's layout, pinned by default) for state_upload /
+        state_download: {"species": [dict of FIELDS tensors] * 2, "er", "ez",
+        "h", "n", "next_id", "step"}."""
+        t = self.torch
+        v = self.view()
+        hs = {"species": [{k: t.empty_like(v["species"][s][k], device="cpu").pin_memory()
+                           if pinned else t.empty_like(v["species"][s][k], device="cpu")
+                           for k in FIELDS} for s in range(2)],
+              "n": list(v["cap"]), "next_id": [0, 0], "step": 0}
+        for k in ("er", "ez", "h"):
+            hs[k] = t.empty_like(v[k], device="cpu").pin_memory() if pinned else \
+                t.empty_like(v[k], device="cpu")
+        return hs
+
+    def _host_struct(self, hs):
+        H = HostState()
+        for s in range(2):
+            H.n[s] = int(hs["n"][s])
+            H.next_id[s] = int(hs["next_id"][s])
+            sp = hs["species"][s]
+            for k in FIELDS:
+                getattr(H, k)[s] = sp[k].data_ptr()
+        H.step = int(hs["step"])
+        for k in ("er", "ez", "h"):
+            setattr(H, k, hs[k].data_ptr() if hs.get(k) is not None else None)
+        return H
+
+    def state_upload(self, hs):
+        """Host -> device through pic_state_upload (asynchronous on the
+        context's stream): the first hs["n"][s] particles of each species, the
+        fields given, counts, next ids and step."""
+        self._hs_keep = hs  # the host memory stays referenced while copies may run
+        _check(lib().pic_state_upload(self._h, C.byref(self._host_struct(hs))), "pic_state_upload")
+
+    def state_download(self, hs):
+        """Device -> host through pic_state_download (synchronising): fills the
+        buffers of hs and its counts, next ids and step."""
+        hs["n"] = [hs["species"][s]["cell"].numel() for s in range(2)]
+        H = self._host_struct(hs)
+        _check(lib().pic_state_download(self._h, C.byref(H)), "pic_state_download")
+        hs["n"] = [H.n[0], H.n[1]]
+        hs["next_id"] = [H.next_id[0], H.next_id[1]]
+        hs["step"] = H.step
+        return hs
 
     def get_state(self, s):
         v = self.view()

@@ -1814,6 +1814,81 @@ int pic_load(pic_ctx *x, const char *path) {
   return PIC_OK;
 }
 
+int pic_state_upload(pic_ctx *x, const pic_host_state *in) {
+  if (!x || !in) return PIC_E_CONFIG;
+  for (int s = 0; s < 2; ++s) {
+    if (in->n[s] < 0 || in->n[s] > x->cap[s]) return PIC_E_STATE;
+    if (in->n[s] > 0 && (!in->cell[s] || !in->a[s] || !in->b[s] || !in->vr[s] || !in->vt[s] ||
+                         !in->vz[s] || !in->w[s] || !in->id[s]))
+      return PIC_E_CONFIG;
+  }
+  if (in->step < 0) return PIC_E_STATE;
+  const size_t rs = x->mixed ? 4 : 8;
+  const int nr = x->g.nr, nz = x->g.nz;
+  cudaStream_t st = x->s;
+  cudaError_t e = cudaSuccess;
+  auto up = [&](void *dst, const void *src, size_t b) {
+    if (e == cudaSuccess && b) e = cudaMemcpyAsync(dst, src, b, cudaMemcpyHostToDevice, st);
+  };
+  for (int s = 0; s < 2; ++s) {
+    Parts &P = cur(x, s);
+    const size_t n = (size_t)in->n[s];
+    up(P.cell, in->cell[s], n * 4);
+    up(P.a, in->a[s], n * rs);
+    up(P.b, in->b[s], n * rs);
+    up(P.vr, in->vr[s], n * rs);
+    up(P.vt, in->vt[s], n * rs);
+    up(P.vz, in->vz[s], n * rs);
+    up(P.w, in->w[s], n * rs);
+    up(P.id, in->id[s], n * 4);
+  }
+  if (in->er) up(x->er, in->er, (size_t)nr * (nz + 1) * 8);
+  if (in->ez) up(x->ez, in->ez, (size_t)(nr + 1) * nz * 8);
+  if (in->h) up(x->h, in->h, (size_t)nr * nz * 8);
+  if (e != cudaSuccess) return PIC_E_CUDA;
+  return pic_set_counts(x, in->n[0], in->n[1], in->next_id[0], in->next_id[1], in->step);
+}
+
+int pic_state_download(pic_ctx *x, pic_host_state *out) {
+  if (!x || !out) return PIC_E_CONFIG;
+  for (int s = 0; s < 2; ++s) {
+    if (out->n[s] < x->n[s]) return PIC_E_STATE;
+    if (x->n[s] > 0 && (!out->cell[s] || !out->a[s] || !out->b[s] || !out->vr[s] ||
+                        !out->vt[s] || !out->vz[s] || !out->w[s] || !out->id[s]))
+      return PIC_E_CONFIG;
+  }
+  const size_t rs = x->mixed ? 4 : 8;
+  const int nr = x->g.nr, nz = x->g.nz;
+  cudaStream_t st = x->s;
+  cudaError_t e = cudaSuccess;
+  auto dn = [&](void *dst, const void *src, size_t b) {
+    if (e == cudaSuccess && b) e = cudaMemcpyAsync(dst, src, b, cudaMemcpyDeviceToHost, st);
+  };
+  for (int s = 0; s < 2; ++s) {
+    Parts &P = cur(x, s);
+    const size_t n = (size_t)x->n[s];
+    dn(out->cell[s], P.cell, n * 4);
+    dn(out->a[s], P.a, n * rs);
+    dn(out->b[s], P.b, n * rs);
+    dn(out->vr[s], P.vr, n * rs);
+    dn(out->vt[s], P.vt, n * rs);
+    dn(out->vz[s], P.vz, n * rs);
+    dn(out->w[s], P.w, n * rs);
+    dn(out->id[s], P.id, n * 4);
+  }
+  if (out->er) dn(out->er, x->er, (size_t)nr * (nz + 1) * 8);
+  if (out->ez) dn(out->ez, x->ez, (size_t)(nr + 1) * nz * 8);
+  if (out->h) dn(out->h, x->h, (size_t)nr * nz * 8);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return PIC_E_CUDA;
+  for (int s = 0; s < 2; ++s) {
+    out->n[s] = x->n[s];
+    out->next_id[s] = x->next_id[s];
+  }
+  out->step = x->step;
+  return PIC_OK;
+}
+
 int pic_set_counts(pic_ctx *x, long long ne, long long ni, uint32_t nide, uint32_t nidi,
                    long long step) {
   if (!x) return PIC_E_CONFIG;

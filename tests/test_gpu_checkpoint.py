@@ -78,3 +78,37 @@ def test_refused_checkpoints(tmp_path):
     with pytest.raises(M.PicError) as e:
         a.load(path)
     assert e.value.code == M.PIC_E_IO
+
+
+def test_host_state_round_trip():
+    """pic_state_download / pic_state_upload move the whole state through
+    host memory: a context stepped after a round trip matches one stepped
+    without it, and an undersized host buffer is refused."""
+    M = P()
+    cfg = M.small_reactor(np_init=6000, mcc_on=1)
+    a = M.Pic(cfg, device=DEV)
+    a.load_particles()
+    for _ in range(2):
+        a.step(1)
+    hs = a.host_state(pinned=True)
+    a.state_download(hs)
+    assert hs["n"] == a.view()["n"] and hs["step"] == a.view()["step"]
+    b = M.Pic(cfg, device=DEV)
+    b.state_upload(hs)
+    for _ in range(2):
+        a.step(1)
+        b.step(1)
+    for s in range(2):
+        # the same particles; the order inside a cell is not fixed by the sort
+        ga, gb = a.get_state(s), b.get_state(s)
+        oa, ob = np.argsort(ga["id"]), np.argsort(gb["id"])
+        np.testing.assert_array_equal(ga["id"][oa], gb["id"][ob])
+        np.testing.assert_array_equal(ga["cell"][oa], gb["cell"][ob])
+        for k in ("a", "b", "vr", "vt", "vz"):
+            np.testing.assert_allclose(gb[k][ob], ga[k][oa], rtol=1e-9,
+                                       atol=1e-9 * np.max(np.abs(ga[k])))
+    small = a.host_state(pinned=False)
+    small["species"][0] = {k: v[:10] for k, v in small["species"][0].items()}
+    with pytest.raises(M.PicError) as e:
+        a.state_download(small)
+    assert e.value.code == M.PIC_E_STATE
