@@ -124,6 +124,32 @@ def reduce_replicas(D, t_ms, pushes, device):
     return tt.item(), nn.item()
 
 
+def bind_near_gpu(torch, dev):
+    """Run this process on the host cores next to the GPU (its PCI device's
+    local_cpulist), so that pinned host buffers come from the GPU's NUMA node
+    and host transfers do not cross the link between host sockets.  Returns
+    the core list, or None where the platform does not expose it."""
+    try:
+        p = torch.cuda.get_device_properties(dev)
+        bus = "%04x:%02x:%02x.0" % (getattr(p, "pci_domain_id"), getattr(p, "pci_bus_id"),
+                                    getattr(p, "pci_device_id"))
+        with open("/sys/bus/pci/devices/%s/local_cpulist" % bus) as f:
+            spec = f.read().strip()
+        cpus = set()
+        for part in spec.split(","):
+            if "-" in part:
+                lo, hi = part.split("-")
+                cpus.update(range(int(lo), int(hi) + 1))
+            elif part:
+                cpus.add(int(part))
+        if not cpus:
+            return None
+        os.sched_setaffinity(0, cpus)
+        return spec
+    except (AttributeError, OSError, ValueError):
+        return None
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -407,6 +433,7 @@ def run_ours(args):
         D.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    host_cpus = bind_near_gpu(torch, dev)
     import paper_2212_08836_gb300 as P
 
     P.lib()
@@ -464,7 +491,7 @@ def run_ours(args):
             "roofline": roof}
     if r["e2e_ms"] is not None:
         te, ne = maxsum(r["e2e_ms"], r["e2e_pushes"])
-        line["e2e"] = {"value": ne / (te * 1e-3), "unit": UNIT,
+        line["e2e"] = {"value": ne / (te * 1e-3), "unit": UNIT, "host_cpus": host_cpus,
                        "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]}
     steps_per_cycle = 1.0 / (cfg["dt"] * cfg["freq"])
     wall = {"plain_fp64": t_max / args.steps * 1e-3 * steps_per_cycle}
