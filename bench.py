@@ -256,6 +256,10 @@ def measure(P, torch, dev, cfg, args, dist, D, do_e2e, sample_clocks, local):
     r["t_ms"] = ev0.elapsed_time(ev1)
     r["push_ms"], r["push_launches"] = pic.profile_read()
     pic.profile(False)
+    # sub-step histogram of one more step, outside the timed region
+    pic.substep_histogram(1)
+    pic.step(1, check=False)
+    r["substep_hist"] = [int(v) for v in pic.substep_histogram(0)]
     r["e2e_ms"] = None
     if do_e2e:
         # the whole state lives in pinned host memory between steps: every
@@ -360,12 +364,16 @@ def run_developed_form(P, torch, dev, args, rank, cycles=5):
     torch.cuda.synchronize(dev)
     t_ms = ev0.elapsed_time(ev1)
     n = st["n"]
+    p64.substep_histogram(1)
+    p64.step(1, check=False)
+    hist = [int(v) for v in p64.substep_histogram(0)]
     p64.close()
     return {"workload": "256x384 reactor after %d RF cycles (%d steps of the mixed form, %.1f s), "
                         "then the FP64 form" % (cycles, n_dev, t_develop),
             "value": pushes / (t_ms * 1e-3), "unit": UNIT, "ms_per_step": t_ms / args.steps,
             "picard_iters": iters, "n": n, "step_status": rcs,
             "accepted_substeps_per_particle_commit": subs / max(args.steps * (n[0] + n[1]), 1),
+            "substep_histogram": hist,
             "develop_steps_relaxed": len(relaxed)}
 
 
@@ -488,7 +496,10 @@ def run_ours(args):
                        "substep_cap_hits": r["substep_cap"]},
             "clocks": r.get("clocks"),
             "gpu_launches": r["launches"],
-            "roofline": roof}
+            "roofline": roof,
+            "substep_histogram": {"bins": r["substep_hist"],
+                                  "note": "particles with k+1 accepted sub-steps in bin k "
+                                          "(bin 15: 16 or more), one step after the timed region"}}
     if r["e2e_ms"] is not None:
         te, ne = maxsum(r["e2e_ms"], r["e2e_pushes"])
         line["e2e"] = {"value": ne / (te * 1e-3), "unit": UNIT, "host_cpus": host_cpus,

@@ -314,6 +314,16 @@ int pic_get_view(pic_ctx *ctx, pic_view *out);
 int pic_save(pic_ctx *ctx, const char *path);
 int pic_load(pic_ctx *ctx, const char *path);
 
+/* Histogram of accepted sub-steps per particle over the state-writing push
+ * passes (the commit or speculative final pass of each step): bin k (k < 15)
+ * counts the particles that took k+1 sub-steps (an in-cell push is one; a
+ * particle absorbed before its first sub-step counts in bin 0), bin 15 those
+ * that took 16 or more.  enable = 1: clear the bins and count from the next
+ * step on; 0: stop counting; -1: leave as is.  counts (nullable, host, 16
+ * values): the bins as they stand before the call acts on enable (synchronises
+ * the stream).  Off after pic_init.  Errors: PIC_E_CONFIG, PIC_E_CUDA. */
+int pic_substep_histogram(pic_ctx *ctx, int enable, unsigned long long *counts);
+
 /* The state of the method in caller-owned HOST memory: per species a
  * structure of arrays in the layout of pic_view (a..w in the context's
  * precision, pic_view.real_size bytes each; cell int32; id uint32), the

@@ -110,6 +110,7 @@ def _load_lib():
     L.pic_mcc_constants.argtypes = [_P, _P, _P, _P, _P]
     L.pic_sort_cells_noalloc.argtypes = [_I, _I, _LL] + [_P] * 16 + [_P, _P]
     L.pic_check_dmul.argtypes = [_P, _P, _P, _LL, _P]
+    L.pic_substep_histogram.argtypes = [_P, _I, _P]
     L.pic_state_upload.argtypes = [_P, C.POINTER(HostState)]
     L.pic_state_download.argtypes = [_P, C.POINTER(HostState)]
     L.pic_profile.argtypes = [_P, _I]
@@ -424,6 +425,14 @@ class Pic:
         self.torch.cuda.synchronize(self.device)
         _check(lib().pic_set_counts(self._h, ns[0], ns[1], next_ids[0], next_ids[1], step),
                "pic_set_counts")
+
+    def substep_histogram(self, enable=-1):
+        """The 16 bins of accepted sub-steps per particle (pic_substep_histogram)
+        as they stand, then enable = 1 clears them and counts from the next
+        step, 0 stops counting, -1 leaves the counting as is."""
+        h = np.zeros(16, dtype=np.uint64)
+        _check(lib().pic_substep_histogram(self._h, int(enable), h.ctypes.data), "pic_substep_histogram")
+        return h
 
     def host_state(self, pinned=True):
         """Host buffers for the whole state (capacity-sized species arrays in

@@ -88,6 +88,8 @@ struct pic_ctx {
   double *vdev;             // [0..1] V^n, V^{n+1}; [4..7] blocking-capacitor state (Circuit)
   double *hu;               // EM unit response of the circuit (nr x nz)
   double *qc;               // charge moved by the conducting ring's current (nodes)
+  unsigned long long *hist; // sub-step histogram (16 bins) of the state-writing passes
+  int hist_on;
   double *rmap64;           // mapped mesh: radial scales of the first cells (RadialMapT)
   float *rmap32;
   int circ_on;
@@ -275,6 +277,7 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
   x->wall = (double *)K.take((size_t)2 * (2 * (nr + 1) + nz + 1) * 8);
   x->wall_spec = (double *)K.take((size_t)2 * (2 * (nr + 1) + nz + 1) * 8);
   x->qc = (double *)K.take((size_t)(nr + 1) * (nz + 1) * 8);
+  x->hist = (unsigned long long *)K.take(16 * 8);
   x->F.Q = (double *)K.take((size_t)nz * nz * 8);
   x->F.QT = (double *)K.take((size_t)nz * nz * 8);
   int n2 = 1;
@@ -425,6 +428,7 @@ void fill_push(pic_ctx *x, int s, double q, double m, const double *erh, const d
   L.wall_r = ws[2];
   L.counters = counters;
   L.ke_lost = kel;
+  L.hist = (write && x->hist_on) ? x->hist : nullptr;
 }
 
 template <typename T>
@@ -784,6 +788,7 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
   if (e == cudaSuccess) e = cudaMemsetAsync(x->h2, 0, nh * 8, x->s);
   if (e == cudaSuccess) e = cudaMemsetAsync(x->wall, 0, (size_t)2 * (2 * (nr + 1) + nz + 1) * 8, x->s);
   if (e == cudaSuccess) e = cudaMemsetAsync(x->qc, 0, (size_t)(nr + 1) * (nz + 1) * 8, x->s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(x->hist, 0, 16 * 8, x->s);
   if (e == cudaSuccess) e = cudaMemsetAsync(x->cnt, 0, sizeof(DevCounters), x->s);
   if (e == cudaSuccess) e = cudaHostAlloc((void **)&x->hn, 8 * kHnSlots, cudaHostAllocDefault);
   if (e == cudaSuccess) e = cudaStreamSynchronize(x->s);
@@ -1811,6 +1816,18 @@ int pic_load(pic_ctx *x, const char *path) {
   }
   x->hist_n = 1;
   x->sample_valid = 0;
+  return PIC_OK;
+}
+
+int pic_substep_histogram(pic_ctx *x, int enable, unsigned long long *counts) {
+  if (!x || enable < -1 || enable > 1) return PIC_E_CONFIG;
+  if (counts) {
+    if (cudaMemcpyAsync(counts, x->hist, 16 * 8, cudaMemcpyDeviceToHost, x->s) != cudaSuccess ||
+        cudaStreamSynchronize(x->s) != cudaSuccess)
+      return PIC_E_CUDA;
+  }
+  if (enable == 1 && cudaMemsetAsync(x->hist, 0, 16 * 8, x->s) != cudaSuccess) return PIC_E_CUDA;
+  if (enable >= 0) x->hist_on = enable;
   return PIC_OK;
 }
 

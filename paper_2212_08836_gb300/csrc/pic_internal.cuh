@@ -234,6 +234,7 @@ struct PushLaunchT {
   double *wall_z0, *wall_zl, *wall_r;
   unsigned long long *counters;
   double *ke_lost;
+  unsigned long long *hist;  // accepted sub-steps per particle, 16 bins (nullptr: off)
   // work queue of the general path (queue == nullptr: all particles).  Block b
   // of the fast kernel appends the particles whose whole-step trial leaves the
   // cell through a z-face only to entries [b*qseg, b*qseg + qblock[b]) and the

@@ -456,6 +456,7 @@ struct GenArgs {
   PartsT<T> p, dst;
   double *wall_z0, *wall_zl, *wall_r;
   double *ke_lost;
+  unsigned long long *hist;  // accepted sub-steps per particle, 16 bins (nullptr: off)
 };
 
 // radial face crossing on a mapped mesh: the normalised radial and azimuthal
@@ -491,6 +492,7 @@ __device__ void push_general(const GenArgs<T> &L, long long p, int c0, T a, T b,
   T tT = tau;
   int nsub = 0;
   int ic_prev = ic;
+  int nacc = 0;  // accepted sub-steps of this particle
   int absorbed = transition_gen<T>(nr, nz, ic, jc, a, b, ur, uz);
   rescale_radial<T>(L.rm, ic_prev, ic, ur, ut);
   while (tau > zero && !absorbed) {
@@ -615,12 +617,14 @@ __device__ void push_general(const GenArgs<T> &L, long long p, int c0, T a, T b,
     ur = nur; ut = nut; uz = nuz;
     tau = tau - step_t;
     Tl.sub++;
+    nacc++;
     ic_prev = ic;
     absorbed = transition_gen<T>(nr, nz, ic, jc, a, b, ur, uz);
     if (absorbed) break;
     rescale_radial<T>(L.rm, ic_prev, ic, ur, ut);
     tT = tau;
   }
+  if (L.hist) atomicAdd(&L.hist[nacc <= 1 ? 0 : (nacc < 16 ? nacc - 1 : 15)], 1ull);
   const T icr = L.rm.icrr(ic);
   T vr = ur * icr, vt = ut * icr, vz = uz * L.icz;
   if (absorbed) {

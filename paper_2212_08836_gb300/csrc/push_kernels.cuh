@@ -240,6 +240,10 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_push_fast(PushL
       L.dst.cell[p] = c0;  // not pushed (absorbed earlier): stays out of the store
     }
     warp_deposit<T>(key, ic, jc, v0, v1, v2, v3, lane, nz, L.ir, L.iz);
+    if (L.hist) {  // in-cell pushes: one sub-step (bin 0), one count per warp
+      const unsigned m = __ballot_sync(0xffffffffu, key >= 0 && !queued);
+      if (lane == 0 && m) atomicAdd(&L.hist[0], (unsigned long long)__popc(m));
+    }
     // queue the rest for the general path (warp-aggregated append to the
     // block's segment; the shared-memory counter keeps it off global atomics)
     // two kinds in the FP64 form only: there the general kernel is bound by its
@@ -272,7 +276,7 @@ __global__ void __launch_bounds__(256) k_push_general(PushLaunchT<T> L) {
   G.nr = L.g.nr; G.nz = L.g.nz; G.ar = L.ar; G.az = L.az;
   G.wt = L.wbt; G.icr = L.icr; G.icz = L.icz; G.cz = L.cz; G.rm = L.rm;
   G.q = L.q; G.m = L.m; G.qf = L.qf; G.ir = L.ir; G.iz = L.iz; G.write = L.write; G.p = L.p;
-  G.oop = L.oop; G.dst = L.dst;
+  G.oop = L.oop; G.dst = L.dst; G.hist = L.hist;
   G.wall_z0 = L.wall_z0; G.wall_zl = L.wall_zl; G.wall_r = L.wall_r; G.ke_lost = L.ke_lost;
   Tally tl = {0, 0, 0, 0, 0, 0};
   const long long gstride = (long long)gridDim.x * blockDim.x;

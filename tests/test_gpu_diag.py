@@ -54,3 +54,30 @@ def test_gauss_residual_stays_at_rounding_over_steps(precision):
         pic.step(1)
     r = np.max(np.abs(pic.gauss_residual().cpu().numpy()))
     assert r <= (1e-12 if precision == 0 else 1e-6) * q_scale, r
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_substep_histogram_counts_every_push(precision):
+    """Every particle of a state-writing pass lands in one bin, and the bins
+    weighted by their sub-step counts give the step's accepted sub-steps."""
+    M = P()
+    cfg = M.small_reactor(np_init=20000, mcc_on=1, precision=precision)
+    pic = M.Pic(cfg, device=DEV)
+    pic.load_particles()
+    pic.step(2)
+    assert pic.substep_histogram(1).sum() == 0  # off until enabled
+    tot_n = tot_sub = 0
+    for _ in range(3):
+        n = sum(pic.view()["n"])
+        rc, st = pic.step(1, check=False)
+        assert rc in (0, M.PIC_E_SUBSTEP)
+        tot_n += n
+        tot_sub += st["substeps"]
+    h = pic.substep_histogram(0)
+    assert int(h.sum()) == tot_n
+    w = int((np.arange(16, dtype=np.uint64) + 1) @ h)
+    # bin 0 also holds particles absorbed before a first sub-step, bin 15 16 or more
+    assert abs(w - tot_sub) <= 1e-3 * tot_sub + 64 * int(h[15])
+    assert h[0] > 0.5 * h.sum() and h[1] > 0
+    pic.step(1)
+    assert np.array_equal(pic.substep_histogram(-1), h)  # stopped counting
