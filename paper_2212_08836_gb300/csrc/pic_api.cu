@@ -598,7 +598,7 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
   F.eps = x->eps;
   F.mu = x->mu;
   F.L = cfg->L;
-  double dr = F.dr, dz = F.dz, hdt2 = 0.5 * cfg->dt * cfg->dt;
+  double dz = F.dz, hdt2 = 0.5 * cfg->dt * cfg->dt;
   std::vector<double> Q((size_t)nz * nz), QT((size_t)nz * nz), lam(nz);
   // FFT path when nz = 4^a 2^b 3^c is even (at most 4096); else the GEMM path
   F.fft = 0;
