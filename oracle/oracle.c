@@ -179,7 +179,7 @@ void oracle_load(int nr, int nz, double dr, double dz, int xa, int nd, double er
                  int64_t n, double te_ev, double ti_ev, double me, double mi, uint64_t seed,
                  int32_t *cell, double *a, double *b, double *vre, double *vte, double *vze,
                  double *vri, double *vti, double *vzi, double *w, uint32_t *id) {
-  og_grid g = {nr, nz, dr, dz, xa, nd, erd};
+  og_grid g = {nr, nz, dr, dz, xa, nd, erd, 0.0};  /* conductivity: not used here */
   const int np_r = nr - nd; /* particles live inside the ring */
   double vthe = sqrt(te_ev * O_QE / me);
   double vthi = sqrt(ti_ev * O_QE / mi);
@@ -859,7 +859,7 @@ double oracle_conduction_charge(void *p, const double *er0, const double *ez0, c
 double oracle_field_energy(int nr, int nz, double dr, double dz, int xa, int nd, double erd,
                            double eps, double mu,
                            const double *er, const double *ez, const double *h) {
-  og_grid g = {nr, nz, dr, dz, xa, nd, erd};
+  og_grid g = {nr, nz, dr, dz, xa, nd, erd, 0.0};  /* conductivity: not used here */
   double W = 0.0;
   for (int i = 0; i < nr; ++i)
     for (int j = 1; j < nz; ++j) {
@@ -884,7 +884,7 @@ void oracle_gauss_residual(int nr, int nz, double dr, double dz, int xa, int nd,
                            double eps,
                            const double *er,
                            const double *ez, const double *Q, double *G) {
-  og_grid g = {nr, nz, dr, dz, xa, nd, erd};
+  og_grid g = {nr, nz, dr, dz, xa, nd, erd, 0.0};  /* conductivity: not used here */
   for (int i = 0; i <= nr; ++i)
     for (int j = 0; j <= nz; ++j) G[i * (nz + 1) + j] = 0.0;
   for (int i = 0; i < nr; ++i)
