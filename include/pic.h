@@ -318,7 +318,8 @@ int pic_load(pic_ctx *ctx, const char *path);
  * passes (the commit or speculative final pass of each step): bin k (k < 15)
  * counts the particles that took k+1 sub-steps (an in-cell push is one; a
  * particle absorbed before its first sub-step counts in bin 0), bin 15 those
- * that took 16 or more.  enable = 1: clear the bins and count from the next
+ * that took 16 or more.  A speculative final pass counts only when the step
+ * adopts it.  enable = 1: clear the bins and count from the next
  * step on; 0: stop counting; -1: leave as is.  counts (nullable, host, 16
  * values): the bins as they stand before the call acts on enable (synchronises
  * the stream).  Off after pic_init.  Errors: PIC_E_CONFIG, PIC_E_CUDA. */

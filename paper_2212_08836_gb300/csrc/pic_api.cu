@@ -89,6 +89,7 @@ struct pic_ctx {
   double *hu;               // EM unit response of the circuit (nr x nz)
   double *qc;               // charge moved by the conducting ring's current (nodes)
   unsigned long long *hist; // sub-step histogram (16 bins) of the state-writing passes
+  unsigned long long *hist_spec;  // the same for a speculative final pass
   int hist_on;
   double *rmap64;           // mapped mesh: radial scales of the first cells (RadialMapT)
   float *rmap32;
@@ -278,6 +279,7 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
   x->wall_spec = (double *)K.take((size_t)2 * (2 * (nr + 1) + nz + 1) * 8);
   x->qc = (double *)K.take((size_t)(nr + 1) * (nz + 1) * 8);
   x->hist = (unsigned long long *)K.take(16 * 8);
+  x->hist_spec = (unsigned long long *)K.take(16 * 8);
   x->F.Q = (double *)K.take((size_t)nz * nz * 8);
   x->F.QT = (double *)K.take((size_t)nz * nz * 8);
   int n2 = 1;
@@ -465,6 +467,7 @@ int push_all(pic_ctx *x, const double *erh, const double *ezh, double *ir, doubl
       L.p = as32(cur(x, s));
       L.dst = oop ? as32(x->P[s][x->cur[s] ^ 1]) : L.p;
       L.oop = oop;
+      if (L.hist && oop) L.hist = x->hist_spec;  // counted once the pass is adopted
       L.ar = x->alpha.ar[s];
       L.az = x->alpha.az[s];
       set_queue(x, x->q_real, L);
@@ -476,6 +479,7 @@ int push_all(pic_ctx *x, const double *erh, const double *ezh, double *ir, doubl
       L.p = cur(x, s);
       L.dst = oop ? x->P[s][x->cur[s] ^ 1] : L.p;
       L.oop = oop;
+      if (L.hist && oop) L.hist = x->hist_spec;  // counted once the pass is adopted
       L.ar = x->alpha64.ar[s];
       L.az = x->alpha64.az[s];
       set_queue(x, x->q_real64, L);
@@ -1286,7 +1290,8 @@ int enqueue_pass(pic_ctx *x, bool spec) {
   if (spec) {
     if (cudaMemsetAsync(x->cnt->push, 0, sizeof(x->cnt->push), s) != cudaSuccess ||
         cudaMemsetAsync(&x->cnt->ke_lost, 0, 8, s) != cudaSuccess ||
-        cudaMemsetAsync(x->wall_spec, 0, nwall * 8, s) != cudaSuccess)
+        cudaMemsetAsync(x->wall_spec, 0, nwall * 8, s) != cudaSuccess ||
+        (x->hist_on && cudaMemsetAsync(x->hist_spec, 0, 16 * 8, s) != cudaSuccess))
       return PIC_E_CUDA;
     r = push_all(x, x->erh, x->ezh, x->ir, x->iz, 1, x->cnt->push, &x->cnt->ke_lost,
                  x->wall_spec, 1);
@@ -1415,6 +1420,10 @@ __global__ void k_addto(double *dst, const double *src, int n) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) dst[t] += src[t];
 }
+__global__ void k_addto_u64(unsigned long long *dst, const unsigned long long *src, int n) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) dst[t] += src[t];
+}
 
 }  // namespace
 
@@ -1487,6 +1496,11 @@ int step_end(pic_ctx *x, StepState &T, int *rc) {
     k_addto<<<(nwall + 255) / 256, 256, 0, s>>>(x->wall, x->wall_spec, nwall);
     if (cudaGetLastError() != cudaSuccess) return PIC_E_CUDA;
     x->launches += 1;
+    if (x->hist_on) {
+      k_addto_u64<<<1, 16, 0, s>>>(x->hist, x->hist_spec, 16);
+      if (cudaGetLastError() != cudaSuccess) return PIC_E_CUDA;
+      x->launches += 1;
+    }
   } else {
     // commit: the half field of the last iteration fed the last solve
     if (cudaMemsetAsync(x->ir, 0, ner * 8, s) != cudaSuccess) return PIC_E_CUDA;
