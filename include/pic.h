@@ -384,16 +384,18 @@ int pic_profile_read(pic_ctx *ctx, double *push_ms, long long *push_launches);
  * start-up and allows no allocation afterwards, or a plugin that only sees
  * the particle arrays.  It sorts n particles (SoA inputs cell..id, layout as
  * above, cell < 0 dropped) into the caller's output arrays (capacity >= n)
- * on `stream`, stably per launch order but with the order inside a cell
- * unspecified, and returns the number kept in *n_out (host).  All scratch
- * lives in one static device array of about 3 MB per GPU, kept until the
- * process exits; it limits the grid to nr * nz <= 262144 cells (larger grids
- * return PIC_E_CONFIG).  Nothing is allocated: no cudaMalloc, no cudaFree.
- * The first call on each device looks up the array's device address with
- * cudaGetSymbolAddress (once per device); make that first call before any
- * stream capture.  Every call reuses the same array, so calls that overlap
- * on the GPU (other streams, other threads) race: serialise them.
- * Synchronises the stream.  Errors: PIC_E_CONFIG, PIC_E_CUDA. */
+ * on `stream`, ascending by cell with the order inside a cell unspecified,
+ * and returns the number kept in *n_out (host).  All scratch lives in one
+ * static device array of about 3 MB per GPU, kept until the process exits;
+ * it limits the grid to nr * nz <= 262144 cells (larger grids return
+ * PIC_E_CONFIG).  Nothing is allocated: no cudaMalloc, no cudaFree.  The
+ * first call on each device looks up the array's device address with
+ * cudaGetSymbolAddress and keeps it for the process; do not call it again
+ * after cudaDeviceReset on that device.  Every call reuses the same array, so
+ * calls that overlap on the GPU (other streams, other threads) race:
+ * serialise them.  Each call reads the kept count back to the host and
+ * synchronises the stream, so it cannot be recorded into a stream capture.
+ * Errors: PIC_E_CONFIG, PIC_E_CUDA. */
 int pic_sort_cells_noalloc(int nr, int nz, long long n, const int32_t *cell_dev,
                            const double *a_dev, const double *b_dev, const double *vr_dev,
                            const double *vt_dev, const double *vz_dev, const double *w_dev,

@@ -9,7 +9,6 @@ without the compiled library raises.
 from __future__ import annotations
 
 import ctypes as C
-import math
 import os
 
 import numpy as np
@@ -504,11 +503,6 @@ def check_dmul(x, y):
     _check(lib().pic_check_dmul(x.data_ptr(), y.data_ptr(), out.data_ptr(), x.numel(),
                                 torch.cuda.current_stream(x.device).cuda_stream), "pic_check_dmul")
     return out
-
-
-def drive_voltage(cfg, step):
-    t = step * cfg["dt"]
-    return cfg["volt"] * math.sin(6.283185307179586 * cfg["freq"] * t)
 
 
 class Cnn:

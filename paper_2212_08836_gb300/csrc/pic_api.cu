@@ -107,7 +107,7 @@ struct pic_ctx {
   long long passes;         // passes enqueued (the first one is never captured)
   int fgrid[2], ggrid[2];   // tuned push grids (fast / general, per form: index 0)
   struct GraphEntry {
-    const void *key[12];
+    const void *key[13];
     cudaGraphExec_t exec;
     long long nlaunch;      // kernels in the graph
   } gcache[64];
@@ -1325,9 +1325,12 @@ int launch_pass(pic_ctx *x, bool spec) {
   // the first pass runs uncaptured (one-time set-up of launch shapes); the
   // legacy default stream cannot be captured, so its passes are never replayed
   if (!x->graphs || x->s == nullptr || x->passes++ == 0) return enqueue_pass(x, spec);
-  const void *key[12] = {x->er, x->ez, x->h, x->er1, x->ez1, x->er2, x->ez2, x->h2,
+  // a speculative pass captures the sub-step histogram's memset and pointer
+  // only while counting is on, so the switch is part of the key
+  const void *key[13] = {x->er, x->ez, x->h, x->er1, x->ez1, x->er2, x->ez2, x->h2,
                          (const void *)(uintptr_t)x->cur[0], (const void *)(uintptr_t)x->cur[1],
-                         (const void *)(uintptr_t)(spec ? 1 : 0), x->erh};
+                         (const void *)(uintptr_t)(spec ? 1 : 0), x->erh,
+                         (const void *)(uintptr_t)(x->hist_on ? 1 : 0)};
   for (int k = 0; k < x->ngraph; ++k)
     if (!memcmp(x->gcache[k].key, key, sizeof(key))) {
       x->launches += x->gcache[k].nlaunch;

@@ -358,7 +358,10 @@ template <typename T>
 cudaError_t launch_mcc_append(const MccLaunchT<T> &M, long long tot, long long ne_new0,
                               long long ni_new0, uint32_t id_e0, uint32_t id_i0, cudaStream_t s);
 
-// exclusive scan of n int32 values; total written to *total_dev (int64)
+// exclusive scan of n int32 values; total written to *total_dev (int64).
+// The scan works in tiles of kScanTile elements and keeps one int64 sum per
+// tile (plus one) in its scratch: scan_scratch_bytes(n) bytes
+constexpr long long kScanTile = 4096;
 size_t scan_scratch_bytes(long long n);
 cudaError_t scan_exclusive(const int32_t *in, int32_t *out, long long n, long long *total_dev,
                            void *scratch, cudaStream_t s);

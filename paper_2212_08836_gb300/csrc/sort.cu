@@ -12,6 +12,7 @@ namespace {
 constexpr int SCAN_BS = 1024;
 constexpr int SCAN_IPT = 4;
 constexpr int SCAN_TILE = SCAN_BS * SCAN_IPT;
+static_assert(SCAN_TILE == kScanTile, "scan tile and the scratch size it implies must agree");
 
 // block-wide exclusive scan of int64 values held one per thread
 __device__ long long block_excl_scan(long long v, long long *tot) {

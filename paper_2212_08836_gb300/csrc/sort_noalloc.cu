@@ -17,7 +17,6 @@ namespace {
 
 // largest grid the static scratch can sort: nr * nz <= kNoallocMaxCells
 constexpr long long kNoallocMaxCells = 1 << 18;
-constexpr long long kScanTile = 4096;  // elements per tile of scan_exclusive
 constexpr size_t kAlignUp(size_t b) { return (b + 255) & ~(size_t)255; }
 constexpr size_t kCountsBytes = kAlignUp((kNoallocMaxCells + 1) * sizeof(int32_t));
 constexpr size_t kCursorBytes = kAlignUp(kNoallocMaxCells * sizeof(int32_t));
@@ -33,7 +32,9 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void *g_addr[kMaxDevices];
 
-// device address of the scratch on the current device (set up once per device)
+// device address of the scratch on the current device (set up once per
+// device; a context destroyed by cudaDeviceReset reloads the module, so the
+// cached address is not valid across a reset)
 cudaError_t scratch_address(void **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -64,6 +65,8 @@ extern "C" int pic_sort_cells_noalloc(int nr, int nz, long long n, const int32_t
                                       void *stream, long long *n_out) {
   if (nr < 1 || nz < 1 || n < 0 || !n_out) return PIC_E_CONFIG;
   if ((long long)nr * nz > kNoallocMaxCells) return PIC_E_CONFIG;
+  // the scan's tile sums must fit the part of the array set aside for them
+  if (scan_scratch_bytes((long long)nr * nz + 1) > kScanBytes) return PIC_E_CONFIG;
   if (n > 0x7FFFFFFFll) return PIC_E_CONFIG;
   if (n > 0 && (!cell || !a || !b || !vr || !vt || !vz || !w || !id || !cell_out || !a_out ||
                 !b_out || !vr_out || !vt_out || !vz_out || !w_out || !id_out))

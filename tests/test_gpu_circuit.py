@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from tests.drive import drive_voltage
 from oracle import es as ES
 from tests.test_gpu_parity import assert_state_close, by_id
 
@@ -76,7 +77,7 @@ def test_step_parity_with_oracle(field_model, cblock):
             np.testing.assert_allclose(q, sim.circ[0], rtol=1e-8)
             assert st["v_electrode"] == phi and st["q_cap"] == q
             # the capacitor takes part of the drive: phi differs from V
-            v = P().drive_voltage(cfg, step + 1)
+            v = drive_voltage(cfg, step + 1)
             assert abs(phi - v) > 0.01 * abs(v)
         else:
             assert phi == st["v_electrode"]

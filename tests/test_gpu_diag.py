@@ -56,13 +56,16 @@ def test_gauss_residual_stays_at_rounding_over_steps(precision):
     assert r <= (1e-12 if precision == 0 else 1e-6) * q_scale, r
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_substep_histogram_counts_every_push(precision):
+@pytest.mark.parametrize("precision,graphs", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_substep_histogram_counts_every_push(precision, graphs):
     """Every particle of a state-writing pass lands in one bin, and the bins
-    weighted by their sub-step counts give the step's accepted sub-steps."""
+    weighted by their sub-step counts give the step's accepted sub-steps.
+    With graph replay the histogram is switched on after the passes have been
+    captured with it off: the replayed speculative passes must still count."""
     M = P()
     cfg = M.small_reactor(np_init=20000, mcc_on=1, precision=precision)
-    pic = M.Pic(cfg, device=DEV)
+    pic = M.Pic(cfg, device=DEV, stream=torch.cuda.Stream(device=DEV) if graphs else None)
+    M.set_graphs(pic, bool(graphs))
     pic.load_particles()
     pic.step(2)
     assert pic.substep_histogram(1).sum() == 0  # off until enabled
@@ -81,3 +84,34 @@ def test_substep_histogram_counts_every_push(precision):
     assert h[0] > 0.5 * h.sum() and h[1] > 0
     pic.step(1)
     assert np.array_equal(pic.substep_histogram(-1), h)  # stopped counting
+
+
+@pytest.mark.parametrize("precision,xa,ring", [(0, 0, 0), (1, 0, 0), (0, 3, 0), (0, 0, 4)])
+def test_energies_match_oracle(precision, xa, ring):
+    """Row a9: pic_diag's kinetic energy per species and field energy against
+    the oracle's sums on the same state (fields, particles); FP64 sums of the
+    same values, so they agree to rounding of the summation order."""
+    M = P()
+    kw = dict(np_init=20000, mcc_on=0, axis_cells=xa, precision=precision)
+    if ring:
+        kw.update(ring_cells=ring, eps_ring=4.0)
+    cfg = M.small_reactor(**kw)
+    pic = M.Pic(cfg, device=DEV)
+    g = O.Grid(cfg["nr"], cfg["nz"], cfg["R"], cfg["L"], xa=xa, nd=ring,
+               erd=4.0 if ring else 1.0)
+    e, i = O.load(g, 20000, 1e15, 3.0, 0.026, 5)
+    if precision == 1:
+        for sp in (e, i):
+            for k in ("a", "b", "vr", "vt", "vz", "w"):
+                sp[k] = sp[k].astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(2)
+    er = rng.normal(size=g.n_er) * 3e3
+    ez = rng.normal(size=g.n_ez) * 3e3
+    h = rng.normal(size=cfg["nr"] * cfg["nz"]) * 5.0
+    pic.set_state([e, i], er=er, ez=ez, h=h)
+    d = pic.diag()
+    for s, (sp, m) in enumerate(((e, O.ME), (i, O.M_AR))):
+        ref = O.kinetic_energy(m, sp)
+        assert abs(d["kinetic"][s] - ref) <= 1e-12 * ref, (s, d["kinetic"][s], ref)
+    ref_f = O.field_energy(g, er, ez, h)
+    assert abs(d["field"] - ref_f) <= 1e-12 * ref_f, (d["field"], ref_f)

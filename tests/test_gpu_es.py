@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from tests.drive import drive_voltage
 from oracle import es as ES
 
 torch = pytest.importorskip("torch")
@@ -61,7 +62,7 @@ def test_es_steps_solve_gauss_with_the_moved_charge(precision):
         Q = pic.node_charge().cpu().numpy()
         er, ez, h = pic.fields()
         assert np.all(h == 0.0)
-        v1 = M.drive_voltage(cfg, k + 1)
+        v1 = drive_voltage(cfg, k + 1)
         _, ero, ezo = ES.solve(nr, nz, cfg["R"] / nr, cfg["L"] / nz, Q, v1)
         tol = 1e-9 if precision == 0 else 1e-5
         assert rel(er, ero) <= tol and rel(ez, ezo) <= tol, k
@@ -79,7 +80,7 @@ def test_em_fields_approach_es_fields_as_c_grows():
             assert rc == 0
         Q = pic.node_charge().cpu().numpy()
         er, ez, _ = pic.fields()
-        v1 = M.drive_voltage(cfg, 3)
+        v1 = drive_voltage(cfg, 3)
         nr, nz = cfg["nr"], cfg["nz"]
         _, ero, ezo = ES.solve(nr, nz, cfg["R"] / nr, cfg["L"] / nz, Q, v1)
         errs.append(max(rel(er, np.concatenate([ero])), rel(ez, ezo)))

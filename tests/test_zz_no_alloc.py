@@ -46,8 +46,16 @@ def test_noalloc_sort_matches_context_sort_twice():
         n_out = C.c_longlong(-1)
         args = [nr, nz, n] + [src[k].data_ptr() for k in P.FIELDS] + \
                [out[k].data_ptr() for k in P.FIELDS] + [stream, C.addressof(n_out)]
+        torch.cuda.synchronize()
+        held, free = torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0]
         rc = P.lib().pic_sort_cells_noalloc(*args)
         assert rc == 0, P.lib().pic_strerror(rc)
+        torch.cuda.synchronize()
+        if call == 1:
+            # the first call may load the module's static array; later calls
+            # take no device memory at all
+            assert torch.cuda.memory_allocated() == held
+            assert torch.cuda.mem_get_info()[0] == free
         m = n_out.value
         assert m == len(ref["cell"])
         got = {k: out[k][:m].cpu().numpy() for k in P.FIELDS}
