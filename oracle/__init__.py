@@ -33,13 +33,25 @@ MU0 = 1.25663706212e-6
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (-ffp-contract=off: no fused multiply-add)."""
+    """Compile the oracle with gcc (-ffp-contract=off: no fused multiply-add).
+    OpenMP, where the compiler has it, only serves the timing form of the
+    push (set_threads > 1); every test runs the serial form."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp,
-                               _SRC, "-lm"])
+        base = ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        try:
+            subprocess.check_call(base + ["-fopenmp"], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's push (1: serial, the form every test uses;
+    more: the timing form of the CPU baseline, particles split over threads
+    with per-thread crossed-charge arrays summed at the end)."""
+    lib().oracle_set_threads(int(n))
 
 
 _lib = None
@@ -85,6 +97,8 @@ def _declare(L):
     L.oracle_philox4x64.argtypes = [_P, _P, _P]
     L.oracle_load.argtypes = ([_I, _I, _D, _D, _I, _I, _D, _D, _D, _D, _L, _D, _D, _D, _D, _U]
                               + [_P] * 11)
+    L.oracle_set_threads.argtypes = [_I]
+    L.oracle_set_threads.restype = None
     L.oracle_push.argtypes = ([_I, _I, _D, _D, _I, _I, _D, _D, _D, _D, _D, _L] + [_P] * 11 + [_I]
                               + [_P] * 5)
     L.oracle_node_charge.argtypes = [_I, _I, _D, _L, _P, _P, _P, _P, _P]

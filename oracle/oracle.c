@@ -427,6 +427,32 @@ static int o_transition(const o_push *P, int *ic, int *jc, double *a, double *b,
   return 0;
 }
 
+/* Start of the landing solve: the time at which the quadratic path
+ * x(s) = v0 s + alpha s^2 / 2 through the trial's end point, x(dtT) = dxh,
+ * first reaches the face at displacement Xh.  For Xh != 0 the face lies
+ * between the start and the trial's end point, so the parabola reaches it in
+ * (0, dtT]; the smaller positive root is the first crossing (the sub-step ends
+ * on the first face crossed).  Xh = 0 is the face the particle sits on: the
+ * nonzero root.  With constant acceleration this is the exact crossing time;
+ * a start on the far side of a grazing crossing could converge to a later
+ * root instead. */
+static double o_first_crossing(double Xh, double dxh, double v0, double dtT) {
+  double alpha = 2.0 * (dxh - v0 * dtT) / (dtT * dtT);
+  if (Xh == 0.0) return -2.0 * v0 / alpha;
+  if (alpha == 0.0) return Xh / v0;
+  double disc = v0 * v0 + 2.0 * alpha * Xh;
+  if (!(disc >= 0.0)) return dtT * (Xh / dxh);
+  /* roots of alpha/2 s^2 + v0 s - Xh = 0 without cancellation:
+   * s1 = qq / (alpha/2), s2 = -Xh / qq with qq = -(v0 + sgn(v0) sqrt(disc)) / 2 */
+  double qq = -0.5 * (v0 + (v0 >= 0.0 ? sqrt(disc) : -sqrt(disc)));
+  double s1 = qq / (0.5 * alpha);
+  double s2 = qq != 0.0 ? -Xh / qq : s1;
+  double s = -1.0;
+  if (s1 > 0.0) s = s1;
+  if (s2 > 0.0 && (s < 0.0 || s2 < s)) s = s2;
+  return s > 0.0 ? s : dtT * (Xh / dxh);
+}
+
 /* Advance one particle over dt.  Returns 1 if absorbed at a wall. */
 static int o_push_one(o_push *P, int *pic, int *pjc, double *pa, double *pb, double *pvr,
                       double *pvt, double *pvz, double w, double dt_full) {
@@ -484,15 +510,7 @@ static int o_push_one(o_push *P, int *pic, int *pjc, double *pa, double *pb, dou
         double X = face - x0;
         double v0 = dir == 0 ? vr : vz;
         double h = dir == 0 ? s.dr : P->dz;
-        double g0;
-        if (X != 0.0) {
-          g0 = dtT * (X / dx);
-        } else {
-          /* return to the face the particle sits on: quadratic model through
-           * the trial end point, x(s) = v0*s + alpha*s^2/2 */
-          double alpha = 2.0 * (dx * h - v0 * dtT) / (dtT * dtT);
-          g0 = -2.0 * v0 / alpha;
-        }
+        double g0 = o_first_crossing(X * h, dx * h, v0, dtT);
         double oth0 = doth * (g0 / dtT);
         double tdt = 0.0, toth = 0.0;
         if (!(g0 > 0.0) || !o_solve_landing(&s, dir, X, g0, oth0, dtT, &tdt, &toth)) continue;
@@ -569,6 +587,31 @@ static int o_push_one(o_push *P, int *pic, int *pjc, double *pa, double *pb, dou
 /* Push + deposit of one species (rows a2/a3, and a6 when write != 0).
  * er/ez hold E^{n+1/2}; ir/iz accumulate (caller zeroes).  counters[6]:
  * substep errors, absorbed, substeps, fallbacks (and ke_lost in kelost). */
+/* threads of the push (1: the serial form every test uses) */
+static int o_threads = 1;
+
+void oracle_set_threads(int n) { o_threads = n < 1 ? 1 : n; }
+
+static void o_push_range(o_push *P, int nz, int64_t p0, int64_t p1, int32_t *cell, double *a,
+                         double *b, double *vr, double *vt, double *vz, const double *w,
+                         int write, double dt) {
+  for (int64_t p = p0; p < p1; ++p) {
+    if (cell[p] < 0) continue;
+    int ic = cell[p] / nz, jc = cell[p] % nz;
+    double pa = a[p], pb = b[p], pvr = vr[p], pvt = vt[p], pvz = vz[p];
+    int gone = o_push_one(P, &ic, &jc, &pa, &pb, &pvr, &pvt, &pvz, w[p], dt);
+    if (write) {
+      cell[p] = gone ? -1 : ic * nz + jc;
+      a[p] = pa; b[p] = pb; vr[p] = pvr; vt[p] = pvt; vz[p] = pvz;
+    }
+  }
+}
+
+static void o_add(double *dst, const double *src, size_t n) {
+  if (!dst) return;
+  for (size_t k = 0; k < n; ++k) dst[k] += src[k];
+}
+
 void oracle_push(int nr, int nz, double dr, double dz, int xa, int nd, double erd, double dt,
                  double q, double m, double bz,
                  int64_t n, int32_t *cell, double *a, double *b, double *vr, double *vt,
@@ -584,14 +627,50 @@ void oracle_push(int nr, int nz, double dr, double dz, int xa, int nd, double er
   P.er = er; P.ez = ez; P.ir = ir; P.iz = iz;
   P.q = q; P.qm = q / m; P.wb = (q / m) * bz; P.m = m;
   P.wall_z0 = wall_z0; P.wall_zl = wall_zl; P.wall_r = wall_r;
-  for (int64_t p = 0; p < n; ++p) {
-    if (cell[p] < 0) continue;
-    int ic = cell[p] / nz, jc = cell[p] % nz;
-    double pa = a[p], pb = b[p], pvr = vr[p], pvt = vt[p], pvz = vz[p];
-    int gone = o_push_one(&P, &ic, &jc, &pa, &pb, &pvr, &pvt, &pvz, w[p], dt);
-    if (write) {
-      cell[p] = gone ? -1 : ic * nz + jc;
-      a[p] = pa; b[p] = pb; vr[p] = pvr; vt[p] = pvt; vz[p] = pvz;
+  int nt = o_threads;
+  if (nt > 1 && n < 64 * (int64_t)nt) nt = 1;
+  if (nt <= 1) {
+    o_push_range(&P, nz, 0, n, cell, a, b, vr, vt, vz, w, write, dt);
+  } else {
+    /* timing form: the particles split into nt contiguous ranges, each pushed
+     * with its own crossed-charge and wall arrays, which are summed at the end
+     * (another summation order than the serial form: equal to rounding) */
+    const size_t ner = (size_t)nr * (nz + 1), nez = (size_t)(nr + 1) * nz;
+    const size_t per = ner + nez + 2 * (size_t)(nr + 1) + (size_t)(nz + 1);
+    double *buf = (double *)calloc((size_t)nt * per, sizeof(double));
+    o_push *Pt = (o_push *)calloc((size_t)nt, sizeof(o_push));
+    if (!buf || !Pt) {
+      free(buf);
+      free(Pt);
+      o_push_range(&P, nz, 0, n, cell, a, b, vr, vt, vz, w, write, dt);
+    } else {
+#pragma omp parallel for num_threads(nt) schedule(static, 1)
+      for (int t = 0; t < nt; ++t) {
+        double *bt = buf + (size_t)t * per;
+        Pt[t] = P;
+        Pt[t].ir = ir ? bt : NULL;
+        Pt[t].iz = iz ? bt + ner : NULL;
+        Pt[t].wall_z0 = wall_z0 ? bt + ner + nez : NULL;
+        Pt[t].wall_zl = wall_zl ? bt + ner + nez + (nr + 1) : NULL;
+        Pt[t].wall_r = wall_r ? bt + ner + nez + 2 * (nr + 1) : NULL;
+        o_push_range(&Pt[t], nz, n * t / nt, n * (t + 1) / nt, cell, a, b, vr, vt, vz, w,
+                     write, dt);
+      }
+      for (int t = 0; t < nt; ++t) {
+        double *bt = buf + (size_t)t * per;
+        o_add(ir, bt, ner);
+        o_add(iz, bt + ner, nez);
+        o_add(wall_z0, bt + ner + nez, (size_t)(nr + 1));
+        o_add(wall_zl, bt + ner + nez + (nr + 1), (size_t)(nr + 1));
+        o_add(wall_r, bt + ner + nez + 2 * (nr + 1), (size_t)(nz + 1));
+        P.n_substep_err += Pt[t].n_substep_err;
+        P.n_absorbed += Pt[t].n_absorbed;
+        P.n_substeps += Pt[t].n_substeps;
+        P.n_fallback += Pt[t].n_fallback;
+        P.ke_lost += Pt[t].ke_lost;
+      }
+      free(buf);
+      free(Pt);
     }
   }
   if (counters) {

@@ -94,6 +94,47 @@ def test_constant_force_parabola_exact(comp):
     assert cnt[0] == 0
 
 
+def test_grazing_crossings_land_on_the_first_crossing():
+    """Electrons decelerated by a uniform E_z whose parabola peaks just beyond
+    the upper z-face of their cell and ends beyond it: each crosses that face
+    exactly once.  The sub-step must end on that (first) crossing and the
+    rest of the step runs in the next cell: two sub-steps per particle, no
+    halving fallback, and the end state of the exact parabola (CN is exact for
+    a constant acceleration).  A landing started on the far side of the
+    crossing time can converge past the first root and fall back to halving."""
+    g = grid()
+    dt = 1e-9
+    n = 400
+    rng = np.random.default_rng(5)
+    k = 1.0                                   # deceleration, cells per step^2
+    Ez = k * g.dz / (QE / ME * dt * dt)      # electrons: a_z = -k dz / dt^2
+    sp_ = rng.uniform(0.85, 1.0, size=n)      # peak time [steps]
+    graze = 0.5 * k * (1.0 - sp_) ** 2        # the peak's height above the end point
+    delta = graze + rng.uniform(1e-5, 5e-3, size=n)  # peak above the face
+    u = k * sp_                               # initial z velocity [cells per step]
+    b0 = 1.0 + delta - 0.5 * k * sp_ ** 2
+    ic = rng.integers(4, g.nr - 4, size=n)
+    jc = rng.integers(5, g.nz - 6, size=n)
+    order = np.argsort(ic * g.nz + jc, kind="stable")
+    sp = {"cell": (ic * g.nz + jc)[order].astype(np.int32), "a": rng.random(n)[order],
+          "b": b0[order], "vr": np.zeros(n), "vt": np.zeros(n), "vz": (u * g.dz / dt)[order],
+          "w": np.ones(n), "id": np.arange(n, dtype=np.uint32)}
+    x0, y0 = xi_eta(g, sp)
+    vz0 = sp["vz"].copy()
+    er, ez, _ = g.zeros_fields()
+    ez[:] = Ez
+    _, _, cnt, _ = O.push(g, dt, -QE, ME, sp, er, ez, write=True)
+    x1, y1 = xi_eta(g, sp)
+    assert cnt[0] == 0 and cnt[3] == 0, cnt
+    assert cnt[2] == 2 * n, cnt
+    acc = -QE / ME * Ez
+    np.testing.assert_allclose(y1 * g.dz, y0 * g.dz + vz0 * dt + 0.5 * acc * dt * dt,
+                               rtol=0, atol=1e-12 * g.dz)
+    np.testing.assert_allclose(sp["vz"], vz0 + acc * dt, rtol=1e-12, atol=1e-9)
+    assert np.array_equal(sp["cell"], (ic * g.nz + jc + 1)[order])
+    np.testing.assert_array_equal(x1, x0)
+
+
 def test_inertial_terms_conserve_energy_and_angular_momentum():
     """E = 0: CN keeps vr^2+vt^2+vz^2 and r*vt exact (arithmetic-mean identity)."""
     g = grid()
@@ -313,3 +354,31 @@ def test_exb_drift():
     vE = -E0 / B
     r = 12.5 * g.dr
     assert np.all(np.abs(vmean - vE) <= 0.02 * abs(vE) + 10 * vE ** 2 / (wc * r))
+
+
+def test_threaded_timing_form_matches_serial():
+    """The oracle's threaded push (the CPU baseline's timing form) gives the
+    serial form's particles bit for bit and its crossed charge, wall tallies
+    and counters up to the summation order."""
+    g = grid()
+    dt = 1e-9
+    sp0 = inputs.particles(g.nr, g.nz, 20000, 9, 8e5, edge_frac=0.02)
+    er, ez = inputs.smooth_fields(g.nr, g.nz, 4, 3e3)
+    outs = []
+    for nt in (1, 4):
+        O.set_threads(nt)
+        sp = {k: v.copy() for k, v in sp0.items()}
+        walls = (np.zeros(g.nr + 1), np.zeros(g.nr + 1), np.zeros(g.nz + 1))
+        ir, iz, cnt, kel = O.push(g, dt, -QE, ME, sp, er, ez, write=True, walls=walls)
+        outs.append((sp, ir, iz, cnt, kel, walls))
+    O.set_threads(1)
+    (s1, ir1, iz1, c1, k1, w1), (s4, ir4, iz4, c4, k4, w4) = outs
+    for k in s1:
+        assert np.array_equal(s1[k], s4[k]), k
+    assert np.array_equal(c1, c4)
+    scale = np.max(np.abs(np.concatenate([ir1, iz1])))
+    np.testing.assert_allclose(ir4, ir1, rtol=0, atol=1e-13 * scale)
+    np.testing.assert_allclose(iz4, iz1, rtol=0, atol=1e-13 * scale)
+    for a, b in zip(w1, w4):
+        np.testing.assert_allclose(b, a, rtol=1e-13, atol=1e-30)
+    assert abs(k4 - k1) <= 1e-13 * abs(k1)
