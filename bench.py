@@ -157,11 +157,22 @@ def dist_env():
     return ws, rank, local
 
 
-def cpu_oracle_rate(n_sample, steps=1, seed=1):
+def host_cores():
+    """Host cores this process may run on (the oracle's push threads)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def cpu_oracle_rate(n_sample, steps=1, seed=1, threads=1):
     """FP64 oracle on a bounded sample: the same reactor and grid with n_sample
-    particles per species; returns (pushes/s, seconds, pushes)."""
+    particles per species, its push split over `threads` host threads (per-
+    thread crossed-charge arrays); returns (pushes/s, seconds, pushes)."""
     import oracle as O
     import paper_2212_08836_gb300 as P
+
+    O.set_threads(threads)
 
     cfg = P.large_reactor()
     g = O.Grid(cfg["nr"], cfg["nz"], cfg["R"], cfg["L"])
@@ -190,19 +201,21 @@ def run_reference(args):
     if rank != 0:
         return 0
     n_sample = args.ref_sample
-    rates = []
+    cores = host_cores()
     # warm-up steps and timed steps, each a fresh bounded sample step
-    rate, secs, pushes = cpu_oracle_rate(n_sample, steps=args.warmup + args.steps)
+    rate, secs, pushes = cpu_oracle_rate(n_sample, steps=args.warmup + args.steps, threads=cores)
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / (args.warmup + args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": "large-electrode VHF reactor 256x384, R=0.3 m, L=0.03 m, Ar 2 Pa, "
                                    "100 MHz 200 V (oracle on a %d-per-species sample)" % n_sample},
-            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "%d macro-particles per species on the full 256x384 grid, "
-                                       "%d whole steps incl. Picard, field solves, MCC, sort"
-                                       % (n_sample, args.warmup + args.steps)},
+                                       "%d whole steps incl. Picard, field solves, MCC, sort; "
+                                       "push over %d threads (OpenMP, per-thread crossed charge), "
+                                       "the rest serial"
+                                       % (n_sample, args.warmup + args.steps, cores)},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -313,18 +326,41 @@ def ensemble_configs(P, rank):
     return cfgs
 
 
+def timed_cycle(P, torch, dev, pic, nsteps, relaxed):
+    """nsteps steps of pic, wall clock with the device synchronised at both
+    ends (host work between the steps included); returns (s, iterations,
+    pushes, statuses)."""
+    from paper_2212_08836_gb300.dispersion import advance
+
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    iters, pushes, rcs = [], 0, []
+    for k in range(nsteps):
+        st = advance(pic, pic.cfg["picard_tol"], relaxed, k)
+        iters.append(st["picard_iters"])
+        pushes += st["pushes"]
+    torch.cuda.synchronize(dev)
+    return time.perf_counter() - t0, iters, pushes
+
+
 def run_developed_form(P, torch, dev, args, rank, cycles=5):
-    """FP64 push rate on a developed discharge: the 256 x 384 reactor after
-    `cycles` RF cycles (sheaths, sheath-accelerated electrons, more face
-    crossings than the Maxwellian start), developed with the mixed form and
-    handed to the FP64 form through host arrays; then args.steps timed steps."""
+    """The developed discharge: the 256 x 384 reactor after `cycles` RF cycles
+    of the mixed form (sheaths, sheath-accelerated electrons, more face
+    crossings than the Maxwellian start).  From that one state, one whole RF
+    cycle (1/(f dt) steps) is timed for each form at the converged Picard
+    tolerance 1e-8: the plain FP64 form, the mixed form with the plain start,
+    and the mixed form with the learned start (the network trained on
+    snapshots of the same discharge).  Wall-seconds per RF cycle with the
+    device synchronised at both ends; the FP64 form's pushes/s too."""
+    from paper_2212_08836_gb300 import guess as GS
     from paper_2212_08836_gb300.dispersion import advance
 
     seed = replica_seed(1, rank)
     cfgm = P.large_reactor(seed=seed, precision=P.PIC_MIXED, capacity_factor=3.0)
     if args.np:
         cfgm["np_init"] = args.np
-    n_dev = int(round(cycles / (cfgm["freq"] * cfgm["dt"])))
+    steps_cycle = int(round(1.0 / (cfgm["freq"] * cfgm["dt"])))
+    n_dev = cycles * steps_cycle
     pic = P.Pic(cfgm, device=dev)
     pic.load_particles()
     relaxed = []
@@ -340,41 +376,57 @@ def run_developed_form(P, torch, dev, args, rank, cycles=5):
     er, ez, h = pic.fields()
     v = pic.view()
     step, next_ids = v["step"], list(v["next_id"])
+
+    def fresh(cfg):
+        q = P.Pic(cfg, device=dev)
+        q.set_state(species, er, ez, h, next_ids=next_ids, step=step)
+        return q
+
+    out = {"workload": "256x384 reactor after %d RF cycles (%d steps of the mixed form, %.1f s), "
+                       "then one RF cycle (%d steps) of each form from that state, tol %.0e"
+                       % (cycles, n_dev, t_develop, steps_cycle, cfgm["picard_tol"]),
+           "steps_per_rf_cycle": steps_cycle, "develop_steps_relaxed": len(relaxed)}
+    walls, iters = {}, {}
+    # ---- learned start: snapshots of this discharge (extrapolated start), training
+    X, T = GS.collect(pic, args.guess_samples)
     pic.close()
+    net = P.Cnn(cfgm["nr"], cfgm["nz"], batch=8, device=dev)
+    t1 = time.perf_counter()
+    loss, val, zero = GS.train(net, X, T, args.guess_epochs)
+    t_train = time.perf_counter() - t1
+    del X, T
+    for name, mode in (("mixed", P.PIC_GUESS_PLAIN), ("mixed_learned_start", P.PIC_GUESS_CNN)):
+        q = fresh(cfgm)
+        P.set_guess(q, mode, net if mode == P.PIC_GUESS_CNN else None)
+        q.step(4, check=False)  # the field history of the learned start refills
+        rel = []
+        w, it, _ = timed_cycle(P, torch, dev, q, steps_cycle, rel)
+        walls[name], iters[name] = w, float(np.mean(it))
+        out[name + "_relaxed_steps"] = len(rel)
+        q.close()
+    net.close()
+    # ---- the plain FP64 form
     cfg = P.large_reactor(seed=seed, capacity_factor=3.0)
     if args.np:
         cfg["np_init"] = args.np
-    p64 = P.Pic(cfg, device=dev)
-    p64.set_state(species, er, ez, h, next_ids=next_ids, step=step)
-    for _ in range(args.warmup):
-        p64.step(1, check=False)
-    stream = p64.stream
-    torch.cuda.synchronize(dev)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    pushes, iters, subs, rcs = 0, [], 0, []
-    for _ in range(args.steps):
-        rc, st = p64.step(1, check=False)
-        rcs.append(rc)
-        pushes += st["pushes"]
-        iters.append(st["picard_iters"])
-        subs += st["substeps"]
-    ev1.record(stream)
-    torch.cuda.synchronize(dev)
-    t_ms = ev0.elapsed_time(ev1)
-    n = st["n"]
-    p64.substep_histogram(1)
-    p64.step(1, check=False)
-    hist = [int(v) for v in p64.substep_histogram(0)]
-    p64.close()
-    return {"workload": "256x384 reactor after %d RF cycles (%d steps of the mixed form, %.1f s), "
-                        "then the FP64 form" % (cycles, n_dev, t_develop),
-            "value": pushes / (t_ms * 1e-3), "unit": UNIT, "ms_per_step": t_ms / args.steps,
-            "picard_iters": iters, "n": n, "step_status": rcs,
-            "accepted_substeps_per_particle_commit": subs / max(args.steps * (n[0] + n[1]), 1),
-            "substep_histogram": hist,
-            "develop_steps_relaxed": len(relaxed)}
+    q = fresh(cfg)
+    q.step(4, check=False)
+    rel = []
+    w, it, pushes = timed_cycle(P, torch, dev, q, steps_cycle, rel)
+    walls["plain_fp64"], iters["plain_fp64"] = w, float(np.mean(it))
+    n = q.view()["n"]
+    q.substep_histogram(1)
+    q.step(1, check=False)
+    hist = [int(x) for x in q.substep_histogram(0)]
+    q.close()
+    out.update({"wall_s_per_rf_cycle": walls, "picard_iters_mean": iters,
+                "plain_fp64_relaxed_steps": len(rel),
+                "value": pushes / w, "unit": UNIT, "ms_per_step": w * 1e3 / steps_cycle, "n": n,
+                "substep_histogram": hist,
+                "learned_start": {"samples": args.guess_samples, "adam_steps": args.guess_epochs,
+                                  "train_s": t_train, "heldout_loss": val,
+                                  "heldout_loss_no_correction": zero}})
+    return out
 
 
 def run_ensemble_form(P, torch, dev, args, rank):
@@ -574,11 +626,17 @@ def run_ours(args):
         wall["mixed_plain_start_same_state"] = rs["plain"]["ms_per_step"] * 1e-3 * steps_per_cycle
         pic.close()
         net.close()
-    line["wall_s_per_rf_cycle"] = wall
+    # the Maxwellian start's step times scaled to an RF cycle (context only)
+    line["wall_s_per_rf_cycle_maxwellian_extrapolated"] = wall
 
-    # ---- FP64 form on a developed discharge (5 RF cycles)
+    # ---- the developed discharge (5 RF cycles): one RF cycle of each form timed
     if "developed" in forms:
-        line["developed_state"] = run_developed_form(P, torch, dev, args, rank)
+        dv = run_developed_form(P, torch, dev, args, rank)
+        line["developed_state"] = dv
+        if "wall_s_per_rf_cycle" in dv:
+            line["wall_s_per_rf_cycle"] = dict(dv["wall_s_per_rf_cycle"],
+                                               note="measured over one RF cycle of the developed "
+                                                    "discharge, tol 1e-8, device synchronised")
 
     # ---- batched ensemble of 16 uneven discharges (mixed form) vs the same
     # discharges stepped one after another
@@ -586,10 +644,13 @@ def run_ours(args):
         line["ensemble"] = run_ensemble_form(P, torch, dev, args, rank)
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        rate, secs, npush = cpu_oracle_rate(args.cpu_sample, steps=1)
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+        cores = host_cores()
+        rate, secs, npush = cpu_oracle_rate(args.cpu_sample, steps=1, threads=cores)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": "%d macro-particles per species on the 256x384 grid, 1 whole "
-                                          "step (%d pushes, %.1f s)" % (args.cpu_sample, npush, secs)}
+                                          "step (%d pushes, %.1f s); push over %d threads (OpenMP, "
+                                          "per-thread crossed charge), field solve, MCC and sort serial"
+                                          % (args.cpu_sample, npush, secs, cores)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -608,7 +669,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--np", type=int, default=0, help="macro-particles per species (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--forms", default="plain,mixed,es,guess,developed,ensemble",
+    ap.add_argument("--forms", default="plain,mixed,es,developed,ensemble",
                     help="comma list of plain (FP64), mixed (FP32 push), es (electrostatic "
                          "model), guess (mixed form "
                          "with the learned Picard start), developed (the FP64 form after 5 RF "

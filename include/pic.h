@@ -279,6 +279,41 @@ int pic_sort(pic_ctx *ctx);
 /* Row a9: FP64 kinetic and field energies and charges.  Synchronises. */
 int pic_diag(pic_ctx *ctx, pic_diag_out *out);
 
+/* Diagnostic kinds of pic_diag_get (row a9; the time-averaged profiles are
+ * the long-run statistics the paper compares, e.g. the ion flux onto the
+ * electrodes of Sec. 4.1).  Node (i, j), i = 0..nr, j = 0..nz, z fastest. */
+enum {
+  PIC_DIAG_ENERGY = 0,       /* pic_diag_out (host destination only) */
+  PIC_DIAG_GAUSS = 1,        /* (nr+1)(nz+1) doubles: pic_gauss_residual */
+  PIC_DIAG_CONTINUITY = 2,   /* (nr+1)(nz+1) doubles: charge balance of the last committed
+                              * step per node, (Q^{n+1} - Q^n) + (W^{n+1} - W^n) + div dQ, with
+                              * Q the S1 x S1 node charge of both species, W the wall (and
+                              * ring-face) tallies on their nodes, dQ the crossed charge of
+                              * the step (Eq. 3); zero up to rounding.  Needs averaging on. */
+  PIC_DIAG_DENSITY_AVG = 3,  /* 2 (nr+1)(nz+1) doubles: electrons then ions, node density
+                              * [m^-3] averaged over the steps since pic_diag_average(ctx, 1):
+                              * sum of w S1 x S1 / (steps x dual volume of the node) */
+  PIC_DIAG_ION_FLUX_AVG = 4, /* 2 (nr+1) doubles: mean Ar+ flux [m^-2 s^-1] absorbed by the
+                              * electrode z = 0, then z = L, per radial node (its dual ring
+                              * on the electrode), over the same window */
+  PIC_DIAG_FIELDS = 5,       /* E_r (nr (nz+1)), E_z ((nr+1) nz), H_theta (nr nz) doubles */
+  PIC_DIAG_COUNTS = 6        /* 4 long long: n_e, n_i, step index, steps averaged */
+};
+
+/* Starts (enable = 1: clears the averages and the window) or stops
+ * (enable = 0) the per-step diagnostics: after every committed step the node
+ * densities of both species are added to the averages and the step's
+ * continuity residual is formed (one extra pass over the particles per
+ * step).  Asynchronous.  Errors: PIC_E_CONFIG, PIC_E_CUDA. */
+int pic_diag_average(pic_ctx *ctx, int enable);
+
+/* One diagnostic of the kinds above into dst (bytes >= its size; on the
+ * device when dst_is_device, else host memory).  Synchronises the stream.
+ * Errors: PIC_E_CONFIG (unknown kind, bytes too small, ENERGY to a device
+ * destination), PIC_E_STATE (CONTINUITY before a step with averaging on,
+ * averages with no step averaged), PIC_E_CUDA. */
+int pic_diag_get(pic_ctx *ctx, int kind, void *dst, size_t bytes, int dst_is_device);
+
 /* Node charge by S1 x S1 weighting of both species, added into q_dev
  * ((nr+1)*(nz+1) doubles, caller zeroes).  Asynchronous. */
 int pic_node_charge(pic_ctx *ctx, double *q_dev);

@@ -26,6 +26,8 @@ PIC_E_NAN = -6
 PIC_E_STATE = -7
 PIC_E_WORKSPACE = -8
 PIC_E_IO = -9
+PIC_DIAG_ENERGY, PIC_DIAG_GAUSS, PIC_DIAG_CONTINUITY, PIC_DIAG_DENSITY_AVG = 0, 1, 2, 3
+PIC_DIAG_ION_FLUX_AVG, PIC_DIAG_FIELDS, PIC_DIAG_COUNTS = 4, 5, 6
 PIC_FEED_GAP = 0
 PIC_FEED_WAVE = 1
 PIC_FP64 = 0
@@ -103,6 +105,8 @@ def _load_lib():
     L.pic_mcc.argtypes = [_P, C.c_ulonglong, _P, _P]
     L.pic_sort.argtypes = [_P]
     L.pic_diag.argtypes = [_P, C.POINTER(DiagOut)]
+    L.pic_diag_average.argtypes = [_P, _I]
+    L.pic_diag_get.argtypes = [_P, _I, _P, C.c_size_t, _I]
     L.pic_node_charge.argtypes = [_P, _P]
     L.pic_get_view.argtypes = [_P, C.POINTER(View)]
     L.pic_set_counts.argtypes = [_P, _LL, _LL, C.c_uint32, C.c_uint32, _LL]
@@ -325,6 +329,41 @@ class Pic:
         _check(lib().pic_diag(self._h, C.byref(d)), "pic_diag")
         return {"kinetic": list(d.kinetic), "field": d.field, "charge": list(d.charge),
                 "n": list(d.n)}
+
+    def diag_average(self, enable=True):
+        """Start (clearing the averages) or stop the per-step diagnostics
+        (pic_diag_average): time-averaged densities and ion fluxes, and the
+        continuity residual of each committed step."""
+        _check(lib().pic_diag_average(self._h, 1 if enable else 0), "pic_diag_average")
+
+    def diag_get(self, kind):
+        """One diagnostic of pic_diag_get as a host numpy array (see
+        include/pic.h for the layouts): GAUSS and CONTINUITY (nr+1, nz+1);
+        DENSITY_AVG (2, nr+1, nz+1) [m^-3]; ION_FLUX_AVG (2, nr+1) [m^-2 s^-1]
+        into z = 0 and z = L; FIELDS (er, ez, h); COUNTS (n_e, n_i, step, steps
+        averaged)."""
+        nr, nz = self.nr, self.nz
+        nn = (nr + 1) * (nz + 1)
+        if kind == PIC_DIAG_ENERGY:
+            return self.diag()
+        shapes = {PIC_DIAG_GAUSS: ((nn,), np.float64), PIC_DIAG_CONTINUITY: ((nn,), np.float64),
+                  PIC_DIAG_DENSITY_AVG: ((2 * nn,), np.float64),
+                  PIC_DIAG_ION_FLUX_AVG: ((2 * (nr + 1),), np.float64),
+                  PIC_DIAG_FIELDS: ((nr * (nz + 1) + (nr + 1) * nz + nr * nz,), np.float64),
+                  PIC_DIAG_COUNTS: ((4,), np.int64)}
+        shape, dt = shapes[kind]
+        out = np.zeros(shape, dtype=dt)
+        _check(lib().pic_diag_get(self._h, int(kind), out.ctypes.data, out.nbytes, 0), "pic_diag_get")
+        if kind in (PIC_DIAG_GAUSS, PIC_DIAG_CONTINUITY):
+            return out.reshape(nr + 1, nz + 1)
+        if kind == PIC_DIAG_DENSITY_AVG:
+            return out.reshape(2, nr + 1, nz + 1)
+        if kind == PIC_DIAG_ION_FLUX_AVG:
+            return out.reshape(2, nr + 1)
+        if kind == PIC_DIAG_FIELDS:
+            a, b = nr * (nz + 1), (nr + 1) * nz
+            return out[:a].copy(), out[a:a + b].copy(), out[a + b:].copy()
+        return out
 
     def node_charge(self):
         t = self.torch

@@ -38,7 +38,15 @@ struct pic_ctx {
   int cur[2];
   int mixed;                 // 1: FP32 particle store and push (PIC_MIXED)
   AlphaOut alpha;            // mixed form: normalised accelerations per species
-  int *queue, *qblock;       // work queue of the general push path (both forms)
+  int *queue, *qblock;       // work queue of the general push path (FP64 form)
+  // mixed form: per species the list of near-axis crossers pushed in FP64
+  // arithmetic, its count, and the side stream that runs the electrons' list
+  // while the ions are pushed
+  int *plist[2];
+  unsigned *pcnt;
+  cudaStream_t pstream;
+  cudaEvent_t pev[2];
+  int pstream_made;
   float *q_real[2];          // mixed form queue records (trial displacements)
   double *q_real64[2];       // FP64 form queue records
   AlphaOut64 alpha64;        // FP64 form: normalised accelerations per species
@@ -62,6 +70,12 @@ struct pic_ctx {
   long long *total;
   void *scan_scratch;
   double *diag;             // 8 doubles
+  // per-step diagnostics (pic_diag_average): node counts of the step, their
+  // sums, node charge after the previous step, continuity residual of the
+  // last step, wall tallies at the window's start and after the previous step
+  int diag_on, cres_valid;
+  long long diag_steps;
+  double *dcnt, *dacc, *qprev, *cres, *wall0, *wallp;
   double numax_e, gmax, pnull_e, pnull_i;
   long long launches;       // kernels enqueued by this context (host count)
   // optional timing of the push launches (CUDA events on the context stream)
@@ -132,6 +146,7 @@ enum {
   kHnMcc = 18,    // 8: collision counts
   kHnDe = 26,     // collision energy change
   kHnIz = 27,     // ionization pairs of the MCC pass
+  kHnKerr = 28,   // kernels that gave up a bounded wait
   kHnSlots = 32
 };
 
@@ -248,15 +263,22 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
       P.id = (uint32_t *)K.take(pc * 4);
     }
   const size_t qc = pc + (size_t)kMaxFastBlocks * 256;  // queue entries
-  x->queue = (int *)K.take(qc * 4);
-  x->qblock = (int *)K.take((size_t)2 * kMaxFastBlocks * 4);  // front and back counts
   if (c->precision == PIC_MIXED) {
+    // the FP32 kernel finishes its crossers inside each tile; it only lists
+    // the near-axis crossers it hands to FP64 arithmetic
+    x->queue = nullptr;
+    x->qblock = nullptr;
+    x->plist[0] = (int *)K.take((size_t)pc * 4);
+    x->plist[1] = (int *)K.take((size_t)pc * 4);
+    x->pcnt = (unsigned *)K.take(256);
     for (int s = 0; s < 2; ++s) {
       x->alpha.ar[s] = (float *)K.take(ner * 4);
       x->alpha.az[s] = (float *)K.take(nez * 4);
     }
-    for (int k = 0; k < 2; ++k) x->q_real[k] = (float *)K.take(qc * 4);
+    for (int k = 0; k < 2; ++k) x->q_real[k] = nullptr;
   } else {
+    x->queue = (int *)K.take(qc * 4);
+    x->qblock = (int *)K.take((size_t)2 * kMaxFastBlocks * 4);  // front and back counts
     for (int s = 0; s < 2; ++s) {
       x->alpha64.ar[s] = (double *)K.take(ner * 8);
       x->alpha64.az[s] = (double *)K.take(nez * 8);
@@ -344,6 +366,15 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
   long long sn = pc > ncell + 1 ? pc : ncell + 1;
   x->scan_scratch = K.take(scan_scratch_bytes(sn));
   x->diag = (double *)K.take(8 * 8);
+  {
+    const size_t nn = (size_t)(nr + 1) * (nz + 1), nwall = (size_t)2 * (2 * (nr + 1) + nz + 1);
+    x->dcnt = (double *)K.take(2 * nn * 8);
+    x->dacc = (double *)K.take(2 * nn * 8);
+    x->qprev = (double *)K.take(nn * 8);
+    x->cres = (double *)K.take(nn * 8);
+    x->wall0 = (double *)K.take(nwall * 8);
+    x->wallp = (double *)K.take(nwall * 8);
+  }
   K.take(0);
   *used = K.off;
   return K.ok;
@@ -431,6 +462,18 @@ void fill_push(pic_ctx *x, int s, double q, double m, const double *erh, const d
   L.counters = counters;
   L.ke_lost = kel;
   L.hist = (write && x->hist_on) ? x->hist : nullptr;
+  L.kerr = &x->cnt->kerr;
+  L.dt = dt;
+  L.icr64 = x->g.dr / dt;
+  L.icz64 = x->g.dz / dt;
+  L.cz64 = dt / x->g.dz;
+  L.rm64.xa = x->g.xa;
+  L.rm64.cr = dt / x->g.dr;
+  L.rm64.icr = x->g.dr / dt;
+  L.rm64.rho0x = x->rmap64;
+  L.rm64.crx = x->rmap64 + kMaxAxisCells;
+  L.rm64.icrx = x->rmap64 + 2 * kMaxAxisCells;
+  L.pcnt = nullptr;
 }
 
 template <typename T>
@@ -448,6 +491,7 @@ int push_all(pic_ctx *x, const double *erh, const double *ezh, double *ir, doubl
   bool timed = x->prof && x->nev < 128 && !x->capturing;
   if (timed) cudaEventRecord(x->ev[2 * x->nev], x->s);
   const int nsp = x->cfg.ions_fixed ? 1 : 2;
+  bool forked = false;
   for (int s = 0; s < nsp; ++s) {
     const double q = s == 0 ? -kQE : kQE, m = s == 0 ? kME : kMAr;
     double *ws[3] = {nullptr, nullptr, nullptr};
@@ -470,9 +514,24 @@ int push_all(pic_ctx *x, const double *erh, const double *ezh, double *ir, doubl
       if (L.hist && oop) L.hist = x->hist_spec;  // counted once the pass is adopted
       L.ar = x->alpha.ar[s];
       L.az = x->alpha.az[s];
-      set_queue(x, x->q_real, L);
+      L.queue = x->plist[s];
+      L.qblock = nullptr;
+      L.q_da = L.q_db = nullptr;
+      L.pcnt = x->pcnt + s;
       fast = L.wbt == 0.f;
       e = launch_push(L, x->s);
+      if (e == cudaSuccess) {
+        if (s == 0 && nsp == 2 && x->pstream_made) {
+          // the electrons' near-axis list on the side stream, beside the ions
+          e = cudaEventRecord(x->pev[0], x->s);
+          if (e == cudaSuccess) e = cudaStreamWaitEvent(x->pstream, x->pev[0], 0);
+          if (e == cudaSuccess) e = launch_push_fp32_axis(L, x->pstream);
+          if (e == cudaSuccess) e = cudaEventRecord(x->pev[1], x->pstream);
+          forked = e == cudaSuccess;
+        } else {
+          e = launch_push_fp32_axis(L, x->s);
+        }
+      }
     } else {
       PushLaunchT<double> L;
       fill_push(x, s, q, m, erh, ezh, ir, iz, write, counters, kel, ws, L);
@@ -492,9 +551,74 @@ int push_all(pic_ctx *x, const double *erh, const double *ezh, double *ir, doubl
       if (timed) x->pending_launches += 1;
     }
   }
+  if (forked && cudaStreamWaitEvent(x->s, x->pev[1], 0) != cudaSuccess) return PIC_E_CUDA;
   if (timed) {
     cudaEventRecord(x->ev[2 * x->nev + 1], x->s);
     x->nev += 1;
+  }
+  return PIC_OK;
+}
+
+// Per-step diagnostics of one node t (pic_diag_average): adds the node counts
+// of the step (cnt: electrons, then ions; sums of w S1 x S1) to the averages,
+// and forms the node's charge balance over the step: the change of the
+// particles' node charge and of the wall tallies on the node, plus the net
+// crossed charge leaving its dual cell (Eq. 3).  init: only the node charge.
+__global__ void k_diag_step(int nr, int nz, int i0, const double *cnt, double *acc,
+                            const double *ir, const double *iz, const double *wall,
+                            const double *wallp, double *qprev, double *cres, int init) {
+  const int nz1 = nz + 1;
+  const long long nn = (long long)(nr + 1) * nz1;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nn) return;
+  const int i = (int)(t / nz1), j = (int)(t - (t / nz1) * nz1);
+  const double ce = cnt[t], ci = cnt[nn + t];
+  const double Q = kQE * ci - kQE * ce;
+  if (!init) {
+    acc[t] += ce;
+    acc[nn + t] += ci;
+    const long long blk = 2LL * (nr + 1) + nz1;
+    double dW = 0.0;
+    for (int sp = 0; sp < 2; ++sp) {
+      const long long b = sp * blk;
+      if (j == 0) dW += wall[b + i] - wallp[b + i];
+      if (j == nz) dW += wall[b + nr + 1 + i] - wallp[b + nr + 1 + i];
+      if (i == i0) dW += wall[b + 2 * (nr + 1) + j] - wallp[b + 2 * (nr + 1) + j];
+    }
+    double div = 0.0;
+    if (i < nr) div += ir[(long long)i * nz1 + j];
+    if (i > 0) div -= ir[(long long)(i - 1) * nz1 + j];
+    if (j < nz) div += iz[(long long)i * nz + j];
+    if (j > 0) div -= iz[(long long)i * nz + j - 1];
+    cres[t] = (Q - qprev[t]) + dW + div;
+  }
+  qprev[t] = Q;
+}
+
+// node counts (sums of w S1 x S1) of both species into dcnt, then the step's
+// diagnostics (init: only the node charge, at the start of a window)
+int diag_step(pic_ctx *x, int init) {
+  const int nr = x->g.nr, nz = x->g.nz;
+  const size_t nn = (size_t)(nr + 1) * (nz + 1), nwall = (size_t)2 * (2 * (nr + 1) + nz + 1);
+  cudaStream_t s = x->s;
+  if (cudaMemsetAsync(x->dcnt, 0, 2 * nn * 8, s) != cudaSuccess) return PIC_E_CUDA;
+  for (int sp = 0; sp < 2; ++sp) {
+    cudaError_t e = x->mixed ? launch_node_charge(x->g, as32(cur(x, sp)), x->n[sp], 1.0,
+                                                  x->dcnt + sp * nn, s)
+                             : launch_node_charge(x->g, cur(x, sp), x->n[sp], 1.0,
+                                                  x->dcnt + sp * nn, s);
+    if (e != cudaSuccess) return PIC_E_CUDA;
+  }
+  k_diag_step<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(nr, nz, nr - x->g.nd, x->dcnt, x->dacc,
+                                                           x->ir, x->iz, x->wall, x->wallp,
+                                                           x->qprev, x->cres, init);
+  if (cudaGetLastError() != cudaSuccess) return PIC_E_CUDA;
+  if (cudaMemcpyAsync(x->wallp, x->wall, nwall * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return PIC_E_CUDA;
+  x->launches += 4;
+  if (!init) {
+    x->diag_steps += 1;
+    x->cres_valid = 1;
   }
   return PIC_OK;
 }
@@ -795,9 +919,21 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
   if (e == cudaSuccess) e = cudaMemsetAsync(x->hist, 0, 16 * 8, x->s);
   if (e == cudaSuccess) e = cudaMemsetAsync(x->cnt, 0, sizeof(DevCounters), x->s);
   if (e == cudaSuccess) e = cudaHostAlloc((void **)&x->hn, 8 * kHnSlots, cudaHostAllocDefault);
+  if (e == cudaSuccess && x->mixed) {
+    // side stream of the electrons' near-axis FP64 list (runs beside the ions)
+    e = cudaStreamCreateWithFlags(&x->pstream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x->pev[0], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x->pev[1], cudaEventDisableTiming);
+    if (e == cudaSuccess) x->pstream_made = 1;
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(x->s);
   if (e != cudaSuccess) {
     if (x->hn) cudaFreeHost(x->hn);
+    if (x->pstream_made) {
+      cudaEventDestroy(x->pev[0]);
+      cudaEventDestroy(x->pev[1]);
+      cudaStreamDestroy(x->pstream);
+    }
     free(x);
     return PIC_E_CUDA;
   }
@@ -845,6 +981,12 @@ void pic_destroy(pic_ctx *ctx) {
   if (ctx->prof) {
     cudaStreamSynchronize(ctx->s);
     for (int k = 0; k < 2 * 128; ++k) cudaEventDestroy(ctx->ev[k]);
+  }
+  if (ctx->pstream_made) {
+    cudaStreamSynchronize(ctx->pstream);
+    cudaEventDestroy(ctx->pev[0]);
+    cudaEventDestroy(ctx->pev[1]);
+    cudaStreamDestroy(ctx->pstream);
   }
   free(ctx);
 }
@@ -1564,6 +1706,8 @@ int step_end(pic_ctx *x, StepState &T, int *rc) {
     return PIC_E_CUDA;
   if (cudaMemcpyAsync(x->hn + kHnKel, &x->cnt->ke_lost, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return PIC_E_CUDA;
+  if (cudaMemcpyAsync(x->hn + kHnKerr, &x->cnt->kerr, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return PIC_E_CUDA;
   if (x->cfg.mcc_on &&
       cudaMemcpyAsync(x->hn + kHnDe, &x->cnt->de_coll, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return PIC_E_CUDA;
@@ -1571,6 +1715,14 @@ int step_end(pic_ctx *x, StepState &T, int *rc) {
   if (sr) return sr;
   if (cudaStreamSynchronize(s) != cudaSuccess) return PIC_E_CUDA;
   sort_finish(x);
+  unsigned long long kerr = 0;
+  memcpy(&kerr, x->hn + kHnKerr, 8);
+  if (kerr) {
+    // a kernel timed out on one of its bounded waits: the step's results are
+    // not trustworthy; the count is cleared for the next call
+    cudaMemsetAsync(&x->cnt->kerr, 0, 8, s);
+    return PIC_E_CUDA;
+  }
   unsigned long long pc[5];
   double kel = 0.0;
   double cst[4] = {0.0, 0.0, T.v1, 0.0};
@@ -1589,6 +1741,11 @@ int step_end(pic_ctx *x, StepState &T, int *rc) {
   S.v_electrode = cst[2];
   S.n[0] = x->n[0];
   S.n[1] = x->n[1];
+  if (x->diag_on) {
+    // the committed step's crossed charge is still in ir / iz
+    int dr = diag_step(x, 0);
+    if (dr) return dr;
+  }
   S.launches = x->launches - T.l0;
   x->step += 1;
   if (S.substep_err && !*rc) *rc = PIC_E_SUBSTEP;
@@ -1648,6 +1805,129 @@ int pic_diag(pic_ctx *x, pic_diag_out *out) {
   out->n[0] = x->n[0];
   out->n[1] = x->n[1];
   return PIC_OK;
+}
+
+int pic_diag_average(pic_ctx *x, int enable) {
+  if (!x || enable < 0 || enable > 1) return PIC_E_CONFIG;
+  if (!enable) {
+    x->diag_on = 0;
+    return PIC_OK;
+  }
+  const size_t nn = (size_t)(x->g.nr + 1) * (x->g.nz + 1);
+  const size_t nwall = (size_t)2 * (2 * (x->g.nr + 1) + x->g.nz + 1);
+  if (cudaMemsetAsync(x->dacc, 0, 2 * nn * 8, x->s) != cudaSuccess ||
+      cudaMemcpyAsync(x->wall0, x->wall, nwall * 8, cudaMemcpyDeviceToDevice, x->s) != cudaSuccess)
+    return PIC_E_CUDA;
+  x->diag_steps = 0;
+  x->cres_valid = 0;
+  int r = diag_step(x, 1);
+  if (r) return r;
+  x->diag_on = 1;
+  return PIC_OK;
+}
+
+int pic_diag_get(pic_ctx *x, int kind, void *dst, size_t bytes, int dst_is_device) {
+  if (!x || !dst) return PIC_E_CONFIG;
+  const int nr = x->g.nr, nz = x->g.nz;
+  const size_t nn = (size_t)(nr + 1) * (nz + 1);
+  const size_t ner = (size_t)nr * (nz + 1), nez = (size_t)(nr + 1) * nz, nh = (size_t)nr * nz;
+  const size_t nwall = (size_t)2 * (2 * (nr + 1) + nz + 1);
+  cudaStream_t s = x->s;
+  const cudaMemcpyKind to = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  auto finish = [&]() { return cudaStreamSynchronize(s) == cudaSuccess ? PIC_OK : PIC_E_CUDA; };
+  // host-computed results go out through this buffer
+  std::vector<double> hv;
+  auto put_host = [&](const void *src, size_t nb) -> int {
+    if (dst_is_device) {
+      if (cudaMemcpyAsync(dst, src, nb, cudaMemcpyHostToDevice, s) != cudaSuccess) return PIC_E_CUDA;
+      return finish();
+    }
+    memcpy(dst, src, nb);
+    return PIC_OK;
+  };
+  // dual volume / electrode area of a node: the ring between the neighbouring
+  // cell centres (the axis disc, the half ring at r = R), times the z extent
+  auto ring = [&](int i) {
+    const double lo = i == 0 ? 0.0 : g_rcentre(x->g, i - 1);
+    const double hi = i == nr ? g_rnode(x->g, nr) : g_rcentre(x->g, i);
+    return kPi * (hi * hi - lo * lo);
+  };
+  switch (kind) {
+    case PIC_DIAG_ENERGY: {
+      if (dst_is_device || bytes < sizeof(pic_diag_out)) return PIC_E_CONFIG;
+      return pic_diag(x, (pic_diag_out *)dst);
+    }
+    case PIC_DIAG_GAUSS: {
+      if (bytes < nn * 8) return PIC_E_CONFIG;
+      int r = pic_gauss_residual(x, x->dcnt);
+      if (r) return r;
+      if (cudaMemcpyAsync(dst, x->dcnt, nn * 8, to, s) != cudaSuccess) return PIC_E_CUDA;
+      return finish();
+    }
+    case PIC_DIAG_CONTINUITY: {
+      if (bytes < nn * 8) return PIC_E_CONFIG;
+      if (!x->cres_valid) return PIC_E_STATE;
+      if (cudaMemcpyAsync(dst, x->cres, nn * 8, to, s) != cudaSuccess) return PIC_E_CUDA;
+      return finish();
+    }
+    case PIC_DIAG_DENSITY_AVG: {
+      if (bytes < 2 * nn * 8) return PIC_E_CONFIG;
+      if (x->diag_steps < 1) return PIC_E_STATE;
+      hv.resize(2 * nn);
+      if (cudaMemcpyAsync(hv.data(), x->dacc, 2 * nn * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return PIC_E_CUDA;
+      int r = finish();
+      if (r) return r;
+      for (int i = 0; i <= nr; ++i) {
+        const double a = ring(i);
+        for (int j = 0; j <= nz; ++j) {
+          const double v = a * ((j == 0 || j == nz) ? 0.5 : 1.0) * x->g.dz;
+          for (int sp = 0; sp < 2; ++sp) {
+            double &d = hv[sp * nn + (size_t)i * (nz + 1) + j];
+            d = d / ((double)x->diag_steps * v);
+          }
+        }
+      }
+      return put_host(hv.data(), 2 * nn * 8);
+    }
+    case PIC_DIAG_ION_FLUX_AVG: {
+      if (bytes < 2 * (size_t)(nr + 1) * 8) return PIC_E_CONFIG;
+      if (x->diag_steps < 1) return PIC_E_STATE;
+      std::vector<double> w1(nwall), w0(nwall);
+      if (cudaMemcpyAsync(w1.data(), x->wall, nwall * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaMemcpyAsync(w0.data(), x->wall0, nwall * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return PIC_E_CUDA;
+      int r = finish();
+      if (r) return r;
+      const size_t blk = 2 * (size_t)(nr + 1) + nz + 1;  // ions: the second species block
+      const double tw = (double)x->diag_steps * x->cfg.dt;
+      hv.resize(2 * (size_t)(nr + 1));
+      for (int e = 0; e < 2; ++e)
+        for (int i = 0; i <= nr; ++i) {
+          const size_t k = blk + (size_t)e * (nr + 1) + i;
+          hv[(size_t)e * (nr + 1) + i] = (w1[k] - w0[k]) / (kQE * tw * ring(i));
+        }
+      return put_host(hv.data(), hv.size() * 8);
+    }
+    case PIC_DIAG_FIELDS: {
+      const size_t nb = (ner + nez + nh) * 8;
+      if (bytes < nb) return PIC_E_CONFIG;
+      char *d = (char *)dst;
+      if (cudaMemcpyAsync(d, x->er, ner * 8, to, s) != cudaSuccess ||
+          cudaMemcpyAsync(d + ner * 8, x->ez, nez * 8, to, s) != cudaSuccess ||
+          cudaMemcpyAsync(d + (ner + nez) * 8, x->h, nh * 8, to, s) != cudaSuccess)
+        return PIC_E_CUDA;
+      return finish();
+    }
+    case PIC_DIAG_COUNTS: {
+      if (bytes < 4 * sizeof(long long)) return PIC_E_CONFIG;
+      const long long c[4] = {x->n[0], x->n[1], x->step, x->diag_steps};
+      if (cudaStreamSynchronize(s) != cudaSuccess) return PIC_E_CUDA;
+      return put_host(c, sizeof(c));
+    }
+    default:
+      return PIC_E_CONFIG;
+  }
 }
 
 int pic_node_charge(pic_ctx *x, double *q) {

@@ -146,7 +146,7 @@ struct DevCounters {
   double norm[2];              // Picard: sum (E_new - E_it)^2, sum E_new^2
   double src;                  // drive-gap energy of the last solve
   unsigned long long iz_slots; // MCC: ionization keys written
-  double pad[1];
+  unsigned long long kerr;     // kernels that gave up a bounded wait (a copy that never landed)
 };
 
 // Field operator (separable direct solve of the H_theta system)
@@ -247,7 +247,20 @@ struct PushLaunchT {
   T *q_da, *q_db;          // queued particle's converged whole-step trial (NaN: none);
                            // its start state is re-read from the store, which the
                            // fast kernel leaves untouched for queued particles
+  unsigned long long *kerr;  // counts bounded waits that timed out (device; never null)
+  // FP32 store: crossers that start in the first kPromoteRows radial cells are
+  // listed (queue[0 .. *pcnt)) and pushed by a second kernel in FP64
+  // arithmetic (double scales from dt and the grid, radial tables rm64)
+  unsigned *pcnt;
+  double dt;
+  double icr64, icz64, cz64;  // dr/dt, dz/dt, dt/dz in double
+  RadialMapT<double> rm64;
 };
+// radial cells next to the axis whose FP32 crossers with a large angular step
+// take FP64 arithmetic: there the centrifugal term of Eq. 4 grows like 1/r and
+// amplifies FP32 rounding
+constexpr int kPromoteRows = 1;
+constexpr float kPromoteRho = 0.125f;  // cells
 // Electrostatic field model (Eq. 8) on the same mesh: potential on the
 // nodes, Gauss's law on the interior nodes (i < nr, 0 < j < nz), separable:
 // orthonormal DST-I along z (GEMM), cyclic reduction along r (field.cu)
@@ -316,6 +329,9 @@ cudaError_t launch_guess_target(const GuessArgs &A, const double *er_next, const
 constexpr int kMaxFastBlocks = 152 * 8;
 template <typename T>
 cudaError_t launch_push(const PushLaunchT<T> &L, cudaStream_t s);
+// FP32 store: the near-axis crossers launch_push listed, pushed in FP64
+// arithmetic (a second launch after it; nothing with an external B_z)
+cudaError_t launch_push_fp32_axis(const PushLaunchT<float> &L, cudaStream_t s);
 // one resident wave of the persistent push kernels (blocks of 256 threads)
 int push_wave_fp64(int general);
 int push_wave_fp32(int general);

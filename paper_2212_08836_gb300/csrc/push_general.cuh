@@ -345,6 +345,33 @@ __device__ __forceinline__ bool landing_gen(const SubT<T> &s, T wt, int dir, T X
   return false;
 }
 
+// Start of a face landing: on the quadratic path x(s) = v0 s + alpha s^2/2
+// through the trial's end point x(tT) = dx (offsets in cells, s in steps),
+// the time of the first crossing of the face at offset X from the start.  A
+// face with X != 0 lies between the start and dx, so the path reaches it in
+// (0, tT]: the smaller positive root, which is exact for a constant
+// acceleration and keeps the solve on the first crossing of a grazing path.
+// X = 0 (the face the particle sits on): the nonzero root.
+template <typename T>
+__device__ __forceinline__ T first_crossing(T X, T dx, T v0, T tT) {
+  const T zero = (T)0, one = (T)1, two = (T)2, h = (T)0.5;
+  const T it = tT == one ? one : Num<T>::rcp(tT);
+  const T alpha = two * (dx - v0 * tT) * (it * it);
+  if (X == zero) return -two * v0 * Num<T>::rcp(alpha);
+  if (alpha == zero) return X * Num<T>::rcp(v0);
+  const T disc = v0 * v0 + two * alpha * X;
+  if (!(disc >= zero)) return tT * X * Num<T>::rcp(dx);
+  // roots of alpha/2 s^2 + v0 s - X = 0 without cancellation: qq/(alpha/2), -X/qq
+  const T sq = sqrt(disc);
+  const T qq = -h * (v0 + (v0 >= zero ? sq : -sq));
+  const T s1 = two * qq * Num<T>::rcp(alpha);
+  const T s2 = qq != zero ? -X * Num<T>::rcp(qq) : s1;
+  T sr = -one;
+  if (s1 > zero) sr = s1;
+  if (s2 > zero && (sr < zero || s2 < sr)) sr = s2;
+  return sr > zero ? sr : tT * X * Num<T>::rcp(dx);
+}
+
 // particle on a face of its cell with its normal velocity pointing out moves to
 // the neighbour cell; r = 0 reflects; walls absorb (1: r = R, 2: z = L, 3: z = 0)
 template <typename T>
@@ -440,21 +467,75 @@ __device__ __forceinline__ bool scalar_interior(const SubT<T> &s, T tau, T &pda,
   return true;
 }
 
+// Landing on a z-face without B_z through the scalar reduction of the
+// in-cell system (Eq. 4 in the normalised units above).  With the landing
+// offset db = X fixed, the r-equation of a sub-step of length tau is the
+// in-cell scalar equation in d = da with k1 = 1, K(tau) = tau ur + tau^2/2 Ar,
+// Ar = ar0 + gar (b + X/2), and ut -> tau ut (solved by fast_solve); the
+// z-equation F(tau) = tau uz + tau^2/2 (az0 + gaz (a + d/2)) - X = 0 is then one
+// equation in tau, solved by Newton with dF/dtau = uz + tau Az + tau^2/4 gaz
+// dd/dtau, dd/dtau ~ ur + tau (Ar + C(d)).  The root is that of the 2x2
+// landing system (landing_gen); false when the reduction does not apply
+// (close to the axis) or does not converge.
+template <typename T>
+__device__ __forceinline__ bool landing_z_scalar(const SubT<T> &s, T X, T t0, T &ptau, T &pda,
+                                                 unsigned &nit) {
+  typedef Num<T> N;
+  const T h = (T)0.5, q = (T)0.25, zero = (T)0, one = (T)1;
+  if (!(s.rho > zero)) return false;
+  const T Ar = s.ar0 + s.gar * (s.b + h * X);
+  const T aza = s.az0 + s.gaz * s.a;
+  const T ut2 = s.ut * s.ut;
+  T tau = t0, pct = zero;
+  for (int it = 0; it < kNewtonMaxGen; ++it) {
+    const T tut = tau * s.ut;
+    if (!(tau > zero) || !(fabs(tut) < q * s.rho)) return false;
+    T d;
+    if (!fast_solve<T>(s.rho, tut, tau * s.ur + h * tau * tau * Ar, one, d, nit)) return false;
+    const T Az = aza + h * s.gaz * d;
+    const T F = tau * s.uz + h * tau * tau * Az - X;
+    const T i1 = N::rcp(s.rho + d);
+    const T C = h * ut2 * (s.rho + s.rho + d) * (i1 * i1);
+    const T dF = s.uz + tau * Az + q * tau * tau * s.gaz * (s.ur + tau * (Ar + C));
+    if (!(dF != zero)) return false;
+    const T st = -F * N::rcp(dF);
+    tau += st;
+    if (!N::finite(tau)) return false;
+    const T ct = N::absb(st), tt = tol_x<T>(tau);
+    if (N::le(ct, tt) || contracted(ct, pct, tt)) {
+      // the radial offset at the converged tau (the last d belongs to the tau
+      // before the update)
+      const T tut1 = tau * s.ut;
+      if (!(tau > zero) || !(fabs(tut1) < q * s.rho) ||
+          !fast_solve<T>(s.rho, tut1, tau * s.ur + h * tau * tau * Ar, one, d, nit))
+        return false;
+      ptau = tau;
+      pda = d;
+      return true;
+    }
+    pct = ct;
+  }
+  return false;
+}
+
 struct Tally {
   unsigned err, abs, sub, fb, newton, snewton;  // snewton: scalar Newton iterations
 };
 
-template <typename T>
+// T: the arithmetic type of the path; S: the scalar type of the particle store
+// and of the accelerations (S = float, T = double: FP32 particles pushed in
+// FP64 arithmetic, results rounded to FP32 once at the end)
+template <typename T, typename S = T>
 struct GenArgs {
   int nr, nz;
-  const T *ar, *az;      // normalised accelerations of the species
+  const S *ar, *az;      // normalised accelerations of the species
   T wt, icr, icz, cz;    // qm*Bz*dt; dr/dt, dz/dt; dt/dz
   RadialMapT<T> rm;      // per-cell radial scales (mapped mesh)
   double q, m;
   T qf;                  // q in T
   double *ir, *iz;       // crossed charge [C]
   int write, oop;        // write the new state; out of place into dst
-  PartsT<T> p, dst;
+  PartsT<S> p, dst;
   double *wall_z0, *wall_zl, *wall_r;
   double *ke_lost;
   unsigned long long *hist;  // accepted sub-steps per particle, 16 bins (nullptr: off)
@@ -472,28 +553,21 @@ __device__ __forceinline__ void rescale_radial(const RadialMapT<T> &rm, int ic_o
   }
 }
 
-// one particle from its start state (offsets a, b; physical velocities);
-// (tr_da, tr_db): the converged interior solution of the whole step from a
-// start strictly inside the cell (NaN: none), which replaces the first
-// interior solve
-template <typename T, bool kB>
-__device__ void push_general(const GenArgs<T> &L, long long p, int c0, T a, T b, T vr0, T vt0,
-                             T vz0, const T w, T tr_da, T tr_db, Tally &Tl) {
+// The sub-step loop of one particle from a point of its step: cell (ic, jc),
+// offsets (a, b), normalised velocities, the time tau left of the step, nsub
+// sub-steps tried and nacc accepted so far; (tr_da, tr_db): the converged
+// interior solution of the next sub-step over tau from a start strictly inside
+// the cell (NaN: none).  Finishes the step: tallies and (write) the new state.
+template <typename T, bool kB, typename S = T>
+__device__ void push_sub(const GenArgs<T, S> &L, long long p, int ic, int jc, T a, T b, T ur,
+                         T ut, T uz, const T w, T tr_da, T tr_db, T tau, int nsub, int nacc,
+                         Tally &Tl) {
   const T zero = (T)0, one = (T)1, h = (T)0.5, two = (T)2;
   const int nr = L.nr, nz = L.nz, nz1 = nz + 1;
   const T wt = L.wt;
-  if (c0 < 0 || c0 >= nr * nz) {
-    if (L.write && L.oop) L.dst.cell[p] = c0;  // absorbed earlier: stays out of the store
-    return;
-  }
-  int ic = c0 / nz, jc = c0 - (c0 / nz) * nz;
-  const T cr0 = L.rm.crr(ic);
-  T ur = vr0 * cr0, ut = vt0 * cr0, uz = vz0 * L.cz;
-  T tau = one;
   T tT = tau;
-  int nsub = 0;
+  const int nsub0 = nsub;
   int ic_prev = ic;
-  int nacc = 0;  // accepted sub-steps of this particle
   int absorbed = transition_gen<T>(nr, nz, ic, jc, a, b, ur, uz);
   rescale_radial<T>(L.rm, ic_prev, ic, ur, ut);
   while (tau > zero && !absorbed) {
@@ -502,10 +576,10 @@ __device__ void push_general(const GenArgs<T> &L, long long p, int c0, T a, T b,
       break;
     }
     SubT<T> s;
-    s.ar0 = L.ar[ic * nz1 + jc];
-    s.gar = L.ar[ic * nz1 + jc + 1] - s.ar0;
-    s.az0 = L.az[ic * nz + jc];
-    s.gaz = L.az[(ic + 1) * nz + jc] - s.az0;
+    s.ar0 = (T)L.ar[ic * nz1 + jc];
+    s.gar = (T)L.ar[ic * nz1 + jc + 1] - s.ar0;
+    s.az0 = (T)L.az[ic * nz + jc];
+    s.gaz = (T)L.az[(ic + 1) * nz + jc] - s.az0;
     s.a = a; s.b = b;
     s.rho = L.rm.rho0(ic) + a;
     s.ur = ur; s.ut = ut; s.uz = uz;
@@ -514,7 +588,7 @@ __device__ void push_general(const GenArgs<T> &L, long long p, int c0, T a, T b,
     // tight: converged to half an ulp (scalar solves), so the CN velocity
     // relation u' = 2 dx / tau - u may replace an evaluation
     bool tight = true;
-    if (nsub == 1 && !Num<T>::nan_bits(tr_da)) {
+    if (nsub == nsub0 + 1 && !Num<T>::nan_bits(tr_da)) {
       da = tr_da;
       db = tr_db;
     } else if (!kB && scalar_interior<T>(s, tT, da, db, Tl.snewton)) {
@@ -546,16 +620,16 @@ __device__ void push_general(const GenArgs<T> &L, long long p, int c0, T a, T b,
         else continue;
         T X = face - x0;
         T v0 = dir == 0 ? ur : uz;
-        T g0;
-        if (X != zero) {
-          g0 = tT * X * Num<T>::rcp(dx);
-        } else {  // quadratic model through the trial end point
-          T alpha = two * (dx - v0 * tT) * (tT == one ? one : Num<T>::rcp(tT * tT));
-          g0 = -two * v0 * Num<T>::rcp(alpha);
-        }
+        const T g0 = first_crossing<T>(X, dx, v0, tT);
         T oth0 = doth * (g0 * (tT == one ? one : Num<T>::rcp(tT)));
         T tt = zero, toth = zero;
-        if (!(g0 > zero) || !landing_gen<T, kB>(s, wt, dir, X, g0, oth0, tt, toth, Tl.newton)) continue;
+        if (!(g0 > zero)) continue;
+        // a z-face (most crossings: cells are flat in z) through the scalar
+        // reduction, else (or if it does not apply) the 2x2 landing system
+        if (!(!kB && dir == 1 && X != zero &&
+              landing_z_scalar<T>(s, X, g0, tt, toth, Tl.snewton)) &&
+            !landing_gen<T, kB>(s, wt, dir, X, g0, oth0, tt, toth, Tl.newton))
+          continue;
         if (!(tt > zero) || tt > tT) continue;
         T xo = (dir == 0 ? b : a) + toth;
         if (xo < zero || xo > one) continue;
@@ -650,10 +724,152 @@ __device__ void push_general(const GenArgs<T> &L, long long p, int c0, T a, T b,
   }
   if (L.write) {
     L.dst.cell[p] = absorbed ? -1 : ic * nz + jc;
-    L.dst.a[p] = a; L.dst.b[p] = b;
-    L.dst.vr[p] = vr; L.dst.vt[p] = vt; L.dst.vz[p] = vz;
+    L.dst.a[p] = (S)a; L.dst.b[p] = (S)b;
+    L.dst.vr[p] = (S)vr; L.dst.vt[p] = (S)vt; L.dst.vz[p] = (S)vz;
     if (L.oop) {
-      L.dst.w[p] = w;
+      L.dst.w[p] = (S)w;
+      L.dst.id[p] = L.p.id[p];
+    }
+  }
+}
+
+// one particle from its start state (offsets a, b; physical velocities);
+// (tr_da, tr_db): the converged interior solution of the whole step from a
+// start strictly inside the cell (NaN: none), which replaces the first
+// interior solve
+template <typename T, bool kB, typename S = T>
+__device__ void push_general(const GenArgs<T, S> &L, long long p, int c0, T a, T b, T vr0, T vt0,
+                             T vz0, const T w, T tr_da, T tr_db, Tally &Tl) {
+  const int nr = L.nr, nz = L.nz;
+  if (c0 < 0 || c0 >= nr * nz) {
+    if (L.write && L.oop) L.dst.cell[p] = c0;  // absorbed earlier: stays out of the store
+    return;
+  }
+  const int ic = c0 / nz, jc = c0 - (c0 / nz) * nz;
+  const T cr0 = L.rm.crr(ic);
+  push_sub<T, kB, S>(L, p, ic, jc, a, b, vr0 * cr0, vt0 * cr0, vz0 * L.cz, w, tr_da, tr_db, (T)1,
+                     0, 0, Tl);
+}
+
+// the four face charges of one accepted sub-step (da, db) from (a, b) in cell
+// (ic, jc): Eq. 3 with m = 1 in flux form (reading of the deposit)
+template <typename T, typename S>
+__device__ __forceinline__ void deposit_sub(const GenArgs<T, S> &L, int ic, int jc, T w, T a, T b,
+                                            T da, T db) {
+  if (!L.ir) return;
+  const T h = (T)0.5, one = (T)1;
+  const int nz = L.nz, nz1 = nz + 1;
+  const T am = a + h * da, bm = b + h * db;
+  const T fr = L.qf * w * da, fz = L.qf * w * db;
+  atomicAdd(&L.ir[ic * nz1 + jc], Num<T>::to_double(fr * (one - bm)));
+  atomicAdd(&L.ir[ic * nz1 + jc + 1], Num<T>::to_double(fr * bm));
+  atomicAdd(&L.iz[ic * nz + jc], Num<T>::to_double(fz * (one - am)));
+  atomicAdd(&L.iz[(ic + 1) * nz + jc], Num<T>::to_double(fz * am));
+}
+
+// A crosser without B_z whose converged whole-step trial (tr_da, tr_db) keeps
+// its radial offset inside the cell and leaves it through one z-face (cells
+// are flat in z: most crossings), as straight-line code: the landing on that
+// face (landing_z_scalar), the transition to the next cell and the rest of the
+// step there through the in-cell scalar solve, so that a warp of such crossers
+// runs converged.  The steps and their arithmetic are those of the sub-step
+// loop for it; at any other turn (a landing that fails or leaves the cell, a
+// wall, a solve that fails, a second crossing, an end on a face) the particle
+// goes on through push_sub from where it stands.
+template <typename T, typename S = T>
+__device__ void push_zcross(const GenArgs<T, S> &L, long long p, int c0, T a, T b, T vr0, T vt0,
+                            T vz0, const T w, T tr_da, T tr_db, Tally &Tl) {
+  typedef Num<T> N;
+  const T zero = (T)0, one = (T)1, two = (T)2;
+  const int nr = L.nr, nz = L.nz, nz1 = nz + 1;
+  if (c0 < 0 || c0 >= nr * nz) {
+    if (L.write && L.oop) L.dst.cell[p] = c0;  // absorbed earlier: stays out of the store
+    return;
+  }
+  int ic = c0 / nz, jc = c0 - (c0 / nz) * nz;
+  const T cr0 = L.rm.crr(ic);
+  T ur = vr0 * cr0, ut = vt0 * cr0, uz = vz0 * L.cz;
+  // ---- sub-step 1: the landing on the z-face the trial leaves through
+  SubT<T> s;
+  s.ar0 = (T)L.ar[ic * nz1 + jc];
+  s.gar = (T)L.ar[ic * nz1 + jc + 1] - s.ar0;
+  s.az0 = (T)L.az[ic * nz + jc];
+  s.gaz = (T)L.az[(ic + 1) * nz + jc] - s.az0;
+  s.a = a; s.b = b;
+  s.rho = L.rm.rho0(ic) + a;
+  s.ur = ur; s.ut = ut; s.uz = uz;
+  s.P = s.rho * ut;
+  const T face = b + tr_db > one ? one : zero;
+  const T X = face - b;
+  const T g0 = first_crossing<T>(X, tr_db, uz, one);
+  T tt = zero, da = zero;
+  if (!N::in01(a) || !N::in01(b) || !(g0 > zero) ||
+      !landing_z_scalar<T>(s, X, g0, tt, da, Tl.snewton) || !(tt > zero) || tt > one ||
+      !(a + da >= zero && a + da <= one)) {
+    push_sub<T, false, S>(L, p, ic, jc, a, b, ur, ut, uz, w, tr_da, tr_db, one, 0, 0, Tl);
+    return;
+  }
+  {
+    ResT<T> o;
+    eval_gen<T, false>(s, zero, da, X, tt, o);
+    deposit_sub<T, S>(L, ic, jc, w, a, b, da, X);
+    a = fmin(fmax(a + da, zero), one);
+    b = face;
+    ur = ur + tt * o.A;
+    uz = uz + tt * o.az;
+    ut = o.ut1;
+    Tl.sub++;
+  }
+  const T tau = one - tt;
+  // ---- through the landed face into the next cell (a wall: the loop)
+  const bool up = face == one;
+  if (!N::in01(a) || (up ? !(uz > zero) || jc + 1 == nz : !(uz < zero) || jc == 0) ||
+      !(tau > zero)) {
+    push_sub<T, false, S>(L, p, ic, jc, a, b, ur, ut, uz, w, (T)NAN, (T)NAN, tau, 1, 1, Tl);
+    return;
+  }
+  jc += up ? 1 : -1;
+  b = up ? zero : one;
+  // ---- sub-step 2: the rest of the step inside the next cell
+  SubT<T> s2;
+  s2.ar0 = (T)L.ar[ic * nz1 + jc];
+  s2.gar = (T)L.ar[ic * nz1 + jc + 1] - s2.ar0;
+  s2.az0 = (T)L.az[ic * nz + jc];
+  s2.gaz = (T)L.az[(ic + 1) * nz + jc] - s2.az0;
+  s2.a = a; s2.b = b;
+  s2.rho = L.rm.rho0(ic) + a;
+  s2.ur = ur; s2.ut = ut; s2.uz = uz;
+  s2.P = s2.rho * ut;
+  T da2 = zero, db2 = zero;
+  const bool in2 = scalar_interior<T>(s2, tau, da2, db2, Tl.snewton);
+  const T a2 = a + da2, b2 = b + db2;
+  if (!in2 || !(a2 >= zero && a2 <= one && b2 >= zero && b2 <= one) || !(s2.rho + da2 > zero)) {
+    push_sub<T, false, S>(L, p, ic, jc, a, b, ur, ut, uz, w, (T)NAN, (T)NAN, tau, 1, 1, Tl);
+    return;
+  }
+  {
+    const T it = tau == one ? one : N::rcp(tau);
+    const T nur = two * da2 * it - ur, nuz = two * db2 * it - uz;
+    const T nut = s2.P * N::rcp(s2.rho + da2);
+    deposit_sub<T, S>(L, ic, jc, w, a, b, da2, db2);
+    a = fmin(fmax(a2, zero), one);
+    b = fmin(fmax(b2, zero), one);
+    ur = nur; uz = nuz; ut = nut;
+    Tl.sub++;
+  }
+  if (!N::in01(a) || !N::in01(b)) {
+    // ended on a face: the loop moves it (or absorbs it) and finishes
+    push_sub<T, false, S>(L, p, ic, jc, a, b, ur, ut, uz, w, (T)NAN, (T)NAN, zero, 2, 2, Tl);
+    return;
+  }
+  if (L.hist) atomicAdd(&L.hist[1], 1ull);  // two accepted sub-steps
+  if (L.write) {
+    const T icr = L.rm.icrr(ic);
+    L.dst.cell[p] = ic * nz + jc;
+    L.dst.a[p] = (S)a; L.dst.b[p] = (S)b;
+    L.dst.vr[p] = (S)(ur * icr); L.dst.vt[p] = (S)(ut * icr); L.dst.vz[p] = (S)(uz * L.icz);
+    if (L.oop) {
+      L.dst.w[p] = (S)w;
       L.dst.id[p] = L.p.id[p];
     }
   }

@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_push_fast(PushL
 
 // queued particles (or all of them when queue == nullptr); blockDim 256
 template <typename T, bool kB>
-__global__ void __launch_bounds__(256) k_push_general(PushLaunchT<T> L) {
+__global__ void __launch_bounds__(256, 2) k_push_general(PushLaunchT<T> L) {
   const int lane = threadIdx.x & 31;
   GenArgs<T> G;
   G.nr = L.g.nr; G.nz = L.g.nz; G.ar = L.ar; G.az = L.az;
@@ -347,6 +347,22 @@ long long general_grid() {
 
 }  // namespace
 
+// every particle through the general path (external B_z, or no queue)
+template <typename T>
+cudaError_t launch_push_all(const PushLaunchT<T> &L, cudaStream_t s) {
+  const long long nsz = L.n_dev ? L.cap : L.n;
+  if (nsz <= 0) return cudaSuccess;
+  const int bs = 256;
+  long long nb = (nsz + bs - 1) / bs;
+  PushLaunchT<T> A = L;
+  A.queue = nullptr;
+  if (L.wbt == (T)0)
+    k_push_general<T, false><<<(unsigned)nb, bs, 0, s>>>(A);
+  else
+    k_push_general<T, true><<<(unsigned)nb, bs, 0, s>>>(A);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_push(const PushLaunchT<T> &L, cudaStream_t s) {
   // with the count on the device the grids depend only on the capacity, so a
@@ -369,15 +385,9 @@ cudaError_t launch_push(const PushLaunchT<T> &L, cudaStream_t s) {
     long long ng = L.ggrid > 0 ? L.ggrid : general_grid<T>();
     if (ng > nb) ng = nb;
     k_push_general<T, false><<<(unsigned)ng, bs, 0, s>>>(A);
-  } else {
-    PushLaunchT<T> A = L;
-    A.queue = nullptr;
-    if (L.wbt == (T)0)
-      k_push_general<T, false><<<(unsigned)nb, bs, 0, s>>>(A);
-    else
-      k_push_general<T, true><<<(unsigned)nb, bs, 0, s>>>(A);
+    return cudaGetLastError();
   }
-  return cudaGetLastError();
+  return launch_push_all<T>(L, s);
 }
 
 }  // namespace pic

@@ -115,3 +115,79 @@ def test_energies_match_oracle(precision, xa, ring):
         assert abs(d["kinetic"][s] - ref) <= 1e-12 * ref, (s, d["kinetic"][s], ref)
     ref_f = O.field_energy(g, er, ez, h)
     assert abs(d["field"] - ref_f) <= 1e-12 * ref_f, (d["field"], ref_f)
+
+
+def _dual_volume(g):
+    """Node dual volumes on the uniform mesh, written from their definition:
+    the ring between the neighbouring cell-centre radii (the axis disc, the
+    half ring at r = R) times dz (half on the electrodes)."""
+    dr, dz = g.R / g.nr, g.L / g.nz
+    rc = (np.arange(g.nr) + 0.5) * dr
+    lo = np.concatenate([[0.0], rc])
+    hi = np.concatenate([rc, [g.R]])
+    ring = np.pi * (hi ** 2 - lo ** 2)
+    zext = np.full(g.nz + 1, dz)
+    zext[0] = zext[-1] = 0.5 * dz
+    return ring, ring[:, None] * zext[None, :]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_averaged_density_and_ion_flux_match_their_definitions(precision):
+    """pic_diag_get(DENSITY_AVG) after k steps equals the mean over those steps
+    of the oracle's w S1 x S1 node sums of the states after each step divided
+    by the dual volume; ION_FLUX_AVG equals the ions' wall tally gained on each
+    electrode node over the window / (e dt k x its electrode ring)."""
+    M = P()
+    cfg = M.small_reactor(np_init=20000, volt=200.0, precision=precision, gas_pressure=5.0)
+    pic = M.Pic(cfg, device=DEV)
+    pic.load_particles()
+    pic.step(5)
+    g = O.Grid(cfg["nr"], cfg["nz"], cfg["R"], cfg["L"])
+    ring, vol = _dual_volume(g)
+    pic.diag_average(True)
+    w0 = pic.wall_charge()[1]
+    acc = np.zeros((2, g.nr + 1, g.nz + 1))
+    k = 4
+    for _ in range(k):
+        pic.step(1)
+        for s in range(2):
+            st = pic.get_state(s)
+            st = {kk: (v.astype(np.float64) if v.dtype == np.float32 else v) for kk, v in st.items()}
+            acc[s] += O.node_charge(g, 1.0, st).reshape(g.nr + 1, g.nz + 1)
+    dens = pic.diag_get(M.PIC_DIAG_DENSITY_AVG)
+    ref = acc / (k * vol)
+    np.testing.assert_allclose(dens, ref, rtol=1e-12, atol=1e-12 * ref.max())
+    w1 = pic.wall_charge()[1]
+    flux = pic.diag_get(M.PIC_DIAG_ION_FLUX_AVG)
+    for e, key in enumerate(("z0", "zl")):
+        fref = (w1[key] - w0[key]) / (O.QE * cfg["dt"] * k * ring)
+        np.testing.assert_allclose(flux[e], fref, rtol=1e-12, atol=1e-12 * max(abs(fref).max(), 1.0))
+    assert list(pic.diag_get(M.PIC_DIAG_COUNTS)[2:]) == [pic.view()["step"], k]
+
+
+@pytest.mark.parametrize("precision,ring", [(0, 0), (1, 0), (0, 4)])
+def test_continuity_residual_per_step(precision, ring):
+    """The per-node charge balance of every committed step (drive, collisions,
+    wall absorption, sticking on the ring's face): the particles' node charge
+    change plus the wall tallies' change plus the net crossed charge out of the
+    node's dual cell is zero to rounding (FP64: 1e-12, FP32 particles: 1e-6 of
+    the charge of a cell's electrons)."""
+    M = P()
+    kw = dict(np_init=20000, volt=300.0, precision=precision, gas_pressure=5.0)
+    if ring:
+        kw.update(ring_cells=ring, eps_ring=4.0)
+    cfg = M.small_reactor(**kw)
+    pic = M.Pic(cfg, device=DEV)
+    pic.load_particles()
+    pic.step(3)
+    pic.diag_average(True)
+    with pytest.raises(M.PicError):
+        pic.diag_get(M.PIC_DIAG_CONTINUITY)
+    q_scale = O.QE * float(np.max(pic.get_state(0)["w"])) * 20
+    absorbed = 0
+    for _ in range(4):
+        rc, st = pic.step(1, check=False)
+        absorbed += st["absorbed"]
+        res = pic.diag_get(M.PIC_DIAG_CONTINUITY)
+        assert np.max(np.abs(res)) <= (1e-12 if precision == 0 else 1e-6) * q_scale
+    assert absorbed > 0

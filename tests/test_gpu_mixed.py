@@ -2,7 +2,7 @@
 solve, current accumulation and diagnostics) against the FP64 oracle.
 
 The oracle receives the same FP32-rounded state (as FP64).  Stated
-tolerance of the FP32 path: 1e-5 relative per pass/step; positions are
+tolerance of the FP32 path: 1e-5 relative per pass/step, every particle; positions are
 compared in global logical coordinates (xi = ic + a), because a particle
 within ~1e-7 of a face may end on either side of it in FP32.
 """
@@ -61,9 +61,6 @@ def test_mixed_push_deposit_parity(nr, nz, n, dt):
     g = O.Grid(nr, nz, 0.05, 0.03)
     e = f32(inputs.particles(nr, nz, n, 1, 8e5))
     i = f32(inputs.particles(nr, nz, n, 2, 3e3))
-    # starts within 0.05 cells of the axis are pinned by the invariants test below:
-    # there the CN result depends strongly on where sub-steps split the step
-    e = {k: v[~((e["cell"] // nz == 0) & (e["a"] < 0.05))] for k, v in e.items()}
     er, ez = inputs.smooth_fields(nr, nz, 3, 3e3)
     pic = make_pic(nr, nz, 0.05, 0.03, dt, n)
     pic.set_state([e, i])
@@ -78,28 +75,24 @@ def test_mixed_push_deposit_parity(nr, nz, n, dt):
         s = {k: v.copy() for k, v in sp.items()}
         O.push(g, dt, q, m, s, er, ez, write=True, ir=ir_o, iz=iz_o)
         refs.append(s)
-    # edge sums of ~1e2 thermal fluxes of both signs amplify the 6e-8 per-particle
-    # FP32 error: 1e-5 in the L2 norm, 5e-5 of the largest edge in the max norm
+    # crossed charge per edge: 1e-5 of the largest edge, and in the L2 norm
     got_i = np.concatenate([ir.cpu().numpy(), iz.cpu().numpy()])
     ref_i = np.concatenate([ir_o, iz_o])
     assert np.linalg.norm(got_i - ref_i) <= TOL32 * np.linalg.norm(ref_i)
-    assert np.max(np.abs(got_i - ref_i)) <= 5 * TOL32 * np.max(np.abs(ref_i))
+    assert np.max(np.abs(got_i - ref_i)) <= TOL32 * np.max(np.abs(ref_i))
     for s in range(2):
         got = pic.get_state(s)
         x1, y1, al1 = gxy(got, nz)
         x0, y0, al0 = gxy(refs[s], nz)
-        assert np.mean(al1 != al0) <= 1e-3
-        both = al1 & al0
-        # per particle: 99.9 % within 1e-6 cells; the worst (several sub-steps close
-        # to the axis, where the centrifugal term amplifies FP32 rounding) within 5e-5
-        for d in (np.abs(x1 - x0)[both], np.abs(y1 - y0)[both]):
-            assert np.quantile(d, 0.999) <= 1e-6
-            assert np.max(d) <= 5 * TOL32
+        assert np.array_equal(al1, al0)
+        # every particle, near-axis starts included: positions within 1e-5 cells,
+        # velocities within 1e-5 of the largest speed
+        for d in (np.abs(x1 - x0)[al0], np.abs(y1 - y0)[al0]):
+            assert np.max(d) <= TOL32
         vs = max(np.max(np.abs(refs[s]["vr"])), np.max(np.abs(refs[s]["vz"])))
         for k in ("vr", "vt", "vz"):
-            d = np.abs(got[k].astype(np.float64) - refs[s][k])[both] / vs
-            assert np.quantile(d, 0.999) <= 1e-6
-            assert np.max(d) <= 5 * TOL32
+            d = np.abs(got[k].astype(np.float64) - refs[s][k])[al0] / vs
+            assert np.max(d) <= TOL32
 
 
 def test_mixed_continuity_and_gauss_on_gpu():
@@ -145,15 +138,20 @@ def test_mixed_full_step_vs_oracle():
         assert rc == 0 and rco == 0
         er, ez, h = pic.fields()
         for got, ref in ((er, sim.er), (ez, sim.ez), (h, sim.h)):
-            assert np.max(np.abs(got - ref)) <= 10 * TOL32 * np.max(np.abs(ref)), step
+            assert np.max(np.abs(got - ref)) <= TOL32 * np.max(np.abs(ref)), step
         for s in range(2):
             got, ref = pic.get_state(s), sim.state(s)
             og, orr = np.argsort(got["id"]), np.argsort(ref["id"])
             assert len(og) == len(orr)
-            xg, yg, _ = gxy({k: v[og] for k, v in got.items()}, nz)
-            xo, yo, _ = gxy({k: v[orr] for k, v in ref.items()}, nz)
-            assert np.max(np.abs(xg - xo)) <= 10 * TOL32
-            assert np.max(np.abs(yg - yo)) <= 10 * TOL32
+            G = {k: v[og] for k, v in got.items()}
+            Rf = {k: v[orr] for k, v in ref.items()}
+            xg, yg, _ = gxy(G, nz)
+            xo, yo, _ = gxy(Rf, nz)
+            assert np.max(np.abs(xg - xo)) <= TOL32
+            assert np.max(np.abs(yg - yo)) <= TOL32
+            vs = max(np.max(np.abs(Rf["vr"])), np.max(np.abs(Rf["vz"])))
+            for k in ("vr", "vt", "vz"):
+                assert np.max(np.abs(G[k].astype(np.float64) - Rf[k])) <= TOL32 * vs
 
 
 def test_mixed_energy_balance_on_gpu():
@@ -176,9 +174,8 @@ def test_mixed_energy_balance_on_gpu():
 def test_mixed_near_axis_invariants():
     """Particles within 1e-4..1e-1 cells of the axis with angular momentum,
     no field: the FP32 CN sub-steps keep |v| and r*v_theta exact to FP32
-    rounding and never cross the axis (centrifugal barrier).  Pointwise
-    parity is not the pin here: next to the axis the CN step is strongly
-    sensitive to where the sub-steps split it."""
+    rounding and never cross the axis (centrifugal barrier), and every
+    particle ends where the FP64 oracle puts it (1e-5)."""
     nr, nz, n, dt = 16, 24, 4000, 5e-10
     g = O.Grid(nr, nz, 0.05, 0.03)
     rng = np.random.default_rng(44)
@@ -210,3 +207,13 @@ def test_mixed_near_axis_invariants():
     L0 = x0 * e["vt"]
     L1 = x1 * got["vt"].astype(np.float64)
     np.testing.assert_allclose(L1, L0, rtol=1e-4, atol=1e-6 * np.max(np.abs(L0)))
+    ref = {k: v.copy() for k, v in e.items()}
+    er0, ez0, _ = g.zeros_fields()
+    O.push(g, dt, -QE, ME, ref, er0, ez0, write=True)
+    xr = (ref["cell"] // nz) + ref["a"]
+    yr = (ref["cell"] % nz) + ref["b"]
+    y1 = (got["cell"] % nz) + got["b"].astype(np.float64)
+    assert np.max(np.abs(x1 - xr)) <= TOL32
+    assert np.max(np.abs(y1 - yr)) <= TOL32
+    for k in ("vr", "vt", "vz"):
+        assert np.max(np.abs(got[k].astype(np.float64) - ref[k])) <= TOL32 * v
