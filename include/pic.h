@@ -450,6 +450,16 @@ int pic_sort_cells_noalloc(int nr, int nz, long long n, const int32_t *cell_dev,
 int pic_check_dmul(const double *x_dev, const double *y_dev, double *out_dev, long long n,
                    void *stream);
 
+/* Throughput probe of the GPU's FP64 FMA pipe, the bound of the plain form's
+ * mover.  The paper has no counterpart: it gives the measured peak that the
+ * FP64 roofline fraction is quoted against.  blocks_per_sm x SMs blocks of
+ * 256 threads each run 8 independent chains of `iters` fused multiply-adds on
+ * the legacy default stream (one warm-up launch, one timed with CUDA events);
+ * *seconds: the timed launch, *tflops: 2 flops per FMA over it.  Synchronises.
+ * Errors: PIC_E_CONFIG (blocks_per_sm outside 1..8, iters < 1, null
+ * outputs), PIC_E_CUDA. */
+int pic_probe_dfma(int blocks_per_sm, int iters, double *seconds, double *tflops);
+
 #ifdef __cplusplus
 }
 #endif

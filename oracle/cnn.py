@@ -134,6 +134,46 @@ def forward(params, x):
     return h, (acts, pres)
 
 
+def round_bf16(a):
+    """Nearest bfloat16 value of each element, as an FP64 array: the FP32 value
+    cut to its top 16 bits, rounded to nearest with ties to even (bfloat16 is
+    the upper half of the IEEE binary32 format)."""
+    b = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+# rounding allowances of forward_bf16's bound: an FP32 sum of K <= 9 x 64
+# products is within K 2^-24 of the sum of their magnitudes (2^-14 covers it),
+# and a bfloat16 step is at most 2^-7 of the value rounded
+FP32_SUM = 2.0 ** -14
+BF16_STEP = 2.0 ** -7
+
+
+def forward_bf16(params, x):
+    """The forward pass as the tensor-core kernels compute it: weights and
+    inputs already bfloat16 values, every hidden activation rounded to
+    bfloat16 after its ReLU, the last layer's output kept unrounded (sums in
+    FP64 here).  Returns (out, bound): an element-wise bound on the difference
+    from the same computation with FP32 sums in any order.  Per layer, a sum
+    is within FP32_SUM x (|w| * |h| + |b|) of the exact one plus the carried
+    difference of its inputs through |w|; the ReLU does not increase it; the
+    bfloat16 rounding of a value off by that much lands within the same
+    difference plus one bfloat16 step."""
+    h = np.asarray(x, dtype=np.float64)
+    e = np.zeros_like(h)
+    for k, (w, b) in enumerate(params):
+        z = conv3x3(h, w, b)
+        aw = np.abs(w)
+        ez = conv3x3(e, aw, np.zeros_like(b)) + FP32_SUM * conv3x3(np.abs(h), aw, np.abs(b))
+        if k + 1 < len(params):
+            h = round_bf16(np.maximum(z, 0.0))
+            e = ez + BF16_STEP * np.abs(h)
+        else:
+            h, e = z, ez
+    return h, e
+
+
 def loss(out, t, m):
     """Mean squared error over the valid points: sum m (out - t)^2 / sum m."""
     return float(np.sum(m * (out - t) ** 2) / np.sum(m))

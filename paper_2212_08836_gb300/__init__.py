@@ -113,6 +113,7 @@ def _load_lib():
     L.pic_mcc_constants.argtypes = [_P, _P, _P, _P, _P]
     L.pic_sort_cells_noalloc.argtypes = [_I, _I, _LL] + [_P] * 16 + [_P, _P]
     L.pic_check_dmul.argtypes = [_P, _P, _P, _LL, _P]
+    L.pic_probe_dfma.argtypes = [_I, _I, C.POINTER(_D), C.POINTER(_D)]
     L.pic_substep_histogram.argtypes = [_P, _I, _P]
     L.pic_state_upload.argtypes = [_P, C.POINTER(HostState)]
     L.pic_state_download.argtypes = [_P, C.POINTER(HostState)]
@@ -531,6 +532,14 @@ class Pic:
         v = self.view()
         self.torch.cuda.synchronize(self.device)
         return tuple(v[k].cpu().numpy().copy() for k in ("er", "ez", "h"))
+
+
+def probe_dfma(blocks_per_sm=4, iters=1 << 16):
+    """Measured FP64 FMA throughput (pic_probe_dfma): (seconds, TFLOP/s)."""
+    sec, tf = C.c_double(0.0), C.c_double(0.0)
+    _check(lib().pic_probe_dfma(int(blocks_per_sm), int(iters), C.byref(sec), C.byref(tf)),
+           "pic_probe_dfma")
+    return sec.value, tf.value
 
 
 def check_dmul(x, y):

@@ -281,3 +281,54 @@ extern "C" int pic_check_dmul(const double *x, const double *y, double *out, lon
   if (cudaGetLastError() != cudaSuccess) return PIC_E_CUDA;
   return cudaStreamSynchronize(s) == cudaSuccess ? PIC_OK : PIC_E_CUDA;
 }
+
+// ---------------------------------------------------------------------------
+// throughput probe of the FP64 FMA pipe (pic_probe_dfma): every thread runs
+// eight independent chains of fused multiply-adds, so the pipe, not their
+// latency, sets the rate
+namespace pic {
+namespace {
+__device__ double g_dfma_sink;
+__global__ void __launch_bounds__(256) k_dfma_probe(int iters, double a, double b) {
+  double x0 = threadIdx.x, x1 = x0 + 1.0, x2 = x0 + 2.0, x3 = x0 + 3.0;
+  double x4 = x0 + 4.0, x5 = x0 + 5.0, x6 = x0 + 6.0, x7 = x0 + 7.0;
+#pragma unroll 4
+  for (int i = 0; i < iters; ++i) {
+    x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+    x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+  }
+  const double s = ((x0 + x1) + (x2 + x3)) + ((x4 + x5) + (x6 + x7));
+  if (s == 1.2345678e300) g_dfma_sink = s;  // keeps the chains live, never taken
+}
+}  // namespace
+}  // namespace pic
+
+extern "C" int pic_probe_dfma(int blocks_per_sm, int iters, double *seconds, double *tflops) {
+  if (blocks_per_sm < 1 || blocks_per_sm > 8 || iters < 1 || !seconds || !tflops)
+    return PIC_E_CONFIG;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return PIC_E_CUDA;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return PIC_E_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return PIC_E_CUDA;
+  }
+  const unsigned nb = (unsigned)(nsm * blocks_per_sm);
+  // a near-one multiplier keeps the values finite over any number of steps
+  pic::k_dfma_probe<<<nb, 256>>>(iters, 0.9999999, 1e-7);  // warm-up
+  cudaEventRecord(e0);
+  pic::k_dfma_probe<<<nb, 256>>>(iters, 0.9999999, 1e-7);
+  cudaEventRecord(e1);
+  cudaError_t e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess || ms <= 0.f) return PIC_E_CUDA;
+  *seconds = ms * 1e-3;
+  *tflops = 2.0 * 8.0 * (double)iters * 256.0 * (double)nb / (*seconds) / 1e12;
+  return PIC_OK;
+}

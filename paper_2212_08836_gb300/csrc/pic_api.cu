@@ -38,7 +38,9 @@ struct pic_ctx {
   int cur[2];
   int mixed;                 // 1: FP32 particle store and push (PIC_MIXED)
   AlphaOut alpha;            // mixed form: normalised accelerations per species
-  int *queue, *qblock;       // work queue of the general push path (FP64 form)
+  int *queue, *qblock;       // work queue of the general push path
+  int *q_cell;               // mixed form: start state of the queued particles
+  float *q_st[6];
   // mixed form: per species the list of near-axis crossers pushed in FP64
   // arithmetic, its count, and the side stream that runs the electrons' list
   // while the ions are pushed
@@ -124,7 +126,17 @@ struct pic_ctx {
     const void *key[13];
     cudaGraphExec_t exec;
     long long nlaunch;      // kernels in the graph
+    // push timing (pic_profile on at capture): events recorded around the
+    // pushes by every replay, and the push launches between them
+    cudaEvent_t pe[2];
+    int ptimed, npush;
   } gcache[64];
+  // the push events of the last replayed pass, read after it completed
+  cudaEvent_t *rep_pe;
+  int rep_npush;
+  // the events a pass being captured records around its pushes (else null)
+  cudaEvent_t *cap_pe;
+  int cap_npush;
   int ngraph;
   cudaStream_t gstream;     // stream of the network
   cudaEvent_t gev[2];
@@ -146,7 +158,6 @@ enum {
   kHnMcc = 18,    // 8: collision counts
   kHnDe = 26,     // collision energy change
   kHnIz = 27,     // ionization pairs of the MCC pass
-  kHnKerr = 28,   // kernels that gave up a bounded wait
   kHnSlots = 32
 };
 
@@ -263,22 +274,22 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
       P.id = (uint32_t *)K.take(pc * 4);
     }
   const size_t qc = pc + (size_t)kMaxFastBlocks * 256;  // queue entries
+  x->queue = (int *)K.take(qc * 4);
+  x->qblock = (int *)K.take((size_t)2 * kMaxFastBlocks * 4);  // front and back counts
   if (c->precision == PIC_MIXED) {
-    // the FP32 kernel finishes its crossers inside each tile; it only lists
-    // the near-axis crossers it hands to FP64 arithmetic
-    x->queue = nullptr;
-    x->qblock = nullptr;
-    x->plist[0] = (int *)K.take((size_t)pc * 4);
-    x->plist[1] = (int *)K.take((size_t)pc * 4);
-    x->pcnt = (unsigned *)K.take(256);
     for (int s = 0; s < 2; ++s) {
       x->alpha.ar[s] = (float *)K.take(ner * 4);
       x->alpha.az[s] = (float *)K.take(nez * 4);
     }
-    for (int k = 0; k < 2; ++k) x->q_real[k] = nullptr;
+    for (int k = 0; k < 2; ++k) x->q_real[k] = (float *)K.take(qc * 4);
+    // queue entries carry the start state: cell, then a, b, vr, vt, vz, w
+    x->q_cell = (int *)K.take(qc * 4);
+    for (int k = 0; k < 6; ++k) x->q_st[k] = (float *)K.take(qc * 4);
+    // per species: near-axis crossers for FP64 arithmetic, and their counts
+    x->plist[0] = (int *)K.take((size_t)pc * 4);
+    x->plist[1] = (int *)K.take((size_t)pc * 4);
+    x->pcnt = (unsigned *)K.take(256);
   } else {
-    x->queue = (int *)K.take(qc * 4);
-    x->qblock = (int *)K.take((size_t)2 * kMaxFastBlocks * 4);  // front and back counts
     for (int s = 0; s < 2; ++s) {
       x->alpha64.ar[s] = (double *)K.take(ner * 8);
       x->alpha64.az[s] = (double *)K.take(nez * 8);
@@ -417,10 +428,21 @@ void prof_collect(pic_ctx *x) {
   for (int k = 0; k < x->nev; ++k) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, x->ev[2 * k], x->ev[2 * k + 1]) == cudaSuccess) x->push_ms += ms;
+    else cudaGetLastError();  // a failed query must not surface as a later launch's error
   }
   x->nev = 0;
   x->push_launches += x->pending_launches;
   x->pending_launches = 0;
+  if (x->rep_pe) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, x->rep_pe[0], x->rep_pe[1]) == cudaSuccess) {
+      x->push_ms += ms;
+      x->push_launches += x->rep_npush;
+    } else {
+      cudaGetLastError();
+    }
+    x->rep_pe = nullptr;
+  }
 }
 
 template <typename T>
@@ -462,7 +484,6 @@ void fill_push(pic_ctx *x, int s, double q, double m, const double *erh, const d
   L.counters = counters;
   L.ke_lost = kel;
   L.hist = (write && x->hist_on) ? x->hist : nullptr;
-  L.kerr = &x->cnt->kerr;
   L.dt = dt;
   L.icr64 = x->g.dr / dt;
   L.icz64 = x->g.dz / dt;
@@ -474,6 +495,9 @@ void fill_push(pic_ctx *x, int s, double q, double m, const double *erh, const d
   L.rm64.crx = x->rmap64 + kMaxAxisCells;
   L.rm64.icrx = x->rmap64 + 2 * kMaxAxisCells;
   L.pcnt = nullptr;
+  L.plist = nullptr;
+  L.q_cell = nullptr;
+  L.q_a = L.q_b = L.q_vr = L.q_vt = L.q_vz = L.q_w = nullptr;
 }
 
 template <typename T>
@@ -490,6 +514,11 @@ int push_all(pic_ctx *x, const double *erh, const double *ezh, double *ir, doubl
              unsigned long long *counters, double *kel, double *wall, int oop = 0) {
   bool timed = x->prof && x->nev < 128 && !x->capturing;
   if (timed) cudaEventRecord(x->ev[2 * x->nev], x->s);
+  // a pass being captured with timing on records its own event pair, which
+  // every replay records again
+  const bool ctimed = x->capturing && x->cap_pe;
+  // external records become event-record nodes that every replay executes
+  if (ctimed) cudaEventRecordWithFlags(x->cap_pe[0], x->s, cudaEventRecordExternal);
   const int nsp = x->cfg.ions_fixed ? 1 : 2;
   bool forked = false;
   for (int s = 0; s < nsp; ++s) {
@@ -514,20 +543,27 @@ int push_all(pic_ctx *x, const double *erh, const double *ezh, double *ir, doubl
       if (L.hist && oop) L.hist = x->hist_spec;  // counted once the pass is adopted
       L.ar = x->alpha.ar[s];
       L.az = x->alpha.az[s];
-      L.queue = x->plist[s];
-      L.qblock = nullptr;
-      L.q_da = L.q_db = nullptr;
+      set_queue(x, x->q_real, L);
+      L.q_cell = x->q_cell;
+      L.q_a = x->q_st[0];
+      L.q_b = x->q_st[1];
+      L.q_vr = x->q_st[2];
+      L.q_vt = x->q_st[3];
+      L.q_vz = x->q_st[4];
+      L.q_w = x->q_st[5];
+      L.plist = x->plist[s];
       L.pcnt = x->pcnt + s;
       fast = L.wbt == 0.f;
       e = launch_push(L, x->s);
       if (e == cudaSuccess) {
-        if (s == 0 && nsp == 2 && x->pstream_made) {
-          // the electrons' near-axis list on the side stream, beside the ions
+        if (x->pstream_made) {
+          // the near-axis lists on the side stream, beside the next launches
+          // (the electrons' beside the ions' pass), joined at the end
           e = cudaEventRecord(x->pev[0], x->s);
           if (e == cudaSuccess) e = cudaStreamWaitEvent(x->pstream, x->pev[0], 0);
           if (e == cudaSuccess) e = launch_push_fp32_axis(L, x->pstream);
           if (e == cudaSuccess) e = cudaEventRecord(x->pev[1], x->pstream);
-          forked = e == cudaSuccess;
+          forked = forked || e == cudaSuccess;
         } else {
           e = launch_push_fp32_axis(L, x->s);
         }
@@ -549,9 +585,11 @@ int push_all(pic_ctx *x, const double *erh, const double *ezh, double *ir, doubl
     if (n > 0) {
       x->launches += fast ? 2 : 1;  // fast + general kernels
       if (timed) x->pending_launches += 1;
+      if (ctimed) x->cap_npush += 1;
     }
   }
   if (forked && cudaStreamWaitEvent(x->s, x->pev[1], 0) != cudaSuccess) return PIC_E_CUDA;
+  if (ctimed) cudaEventRecordWithFlags(x->cap_pe[1], x->s, cudaEventRecordExternal);
   if (timed) {
     cudaEventRecord(x->ev[2 * x->nev + 1], x->s);
     x->nev += 1;
@@ -921,7 +959,11 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
   if (e == cudaSuccess) e = cudaHostAlloc((void **)&x->hn, 8 * kHnSlots, cudaHostAllocDefault);
   if (e == cudaSuccess && x->mixed) {
     // side stream of the electrons' near-axis FP64 list (runs beside the ions)
-    e = cudaStreamCreateWithFlags(&x->pstream, cudaStreamNonBlocking);
+    // the highest priority: its few blocks are placed before the next
+    // persistent push kernel fills the SMs
+    int lo = 0, hi = 0;
+    e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&x->pstream, cudaStreamNonBlocking, hi);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x->pev[0], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x->pev[1], cudaEventDisableTiming);
     if (e == cudaSuccess) x->pstream_made = 1;
@@ -971,7 +1013,13 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
 void pic_destroy(pic_ctx *ctx) {
   if (!ctx) return;
   if (ctx->ngraph || ctx->hn) cudaStreamSynchronize(ctx->s);
-  for (int k = 0; k < ctx->ngraph; ++k) cudaGraphExecDestroy(ctx->gcache[k].exec);
+  for (int k = 0; k < ctx->ngraph; ++k) {
+    cudaGraphExecDestroy(ctx->gcache[k].exec);
+    if (ctx->gcache[k].ptimed) {
+      cudaEventDestroy(ctx->gcache[k].pe[0]);
+      cudaEventDestroy(ctx->gcache[k].pe[1]);
+    }
+  }
   if (ctx->hn) cudaFreeHost(ctx->hn);
   if (ctx->gev_made) {
     cudaStreamSynchronize(ctx->s);
@@ -1002,6 +1050,7 @@ int pic_profile(pic_ctx *x, int enable) {
   x->nev = 0;
   x->push_ms = 0.0;
   x->push_launches = x->pending_launches = 0;
+  x->rep_pe = nullptr;
   if (!enable && x->prof) {
     for (int k = 0; k < 2 * 128; ++k) cudaEventDestroy(x->ev[k]);
     x->prof = 0;
@@ -1474,11 +1523,28 @@ int launch_pass(pic_ctx *x, bool spec) {
                          (const void *)(uintptr_t)(spec ? 1 : 0), x->erh,
                          (const void *)(uintptr_t)(x->hist_on ? 1 : 0)};
   for (int k = 0; k < x->ngraph; ++k)
-    if (!memcmp(x->gcache[k].key, key, sizeof(key))) {
+    if (!memcmp(x->gcache[k].key, key, sizeof(key)) && (!x->prof || x->gcache[k].ptimed)) {
       x->launches += x->gcache[k].nlaunch;
+      if (x->prof) {
+        x->rep_pe = x->gcache[k].pe;
+        x->rep_npush = x->gcache[k].npush;
+      }
       return cudaGraphLaunch(x->gcache[k].exec, x->s) == cudaSuccess ? PIC_OK : PIC_E_CUDA;
     }
   if (x->ngraph == 64) return enqueue_pass(x, spec);
+  pic_ctx::GraphEntry &N = x->gcache[x->ngraph];
+  N.ptimed = 0;
+  N.npush = 0;
+  if (x->prof) {
+    if (cudaEventCreate(&N.pe[0]) != cudaSuccess) return PIC_E_CUDA;
+    if (cudaEventCreate(&N.pe[1]) != cudaSuccess) {
+      cudaEventDestroy(N.pe[0]);
+      return PIC_E_CUDA;
+    }
+    N.ptimed = 1;
+    x->cap_pe = N.pe;
+    x->cap_npush = 0;
+  }
   cudaGraph_t g = nullptr;
   if (cudaStreamBeginCapture(x->s, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
     return PIC_E_CUDA;
@@ -1486,20 +1552,40 @@ int launch_pass(pic_ctx *x, bool spec) {
   x->capturing = 1;
   int r = enqueue_pass(x, spec);
   x->capturing = 0;
+  x->cap_pe = nullptr;
+  N.npush = x->cap_npush;
   cudaError_t e = cudaStreamEndCapture(x->s, &g);
+  auto drop_events = [&]() {
+    if (N.ptimed) {
+      cudaEventDestroy(N.pe[0]);
+      cudaEventDestroy(N.pe[1]);
+      N.ptimed = 0;
+    }
+  };
   if (r) {
     if (g) cudaGraphDestroy(g);
+    drop_events();
     return r;
   }
-  if (e != cudaSuccess) return PIC_E_CUDA;
+  if (e != cudaSuccess) {
+    drop_events();
+    return PIC_E_CUDA;
+  }
   cudaGraphExec_t ex = nullptr;
   e = cudaGraphInstantiate(&ex, g, 0);
   cudaGraphDestroy(g);
-  if (e != cudaSuccess) return PIC_E_CUDA;
+  if (e != cudaSuccess) {
+    drop_events();
+    return PIC_E_CUDA;
+  }
   pic_ctx::GraphEntry &E = x->gcache[x->ngraph++];
   memcpy(E.key, key, sizeof(key));
   E.exec = ex;
   E.nlaunch = x->launches - l0;
+  if (E.ptimed) {
+    x->rep_pe = E.pe;
+    x->rep_npush = E.npush;
+  }
   return cudaGraphLaunch(ex, x->s) == cudaSuccess ? PIC_OK : PIC_E_CUDA;
 }
 
@@ -1706,8 +1792,6 @@ int step_end(pic_ctx *x, StepState &T, int *rc) {
     return PIC_E_CUDA;
   if (cudaMemcpyAsync(x->hn + kHnKel, &x->cnt->ke_lost, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return PIC_E_CUDA;
-  if (cudaMemcpyAsync(x->hn + kHnKerr, &x->cnt->kerr, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-    return PIC_E_CUDA;
   if (x->cfg.mcc_on &&
       cudaMemcpyAsync(x->hn + kHnDe, &x->cnt->de_coll, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return PIC_E_CUDA;
@@ -1715,14 +1799,6 @@ int step_end(pic_ctx *x, StepState &T, int *rc) {
   if (sr) return sr;
   if (cudaStreamSynchronize(s) != cudaSuccess) return PIC_E_CUDA;
   sort_finish(x);
-  unsigned long long kerr = 0;
-  memcpy(&kerr, x->hn + kHnKerr, 8);
-  if (kerr) {
-    // a kernel timed out on one of its bounded waits: the step's results are
-    // not trustworthy; the count is cleared for the next call
-    cudaMemsetAsync(&x->cnt->kerr, 0, 8, s);
-    return PIC_E_CUDA;
-  }
   unsigned long long pc[5];
   double kel = 0.0;
   double cst[4] = {0.0, 0.0, T.v1, 0.0};
@@ -2280,7 +2356,14 @@ namespace {
 
 void drop_graphs(pic_ctx *x) {
   if (x->ngraph) cudaStreamSynchronize(x->s);
-  for (int k = 0; k < x->ngraph; ++k) cudaGraphExecDestroy(x->gcache[k].exec);
+  for (int k = 0; k < x->ngraph; ++k) {
+    cudaGraphExecDestroy(x->gcache[k].exec);
+    if (x->gcache[k].ptimed) {
+      cudaEventDestroy(x->gcache[k].pe[0]);
+      cudaEventDestroy(x->gcache[k].pe[1]);
+    }
+  }
+  x->rep_pe = nullptr;
   x->ngraph = 0;
 }
 

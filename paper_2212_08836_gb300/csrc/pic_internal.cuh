@@ -146,7 +146,7 @@ struct DevCounters {
   double norm[2];              // Picard: sum (E_new - E_it)^2, sum E_new^2
   double src;                  // drive-gap energy of the last solve
   unsigned long long iz_slots; // MCC: ionization keys written
-  unsigned long long kerr;     // kernels that gave up a bounded wait (a copy that never landed)
+  double pad[1];
 };
 
 // Field operator (separable direct solve of the H_theta system)
@@ -247,20 +247,22 @@ struct PushLaunchT {
   T *q_da, *q_db;          // queued particle's converged whole-step trial (NaN: none);
                            // its start state is re-read from the store, which the
                            // fast kernel leaves untouched for queued particles
-  unsigned long long *kerr;  // counts bounded waits that timed out (device; never null)
-  // FP32 store: crossers that start in the first kPromoteRows radial cells are
-  // listed (queue[0 .. *pcnt)) and pushed by a second kernel in FP64
-  // arithmetic (double scales from dt and the grid, radial tables rm64)
+  // FP32 store: the queue entries carry the start state (nullptr: re-read
+  // from the store, the FP64 form)
+  int *q_cell;
+  T *q_a, *q_b, *q_vr, *q_vt, *q_vz, *q_w;
+  // FP32 store: crossers next to the axis are listed (plist[0 .. *pcnt)) by
+  // the general kernel and pushed by a third kernel in FP64 arithmetic
+  // (double scales, radial tables rm64); pcnt == nullptr: none
+  int *plist;
   unsigned *pcnt;
   double dt;
   double icr64, icz64, cz64;  // dr/dt, dz/dt, dt/dz in double
   RadialMapT<double> rm64;
 };
-// radial cells next to the axis whose FP32 crossers with a large angular step
-// take FP64 arithmetic: there the centrifugal term of Eq. 4 grows like 1/r and
-// amplifies FP32 rounding
-constexpr int kPromoteRows = 1;
-constexpr float kPromoteRho = 0.125f;  // cells
+// radial cells next to the axis whose FP32 crossers may take FP64 arithmetic
+// (the centrifugal term of Eq. 4 grows like 1/r and amplifies FP32 rounding)
+constexpr int kPromoteRows = 2;
 // Electrostatic field model (Eq. 8) on the same mesh: potential on the
 // nodes, Gauss's law on the interior nodes (i < nr, 0 < j < nz), separable:
 // orthonormal DST-I along z (GEMM), cyclic reduction along r (field.cu)

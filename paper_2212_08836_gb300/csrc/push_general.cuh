@@ -620,13 +620,17 @@ __device__ void push_sub(const GenArgs<T, S> &L, long long p, int ic, int jc, T 
         else continue;
         T X = face - x0;
         T v0 = dir == 0 ? ur : uz;
-        const T g0 = first_crossing<T>(X, dx, v0, tT);
+        // the start only seeds Newton: FP32 arithmetic is enough, and keeps the
+        // square root and reciprocals off the FP64 form's narrow FP64 pipe
+        const T g0 = (T)first_crossing<float>((float)X, (float)dx, (float)v0, (float)tT);
         T oth0 = doth * (g0 * (tT == one ? one : Num<T>::rcp(tT)));
         T tt = zero, toth = zero;
         if (!(g0 > zero)) continue;
-        // a z-face (most crossings: cells are flat in z) through the scalar
-        // reduction, else (or if it does not apply) the 2x2 landing system
-        if (!(!kB && dir == 1 && X != zero &&
+        // FP32: a z-face (most crossings: cells are flat in z) through the
+        // scalar reduction, else (or if it does not apply) the 2x2 landing
+        // system (the FP64 form keeps the 2x2 solve: its scalar solves run on
+        // the integer pipes and measured slower in this divergent kernel)
+        if (!(!kB && sizeof(T) == 4 && dir == 1 && X != zero &&
               landing_z_scalar<T>(s, X, g0, tt, toth, Tl.snewton)) &&
             !landing_gen<T, kB>(s, wt, dir, X, g0, oth0, tt, toth, Tl.newton))
           continue;
@@ -789,6 +793,10 @@ __device__ void push_zcross(const GenArgs<T, S> &L, long long p, int c0, T a, T 
   int ic = c0 / nz, jc = c0 - (c0 / nz) * nz;
   const T cr0 = L.rm.crr(ic);
   T ur = vr0 * cr0, ut = vt0 * cr0, uz = vz0 * L.cz;
+  if (N::nan_bits(tr_da) || !(b + tr_db < zero || b + tr_db > one)) {
+    push_sub<T, false, S>(L, p, ic, jc, a, b, ur, ut, uz, w, tr_da, tr_db, one, 0, 0, Tl);
+    return;
+  }
   // ---- sub-step 1: the landing on the z-face the trial leaves through
   SubT<T> s;
   s.ar0 = (T)L.ar[ic * nz1 + jc];
@@ -801,7 +809,7 @@ __device__ void push_zcross(const GenArgs<T, S> &L, long long p, int c0, T a, T 
   s.P = s.rho * ut;
   const T face = b + tr_db > one ? one : zero;
   const T X = face - b;
-  const T g0 = first_crossing<T>(X, tr_db, uz, one);
+  const T g0 = (T)first_crossing<float>((float)X, (float)tr_db, (float)uz, 1.f);
   T tt = zero, da = zero;
   if (!N::in01(a) || !N::in01(b) || !(g0 > zero) ||
       !landing_z_scalar<T>(s, X, g0, tt, da, Tl.snewton) || !(tt > zero) || tt > one ||

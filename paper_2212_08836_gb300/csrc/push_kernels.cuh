@@ -143,6 +143,29 @@ __device__ __forceinline__ void load_state(const PartsT<T> &P, long long p, long
   }
 }
 
+// FP32 crossers that take FP64 arithmetic (the centrifugal term of Eq. 4
+// grows like 1/r and amplifies FP32 rounding): in the first radial cells, a
+// straight path over the step that comes closer to the axis than 1/8 of the
+// start radius (the amplification grows like rho / rho_min), or a CN
+// whole-step trial (d: its radial displacement, NaN: none) that ends that close
+template <typename T>
+__device__ __forceinline__ bool near_axis32(const PushLaunchT<T> &L, int c, T a, T vr, T vt, T d) {
+  const int nz = L.g.nz;
+  if (c < 0 || c >= kPromoteRows * nz) return false;
+  const int ic = c / nz;
+  const T crr = L.rm.crr(ic);
+  const T rho = L.rm.rho0(ic) + a, ur = vr * crr, ut = vt * crr;
+  const T u2 = ur * ur + ut * ut;
+  bool close = false;
+  if (ur < (T)0 && u2 > (T)0) {
+    const T sm = fmin(-rho * ur / u2, (T)1);
+    const T x = rho + ur * sm, y = ut * sm;
+    close = (T)64 * (x * x + y * y) < rho * rho;
+  }
+  if (!Num<T>::nan_bits(d)) close = close || (T)64 * (rho + d) * (rho + d) < rho * rho;
+  return close;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_push_fast(PushLaunchT<T> L) {
   const int lane = threadIdx.x & 31;
@@ -154,6 +177,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_push_fast(PushL
   // crossings of the trial from the front, [1] the rest from the back
   __shared__ int s_qn[2];
   if (threadIdx.x < 2) s_qn[threadIdx.x] = 0;
+  // the near-axis list of this pass starts empty (the general kernel, which
+  // fills it, runs after this kernel on the same stream)
+  if (L.pcnt && blockIdx.x == 0 && threadIdx.x == 0) *L.pcnt = 0u;
   __syncthreads();
   const long long qoff = (long long)blockIdx.x * L.qseg;
   const long long n = L.n_dev ? *L.n_dev : L.n;
@@ -208,7 +234,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_push_fast(PushL
           e = zb + N::mul(q, gaz) * d;
           const T a1 = a + d, b1 = b + e;
           acc = Num<T>::in01(a1) && Num<T>::in01(b1);
-          zcross = Num<T>::in01(a1) && !Num<T>::in01(b1);
+          // FP32: an end much closer to the axis than the start is queued (it
+          // may need FP64: the centrifugal term grows like 1/r)
+          if (sizeof(T) == 4 && acc && ic < kPromoteRows)
+            acc = !((T)64 * (rho + d) * (rho + d) < rho * rho);
+          zcross = Num<T>::in01(a1) && (b1 < zero || b1 > one);
           if (acc) {
             n_acc++;
             const T qw = N::mul(L.qf, w);
@@ -245,18 +275,28 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_push_fast(PushL
       if (lane == 0 && m) atomicAdd(&L.hist[0], (unsigned long long)__popc(m));
     }
     // queue the rest for the general path (warp-aggregated append to the
-    // block's segment; the shared-memory counter keeps it off global atomics)
-    // two kinds in the FP64 form only: there the general kernel is bound by its
-    // FP64 pipe, which spends a whole warp slot on each instruction of a
-    // divergent warp (the FP32 form is issue-bound and gains nothing from it)
-    const bool front = sizeof(T) == 8 ? zcross : true;
+    // block's segment; the shared-memory counter keeps it off global atomics),
+    // in two kinds: the crossings of the trial through a z-face only from the
+    // front, the rest from the back, so that the general kernel's warps take
+    // one sub-step sequence at a time.  FP32 entries carry the start state
+    // (written coalesced here, read coalesced there: no scattered re-read)
+    const bool front = zcross && trial;
     const long long kf = seg_append(&s_qn[0], queued && front, lane, qoff);
-    const long long kb = sizeof(T) == 8 ? seg_append(&s_qn[1], queued && !front, lane, 0) : 0;
+    const long long kb = seg_append(&s_qn[1], queued && !front, lane, 0);
     const long long k = front ? kf : qoff + L.qseg - 1 - kb;
     if (queued) {
       L.queue[k] = (int)p;
       L.q_da[k] = trial ? d : (T)NAN;
       L.q_db[k] = e;
+      if (L.q_cell) {
+        L.q_cell[k] = c0;
+        L.q_a[k] = a;
+        L.q_b[k] = b;
+        L.q_vr[k] = cur.vr;
+        L.q_vt[k] = cur.vt;
+        L.q_vz[k] = cur.vz;
+        L.q_w[k] = w;
+      }
     }
   }
   __syncthreads();
@@ -270,7 +310,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_push_fast(PushL
 
 // queued particles (or all of them when queue == nullptr); blockDim 256
 template <typename T, bool kB>
-__global__ void __launch_bounds__(256, 2) k_push_general(PushLaunchT<T> L) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_push_general(PushLaunchT<T> L) {
   const int lane = threadIdx.x & 31;
   GenArgs<T> G;
   G.nr = L.g.nr; G.nz = L.g.nz; G.ar = L.ar; G.az = L.az;
@@ -291,8 +331,9 @@ __global__ void __launch_bounds__(256, 2) k_push_general(PushLaunchT<T> L) {
                          : seg_entry_back(s_preb, L.qgrid, L.qseg, (int)(q - total_f));
     };
     if (sizeof(T) == 4) {
-      // FP32 form: the next entry's start state (a scattered re-read from the
-      // store) is loaded while this one is pushed
+      // FP32 form: the entries carry the start state; the next entry is loaded
+      // while this one is pushed.  z-face crossers (the front kind) take the
+      // straight-line routine; crossers next to the axis go to the FP64 list
       struct Ent {
         long long p;
         PState<T> s;
@@ -303,15 +344,34 @@ __global__ void __launch_bounds__(256, 2) k_push_general(PushLaunchT<T> L) {
         en.p = L.queue[k];
         en.da = L.q_da[k];
         en.db = L.q_db[k];
-        load_state(L.p, en.p, en.p + 1, en.s);
+        en.s.c = L.q_cell[k];
+        en.s.a = L.q_a[k];
+        en.s.b = L.q_b[k];
+        en.s.vr = L.q_vr[k];
+        en.s.vt = L.q_vt[k];
+        en.s.vz = L.q_vz[k];
+        en.s.w = L.q_w[k];
       };
       Ent nx;
       if (gtid < total) fetch(gtid, nx);
       for (long long q = gtid; q < total; q += gstride) {
         const Ent cu = nx;
         if (q + gstride < total) fetch(q + gstride, nx);
-        push_general<T, kB>(G, cu.p, cu.s.c, cu.s.a, cu.s.b, cu.s.vr, cu.s.vt, cu.s.vz, cu.s.w,
-                            cu.da, cu.db, tl);
+        if (L.pcnt && near_axis32(L, cu.s.c, cu.s.a, cu.s.vr, cu.s.vt, cu.da)) {
+          const unsigned am = __activemask();
+          const unsigned pm = __ballot_sync(am, true);
+          const int leader = __ffs(pm) - 1;
+          unsigned base = 0;
+          if (lane == leader) base = atomicAdd(L.pcnt, (unsigned)__popc(pm));
+          base = __shfl_sync(pm, base, leader);
+          L.plist[base + __popc(pm & ((1u << lane) - 1u))] = (int)cu.p;
+        } else if (!kB && q < total_f) {
+          push_zcross<T>(G, cu.p, cu.s.c, cu.s.a, cu.s.b, cu.s.vr, cu.s.vt, cu.s.vz, cu.s.w,
+                         cu.da, cu.db, tl);
+        } else {
+          push_general<T, kB>(G, cu.p, cu.s.c, cu.s.a, cu.s.b, cu.s.vr, cu.s.vt, cu.s.vz,
+                              cu.s.w, cu.da, cu.db, tl);
+        }
       }
     } else {
       for (long long q = gtid; q < total; q += gstride) {
@@ -369,6 +429,7 @@ cudaError_t launch_push(const PushLaunchT<T> &L, cudaStream_t s) {
   // captured launch stays valid while the count changes
   const long long nsz = L.n_dev ? L.cap : L.n;
   if (nsz <= 0) return cudaSuccess;
+
   const int bs = 256;
   long long nb = (nsz + bs - 1) / bs;
   if (L.wbt == (T)0 && L.queue) {

@@ -196,3 +196,19 @@ def test_trained_start_gains_over_the_plain_start():
     assert r["cnn"]["steps"] >= 110
     assert fc < 0.7 * fp and fc < 0.7 * fe, r
     assert r["cnn"]["picard_iters"] <= r["plain"]["picard_iters"] + 0.05, r
+
+
+@pytest.mark.parametrize("nr,nz,batch", [(8, 12, 1), (13, 70, 2), (33, 65, 1)])
+def test_forward_elementwise_within_bf16_bound(nr, nz, batch):
+    """Every output element of the tensor-core forward pass against the oracle
+    pass that rounds each hidden activation to bfloat16 as the kernels do
+    (oracle.cnn.forward_bf16), within that pass's element-wise bound (FP32
+    sums in any order, one bfloat16 step per rounding decision taken from a
+    slightly different sum, carried through the later layers)."""
+    net, ps, rng = setup(nr, nz, batch, 13)
+    x = bf16(rng.normal(size=(batch, 14, nr + 1, nz + 1)))
+    y = net.forward(torch.tensor(x, dtype=torch.float32, device=DEV)).cpu().numpy()
+    for b in range(batch):
+        ref, bound = Q.forward_bf16(ps, x[b])
+        err = np.abs(y[b] - ref)
+        assert np.all(err <= bound + 1e-30), float(np.max(err / np.maximum(bound, 1e-300)))

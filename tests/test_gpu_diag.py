@@ -191,3 +191,39 @@ def test_continuity_residual_per_step(precision, ring):
         res = pic.diag_get(M.PIC_DIAG_CONTINUITY)
         assert np.max(np.abs(res)) <= (1e-12 if precision == 0 else 1e-6) * q_scale
     assert absorbed > 0
+
+
+def test_fp64_fma_probe_reports_a_plausible_peak():
+    """pic_probe_dfma (the FP64 roofline's denominator): independent FMA chains
+    on every SM; the rate lies between a tenth of and twice the GB300 unit
+    count (304 DFMA per cycle at 2.07 GHz = 1.26 TFLOP/s), and a longer run
+    takes proportionally longer."""
+    M = P()
+    s1, tf1 = M.probe_dfma(4, 1 << 12)
+    s2, tf2 = M.probe_dfma(4, 1 << 14)
+    assert 0.126 < tf2 < 2.52, tf2
+    assert 2.0 < s2 / s1 < 8.0, (s1, s2)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_push_timing_under_graph_replay(precision):
+    """pic_profile's push timing while the Picard passes replay from captured
+    graphs (the benchmark's configuration): every step completes, and the
+    pushes of the replayed passes are timed (a positive total over the
+    expected number of launches)."""
+    M = P()
+    cfg = M.small_reactor(np_init=20000, volt=200.0, precision=precision)
+    pic = M.Pic(cfg, device=DEV, stream=torch.cuda.Stream(device=DEV))
+    M.set_graphs(pic, True)
+    pic.load_particles()
+    pic.profile(True)
+    pic.step(3)
+    pic.profile(True)
+    iters = 0
+    for _ in range(3):
+        rc, st = pic.step(1)
+        assert rc == 0
+        iters += st["picard_iters"]
+    ms, nl = pic.profile_read()
+    assert ms > 0.0
+    assert nl >= 2 * iters

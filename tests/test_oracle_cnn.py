@@ -91,3 +91,38 @@ def test_features_scale_invariant_and_masked():
     # increments are RMS-normalised: channels 0-1 have unit RMS over the valid points
     v = np.concatenate([x[0][:nr, :].ravel(), x[1][:, :nz].ravel()])
     assert abs(np.sqrt(np.mean(v * v)) - 1.0) < 1e-9
+
+
+def test_bf16_rounding_matches_torch():
+    """round_bf16 against torch's float32 -> bfloat16 conversion (round to
+    nearest even), including ties, subnormals, zeros and large values."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(3)
+    a = np.concatenate([rng.normal(size=5000) * 10 ** rng.uniform(-30, 30, size=5000),
+                        [0.0, -0.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, 1e-40, -1e-39, 3e38]])
+    a = a.astype(np.float32)
+    ref = torch.tensor(a).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(Q.round_bf16(a), ref)
+
+
+def test_forward_bf16_bound_holds_under_perturbed_sums():
+    """forward_bf16's element-wise bound: the same network evaluated with
+    every sum perturbed by up to the FP32 allowance (random signs) and the
+    hidden activations rounded to bfloat16 from the perturbed sums stays
+    within the bound of the unperturbed pass (and does differ from it)."""
+    rng = np.random.default_rng(11)
+    ps = Q.init_params([14, 16, 16, 2], 4)
+    ps = [(Q.round_bf16(w), rng.normal(size=b.shape) * 0.05) for w, b in ps]
+    x = Q.round_bf16(rng.normal(size=(14, 9, 13)))
+    ref, bound = Q.forward_bf16(ps, x)
+    worst = 0.0
+    for trial in range(20):
+        h = x
+        for k, (w, b) in enumerate(ps):
+            z = Q.conv3x3(h, w, b)
+            scale = Q.FP32_SUM * Q.conv3x3(np.abs(h), np.abs(w), np.abs(b))
+            z = z + scale * rng.uniform(-1, 1, size=z.shape)
+            h = Q.round_bf16(np.maximum(z, 0.0)) if k + 1 < len(ps) else z
+        assert np.all(np.abs(h - ref) <= bound), np.max(np.abs(h - ref) / bound)
+        worst = max(worst, float(np.max(np.abs(h - ref))))
+    assert worst > 0.0
