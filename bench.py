@@ -40,8 +40,8 @@ DFMA_PER_CYCLE = 304
 BYTES_PER_PUSH_FP64 = 52
 # ncu DRAM bytes (read + write) per push of the current FP64 kernel, from the
 # profile in profiles/ (None when the kernel changed after the capture)
-TRAFFIC_PER_PUSH = 85.8  # DRAM bytes per push of the FP64 push kernels: ncu dram__bytes_read + write, 4M/species case
-TRAFFIC_PER_PUSH_FP32 = 44.9  # the same for the FP32 push kernels of the mixed form
+TRAFFIC_PER_PUSH = 85.7  # DRAM bytes per push of the FP64 push kernels: ncu dram__bytes_read + write, 4M/species case
+TRAFFIC_PER_PUSH_FP32 = 34.6  # the same for the FP32 push kernels of the mixed form
 
 
 def peaks():
