@@ -2,17 +2,34 @@
 // the method itself produces, used only as the initial iterate of the
 // nonlinear iteration of Sec. 2.1.
 //
-// Tensors inside are channels-last (position-major) BF16 with the channel
-// count padded to a multiple of 16; positions run over batch x (nr+1) x (nz+1).
-// Every convolution is an implicit GEMM on the tensor cores
-// (mma.sync m16n8k16, BF16 operands, FP32 accumulation):
+// Activations and gradients are BF16 in planes of 8 channels: plane k holds
+// channels 8k..8k+7 of every position (16 bytes per position), the channel
+// count padded to a multiple of 16, on the grid with a one-point zero halo:
+// positions run over batch x (nr+3) x (nz+3), and the halo points hold zeros,
+// so every tap of a 3x3 convolution is a fixed offset in the position index
+// (no boundary tests).  The network output is FP32, position-major, without
+// the halo.
+//
+// Convolutions (forward and data gradient) run on the fifth-generation tensor
+// cores: per tile of 128 positions, three bands of 130 input positions (the
+// rows above, at and below the tile, one position either side) are copied by
+// the tensor memory accelerator (one 3-D box per band: contiguous 2080-byte
+// runs of every plane) into shared memory, where a plane of a band is exactly
+// the no-swizzle K-major operand layout (8 rows x 16 bytes per core matrix);
+// each tap is the band shifted by one row (a different start address of the
+// same shared-memory descriptor), and tcgen05.mma accumulates the 9 taps in
+// tensor memory; the epilogue reads it back with tcgen05.ld and stores each
+// plane coalesced.  Weight gradients use mma.sync (positions as the reduction
+// dimension).
 //   forward      out[q][o] = b[o] + sum_{tap, c} W[tap][o][c] in[q + off(tap)][c]
 //   data grad    dIn[q][c] = sum_{tap, o} W[8 - tap][o][c] dOut[q + off(tap)][o]
 //                (the same kernel with the flipped, transposed weights), times
 //                the ReLU derivative of the layer below
 //   weight grad  dW[tap][o][c] = sum_q dOut[q][o] in[q + off(tap)][c]
-// with off(tap) the neighbour (dy, dx) = (tap / 3 - 1, tap % 3 - 1) and zero
-// outside the grid.  FP32 master weights and Adam state (Kingma & Ba 2015).
+// with off(tap) the neighbour (dy, dx) = (tap / 3 - 1, tap % 3 - 1).  FP32
+// master weights and Adam state (Kingma & Ba 2015).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <vector>
@@ -24,9 +41,11 @@ namespace pic {
 namespace {
 
 typedef __nv_bfloat16 bf16;
-constexpr int kBM = 64;        // positions per block of the convolution kernels
+constexpr int kBM = 64;        // positions per step of the weight-gradient kernel
 constexpr int kMaxL = 8;       // most layers
 constexpr int kWChunk = 2048;  // positions per block of the weight-gradient kernel
+constexpr int kTM = 128;       // positions per tile of the tensor-core convolution (MMA M)
+constexpr int kBand = kTM + 2; // input rows per band
 
 __device__ __forceinline__ void mma16816(float c[4], const uint32_t a[4], const uint32_t b[2]) {
   asm volatile(
@@ -42,120 +61,339 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 }
 
 struct Geo {
-  int H, W;
-  long long P, npos;  // points per sample, batch x P
+  int H, W;             // grid points along r and z
+  int Hp, Wp;           // with the halo
+  int P, Pp;            // points per sample without / with the halo
+  int npos, npp;        // batch x P, batch x Pp
+  long long ps;         // elements between the planes of an activation buffer (capacity x 8)
 };
 
-// neighbour of position q at (dy, dx), or -1 outside the grid
-__device__ __forceinline__ long long neighbour(const Geo &g, long long q, int dy, int dx) {
-  long long b = q / g.P;
-  int p = (int)(q - b * g.P);
-  int y = p / g.W, x = p - y * g.W;
-  int yy = y + dy, xx = x + dx;
-  if (yy < 0 || yy >= g.H || xx < 0 || xx >= g.W) return -1;
-  return b * g.P + (long long)yy * g.W + xx;
+// position q of the haloed grid: interior?  (*qu: its index without the halo)
+__device__ __forceinline__ bool interior(const Geo &g, int q, int *qu) {
+  const int b = q / g.Pp;
+  const int r = q - b * g.Pp;
+  const int yp = r / g.Wp, xp = r - yp * g.Wp;
+  *qu = b * g.P + (yp - 1) * g.W + (xp - 1);
+  return yp >= 1 && yp <= g.H && xp >= 1 && xp <= g.W;
 }
 
-// MODE 0: + bias, ReLU, BF16 out; 1: + bias, FP32 out; 2: times (mask > 0), BF16 out
-template <int CIN, int COUT, int MODE>
-__global__ void __launch_bounds__(128) k_conv(Geo g, const bf16 *__restrict__ in,
-                                              const bf16 *__restrict__ w,
-                                              const float *__restrict__ bias,
-                                              const bf16 *__restrict__ mask, void *out) {
-  constexpr int SA = CIN + 8;  // row stride in shared memory (conflict-free fragments)
-  constexpr int CH = CIN / 8;  // 16-byte chunks per row
-  constexpr int NT = COUT / 8;
-  __shared__ __align__(16) bf16 As[kBM * SA];
-  __shared__ __align__(16) bf16 Ws[COUT * SA];
-  __shared__ long long rowq[kBM];
-  __shared__ int rowy[kBM], rowx[kBM];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int gq = lane >> 2, t4 = lane & 3;
-  const long long m0 = (long long)blockIdx.x * kBM;
-  if (tid < kBM) {
-    long long q = m0 + tid;
-    if (q < g.npos) {
-      long long b = q / g.P;
-      int p = (int)(q - b * g.P);
-      rowy[tid] = p / g.W;
-      rowx[tid] = p - (p / g.W) * g.W;
-      rowq[tid] = q;
-    } else {
-      rowy[tid] = -1000000;
-      rowx[tid] = 0;
-      rowq[tid] = 0;
-    }
+// ---- tensor-core convolution ------------------------------------------------
+
+// Shared memory of one CTA: kStages buffers of three bands (each CIN/8 planes
+// of kBand 16-byte rows, as the 3-D box lands), the nine taps' weights (CIN/8
+// planes of COUT 16-byte rows each), the bias, the mbarriers (per stage: bands
+// landed / stage free; per accumulator: MMAs done / epilogue done), an abort
+// flag and the tensor-memory address.
+constexpr int kStages = 3;
+
+template <int CIN, int COUT>
+struct TcLayout {
+  static constexpr int kPlanes = CIN / 8;
+  static constexpr int kLboA = kBand * 16;
+  static constexpr int kBandBytes = (kPlanes * kLboA + 127) / 128 * 128;  // copy destinations 128-byte aligned
+  static constexpr int kStageBytes = 3 * kBandBytes;
+  static constexpr int kLboB = COUT * 16;
+  static constexpr int kTapBytes = kPlanes * kLboB;
+  static constexpr int kOffW = kStages * kStageBytes;
+  static constexpr int kOffBias = kOffW + 9 * kTapBytes;
+  static constexpr int kOffBar = kOffBias + COUT * 4;
+  static constexpr int kBytes = kOffBar + 96;
+  static constexpr int kTmemCols = 2 * COUT < 32 ? 32 : 2 * COUT;  // two accumulators
+  static constexpr uint32_t kTxBytes = 3u * kPlanes * kBand * 16u;
+  static constexpr int kEpiWarps = COUT >= 32 ? 8 : 4;  // two per TMEM lane quarter for 64 columns
+  static constexpr int kThreads = 64 + 32 * kEpiWarps;   // warp 0 copies, warp 1 issues MMAs
+  static_assert(kBandBytes % 128 == 0 && kTapBytes % 128 == 0 && kOffBar % 8 == 0, "alignment");
+  static_assert(kTmemCols == 32 || kTmemCols == 64 || kTmemCols == 128 || kTmemCols == 256, "TMEM");
+  static_assert(kBytes <= 227 * 1024, "shared memory");
+};
+
+struct ConvArgs {
+  Geo g;
+  const bf16 *w;       // [9][COUT][CIN]
+  const float *bias;   // [COUT] (modes 0, 1)
+  const bf16 *mask;    // mode 2: ReLU output of the layer below, BF16 planes
+  void *out;           // modes 0, 2: BF16 planes [COUT/8][ps]; mode 1: FP32 [npos][COUT]
+  int ntiles;
+  int *err;            // bit 0: a wait gave up; bit 2: misaligned shared memory
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// shared-memory matrix descriptor: no swizzle, K-major core matrices of 8 rows
+// x 16 bytes; lbo = bytes between core matrices along K, sbo = along M/N
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// bounded wait on an mbarrier phase (about a second at most); gives up early
+// when another role has raised the abort flag, and raises it when it gives up
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, volatile int *abort) {
+  for (int it = 0; it < (1 << 22); ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((it & 255) == 255 && *abort) return false;
   }
-  float acc[NT][4];
+  *abort = 1;
+  return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// the three bands of tile t into stage st (one thread)
+template <int CIN, int COUT>
+__device__ __forceinline__ void load_bands(const CUtensorMap *tm, const Geo &g, int t, int st,
+                                           uint32_t base, uint32_t bar) {
+  using Lt = TcLayout<CIN, COUT>;
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+               "r"(Lt::kTxBytes)
+               : "memory");
+  const int q0 = t * kTM;
 #pragma unroll
-  for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-  __syncthreads();
+  for (int dy = 0; dy < 3; ++dy) {
+    const int row = q0 + (dy - 1) * g.Wp - 1;
+    const uint32_t dst = base + st * Lt::kStageBytes + dy * Lt::kBandBytes;
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(tm), "r"(0), "r"(row), "r"(0), "r"(bar)
+        : "memory");
+  }
+}
+
+// the 9 taps x CIN/16 MMAs of the tile in stage st into accumulator j (one
+// thread); the descriptors differ only in their start addresses, which stay
+// below 256 KB, so each is the first one plus a constant
+template <int CIN, int COUT>
+__device__ __forceinline__ void issue_mmas(uint32_t base, int st, int j, uint32_t tmem) {
+  using Lt = TcLayout<CIN, COUT>;
+  constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(COUT >> 3) << 17) |
+                             ((uint32_t)(kTM >> 4) << 24);  // f32 += bf16 x bf16, K-major A and B
+  const uint32_t d = tmem + (uint32_t)(j * COUT);
+  const uint64_t a0 = smem_desc(base + st * Lt::kStageBytes, Lt::kLboA, 128);
+  const uint64_t b0 = smem_desc(base + Lt::kOffW, Lt::kLboB, 128);
+#pragma unroll
   for (int tap = 0; tap < 9; ++tap) {
-    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-    for (int c = tid; c < kBM * CH; c += 128) {
-      const int r = c / CH, k8 = c - (c / CH) * CH;
-      const int yy = rowy[r] + dy, xx = rowx[r] + dx;
-      uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (yy >= 0 && yy < g.H && xx >= 0 && xx < g.W)
-        v = *reinterpret_cast<const uint4 *>(in + (rowq[r] + (long long)dy * g.W + dx) * CIN + k8 * 8);
-      *reinterpret_cast<uint4 *>(As + r * SA + k8 * 8) = v;
-    }
-    for (int c = tid; c < COUT * CH; c += 128) {
-      const int r = c / CH, k8 = c - (c / CH) * CH;
-      *reinterpret_cast<uint4 *>(Ws + r * SA + k8 * 8) =
-          *reinterpret_cast<const uint4 *>(w + ((long long)tap * COUT + r) * CIN + k8 * 8);
-    }
-    __syncthreads();
-    const bf16 *Aw = As + warp * 16 * SA;
 #pragma unroll
-    for (int k0 = 0; k0 < CIN; k0 += 16) {
-      uint32_t a[4];
-      a[0] = *reinterpret_cast<const uint32_t *>(Aw + gq * SA + k0 + 2 * t4);
-      a[1] = *reinterpret_cast<const uint32_t *>(Aw + (gq + 8) * SA + k0 + 2 * t4);
-      a[2] = *reinterpret_cast<const uint32_t *>(Aw + gq * SA + k0 + 8 + 2 * t4);
-      a[3] = *reinterpret_cast<const uint32_t *>(Aw + (gq + 8) * SA + k0 + 8 + 2 * t4);
-#pragma unroll
-      for (int n = 0; n < NT; ++n) {
-        uint32_t b[2];
-        b[0] = *reinterpret_cast<const uint32_t *>(Ws + (n * 8 + gq) * SA + k0 + 2 * t4);
-        b[1] = *reinterpret_cast<const uint32_t *>(Ws + (n * 8 + gq) * SA + k0 + 8 + 2 * t4);
-        mma16816(acc[n], a, b);
-      }
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int n = 0; n < NT; ++n) {
-#pragma unroll
-    for (int hf = 0; hf < 2; ++hf) {
-      const int row = warp * 16 + gq + 8 * hf;
-      const long long q = m0 + row;
-      if (q >= g.npos) continue;
-      const int col = n * 8 + 2 * t4;
-      float v0 = acc[n][2 * hf], v1 = acc[n][2 * hf + 1];
-      if (MODE == 0 || MODE == 1) {
-        v0 += bias[col];
-        v1 += bias[col + 1];
-      }
-      if (MODE == 0) {
-        v0 = fmaxf(v0, 0.f);
-        v1 = fmaxf(v1, 0.f);
-      }
-      if (MODE == 2) {
-        __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162 *>(mask + q * COUT + col);
-        if (!(__low2float(mk) > 0.f)) v0 = 0.f;
-        if (!(__high2float(mk) > 0.f)) v1 = 0.f;
-      }
-      if (MODE == 1)
-        *reinterpret_cast<float2 *>(static_cast<float *>(out) + q * COUT + col) = make_float2(v0, v1);
-      else
-        *reinterpret_cast<uint32_t *>(static_cast<bf16 *>(out) + q * COUT + col) = pack_bf16(v0, v1);
+    for (int kk = 0; kk < Lt::kPlanes / 2; ++kk) {
+      const uint64_t ad =
+          a0 + (uint64_t)(((tap / 3) * Lt::kBandBytes + (tap % 3) * 16 + 2 * kk * Lt::kLboA) >> 4);
+      const uint64_t bd = b0 + (uint64_t)((tap * Lt::kTapBytes + 2 * kk * Lt::kLboB) >> 4);
+      const uint32_t acc = (tap | kk) != 0;
+      asm volatile(
+          "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+          "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+          "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
     }
   }
 }
 
-// dW[tap][o][c] += sum over a chunk of positions; grid (chunks, 9).  The
-// centre tap also accumulates the bias gradient.
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+// N FP32 columns (16 or 32) of this thread's TMEM lane, waited for inside the
+// same statement (the registers are not valid before tcgen05.wait::ld)
+template <int N>
+__device__ __forceinline__ void tmem_ld(uint32_t ta, float *v) {
+  uint32_t r[N];
+  if constexpr (N == 16)
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(ta)
+        : "memory");
+  else
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(ta)
+        : "memory");
+#pragma unroll
+  for (int i = 0; i < N; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// tile t's results from accumulator j: thread = one position (TMEM lane
+// 32 quarter + lane), columns cbeg .. cbeg + N - 1
+template <int COUT, int MODE, int N>
+__device__ __forceinline__ void epilogue(const ConvArgs &a, const float *sbias, int t, int j,
+                                         uint32_t tmem, int quarter, int cbeg) {
+  const int lane = threadIdx.x & 31;
+  const int q = t * kTM + 32 * quarter + lane;
+  int qu = 0;
+  const bool live = q < a.g.npp;
+  const bool in = live && interior(a.g, q, &qu);
+  float v[N];
+  tmem_ld<N>(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(j * COUT + cbeg), v);
+  if (MODE == 1) {
+    if (in) {
+      float4 *o = reinterpret_cast<float4 *>(static_cast<float *>(a.out) + (long long)qu * COUT + cbeg);
+#pragma unroll
+      for (int i = 0; i < N / 4; ++i)
+        o[i] = make_float4(v[4 * i] + sbias[cbeg + 4 * i], v[4 * i + 1] + sbias[cbeg + 4 * i + 1],
+                           v[4 * i + 2] + sbias[cbeg + 4 * i + 2], v[4 * i + 3] + sbias[cbeg + 4 * i + 3]);
+    }
+    return;
+  }
+  if (!live) return;
+#pragma unroll
+  for (int k = 0; k < N / 8; ++k) {
+    const long long off = (long long)((cbeg >> 3) + k) * a.g.ps + (long long)q * 8;
+    float *w = v + 8 * k;
+    if (MODE == 0) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) w[i] = in ? fmaxf(w[i] + sbias[cbeg + 8 * k + i], 0.f) : 0.f;
+    } else {
+      uint4 m = *reinterpret_cast<const uint4 *>(a.mask + off);
+      const bf16 *mb = reinterpret_cast<const bf16 *>(&m);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) w[i] = (in && __bfloat162float(mb[i]) > 0.f) ? w[i] : 0.f;
+    }
+    *reinterpret_cast<uint4 *>(static_cast<bf16 *>(a.out) + off) =
+        make_uint4(pack_bf16(w[0], w[1]), pack_bf16(w[2], w[3]), pack_bf16(w[4], w[5]),
+                   pack_bf16(w[6], w[7]));
+  }
+}
+
+// MODE 0: + bias, ReLU, BF16 out (halo points zero); 1: + bias, FP32 out
+// without the halo; 2: times (mask > 0), BF16 out (halo points zero).
+// Persistent and warp-specialised: CTA b takes tiles b, b + grid, ...; warp 0
+// copies the bands of the coming tiles into a ring of kStages stages, warp 1
+// issues each tile's MMAs into one of two TMEM accumulators as soon as its
+// bands have landed and the accumulator is drained, and the remaining warps
+// drain the accumulators (two warps per TMEM lane quarter for 64 channels),
+// all ordered by mbarriers.
+template <int CIN, int COUT, int MODE>
+__global__ void __launch_bounds__(TcLayout<CIN, COUT>::kThreads)
+    k_conv_tc(const __grid_constant__ CUtensorMap tm, ConvArgs a) {
+  using Lt = TcLayout<CIN, COUT>;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t base = smem_u32(sm);
+  if ((base & 1023u) != 0u) {  // uniform: every thread sees the same base
+    if (tid == 0) atomicOr(a.err, 4);
+    return;
+  }
+  const uint32_t bar = base + Lt::kOffBar;
+  auto full = [&](int st) { return bar + 8u * st; };
+  auto empty = [&](int st) { return bar + 24u + 8u * st; };
+  auto accf = [&](int j) { return bar + 48u + 8u * j; };
+  auto acce = [&](int j) { return bar + 64u + 8u * j; };
+  volatile int *abort = reinterpret_cast<volatile int *>(sm + Lt::kOffBar + 80);
+  uint32_t *slot = reinterpret_cast<uint32_t *>(sm + Lt::kOffBar + 84);
+  float *sbias = reinterpret_cast<float *>(sm + Lt::kOffBias);
+  if (tid == 0) {
+    for (int k = 0; k < 3; ++k) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full(k)));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(empty(k)));
+    }
+    for (int k = 0; k < 2; ++k) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(accf(k)));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(acce(k)), "n"(Lt::kEpiWarps));
+    }
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(slot)),
+                 "n"(Lt::kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  for (int e = tid; e < 9 * COUT * Lt::kPlanes; e += blockDim.x) {
+    const int tap = e / (COUT * Lt::kPlanes), r = e - tap * (COUT * Lt::kPlanes);
+    const int o = r / Lt::kPlanes, ch = r - o * Lt::kPlanes;
+    *reinterpret_cast<uint4 *>(sm + Lt::kOffW + tap * Lt::kTapBytes + ch * Lt::kLboB + o * 16) =
+        *reinterpret_cast<const uint4 *>(a.w + ((long long)tap * COUT + o) * CIN + ch * 8);
+  }
+  if (MODE != 2)
+    for (int o = tid; o < COUT; o += blockDim.x) sbias[o] = a.bias[o];
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
+  const int G = gridDim.x;
+  if (warp == 0) {
+    if (lane == 0) {
+      int last[3] = {-1, -1, -1};  // latest tile copied into each stage
+      int k = 0;
+      for (int t = blockIdx.x; t < a.ntiles; t += G, ++k) {
+        const int st = k % 3, u = k / 3;
+        if (u > 0 && !bar_wait(empty(st), (u - 1) & 1, abort)) break;
+        load_bands<CIN, COUT>(&tm, a.g, t, st, base, full(st));
+        last[st] = k;
+      }
+      if (*abort)  // let the copies in flight land (bounded)
+        for (int st = 0; st < 3; ++st)
+          if (last[st] >= 0) {
+            volatile int never = 0;
+            bar_wait(full(st), (last[st] / 3) & 1, &never);
+          }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int lastk = -1;
+      int k = 0;
+      for (int t = blockIdx.x; t < a.ntiles; t += G, ++k) {
+        const int st = k % 3, j = k & 1, v = k >> 1;
+        if (!bar_wait(full(st), (k / 3) & 1, abort)) break;
+        if (v > 0 && !bar_wait(acce(j), (v - 1) & 1, abort)) break;
+        tc_fence_after();
+        issue_mmas<CIN, COUT>(base, st, j, tmem);
+        tc_commit(empty(st));
+        tc_commit(accf(j));
+        lastk = k;
+      }
+      if (*abort && lastk >= 0) {  // let the MMAs in flight finish (bounded)
+        volatile int never = 0;
+        bar_wait(accf(lastk & 1), (lastk >> 1) & 1, &never);
+      }
+    }
+  } else {
+    const int ew = warp - 2, quarter = warp & 3;
+    constexpr int N = COUT >= 32 ? COUT / 2 : COUT;
+    const int cbeg = COUT >= 32 ? (ew >> 2) * N : 0;
+    int k = 0;
+    for (int t = blockIdx.x; t < a.ntiles; t += G, ++k) {
+      const int j = k & 1, v = k >> 1;
+      // warp-uniform: tcgen05.ld needs the whole warp
+      if (!__all_sync(0xffffffffu, bar_wait(accf(j), v & 1, abort))) break;
+      tc_fence_after();
+      epilogue<COUT, MODE, N>(a, sbias, t, j, tmem, quarter, cbeg);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce(j)) : "memory");
+    }
+  }
+  __syncthreads();
+  if (tid == 0 && *abort) atomicOr(a.err, 1);
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "n"(Lt::kTmemCols));
+}
+
+// dW[tap][o][c] += sum over a chunk of positions of the haloed grid (dOut is
+// zero on the halo); grid (chunks, 9).  The centre tap also accumulates the
+// bias gradient.
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(128) k_wgrad(Geo g, const bf16 *__restrict__ in,
                                                const bf16 *__restrict__ dz, float *dw,
@@ -179,24 +417,24 @@ __global__ void __launch_bounds__(128) k_wgrad(Geo g, const bf16 *__restrict__ i
     for (int j = 0; j < WN; ++j) acc[i][j][0] = acc[i][j][1] = acc[i][j][2] = acc[i][j][3] = 0.f;
   float bsum = 0.f;  // bias gradient of channel tid (centre tap, tid < COUT)
   const long long c0 = (long long)blockIdx.x * kWChunk;
-  for (long long s0 = c0; s0 < c0 + kWChunk && s0 < g.npos; s0 += kBM) {
+  const long long off = (long long)dy * g.Wp + dx;
+  for (long long s0 = c0; s0 < c0 + kWChunk && s0 < g.npp; s0 += kBM) {
     for (int e = tid; e < kBM * (COUT / 8); e += 128) {
-      const int r = e / (COUT / 8), k8 = e - (e / (COUT / 8)) * (COUT / 8);
+      const int k8 = e / kBM, r = e - k8 * kBM;
       const long long q = s0 + r;
       uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (q < g.npos) v = *reinterpret_cast<const uint4 *>(dz + q * COUT + k8 * 8);
+      if (q < g.npp) v = *reinterpret_cast<const uint4 *>(dz + k8 * g.ps + q * 8);
       const bf16 *pv = reinterpret_cast<const bf16 *>(&v);
 #pragma unroll
       for (int j = 0; j < 8; ++j) Dt[(k8 * 8 + j) * SK + r] = pv[j];
     }
     for (int e = tid; e < kBM * (CIN / 8); e += 128) {
-      const int r = e / (CIN / 8), k8 = e - (e / (CIN / 8)) * (CIN / 8);
+      const int k8 = e / kBM, r = e - k8 * kBM;
       const long long q = s0 + r;
       uint4 v = make_uint4(0u, 0u, 0u, 0u);
-      if (q < g.npos) {
-        long long nq = neighbour(g, q, dy, dx);
-        if (nq >= 0) v = *reinterpret_cast<const uint4 *>(in + nq * CIN + k8 * 8);
-      }
+      const long long nq = q + off;
+      if (q < g.npp && nq >= 0 && nq < g.npp)
+        v = *reinterpret_cast<const uint4 *>(in + k8 * g.ps + nq * 8);
       const bf16 *pv = reinterpret_cast<const bf16 *>(&v);
 #pragma unroll
       for (int j = 0; j < 8; ++j) It[(k8 * 8 + j) * SK + r] = pv[j];
@@ -241,15 +479,24 @@ __global__ void __launch_bounds__(128) k_wgrad(Geo g, const bf16 *__restrict__ i
   if (tap == 4 && tid < COUT) atomicAdd(&db[tid], bsum);
 }
 
-// NCHW FP32 [B][c_real][H][W] -> position-major BF16 [B*P][cp] (zero padding channels)
+// NCHW FP32 [B][c_real][H][W] -> BF16 planes of the haloed grid (zero on the
+// halo and in the padding channels); thread = (position, plane)
 __global__ void k_pack(Geo g, int c_real, int cp, const float *x, bf16 *out) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= g.npos * cp) return;
-  long long q = t / cp;
-  int c = (int)(t - q * cp);
-  long long b = q / g.P, p = q - b * g.P;
-  float v = c < c_real ? x[(b * c_real + c) * g.P + p] : 0.f;
-  out[t] = __float2bfloat16_rn(v);
+  if (t >= (long long)g.npp * (cp / 8)) return;
+  const int k = (int)(t / g.npp), q = (int)(t - (long long)k * g.npp);
+  int qu;
+  const bool in = interior(g, q, &qu);
+  const int b = qu / g.P, p = qu - b * g.P;
+  float v[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int c = 8 * k + i;
+    v[i] = in && c < c_real ? x[((long long)b * c_real + c) * g.P + p] : 0.f;
+  }
+  *reinterpret_cast<uint4 *>(out + k * g.ps + (long long)q * 8) =
+      make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]),
+                 pack_bf16(v[6], v[7]));
 }
 
 // position-major FP32 [B*P][cp] -> NCHW [B][c_real][H][W]
@@ -260,30 +507,32 @@ __global__ void k_unpack(Geo g, int c_real, int cp, const float *y, float *out) 
   long long r = t - b * c_real * g.P;
   int c = (int)(r / g.P);
   long long p = r - (long long)c * g.P;
-  out[t] = y[(b * g.P + p) * cp + c];
+  out[t] = y[((long long)b * g.P + p) * cp + c];
 }
 
 // loss = mean over the batch of sum_valid (y - t)^2 / nvalid; dZ of the last
-// layer (BF16, cp channels) = d loss / d y.  Valid: channel 0 on rows < H-1
-// (E_r), channel 1 on columns < W-1 (E_z).
+// layer (BF16, cp channels, haloed grid, zero on the halo) = d loss / d y.
+// Valid: channel 0 on rows < H-1 (E_r), channel 1 on columns < W-1 (E_z).
 __global__ void k_loss(Geo g, int cp, const float *y, const float *t, int batch, double nvalid,
                        bf16 *dz, double *acc) {
-  long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
   double l = 0.0;
-  if (q < g.npos) {
-    long long b = q / g.P;
-    int p = (int)(q - b * g.P);
+  if (q < g.npp) {
+    int qu;
+    const bool in = interior(g, q, &qu);
+    const int b = qu / g.P;
+    const int p = qu - b * g.P;
     int yy = p / g.W, xx = p - (p / g.W) * g.W;
     const float sc = (float)(2.0 / ((double)batch * nvalid));
     for (int c = 0; c < cp; ++c) {
       float d = 0.f;
-      bool valid = (c == 0 && yy < g.H - 1) || (c == 1 && xx < g.W - 1);
+      bool valid = in && ((c == 0 && yy < g.H - 1) || (c == 1 && xx < g.W - 1));
       if (valid) {
-        float r = y[q * cp + c] - t[(b * 2 + c) * g.P + p];
+        float r = y[(long long)qu * cp + c] - t[((long long)b * 2 + c) * g.P + p];
         l += (double)r * (double)r;
         d = sc * r;
       }
-      dz[q * cp + c] = __float2bfloat16_rn(d);
+      dz[(c >> 3) * g.ps + (long long)q * 8 + (c & 7)] = __float2bfloat16_rn(d);
     }
   }
 #pragma unroll
@@ -353,17 +602,21 @@ int pad16(int c) { return (c + 15) / 16 * 16; }
 using namespace pic;
 
 struct pic_cnn {
+  CUtensorMap tm_act[kMaxL];  // band copies of act[l] (cinp[l] channels)
+  CUtensorMap tm_dz[2][2];    // of dz[k] with 16 / 64 channels
   pic_cnn_config cfg;
   cudaStream_t s;
-  Geo geo1;            // batch 1
+  int nsm;
+  int *err;            // set by the tensor-core kernels when a wait gives up
   LayerMeta M;
   long long nparam, ngpad;
   float *master, *m, *v, *gpad, *gtmp;
   bf16 *wf[kMaxL], *wb[kMaxL];
   float *bias[kMaxL];
-  bf16 *act[kMaxL];    // act[0]: packed input; act[l]: output of layer l-1 (hidden)
-  float *out;          // [bmax*P][coutp(last)]
-  bf16 *dz[2];         // gradient ping-pong [bmax*P][64]
+  bf16 *act[kMaxL];    // act[0]: packed input; act[l]: output of layer l-1 (hidden);
+                       // haloed grid [bmax*Pp][cinp[l]]
+  float *out;          // [bmax*P][coutp(last)], without the halo
+  bf16 *dz[2];         // gradient ping-pong, haloed grid [bmax*Pp][64]
   double *lossacc;
   int t;               // Adam steps taken
 };
@@ -409,6 +662,7 @@ bool layout(pic_cnn *x, const pic_cnn_config *c, char *base, size_t *used) {
   meta(c, x->M, x->nparam, x->ngpad);
   const long long P = (long long)(c->nr + 1) * (c->nz + 1);
   const long long NP = P * c->batch;
+  const long long NPP = (long long)(c->nr + 3) * (c->nz + 3) * c->batch;
   x->master = (float *)K.take(x->nparam * 4);
   x->m = (float *)K.take(x->nparam * 4);
   x->v = (float *)K.take(x->nparam * 4);
@@ -419,12 +673,13 @@ bool layout(pic_cnn *x, const pic_cnn_config *c, char *base, size_t *used) {
     x->wf[l] = (bf16 *)K.take(nw * 2);
     x->wb[l] = (bf16 *)K.take(nw * 2);
     x->bias[l] = (float *)K.take(x->M.coutp[l] * 4);
-    x->act[l] = (bf16 *)K.take((size_t)NP * x->M.cinp[l] * 2);
+    x->act[l] = (bf16 *)K.take((size_t)NPP * x->M.cinp[l] * 2);
   }
   x->out = (float *)K.take((size_t)NP * x->M.coutp[x->M.L - 1] * 4);
-  x->dz[0] = (bf16 *)K.take((size_t)NP * 64 * 2);
-  x->dz[1] = (bf16 *)K.take((size_t)NP * 64 * 2);
+  x->dz[0] = (bf16 *)K.take((size_t)NPP * 64 * 2);
+  x->dz[1] = (bf16 *)K.take((size_t)NPP * 64 * 2);
   x->lossacc = (double *)K.take(256);
+  x->err = (int *)K.take(256);
   *used = K.off + 256;
   return true;
 }
@@ -433,9 +688,78 @@ Geo geo(const pic_cnn *x, int batch) {
   Geo g;
   g.H = x->cfg.nr + 1;
   g.W = x->cfg.nz + 1;
-  g.P = (long long)g.H * g.W;
+  g.Hp = g.H + 2;
+  g.Wp = g.W + 2;
+  g.P = g.H * g.W;
+  g.Pp = g.Hp * g.Wp;
   g.npos = g.P * batch;
+  g.npp = g.Pp * batch;
+  g.ps = 8LL * g.Pp * x->cfg.batch;
   return g;
+}
+
+// 3-D tensor map of a plane buffer (8 channels x rows x cin/8 planes): one box
+// = one band of kBand positions of every plane, no swizzle, zero outside
+cudaError_t encode_rows(CUtensorMap *m, void *ptr, int cin, long long rows) {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return (PFN_cuTensorMapEncodeTiled_v12000)f;
+  }();
+  if (!fn) return cudaErrorNotSupported;
+  cuuint64_t dim[3] = {8, (cuuint64_t)rows, (cuuint64_t)(cin / 8)};
+  cuuint64_t str[2] = {16, (cuuint64_t)rows * 16};
+  cuuint32_t box[3] = {8, (cuuint32_t)kBand, (cuuint32_t)(cin / 8)}, es[3] = {1, 1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, ptr, dim, str, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t encode_maps(pic_cnn *x) {
+  const long long rows = (long long)(x->cfg.nr + 3) * (x->cfg.nz + 3) * x->cfg.batch;
+  cudaError_t e = cudaSuccess;
+  for (int l = 0; l < x->M.L && e == cudaSuccess; ++l)
+    e = encode_rows(&x->tm_act[l], x->act[l], x->M.cinp[l], rows);
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    e = encode_rows(&x->tm_dz[k][0], x->dz[k], 16, rows);
+    if (e == cudaSuccess) e = encode_rows(&x->tm_dz[k][1], x->dz[k], 64, rows);
+  }
+  return e;
+}
+
+// resident CTAs per SM of one tensor-core kernel (shared memory and the 512
+// tensor-memory columns), with its dynamic shared memory size set once
+template <int CIN, int COUT, int MODE>
+int tc_blocks_per_sm() {
+  static const int n = [] {
+    using Lt = TcLayout<CIN, COUT>;
+    auto k = k_conv_tc<CIN, COUT, MODE>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Lt::kBytes) !=
+        cudaSuccess)
+      return 0;
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, Lt::kThreads, Lt::kBytes) != cudaSuccess)
+      return 0;
+    return b < 512 / Lt::kTmemCols ? b : 512 / Lt::kTmemCols;
+  }();
+  return n;
+}
+
+template <int CIN, int COUT, int MODE>
+cudaError_t conv_tc(pic_cnn *x, const CUtensorMap &tm, const Geo &g, const bf16 *w,
+                    const float *bias, const bf16 *mask, void *out) {
+  using Lt = TcLayout<CIN, COUT>;
+  const int per_sm = tc_blocks_per_sm<CIN, COUT, MODE>();
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  ConvArgs a{g, w, bias, mask, out, (g.npp + kTM - 1) / kTM, x->err};
+  const int grid = a.ntiles < x->nsm * per_sm ? a.ntiles : x->nsm * per_sm;
+  k_conv_tc<CIN, COUT, MODE><<<grid, Lt::kThreads, Lt::kBytes, x->s>>>(tm, a);
+  return cudaGetLastError();
 }
 
 cudaError_t publish(pic_cnn *x) {
@@ -450,22 +774,20 @@ cudaError_t publish(pic_cnn *x) {
 cudaError_t conv_fwd(pic_cnn *x, int l, const Geo &g) {
   const int ci = x->M.cinp[l], co = x->M.coutp[l];
   const bool last = l + 1 == x->M.L;
-  dim3 grid((unsigned)((g.npos + kBM - 1) / kBM));
   void *out = last ? (void *)x->out : (void *)x->act[l + 1];
+  const CUtensorMap &tm = x->tm_act[l];
   if (ci == 16 && co == 64 && !last)
-    k_conv<16, 64, 0><<<grid, 128, 0, x->s>>>(g, x->act[l], x->wf[l], x->bias[l], nullptr, out);
-  else if (ci == 64 && co == 64 && !last)
-    k_conv<64, 64, 0><<<grid, 128, 0, x->s>>>(g, x->act[l], x->wf[l], x->bias[l], nullptr, out);
-  else if (ci == 64 && co == 16 && last)
-    k_conv<64, 16, 1><<<grid, 128, 0, x->s>>>(g, x->act[l], x->wf[l], x->bias[l], nullptr, out);
-  else
-    return cudaErrorInvalidValue;
-  return cudaGetLastError();
+    return conv_tc<16, 64, 0>(x, tm, g, x->wf[l], x->bias[l], nullptr, out);
+  if (ci == 64 && co == 64 && !last)
+    return conv_tc<64, 64, 0>(x, tm, g, x->wf[l], x->bias[l], nullptr, out);
+  if (ci == 64 && co == 16 && last)
+    return conv_tc<64, 16, 1>(x, tm, g, x->wf[l], x->bias[l], nullptr, out);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t forward(pic_cnn *x, const float *xin, int batch) {
   Geo g = geo(x, batch);
-  long long n = g.npos * 16;
+  long long n = (long long)g.npp * 2;  // positions x planes of the 16 input channels
   k_pack<<<(unsigned)((n + 255) / 256), 256, 0, x->s>>>(g, PIC_CNN_IN, 16, xin, x->act[0]);
   for (int l = 0; l < x->M.L; ++l) {
     cudaError_t e = conv_fwd(x, l, g);
@@ -483,12 +805,11 @@ cudaError_t backward(pic_cnn *x, const float *t, int batch) {
   if (e != cudaSuccess) return e;
   const double nvalid = (double)x->cfg.nr * (x->cfg.nz + 1) + (double)(x->cfg.nr + 1) * x->cfg.nz;
   const int cpo = x->M.coutp[L - 1];
-  k_loss<<<(unsigned)((g.npos + 255) / 256), 256, 0, x->s>>>(g, cpo, x->out, t, batch, nvalid,
-                                                             x->dz[0], x->lossacc);
+  k_loss<<<(unsigned)((g.npp + 255) / 256), 256, 0, x->s>>>(g, cpo, x->out, t, batch, nvalid,
+                                                            x->dz[0], x->lossacc);
   int cur = 0;
-  const unsigned nch = (unsigned)((g.npos + kWChunk - 1) / kWChunk);
+  const unsigned nch = (unsigned)((g.npp + kWChunk - 1) / kWChunk);
   dim3 wg(nch, 9);
-  dim3 cg((unsigned)((g.npos + kBM - 1) / kBM));
   for (int l = L - 1; l >= 0; --l) {
     const int ci = x->M.cinp[l], co = x->M.coutp[l];
     float *dw = x->gpad + x->M.offdw[l];
@@ -501,18 +822,28 @@ cudaError_t backward(pic_cnn *x, const float *t, int batch) {
     if (l == 0) break;
     // data gradient into the layer below, times its ReLU derivative
     bf16 *nx = x->dz[cur ^ 1];
+    const CUtensorMap &tmz = x->tm_dz[cur][co == 16 ? 0 : 1];
+    cudaError_t ce;
     if (co == 16 && ci == 64)
-      k_conv<16, 64, 2><<<cg, 128, 0, x->s>>>(g, dzl, x->wb[l], nullptr, x->act[l], nx);
+      ce = conv_tc<16, 64, 2>(x, tmz, g, x->wb[l], nullptr, x->act[l], nx);
     else if (co == 64 && ci == 64)
-      k_conv<64, 64, 2><<<cg, 128, 0, x->s>>>(g, dzl, x->wb[l], nullptr, x->act[l], nx);
+      ce = conv_tc<64, 64, 2>(x, tmz, g, x->wb[l], nullptr, x->act[l], nx);
     else
       return cudaErrorInvalidValue;
+    if (ce != cudaSuccess) return ce;
     cur ^= 1;
   }
   return cudaGetLastError();
 }
 
 int rc(cudaError_t e) { return e == cudaSuccess ? PIC_OK : PIC_E_CUDA; }
+
+// after a stream synchronisation: PIC_E_CUDA if a tensor-core kernel gave up
+int rc_err(pic_cnn *x, cudaError_t e) {
+  int h = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&h, x->err, sizeof(int), cudaMemcpyDeviceToHost);
+  return e == cudaSuccess && h == 0 ? PIC_OK : PIC_E_CUDA;
+}
 
 }  // namespace
 
@@ -538,7 +869,13 @@ int pic_cnn_init(const pic_cnn_config *c, void *ws, size_t bytes, void *stream, 
   x->t = 0;
   size_t used = 0;
   layout(x, c, (char *)ws, &used);
-  x->geo1 = geo(x, 1);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&x->nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      encode_maps(x) != cudaSuccess) {
+    delete x;
+    return PIC_E_CUDA;
+  }
   // He-normal weights from a fixed-seed generator on the host, zero biases
   std::vector<float> h(x->nparam, 0.f);
   uint64_t st = c->seed * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
@@ -558,6 +895,7 @@ int pic_cnn_init(const pic_cnn_config *c, void *ws, size_t bytes, void *stream, 
   cudaError_t e = cudaMemcpyAsync(x->master, h.data(), x->nparam * 4, cudaMemcpyHostToDevice, x->s);
   if (e == cudaSuccess) e = cudaMemsetAsync(x->m, 0, x->nparam * 4, x->s);
   if (e == cudaSuccess) e = cudaMemsetAsync(x->v, 0, x->nparam * 4, x->s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(x->err, 0, sizeof(int), x->s);
   if (e == cudaSuccess) e = publish(x);
   if (e == cudaSuccess) e = cudaStreamSynchronize(x->s);
   if (e != cudaSuccess) {
@@ -598,7 +936,7 @@ int pic_cnn_forward(pic_cnn *x, const float *xin, int batch, float *y) {
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(x->s);
-  return rc(e);
+  return rc_err(x, e);
 }
 
 int pic_cnn_loss_grad(pic_cnn *x, const float *xin, const float *t, int batch, double *loss,
@@ -615,7 +953,7 @@ int pic_cnn_loss_grad(pic_cnn *x, const float *xin, const float *t, int batch, d
     e = cudaMemcpyAsync(grad, x->gtmp, x->nparam * 4, cudaMemcpyDeviceToHost, x->s);
   if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, x->lossacc, 8, cudaMemcpyDeviceToHost, x->s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(x->s);
-  return rc(e);
+  return rc_err(x, e);
 }
 
 int pic_cnn_train_step(pic_cnn *x, const float *xin, const float *t, int batch, float lr,
@@ -633,7 +971,7 @@ int pic_cnn_train_step(pic_cnn *x, const float *xin, const float *t, int batch, 
   if (e == cudaSuccess) e = publish(x);
   if (e == cudaSuccess && loss) e = cudaMemcpyAsync(loss, x->lossacc, 8, cudaMemcpyDeviceToHost, x->s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(x->s);
-  return rc(e);
+  return rc_err(x, e);
 }
 
 }  // extern "C"
@@ -648,6 +986,7 @@ int cnn_forward_async(pic_cnn *x, const float *xin, const float **y_posmajor, in
   return PIC_OK;
 }
 cudaStream_t cnn_stream(const pic_cnn *x) { return x->s; }
+const int *cnn_err_flag(const pic_cnn *x) { return x->err; }
 int cnn_layers(const pic_cnn *x) { return x->M.L; }
 int cnn_grid(const pic_cnn *x, int *nr, int *nz) {
   *nr = x->cfg.nr;

@@ -22,6 +22,7 @@ int cnn_forward_async(pic_cnn *x, const float *xin, const float **y_posmajor, in
 int cnn_grid(const pic_cnn *x, int *nr, int *nz);
 cudaStream_t cnn_stream(const pic_cnn *x);
 int cnn_layers(const pic_cnn *x);
+const int *cnn_err_flag(const pic_cnn *x);
 }  // namespace pic
 
 struct pic_ctx {
@@ -1447,7 +1448,13 @@ int guess_start(pic_ctx *x, double v1, int *used) {
   }
   if (cudaMemcpyAsync(&bad, x->gbad, sizeof(int), cudaMemcpyDeviceToHost, x->s) != cudaSuccess)
     return PIC_E_CUDA;
+  int cnn_err = 0;
+  if (x->guess_mode == PIC_GUESS_CNN &&
+      cudaMemcpyAsync(&cnn_err, cnn_err_flag(x->cnn), sizeof(int), cudaMemcpyDeviceToHost, x->s) !=
+          cudaSuccess)
+    return PIC_E_CUDA;
   if (cudaStreamSynchronize(x->s) != cudaSuccess) return PIC_E_CUDA;
+  if (cnn_err) return PIC_E_CUDA;  // a tensor-core kernel of the network gave up a wait
   if (!bad) *used = x->guess_mode;
   return PIC_OK;
 }
