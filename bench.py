@@ -474,7 +474,7 @@ def run_ensemble_form(P, torch, dev, args, rank):
     torch.cuda.synchronize(dev)
     E = P.Ensemble(mem)
     E.step(args.warmup)
-    frac, ms_round = E.tune(rounds=3)
+    frac, pers, ms_round = E.tune(rounds=3)
     E.step(1)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
@@ -508,7 +508,9 @@ def run_ensemble_form(P, torch, dev, args, rank):
            "value": pushes / t_ens, "unit": UNIT, "ms_per_step": t_ens * 1e3 / args.steps,
            "sequential_value": p_seq / t_seq, "sequential_ms_per_step": t_seq * 1e3 / args.steps,
            "speedup_vs_sequential": (pushes / t_ens) / (p_seq / t_seq),
-           "tuner": {"push_grid_fraction": frac, "ms_per_round": ms_round},
+           "tuner": {"push_grid_fraction": frac, "persistent": pers,
+                     "ms_per_round": {"per_member": ms_round[:3], "persistent": ms_round[3:],
+                                      "fractions": [1.0, 0.5, 0.25]}},
            "timing": "host clock around whole ensemble steps (device synchronised)"}
     E.close()
     for pic in mem:
@@ -541,7 +543,7 @@ def run_ours(args):
     forms = args.forms.split(",")
     if "plain" not in forms:
         # profiling aids (no headline line is printed): the mixed form alone,
-        # and/or the learned start's network alone
+        # the learned start's network alone, and/or the ensemble alone
         out = {"profiling_only": True}
         if "mixed" in forms:
             cfgm = P.large_reactor(seed=replica_seed(1, rank), precision=P.PIC_MIXED)
@@ -552,6 +554,8 @@ def run_ours(args):
                         "push_ms_per_launch": rm["push_ms"] / max(rm["push_launches"], 1)})
         if "cnn" in forms:
             out["cnn"] = run_cnn_form(P, torch, dev)
+        if "ensemble" in forms:
+            out["ensemble"] = run_ensemble_form(P, torch, dev, args, rank)
         if rank == 0:
             print(json.dumps(out))
         return 0

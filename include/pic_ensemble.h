@@ -4,19 +4,30 @@
  * several independent discharges of any sizes side by side on one GPU.  Each
  * member is an ordinary pic_ctx (its own workspace and CUDA stream, created
  * with pic_init and loaded by the caller).  pic_ensemble_step advances all
- * members by whole steps: the Picard passes of the members are issued
- * together (one per member and round, each replayed from a CUDA graph
- * captured once per buffer configuration), so that kernels of different
- * members overlap on the GPU, with one host wait per round; members leave the
- * round loop as they converge.  Results are identical to stepping each
- * member alone with pic_step.
+ * members by whole steps in rounds: one Picard pass of every unconverged
+ * member per round, then one host wait; members leave the round loop as they
+ * converge.  A round is issued in one of two ways:
+ *   persistent (the default when every member has the same precision, both
+ *     species moving, no magnetic field): each member's pre-push part (E^{n+1/2}
+ *     and cleared currents) on its own stream, then on the ensemble's lead
+ *     stream, per species, one launch of the fast and one of the general push
+ *     kernel over every active member (work items = (member, virtual block);
+ *     each member's launch parameters are uploaded per round), then each
+ *     member's field solve on its own stream;
+ *   per member: each member's whole pass replayed from a CUDA graph captured
+ *     once per buffer configuration, the members' kernels overlapping on the GPU.
+ * Both give the same particles, fields and counts as stepping each member alone
+ * with pic_step (up to the summation order of the crossed charge).
  *
- * pic_ensemble_tune times candidate grid sizes of the persistent push kernels
- * (the particle tile each block strides over) on the ensemble's own state and
- * keeps the fastest.
+ * pic_ensemble_tune times whole rounds on the ensemble's own state for the
+ * candidates (per member | persistent) x (virtual grid of the push kernels:
+ * 1, 1/2, 1/4 of one resident wave, i.e. 1, 2, 4 particle tiles of 256 per
+ * block visit) and keeps the fastest.  The sort has no bin size to tune (it
+ * sorts by cell).
  *
- * Errors: PIC_OK or a negative PIC_E_* code of pic.h; the ensemble owns no
- * device memory and does not own its members (destroy them after it).
+ * Errors: PIC_OK or a negative PIC_E_* code of pic.h.  The ensemble owns a
+ * CUDA stream, events, 2 x ~90 KB of pinned host and device memory for the
+ * launch parameters, and none of its members (destroy them after it).
  */
 #ifndef PIC_ENSEMBLE_H
 #define PIC_ENSEMBLE_H
@@ -38,9 +49,16 @@ typedef struct pic_ensemble pic_ensemble;
 int pic_set_graphs(pic_ctx *ctx, int on);
 
 /* n members (1..PIC_ENSEMBLE_MAX), distinct, each ready to step; turns graph
- * replay on for every member.  PIC_E_CONFIG on invalid arguments. */
+ * replay on for every member and chooses persistent rounds where the members
+ * allow them.  PIC_E_CONFIG on invalid arguments, PIC_E_CUDA when the stream,
+ * events or staging cannot be created. */
 int pic_ensemble_create(pic_ctx *const *members, int n, pic_ensemble **out);
 void pic_ensemble_destroy(pic_ensemble *ens);
+
+/* Persistent rounds on (1) or per-member rounds (0).  PIC_E_CONFIG when on = 1
+ * and the members do not allow persistent rounds (precisions differ, fixed
+ * ions, a magnetic field). */
+int pic_ensemble_set_persistent(pic_ensemble *ens, int on);
 
 /* Advances every member by nsteps; stats (nullable) receives the last step's
  * statistics of each member (n entries).  The first member error stops the
@@ -48,11 +66,15 @@ void pic_ensemble_destroy(pic_ensemble *ens);
  * returned after the step. */
 int pic_ensemble_step(pic_ensemble *ens, int nsteps, pic_step_stats *stats);
 
-/* Times `rounds` Picard rounds of the whole ensemble for each candidate grid
- * fraction (1, 1/2, 1/4 of one resident wave of the push kernels), applies the
- * fastest and returns it in *frac_out (nullable) with the times per round in
- * ms_out[3] (nullable).  Changes no particle or field state. */
-int pic_ensemble_tune(pic_ensemble *ens, int rounds, float *frac_out, double *ms_out);
+/* Times `rounds` Picard rounds of the whole ensemble for each candidate:
+ * c = 0..2 per-member rounds and c = 3..5 persistent rounds, with the push
+ * kernels' grid fraction 1, 1/2, 1/4 of one resident wave (c % 3); applies the
+ * fastest and returns its fraction in *frac_out and 1 if persistent in
+ * *persistent_out (both nullable), with the best time per round of each
+ * candidate in ms_out[6] (nullable; -1 for a candidate the members do not
+ * allow).  Changes no particle or field state. */
+int pic_ensemble_tune(pic_ensemble *ens, int rounds, float *frac_out, int *persistent_out,
+                      double *ms_out);
 
 #ifdef __cplusplus
 }

@@ -146,7 +146,8 @@ def _load_lib():
     L.pic_ensemble_destroy.argtypes = [_P]
     L.pic_ensemble_destroy.restype = None
     L.pic_ensemble_step.argtypes = [_P, _I, _P]
-    L.pic_ensemble_tune.argtypes = [_P, _I, C.POINTER(C.c_float), C.POINTER(_D)]
+    L.pic_ensemble_set_persistent.argtypes = [_P, _I]
+    L.pic_ensemble_tune.argtypes = [_P, _I, C.POINTER(C.c_float), C.POINTER(_I), C.POINTER(_D)]
     L.pic_guess_sample.argtypes = [_P, _P, _P, C.POINTER(_I)]
     return L
 
@@ -683,8 +684,19 @@ class Ensemble:
             _check(rc, "pic_ensemble_step")
         return rc, [s.as_dict() for s in st]
 
+    def set_persistent(self, on=True):
+        """Persistent rounds (one push launch per species over all members) or
+        per-member rounds (each member's pass replayed from its CUDA graph)."""
+        _check(lib().pic_ensemble_set_persistent(self._h, int(bool(on))),
+               "pic_ensemble_set_persistent")
+
     def tune(self, rounds=3):
+        """(grid fraction, persistent?, best ms per round of the 6 candidates:
+        per-member rounds at fractions 1, 1/2, 1/4, then persistent ones; -1
+        where the members do not allow persistent rounds)."""
         f = C.c_float(0.0)
-        ms = (_D * 3)()
-        _check(lib().pic_ensemble_tune(self._h, int(rounds), C.byref(f), ms), "pic_ensemble_tune")
-        return float(f.value), list(ms)
+        pers = _I(0)
+        ms = (_D * 6)()
+        _check(lib().pic_ensemble_tune(self._h, int(rounds), C.byref(f), C.byref(pers), ms),
+               "pic_ensemble_tune")
+        return float(f.value), bool(pers.value), list(ms)

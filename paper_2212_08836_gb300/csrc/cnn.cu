@@ -79,32 +79,39 @@ __device__ __forceinline__ bool interior(const Geo &g, int q, int *qu) {
 
 // ---- tensor-core convolution ------------------------------------------------
 
+// A band is copied as whole 128-byte rows of its planes (8 positions x 8
+// channels): kGroups rows from the row holding its first position, so the
+// band starts (first position mod 8) positions into each plane copy, an
+// offset folded into the descriptors' start addresses like the taps' shifts.
+constexpr int kGroups = 18;  // 144 positions >= 7 + kBand
+
 // Shared memory of one CTA: kStages buffers of three bands (each CIN/8 planes
-// of kBand 16-byte rows, as the 3-D box lands), the nine taps' weights (CIN/8
+// of kGroups x 128 bytes, as the 3-D box lands), the nine taps' weights (CIN/8
 // planes of COUT 16-byte rows each), the bias, the mbarriers (per stage: bands
 // landed / stage free; per accumulator: MMAs done / epilogue done), an abort
-// flag and the tensor-memory address.
-constexpr int kStages = 3;
-
+// flag and the tensor-memory address.  As many stages (up to 4) as fit.
 template <int CIN, int COUT>
 struct TcLayout {
   static constexpr int kPlanes = CIN / 8;
-  static constexpr int kLboA = kBand * 16;
-  static constexpr int kBandBytes = (kPlanes * kLboA + 127) / 128 * 128;  // copy destinations 128-byte aligned
+  static constexpr int kLboA = kGroups * 128;
+  static constexpr int kBandBytes = kPlanes * kLboA;
   static constexpr int kStageBytes = 3 * kBandBytes;
   static constexpr int kLboB = COUT * 16;
   static constexpr int kTapBytes = kPlanes * kLboB;
+  static constexpr int kFixed = 9 * kTapBytes + COUT * 4 + 112;
+  static constexpr int kStages = (227 * 1024 - kFixed) / kStageBytes > 4 ? 4
+                                                                         : (227 * 1024 - kFixed) / kStageBytes;
   static constexpr int kOffW = kStages * kStageBytes;
   static constexpr int kOffBias = kOffW + 9 * kTapBytes;
   static constexpr int kOffBar = kOffBias + COUT * 4;
-  static constexpr int kBytes = kOffBar + 96;
+  static constexpr int kBytes = kOffBar + 112;
   static constexpr int kTmemCols = 2 * COUT < 32 ? 32 : 2 * COUT;  // two accumulators
-  static constexpr uint32_t kTxBytes = 3u * kPlanes * kBand * 16u;
+  static constexpr uint32_t kTxBytes = 3u * kPlanes * kGroups * 128u;
   static constexpr int kEpiWarps = COUT >= 32 ? 8 : 4;  // two per TMEM lane quarter for 64 columns
   static constexpr int kThreads = 64 + 32 * kEpiWarps;   // warp 0 copies, warp 1 issues MMAs
   static_assert(kBandBytes % 128 == 0 && kTapBytes % 128 == 0 && kOffBar % 8 == 0, "alignment");
   static_assert(kTmemCols == 32 || kTmemCols == 64 || kTmemCols == 128 || kTmemCols == 256, "TMEM");
-  static_assert(kBytes <= 227 * 1024, "shared memory");
+  static_assert(kStages >= 2 && kBytes <= 227 * 1024, "shared memory");
 };
 
 struct ConvArgs {
@@ -153,6 +160,16 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
+// first position of band dy of tile t, and the 128-byte row (8 positions)
+// holding it (floor division: the first bands start before position 0)
+__device__ __forceinline__ int band_start(const Geo &g, int t, int dy) {
+  return t * kTM + (dy - 1) * g.Wp - 1;
+}
+__device__ __forceinline__ int band_group(const Geo &g, int t, int dy) {
+  const int s = band_start(g, t, dy);
+  return s >= 0 ? s >> 3 : -((7 - s) >> 3);
+}
+
 // the three bands of tile t into stage st (one thread)
 template <int CIN, int COUT>
 __device__ __forceinline__ void load_bands(const CUtensorMap *tm, const Geo &g, int t, int st,
@@ -161,15 +178,13 @@ __device__ __forceinline__ void load_bands(const CUtensorMap *tm, const Geo &g, 
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
                "r"(Lt::kTxBytes)
                : "memory");
-  const int q0 = t * kTM;
 #pragma unroll
   for (int dy = 0; dy < 3; ++dy) {
-    const int row = q0 + (dy - 1) * g.Wp - 1;
     const uint32_t dst = base + st * Lt::kStageBytes + dy * Lt::kBandBytes;
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
         "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-        "l"(tm), "r"(0), "r"(row), "r"(0), "r"(bar)
+        "l"(tm), "r"(0), "r"(band_group(g, t, dy)), "r"(0), "r"(bar)
         : "memory");
   }
 }
@@ -178,8 +193,12 @@ __device__ __forceinline__ void load_bands(const CUtensorMap *tm, const Geo &g, 
 // thread); the descriptors differ only in their start addresses, which stay
 // below 256 KB, so each is the first one plus a constant
 template <int CIN, int COUT>
-__device__ __forceinline__ void issue_mmas(uint32_t base, int st, int j, uint32_t tmem) {
+__device__ __forceinline__ void issue_mmas(const Geo &g, int t, uint32_t base, int st, int j,
+                                           uint32_t tmem) {
   using Lt = TcLayout<CIN, COUT>;
+  int off[3];  // positions from the start of each plane copy to the band's first
+#pragma unroll
+  for (int dy = 0; dy < 3; ++dy) off[dy] = band_start(g, t, dy) - 8 * band_group(g, t, dy);
   constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(COUT >> 3) << 17) |
                              ((uint32_t)(kTM >> 4) << 24);  // f32 += bf16 x bf16, K-major A and B
   const uint32_t d = tmem + (uint32_t)(j * COUT);
@@ -189,8 +208,8 @@ __device__ __forceinline__ void issue_mmas(uint32_t base, int st, int j, uint32_
   for (int tap = 0; tap < 9; ++tap) {
 #pragma unroll
     for (int kk = 0; kk < Lt::kPlanes / 2; ++kk) {
-      const uint64_t ad =
-          a0 + (uint64_t)(((tap / 3) * Lt::kBandBytes + (tap % 3) * 16 + 2 * kk * Lt::kLboA) >> 4);
+      const uint64_t ad = a0 + (uint64_t)(((tap / 3) * Lt::kBandBytes +
+                                           (off[tap / 3] + tap % 3) * 16 + 2 * kk * Lt::kLboA) >> 4);
       const uint64_t bd = b0 + (uint64_t)((tap * Lt::kTapBytes + 2 * kk * Lt::kLboB) >> 4);
       const uint32_t acc = (tap | kk) != 0;
       asm volatile(
@@ -253,6 +272,15 @@ __device__ __forceinline__ void epilogue(const ConvArgs &a, const float *sbias, 
     return;
   }
   if (!live) return;
+  // mode 2: every plane's mask loaded before any store (the stores could alias
+  // it as far as the compiler knows, which would serialise load and store)
+  uint4 mk[N / 8];
+  if (MODE == 2) {
+#pragma unroll
+    for (int k = 0; k < N / 8; ++k)
+      mk[k] = __ldg(reinterpret_cast<const uint4 *>(a.mask + (long long)((cbeg >> 3) + k) * a.g.ps +
+                                                    (long long)q * 8));
+  }
 #pragma unroll
   for (int k = 0; k < N / 8; ++k) {
     const long long off = (long long)((cbeg >> 3) + k) * a.g.ps + (long long)q * 8;
@@ -261,8 +289,7 @@ __device__ __forceinline__ void epilogue(const ConvArgs &a, const float *sbias, 
 #pragma unroll
       for (int i = 0; i < 8; ++i) w[i] = in ? fmaxf(w[i] + sbias[cbeg + 8 * k + i], 0.f) : 0.f;
     } else {
-      uint4 m = *reinterpret_cast<const uint4 *>(a.mask + off);
-      const bf16 *mb = reinterpret_cast<const bf16 *>(&m);
+      const bf16 *mb = reinterpret_cast<const bf16 *>(&mk[k]);
 #pragma unroll
       for (int i = 0; i < 8; ++i) w[i] = (in && __bfloat162float(mb[i]) > 0.f) ? w[i] : 0.f;
     }
@@ -292,15 +319,16 @@ __global__ void __launch_bounds__(TcLayout<CIN, COUT>::kThreads)
     return;
   }
   const uint32_t bar = base + Lt::kOffBar;
+  constexpr int S = Lt::kStages;
   auto full = [&](int st) { return bar + 8u * st; };
-  auto empty = [&](int st) { return bar + 24u + 8u * st; };
-  auto accf = [&](int j) { return bar + 48u + 8u * j; };
-  auto acce = [&](int j) { return bar + 64u + 8u * j; };
-  volatile int *abort = reinterpret_cast<volatile int *>(sm + Lt::kOffBar + 80);
-  uint32_t *slot = reinterpret_cast<uint32_t *>(sm + Lt::kOffBar + 84);
+  auto empty = [&](int st) { return bar + 32u + 8u * st; };
+  auto accf = [&](int j) { return bar + 64u + 8u * j; };
+  auto acce = [&](int j) { return bar + 80u + 8u * j; };
+  volatile int *abort = reinterpret_cast<volatile int *>(sm + Lt::kOffBar + 96);
+  uint32_t *slot = reinterpret_cast<uint32_t *>(sm + Lt::kOffBar + 100);
   float *sbias = reinterpret_cast<float *>(sm + Lt::kOffBias);
   if (tid == 0) {
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < S; ++k) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full(k)));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(empty(k)));
     }
@@ -333,19 +361,19 @@ __global__ void __launch_bounds__(TcLayout<CIN, COUT>::kThreads)
   const int G = gridDim.x;
   if (warp == 0) {
     if (lane == 0) {
-      int last[3] = {-1, -1, -1};  // latest tile copied into each stage
+      int last[4] = {-1, -1, -1, -1};  // latest tile copied into each stage
       int k = 0;
       for (int t = blockIdx.x; t < a.ntiles; t += G, ++k) {
-        const int st = k % 3, u = k / 3;
+        const int st = k % S, u = k / S;
         if (u > 0 && !bar_wait(empty(st), (u - 1) & 1, abort)) break;
         load_bands<CIN, COUT>(&tm, a.g, t, st, base, full(st));
         last[st] = k;
       }
       if (*abort)  // let the copies in flight land (bounded)
-        for (int st = 0; st < 3; ++st)
+        for (int st = 0; st < S; ++st)
           if (last[st] >= 0) {
             volatile int never = 0;
-            bar_wait(full(st), (last[st] / 3) & 1, &never);
+            bar_wait(full(st), (last[st] / S) & 1, &never);
           }
     }
   } else if (warp == 1) {
@@ -353,11 +381,11 @@ __global__ void __launch_bounds__(TcLayout<CIN, COUT>::kThreads)
       int lastk = -1;
       int k = 0;
       for (int t = blockIdx.x; t < a.ntiles; t += G, ++k) {
-        const int st = k % 3, j = k & 1, v = k >> 1;
-        if (!bar_wait(full(st), (k / 3) & 1, abort)) break;
+        const int st = k % S, j = k & 1, v = k >> 1;
+        if (!bar_wait(full(st), (k / S) & 1, abort)) break;
         if (v > 0 && !bar_wait(acce(j), (v - 1) & 1, abort)) break;
         tc_fence_after();
-        issue_mmas<CIN, COUT>(base, st, j, tmem);
+        issue_mmas<CIN, COUT>(a.g, t, base, st, j, tmem);
         tc_commit(empty(st));
         tc_commit(accf(j));
         lastk = k;
@@ -634,6 +662,12 @@ struct Carve {
   }
 };
 
+// positions of an activation plane: the haloed grid of the largest batch,
+// rounded up to whole 128-byte rows of the tensor maps
+long long cap_rows(const pic_cnn_config *c) {
+  return ((long long)(c->nr + 3) * (c->nz + 3) * c->batch + 7) / 8 * 8;
+}
+
 bool cfg_ok(const pic_cnn_config *c) {
   return c && c->nr >= 1 && c->nz >= 1 && c->width == 64 && c->depth >= 2 && c->depth <= kMaxL &&
          c->batch >= 1 && c->batch <= 64;
@@ -662,7 +696,7 @@ bool layout(pic_cnn *x, const pic_cnn_config *c, char *base, size_t *used) {
   meta(c, x->M, x->nparam, x->ngpad);
   const long long P = (long long)(c->nr + 1) * (c->nz + 1);
   const long long NP = P * c->batch;
-  const long long NPP = (long long)(c->nr + 3) * (c->nz + 3) * c->batch;
+  const long long NPP = cap_rows(c);
   x->master = (float *)K.take(x->nparam * 4);
   x->m = (float *)K.take(x->nparam * 4);
   x->v = (float *)K.take(x->nparam * 4);
@@ -694,12 +728,13 @@ Geo geo(const pic_cnn *x, int batch) {
   g.Pp = g.Hp * g.Wp;
   g.npos = g.P * batch;
   g.npp = g.Pp * batch;
-  g.ps = 8LL * g.Pp * x->cfg.batch;
+  g.ps = 8LL * cap_rows(&x->cfg);
   return g;
 }
 
-// 3-D tensor map of a plane buffer (8 channels x rows x cin/8 planes): one box
-// = one band of kBand positions of every plane, no swizzle, zero outside
+// 3-D tensor map of a plane buffer (64 elements = 8 positions x 8 channels per
+// 128-byte row, rows / 8 rows, cin / 8 planes): one box = kGroups rows of
+// every plane, no swizzle, zero outside
 cudaError_t encode_rows(CUtensorMap *m, void *ptr, int cin, long long rows) {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
     void *f = nullptr;
@@ -711,9 +746,9 @@ cudaError_t encode_rows(CUtensorMap *m, void *ptr, int cin, long long rows) {
     return (PFN_cuTensorMapEncodeTiled_v12000)f;
   }();
   if (!fn) return cudaErrorNotSupported;
-  cuuint64_t dim[3] = {8, (cuuint64_t)rows, (cuuint64_t)(cin / 8)};
-  cuuint64_t str[2] = {16, (cuuint64_t)rows * 16};
-  cuuint32_t box[3] = {8, (cuuint32_t)kBand, (cuuint32_t)(cin / 8)}, es[3] = {1, 1, 1};
+  cuuint64_t dim[3] = {64, (cuuint64_t)(rows / 8), (cuuint64_t)(cin / 8)};
+  cuuint64_t str[2] = {128, (cuuint64_t)rows * 16};
+  cuuint32_t box[3] = {64, (cuuint32_t)kGroups, (cuuint32_t)(cin / 8)}, es[3] = {1, 1, 1};
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, ptr, dim, str, box, es,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -721,7 +756,7 @@ cudaError_t encode_rows(CUtensorMap *m, void *ptr, int cin, long long rows) {
 }
 
 cudaError_t encode_maps(pic_cnn *x) {
-  const long long rows = (long long)(x->cfg.nr + 3) * (x->cfg.nz + 3) * x->cfg.batch;
+  const long long rows = cap_rows(&x->cfg);
   cudaError_t e = cudaSuccess;
   for (int l = 0; l < x->M.L && e == cudaSuccess; ++l)
     e = encode_rows(&x->tm_act[l], x->act[l], x->M.cinp[l], rows);

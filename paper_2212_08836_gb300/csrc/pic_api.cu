@@ -598,6 +598,60 @@ int push_all(pic_ctx *x, const double *erh, const double *ezh, double *ir, doubl
   return PIC_OK;
 }
 
+// One species' push parameters of a pass, as push_all sets them, for a
+// launch over several discharges (an ensemble round).  spec: the speculative
+// (writing, out of place) pass.
+void round_launch(pic_ctx *x, int s, bool spec, PushLaunchT<float> &L) {
+  const double q = s == 0 ? -kQE : kQE, m = s == 0 ? kME : kMAr;
+  double *ws[3] = {nullptr, nullptr, nullptr};
+  if (spec) {
+    const int nr = x->g.nr, nz = x->g.nz;
+    double *w0 = x->wall_spec + (size_t)s * (2 * (nr + 1) + nz + 1);
+    ws[0] = w0;
+    ws[1] = w0 + (nr + 1);
+    ws[2] = w0 + 2 * (nr + 1);
+  }
+  fill_push(x, s, q, m, x->erh, x->ezh, x->ir, x->iz, spec ? 1 : 0,
+            spec ? x->cnt->push : nullptr, spec ? &x->cnt->ke_lost : nullptr, ws, L);
+  L.p = as32(cur(x, s));
+  L.dst = spec ? as32(x->P[s][x->cur[s] ^ 1]) : L.p;
+  L.oop = spec ? 1 : 0;
+  if (L.hist && spec) L.hist = x->hist_spec;
+  L.ar = x->alpha.ar[s];
+  L.az = x->alpha.az[s];
+  set_queue(x, x->q_real, L);
+  L.q_cell = x->q_cell;
+  L.q_a = x->q_st[0];
+  L.q_b = x->q_st[1];
+  L.q_vr = x->q_st[2];
+  L.q_vt = x->q_st[3];
+  L.q_vz = x->q_st[4];
+  L.q_w = x->q_st[5];
+  L.plist = x->plist[s];
+  L.pcnt = x->pcnt + s;
+}
+
+void round_launch(pic_ctx *x, int s, bool spec, PushLaunchT<double> &L) {
+  const double q = s == 0 ? -kQE : kQE, m = s == 0 ? kME : kMAr;
+  double *ws[3] = {nullptr, nullptr, nullptr};
+  if (spec) {
+    const int nr = x->g.nr, nz = x->g.nz;
+    double *w0 = x->wall_spec + (size_t)s * (2 * (nr + 1) + nz + 1);
+    ws[0] = w0;
+    ws[1] = w0 + (nr + 1);
+    ws[2] = w0 + 2 * (nr + 1);
+  }
+  fill_push(x, s, q, m, x->erh, x->ezh, x->ir, x->iz, spec ? 1 : 0,
+            spec ? x->cnt->push : nullptr, spec ? &x->cnt->ke_lost : nullptr, ws, L);
+  L.p = cur(x, s);
+  L.dst = spec ? x->P[s][x->cur[s] ^ 1] : L.p;
+  L.oop = spec ? 1 : 0;
+  if (L.hist && spec) L.hist = x->hist_spec;
+  L.ar = x->alpha64.ar[s];
+  L.az = x->alpha64.az[s];
+  set_queue(x, x->q_real64, L);
+}
+
 // Per-step diagnostics of one node t (pic_diag_average): adds the node counts
 // of the step (cnt: electrons, then ions; sums of w S1 x S1) to the averages,
 // and forms the node's charge balance over the step: the change of the
@@ -1470,7 +1524,9 @@ int guess_start(pic_ctx *x, double v1, int *used) {
 // the commit push is skipped (*spec = 1); if not, the iteration goes on.
 // one Picard pass: E^{n+1/2,k}, push + deposit (speculative: writing the new
 // state out of place), field solve, norms copied to pinned host memory
-int enqueue_pass(pic_ctx *x, bool spec) {
+// the pass up to the push: E^{n+1/2,k} and alpha, cleared crossed charge
+// (and, speculative, the counters and tallies the writing pass fills)
+int enqueue_pre(pic_ctx *x, bool spec) {
   const int nr = x->g.nr, nz = x->g.nz;
   const size_t ner = (size_t)nr * (nz + 1), nez = (size_t)(nr + 1) * nz;
   const size_t nwall = (size_t)2 * (2 * (nr + 1) + nz + 1);
@@ -1484,19 +1540,19 @@ int enqueue_pass(pic_ctx *x, bool spec) {
   x->launches += 1;
   if (cudaMemsetAsync(x->ir, 0, ner * 8, s) != cudaSuccess) return PIC_E_CUDA;
   if (cudaMemsetAsync(x->iz, 0, nez * 8, s) != cudaSuccess) return PIC_E_CUDA;
-  int r;
   if (spec) {
     if (cudaMemsetAsync(x->cnt->push, 0, sizeof(x->cnt->push), s) != cudaSuccess ||
         cudaMemsetAsync(&x->cnt->ke_lost, 0, 8, s) != cudaSuccess ||
         cudaMemsetAsync(x->wall_spec, 0, nwall * 8, s) != cudaSuccess ||
         (x->hist_on && cudaMemsetAsync(x->hist_spec, 0, 16 * 8, s) != cudaSuccess))
       return PIC_E_CUDA;
-    r = push_all(x, x->erh, x->ezh, x->ir, x->iz, 1, x->cnt->push, &x->cnt->ke_lost,
-                 x->wall_spec, 1);
-  } else {
-    r = push_all(x, x->erh, x->ezh, x->ir, x->iz, 0, nullptr, nullptr, nullptr);
   }
-  if (r) return r;
+  return PIC_OK;
+}
+
+// the pass after the push: implicit field solve, norms to pinned host memory
+int enqueue_post(pic_ctx *x) {
+  cudaStream_t s = x->s;
   if (x->cfg.field_model == PIC_FIELD_ES) {
     // Q^{n+1} = Q^n - div I, E^{n+1} = -grad phi^{n+1}; H stays zero
     EsOp E = x->es;
@@ -1514,6 +1570,18 @@ int enqueue_pass(pic_ctx *x, bool spec) {
   if (cudaMemcpyAsync(x->hn, x->cnt->norm, 3 * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return PIC_E_CUDA;
   return PIC_OK;
+}
+
+int enqueue_pass(pic_ctx *x, bool spec) {
+  int r = enqueue_pre(x, spec);
+  if (r) return r;
+  if (spec)
+    r = push_all(x, x->erh, x->ezh, x->ir, x->iz, 1, x->cnt->push, &x->cnt->ke_lost, x->wall_spec,
+                 1);
+  else
+    r = push_all(x, x->erh, x->ezh, x->ir, x->iz, 0, nullptr, nullptr, nullptr);
+  if (r) return r;
+  return enqueue_post(x);
 }
 
 // the pass for the current buffers, replayed from a graph captured the first
@@ -2357,6 +2425,14 @@ int pic_guess_sample(pic_ctx *x, float *x_dev, float *t_dev, int *valid) {
 struct pic_ensemble {
   int n;
   pic_ctx *m[PIC_ENSEMBLE_MAX];
+  // persistent rounds: each species' push of every active member in one
+  // launch of the fast and one of the general kernel, on the lead stream
+  int persistent;
+  cudaStream_t lead;
+  cudaEvent_t ev_pre[PIC_ENSEMBLE_MAX], ev_sp[2];
+  char *stage;  // pinned: per species, the members' launch parameters, then the item offsets
+  char *dbuf;   // device copy
+  int ready;
 };
 
 namespace {
@@ -2375,6 +2451,86 @@ void drop_graphs(pic_ctx *x) {
 }
 
 }  // namespace
+
+// staging of one species' launch parameters (persistent rounds)
+constexpr size_t kMaxLaunchBytes = sizeof(PushLaunchT<double>) > sizeof(PushLaunchT<float>)
+                                       ? sizeof(PushLaunchT<double>)
+                                       : sizeof(PushLaunchT<float>);
+constexpr size_t kSlotLaunch = (PIC_ENSEMBLE_MAX * kMaxLaunchBytes + 255) / 256 * 256;
+constexpr size_t kSlot = (kSlotLaunch + 2 * (PIC_ENSEMBLE_MAX + 1) * sizeof(int) + 255) / 256 * 256;
+
+// one Picard pass of the members A[0..nl) (all of precision T): each member's
+// pre-push part on its stream; on the lead stream, per species, the members'
+// launch parameters uploaded and their fast and general phases in one launch
+// each (the mixed form's near-axis lists then on each member's stream); then
+// each member's field solve on its stream
+template <typename T>
+int round_persistent(pic_ensemble *E, const int *A, int nl, std::vector<StepState> &St) {
+  for (int a = 0; a < nl; ++a) {
+    pic_ctx *x = E->m[A[a]];
+    int r = enqueue_pre(x, St[A[a]].spec);
+    if (r) return r;
+    if (cudaEventRecord(E->ev_pre[a], x->s) != cudaSuccess ||
+        cudaStreamWaitEvent(E->lead, E->ev_pre[a], 0) != cudaSuccess)
+      return PIC_E_CUDA;
+  }
+  for (int s = 0; s < 2; ++s) {
+    char *h = E->stage + s * kSlot;
+    char *d = E->dbuf + s * kSlot;
+    PushLaunchT<T> *Ls = reinterpret_cast<PushLaunchT<T> *>(h);
+    int *first = reinterpret_cast<int *>(h + kSlotLaunch);
+    first[0] = 0;
+    first[nl + 1] = 0;
+    for (int a = 0; a < nl; ++a) {
+      round_launch(E->m[A[a]], s, St[A[a]].spec, Ls[a]);
+      int nf = 0, ng = 0;
+      push_shape(Ls[a], &nf, &ng);
+      first[a + 1] = first[a] + nf;
+      first[nl + 2 + a] = first[nl + 1 + a] + ng;
+    }
+    if (cudaMemcpyAsync(d, h, nl * sizeof(PushLaunchT<T>), cudaMemcpyHostToDevice, E->lead) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(d + kSlotLaunch, h + kSlotLaunch, (size_t)(2 * nl + 2) * sizeof(int),
+                        cudaMemcpyHostToDevice, E->lead) != cudaSuccess)
+      return PIC_E_CUDA;
+    if (launch_push_multi<T>(reinterpret_cast<const PushLaunchT<T> *>(d),
+                             reinterpret_cast<const int *>(d + kSlotLaunch), nl,
+                             E->lead) != cudaSuccess)
+      return PIC_E_CUDA;
+    E->m[A[0]]->launches += 2;
+    if (cudaEventRecord(E->ev_sp[s], E->lead) != cudaSuccess) return PIC_E_CUDA;
+    if constexpr (sizeof(T) == 4) {
+      // the near-axis lists of this species on each member's stream, beside
+      // the next launches on the lead stream
+      for (int a = 0; a < nl; ++a) {
+        pic_ctx *x = E->m[A[a]];
+        if (cudaStreamWaitEvent(x->s, E->ev_sp[s], 0) != cudaSuccess ||
+            launch_push_fp32_axis(Ls[a], x->s) != cudaSuccess)
+          return PIC_E_CUDA;
+        x->launches += 1;
+      }
+    }
+  }
+  for (int a = 0; a < nl; ++a) {
+    pic_ctx *x = E->m[A[a]];
+    if (sizeof(T) == 8 && cudaStreamWaitEvent(x->s, E->ev_sp[1], 0) != cudaSuccess)
+      return PIC_E_CUDA;
+    int r = enqueue_post(x);
+    if (r) return r;
+  }
+  return PIC_OK;
+}
+
+// members that a persistent round can take together: one precision, both
+// species moving, the fast path (no magnetic field) and the queue
+bool persistent_ok(const pic_ensemble *E) {
+  for (int i = 0; i < E->n; ++i) {
+    const pic_ctx *x = E->m[i];
+    if (x->mixed != E->m[0]->mixed || x->cfg.ions_fixed || x->cfg.bz != 0.0 || !x->queue)
+      return false;
+  }
+  return true;
+}
 
 int pic_set_graphs(pic_ctx *x, int on) {
   if (!x) return PIC_E_CONFIG;
@@ -2398,11 +2554,48 @@ int pic_ensemble_create(pic_ctx *const *members, int n, pic_ensemble **out) {
     E->m[i] = members[i];
     members[i]->graphs = 1;
   }
+  // the lead stream, its events and the launch-parameter staging of
+  // persistent rounds
+  bool ok = cudaStreamCreateWithFlags(&E->lead, cudaStreamNonBlocking) == cudaSuccess;
+  int nev = 0;
+  for (; ok && nev < n; ++nev)
+    ok = cudaEventCreateWithFlags(&E->ev_pre[nev], cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&E->ev_sp[0], cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaEventCreateWithFlags(&E->ev_sp[1], cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaHostAlloc((void **)&E->stage, 2 * kSlot, cudaHostAllocDefault) == cudaSuccess;
+  ok = ok && cudaMalloc((void **)&E->dbuf, 2 * kSlot) == cudaSuccess;
+  if (!ok) {
+    E->ready = 0;
+    pic_ensemble_destroy(E);
+    return PIC_E_CUDA;
+  }
+  E->ready = 1;
+  E->persistent = persistent_ok(E) ? 1 : 0;
   *out = E;
   return PIC_OK;
 }
 
-void pic_ensemble_destroy(pic_ensemble *E) { free(E); }
+void pic_ensemble_destroy(pic_ensemble *E) {
+  if (!E) return;
+  if (E->lead) {
+    cudaStreamSynchronize(E->lead);
+    cudaStreamDestroy(E->lead);
+  }
+  for (int i = 0; i < E->n; ++i)
+    if (E->ev_pre[i]) cudaEventDestroy(E->ev_pre[i]);
+  for (int k = 0; k < 2; ++k)
+    if (E->ev_sp[k]) cudaEventDestroy(E->ev_sp[k]);
+  if (E->stage) cudaFreeHost(E->stage);
+  if (E->dbuf) cudaFree(E->dbuf);
+  free(E);
+}
+
+int pic_ensemble_set_persistent(pic_ensemble *E, int on) {
+  if (!E) return PIC_E_CONFIG;
+  if (on && !persistent_ok(E)) return PIC_E_CONFIG;
+  E->persistent = on ? 1 : 0;
+  return PIC_OK;
+}
 
 int pic_ensemble_step(pic_ensemble *E, int nsteps, pic_step_stats *st) {
   if (!E || nsteps < 0) return PIC_E_CONFIG;
@@ -2419,12 +2612,22 @@ int pic_ensemble_step(pic_ensemble *E, int nsteps, pic_step_stats *st) {
     // rounds: one Picard pass of every unconverged member, then one wait
     int nact = n;
     while (nact) {
-      for (int i = 0; i < n; ++i) {
-        if (!active[i]) continue;
-        pic_ctx *x = E->m[i];
-        int r = launch_pass(x, T[i].spec);
+      if (E->persistent) {
+        int A[PIC_ENSEMBLE_MAX], nl = 0;
+        for (int i = 0; i < n; ++i)
+          if (active[i]) A[nl++] = i;
+        int r = E->m[0]->mixed ? round_persistent<float>(E, A, nl, T)
+                               : round_persistent<double>(E, A, nl, T);
         if (r) return r;
-        T[i].S.pushes += x->n[0] + x->n[1];
+        for (int a = 0; a < nl; ++a) T[A[a]].S.pushes += E->m[A[a]]->n[0] + E->m[A[a]]->n[1];
+      } else {
+        for (int i = 0; i < n; ++i) {
+          if (!active[i]) continue;
+          pic_ctx *x = E->m[i];
+          int r = launch_pass(x, T[i].spec);
+          if (r) return r;
+          T[i].S.pushes += x->n[0] + x->n[1];
+        }
       }
       for (int i = 0; i < n; ++i) {
         if (!active[i]) continue;
@@ -2462,31 +2665,46 @@ int pic_ensemble_step(pic_ensemble *E, int nsteps, pic_step_stats *st) {
   return rc;
 }
 
-int pic_ensemble_tune(pic_ensemble *E, int rounds, float *frac_out, double *ms_out) {
+int pic_ensemble_tune(pic_ensemble *E, int rounds, float *frac_out, int *persistent_out,
+                      double *ms_out) {
   if (!E || rounds < 1) return PIC_E_CONFIG;
   const float fr[3] = {1.0f, 0.5f, 0.25f};
+  const bool pok = persistent_ok(E);
   double best = 1e300;
   int bi = 0;
-  for (int c = 0; c < 3; ++c) {
+  std::vector<StepState> T(E->n);
+  int A[PIC_ENSEMBLE_MAX];
+  for (int i = 0; i < E->n; ++i) A[i] = i;
+  for (int c = 0; c < 6; ++c) {
+    const int f = c % 3, pers = c / 3;
+    if (ms_out) ms_out[c] = -1.0;
+    if (pers && !pok) continue;
     for (int i = 0; i < E->n; ++i) {
       pic_ctx *x = E->m[i];
       drop_graphs(x);
       int wf = x->mixed ? push_wave_fp32(0) : push_wave_fp64(0);
       int wg = x->mixed ? push_wave_fp32(1) : push_wave_fp64(1);
-      x->fgrid[0] = fr[c] < 1.0f ? (int)(wf * fr[c]) > 0 ? (int)(wf * fr[c]) : 1 : 0;
-      x->ggrid[0] = fr[c] < 1.0f ? (int)(wg * fr[c]) > 0 ? (int)(wg * fr[c]) : 1 : 0;
+      x->fgrid[0] = fr[f] < 1.0f ? (int)(wf * fr[f]) > 0 ? (int)(wf * fr[f]) : 1 : 0;
+      x->ggrid[0] = fr[f] < 1.0f ? (int)(wg * fr[f]) > 0 ? (int)(wg * fr[f]) : 1 : 0;
       if (upload_step(x, volt_at(x, x->step), volt_at(x, x->step + 1))) return PIC_E_CUDA;
       int r = plain_start(x, volt_at(x, x->step + 1));
       if (r) return r;
+      memset(&T[i], 0, sizeof(StepState));
     }
     double tbest = 1e300;
     for (int rep = 0; rep < rounds + 1; ++rep) {
       for (int i = 0; i < E->n; ++i)
         if (cudaStreamSynchronize(E->m[i]->s) != cudaSuccess) return PIC_E_CUDA;
       auto t0 = std::chrono::steady_clock::now();
-      for (int i = 0; i < E->n; ++i) {
-        int r = enqueue_pass(E->m[i], false);
+      if (pers) {
+        int r = E->m[0]->mixed ? round_persistent<float>(E, A, E->n, T)
+                               : round_persistent<double>(E, A, E->n, T);
         if (r) return r;
+      } else {
+        for (int i = 0; i < E->n; ++i) {
+          int r = enqueue_pass(E->m[i], false);
+          if (r) return r;
+        }
       }
       for (int i = 0; i < E->n; ++i)
         if (cudaStreamSynchronize(E->m[i]->s) != cudaSuccess) return PIC_E_CUDA;
@@ -2500,13 +2718,17 @@ int pic_ensemble_tune(pic_ensemble *E, int rounds, float *frac_out, double *ms_o
       bi = c;
     }
   }
+  const int f = bi % 3;
   for (int i = 0; i < E->n; ++i) {
     pic_ctx *x = E->m[i];
+    drop_graphs(x);
     int wf = x->mixed ? push_wave_fp32(0) : push_wave_fp64(0);
     int wg = x->mixed ? push_wave_fp32(1) : push_wave_fp64(1);
-    x->fgrid[0] = bi ? (int)(wf * fr[bi]) : 0;
-    x->ggrid[0] = bi ? (int)(wg * fr[bi]) : 0;
+    x->fgrid[0] = f ? (int)(wf * fr[f]) : 0;
+    x->ggrid[0] = f ? (int)(wg * fr[f]) : 0;
   }
-  if (frac_out) *frac_out = fr[bi];
+  E->persistent = bi / 3;
+  if (frac_out) *frac_out = fr[f];
+  if (persistent_out) *persistent_out = E->persistent;
   return PIC_OK;
 }

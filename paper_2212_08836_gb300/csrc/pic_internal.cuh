@@ -331,6 +331,13 @@ cudaError_t launch_guess_target(const GuessArgs &A, const double *er_next, const
 constexpr int kMaxFastBlocks = 152 * 8;
 template <typename T>
 cudaError_t launch_push(const PushLaunchT<T> &L, cudaStream_t s);
+// the virtual grids launch_push would use for L (sets L.qgrid, L.qseg)
+template <typename T>
+void push_shape(PushLaunchT<T> &L, int *nfast, int *ngen);
+// fast and general phases of nl discharges, one launch each (Ls, first in
+// device memory: first[0..nl] fast item offsets, first[nl+1..2nl+1] general)
+template <typename T>
+cudaError_t launch_push_multi(const PushLaunchT<T> *Ls, const int *first, int nl, cudaStream_t s);
 // FP32 store: the near-axis crossers launch_push listed, pushed in FP64
 // arithmetic (a second launch after it; nothing with an external B_z)
 cudaError_t launch_push_fp32_axis(const PushLaunchT<float> &L, cudaStream_t s);

@@ -42,6 +42,9 @@ __global__ void __launch_bounds__(32) k_push_promoted32(PushLaunchT<float> L) {
 }  // namespace
 
 template cudaError_t launch_push<float>(const PushLaunchT<float> &L, cudaStream_t s);
+template void push_shape<float>(PushLaunchT<float> &L, int *nfast, int *ngen);
+template cudaError_t launch_push_multi<float>(const PushLaunchT<float> *Ls, const int *first, int nl,
+                                               cudaStream_t s);
 
 cudaError_t launch_push_fp32_axis(const PushLaunchT<float> &L, cudaStream_t s) {
   const long long nsz = L.n_dev ? L.cap : L.n;

@@ -7,6 +7,9 @@
 
 namespace pic {
 template cudaError_t launch_push<double>(const PushLaunchT<double> &L, cudaStream_t s);
+template void push_shape<double>(PushLaunchT<double> &L, int *nfast, int *ngen);
+template cudaError_t launch_push_multi<double>(const PushLaunchT<double> *Ls, const int *first, int nl,
+                                               cudaStream_t s);
 int push_wave_fp64(int general) {
   return (int)(general ? general_grid<double>() : fast_grid<double>());
 }

@@ -166,12 +166,14 @@ __device__ __forceinline__ bool near_axis32(const PushLaunchT<T> &L, int c, T a,
   return close;
 }
 
+// the fast phase of block `bid` of a grid of `nblk` blocks (a launch of its
+// own, or one work item of a launch over several discharges)
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_push_fast(PushLaunchT<T> L) {
+__device__ __forceinline__ void push_fast_body(const PushLaunchT<T> &L, int bid, int nblk) {
   const int lane = threadIdx.x & 31;
   const int nz = L.g.nz, nz1 = nz + 1, ncell = L.g.nr * nz;
   const T zero = (T)0, one = (T)1, h = (T)0.5, q = (T)0.25;
-  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long stride = (long long)nblk * blockDim.x;
   unsigned n_newton = 0, n_acc = 0;
   // entries this block appended to its queue segment: [0] z-face-only
   // crossings of the trial from the front, [1] the rest from the back
@@ -179,11 +181,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_push_fast(PushL
   if (threadIdx.x < 2) s_qn[threadIdx.x] = 0;
   // the near-axis list of this pass starts empty (the general kernel, which
   // fills it, runs after this kernel on the same stream)
-  if (L.pcnt && blockIdx.x == 0 && threadIdx.x == 0) *L.pcnt = 0u;
+  if (L.pcnt && bid == 0 && threadIdx.x == 0) *L.pcnt = 0u;
   __syncthreads();
-  const long long qoff = (long long)blockIdx.x * L.qseg;
+  const long long qoff = (long long)bid * L.qseg;
   const long long n = L.n_dev ? *L.n_dev : L.n;
-  long long base = (long long)blockIdx.x * blockDim.x;
+  long long base = (long long)bid * blockDim.x;
   // FP32 form: the next tile's state is loaded while this one is pushed (the
   // kernel is issue-bound; the FP64 form is bound by its FP64 pipe instead)
   constexpr bool kPrefetch = sizeof(T) == 4;
@@ -301,16 +303,22 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_push_fast(PushL
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    L.qblock[blockIdx.x] = s_qn[0];
-    L.qblock[L.qgrid + blockIdx.x] = s_qn[1];
+    L.qblock[bid] = s_qn[0];
+    L.qblock[L.qgrid + bid] = s_qn[1];
   }
   Tally T0 = {0, 0, 0, 0, 0, 0};
   flush_tally(L.counters, T0, lane, n_newton, n_acc);
 }
 
-// queued particles (or all of them when queue == nullptr); blockDim 256
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3) k_push_fast(PushLaunchT<T> L) {
+  push_fast_body<T>(L, blockIdx.x, gridDim.x);
+}
+
+// queued particles (or all of them when queue == nullptr) of block `bid` of
+// `nblk`; blockDim 256
 template <typename T, bool kB>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_push_general(PushLaunchT<T> L) {
+__device__ __forceinline__ void push_general_body(const PushLaunchT<T> &L, int bid, int nblk) {
   const int lane = threadIdx.x & 31;
   GenArgs<T> G;
   G.nr = L.g.nr; G.nz = L.g.nz; G.ar = L.ar; G.az = L.az;
@@ -319,8 +327,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_push_general(Pu
   G.oop = L.oop; G.dst = L.dst; G.hist = L.hist;
   G.wall_z0 = L.wall_z0; G.wall_zl = L.wall_zl; G.wall_r = L.wall_r; G.ke_lost = L.ke_lost;
   Tally tl = {0, 0, 0, 0, 0, 0};
-  const long long gstride = (long long)gridDim.x * blockDim.x;
-  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long gstride = (long long)nblk * blockDim.x;
+  const long long gtid = (long long)bid * blockDim.x + threadIdx.x;
   if (L.queue) {
     // the z-face-only crossings first, then the rest (uniform warps)
     __shared__ int s_pre[kMaxFastBlocks + 1], s_preb[kMaxFastBlocks + 1];
@@ -391,6 +399,61 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_push_general(Pu
   flush_tally(L.counters, tl, lane, 0, 0);
 }
 
+template <typename T, bool kB>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) k_push_general(PushLaunchT<T> L) {
+  push_general_body<T, kB>(L, blockIdx.x, gridDim.x);
+}
+
+// One launch over several discharges (an ensemble's Picard round): work item
+// k of first[nl] is virtual block k - first[j] of launch j, first[j] <= k <
+// first[j + 1], whose grid is first[j + 1] - first[j] blocks.  The launch's
+// parameters are copied into shared memory once per item.
+template <typename T>
+__device__ __forceinline__ const PushLaunchT<T> &multi_item(const PushLaunchT<T> *Ls,
+                                                            const int *first, int nl, int k,
+                                                            int &vb, int &vg) {
+  __shared__ __align__(16) int s_launch[sizeof(PushLaunchT<T>) / 4];
+  __shared__ int s_j;
+  static_assert(sizeof(PushLaunchT<T>) % 4 == 0, "launch parameters in 4-byte words");
+  __syncthreads();  // the previous item is done with s_launch
+  if (threadIdx.x == 0) {
+    int j = 0;
+    while (j + 1 < nl && first[j + 1] <= k) ++j;
+    s_j = j;
+  }
+  __syncthreads();
+  const int j = s_j;
+  const int *src = reinterpret_cast<const int *>(Ls + j);
+  for (int i = threadIdx.x; i < (int)(sizeof(PushLaunchT<T>) / 4); i += blockDim.x)
+    s_launch[i] = src[i];
+  vb = k - first[j];
+  vg = first[j + 1] - first[j];
+  __syncthreads();
+  return *reinterpret_cast<const PushLaunchT<T> *>(s_launch);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 5 : 3)
+    k_push_fast_multi(const PushLaunchT<T> *Ls, const int *first, int nl) {
+  const int total = first[nl];
+  for (int k = blockIdx.x; k < total; k += gridDim.x) {
+    int vb, vg;
+    const PushLaunchT<T> &L = multi_item<T>(Ls, first, nl, k, vb, vg);
+    push_fast_body<T>(L, vb, vg);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2)
+    k_push_general_multi(const PushLaunchT<T> *Ls, const int *first, int nl) {
+  const int total = first[nl];
+  for (int k = blockIdx.x; k < total; k += gridDim.x) {
+    int vb, vg;
+    const PushLaunchT<T> &L = multi_item<T>(Ls, first, nl, k, vb, vg);
+    push_general_body<T, false>(L, vb, vg);
+  }
+}
+
 // grids of the persistent kernels (one wave of resident blocks)
 template <typename T>
 long long fast_grid() {
@@ -420,6 +483,36 @@ cudaError_t launch_push_all(const PushLaunchT<T> &L, cudaStream_t s) {
     k_push_general<T, false><<<(unsigned)nb, bs, 0, s>>>(A);
   else
     k_push_general<T, true><<<(unsigned)nb, bs, 0, s>>>(A);
+  return cudaGetLastError();
+}
+
+// the virtual grids of one discharge's fast and general phases (as
+// launch_push would launch them); L.qgrid and L.qseg are set
+template <typename T>
+void push_shape(PushLaunchT<T> &L, int *nfast, int *ngen) {
+  const long long nsz = L.n_dev ? L.cap : L.n;
+  const int bs = 256;
+  long long nb = (nsz + bs - 1) / bs;
+  if (nb < 1) nb = 1;
+  long long nf = L.fgrid > 0 ? L.fgrid : fast_grid<T>();
+  if (nf > kMaxFastBlocks) nf = kMaxFastBlocks;
+  if (nf > nb) nf = nb;
+  L.qgrid = (int)nf;
+  L.qseg = (nb + nf - 1) / nf * bs;
+  long long ng = L.ggrid > 0 ? L.ggrid : general_grid<T>();
+  if (ng > nb) ng = nb;
+  *nfast = (int)nf;
+  *ngen = (int)ng;
+}
+
+// fast then general phase of nl discharges in two launches of one resident
+// wave each; Ls and first (item offsets: fast [nl + 1], then general [nl + 1])
+// in device memory
+template <typename T>
+cudaError_t launch_push_multi(const PushLaunchT<T> *Ls, const int *first, int nl,
+                              cudaStream_t s) {
+  k_push_fast_multi<T><<<(unsigned)fast_grid<T>(), 256, 0, s>>>(Ls, first, nl);
+  k_push_general_multi<T><<<(unsigned)general_grid<T>(), 256, 0, s>>>(Ls, first + nl + 1, nl);
   return cudaGetLastError();
 }
 

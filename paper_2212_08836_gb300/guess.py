@@ -23,8 +23,8 @@ import argparse
 
 import numpy as np
 
-from . import (PIC_GUESS_CNN, PIC_GUESS_EXTRAP, PIC_GUESS_PLAIN, PIC_MIXED, Cnn, Pic,
-               guess_sample, large_reactor, set_guess)
+from . import (PIC_E_CAPACITY, PIC_GUESS_CNN, PIC_GUESS_EXTRAP, PIC_GUESS_PLAIN, PIC_MIXED, Cnn,
+               Pic, PicError, guess_sample, large_reactor, set_guess)
 
 
 def collect(pic, steps):
@@ -100,13 +100,28 @@ def run_starts(pic, net, steps):
     return out
 
 
+def _step(pic, n, capped):
+    """n steps; a step that could not append all ionization pairs (the store is
+    full) is committed all the same and counted in capped[0]."""
+    for _ in range(n):
+        try:
+            st = pic.step(1)[1]
+        except PicError as e:
+            if e.code != PIC_E_CAPACITY:
+                raise
+            capped[0] += 1
+            st = None
+    return st
+
+
 def campaign(a, log=print):
     """Pairs from 9 discharges (1/2/5 Pa x 100/200/300 V), training, then
     Picard iterations and wall time per RF cycle, plain against learned start."""
     import time
     import torch
     runs = [(p, v) for p in (1.0, 2.0, 5.0) for v in (100.0, 200.0, 300.0)]
-    base = large_reactor(precision=PIC_MIXED, np_init=a.np, capacity_factor=2.5)
+    base = large_reactor(precision=PIC_MIXED, np_init=a.np, capacity_factor=a.capacity)
+    capped = [0]
     H, W = base["nr"] + 1, base["nz"] + 1
     n = a.per_run * len(runs)
     X = torch.empty((n, 14, H, W), dtype=torch.bfloat16, device="cuda")
@@ -117,18 +132,20 @@ def campaign(a, log=print):
         cfg = dict(base, gas_pressure=p, volt=v, seed=int(10 * p + v))
         pic = Pic(cfg)
         pic.load_particles()
-        pic.step(a.warmup)
+        _step(pic, a.warmup, capped)
         set_guess(pic, PIC_GUESS_EXTRAP)
         got = 0
         while got < a.per_run:
-            pic.step(1)
+            _step(pic, 1, capped)
             smp = guess_sample(pic)
             if smp is not None:
                 X[k].copy_(smp[0])
                 T[k].copy_(smp[1])
                 k += 1
                 got += 1
-        log("collected %d pairs at %.0f Pa %.0f V (%.0f s)" % (got, p, v, time.perf_counter() - t0))
+        log("collected %d pairs at %.0f Pa %.0f V (%.0f s, %d M / %d M particles)"
+            % (got, p, v, time.perf_counter() - t0, pic.diag()["n"][0] >> 20,
+               pic.diag()["n"][1] >> 20))
         pic.close()
     # one permutation, so that the held-out fifth mixes every discharge
     order = torch.randperm(n, generator=torch.Generator().manual_seed(0))
@@ -139,7 +156,7 @@ def campaign(a, log=print):
     log("train %.3e held-out %.3e (no correction %.3e), %.0f s" % (loss, val, zero, t_train))
     del X, T
     torch.cuda.empty_cache()
-    res = {"pairs": n, "params": net.num_params, "depth": a.depth, "adam_steps": a.epochs,
+    res = {"pairs": n, "params": net.num_params, "np_init": a.np, "capacity_factor": a.capacity, "depth": a.depth, "adam_steps": a.epochs,
            "train_s": t_train, "heldout_loss": val, "heldout_loss_no_correction": zero,
            "cycles": []}
     steps_cycle = int(round(1.0 / (base["freq"] * base["dt"])))
@@ -147,16 +164,18 @@ def campaign(a, log=print):
         cfg = dict(base, gas_pressure=p, volt=v, seed=int(10 * p + v) + 7)
         pic = Pic(cfg)
         pic.load_particles()
-        pic.step(a.warmup)
+        _step(pic, a.warmup, capped)
         row = {"pressure_pa": p, "volt": v}
         for name, mode in (("plain", PIC_GUESS_PLAIN), ("learned", PIC_GUESS_CNN)):
             set_guess(pic, mode, net if mode == PIC_GUESS_CNN else None)
-            pic.step(4)
+            _step(pic, 4, capped)
             torch.cuda.synchronize()
             t2 = time.perf_counter()
             it, used = [], []
             for _ in range(steps_cycle):
-                _, st = pic.step(1)
+                st = _step(pic, 1, capped)
+                if st is None:
+                    continue
                 it.append(st["picard_iters"])
                 used.append(st["guess"])
             torch.cuda.synchronize()
@@ -166,6 +185,7 @@ def campaign(a, log=print):
         log(str(row))
         res["cycles"].append(row)
         pic.close()
+    res["capacity_limited_steps"] = capped[0]
     net_params = net.get_params()
     net.close()
     return res, net_params
@@ -183,6 +203,7 @@ def main():
     ap.add_argument("--depth", type=int, default=5)
     ap.add_argument("--campaign", action="store_true")
     ap.add_argument("--per-run", type=int, default=2222)
+    ap.add_argument("--capacity", type=float, default=2.5)
     a = ap.parse_args()
     if a.campaign:
         import json

@@ -65,11 +65,24 @@ def test_graph_replay_matches_kernel_launches():
     compare(a, b, "graphs")
 
 
-def test_ensemble_matches_members_stepped_alone():
+# members of one precision, for persistent rounds (one push launch per species
+# over every member)
+CFGS64 = [dict(nr=16, nz=24, np_init=8000, seed=3, volt=150.0),
+          dict(nr=32, nz=64, np_init=40000, seed=4, freq=80e6, dt=1.0 / (200 * 80e6)),
+          dict(nr=24, nz=48, np_init=20000, seed=6, gas_pressure=5.0)]
+CFGS32 = [dict(c, precision=1, picard_tol=1e-6) for c in CFGS64]
+
+
+@pytest.mark.parametrize("cfgs,persistent", [(CFGS, False), (CFGS64, True), (CFGS64, False),
+                                             (CFGS32, True)],
+                         ids=["mixed-precisions", "fp64-persistent", "fp64-per-member",
+                              "fp32-persistent"])
+def test_ensemble_matches_members_stepped_alone(cfgs, persistent):
     M = P()
-    alone = [make(c) for c in CFGS]
-    ens_m = [make(c) for c in CFGS]
+    alone = [make(c) for c in cfgs]
+    ens_m = [make(c) for c in cfgs]
     E = M.Ensemble(ens_m)
+    E.set_persistent(persistent)
     for _ in range(3):
         rc, st = E.step(1)
         assert rc == 0
@@ -86,8 +99,10 @@ def test_tune_changes_no_state_and_keeps_results():
     ens_m = [make(c) for c in CFGS]
     ref = [make(c) for c in CFGS]
     E = M.Ensemble(ens_m)
-    frac, ms = E.tune(rounds=2)
-    assert frac in (1.0, 0.5, 0.25) and all(t > 0 for t in ms)
+    frac, pers, ms = E.tune(rounds=2)
+    # members of two precisions: no persistent candidates
+    assert frac in (1.0, 0.5, 0.25) and not pers
+    assert all(t > 0 for t in ms[:3]) and all(t == -1.0 for t in ms[3:])
     for a, b in zip(ens_m, ref):
         compare(a, b, "after tune")
     E.step(2)
@@ -95,3 +110,22 @@ def test_tune_changes_no_state_and_keeps_results():
         p.step(2)
     for i, (a, b) in enumerate(zip(ens_m, ref)):
         compare(a, b, "tuned member %d" % i)
+
+
+def test_persistent_tune_and_rejection():
+    """Members of one precision offer all six candidates; members of two
+    precisions refuse persistent rounds."""
+    M = P()
+    ens_m = [make(c) for c in CFGS64]
+    ref = [make(c) for c in CFGS64]
+    E = M.Ensemble(ens_m)
+    frac, pers, ms = E.tune(rounds=2)
+    assert frac in (1.0, 0.5, 0.25) and all(t > 0 for t in ms)
+    E.step(2)
+    for p in ref:
+        p.step(2)
+    for i, (a, b) in enumerate(zip(ens_m, ref)):
+        compare(a, b, "tuned persistent=%s member %d" % (pers, i))
+    E2 = M.Ensemble([make(c) for c in CFGS])
+    with pytest.raises(M.PicError):
+        E2.set_persistent(True)
