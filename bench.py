@@ -282,30 +282,28 @@ def measure(P, torch, dev, cfg, args, dist, D, do_e2e, sample_clocks, local):
     r["e2e_ms"] = None
     if do_e2e:
         # the whole state lives in pinned host memory between steps: every
-        # step uploads it through the C ABI (pic_state_upload), steps, and
-        # reads the new state back (pic_state_download)
+        # step uploads it through the C ABI, steps, and reads the new state
+        # back (pic_step_host: each step's download overlapped piece by piece
+        # with the next step's upload)
         hs = pic.host_state(pinned=True)
         pic.state_download(hs)
         rs = pic.view()["species"][0]["a"].element_size()
-        barrier()
-        e2e_pushes = h2d = d2h = 0
-        ev2 = torch.cuda.Event(enable_timing=True)
-        ev3 = torch.cuda.Event(enable_timing=True)
         nf = sum(hs[k].numel() * 8 for k in ("er", "ez", "h"))
-        ev2.record(stream)
-        for _ in range(args.steps):
-            h2d += sum(hs["n"]) * (8 + 6 * rs) + nf
-            pic.state_upload(hs)
-            _, st = pic.step(1)
-            e2e_pushes += st["pushes"]
-            pic.state_download(hs)
-            d2h += sum(hs["n"]) * (8 + 6 * rs) + nf
-        ev3.record(stream)
+        n_start = sum(hs["n"])
         barrier()
-        r["e2e_ms"] = ev2.elapsed_time(ev3)
-        r["e2e_pushes"] = e2e_pushes
-        r["h2d"] = h2d // args.steps
-        r["d2h"] = d2h // args.steps
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        _, st = pic.step_host(hs, args.steps)
+        t1 = time.perf_counter()
+        barrier()
+        n_end = sum(hs["n"])
+        # bytes per step: every step moves the whole state both ways (counts
+        # change by the step's ionization and wall losses: their mean)
+        per = 0.5 * (n_start + n_end) * (8 + 6 * rs) + nf
+        r["e2e_ms"] = (t1 - t0) * 1e3
+        r["e2e_pushes"] = st["pushes"]
+        r["h2d"] = int(per)
+        r["d2h"] = int(per)
     pic.close()
     del pic
     torch.cuda.empty_cache()

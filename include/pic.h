@@ -393,6 +393,23 @@ int pic_state_upload(pic_ctx *ctx, const pic_host_state *in);
  * smaller than the counts; nothing is copied), PIC_E_CUDA. */
 int pic_state_download(pic_ctx *ctx, pic_host_state *out);
 
+/* Advances a state kept in caller-owned host memory (pinned, for the copies to
+ * run asynchronously) by nsteps steps: per step the state is copied host ->
+ * device, stepped (pic_step) and copied device -> host into the same arrays,
+ * counts, next ids and step index updated; stats (nullable) receives the last
+ * step's statistics with `pushes` summed over the nsteps steps.  The copies are pieces of at most 64 MB on two copy
+ * streams of the context: the upload of a piece for step k+1 starts as soon
+ * as the same piece of step k's result has landed on the host, so the
+ * device -> host and host -> device copies overlap (the host link is full
+ * duplex).  The same result as nsteps x (pic_state_upload, pic_step,
+ * pic_state_download).  On entry hs->n[s] is the number of particles of
+ * species s in the host state; the host arrays must hold the context's
+ * capacity of each species (pic_get_view's cap), up to which the counts can
+ * grow.  Returns after the last copy has finished.
+ * Errors: those of pic_state_upload and pic_step (non-fatal PIC_E_SUBSTEP /
+ * PIC_E_CAPACITY after all steps). */
+int pic_step_host(pic_ctx *ctx, pic_host_state *hs, int nsteps, pic_step_stats *stats);
+
 /* Set particle counts / next ids / step index after the caller wrote state
  * through pic_get_view.  Errors: PIC_E_STATE (count beyond capacity). */
 int pic_set_counts(pic_ctx *ctx, long long ne, long long ni, uint32_t next_id_e,

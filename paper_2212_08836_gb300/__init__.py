@@ -117,6 +117,7 @@ def _load_lib():
     L.pic_substep_histogram.argtypes = [_P, _I, _P]
     L.pic_state_upload.argtypes = [_P, C.POINTER(HostState)]
     L.pic_state_download.argtypes = [_P, C.POINTER(HostState)]
+    L.pic_step_host.argtypes = [_P, C.POINTER(HostState), _I, _P]
     L.pic_profile.argtypes = [_P, _I]
     L.pic_profile_read.argtypes = [_P, _P, _P]
     L.pic_cnn_workspace_size.argtypes = [C.POINTER(CnnConfig)]
@@ -520,6 +521,26 @@ class Pic:
         hs["next_id"] = [H.next_id[0], H.next_id[1]]
         hs["step"] = H.step
         return hs
+
+    def step_host(self, hs, n=1, check=True):
+        """n steps of a state kept in (pinned) host memory through pic_step_host:
+        per step host -> device, step, device -> host into the buffers of hs,
+        with each step's download overlapped with the next step's upload.
+        The host arrays of hs hold the context's capacity (host_state does);
+        hs["n"] are the particles in them.  Returns (code, stats of the last
+        step) and updates hs's counts."""
+        for s in range(2):
+            if hs["species"][s]["cell"].numel() < self.view()["cap"][s]:
+                raise ValueError("host arrays must hold the context's capacity")
+        H = self._host_struct(hs)
+        st = StepStats()
+        rc = lib().pic_step_host(self._h, C.byref(H), int(n), C.addressof(st))
+        if check and rc not in (PIC_OK, PIC_E_SUBSTEP):
+            _check(rc, "pic_step_host")
+        hs["n"] = [H.n[0], H.n[1]]
+        hs["next_id"] = [H.next_id[0], H.next_id[1]]
+        hs["step"] = H.step
+        return rc, st.as_dict()
 
     def get_state(self, s):
         v = self.view()

@@ -50,6 +50,10 @@ struct pic_ctx {
   cudaStream_t pstream;
   cudaEvent_t pev[2];
   int pstream_made;
+  // pic_step_host: copy streams (device -> host, host -> device) and their events
+  cudaStream_t hs_dn, hs_up;
+  cudaEvent_t hs_ev[130];
+  int hs_made;
   float *q_real[2];          // mixed form queue records (trial displacements)
   double *q_real64[2];       // FP64 form queue records
   AlphaOut64 alpha64;        // FP64 form: normalised accelerations per species
@@ -1090,6 +1094,13 @@ void pic_destroy(pic_ctx *ctx) {
     cudaEventDestroy(ctx->pev[0]);
     cudaEventDestroy(ctx->pev[1]);
     cudaStreamDestroy(ctx->pstream);
+  }
+  if (ctx->hs_made) {
+    cudaStreamSynchronize(ctx->hs_dn);
+    cudaStreamSynchronize(ctx->hs_up);
+    for (int k = 0; k < 130; ++k) cudaEventDestroy(ctx->hs_ev[k]);
+    cudaStreamDestroy(ctx->hs_dn);
+    cudaStreamDestroy(ctx->hs_up);
   }
   free(ctx);
 }
@@ -2352,6 +2363,92 @@ int pic_state_download(pic_ctx *x, pic_host_state *out) {
   }
   out->step = x->step;
   return PIC_OK;
+}
+
+// pic_step_host: the state's arrays as (device, host, bytes) pieces of at
+// most kHostPiece bytes, species 0 then 1 (cell, a, b, vr, vt, vz, w, id),
+// then the fields
+namespace {
+constexpr size_t kHostPiece = 64u << 20;
+constexpr int kHostPieces = 128;
+struct HostPiece {
+  char *dev, *host;
+  size_t bytes;
+};
+int host_pieces(pic_ctx *x, pic_host_state *hs, HostPiece *out) {
+  const size_t rs = x->mixed ? 4 : 8;
+  const int nr = x->g.nr, nz = x->g.nz;
+  int k = 0;
+  auto add = [&](void *dev, void *host, size_t b) {
+    for (size_t o = 0; o < b && k < kHostPieces; o += kHostPiece)
+      out[k++] = {(char *)dev + o, (char *)host + o, b - o < kHostPiece ? b - o : kHostPiece};
+  };
+  for (int s = 0; s < 2; ++s) {
+    Parts &P = cur(x, s);
+    const size_t n = (size_t)x->n[s];
+    add(P.cell, hs->cell[s], n * 4);
+    add(P.a, hs->a[s], n * rs);
+    add(P.b, hs->b[s], n * rs);
+    add(P.vr, hs->vr[s], n * rs);
+    add(P.vt, hs->vt[s], n * rs);
+    add(P.vz, hs->vz[s], n * rs);
+    add(P.w, hs->w[s], n * rs);
+    add(P.id, hs->id[s], n * 4);
+  }
+  if (hs->er) add(x->er, hs->er, (size_t)nr * (nz + 1) * 8);
+  if (hs->ez) add(x->ez, hs->ez, (size_t)(nr + 1) * nz * 8);
+  if (hs->h) add(x->h, hs->h, (size_t)nr * nz * 8);
+  return k;
+}
+}  // namespace
+
+int pic_step_host(pic_ctx *x, pic_host_state *hs, int nsteps, pic_step_stats *st) {
+  if (!x || !hs || nsteps < 0) return PIC_E_CONFIG;
+  if (!x->hs_made) {
+    bool ok = cudaStreamCreateWithFlags(&x->hs_dn, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&x->hs_up, cudaStreamNonBlocking) == cudaSuccess;
+    for (int k = 0; ok && k < 130; ++k)
+      ok = cudaEventCreateWithFlags(&x->hs_ev[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) return PIC_E_CUDA;
+    x->hs_made = 1;
+  }
+  int r = pic_state_upload(x, hs);
+  if (r) return r;
+  int rc = PIC_OK;
+  HostPiece pc[kHostPieces];
+  long long pushes = 0;
+  for (int it = 0; it < nsteps; ++it) {
+    r = pic_step(x, 1, st);
+    if (st) {
+      pushes += st->pushes;
+      st->pushes = pushes;
+    }
+    if (r && r != PIC_E_SUBSTEP && r != PIC_E_CAPACITY) return r;
+    if (r) rc = r;
+    const int np = host_pieces(x, hs, pc);
+    const bool more = it + 1 < nsteps;
+    // the result back to the host, piece by piece; the next step's upload of
+    // each piece starts as soon as that piece has landed (the link is full duplex)
+    cudaError_t e = cudaEventRecord(x->hs_ev[128], x->s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(x->hs_dn, x->hs_ev[128], 0);
+    for (int k = 0; k < np && e == cudaSuccess; ++k) {
+      e = cudaMemcpyAsync(pc[k].host, pc[k].dev, pc[k].bytes, cudaMemcpyDeviceToHost, x->hs_dn);
+      if (e == cudaSuccess && more) e = cudaEventRecord(x->hs_ev[k], x->hs_dn);
+      if (e == cudaSuccess && more) e = cudaStreamWaitEvent(x->hs_up, x->hs_ev[k], 0);
+      if (e == cudaSuccess && more)
+        e = cudaMemcpyAsync(pc[k].dev, pc[k].host, pc[k].bytes, cudaMemcpyHostToDevice, x->hs_up);
+    }
+    if (e == cudaSuccess && more) e = cudaEventRecord(x->hs_ev[129], x->hs_up);
+    if (e == cudaSuccess && more) e = cudaStreamWaitEvent(x->s, x->hs_ev[129], 0);
+    if (e == cudaSuccess && !more) e = cudaStreamSynchronize(x->hs_dn);
+    if (e != cudaSuccess) return PIC_E_CUDA;
+    for (int s = 0; s < 2; ++s) {
+      hs->n[s] = x->n[s];
+      hs->next_id[s] = x->next_id[s];
+    }
+    hs->step = x->step;
+  }
+  return rc;
 }
 
 int pic_set_counts(pic_ctx *x, long long ne, long long ni, uint32_t nide, uint32_t nidi,

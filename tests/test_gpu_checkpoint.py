@@ -112,3 +112,43 @@ def test_host_state_round_trip():
     with pytest.raises(M.PicError) as e:
         a.state_download(small)
     assert e.value.code == M.PIC_E_STATE
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_step_host_matches_upload_step_download(precision):
+    """pic_step_host (download of each step overlapped with the next step's
+    upload) gives the host state that the same steps give through
+    pic_state_upload / pic_step / pic_state_download, step counters and the
+    summed pushes included."""
+    M = P()
+    cfg = M.small_reactor(np_init=20000, mcc_on=1, gas_pressure=10.0, precision=precision,
+                          picard_tol=1e-8 if precision == 0 else 1e-5)
+    a, b = M.Pic(cfg, device=DEV), M.Pic(cfg, device=DEV)
+    a.load_particles()
+    b.load_particles()
+    ha, hb = a.host_state(pinned=True), b.host_state(pinned=True)
+    a.state_download(ha)
+    b.state_download(hb)
+    pushes = 0
+    for _ in range(4):
+        b.state_upload(hb)
+        _, st = b.step(1)
+        pushes += st["pushes"]
+        b.state_download(hb)
+    rc, sa = a.step_host(ha, 4)
+    assert rc == 0 and sa["pushes"] == pushes
+    assert ha["n"] == hb["n"] and ha["next_id"] == hb["next_id"] and ha["step"] == hb["step"]
+    for s in range(2):
+        n = ha["n"][s]
+        ga = {k: ha["species"][s][k][:n].numpy() for k in ("id", "cell", "a", "b", "vr", "vt", "vz")}
+        gb = {k: hb["species"][s][k][:n].numpy() for k in ("id", "cell", "a", "b", "vr", "vt", "vz")}
+        oa, ob = np.argsort(ga["id"]), np.argsort(gb["id"])
+        np.testing.assert_array_equal(ga["id"][oa], gb["id"][ob])
+        np.testing.assert_array_equal(ga["cell"][oa], gb["cell"][ob])
+        tol = 1e-9 if precision == 0 else 1e-5
+        for k in ("a", "b", "vr", "vt", "vz"):
+            x, y = ga[k][oa].astype(np.float64), gb[k][ob].astype(np.float64)
+            np.testing.assert_allclose(x, y, rtol=tol, atol=tol * np.max(np.abs(y)))
+    for k in ("er", "ez", "h"):
+        x, y = ha[k].numpy(), hb[k].numpy()
+        assert np.max(np.abs(x - y)) <= 1e-6 * max(np.max(np.abs(y)), 1e-300)
