@@ -50,6 +50,17 @@ struct pic_ctx {
   cudaStream_t pstream;
   cudaEvent_t pev[2];
   int pstream_made;
+  // the ions' push of a pass on a second stream beside the electrons' (the
+  // persistent kernels fill the SMs the other species' tails leave idle),
+  // with its own queue buffers
+  cudaStream_t sstream;
+  cudaEvent_t sev[2];
+  int sstream_made;
+  int *queue2, *qblock2;
+  float *q_real2[2];
+  double *q_real64_2[2];
+  int *q_cell2;
+  float *q_st2[6];
   // pic_step_host: copy streams (device -> host, host -> device) and their events
   cudaStream_t hs_dn, hs_up;
   cudaEvent_t hs_ev[130];
@@ -281,6 +292,8 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
   const size_t qc = pc + (size_t)kMaxFastBlocks * 256;  // queue entries
   x->queue = (int *)K.take(qc * 4);
   x->qblock = (int *)K.take((size_t)2 * kMaxFastBlocks * 4);  // front and back counts
+  x->queue2 = (int *)K.take(qc * 4);                           // the ions' (second stream)
+  x->qblock2 = (int *)K.take((size_t)2 * kMaxFastBlocks * 4);
   if (c->precision == PIC_MIXED) {
     for (int s = 0; s < 2; ++s) {
       x->alpha.ar[s] = (float *)K.take(ner * 4);
@@ -290,6 +303,9 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
     // queue entries carry the start state: cell, then a, b, vr, vt, vz, w
     x->q_cell = (int *)K.take(qc * 4);
     for (int k = 0; k < 6; ++k) x->q_st[k] = (float *)K.take(qc * 4);
+    for (int k = 0; k < 2; ++k) x->q_real2[k] = (float *)K.take(qc * 4);
+    x->q_cell2 = (int *)K.take(qc * 4);
+    for (int k = 0; k < 6; ++k) x->q_st2[k] = (float *)K.take(qc * 4);
     // per species: near-axis crossers for FP64 arithmetic, and their counts
     x->plist[0] = (int *)K.take((size_t)pc * 4);
     x->plist[1] = (int *)K.take((size_t)pc * 4);
@@ -300,6 +316,7 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
       x->alpha64.az[s] = (double *)K.take(nez * 8);
     }
     for (int k = 0; k < 2; ++k) x->q_real64[k] = (double *)K.take(qc * 8);
+    for (int k = 0; k < 2; ++k) x->q_real64_2[k] = (double *)K.take(qc * 8);
   }
   x->er = (double *)K.take(ner * 8);
   x->ez = (double *)K.take(nez * 8);
@@ -526,8 +543,18 @@ int push_all(pic_ctx *x, const double *erh, const double *ezh, double *ir, doubl
   if (ctimed) cudaEventRecordWithFlags(x->cap_pe[0], x->s, cudaEventRecordExternal);
   const int nsp = x->cfg.ions_fixed ? 1 : 2;
   bool forked = false;
+  // the ions on the second stream, forked after the pass's set-up and joined
+  // before the field solve
+  const bool split = nsp == 2 && x->sstream_made;
+  if (split) {
+    if (cudaEventRecord(x->sev[0], x->s) != cudaSuccess ||
+        cudaStreamWaitEvent(x->sstream, x->sev[0], 0) != cudaSuccess)
+      return PIC_E_CUDA;
+  }
   for (int s = 0; s < nsp; ++s) {
     const double q = s == 0 ? -kQE : kQE, m = s == 0 ? kME : kMAr;
+    const bool two = split && s == 1;
+    cudaStream_t ss = two ? x->sstream : x->s;
     double *ws[3] = {nullptr, nullptr, nullptr};
     if (wall) {
       int nr = x->g.nr, nz = x->g.nz;
@@ -548,19 +575,26 @@ int push_all(pic_ctx *x, const double *erh, const double *ezh, double *ir, doubl
       if (L.hist && oop) L.hist = x->hist_spec;  // counted once the pass is adopted
       L.ar = x->alpha.ar[s];
       L.az = x->alpha.az[s];
-      set_queue(x, x->q_real, L);
-      L.q_cell = x->q_cell;
-      L.q_a = x->q_st[0];
-      L.q_b = x->q_st[1];
-      L.q_vr = x->q_st[2];
-      L.q_vt = x->q_st[3];
-      L.q_vz = x->q_st[4];
-      L.q_w = x->q_st[5];
+      set_queue(x, two ? x->q_real2 : x->q_real, L);
+      if (two) {
+        L.queue = x->queue2;
+        L.qblock = x->qblock2;
+      }
+      float *const *qs = two ? x->q_st2 : x->q_st;
+      L.q_cell = two ? x->q_cell2 : x->q_cell;
+      L.q_a = qs[0];
+      L.q_b = qs[1];
+      L.q_vr = qs[2];
+      L.q_vt = qs[3];
+      L.q_vz = qs[4];
+      L.q_w = qs[5];
       L.plist = x->plist[s];
       L.pcnt = x->pcnt + s;
       fast = L.wbt == 0.f;
-      e = launch_push(L, x->s);
-      if (e == cudaSuccess) {
+      e = launch_push(L, ss);
+      if (e == cudaSuccess && two) {
+        e = launch_push_fp32_axis(L, ss);  // the ions' near-axis list after their push
+      } else if (e == cudaSuccess) {
         if (x->pstream_made) {
           // the near-axis lists on the side stream, beside the next launches
           // (the electrons' beside the ions' pass), joined at the end
@@ -582,9 +616,13 @@ int push_all(pic_ctx *x, const double *erh, const double *ezh, double *ir, doubl
       if (L.hist && oop) L.hist = x->hist_spec;  // counted once the pass is adopted
       L.ar = x->alpha64.ar[s];
       L.az = x->alpha64.az[s];
-      set_queue(x, x->q_real64, L);
+      set_queue(x, two ? x->q_real64_2 : x->q_real64, L);
+      if (two) {
+        L.queue = x->queue2;
+        L.qblock = x->qblock2;
+      }
       fast = L.wbt == 0.0;
-      e = launch_push(L, x->s);
+      e = launch_push(L, ss);
     }
     if (e != cudaSuccess) return PIC_E_CUDA;
     if (n > 0) {
@@ -594,6 +632,9 @@ int push_all(pic_ctx *x, const double *erh, const double *ezh, double *ir, doubl
     }
   }
   if (forked && cudaStreamWaitEvent(x->s, x->pev[1], 0) != cudaSuccess) return PIC_E_CUDA;
+  if (split && (cudaEventRecord(x->sev[1], x->sstream) != cudaSuccess ||
+                cudaStreamWaitEvent(x->s, x->sev[1], 0) != cudaSuccess))
+    return PIC_E_CUDA;
   if (ctimed) cudaEventRecordWithFlags(x->cap_pe[1], x->s, cudaEventRecordExternal);
   if (timed) {
     cudaEventRecord(x->ev[2 * x->nev + 1], x->s);
@@ -1027,6 +1068,12 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x->pev[1], cudaEventDisableTiming);
     if (e == cudaSuccess) x->pstream_made = 1;
   }
+  if (e == cudaSuccess) {
+    e = cudaStreamCreateWithFlags(&x->sstream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x->sev[0], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x->sev[1], cudaEventDisableTiming);
+    if (e == cudaSuccess) x->sstream_made = 1;
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(x->s);
   if (e != cudaSuccess) {
     if (x->hn) cudaFreeHost(x->hn);
@@ -1094,6 +1141,12 @@ void pic_destroy(pic_ctx *ctx) {
     cudaEventDestroy(ctx->pev[0]);
     cudaEventDestroy(ctx->pev[1]);
     cudaStreamDestroy(ctx->pstream);
+  }
+  if (ctx->sstream_made) {
+    cudaStreamSynchronize(ctx->sstream);
+    cudaEventDestroy(ctx->sev[0]);
+    cudaEventDestroy(ctx->sev[1]);
+    cudaStreamDestroy(ctx->sstream);
   }
   if (ctx->hs_made) {
     cudaStreamSynchronize(ctx->hs_dn);
