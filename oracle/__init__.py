@@ -106,6 +106,12 @@ def _declare(L):
     L.oracle_field_create.restype = _P
     L.oracle_field_destroy.argtypes = [_P]
     L.oracle_field_solve.argtypes = [_P, _P, _P, _P, _P, _P, _D, _D, _D, _P, _P, _P, _P]
+    L.oracle_port_create.argtypes = [_I, _I, _D, _D, _I, _I, _I, _D, _D, _D, _D, _D]
+    L.oracle_port_create.restype = _P
+    L.oracle_port_destroy.argtypes = [_P]
+    L.oracle_port_solve.argtypes = [_P] + [_P] * 8 + [_D, _D] + [_P] * 7
+    L.oracle_port_energy.argtypes = [_P] * 7
+    L.oracle_port_energy.restype = _D
     L.oracle_conduction_charge.argtypes = [_P, _P, _P, _P, _P, _P]
     L.oracle_conduction_charge.restype = _D
     L.oracle_field_energy.argtypes = [_I, _I, _D, _D, _I, _I, _D, _D, _D, _P, _P, _P]
@@ -292,6 +298,46 @@ class FieldSolver:
         the Ohmic energy of the step."""
         return lib().oracle_conduction_charge(self._h, _p(er0), _p(ez0), _p(er1), _p(ez1),
                                               _p(qc))
+
+
+class PortSolver:
+    """Implicit CN Maxwell solve with the axial dielectric port below the
+    powered electrode (Sec. 2.2, Eqs. 5 and 7), by banded Cholesky of the
+    H system of reactor and port together.  ip: the port's inner radius is
+    r(ip) (the electrode's); nzp cells of height dzp; erq: its relative
+    permittivity."""
+
+    def __init__(self, grid: Grid, dt, ip, nzp, dzp, erq, eps=EPS0, mu=MU0):
+        self.grid, self.dt, self.eps, self.mu = grid, dt, eps, mu
+        self.ip, self.nzp, self.dzp, self.erq = ip, nzp, dzp, erq
+        self._h = lib().oracle_port_create(grid.nr, grid.nz, grid.dr, grid.dz, grid.xa, ip, nzp,
+                                           dzp, erq, dt, eps, mu)
+        if not self._h:
+            raise RuntimeError("oracle port matrix not positive definite")
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().oracle_port_destroy(self._h)
+            self._h = None
+
+    def zeros_port(self):
+        """(erp, ezp, hp): port E_r edges and H cells (nr - ip) x nzp, E_z edges
+        (nr - ip + 1) x nzp."""
+        m = self.grid.nr - self.ip
+        return (np.zeros(m * self.nzp), np.zeros((m + 1) * self.nzp), np.zeros(m * self.nzp))
+
+    def solve(self, er0, ez0, h0, erp0, ezp0, hp0, ir, iz, phi0, phi1):
+        g = self.grid
+        er1, ez1, h1 = g.zeros_fields()
+        erp1, ezp1, hp1 = self.zeros_port()
+        src = np.zeros(1)
+        lib().oracle_port_solve(self._h, _p(er0), _p(ez0), _p(h0), _p(erp0), _p(ezp0), _p(hp0),
+                                _p(ir), _p(iz), phi0, phi1, _p(er1), _p(ez1), _p(h1), _p(erp1),
+                                _p(ezp1), _p(hp1), _p(src))
+        return er1, ez1, h1, erp1, ezp1, hp1, float(src[0])
+
+    def energy(self, er, ez, h, erp, ezp, hp):
+        return lib().oracle_port_energy(self._h, _p(er), _p(ez), _p(h), _p(erp), _p(ezp), _p(hp))
 
 
 def sigma_el(eps):

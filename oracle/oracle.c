@@ -1191,6 +1191,322 @@ int64_t oracle_sort(int ncell, int64_t n, int32_t *cell, double *a, double *b, d
   return m;
 }
 
+/* ------------------------------------------------ axial dielectric port */
+/* The paper's feed (Sec. 2.2, Fig. 1): below the powered electrode, a coaxial
+ * port filled with a dielectric (relative permittivity erq) runs from the
+ * electrode radius r_p = r(ip) to r = R, nzp cells of height dzp deep; the
+ * electrode's stem (r < r_p) and the outer wall (r = R) are conductors (E_z = 0
+ * on them), the powered electrode face (z = 0, r < r_p) stays a plate (E_r = 0)
+ * and the reactor's side wall r = R a conductor (E_z = 0).  The port cells
+ * carry H_theta like the reactor's; the E_r edges on z = 0 for r > r_p join the
+ * two (interface edges: their dual face is half in the port, half in the
+ * reactor, D = eps 2 pi r (erq dzp / 2 + dz / 2)).  At the port's end (z = -nzp
+ * dzp) Eq. 5, Mur's condition for the outgoing TEM wave with an incoming one,
+ * is taken in its characteristic form E_r + eta H_theta = 2 E_r^+ (eta =
+ * sqrt(mu / (erq eps))), CN-centred, with the incoming wave of Eq. 7's
+ * reading: the coaxial TEM field E_r^+(r) = phi^+ / (r ln(R / r_p)) of half
+ * the electrode potential, phi^+ = phi / 2 (the paper's phi^+ ~ phi / 2).  So
+ * 2 E_r^+ at the half step is phi^{n+1/2} / (r ln(R / r_p)); eliminating E as in
+ * the reactor adds dt 2 pi r_{i+1/2} dr_i eta to the diagonal of the bottom
+ * port cells.  H unknowns are numbered column by column, the nzp port cells
+ * (bottom to top) before the column's reactor cells (dummy identity rows where
+ * r < r_p), so the system is banded with bandwidth nzp + nz; banded Cholesky. */
+typedef struct {
+  int nr, nz, ip, nzp, cs, n, bw, xa;
+  double dr, dz, dzp, erq, dt, eps, mu, lnr;
+  double *Lb;
+} o_pfield;
+
+static double *o_pband(o_pfield *F, int i, int j) {
+  return &F->Lb[(size_t)i * (F->bw + 1) + (j - i + F->bw)];
+}
+static int o_pidx(const o_pfield *F, int i, int jj) { return i * F->cs + F->nzp + jj; }
+static double o_dint(const og_grid *g, const o_pfield *F, int i) {
+  return F->eps * O_TWO_PI * o_rhalf(g, i) * (0.5 * F->erq * F->dzp + 0.5 * F->dz);
+}
+static double o_dpr(const og_grid *g, const o_pfield *F, int i) {
+  return F->eps * F->erq * O_TWO_PI * o_rhalf(g, i) * F->dzp;
+}
+static double o_dpz(const og_grid *g, const o_pfield *F, int i) {
+  return F->eps * F->erq * o_area_z(g, i);
+}
+static double o_vol_hp(const og_grid *g, const o_pfield *F, int i) {
+  return O_TWO_PI * o_rhalf(g, i) * o_drc(g, i) * F->dzp;
+}
+/* 2 E_r^+ at the half step on the port's end edge (i + 1/2) */
+static double o_port_ein2(const og_grid *g, const o_pfield *F, int i, double phi_half) {
+  return phi_half / (o_rhalf(g, i) * F->lnr);
+}
+
+void *oracle_port_create(int nr, int nz, double dr, double dz, int xa, int ip, int nzp,
+                         double dzp, double erq, double dt, double eps, double mu) {
+  if (ip < 1 || ip >= nr || nzp < 1) return NULL;
+  o_pfield *F = (o_pfield *)calloc(1, sizeof(o_pfield));
+  og_grid g = {nr, nz, dr, dz, xa, 0, 1.0, 0.0};
+  F->nr = nr; F->nz = nz; F->ip = ip; F->nzp = nzp; F->xa = xa;
+  F->dr = dr; F->dz = dz; F->dzp = dzp; F->erq = erq; F->dt = dt; F->eps = eps; F->mu = mu;
+  F->lnr = log(o_rnode(&g, nr) / o_rnode(&g, ip));
+  F->cs = nzp + nz;
+  F->n = nr * F->cs;
+  F->bw = F->cs;
+  F->Lb = (double *)calloc((size_t)F->n * (F->bw + 1), sizeof(double));
+  if (!F->Lb) { free(F); return NULL; }
+  const double hdt2 = 0.5 * dt * dt, eta = sqrt(mu / (erq * eps));
+  for (int i = 0; i < nr; ++i) {
+    const double s = O_TWO_PI * o_rhalf(&g, i), L = o_drc(&g, i);
+    for (int j = 0; j < nz; ++j) *o_pband(F, o_pidx(F, i, j), o_pidx(F, i, j)) += 2.0 * mu * o_vol_h(&g, i);
+    for (int q = 0; q < nzp; ++q) {
+      const int c = o_pidx(F, i, q - nzp);
+      *o_pband(F, c, c) += i >= ip ? 2.0 * mu * o_vol_hp(&g, F, i) : 1.0;
+    }
+    /* reactor E_r edges j = 1..nz-1 */
+    for (int j = 1; j < nz; ++j) {
+      const double W = L / (eps * o_area_r(&g, i));
+      const int lo = o_pidx(F, i, j - 1), hi = o_pidx(F, i, j);
+      *o_pband(F, lo, lo) += hdt2 * W * s * s;
+      *o_pband(F, hi, hi) += hdt2 * W * s * s;
+      *o_pband(F, hi, lo) -= hdt2 * W * s * s;
+    }
+    if (i < ip) continue;
+    /* interface edge (z = 0) and the port's E_r edges between its rows */
+    {
+      const double W = L / o_dint(&g, F, i);
+      const int lo = o_pidx(F, i, -1), hi = o_pidx(F, i, 0);
+      *o_pband(F, lo, lo) += hdt2 * W * s * s;
+      *o_pband(F, hi, hi) += hdt2 * W * s * s;
+      *o_pband(F, hi, lo) -= hdt2 * W * s * s;
+    }
+    for (int q = 1; q < nzp; ++q) {
+      const double W = L / o_dpr(&g, F, i);
+      const int lo = o_pidx(F, i, q - 1 - nzp), hi = o_pidx(F, i, q - nzp);
+      *o_pband(F, lo, lo) += hdt2 * W * s * s;
+      *o_pband(F, hi, hi) += hdt2 * W * s * s;
+      *o_pband(F, hi, lo) -= hdt2 * W * s * s;
+    }
+    /* the port's end: E_r = 2 E^+ - eta H */
+    { const int c = o_pidx(F, i, -nzp); *o_pband(F, c, c) += dt * s * L * eta; }
+  }
+  /* E_z edges: reactor (i, j + 1/2) for i < nr (i = nr: wall, E_z = 0); the
+   * port's (i, q + 1/2) for ip < i < nr (r_p and R: conductors) */
+  for (int i = 0; i < nr; ++i) {
+    const double sr = O_TWO_PI * o_rhalf(&g, i);
+    const double sl = i >= 1 ? O_TWO_PI * o_rhalf(&g, i - 1) : 0.0;
+    for (int j = 0; j < nz; ++j) {
+      const double W = dz / (eps * o_area_z(&g, i));
+      const int cr = o_pidx(F, i, j);
+      *o_pband(F, cr, cr) += hdt2 * W * sr * sr;
+      if (i >= 1) {
+        const int cl = o_pidx(F, i - 1, j);
+        *o_pband(F, cl, cl) += hdt2 * W * sl * sl;
+        *o_pband(F, cr, cl) -= hdt2 * W * sl * sr;
+      }
+    }
+    if (i <= ip) continue;
+    for (int q = 0; q < nzp; ++q) {
+      const double W = dzp / o_dpz(&g, F, i);
+      const int cr = o_pidx(F, i, q - nzp), cl = o_pidx(F, i - 1, q - nzp);
+      *o_pband(F, cr, cr) += hdt2 * W * sr * sr;
+      *o_pband(F, cl, cl) += hdt2 * W * sl * sl;
+      *o_pband(F, cr, cl) -= hdt2 * W * sl * sr;
+    }
+  }
+  int n = F->n, bw = F->bw;
+  for (int i = 0; i < n; ++i) {
+    int j0 = i - bw < 0 ? 0 : i - bw;
+    for (int j = j0; j <= i; ++j) {
+      double sum = *o_pband(F, i, j);
+      int k0 = j0 > j - bw ? j0 : j - bw;
+      for (int k = k0; k < j; ++k) sum -= *o_pband(F, i, k) * *o_pband(F, j, k);
+      if (i == j) {
+        if (!(sum > 0.0)) { free(F->Lb); free(F); return NULL; }
+        *o_pband(F, i, i) = sqrt(sum);
+      } else {
+        *o_pband(F, i, j) = sum / *o_pband(F, j, j);
+      }
+    }
+  }
+  return F;
+}
+
+void oracle_port_destroy(void *p) {
+  o_pfield *F = (o_pfield *)p;
+  if (!F) return;
+  free(F->Lb);
+  free(F);
+}
+
+/* One implicit field solve with the port.  Reactor arrays as in
+ * oracle_field_solve (E_r of j = 0 holds the interface edges for i >= ip, E_z of
+ * i = nr stays zero); port arrays: hp[(i-ip)*nzp + q], erp[(i-ip)*nzp + q] (E_r on
+ * the port's lower face of cell (i, q): q = 0 the end edge), ezp[(i-ip)*nzp + q]
+ * for nodes i = ip..nr (zero on the conductors).  phi0, phi1: electrode
+ * potential at n and n+1.  *src: energy delivered through the port's end. */
+void oracle_port_solve(void *p, const double *er0, const double *ez0, const double *h0,
+                       const double *erp0, const double *ezp0, const double *hp0,
+                       const double *ir, const double *iz, double phi0, double phi1,
+                       double *er1, double *ez1, double *h1, double *erp1, double *ezp1,
+                       double *hp1, double *src) {
+  o_pfield *F = (o_pfield *)p;
+  const int nr = F->nr, nz = F->nz, ip = F->ip, nzp = F->nzp;
+  og_grid g = {nr, nz, F->dr, F->dz, F->xa, 0, 1.0, 0.0};
+  const double dt = F->dt, eps = F->eps, mu = F->mu, eta = sqrt(mu / (F->erq * eps));
+  const double phih = 0.5 * (phi0 + phi1);
+  double *x = (double *)calloc((size_t)F->n, sizeof(double));
+  for (int i = 0; i < nr; ++i) {
+    for (int j = 0; j < nz; ++j) x[o_pidx(F, i, j)] = 2.0 * mu * o_vol_h(&g, i) * h0[i * nz + j];
+    if (i >= ip)
+      for (int q = 0; q < nzp; ++q)
+        x[o_pidx(F, i, q - nzp)] = 2.0 * mu * o_vol_hp(&g, F, i) * hp0[(i - ip) * nzp + q];
+  }
+  /* - dt C^T L Et over the unknown edges (and the end edges' 2 E^+) */
+  for (int i = 0; i < nr; ++i) {
+    const double s = O_TWO_PI * o_rhalf(&g, i), L = o_drc(&g, i);
+    for (int j = 1; j < nz; ++j) {
+      const double D = eps * o_area_r(&g, i);
+      const double et = (D * er0[i * (nz + 1) + j] - 0.5 * ir[i * (nz + 1) + j]) / D;
+      x[o_pidx(F, i, j)] -= dt * (-s) * L * et;
+      x[o_pidx(F, i, j - 1)] -= dt * (s) * L * et;
+    }
+    if (i < ip) continue;
+    {
+      const double D = o_dint(&g, F, i);
+      const double et = (D * er0[i * (nz + 1)] - 0.5 * ir[i * (nz + 1)]) / D;
+      x[o_pidx(F, i, 0)] -= dt * (-s) * L * et;
+      x[o_pidx(F, i, -1)] -= dt * (s) * L * et;
+    }
+    for (int q = 1; q < nzp; ++q) {
+      const double et = erp0[(i - ip) * nzp + q];
+      x[o_pidx(F, i, q - nzp)] -= dt * (-s) * L * et;
+      x[o_pidx(F, i, q - 1 - nzp)] -= dt * (s) * L * et;
+    }
+    x[o_pidx(F, i, -nzp)] -= dt * (-s) * L * o_port_ein2(&g, F, i, phih);
+  }
+  for (int i = 0; i < nr; ++i) {
+    const double sr = O_TWO_PI * o_rhalf(&g, i);
+    const double sl = i >= 1 ? O_TWO_PI * o_rhalf(&g, i - 1) : 0.0;
+    for (int j = 0; j < nz; ++j) {
+      const double D = eps * o_area_z(&g, i);
+      const double et = (D * ez0[i * nz + j] - 0.5 * iz[i * nz + j]) / D;
+      x[o_pidx(F, i, j)] -= dt * sr * F->dz * et;
+      if (i >= 1) x[o_pidx(F, i - 1, j)] -= dt * (-sl) * F->dz * et;
+    }
+    if (i <= ip) continue;
+    for (int q = 0; q < nzp; ++q) {
+      const double et = ezp0[(i - ip) * nzp + q];
+      x[o_pidx(F, i, q - nzp)] -= dt * sr * F->dzp * et;
+      x[o_pidx(F, i - 1, q - nzp)] -= dt * (-sl) * F->dzp * et;
+    }
+  }
+  /* banded Cholesky solve: x = H^{n+1/2} */
+  {
+    const int n = F->n, bw = F->bw;
+    for (int i = 0; i < n; ++i) {
+      double sum = x[i];
+      const int k0 = i - bw < 0 ? 0 : i - bw;
+      for (int k = k0; k < i; ++k) sum -= *o_pband(F, i, k) * x[k];
+      x[i] = sum / *o_pband(F, i, i);
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      double sum = x[i];
+      const int k1 = i + bw > n - 1 ? n - 1 : i + bw;
+      for (int k = i + 1; k <= k1; ++k) sum -= *o_pband(F, k, i) * x[k];
+      x[i] = sum / *o_pband(F, i, i);
+    }
+  }
+  for (int i = 0; i < nr; ++i) {
+    for (int j = 0; j < nz; ++j) h1[i * nz + j] = 2.0 * x[o_pidx(F, i, j)] - h0[i * nz + j];
+    if (i >= ip)
+      for (int q = 0; q < nzp; ++q)
+        hp1[(i - ip) * nzp + q] = 2.0 * x[o_pidx(F, i, q - nzp)] - hp0[(i - ip) * nzp + q];
+  }
+  double srcE = 0.0;
+  for (int i = 0; i < nr; ++i) {
+    const double s = O_TWO_PI * o_rhalf(&g, i), L = o_drc(&g, i);
+    for (int j = 0; j <= nz; ++j) {
+      const int e = i * (nz + 1) + j;
+      if (j == nz || (j == 0 && i < ip)) { er1[e] = 0.0; continue; }
+      const double ch = -s * x[o_pidx(F, i, j)] + s * x[o_pidx(F, i, j - 1)];
+      const double D = j == 0 ? o_dint(&g, F, i) : eps * o_area_r(&g, i);
+      er1[e] = (D * er0[e] + dt * ch - ir[e]) / D;
+    }
+    if (i < ip) continue;
+    for (int q = 0; q < nzp; ++q) {
+      const int e = (i - ip) * nzp + q;
+      if (q == 0) {
+        const double xb = x[o_pidx(F, i, -nzp)];
+        const double eh = o_port_ein2(&g, F, i, phih) - eta * xb;
+        erp1[e] = 2.0 * eh - erp0[e];
+        srcE += eh * L * dt * s * xb;
+      } else {
+        const double ch = -s * x[o_pidx(F, i, q - nzp)] + s * x[o_pidx(F, i, q - 1 - nzp)];
+        erp1[e] = erp0[e] + dt * ch / o_dpr(&g, F, i);
+      }
+    }
+  }
+  for (int i = 0; i <= nr; ++i) {
+    const double sr = i < nr ? O_TWO_PI * o_rhalf(&g, i) : 0.0;
+    const double sl = i >= 1 ? O_TWO_PI * o_rhalf(&g, i - 1) : 0.0;
+    for (int j = 0; j < nz; ++j) {
+      const int e = i * nz + j;
+      if (i == nr) { ez1[e] = 0.0; continue; }
+      double ch = sr * x[o_pidx(F, i, j)];
+      if (i >= 1) ch -= sl * x[o_pidx(F, i - 1, j)];
+      const double D = eps * o_area_z(&g, i);
+      ez1[e] = (D * ez0[e] + dt * ch - iz[e]) / D;
+    }
+    if (i < ip) continue;
+    for (int q = 0; q < nzp; ++q) {
+      const int e = (i - ip) * nzp + q;
+      if (i == ip || i == nr) { ezp1[e] = 0.0; continue; }
+      const double ch = sr * x[o_pidx(F, i, q - nzp)] - sl * x[o_pidx(F, i - 1, q - nzp)];
+      ezp1[e] = ezp0[e] + dt * ch / o_dpz(&g, F, i);
+    }
+  }
+  if (src) *src = srcE;
+  free(x);
+}
+
+/* Field energy of the reactor and the port: sum over edges of D L E^2 / 2 and
+ * over H cells of mu V_h H^2 / 2 (the interface edges with their D). */
+double oracle_port_energy(void *p, const double *er, const double *ez, const double *h,
+                          const double *erp, const double *ezp, const double *hp) {
+  o_pfield *F = (o_pfield *)p;
+  const int nr = F->nr, nz = F->nz, ip = F->ip, nzp = F->nzp;
+  og_grid g = {nr, nz, F->dr, F->dz, F->xa, 0, 1.0, 0.0};
+  double W = 0.0;
+  for (int i = 0; i < nr; ++i) {
+    const double L = o_drc(&g, i);
+    for (int j = 0; j < nz; ++j) W += 0.5 * F->mu * o_vol_h(&g, i) * h[i * nz + j] * h[i * nz + j];
+    for (int j = 1; j < nz; ++j) {
+      const double e = er[i * (nz + 1) + j];
+      W += 0.5 * F->eps * o_area_r(&g, i) * L * e * e;
+    }
+    if (i >= ip) {
+      const double e = er[i * (nz + 1)];
+      W += 0.5 * o_dint(&g, F, i) * L * e * e;
+      for (int q = 0; q < nzp; ++q) {
+        const double hv = hp[(i - ip) * nzp + q];
+        W += 0.5 * F->mu * o_vol_hp(&g, F, i) * hv * hv;
+        if (q >= 1) {
+          const double ev = erp[(i - ip) * nzp + q];
+          W += 0.5 * o_dpr(&g, F, i) * L * ev * ev;
+        }
+      }
+    }
+  }
+  for (int i = 0; i < nr; ++i)
+    for (int j = 0; j < nz; ++j) {
+      const double e = ez[i * nz + j];
+      W += 0.5 * F->eps * o_area_z(&g, i) * F->dz * e * e;
+    }
+  for (int i = ip + 1; i < nr; ++i)
+    for (int q = 0; q < nzp; ++q) {
+      const double e = ezp[(i - ip) * nzp + q];
+      W += 0.5 * o_dpz(&g, F, i) * F->dzp * e * e;
+    }
+  return W;
+}
+
 /* ----------------------------------------------------------- full step */
 /* One time step of the implicit method (rows a2-a8): Picard iteration of
  * push+deposit and field solve (Sec. 2.1, after Taitano 2013 / Eremin 2022),

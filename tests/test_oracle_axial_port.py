@@ -1,0 +1,90 @@
+"""Axial dielectric port (Sec. 2.2, Fig. 1; Eqs. 5 and 7) in the oracle's
+field solve: a coaxial port filled with a dielectric below the powered
+electrode, fed by an incoming TEM wave of half the electrode potential
+through Mur's condition at its end.
+
+Pins, none of which retypes the solver:
+  * the discrete energy identity of the CN scheme: with no particles, the
+    field energy of reactor and port changes by exactly the energy the port's
+    end delivers (what the solve reports as src), from random fields;
+  * the coaxial TEM mode: with a slowly varying drive the port's fields are
+    E_r, H_theta proportional to 1/r across the annulus and E_z ~ 0;
+  * the quasi-static limit: a drive slow against the transit time gives the
+    electrode potential the drive's, i.e. E_z = phi / L between the plates on
+    the axis side, and the incident wave of half the potential doubles at the
+    (open, capacitive) reactor end.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+
+
+def setup(nr=16, nz=12, R=0.1, L=0.02, ip=10, nzp=6, Lp=0.03, erq=3.8, dt=2e-11):
+    g = O.Grid(nr, nz, R, L)
+    P = O.PortSolver(g, dt, ip, nzp, Lp / nzp, erq)
+    return g, P
+
+
+def test_energy_identity_from_random_fields():
+    g, P = setup()
+    rng = np.random.default_rng(5)
+    er, ez, h = (rng.normal(size=g.n_er) * 1e3, rng.normal(size=g.n_ez) * 1e3,
+                 rng.normal(size=g.nr * g.nz))
+    erp, ezp, hp = P.zeros_port()
+    erp[:] = rng.normal(size=erp.size) * 1e3
+    ezp[:] = rng.normal(size=ezp.size) * 1e3
+    hp[:] = rng.normal(size=hp.size)
+    # fields on conductors and plates are zero
+    er.reshape(g.nr, g.nz + 1)[:, g.nz] = 0.0
+    er.reshape(g.nr, g.nz + 1)[: P.ip, 0] = 0.0
+    ez.reshape(g.nr + 1, g.nz)[g.nr, :] = 0.0
+    m = g.nr - P.ip
+    ezp.reshape(m + 1, P.nzp)[0, :] = 0.0
+    ezp.reshape(m + 1, P.nzp)[m, :] = 0.0
+    ir, iz = np.zeros(g.n_er), np.zeros(g.n_ez)
+    for phi0, phi1 in ((0.0, 0.0), (3.0, 7.5), (-40.0, 12.0)):
+        W0 = P.energy(er, ez, h, erp, ezp, hp)
+        er1, ez1, h1, erp1, ezp1, hp1, src = P.solve(er, ez, h, erp, ezp, hp, ir, iz, phi0, phi1)
+        W1 = P.energy(er1, ez1, h1, erp1, ezp1, hp1)
+        assert abs(W1 - W0 - src) <= 1e-11 * W0, (W1 - W0, src)
+        if phi0 == phi1 == 0.0:
+            assert src <= 0.0  # Mur's condition only lets energy out
+
+
+def drive(P, g, steps, omega, V):
+    er, ez, h = g.zeros_fields()
+    erp, ezp, hp = P.zeros_port()
+    ir, iz = np.zeros(g.n_er), np.zeros(g.n_ez)
+    for n in range(steps):
+        phi0, phi1 = V * np.sin(omega * n * P.dt), V * np.sin(omega * (n + 1) * P.dt)
+        er, ez, h, erp, ezp, hp, _ = P.solve(er, ez, h, erp, ezp, hp, ir, iz, phi0, phi1)
+    return er, ez, h, erp, ezp, hp, V * np.sin(omega * steps * P.dt)
+
+
+def test_quasi_static_tem_mode_and_gap_field():
+    # a port twice the reactor's height, as the paper's (6.5 against 3 cm), so
+    # that its end is well away from the junction's fringing field
+    g, P = setup(dt=1e-11, nzp=12, Lp=0.06)
+    # a period of 4000 steps (25 MHz, wavelength 12 m against a 5 cm domain)
+    omega = 2 * np.pi / (4000 * P.dt)
+    er, ez, h, erp, ezp, hp, phi = drive(P, g, 1000, omega, 100.0)  # a quarter period: phi = V
+    m = g.nr - P.ip
+    rh = 0.5 * (g.r_nodes()[P.ip:-1] + g.r_nodes()[P.ip + 1:])   # r_{i+1/2} of the port columns
+    # TEM at the port's end (the junction with the reactor, a few cells above,
+    # adds the fringing field): r E_r constant across the annulus, E_z small
+    Erp = erp.reshape(m, P.nzp)
+    Ezp = ezp.reshape(m + 1, P.nzp)
+    for q in (0, 1):
+        rE = rh * Erp[:, q]
+        assert np.max(np.abs(rE - rE.mean())) <= 1e-2 * np.abs(rE.mean()), q
+    assert np.max(np.abs(Ezp[:, 0])) <= 5e-2 * np.max(np.abs(Erp[:, 0]))
+    # the coaxial voltage across the annulus equals the electrode potential at
+    # every height of the port (the incident wave of phi / 2, doubled)
+    dr = np.diff(g.r_nodes()[P.ip:])
+    for q in range(P.nzp):
+        Vc = Erp[:, q] @ dr
+        assert abs(Vc - phi) <= 1e-2 * phi, (q, Vc, phi)
+    # gap field on the axis side: E_z = phi / L (directed from the powered plate)
+    Ez = ez.reshape(g.nr + 1, g.nz)
+    assert np.max(np.abs(Ez[: P.ip // 2] * g.L - phi)) <= 1e-2 * phi
