@@ -66,6 +66,15 @@ extern "C" {
                                absorbing condition E_z + eta H_theta = 2 E_in with the incoming
                                wave E_in = V(t)/(2L), eta = sqrt(mu/eps); outgoing waves leave,
                                a slow drive gives the gap voltage V(t).  EM model only. */
+#define PIC_FEED_AXIAL 2    /* the paper's feed (Sec. 2.2, Fig. 1): a coaxial port filled with a
+                               dielectric (eps_port) below the powered electrode, from its radius
+                               r_p = r(port_rin) out to R, port_cells cells of port_len / port_cells
+                               deep; the electrode's stem and the outer wall are conductors, as is
+                               the reactor's side wall r = R.  At the port's end Eq. 5 (Mur's
+                               condition) in the form E_r + eta H = 2 E_r^+ with the incoming TEM
+                               wave of Eq. 7's reading, E_r^+ = (V(t) / 2) / (r ln(R / r_p)): half
+                               the electrode potential.  EM model, no capacitor, rings or wave
+                               port; the port's fields through pic_get_view. */
 
 typedef struct pic_ctx pic_ctx; /* opaque; host memory owned by the library */
 
@@ -106,6 +115,11 @@ typedef struct pic_config {
                                  at the half step); a large value models a metal (Sec. 2.1).
                                  Needs ring_cells > 0 and the EM model (an electrostatic run
                                  models a metal by a large eps_ring); 0 = none */
+  int port_cells;             /* PIC_FEED_AXIAL: cells along z of the port (>= 1) */
+  double port_len;            /* PIC_FEED_AXIAL: the port's length [m] */
+  int port_rin;               /* PIC_FEED_AXIAL: the port's inner radius is the node r(port_rin),
+                                 1 <= port_rin < nr (the powered electrode's radius) */
+  double eps_port;            /* PIC_FEED_AXIAL: relative permittivity of the port (>= 1) */
 } pic_config;
 
 /* Per-step statistics (host struct). */
@@ -149,6 +163,13 @@ typedef struct pic_view {
   double *qcond;              /* charge [C] the conducting ring's current moved since pic_init,
                                  per node (nr+1) x (nz+1); Gauss's law holds with it added to
                                  the particle and wall charge (zero without sigma_ring) */
+  /* PIC_FEED_AXIAL (else null / 0): the port's fields at n, m = nr - port_rin columns of
+   * port_cells cells (q = 0 at the port's end): H at port_h[k * port_cells + q] (cell
+   * (port_rin + k, q)), E_r at port_er[k * port_cells + q] (the lower face of that cell: q = 0
+   * the end edge; the top faces are the interface edges, E_r of j = 0 in er), E_z at
+   * port_ez[k * port_cells + q] for nodes k = 0..m (zero on the conductors k = 0 and m) */
+  double *port_h, *port_er, *port_ez;
+  int port_m, port_cells;
 } pic_view;
 
 /* Conservation diagnostics (row a9), host struct filled by pic_diag. */
@@ -264,6 +285,18 @@ int pic_fourier_bessel(pic_ctx *ctx, int alpha, int row, int nmodes, double *coe
 int pic_field_solve(pic_ctx *ctx, const double *er0_dev, const double *ez0_dev,
                     const double *h0_dev, const double *ir_dev, const double *iz_dev, double v0,
                     double v1, double *er1_dev, double *ez1_dev, double *h1_dev, double *src_dev);
+
+/* pic_field_solve with the axial port (PIC_FEED_AXIAL): the port's fields at n
+ * (hp0, erp0, ezp0) and n+1 (hp1, erp1, ezp1) in the layout of pic_view's
+ * port arrays; phi0, phi1: the electrode potential at n and n+1 (the incoming
+ * wave carries half of it).  src_dev (nullable): the energy delivered through
+ * the port's end.  Errors: PIC_E_CONFIG (not an axial-port context), PIC_E_CUDA. */
+int pic_port_field_solve(pic_ctx *ctx, const double *er0_dev, const double *ez0_dev,
+                         const double *h0_dev, const double *hp0_dev, const double *erp0_dev,
+                         const double *ezp0_dev, const double *ir_dev, const double *iz_dev,
+                         double phi0, double phi1, double *er1_dev, double *ez1_dev,
+                         double *h1_dev, double *hp1_dev, double *erp1_dev, double *ezp1_dev,
+                         double *src_dev);
 
 /* Row a7 (Sec. 2.1, null collision after Mertmann et al. 2011): one MCC pass
  * over the context's particles for step index `step`, appending ionization

@@ -132,6 +132,9 @@ def _declare(L):
     L.oracle_step.argtypes = [C.POINTER(Cfg), _P, _U, C.POINTER(Species), _I, _P, _P, _P, _P,
                               _P, _P, C.POINTER(Stats), _P]
     L.oracle_step.restype = _I
+    L.oracle_step_port.argtypes = [C.POINTER(Cfg), _P, _U, C.POINTER(Species), _I] + [_P] * 9 + \
+        [C.POINTER(Stats)]
+    L.oracle_step_port.restype = _I
 
 
 def _p(x):
@@ -390,9 +393,12 @@ class Sim:
     def __init__(self, grid: Grid, dt, *, freq=0.0, volt=0.0, tol=1e-8, kmax=50, bz=0.0,
                  mcc_on=False, ng=0.0, tg=300.0, seed=0, eps=EPS0, mu=MU0, numax=None,
                  gmax=None, cap=None, species=None, charges=(-QE, QE), masses=(ME, M_AR),
-                 cblock=0.0, wave=False):
+                 cblock=0.0, wave=False, port=None):
         """cblock: blocking capacitor [F] in series with the generator (Eq. 6),
-        0 = the electrode follows V(t); its state is self.circ = [q^n, phi^n]."""
+        0 = the electrode follows V(t); its state is self.circ = [q^n, phi^n].
+        port: (ip, nzp, port_len, erq) for the axial dielectric port (the reactor's
+        side wall then a conductor; the electrode follows V(t)); its fields are
+        self.hp, self.erp, self.ezp."""
         self.grid = grid
         self.cfg = Cfg()
         c = self.cfg
@@ -413,7 +419,13 @@ class Sim:
             c.numax_e, c.gmax = nu_e, g_max
             c.pnull_e = -np.expm1(-nu_e * dt)
             c.pnull_i = -np.expm1(-nu_i * dt)
-        self.field = FieldSolver(grid, dt, eps, mu, wave)
+        self.port = None
+        if port is not None:
+            ip, nzp, lp, erq = port
+            self.port = PortSolver(grid, dt, ip, nzp, lp / nzp, erq, eps, mu)
+            self.erp, self.ezp, self.hp = self.port.zeros_port()
+        else:
+            self.field = FieldSolver(grid, dt, eps, mu, wave)
         self.er, self.ez, self.h = grid.zeros_fields()
         self.wall_z0 = np.zeros(2 * (grid.nr + 1))
         self.wall_zl = np.zeros(2 * (grid.nr + 1))
@@ -450,9 +462,16 @@ class Sim:
         st = Stats()
         if self.grid.sgd > 0.0:
             er0, ez0 = self.er.copy(), self.ez.copy()
-        rc = lib().oracle_step(C.byref(self.cfg), self.field._h, self.step_index, T, len(self.sp),
-                               _p(self.er), _p(self.ez), _p(self.h), _p(self.wall_z0),
-                               _p(self.wall_zl), _p(self.wall_r), C.byref(st), _p(self.circ))
+        if self.port is not None:
+            rc = lib().oracle_step_port(C.byref(self.cfg), self.port._h, self.step_index, T,
+                                        len(self.sp), _p(self.er), _p(self.ez), _p(self.h),
+                                        _p(self.hp), _p(self.erp), _p(self.ezp), _p(self.wall_z0),
+                                        _p(self.wall_zl), _p(self.wall_r), C.byref(st))
+        else:
+            rc = lib().oracle_step(C.byref(self.cfg), self.field._h, self.step_index, T,
+                                   len(self.sp), _p(self.er), _p(self.ez), _p(self.h),
+                                   _p(self.wall_z0), _p(self.wall_zl), _p(self.wall_r),
+                                   C.byref(st), _p(self.circ))
         for s, d in enumerate(self.sp):
             d["n"] = T[s].n
             d["next_id"] = T[s].next_id

@@ -1580,11 +1580,36 @@ static double o_circuit(const orc_cfg *cfg, void *field, const double *er, const
   return v1 - (qn + dq) / (cfg->cblock + gu);
 }
 
+/* the axial port's solver and its fields at n (oracle_step_port) */
+typedef struct {
+  void *pf;
+  double *hp, *erp, *ezp;
+} o_port_state;
+
+static int o_step(const orc_cfg *cfg, void *field, o_port_state *ps, uint64_t step,
+                  orc_species *sp, int nspec, double *er, double *ez, double *h, double *wall_z0,
+                  double *wall_zl, double *wall_r, orc_stats *st, double *circ);
+
 /* circ (nullable; used when cfg->cblock > 0): {capacitor charge q^n,
  * electrode potential phi^n} in, the values at n+1 out after a converged step. */
 int oracle_step(const orc_cfg *cfg, void *field, uint64_t step, orc_species *sp, int nspec,
                 double *er, double *ez, double *h, double *wall_z0, double *wall_zl,
                 double *wall_r, orc_stats *st, double *circ) {
+  return o_step(cfg, field, NULL, step, sp, nspec, er, ez, h, wall_z0, wall_zl, wall_r, st, circ);
+}
+
+/* The same step with the axial port (its solver from oracle_port_create; its
+ * fields hp, erp, ezp at n in, at n+1 out); the electrode follows V(t). */
+int oracle_step_port(const orc_cfg *cfg, void *port, uint64_t step, orc_species *sp, int nspec,
+                     double *er, double *ez, double *h, double *hp, double *erp, double *ezp,
+                     double *wall_z0, double *wall_zl, double *wall_r, orc_stats *st) {
+  o_port_state ps = {port, hp, erp, ezp};
+  return o_step(cfg, NULL, &ps, step, sp, nspec, er, ez, h, wall_z0, wall_zl, wall_r, st, NULL);
+}
+
+static int o_step(const orc_cfg *cfg, void *field, o_port_state *ps, uint64_t step,
+                  orc_species *sp, int nspec, double *er, double *ez, double *h, double *wall_z0,
+                  double *wall_zl, double *wall_r, orc_stats *st, double *circ) {
   int nr = cfg->nr, nz = cfg->nz;
   size_t ner = (size_t)nr * (nz + 1), nez = (size_t)(nr + 1) * nz, nh = (size_t)nr * nz;
   double *er1 = (double *)malloc(sizeof(double) * ner), *ez1 = (double *)malloc(sizeof(double) * nez);
@@ -1596,14 +1621,25 @@ int oracle_step(const orc_cfg *cfg, void *field, uint64_t step, orc_species *sp,
   double v0 = cfg->volt * sin(O_TWO_PI * cfg->freq * t0);
   double v1 = cfg->volt * sin(O_TWO_PI * cfg->freq * t1);
   memset(st, 0, sizeof(*st));
-  const int circ_on = cfg->cblock > 0.0 && circ != NULL;
+  const int circ_on = cfg->cblock > 0.0 && circ != NULL && ps == NULL;
+  /* the port's fields of the current iterate */
+  size_t np = 0, nzz = 0;
+  double *hp1 = NULL, *erp1 = NULL, *ezp1 = NULL;
+  if (ps) {
+    const o_pfield *P = (const o_pfield *)ps->pf;
+    np = (size_t)(P->nr - P->ip) * P->nzp;
+    nzz = (size_t)(P->nr - P->ip + 1) * P->nzp;
+    hp1 = (double *)calloc(np, sizeof(double));
+    erp1 = (double *)calloc(np, sizeof(double));
+    ezp1 = (double *)calloc(nzz, sizeof(double));
+  }
   double phi0 = v0, phi1 = v1; /* electrode potential at n and n+1 */
   if (circ_on) phi0 = circ[1];
   /* initial iterate E^{n+1,0} = E^n (unknown edges); without a capacitor or
    * wave port the prescribed gap edges take V^{n+1}, else they keep E^n's */
   memcpy(er1, er, sizeof(double) * ner);
   memcpy(ez1, ez, sizeof(double) * nez);
-  if (!circ_on && !cfg->wave)
+  if (!circ_on && !cfg->wave && !ps)
     for (int j = 0; j < nz; ++j) ez1[nr * nz + j] = v1 / cfg->L;
   int conv = 0;
   double src = 0.0, res = 0.0;
@@ -1618,7 +1654,11 @@ int oracle_step(const orc_cfg *cfg, void *field, uint64_t step, orc_species *sp,
                   sp[s].a, sp[s].b, sp[s].vr, sp[s].vt, sp[s].vz, sp[s].w, erh, ezh, ir, iz, 0,
                   NULL, NULL, NULL, NULL, NULL);
     if (circ_on) phi1 = o_circuit(cfg, field, er, ez, h, ir, iz, phi0, v1, circ[0]);
-    oracle_field_solve(field, er, ez, h, ir, iz, phi0, phi1, cfg->L, ern, ezn, h1, &src);
+    if (ps)
+      oracle_port_solve(ps->pf, er, ez, h, ps->erp, ps->ezp, ps->hp, ir, iz, phi0, phi1, ern, ezn,
+                        h1, erp1, ezp1, hp1, &src);
+    else
+      oracle_field_solve(field, er, ez, h, ir, iz, phi0, phi1, cfg->L, ern, ezn, h1, &src);
     double dn = 0.0, nn = 0.0;
     for (int i = 0; i < nr; ++i)
       for (int j = 1; j < nz; ++j) {
@@ -1658,6 +1698,11 @@ int oracle_step(const orc_cfg *cfg, void *field, uint64_t step, orc_species *sp,
     memcpy(er, er1, sizeof(double) * ner);
     memcpy(ez, ez1, sizeof(double) * nez);
     memcpy(h, h1, sizeof(double) * nh);
+    if (ps) {
+      memcpy(ps->hp, hp1, sizeof(double) * np);
+      memcpy(ps->erp, erp1, sizeof(double) * np);
+      memcpy(ps->ezp, ezp1, sizeof(double) * nzz);
+    }
     st->src_energy = src;
     if (circ_on) {
       circ[0] = cfg->cblock * (v1 - phi1);
@@ -1678,5 +1723,6 @@ int oracle_step(const orc_cfg *cfg, void *field, uint64_t step, orc_species *sp,
     if (st->counters[0] && !rc) rc = -4;
   }
   free(er1); free(ez1); free(ern); free(ezn); free(erh); free(ezh); free(ir); free(iz); free(h1);
+  free(hp1); free(erp1); free(ezp1);
   return rc;
 }

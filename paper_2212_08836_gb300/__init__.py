@@ -30,6 +30,7 @@ PIC_DIAG_ENERGY, PIC_DIAG_GAUSS, PIC_DIAG_CONTINUITY, PIC_DIAG_DENSITY_AVG = 0, 
 PIC_DIAG_ION_FLUX_AVG, PIC_DIAG_FIELDS, PIC_DIAG_COUNTS = 4, 5, 6
 PIC_FEED_GAP = 0
 PIC_FEED_WAVE = 1
+PIC_FEED_AXIAL = 2
 PIC_FP64 = 0
 PIC_MIXED = 1
 
@@ -47,7 +48,8 @@ class Config(C.Structure):
                 ("eps", _D), ("mu", _D), ("seed", C.c_ulonglong), ("precision", _I),
                 ("field_model", _I), ("cblock", _D), ("ions_fixed", _I), ("feed", _I),
                 ("ring_cells", _I), ("eps_ring", _D), ("axis_cells", _I),
-                ("sigma_ring", _D)]
+                ("sigma_ring", _D), ("port_cells", _I), ("port_len", _D), ("port_rin", _I),
+                ("eps_port", _D)]
 
 
 class StepStats(C.Structure):
@@ -79,7 +81,8 @@ class View(C.Structure):
     _fields_ = [("cell", _P * 2), ("a", _P * 2), ("b", _P * 2), ("vr", _P * 2), ("vt", _P * 2),
                 ("vz", _P * 2), ("w", _P * 2), ("id", _P * 2), ("n", _LL * 2), ("cap", _LL * 2),
                 ("next_id", C.c_uint32 * 2), ("er", _P), ("ez", _P), ("h", _P), ("step", _LL),
-                ("real_size", _I), ("wall", _P), ("qcond", _P)]
+                ("real_size", _I), ("wall", _P), ("qcond", _P), ("port_h", _P),
+                ("port_er", _P), ("port_ez", _P), ("port_m", _I), ("port_cells", _I)]
 
 
 class DiagOut(C.Structure):
@@ -117,6 +120,7 @@ def _load_lib():
     L.pic_substep_histogram.argtypes = [_P, _I, _P]
     L.pic_state_upload.argtypes = [_P, C.POINTER(HostState)]
     L.pic_state_download.argtypes = [_P, C.POINTER(HostState)]
+    L.pic_port_field_solve.argtypes = [_P] + [_P] * 8 + [_D, _D] + [_P] * 7
     L.pic_step_host.argtypes = [_P, C.POINTER(HostState), _I, _P]
     L.pic_profile.argtypes = [_P, _I]
     L.pic_profile_read.argtypes = [_P, _P, _P]
@@ -191,7 +195,7 @@ def small_reactor(**kw):
                np_init=40000, capacity_factor=1.5, picard_tol=1e-8, picard_max=50, mcc_on=1,
                bz=0.0, eps=0.0, mu=0.0, seed=0, precision=PIC_FP64, field_model=0, cblock=0.0,
                ions_fixed=0, feed=0, ring_cells=0, eps_ring=1.0, axis_cells=0,
-               sigma_ring=0.0)
+               sigma_ring=0.0, port_cells=0, port_len=0.0, port_rin=0, eps_port=1.0)
     cfg.update(kw)
     return cfg
 
@@ -206,7 +210,7 @@ def large_reactor(**kw):
                np_init=16 * 1024 * 1024, capacity_factor=1.25, picard_tol=1e-8, picard_max=50,
                mcc_on=1, bz=0.0, eps=0.0, mu=0.0, seed=1, precision=PIC_FP64, field_model=0,
                cblock=0.0, ions_fixed=0, feed=0, ring_cells=0, eps_ring=1.0, axis_cells=0,
-               sigma_ring=0.0)
+               sigma_ring=0.0, port_cells=0, port_len=0.0, port_rin=0, eps_port=1.0)
     cfg.update(kw)
     return cfg
 
@@ -279,6 +283,17 @@ class Pic:
                                      er1.data_ptr(), ez1.data_ptr(), h1.data_ptr(),
                                      src.data_ptr() if src is not None else None),
                "pic_field_solve")
+
+    def port_field_solve(self, er0, ez0, h0, hp0, erp0, ezp0, ir, iz, phi0, phi1, er1, ez1, h1,
+                         hp1, erp1, ezp1, src=None):
+        """pic_port_field_solve: the field solve with the axial port's fields
+        (device tensors in pic_view's port layout)."""
+        a = [er0, ez0, h0, hp0, erp0, ezp0, ir, iz]
+        b = [er1, ez1, h1, hp1, erp1, ezp1]
+        _check(lib().pic_port_field_solve(self._h, *[t.data_ptr() for t in a], float(phi0),
+                                          float(phi1), *[t.data_ptr() for t in b],
+                                          src.data_ptr() if src is not None else None),
+               "pic_port_field_solve")
 
     def circuit(self):
         """(q^n, phi^n): blocking-capacitor charge and electrode potential."""
@@ -427,6 +442,11 @@ class Pic:
         out["h"] = self._tensor(v.h, nr * nz, t.float64)
         out["wall"] = self._tensor(v.wall, 2 * (2 * (nr + 1) + nz + 1), t.float64)
         out["qcond"] = self._tensor(v.qcond, (nr + 1) * (nz + 1), t.float64)
+        if v.port_m:
+            m, q = v.port_m, v.port_cells
+            out["port_h"] = self._tensor(v.port_h, m * q, t.float64)
+            out["port_er"] = self._tensor(v.port_er, m * q, t.float64)
+            out["port_ez"] = self._tensor(v.port_ez, (m + 1) * q, t.float64)
         return out
 
     def wall_charge(self):

@@ -84,21 +84,38 @@ enum { kT2ear = 0, kT2eaz = 1, kTear = 2, kTeaz = 3, kTs = 4, kTvh = 5, kTw = 6,
 __device__ __forceinline__ double tab(const FieldOp &F, int k, int i) {
   return F.rtab[k * (F.nr + 1) + i];
 }
+// axial port: D of the interface edge (i + 1/2, 0), half in the port and half in
+// the reactor; of the port's E_r and E_z edges; 2 E^+ on the end edge
+__device__ __forceinline__ double port_dint(const FieldOp &F, int i) {
+  return F.eps * tab(F, kTs, i) * 0.5 * (F.port.erq * F.port.dzp + F.dz);
+}
+__device__ __forceinline__ double port_dr(const FieldOp &F, int i) {
+  return F.eps * F.port.erq * tab(F, kTs, i) * F.port.dzp;
+}
+__device__ __forceinline__ double port_dz(const FieldOp &F, int i) {
+  return F.port.erq / tab(F, kTeaz, i);  // erq eps A_z
+}
+__device__ __forceinline__ double port_ein2(const FieldOp &F, int i, double phi_half) {
+  return phi_half * kTwoPi / (tab(F, kTs, i) * F.port.lnr);
+}
 __device__ __forceinline__ double rhs_at(const FieldOp &F, const double *er0, const double *ez0,
                                         const double *h0, const double *ir, const double *iz,
                                         double v0, double v1, int i, int j) {
   int nr = F.nr, nz = F.nz, nz1 = nz + 1;
   int c = i * nz + j;
+  if (F.unit_c >= 0) return c == F.unit_c ? 1.0 : 0.0;
   double dr = tab(F, kTw, i), dz = F.dz;  // E_r edge length: the cell width
   double s = tab(F, kTs, i);
   double r2 = tab(F, kT2ear, i);
   double etb = 0.0, ett = 0.0;
   double gr = tab(F, kTgr, i);
   if (j != 0) etb = er0[i * nz1 + j] * gr - ir[i * nz1 + j] * r2;
+  else if (F.port.on && i >= F.port.ip)
+    etb = er0[i * nz1] - ir[i * nz1] / (2.0 * port_dint(F, i));  // interface edge
   if (j + 1 != nz) ett = er0[i * nz1 + j + 1] * gr - ir[i * nz1 + j + 1] * r2;
   double etl = ez0[i * nz + j] * tab(F, kTgz, i) - iz[i * nz + j] * tab(F, kT2eaz, i);
   double etr;
-  if (i + 1 == nr) etr = 0.5 * (v0 + v1) / F.L;
+  if (i + 1 == nr) etr = F.port.on ? 0.0 : 0.5 * (v0 + v1) / F.L;  // axial port: a conducting wall
   else etr = ez0[(i + 1) * nz + j] * tab(F, kTgz, i + 1) - iz[(i + 1) * nz + j] * tab(F, kT2eaz, i + 1);
   double curl = (-s) * dr * etb + s * dr * ett + s * dz * etl + (-s) * dz * etr;
   return 2.0 * F.mu * tab(F, kTvh, i) * h0[c] - F.dt * curl;
@@ -409,6 +426,112 @@ __device__ __forceinline__ double hh_at(const FieldOp &F, double dl, int i, int 
   return v;
 }
 
+// ---- axial port (PortOp) ------------------------------------------------------
+// right-hand side of the port cells: 2 mu V_H H^n - dt C^T L Et over their
+// edges (the interface edges' Et with the crossed charge; 2 E^+ on the end
+// edges, whose -eta H part sits in the port block)
+__global__ void k_rhs_port(FieldOp F, const double *er0, const double *ir, double v0, double v1) {
+  if (F.vd) {
+    v0 = F.vd[0];
+    v1 = F.vd[1];
+  }
+  const PortOp &P = F.port;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= P.np) return;
+  const int k = p / P.nzp, q = p - k * P.nzp, i = P.ip + k, nz1 = F.nz + 1;
+  const double s = tab(F, kTs, i), L = tab(F, kTw, i), dzp = P.dzp;
+  const double etb = q == 0 ? port_ein2(F, i, 0.5 * (v0 + v1)) : P.erp0[p];
+  const double ett = q + 1 == P.nzp ? er0[i * nz1] - ir[i * nz1] / (2.0 * port_dint(F, i))
+                                     : P.erp0[p + 1];
+  const double etl = i == P.ip ? 0.0 : P.ezp0[k * P.nzp + q];
+  const double etr = i + 1 == F.nr ? 0.0 : P.ezp0[(k + 1) * P.nzp + q];
+  const double curl = (-s) * L * etb + s * L * ett + s * dzp * etl + (-s) * dzp * etr;
+  const double vh = tab(F, kTvh, i) * dzp / F.dz;
+  P.rhsp[p] = 2.0 * F.mu * vh * P.hp0[p] - F.dt * curl;
+}
+
+// y_P = Binv rhs_P: one warp per row
+__global__ void k_port_solve(FieldOp F) {
+  const PortOp &P = F.port;
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (row >= P.np) return;
+  const double *a = P.Binv + (long long)row * P.np;
+  double v = 0.0;
+  for (int c = lane; c < P.np; c += 32) v += a[c] * P.rhsp[c];
+  v = warp_sum(v);
+  if (lane == 0) P.hhp[row] = v;
+}
+
+// t = U^T y (interface differences), ws = Cinv t: one block
+__global__ void k_port_wood(FieldOp F) {
+  const PortOp &P = F.port;
+  extern __shared__ double t[];
+  for (int e = threadIdx.x; e < P.m; e += blockDim.x)
+    t[e] = hhalf_at(F, P.ip + e, 0) - P.hhp[e * P.nzp + P.nzp - 1];
+  __syncthreads();
+  for (int e = threadIdx.x; e < P.m; e += blockDim.x) {
+    const double *c = P.Cinv + (long long)e * P.m;
+    double v = 0.0;
+    for (int f = 0; f < P.m; ++f) v += c[f] * t[f];
+    P.ws[e] = v;
+  }
+}
+
+// x = y - Z ws: the reactor's hhalf (in its own layout) and the port's H
+__global__ void k_port_fix(FieldOp F, long long nh) {
+  const PortOp &P = F.port;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < nh) {
+    double v = 0.0;
+    for (int e = 0; e < P.m; ++e) v += P.ZR[(long long)e * nh + t] * P.ws[e];
+    F.hhalf[t] -= v;
+  } else if (t < nh + P.np) {
+    const int p = (int)(t - nh);
+    double v = 0.0;
+    for (int e = 0; e < P.m; ++e) v += P.ZP[(long long)e * P.np + p] * P.ws[e];
+    P.hhp[p] -= v;
+  }
+}
+
+// the port's H^{n+1}, E^{n+1} (end edges by Mur's relation) and the energy its
+// end delivers
+__global__ void __launch_bounds__(256) k_update_port(FieldOp F, double v0, double v1,
+                                                     DevCounters *cnt) {
+  if (F.vd) {
+    v0 = F.vd[0];
+    v1 = F.vd[1];
+  }
+  const PortOp &P = F.port;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nzp = P.nzp;
+  double src = 0.0;
+  if (t < P.np) {
+    const int k = t / nzp, q = t - k * nzp, i = P.ip + k;
+    const double s = tab(F, kTs, i), L = tab(F, kTw, i);
+    P.hp1[t] = 2.0 * P.hhp[t] - P.hp0[t];
+    if (q == 0) {
+      const double eh = port_ein2(F, i, 0.5 * (v0 + v1)) - P.eta * P.hhp[t];
+      P.erp1[t] = 2.0 * eh - P.erp0[t];
+      src = eh * L * F.dt * s * P.hhp[t];
+    } else {
+      const double ch = -s * P.hhp[t] + s * P.hhp[t - 1];
+      P.erp1[t] = P.erp0[t] + F.dt * ch / port_dr(F, i);
+    }
+  }
+  const int nez = (P.m + 1) * nzp;
+  if (t < nez) {
+    const int k = t / nzp, q = t - k * nzp, i = P.ip + k;
+    if (i == P.ip || i == F.nr) {
+      P.ezp1[t] = 0.0;
+    } else {
+      const double ch = tab(F, kTs, i) * P.hhp[k * nzp + q] - tab(F, kTs, i - 1) * P.hhp[(k - 1) * nzp + q];
+      P.ezp1[t] = P.ezp0[t] + F.dt * ch / port_dz(F, i);
+    }
+  }
+  src = warp_sum(src);
+  if ((threadIdx.x & 31) == 0 && src != 0.0) atomicAdd(&cnt->src, src);
+}
+
 // H1 = 2 H_half - H0; E1 from Ampere; Picard norms and drive-gap energy.
 // With the blocking capacitor, Eq. 6 fixes the electrode potential first:
 // Ampere's law summed over the first row of E_z edges (i < nr) telescopes, so
@@ -448,7 +571,13 @@ __global__ void __launch_bounds__(256) k_update(FieldOp F, const double *er0, co
   }
   if (t < ner) {
     int i = (int)(t / nz1), j = (int)(t - (t / nz1) * nz1);
-    if (j == 0 || j == nz) {
+    if (j == 0 && F.port.on && i >= F.port.ip) {
+      // interface edge: the port's top cell below, the reactor's first cell above
+      const double s = tab(F, kTs, i);
+      const double ch = -s * hh_at(F, dl, i, 0) +
+                        s * F.port.hhp[(i - F.port.ip) * F.port.nzp + F.port.nzp - 1];
+      er1[t] = er0[t] + (dt * ch - ir[t]) / port_dint(F, i);
+    } else if (j == 0 || j == nz) {
       er1[t] = 0.0;
     } else {
       double s = tab(F, kTs, i);
@@ -468,7 +597,9 @@ __global__ void __launch_bounds__(256) k_update(FieldOp F, const double *er0, co
     double ch = 0.0;
     if (i <= nr - 1) ch += tab(F, kTs, i) * hh_at(F, dl, i, j);
     if (i >= 1) ch += -tab(F, kTs, i - 1) * hh_at(F, dl, i - 1, j);
-    if (i == nr) {
+    if (i == nr && F.port.on) {
+      ez1[t] = 0.0;  // the reactor's side wall: a conductor
+    } else if (i == nr) {
       double eh;
       if (F.wave) {  // wave port: the boundary field follows H at the outermost node
         eh = 0.5 * (v0 + v1) / F.L - F.eta * hh_at(F, dl, nr - 1, j);
@@ -709,14 +840,9 @@ cudaError_t launch_half_field_alpha64(const Grid &g, const double *er0, const do
   return cudaGetLastError();
 }
 
-cudaError_t launch_field_solve(const FieldOp &F, const double *er0, const double *ez0,
-                               const double *h0, const double *ir, const double *iz, double v0,
-                               double v1, double *er1, double *ez1, double *h1, const double *er_it,
-                               const double *ez_it, DevCounters *cnt, cudaStream_t s) {
-  cudaError_t e;
-  int nc = F.nr * F.nz;
-  if ((e = cudaMemsetAsync(&cnt->norm[0], 0, 3 * sizeof(double), s)) != cudaSuccess) return e;
-  k_rhs<<<(nc + 255) / 256, 256, 0, s>>>(F, er0, ez0, h0, ir, iz, v0, v1);
+// the reactor's separable solve of F.rhs into F.hhalf (DCT along z, cyclic
+// reduction per mode, inverse DCT)
+void solve_core(const FieldOp &F, cudaStream_t s) {
   dim3 grid((F.nz + TM - 1) / TM, (F.nr + TM - 1) / TM);
   int h = F.half;
   Gemm G;
@@ -762,10 +888,46 @@ cudaError_t launch_field_solve(const FieldOp &F, const double *er0, const double
   } else {
     k_gemm<<<grid, 256, 0, s>>>(F.nr, F.nz, F.nz, F.hat, F.QT, F.hhalf);
   }
+}
+
+cudaError_t launch_field_solve(const FieldOp &F, const double *er0, const double *ez0,
+                               const double *h0, const double *ir, const double *iz, double v0,
+                               double v1, double *er1, double *ez1, double *h1, const double *er_it,
+                               const double *ez_it, DevCounters *cnt, cudaStream_t s) {
+  cudaError_t e;
+  int nc = F.nr * F.nz;
+  if ((e = cudaMemsetAsync(&cnt->norm[0], 0, 3 * sizeof(double), s)) != cudaSuccess) return e;
+  k_rhs<<<(nc + 255) / 256, 256, 0, s>>>(F, er0, ez0, h0, ir, iz, v0, v1);
+  const PortOp &P = F.port;
+  if (P.on) k_rhs_port<<<(P.np + 255) / 256, 256, 0, s>>>(F, er0, ir, v0, v1);
+  solve_core(F, s);
+  if (P.on) {
+    // the port block, then the interface coupling (Woodbury)
+    k_port_solve<<<(unsigned)(((long long)P.np * 32 + 255) / 256), 256, 0, s>>>(F);
+    k_port_wood<<<1, 256, (size_t)P.m * sizeof(double), s>>>(F);
+    const long long nh = (long long)F.nr * F.nz;
+    k_port_fix<<<(unsigned)((nh + P.np + 255) / 256), 256, 0, s>>>(F, nh);
+  }
   long long ner = (long long)F.nr * (F.nz + 1), nez = (long long)(F.nr + 1) * F.nz;
   long long n = ner > nez ? ner : nez;
   k_update<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(F, er0, ez0, h0, ir, iz, v0, v1, er1, ez1,
                                                        h1, er_it, ez_it, cnt);
+  if (P.on) {
+    const int np2 = P.np > (P.m + 1) * P.nzp ? P.np : (P.m + 1) * P.nzp;
+    k_update_port<<<(np2 + 255) / 256, 256, 0, s>>>(F, v0, v1, cnt);
+  }
+  return cudaGetLastError();
+}
+
+// the reactor's separable solve of the unit right-hand side of H cell c into
+// F.hhalf (the axial port's set-up: columns of B_R^{-1} U)
+cudaError_t launch_unit_solve(const FieldOp &Fin, int c, cudaStream_t s) {
+  FieldOp F = Fin;
+  F.unit_c = c;
+  F.port.on = 0;
+  const int nc = F.nr * F.nz;
+  k_rhs<<<(nc + 255) / 256, 256, 0, s>>>(F, nullptr, nullptr, nullptr, nullptr, nullptr, 0.0, 0.0);
+  solve_core(F, s);
   return cudaGetLastError();
 }
 

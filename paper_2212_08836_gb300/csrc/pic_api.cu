@@ -61,6 +61,9 @@ struct pic_ctx {
   double *q_real64_2[2];
   int *q_cell2;
   float *q_st2[6];
+  // axial port (PIC_FEED_AXIAL): its fields at n and n+1 (the solve's output,
+  // copied in when a step commits)
+  double *hp, *erp, *ezp, *hp2, *erp2, *ezp2;
   // pic_step_host: copy streams (device -> host, host -> device) and their events
   cudaStream_t hs_dn, hs_up;
   cudaEvent_t hs_ev[130];
@@ -252,7 +255,14 @@ bool valid(const pic_config *c) {
   if (!(c->cblock >= 0.0) || !isfinite(c->cblock)) return false;
   if (c->ions_fixed != 0 && c->ions_fixed != 1) return false;
   if (c->axis_cells < 0 || c->axis_cells > kMaxAxisCells || c->axis_cells >= c->nr) return false;
-  if (c->feed != PIC_FEED_GAP && c->feed != PIC_FEED_WAVE) return false;
+  if (c->feed != PIC_FEED_GAP && c->feed != PIC_FEED_WAVE && c->feed != PIC_FEED_AXIAL) return false;
+  if (c->feed == PIC_FEED_AXIAL &&
+      (c->field_model != PIC_FIELD_EM || c->cblock > 0.0 || c->ring_cells != 0 ||
+       c->sigma_ring != 0.0 || c->port_cells < 1 || !(c->port_len > 0.0) ||
+       !isfinite(c->port_len) || c->port_rin < 1 || c->port_rin >= c->nr ||
+       !(c->eps_port >= 1.0) || !isfinite(c->eps_port) ||
+       c->nr - c->port_rin > 4096 || (long long)(c->nr - c->port_rin) * c->port_cells > 8192))
+    return false;
   if (c->ring_cells < 0 || (c->ring_cells > 0 && (!(c->eps_ring >= 1.0) || !isfinite(c->eps_ring) ||
                                                   c->ring_cells + c->axis_cells > c->nr - 2)))
     return false;
@@ -344,6 +354,23 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
   x->F.rhs = (double *)K.take(nh * 8);
   x->F.hat = (double *)K.take(nh * 8);
   x->F.hhalf = (double *)K.take(nh * 8);
+  if (c->feed == PIC_FEED_AXIAL) {
+    PortOp &P = x->F.port;
+    const int m = nr - c->port_rin, nzp = c->port_cells, np = m * nzp, nzz = (m + 1) * nzp;
+    P.Binv = (const double *)K.take((size_t)np * np * 8);
+    P.ZR = (const double *)K.take((size_t)m * nh * 8);
+    P.ZP = (const double *)K.take((size_t)m * np * 8);
+    P.Cinv = (const double *)K.take((size_t)m * m * 8);
+    P.rhsp = (double *)K.take((size_t)np * 8);
+    P.hhp = (double *)K.take((size_t)np * 8);
+    P.ws = (double *)K.take((size_t)m * 8);
+    x->hp = (double *)K.take((size_t)np * 8);
+    x->erp = (double *)K.take((size_t)np * 8);
+    x->ezp = (double *)K.take((size_t)nzz * 8);
+    x->hp2 = (double *)K.take((size_t)np * 8);
+    x->erp2 = (double *)K.take((size_t)np * 8);
+    x->ezp2 = (double *)K.take((size_t)nzz * 8);
+  }
   {
     const int M = nz - 1, n2e = x->F.n2;
     x->es.nr = nr;
@@ -793,6 +820,169 @@ int pic_workspace_size(const pic_config *cfg, size_t *bytes) {
   return PIC_OK;
 }
 
+namespace {
+// Axial port set-up (PIC_FEED_AXIAL; FieldOp's PortOp): the port block's
+// inverse (banded Cholesky, one solve per column), the reactor part of
+// B^{-1} U (one separable solve per interface edge), the port part, and the
+// interface (capacitance) matrix W^{-1} + U^T Z, inverted.  Synchronises.
+int port_setup(pic_ctx *x, const pic_config *cfg) {
+  FieldOp &F = x->F;
+  PortOp &P = F.port;
+  const Grid &G = x->g;
+  const int nr = G.nr, nz = G.nz, ip = cfg->port_rin, nzp = cfg->port_cells, m = nr - ip;
+  const int np = m * nzp;
+  const size_t nh = (size_t)nr * nz;
+  P.on = 1;
+  P.ip = ip;
+  P.nzp = nzp;
+  P.m = m;
+  P.np = np;
+  P.dzp = cfg->port_len / nzp;
+  P.erq = cfg->eps_port;
+  P.eta = sqrt(x->mu / (cfg->eps_port * x->eps));
+  P.lnr = log(g_rnode(G, nr) / g_rnode(G, ip));
+  P.hp0 = x->hp;
+  P.erp0 = x->erp;
+  P.ezp0 = x->ezp;
+  P.hp1 = x->hp2;
+  P.erp1 = x->erp2;
+  P.ezp1 = x->ezp2;
+  const double dt = cfg->dt, hdt2 = 0.5 * dt * dt, eps = x->eps, mu = x->mu;
+  const double dzp = P.dzp, erq = P.erq;
+  // the port block (mass, the E_r edges between its rows, its interior E_z
+  // edges, Mur's term at the end), lower band of width nzp
+  const int bw = nzp;
+  std::vector<double> Lb((size_t)np * (bw + 1), 0.0);
+  auto band = [&](int a, int b) -> double & { return Lb[(size_t)a * (bw + 1) + (b - a + bw)]; };
+  for (int k = 0; k < m; ++k) {
+    const int i = ip + k;
+    const double sv = kTwoPi * g_rcentre(G, i), L = g_width(G, i);
+    for (int q = 0; q < nzp; ++q) band(k * nzp + q, k * nzp + q) += 2.0 * mu * sv * L * dzp;
+    for (int q = 1; q < nzp; ++q) {
+      const double w = hdt2 * (L / (eps * erq * sv * dzp)) * sv * sv;
+      const int lo = k * nzp + q - 1, hi = k * nzp + q;
+      band(lo, lo) += w;
+      band(hi, hi) += w;
+      band(hi, lo) -= w;
+    }
+    band(k * nzp, k * nzp) += dt * sv * L * P.eta;
+  }
+  for (int k = 1; k < m; ++k) {
+    const int i = ip + k;
+    const double sr = kTwoPi * g_rcentre(G, i), sl = kTwoPi * g_rcentre(G, i - 1);
+    const double W = dzp / (eps * erq * g_area_z(G, i));
+    for (int q = 0; q < nzp; ++q) {
+      const int cr = k * nzp + q, cl = (k - 1) * nzp + q;
+      band(cr, cr) += hdt2 * W * sr * sr;
+      band(cl, cl) += hdt2 * W * sl * sl;
+      band(cr, cl) -= hdt2 * W * sl * sr;
+    }
+  }
+  for (int a = 0; a < np; ++a) {
+    const int j0 = a - bw < 0 ? 0 : a - bw;
+    for (int b = j0; b <= a; ++b) {
+      double sum = band(a, b);
+      const int k0 = j0 > b - bw ? j0 : b - bw;
+      for (int k = k0; k < b; ++k) sum -= band(a, k) * band(b, k);
+      if (a == b) {
+        if (!(sum > 0.0)) return PIC_E_CONFIG;
+        band(a, a) = sqrt(sum);
+      } else {
+        band(a, b) = sum / band(b, b);
+      }
+    }
+  }
+  std::vector<double> Binv((size_t)np * np), col(np);
+  for (int c = 0; c < np; ++c) {
+    std::fill(col.begin(), col.end(), 0.0);
+    col[c] = 1.0;
+    for (int a = 0; a < np; ++a) {
+      double sum = col[a];
+      for (int k = a - bw < 0 ? 0 : a - bw; k < a; ++k) sum -= band(a, k) * col[k];
+      col[a] = sum / band(a, a);
+    }
+    for (int a = np - 1; a >= 0; --a) {
+      double sum = col[a];
+      const int k1 = a + bw > np - 1 ? np - 1 : a + bw;
+      for (int k = a + 1; k <= k1; ++k) sum -= band(k, a) * col[k];
+      col[a] = sum / band(a, a);
+    }
+    for (int a = 0; a < np; ++a) Binv[(size_t)a * np + c] = col[a];
+  }
+  // reactor part of Z: B_R^{-1} e(ip + e, 0), one separable solve each
+  cudaError_t ce = cudaSuccess;
+  for (int e = 0; e < m && ce == cudaSuccess; ++e) {
+    ce = launch_unit_solve(F, (ip + e) * nz, x->s);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync((void *)(P.ZR + (size_t)e * nh), F.hhalf, nh * 8,
+                           cudaMemcpyDeviceToDevice, x->s);
+  }
+  std::vector<double> zr((size_t)m * nh);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(zr.data(), P.ZR, zr.size() * 8, cudaMemcpyDeviceToHost, x->s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(x->s);
+  if (ce != cudaSuccess) return PIC_E_CUDA;
+  // H(i, 0) of a solve in the layout of FieldOp::hhalf
+  auto h0of = [&](const double *a, int i) {
+    if (!F.half) return a[(size_t)i * nz];
+    const int h = F.half;
+    return a[(size_t)i * h] + a[(size_t)nr * h + (size_t)i * h];
+  };
+  std::vector<double> zp((size_t)m * np), cap((size_t)m * m);
+  for (int f = 0; f < m; ++f)
+    for (int p = 0; p < np; ++p) zp[(size_t)f * np + p] = -Binv[(size_t)p * np + f * nzp + nzp - 1];
+  for (int e = 0; e < m; ++e) {
+    const int i = ip + e;
+    const double sv = kTwoPi * g_rcentre(G, i), L = g_width(G, i);
+    const double dint = eps * sv * 0.5 * (erq * dzp + G.dz);
+    const double w = hdt2 * (L / dint) * sv * sv;
+    for (int f = 0; f < m; ++f)
+      cap[(size_t)e * m + f] = (e == f ? 1.0 / w : 0.0) + h0of(zr.data() + (size_t)f * nh, i) +
+                               Binv[(size_t)(e * nzp + nzp - 1) * np + f * nzp + nzp - 1];
+  }
+  // symmetric positive definite: Cholesky, then the inverse column by column
+  for (int a = 0; a < m; ++a)
+    for (int b = 0; b <= a; ++b) {
+      double sum = cap[(size_t)a * m + b];
+      for (int k = 0; k < b; ++k) sum -= cap[(size_t)a * m + k] * cap[(size_t)b * m + k];
+      if (a == b) {
+        if (!(sum > 0.0)) return PIC_E_CONFIG;
+        cap[(size_t)a * m + a] = sqrt(sum);
+      } else {
+        cap[(size_t)a * m + b] = sum / cap[(size_t)b * m + b];
+      }
+    }
+  std::vector<double> cinv((size_t)m * m), v(m);
+  for (int c = 0; c < m; ++c) {
+    std::fill(v.begin(), v.end(), 0.0);
+    v[c] = 1.0;
+    for (int a = 0; a < m; ++a) {
+      double sum = v[a];
+      for (int k = 0; k < a; ++k) sum -= cap[(size_t)a * m + k] * v[k];
+      v[a] = sum / cap[(size_t)a * m + a];
+    }
+    for (int a = m - 1; a >= 0; --a) {
+      double sum = v[a];
+      for (int k = a + 1; k < m; ++k) sum -= cap[(size_t)k * m + a] * v[k];
+      v[a] = sum / cap[(size_t)a * m + a];
+    }
+    for (int a = 0; a < m; ++a) cinv[(size_t)a * m + c] = v[a];
+  }
+  const size_t nzz = (size_t)(m + 1) * nzp;
+  ce = cudaMemcpyAsync((void *)P.Binv, Binv.data(), Binv.size() * 8, cudaMemcpyHostToDevice, x->s);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync((void *)P.ZP, zp.data(), zp.size() * 8, cudaMemcpyHostToDevice, x->s);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync((void *)P.Cinv, cinv.data(), cinv.size() * 8, cudaMemcpyHostToDevice, x->s);
+  for (double *a : {x->hp, x->erp, x->hp2, x->erp2})
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(a, 0, (size_t)np * 8, x->s);
+  for (double *a : {x->ezp, x->ezp2})
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(a, 0, nzz * 8, x->s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(x->s);
+  return ce == cudaSuccess ? PIC_OK : PIC_E_CUDA;
+}
+}  // namespace
+
 int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes, void *stream,
              pic_ctx **out) {
   if (!out) return PIC_E_CONFIG;
@@ -864,6 +1054,7 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
   F.eps = x->eps;
   F.mu = x->mu;
   F.L = cfg->L;
+  F.unit_c = -1;
   double dz = F.dz, hdt2 = 0.5 * cfg->dt * cfg->dt;
   std::vector<double> Q((size_t)nz * nz), QT((size_t)nz * nz), lam(nz);
   // FFT path when nz = 4^a 2^b 3^c is even (at most 4096); else the GEMM path
@@ -1089,6 +1280,13 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
   x->es.vd = x->vdev;
   x->hist_n = 1;
   x->fb_alpha = -1;
+  if (cfg->feed == PIC_FEED_AXIAL) {
+    const int pr = port_setup(x, cfg);
+    if (pr) {
+      pic_destroy(x);
+      return pr;
+    }
+  }
   if (cfg->cblock > 0.0) {
     // unit response: H^{n+1} of a unit electrode potential at n+1 with no
     // fields at n and no charge (fields, H and the crossed charge are zero here)
@@ -1390,6 +1588,32 @@ int pic_field_solve(pic_ctx *x, const double *er0, const double *ez0, const doub
   return cuda_rc(e);
 }
 
+int pic_port_field_solve(pic_ctx *x, const double *er0, const double *ez0, const double *h0,
+                         const double *hp0, const double *erp0, const double *ezp0,
+                         const double *ir, const double *iz, double phi0, double phi1,
+                         double *er1, double *ez1, double *h1, double *hp1, double *erp1,
+                         double *ezp1, double *src) {
+  if (!x || !x->F.port.on) return PIC_E_CONFIG;
+  if (!er0 || !ez0 || !h0 || !hp0 || !erp0 || !ezp0 || !ir || !iz || !er1 || !ez1 || !h1 ||
+      !hp1 || !erp1 || !ezp1)
+    return PIC_E_CONFIG;
+  FieldOp F = x->F;
+  F.vd = nullptr;  // the caller's potentials
+  F.cc = Circuit{};
+  F.port.hp0 = hp0;
+  F.port.erp0 = erp0;
+  F.port.ezp0 = ezp0;
+  F.port.hp1 = hp1;
+  F.port.erp1 = erp1;
+  F.port.ezp1 = ezp1;
+  cudaError_t e = launch_field_solve(F, er0, ez0, h0, ir, iz, phi0, phi1, er1, ez1, h1, nullptr,
+                                     nullptr, x->cnt, x->s);
+  x->launches += 10;
+  if (e == cudaSuccess && src)
+    e = cudaMemcpyAsync(src, &x->cnt->src, 8, cudaMemcpyDeviceToDevice, x->s);
+  return cuda_rc(e);
+}
+
 int pic_es_solve(pic_ctx *x, const double *Q, double phi0, double *er, double *ez) {
   if (!x || !Q || !er || !ez) return PIC_E_CONFIG;
   EsOp E = x->es;
@@ -1525,7 +1749,7 @@ int plain_start(pic_ctx *x, double v1) {
   cudaError_t e = cudaMemcpyAsync(x->er1, x->er, ner * 8, cudaMemcpyDeviceToDevice, x->s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(x->ez1, x->ez, nez * 8, cudaMemcpyDeviceToDevice, x->s);
   // with the blocking capacitor or the wave port the gap edges keep E^n's
-  if (e == cudaSuccess && !x->circ_on && !x->F.wave) {
+  if (e == cudaSuccess && !x->circ_on && !x->F.wave && !x->F.port.on) {
     k_fill<<<(nz + 127) / 128, 128, 0, x->s>>>(x->ez1 + (size_t)nr * nz, nz, v1 / x->cfg.L);
     e = cudaGetLastError();
     x->launches += 1;
@@ -1557,7 +1781,7 @@ int guess_start(pic_ctx *x, double v1, int *used) {
   if (launch_guess_apply(A, y, cp, v1 / x->cfg.L, x->er1, x->ez1, x->gbad, x->s) != cudaSuccess)
     return PIC_E_CUDA;
   x->launches += 1;
-  if (x->circ_on || x->F.wave) {
+  if (x->circ_on || x->F.wave || x->F.port.on) {
     // the gap edges keep E^n's, as in the plain start
     const size_t g0 = (size_t)x->g.nr * x->g.nz;
     if (cudaMemcpyAsync(x->ez1 + g0, x->ez + g0, (size_t)x->g.nz * 8, cudaMemcpyDeviceToDevice,
@@ -1901,6 +2125,15 @@ int step_end(pic_ctx *x, StepState &T, int *rc) {
   t = x->er; x->er = x->er1; x->er1 = t;
   t = x->ez; x->ez = x->ez1; x->ez1 = t;
   t = x->h; x->h = x->h2; x->h2 = t;
+  if (x->F.port.on) {
+    // the port's fields of the last solve (fixed buffers: the captured passes stay valid)
+    const PortOp &P = x->F.port;
+    const size_t nzz = (size_t)(P.m + 1) * P.nzp;
+    if (cudaMemcpyAsync(x->hp, x->hp2, (size_t)P.np * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(x->erp, x->erp2, (size_t)P.np * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(x->ezp, x->ezp2, nzz * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return PIC_E_CUDA;
+  }
   if (x->guess_mode != PIC_GUESS_PLAIN) {
     // training target of this step, then E^n joins the history (its buffer
     // is now er1/ez1) and the committed crossed charge is kept
@@ -2192,6 +2425,16 @@ int pic_get_view(pic_ctx *x, pic_view *v) {
   v->real_size = x->mixed ? 4 : 8;
   v->wall = x->wall;
   v->qcond = x->qc;
+  if (x->F.port.on) {
+    v->port_h = x->hp;
+    v->port_er = x->erp;
+    v->port_ez = x->ezp;
+    v->port_m = x->F.port.m;
+    v->port_cells = x->F.port.nzp;
+  } else {
+    v->port_h = v->port_er = v->port_ez = nullptr;
+    v->port_m = v->port_cells = 0;
+  }
   return PIC_OK;
 }
 
@@ -2206,6 +2449,7 @@ struct CkptHeader {
   double circ[4], rho_prev;
   double hamp[64], hfreq[64], hph[64];
   int32_t ring_cells, conducting;  // the ring's extent and whether it carries a conduction tally
+  int32_t port_m, port_cells;      // the axial port's extent (0, 0: none)
 };
 const char kCkptMagic[8] = {'P', 'I', 'C', 'C', 'K', 'P', 'T', '1'};
 
@@ -2230,6 +2474,12 @@ int ckpt_arrays(pic_ctx *x, const long long n[2], F &&f) {
     if (int r = f(x->qn, (size_t)(nr + 1) * (nz + 1) * 8)) return r;
   if (x->g.sgd > 0.0)
     if (int r = f(x->qc, (size_t)(nr + 1) * (nz + 1) * 8)) return r;
+  if (x->F.port.on) {
+    const PortOp &P = x->F.port;
+    if (int r = f(x->hp, (size_t)P.np * 8)) return r;
+    if (int r = f(x->erp, (size_t)P.np * 8)) return r;
+    if (int r = f(x->ezp, (size_t)(P.m + 1) * P.nzp * 8)) return r;
+  }
   return PIC_OK;
 }
 
@@ -2240,7 +2490,9 @@ int pic_save(pic_ctx *x, const char *path) {
   CkptHeader H;
   memset(&H, 0, sizeof(H));
   memcpy(H.magic, kCkptMagic, 8);
-  H.version = 2;
+  H.version = 3;
+  H.port_m = x->F.port.on ? x->F.port.m : 0;
+  H.port_cells = x->F.port.on ? x->F.port.nzp : 0;
   H.nr = x->g.nr;
   H.nz = x->g.nz;
   H.precision = x->cfg.precision;
@@ -2288,12 +2540,14 @@ int pic_load(pic_ctx *x, const char *path) {
   if (!fp) return PIC_E_IO;
   CkptHeader H;
   int rc = fread(&H, sizeof(H), 1, fp) == 1 ? PIC_OK : PIC_E_IO;
-  if (!rc && (memcmp(H.magic, kCkptMagic, 8) != 0 || H.version != 2 || H.nharm < 0 ||
+  if (!rc && (memcmp(H.magic, kCkptMagic, 8) != 0 || H.version != 3 || H.nharm < 0 ||
               H.nharm > 64))
     rc = PIC_E_IO;
   if (!rc && (H.nr != x->g.nr || H.nz != x->g.nz || H.precision != x->cfg.precision ||
               H.field_model != x->cfg.field_model || H.xa != x->g.xa ||
               H.ring_cells != x->g.nd || H.conducting != (x->g.sgd > 0.0 ? 1 : 0) ||
+              H.port_m != (x->F.port.on ? x->F.port.m : 0) ||
+              H.port_cells != (x->F.port.on ? x->F.port.nzp : 0) ||
               H.real_size != (x->mixed ? 4 : 8) || H.n[0] < 0 || H.n[1] < 0 ||
               H.n[0] > x->cap[0] || H.n[1] > x->cap[1] || H.step < 0 ||
               (H.circ_on != 0) != (x->circ_on != 0)))

@@ -162,6 +162,28 @@ struct Circuit {
   double cr;         // ES: eps sum_{i<nr} A_z(i) / L, the vacuum response of the plate flow
 };
 
+// Axial dielectric port below the powered electrode (PIC_FEED_AXIAL): m = nr -
+// ip columns of nzp cells of height dzp, relative permittivity erq, Mur's
+// condition at the end with the incoming wave of half the electrode potential.
+// The H system of reactor and port is B + U W U^T: B = the reactor's separable
+// operator and the port block (its dense inverse Binv), U W U^T the m interface
+// edges on z = 0 joining reactor cell (ip + e, 0) and port cell (e, nzp - 1).
+// Solved exactly (Woodbury): x = y - Z Cinv U^T y, y = B^{-1} b, Z = B^{-1} U
+// (ZR: its reactor part in the layout of FieldOp::hhalf, ZP: its port part),
+// Cinv = (W^{-1} + U^T Z)^{-1}.
+struct PortOp {
+  int on, ip, nzp, m, np;
+  double dzp, erq, eta, lnr;
+  const double *Binv;  // np x np, row-major
+  const double *ZR;    // m blocks of the reactor hhalf layout
+  const double *ZP;    // m x np
+  const double *Cinv;  // m x m
+  double *rhsp, *hhp;  // port right-hand side and H^{n+1/2} (np each)
+  double *ws;          // m: Cinv U^T y
+  const double *hp0, *erp0, *ezp0;  // port fields at n: H, E_r (end edge first), E_z
+  double *hp1, *erp1, *ezp1;        // at n+1
+};
+
 struct FieldOp {
   int nr, nz;
   int half;            // nz/2 when nz is even: even/odd split of the DCT (else 0)
@@ -195,6 +217,10 @@ struct FieldOp {
   // wave port on r = R: E_z^{n+1/2}(R) = 2 E_in^{n+1/2} - eta H^{n+1/2}(nr-1/2)
   int wave;
   double eta;
+  // unit right-hand side (>= 0: the solve's rhs is the unit vector of this H
+  // cell, for the set-up of the axial port's coupling; else -1)
+  int unit_c;
+  PortOp port;
 };
 
 // Radial scales of a cell in the push's normalised units: lengths in units of
@@ -346,6 +372,9 @@ int push_wave_fp64(int general);
 int push_wave_fp32(int general);
 
 // launchers (return cudaError_t of the launch)
+// the reactor's separable solve of the unit right-hand side of H cell c into
+// F.hhalf (set-up of the axial port's coupling)
+cudaError_t launch_unit_solve(const FieldOp &F, int c, cudaStream_t s);
 cudaError_t launch_field_solve(const FieldOp &F, const double *er0, const double *ez0,
                                const double *h0, const double *ir, const double *iz, double v0,
                                double v1, double *er1, double *ez1, double *h1, const double *er_it,
