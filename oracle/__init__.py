@@ -133,7 +133,7 @@ def _declare(L):
                               _P, _P, C.POINTER(Stats), _P]
     L.oracle_step.restype = _I
     L.oracle_step_port.argtypes = [C.POINTER(Cfg), _P, _U, C.POINTER(Species), _I] + [_P] * 9 + \
-        [C.POINTER(Stats)]
+        [C.POINTER(Stats), _P]
     L.oracle_step_port.restype = _I
 
 
@@ -397,8 +397,8 @@ class Sim:
         """cblock: blocking capacitor [F] in series with the generator (Eq. 6),
         0 = the electrode follows V(t); its state is self.circ = [q^n, phi^n].
         port: (ip, nzp, port_len, erq) for the axial dielectric port (the reactor's
-        side wall then a conductor; the electrode follows V(t)); its fields are
-        self.hp, self.erp, self.ezp."""
+        side wall then a conductor; the electrode at V(t) or, with cblock, Eq. 6's
+        circuit); its fields are self.hp, self.erp, self.ezp."""
         self.grid = grid
         self.cfg = Cfg()
         c = self.cfg
@@ -466,7 +466,8 @@ class Sim:
             rc = lib().oracle_step_port(C.byref(self.cfg), self.port._h, self.step_index, T,
                                         len(self.sp), _p(self.er), _p(self.ez), _p(self.h),
                                         _p(self.hp), _p(self.erp), _p(self.ezp), _p(self.wall_z0),
-                                        _p(self.wall_zl), _p(self.wall_r), C.byref(st))
+                                        _p(self.wall_zl), _p(self.wall_r), C.byref(st),
+                                        _p(self.circ))
         else:
             rc = lib().oracle_step(C.byref(self.cfg), self.field._h, self.step_index, T,
                                    len(self.sp), _p(self.er), _p(self.ez), _p(self.h),

@@ -1586,6 +1586,45 @@ typedef struct {
   double *hp, *erp, *ezp;
 } o_port_state;
 
+/* Eq. 6 with the axial port: the reactor-side current is that through the
+ * dual faces of the first row of E_z edges over the powered electrode
+ * (i < ip, j = 1/2); the solve is affine in phi^{n+1} through Eq. 7's incoming
+ * wave, so a solve at phi = V^{n+1} and the response to a unit potential give
+ * phi^{n+1} as in o_circuit. */
+static double o_circuit_port(const orc_cfg *cfg, o_port_state *ps, const double *er,
+                             const double *ez, const double *h, const double *ir,
+                             const double *iz, double phi_n, double v1, double qn) {
+  const o_pfield *P = (const o_pfield *)ps->pf;
+  const int nr = cfg->nr, nz = cfg->nz;
+  const size_t ner = (size_t)nr * (nz + 1), nez = (size_t)(nr + 1) * nz, nh = (size_t)nr * nz;
+  const size_t np = (size_t)(P->nr - P->ip) * P->nzp, nzz = (size_t)(P->nr - P->ip + 1) * P->nzp;
+  og_grid g = {nr, nz, cfg->dr, cfg->dz, cfg->xa, 0, 1.0, 0.0};
+  double *a[6], *u[6], *z[8];
+  const size_t sz[6] = {ner, nez, nh, np, nzz, np};
+  for (int k = 0; k < 6; ++k) {
+    a[k] = (double *)malloc(sizeof(double) * sz[k]);
+    u[k] = (double *)malloc(sizeof(double) * sz[k]);
+    z[k] = (double *)calloc(sz[k], sizeof(double));
+  }
+  z[6] = (double *)calloc(ner, sizeof(double));
+  z[7] = (double *)calloc(nez, sizeof(double));
+  double src;
+  /* outputs in oracle_port_solve order: er, ez, h, erp, ezp, hp */
+  oracle_port_solve(ps->pf, er, ez, h, ps->erp, ps->ezp, ps->hp, ir, iz, phi_n, v1, a[0], a[1],
+                    a[2], a[3], a[4], a[5], &src);
+  oracle_port_solve(ps->pf, z[0], z[1], z[2], z[3], z[4], z[5], z[6], z[7], 0.0, 1.0, u[0], u[1],
+                    u[2], u[3], u[4], u[5], &src);
+  double dq = 0.0, gu = 0.0;
+  for (int i = 0; i < P->ip; ++i) {
+    const double ea = cfg->eps * o_area_z(&g, i);
+    dq += ea * (a[1][i * nz] - ez[i * nz]) + iz[i * nz];
+    gu += ea * u[1][i * nz];
+  }
+  for (int k = 0; k < 6; ++k) { free(a[k]); free(u[k]); free(z[k]); }
+  free(z[6]); free(z[7]);
+  return v1 - (qn + dq) / (cfg->cblock + gu);
+}
+
 static int o_step(const orc_cfg *cfg, void *field, o_port_state *ps, uint64_t step,
                   orc_species *sp, int nspec, double *er, double *ez, double *h, double *wall_z0,
                   double *wall_zl, double *wall_r, orc_stats *st, double *circ);
@@ -1599,12 +1638,14 @@ int oracle_step(const orc_cfg *cfg, void *field, uint64_t step, orc_species *sp,
 }
 
 /* The same step with the axial port (its solver from oracle_port_create; its
- * fields hp, erp, ezp at n in, at n+1 out); the electrode follows V(t). */
+ * fields hp, erp, ezp at n in, at n+1 out); the electrode follows V(t), or
+ * with cfg->cblock > 0 and circ given, Eq. 6's circuit (circ as in oracle_step). */
 int oracle_step_port(const orc_cfg *cfg, void *port, uint64_t step, orc_species *sp, int nspec,
                      double *er, double *ez, double *h, double *hp, double *erp, double *ezp,
-                     double *wall_z0, double *wall_zl, double *wall_r, orc_stats *st) {
+                     double *wall_z0, double *wall_zl, double *wall_r, orc_stats *st,
+                     double *circ) {
   o_port_state ps = {port, hp, erp, ezp};
-  return o_step(cfg, NULL, &ps, step, sp, nspec, er, ez, h, wall_z0, wall_zl, wall_r, st, NULL);
+  return o_step(cfg, NULL, &ps, step, sp, nspec, er, ez, h, wall_z0, wall_zl, wall_r, st, circ);
 }
 
 static int o_step(const orc_cfg *cfg, void *field, o_port_state *ps, uint64_t step,
@@ -1621,7 +1662,7 @@ static int o_step(const orc_cfg *cfg, void *field, o_port_state *ps, uint64_t st
   double v0 = cfg->volt * sin(O_TWO_PI * cfg->freq * t0);
   double v1 = cfg->volt * sin(O_TWO_PI * cfg->freq * t1);
   memset(st, 0, sizeof(*st));
-  const int circ_on = cfg->cblock > 0.0 && circ != NULL && ps == NULL;
+  const int circ_on = cfg->cblock > 0.0 && circ != NULL;
   /* the port's fields of the current iterate */
   size_t np = 0, nzz = 0;
   double *hp1 = NULL, *erp1 = NULL, *ezp1 = NULL;
@@ -1653,7 +1694,8 @@ static int o_step(const orc_cfg *cfg, void *field, o_port_state *ps, uint64_t st
       oracle_push(nr, nz, cfg->dr, cfg->dz, cfg->xa, cfg->nd, cfg->erd, cfg->dt, sp[s].q, sp[s].m, cfg->bz, sp[s].n, sp[s].cell,
                   sp[s].a, sp[s].b, sp[s].vr, sp[s].vt, sp[s].vz, sp[s].w, erh, ezh, ir, iz, 0,
                   NULL, NULL, NULL, NULL, NULL);
-    if (circ_on) phi1 = o_circuit(cfg, field, er, ez, h, ir, iz, phi0, v1, circ[0]);
+    if (circ_on && ps) phi1 = o_circuit_port(cfg, ps, er, ez, h, ir, iz, phi0, v1, circ[0]);
+    else if (circ_on) phi1 = o_circuit(cfg, field, er, ez, h, ir, iz, phi0, v1, circ[0]);
     if (ps)
       oracle_port_solve(ps->pf, er, ez, h, ps->erp, ps->ezp, ps->hp, ir, iz, phi0, phi1, ern, ezn,
                         h1, erp1, ezp1, hp1, &src);

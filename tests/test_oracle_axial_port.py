@@ -88,3 +88,57 @@ def test_quasi_static_tem_mode_and_gap_field():
     # gap field on the axis side: E_z = phi / L (directed from the powered plate)
     Ez = ez.reshape(g.nr + 1, g.nz)
     assert np.max(np.abs(Ez[: P.ip // 2] * g.L - phi)) <= 1e-2 * phi
+
+
+# ---- the axial port with the blocking capacitor (Eq. 6 feeding Eq. 7) --------
+
+F, V0 = 60e6, 100.0
+PORT = (10, 6, 0.03, 3.8)
+
+
+def volt(k, dt):
+    return V0 * np.sin(2 * np.pi * F * k * dt)
+
+
+def port_plasma(g, seed=4):
+    return O.load(g, 2000, 1e15, 8.0, 0.026, seed)
+
+
+def test_port_large_capacitor_reduces_to_the_driven_port():
+    g = O.Grid(16, 12, 0.1, 0.02)
+    e, i = port_plasma(g)
+    dt = 2e-11
+    a = O.Sim(g, dt, freq=F, volt=V0, tol=1e-12, species=[e, i], port=PORT)
+    b = O.Sim(g, dt, freq=F, volt=V0, tol=1e-12, species=[e, i], port=PORT, cblock=1e3)
+    for k in range(1, 4):
+        assert a.step()[0] == 0 and b.step()[0] == 0
+        assert abs(b.circ[1] - volt(k, dt)) <= 1e-12 * V0
+        for x, y in ((a.er, b.er), (a.ez, b.ez), (a.h, b.h), (a.erp, b.erp), (a.hp, b.hp)):
+            assert np.max(np.abs(x - y)) <= 1e-9 * np.max(np.abs(x))
+
+
+@pytest.mark.parametrize("C", [3e-11, 1e-30])
+def test_port_capacitor_charge_follows_amperes_law(C):
+    """Ampere's law summed over the E_z edges of the first row over the
+    electrode (i < ip) telescopes to dt 2 pi r_{ip-1/2} H^{n+1/2}(ip-1/2, 1/2),
+    an expression of the electrode current that the oracle's circuit never
+    evaluates: the capacitor charge must change by it every step."""
+    g = O.Grid(16, 12, 0.1, 0.02)
+    e, i = port_plasma(g)
+    dt = 2e-11
+    ip = PORT[0]
+    c = (ip - 1) * g.nz
+    rh = 2 * np.pi * (ip - 0.5) * g.dr
+    s = O.Sim(g, dt, freq=F, volt=V0, tol=1e-13, species=[e, i], port=PORT, cblock=C)
+    free = O.Sim(g, dt, freq=F, volt=V0, tol=1e-13, species=[e, i], port=PORT)
+    for k in range(1, 5):
+        h0, q0, fh0 = s.h.copy(), s.circ[0], free.h.copy()
+        assert s.step()[0] == 0 and free.step()[0] == 0
+        flow = dt * rh * 0.5 * (h0[c] + s.h[c])
+        scale = abs(dt * rh * 0.5 * (fh0[c] + free.h[c]))
+        assert scale > 0
+        assert abs(flow - (s.circ[0] - q0)) <= 1e-6 * scale, (k, flow, s.circ[0] - q0)
+        if C < 1e-20:  # floating electrode: no current
+            assert abs(flow) <= 1e-6 * scale
+        np.testing.assert_allclose(s.circ[0], C * (volt(k, dt) - s.circ[1]), rtol=1e-12,
+                                   atol=1e-40)
