@@ -73,8 +73,9 @@ extern "C" {
                                the reactor's side wall r = R.  At the port's end Eq. 5 (Mur's
                                condition) in the form E_r + eta H = 2 E_r^+ with the incoming TEM
                                wave of Eq. 7's reading, E_r^+ = (V(t) / 2) / (r ln(R / r_p)): half
-                               the electrode potential.  EM model, no capacitor, rings or wave
-                               port; the port's fields through pic_get_view. */
+                               the electrode potential (with cblock > 0, Eq. 6's phi(t) instead
+                               of V(t)).  EM model, no rings or wave port; the port's fields
+                               through pic_get_view. */
 
 typedef struct pic_ctx pic_ctx; /* opaque; host memory owned by the library */
 
@@ -102,7 +103,8 @@ typedef struct pic_config {
                                  powered electrode (Eq. 6); 0 = none (the electrode is at V(t)) */
   int ions_fixed;             /* 1: ions stay at their positions (no push, deposit or sort), as in
                                  the dispersion test of Sec. 3.1; requires mcc_on = 0 */
-  int feed;                   /* PIC_FEED_GAP or PIC_FEED_WAVE (EM model, no capacitor) */
+  int feed;                   /* PIC_FEED_GAP, PIC_FEED_WAVE (EM model, no capacitor) or
+                                 PIC_FEED_AXIAL (EM model) */
   int ring_cells;             /* dielectric ring: the outer ring_cells cells (r > R_d) are filled
                                  with a dielectric of relative permittivity eps_ring; particles
                                  move in r < R_d and stick at the ring face (0 = none) */
@@ -239,12 +241,14 @@ int pic_es_solve(pic_ctx *ctx, const double *Q_dev, double phi0, double *er_dev,
 /* Blocking capacitor (Eq. 6, cfg.cblock > 0).  Each Picard iteration solves
  * for the electrode potential phi^{n+1} that makes the reactor-side current
  * (displacement current plus crossed charge through the dual faces of the
- * first row of E_z edges above the powered plate, i < nr) equal to the
- * capacitor current (C (V^{n+1} - phi^{n+1}) - q^n) / dt.  The field solve is
- * affine in phi^{n+1}, so the equation is solved exactly from the solve at
- * V^{n+1} and a unit response computed at pic_init (EM) or known in closed
- * form (ES: the vacuum potential 1 - z/L).  The potential then drives the gap
- * (EM) or the plate and gap Dirichlet values (ES).  The state starts at
+ * first row of E_z edges above the powered plate, i < nr; with the axial port
+ * i < port_rin, the electrode's radius) equal to the capacitor current
+ * (C (V^{n+1} - phi^{n+1}) - q^n) / dt.  The field solve is affine in
+ * phi^{n+1}, so the equation is solved exactly from the solve at V^{n+1} and a
+ * unit response computed at pic_init (EM, through the port when there is one)
+ * or known in closed form (ES: the vacuum potential 1 - z/L).  The potential
+ * then drives the gap (EM), the axial port's incoming wave (half of it), or
+ * the plate and gap Dirichlet values (ES).  The state starts at
  * q = 0, phi = V(t) at pic_init and pic_load_particles.
  * pic_circuit_get: q^n [C] and phi^n [V] (host, nullable); without a
  * capacitor q = 0 and phi = V(t^n).  Synchronises.

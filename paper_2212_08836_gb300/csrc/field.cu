@@ -426,6 +426,13 @@ __device__ __forceinline__ double hh_at(const FieldOp &F, double dl, int i, int 
   return v;
 }
 
+// the same for the port's cells (p < np)
+__device__ __forceinline__ double hhp_at(const FieldOp &F, double dl, int p) {
+  double v = F.port.hhp[p];
+  if (F.cc.st) v += dl * (0.5 * F.port.hup[p]);
+  return v;
+}
+
 // ---- axial port (PortOp) ------------------------------------------------------
 // right-hand side of the port cells: 2 mu V_H H^n - dt C^T L Et over their
 // edges (the interface edges' Et with the crossed charge; 2 E^+ on the end
@@ -435,6 +442,7 @@ __global__ void k_rhs_port(FieldOp F, const double *er0, const double *ir, doubl
     v0 = F.vd[0];
     v1 = F.vd[1];
   }
+  if (F.cc.st) v0 = F.cc.st[2];  // the electrode potential phi^n
   const PortOp &P = F.port;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P.np) return;
@@ -494,12 +502,19 @@ __global__ void k_port_fix(FieldOp F, long long nh) {
 }
 
 // the port's H^{n+1}, E^{n+1} (end edges by Mur's relation) and the energy its
-// end delivers
+// end delivers; with the blocking capacitor the electrode's correction dl
+// (written by k_update, launched before) moves phi^{n+1} and the port's H
 __global__ void __launch_bounds__(256) k_update_port(FieldOp F, double v0, double v1,
                                                      DevCounters *cnt) {
   if (F.vd) {
     v0 = F.vd[0];
     v1 = F.vd[1];
+  }
+  double dl = 0.0;
+  if (F.cc.st) {
+    v0 = F.cc.st[2];
+    dl = F.cc.st[1];
+    v1 += dl;
   }
   const PortOp &P = F.port;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -508,13 +523,14 @@ __global__ void __launch_bounds__(256) k_update_port(FieldOp F, double v0, doubl
   if (t < P.np) {
     const int k = t / nzp, q = t - k * nzp, i = P.ip + k;
     const double s = tab(F, kTs, i), L = tab(F, kTw, i);
-    P.hp1[t] = 2.0 * P.hhp[t] - P.hp0[t];
+    const double hh = hhp_at(F, dl, t);
+    P.hp1[t] = 2.0 * hh - P.hp0[t];
     if (q == 0) {
-      const double eh = port_ein2(F, i, 0.5 * (v0 + v1)) - P.eta * P.hhp[t];
+      const double eh = port_ein2(F, i, 0.5 * (v0 + v1)) - P.eta * hh;
       P.erp1[t] = 2.0 * eh - P.erp0[t];
-      src = eh * L * F.dt * s * P.hhp[t];
+      src = eh * L * F.dt * s * hh;
     } else {
-      const double ch = -s * P.hhp[t] + s * P.hhp[t - 1];
+      const double ch = -s * hh + s * hhp_at(F, dl, t - 1);
       P.erp1[t] = P.erp0[t] + F.dt * ch / port_dr(F, i);
     }
   }
@@ -524,7 +540,8 @@ __global__ void __launch_bounds__(256) k_update_port(FieldOp F, double v0, doubl
     if (i == P.ip || i == F.nr) {
       P.ezp1[t] = 0.0;
     } else {
-      const double ch = tab(F, kTs, i) * P.hhp[k * nzp + q] - tab(F, kTs, i - 1) * P.hhp[(k - 1) * nzp + q];
+      const double ch = tab(F, kTs, i) * hhp_at(F, dl, k * nzp + q) -
+                        tab(F, kTs, i - 1) * hhp_at(F, dl, (k - 1) * nzp + q);
       P.ezp1[t] = P.ezp0[t] + F.dt * ch / port_dz(F, i);
     }
   }
@@ -534,9 +551,11 @@ __global__ void __launch_bounds__(256) k_update_port(FieldOp F, double v0, doubl
 
 // H1 = 2 H_half - H0; E1 from Ampere; Picard norms and drive-gap energy.
 // With the blocking capacitor, Eq. 6 fixes the electrode potential first:
-// Ampere's law summed over the first row of E_z edges (i < nr) telescopes, so
-// dt x the reactor-side current is dt 2 pi r_{nr-1/2} H^{n+1/2}(nr-1/2, 1/2),
-// affine in the potential; every thread evaluates the same expression.
+// Ampere's law summed over the first row of E_z edges over the electrode
+// (i < nr; with the axial port i < ip, the electrode's radius) telescopes, so
+// dt x the reactor-side current is dt 2 pi r_{e-1/2} H^{n+1/2}(e-1/2, 1/2)
+// (e = nr or ip), affine in the potential; every thread evaluates the same
+// expression.
 __global__ void __launch_bounds__(256) k_update(FieldOp F, const double *er0, const double *ez0,
                                                 const double *h0, const double *ir,
                                                 const double *iz, double v0, double v1,
@@ -555,9 +574,10 @@ __global__ void __launch_bounds__(256) k_update(FieldOp F, const double *er0, co
   double dl = 0.0;
   if (F.cc.st) {
     v0 = F.cc.st[2];
-    const double s = dt * tab(F, kTs, nr - 1);
-    const double q0 = s * hhalf_at(F, nr - 1, 0);          // electrode at V^{n+1}
-    const double gu = s * (0.5 * F.cc.hu[(nr - 1) * nz]);   // per unit potential
+    const int rim = (F.port.on ? F.port.ip : nr) - 1;
+    const double s = dt * tab(F, kTs, rim);
+    const double q0 = s * hhalf_at(F, rim, 0);              // electrode at V^{n+1}
+    const double gu = s * (0.5 * F.cc.hu[rim * nz]);        // per unit potential
     dl = -(F.cc.st[0] + q0) / (F.cc.C + gu);
     if (t == 0) {
       F.cc.st[1] = dl;
@@ -575,7 +595,7 @@ __global__ void __launch_bounds__(256) k_update(FieldOp F, const double *er0, co
       // interface edge: the port's top cell below, the reactor's first cell above
       const double s = tab(F, kTs, i);
       const double ch = -s * hh_at(F, dl, i, 0) +
-                        s * F.port.hhp[(i - F.port.ip) * F.port.nzp + F.port.nzp - 1];
+                        s * hhp_at(F, dl, (i - F.port.ip) * F.port.nzp + F.port.nzp - 1);
       er1[t] = er0[t] + (dt * ch - ir[t]) / port_dint(F, i);
     } else if (j == 0 || j == nz) {
       er1[t] = 0.0;

@@ -63,7 +63,7 @@ struct pic_ctx {
   float *q_st2[6];
   // axial port (PIC_FEED_AXIAL): its fields at n and n+1 (the solve's output,
   // copied in when a step commits)
-  double *hp, *erp, *ezp, *hp2, *erp2, *ezp2;
+  double *hp, *erp, *ezp, *hp2, *erp2, *ezp2, *hup;
   // pic_step_host: copy streams (device -> host, host -> device) and their events
   cudaStream_t hs_dn, hs_up;
   cudaEvent_t hs_ev[130];
@@ -257,7 +257,7 @@ bool valid(const pic_config *c) {
   if (c->axis_cells < 0 || c->axis_cells > kMaxAxisCells || c->axis_cells >= c->nr) return false;
   if (c->feed != PIC_FEED_GAP && c->feed != PIC_FEED_WAVE && c->feed != PIC_FEED_AXIAL) return false;
   if (c->feed == PIC_FEED_AXIAL &&
-      (c->field_model != PIC_FIELD_EM || c->cblock > 0.0 || c->ring_cells != 0 ||
+      (c->field_model != PIC_FIELD_EM || c->ring_cells != 0 ||
        c->sigma_ring != 0.0 || c->port_cells < 1 || !(c->port_len > 0.0) ||
        !isfinite(c->port_len) || c->port_rin < 1 || c->port_rin >= c->nr ||
        !(c->eps_port >= 1.0) || !isfinite(c->eps_port) ||
@@ -370,6 +370,7 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
     x->hp2 = (double *)K.take((size_t)np * 8);
     x->erp2 = (double *)K.take((size_t)np * 8);
     x->ezp2 = (double *)K.take((size_t)nzz * 8);
+    x->hup = (double *)K.take((size_t)np * 8);
   }
   {
     const int M = nz - 1, n2e = x->F.n2;
@@ -1297,6 +1298,12 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
     if (e == cudaSuccess)
       e = launch_field_solve(U, x->er, x->ez, x->h, x->ir, x->iz, 0.0, 1.0, x->er2, x->ez2, x->hu,
                              nullptr, nullptr, x->cnt, x->s);
+    // with the axial port the unit potential enters as Eq. 7's incoming wave
+    // (the port's fields at n are zero here); keep the port's H^{n+1} as well
+    if (e == cudaSuccess && x->F.port.on) {
+      e = cudaMemcpyAsync(x->hup, x->hp2, (size_t)x->F.port.np * 8, cudaMemcpyDeviceToDevice, x->s);
+      x->F.port.hup = x->hup;
+    }
     double cr = 0.0;
     for (int i = 0; i < nr; ++i) cr += x->eps * az(i);
     x->circ_on = 1;

@@ -182,6 +182,8 @@ struct PortOp {
   double *ws;          // m: Cinv U^T y
   const double *hp0, *erp0, *ezp0;  // port fields at n: H, E_r (end edge first), E_z
   double *hp1, *erp1, *ezp1;        // at n+1
+  const double *hup;  // with the blocking capacitor: the port's H^{n+1} response to a
+                      // unit electrode potential at n+1 (np; Circuit.hu's counterpart)
 };
 
 struct FieldOp {

@@ -101,6 +101,40 @@ def test_vacuum_steps_follow_the_oracle():
         assert close(a.cpu().numpy(), b, 1e-9)
 
 
+def test_vacuum_capacitor_energy_and_charge():
+    """The capacitor-fed port with no particles: the field energy of reactor
+    and port changes by exactly what the port's end delivers, and the
+    capacitor charge by the electrode current dt 2 pi r_{ip-1/2} H^{n+1/2}
+    at the electrode's rim, the telescoped Ampere law over its first row of
+    E_z edges (an expression the step's circuit solve does not evaluate)."""
+    nr, nz, ip, nzp = 16, 12, 10, 6
+    pic, cfg = make(nr, nz, ip, nzp, freq=200e6, volt=80.0, mcc_on=0, picard_tol=1e-12,
+                    cblock=8e-12)
+    g = O.Grid(nr, nz, cfg["R"], cfg["L"])
+    S = O.PortSolver(g, cfg["dt"], ip, nzp, cfg["port_len"] / nzp, cfg["eps_port"])
+    c, rh, dt = (ip - 1) * nz, 2 * np.pi * (ip - 0.5) * g.dr, cfg["dt"]
+
+    def fields():
+        v = pic.view()
+        return [v[k].cpu().numpy().copy() for k in ("er", "ez", "h", "port_er", "port_ez", "port_h")]
+
+    W = S.energy(*fields())
+    for n in range(40):
+        f0 = fields()
+        q0, _ = pic.circuit()
+        rc, st = pic.step(1)
+        assert rc == 0
+        f1 = fields()
+        W1 = S.energy(*f1)
+        assert abs(W1 - W - st["src_energy"]) <= 1e-9 * max(W1, 1e-300) + 1e-24, n
+        W = W1
+        q1, phi = pic.circuit()
+        flow = dt * rh * 0.5 * (f0[2][c] + f1[2][c])
+        assert abs(flow - (q1 - q0)) <= 1e-7 * max(abs(q1 - q0), 1e-300), n
+    v = cfg["volt"] * np.sin(2 * np.pi * cfg["freq"] * 40 * dt)
+    assert abs(phi - v) > 0.05 * abs(v)
+
+
 def test_discharge_energy_and_gauss():
     M = P()
     nr, nz, ip, nzp = 32, 24, 22, 12
@@ -134,21 +168,23 @@ def test_discharge_energy_and_gauss():
     assert np.max(np.abs(gauss_interior() - G0)) <= 1e-9 * qs
 
 
-def test_full_steps_with_the_port_match_the_oracle():
+@pytest.mark.parametrize("cblock", [0.0, 1e-11], ids=["driven", "capacitor"])
+def test_full_steps_with_the_port_match_the_oracle(cblock):
     """Whole steps (Picard iteration of push, deposit and the port's field
     solve, commit, sort) of a small discharge fed through the axial port,
     against the oracle's steps with the same port: same iteration counts,
-    fields of reactor and port and every particle to 1e-10."""
+    fields of reactor and port and every particle to 1e-10.  With the blocking
+    capacitor (Eq. 6) the electrode potential and the capacitor charge too."""
     from tests.test_gpu_parity import assert_state_close, by_id
     M = P()
     nr, nz, ip, nzp, n = 24, 32, 16, 10, 30000
     pic, cfg = make(nr, nz, ip, nzp, Lp=0.04, dt=5e-11, freq=100e6, volt=200.0, mcc_on=0,
-                    np_init=n, capacity_factor=1.5, picard_tol=1e-10)
+                    np_init=n, capacity_factor=1.5, picard_tol=1e-10, cblock=cblock)
     g = O.Grid(nr, nz, cfg["R"], cfg["L"])
     e, i = O.load(g, n, 1e15, 6.0, 0.026, 23)
     pic.set_state([e, i])
     sim = O.Sim(g, cfg["dt"], freq=cfg["freq"], volt=cfg["volt"], tol=cfg["picard_tol"],
-                kmax=cfg["picard_max"], species=[e, i], cap=int(n * 1.5),
+                kmax=cfg["picard_max"], species=[e, i], cap=int(n * 1.5), cblock=cblock,
                 port=(ip, nzp, cfg["port_len"], cfg["eps_port"]))
     for step in range(3):
         rc, st = pic.step(1)
@@ -165,3 +201,8 @@ def test_full_steps_with_the_port_match_the_oracle():
             assert_state_close(got, ref, rtol=1e-10, what="step %d species %d " % (step, s), nz=nz)
         assert st["absorbed"] == sto.counters[1]
         assert abs(st["src_energy"] - sto.src_energy) <= 1e-9 * max(abs(sto.src_energy), 1e-30)
+        if cblock > 0:
+            q, phi = pic.circuit()
+            np.testing.assert_allclose(phi, sim.circ[1], rtol=1e-10)
+            np.testing.assert_allclose(q, sim.circ[0], rtol=1e-8)
+            assert q != 0.0
