@@ -275,6 +275,32 @@ def measure(P, torch, dev, cfg, args, dist, D, do_e2e, sample_clocks, local):
     r["t_ms"] = ev0.elapsed_time(ev1)
     r["push_ms"], r["push_launches"] = pic.profile_read()
     pic.profile(False)
+    # the same steps with timing off, the Picard iteration run from the host
+    # (one wait per pass) and on the device (one conditional graph and one
+    # wait per step), alternating step by step so that both see the same
+    # discharge (its iteration count changes as it develops); each step timed
+    # alone, after one step of each that captures the graphs
+    for on in (False, True):
+        P.set_device_picard(pic, on)
+        pic.step(1)
+    barrier()
+    loop = {"host": [], "device": []}
+    its = {"host": [], "device": []}
+    for i in range(2 * args.steps):
+        on = i % 2 == 1
+        P.set_device_picard(pic, on)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, st = pic.step(1)
+        e1.record(stream)
+        e1.synchronize()
+        key = "device" if on else "host"
+        loop[key].append(e0.elapsed_time(e1))
+        its[key].append(st["picard_iters"])
+    barrier()
+    r["picard_loop"] = {k: {"ms_per_step": sum(v) / len(v), "picard_iters": its[k]}
+                        for k, v in loop.items()}
     # sub-step histogram of one more step, outside the timed region
     pic.substep_histogram(1)
     pic.step(1, check=False)
@@ -597,6 +623,11 @@ def run_ours(args):
             "clocks": r.get("clocks"),
             "gpu_launches": r["launches"],
             "roofline": roof,
+            "picard_loop": {"plain_fp64": r["picard_loop"],
+                            "note": "steps after the timed region with timing off, "
+                                    "alternating: the iteration from the host (a wait per "
+                                    "pass) against the device loop (pic_set_device_picard; "
+                                    "one wait per step), each step timed alone"},
             "substep_histogram": {"bins": r["substep_hist"],
                                   "note": "particles with k+1 accepted sub-steps in bin k "
                                           "(bin 15: 16 or more), one step after the timed region"}}
@@ -634,6 +665,7 @@ def run_ours(args):
                                  "peak_tflops": fp32_peak,
                                  "peak_kind": "FP32: 128 lanes x 152 SMs x 2 x max SM clock"}}}
         wall["mixed"] = tm / args.steps * 1e-3 * steps_per_cycle
+        line["picard_loop"]["mixed"] = rm["picard_loop"]
     # ---- electrostatic field model (Eq. 8) on the same reactor, mixed form
     if "es" in forms:
         cfge = P.large_reactor(seed=replica_seed(1, rank), precision=P.PIC_MIXED, field_model=P.PIC_FIELD_ES)

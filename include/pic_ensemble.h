@@ -48,6 +48,19 @@ typedef struct pic_ensemble pic_ensemble;
  * launches kernel by kernel. */
 int pic_set_graphs(pic_ctx *ctx, int on);
 
+/* The Picard iteration of Sec. 2.1 run on the device (on = 1, the default):
+ * with graph replay on and pic_profile off, each step launches one graph per
+ * buffer configuration whose conditional while-node repeats the pass (the
+ * speculative or the plain one, chosen by an if/else node), the convergence
+ * test on the device (the same residual, tolerance, iteration limit and
+ * speculation rule as the host loop) and the copy of the new iterate, until
+ * the residual is below the tolerance, not finite, or the limit is reached;
+ * the host waits once for the loop instead of once per pass.  The results
+ * are those of the host loop (the same kernels in the same order).  on = 0,
+ * graphs off, timing on, the context's first pass, or a driver without
+ * conditional graph nodes: the host loop.  PIC_E_CONFIG for on not 0 or 1. */
+int pic_set_device_picard(pic_ctx *ctx, int on);
+
 /* n members (1..PIC_ENSEMBLE_MAX), distinct, each ready to step; turns graph
  * replay on for every member and chooses persistent rounds where the members
  * allow them.  PIC_E_CONFIG on invalid arguments, PIC_E_CUDA when the stream,

@@ -138,6 +138,7 @@ def _load_lib():
     L.pic_cnn_train_step.argtypes = [_P, _P, _P, _I, C.c_float, _P]
     L.pic_set_guess.argtypes = [_P, _I, _P]
     L.pic_set_graphs.argtypes = [_P, _I]
+    L.pic_set_device_picard.argtypes = [_P, _I]
     L.pic_es_solve.argtypes = [_P, _P, _D, _P, _P]
     L.pic_circuit_get.argtypes = [_P, _P, _P]
     L.pic_circuit_set.argtypes = [_P, _D, _D]
@@ -693,6 +694,12 @@ def guess_sample(pic):
 def set_graphs(pic, on=True):
     """Replay the Picard passes of ``pic`` from captured CUDA graphs."""
     _check(lib().pic_set_graphs(pic._h, 1 if on else 0), "pic_set_graphs")
+
+
+def set_device_picard(pic, on=True):
+    """Run the Picard iteration as one conditional graph per step (graphs on,
+    timing off; the default) or from the host, one wait per pass."""
+    _check(lib().pic_set_device_picard(pic._h, 1 if on else 0), "pic_set_device_picard")
 
 
 class Ensemble:

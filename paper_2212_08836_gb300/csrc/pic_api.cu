@@ -160,6 +160,19 @@ struct pic_ctx {
   cudaStream_t gstream;     // stream of the network
   cudaEvent_t gev[2];
   int gev_made, cnn_layers;
+  // Picard iteration on the device (graphs on, timing off): one graph per
+  // buffer configuration holding a conditional while-node whose body runs
+  // the speculative or the plain pass (an if/else node), the convergence
+  // test and the iterate copy; the host waits once, after the loop
+  int dloop;                // 1: use it where it applies (the default)
+  int dl_capture;           // a loop body is being captured (no host read-back)
+  struct LoopEntry {
+    const void *key[12];
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    long long nl_plain, nl_spec;  // kernels in one plain / speculative pass
+  } lcache[32];
+  int nloop;
 };
 
 namespace {
@@ -177,7 +190,8 @@ enum {
   kHnMcc = 18,    // 8: collision counts
   kHnDe = 26,     // collision energy change
   kHnIz = 27,     // ionization pairs of the MCC pass
-  kHnSlots = 32
+  kHnLoop = 32,   // 13: the device Picard loop's state (kPd* below)
+  kHnSlots = 48
 };
 
 // cyclic-reduction coefficients (the layout k_cr reads) of the tridiagonal
@@ -1281,6 +1295,7 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
   x->es.vd = x->vdev;
   x->hist_n = 1;
   x->fb_alpha = -1;
+  x->dloop = 1;
   if (cfg->feed == PIC_FEED_AXIAL) {
     const int pr = port_setup(x, cfg);
     if (pr) {
@@ -1352,6 +1367,11 @@ void pic_destroy(pic_ctx *ctx) {
     cudaEventDestroy(ctx->sev[0]);
     cudaEventDestroy(ctx->sev[1]);
     cudaStreamDestroy(ctx->sstream);
+  }
+  if (ctx->nloop) cudaStreamSynchronize(ctx->s);
+  for (int k = 0; k < ctx->nloop; ++k) {
+    cudaGraphExecDestroy(ctx->lcache[k].exec);
+    cudaGraphDestroy(ctx->lcache[k].graph);
   }
   if (ctx->hs_made) {
     cudaStreamSynchronize(ctx->hs_dn);
@@ -1862,7 +1882,9 @@ int enqueue_post(pic_ctx *x) {
       return PIC_E_CUDA;
     x->launches += 5;
   }
-  if (cudaMemcpyAsync(x->hn, x->cnt->norm, 3 * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+  // (a pass inside the device loop leaves the norms to its convergence test)
+  if (!x->dl_capture &&
+      cudaMemcpyAsync(x->hn, x->cnt->norm, 3 * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return PIC_E_CUDA;
   return PIC_OK;
 }
@@ -1981,6 +2003,200 @@ void finish_pass(pic_ctx *x, int k, double &rprev, double &res, double &src, dou
   rprev = res;
 }
 
+// ---- the Picard iteration on the device ---------------------------------------
+// State of the loop in vdev[16..28] (doubles; read back once, after the loop):
+enum {
+  kPdK = 0,       // passes run
+  kPdConv,        // 1: converged
+  kPdSpec,        // 1: the next pass (after the test: the pass just run) is speculative
+  kPdSpecOk,      // 1: the converged pass was the speculative one
+  kPdNan,         // 1: the residual was not finite
+  kPdRes,         // residual of the last pass
+  kPdRprev,       // residual of the pass before (the contraction estimate)
+  kPdFirst,       // residual of the first pass
+  kPdSrc,         // drive energy of the last solve
+  kPdRho,         // contraction rate carried between steps (pic_ctx::rho_prev)
+  kPdTol,         // the Picard tolerance
+  kPdKmax,        // the iteration limit
+  kPdNspec,       // speculative passes run
+  kPdSlots = 13
+};
+constexpr int kPdBase = 16;  // offset of the loop state in vdev
+
+// The convergence test of one pass (the host loop's finish_pass, on the
+// device): residual from the solve's norms, the speculation decision for the
+// next pass, and the conditions of the while-node (go on) and of the if-node
+// (the next pass speculative).  One thread.
+__global__ void k_picard_ctl(cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hs,
+                             const double *norm, double *pd) {
+  const double res = sqrt(norm[0]) / fmax(sqrt(norm[1]), 1e-30);
+  const int k = (int)pd[kPdK];
+  const double rprev = pd[kPdRprev];
+  const bool spec = pd[kPdSpec] != 0.0;
+  if (k == 0) pd[kPdFirst] = res;
+  pd[kPdRes] = res;
+  pd[kPdSrc] = norm[2];
+  if (spec) pd[kPdNspec] += 1.0;
+  if (k > 0 && rprev > 0.0) pd[kPdRho] = res / rprev;
+  unsigned go = 1, next_spec = 0;
+  if (!isfinite(res)) {
+    pd[kPdNan] = 1.0;
+    go = 0;
+  } else if (res < pd[kPdTol]) {
+    pd[kPdConv] = 1.0;
+    pd[kPdSpecOk] = spec ? 1.0 : 0.0;
+    go = 0;
+  } else {
+    const double rho = k > 0 ? res / rprev : pd[kPdRho];
+    next_spec = rho > 0.0 && rho < 1.0 && res * rho < pd[kPdTol];
+    pd[kPdRprev] = res;
+  }
+  pd[kPdK] = (double)(k + 1);
+  if (k + 1 >= (int)pd[kPdKmax]) go = 0;
+  pd[kPdSpec] = next_spec ? 1.0 : 0.0;
+  cudaGraphSetConditional(hw, go);
+  cudaGraphSetConditional(hs, next_spec);
+}
+
+// capture one pass into a body graph of the loop (no dependencies: the first
+// node of its branch); *nl = kernels in it
+int capture_pass_into(pic_ctx *x, cudaGraph_t body, bool spec, long long *nl) {
+  if (cudaStreamBeginCaptureToGraph(x->s, body, nullptr, nullptr, 0,
+                                    cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return PIC_E_CUDA;
+  const long long l0 = x->launches;
+  x->capturing = 1;
+  x->dl_capture = 1;
+  const int r = enqueue_pass(x, spec);
+  x->capturing = 0;
+  x->dl_capture = 0;
+  *nl = x->launches - l0;
+  x->launches = l0;
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(x->s, &g);
+  if (r) return r;
+  return e == cudaSuccess ? PIC_OK : PIC_E_CUDA;
+}
+
+// the loop graph of the current buffer configuration: while (go) { if (spec)
+// speculative pass else plain pass; convergence test; er1/ez1 <- er2/ez2 }
+// (the copy takes the place of the host loop's pointer swap, so that the
+// captured passes keep their buffers)
+int build_loop(pic_ctx *x, pic_ctx::LoopEntry &L) {
+  const int nr = x->g.nr, nz = x->g.nz;
+  const size_t ner = (size_t)nr * (nz + 1), nez = (size_t)(nr + 1) * nz;
+  cudaGraph_t G = nullptr;
+  if (cudaGraphCreate(&G, 0) != cudaSuccess) return PIC_E_CUDA;
+  auto fail = [&](int r) {
+    cudaGraphDestroy(G);
+    return r;
+  };
+  cudaGraphConditionalHandle hw, hs;
+  if (cudaGraphConditionalHandleCreate(&hw, G, 1, cudaGraphCondAssignDefault) != cudaSuccess ||
+      cudaGraphConditionalHandleCreate(&hs, G, 0, cudaGraphCondAssignDefault) != cudaSuccess)
+    return fail(PIC_E_CUDA);
+  cudaGraphNodeParams wp = {};
+  wp.type = cudaGraphNodeTypeConditional;
+  wp.conditional.handle = hw;
+  wp.conditional.type = cudaGraphCondTypeWhile;
+  wp.conditional.size = 1;
+  cudaGraphNode_t wn;
+  if (cudaGraphAddNode(&wn, G, nullptr, nullptr, 0, &wp) != cudaSuccess) return fail(PIC_E_CUDA);
+  cudaGraph_t body = wp.conditional.phGraph_out[0];
+  cudaGraphNodeParams ip = {};
+  ip.type = cudaGraphNodeTypeConditional;
+  ip.conditional.handle = hs;
+  ip.conditional.type = cudaGraphCondTypeIf;
+  ip.conditional.size = 2;
+  cudaGraphNode_t in;
+  if (cudaGraphAddNode(&in, body, nullptr, nullptr, 0, &ip) != cudaSuccess)
+    return fail(PIC_E_CUDA);
+  int r = capture_pass_into(x, ip.conditional.phGraph_out[0], true, &L.nl_spec);
+  if (!r) r = capture_pass_into(x, ip.conditional.phGraph_out[1], false, &L.nl_plain);
+  if (r) return fail(r);
+  if (cudaStreamBeginCaptureToGraph(x->s, body, &in, nullptr, 1,
+                                    cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return fail(PIC_E_CUDA);
+  k_picard_ctl<<<1, 1, 0, x->s>>>(hw, hs, x->cnt->norm, x->vdev + kPdBase);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(x->er1, x->er2, ner * 8, cudaMemcpyDeviceToDevice, x->s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(x->ez1, x->ez2, nez * 8, cudaMemcpyDeviceToDevice, x->s);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(x->s, &g);
+  if (e != cudaSuccess || ee != cudaSuccess) return fail(PIC_E_CUDA);
+  cudaGraphExec_t ex = nullptr;
+  if (cudaGraphInstantiate(&ex, G, 0) != cudaSuccess) return fail(PIC_E_CUDA);
+  L.graph = G;
+  L.exec = ex;
+  return PIC_OK;
+}
+
+// The iteration as one graph launch and one wait.  *handled = false when it
+// does not apply (no graphs, timing on, the uncaptured first pass, a full
+// cache, a failed build): the host loop runs instead.
+int picard_device(pic_ctx *x, pic_step_stats &S, bool &conv, int &k, double &res, double &src,
+                  double &first, int &spec_ok, bool &handled) {
+  handled = false;
+  if (!x->dloop || !x->graphs || x->s == nullptr || x->prof || x->passes == 0) return PIC_OK;
+  const void *key[12] = {x->er, x->ez, x->h, x->er1, x->ez1, x->er2, x->ez2, x->h2,
+                         (const void *)(uintptr_t)x->cur[0], (const void *)(uintptr_t)x->cur[1],
+                         x->erh, (const void *)(uintptr_t)(x->hist_on ? 1 : 0)};
+  pic_ctx::LoopEntry *L = nullptr;
+  for (int i = 0; i < x->nloop; ++i)
+    if (!memcmp(x->lcache[i].key, key, sizeof(key))) L = &x->lcache[i];
+  if (!L) {
+    if (x->nloop == 32) return PIC_OK;
+    pic_ctx::LoopEntry &N = x->lcache[x->nloop];
+    if (build_loop(x, N)) {
+      // not available here (e.g. a driver without conditional nodes): the
+      // host loop from now on; a capture left open would poison the stream
+      cudaStreamCaptureStatus cs;
+      if (cudaStreamIsCapturing(x->s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(x->s, &g);
+        if (g) cudaGraphDestroy(g);
+      }
+      cudaGetLastError();
+      x->dloop = 0;
+      return PIC_OK;
+    }
+    memcpy(N.key, key, sizeof(key));
+    L = &N;
+    x->nloop += 1;
+  }
+  handled = true;
+  // pageable source: staged before the call returns
+  double pd[kPdSlots] = {};
+  pd[kPdRho] = x->rho_prev;
+  pd[kPdTol] = x->cfg.picard_tol;
+  pd[kPdKmax] = (double)x->cfg.picard_max;
+  double *dpd = x->vdev + kPdBase;
+  if (cudaMemcpyAsync(dpd, pd, sizeof(pd), cudaMemcpyHostToDevice, x->s) != cudaSuccess)
+    return PIC_E_CUDA;
+  if (cudaGraphLaunch(L->exec, x->s) != cudaSuccess) return PIC_E_CUDA;
+  if (cudaMemcpyAsync(x->hn + kHnLoop, dpd, sizeof(pd), cudaMemcpyDeviceToHost, x->s) !=
+      cudaSuccess)
+    return PIC_E_CUDA;
+  if (cudaStreamSynchronize(x->s) != cudaSuccess) return PIC_E_CUDA;
+  memcpy(pd, x->hn + kHnLoop, sizeof(pd));
+  const int passes = (int)pd[kPdK], nspec = (int)pd[kPdNspec];
+  x->passes += passes;
+  x->launches += (long long)(passes - nspec) * L->nl_plain + (long long)nspec * L->nl_spec + passes;
+  S.pushes += (long long)passes * (x->n[0] + x->n[1]);
+  x->rho_prev = pd[kPdRho];
+  res = pd[kPdRes];
+  src = pd[kPdSrc];
+  first = pd[kPdFirst];
+  conv = pd[kPdConv] != 0.0;
+  spec_ok = conv && pd[kPdSpecOk] != 0.0 ? 1 : 0;
+  k = conv ? passes - 1 : passes;
+  if (pd[kPdNan] != 0.0) {
+    S.picard_iters = passes;
+    return PIC_E_NAN;
+  }
+  return PIC_OK;
+}
+
 // the nonlinear iteration of Sec. 2.1 from the start in er1/ez1: push + deposit
 // with E^{n+1/2,k}, implicit field solve, relative-change test
 //
@@ -1999,6 +2215,9 @@ int picard(pic_ctx *x, double v0, double v1, pic_step_stats &S, bool &conv, int 
   src = 0.0;
   first = 0.0;
   spec_ok = 0;
+  bool handled = false;
+  const int dr = picard_device(x, S, conv, k, res, src, first, spec_ok, handled);
+  if (handled) return dr;
   bool spec = false;
   double rprev = 0.0;
   for (k = 0; k < x->cfg.picard_max; ++k) {
@@ -2946,6 +3165,12 @@ bool persistent_ok(const pic_ensemble *E) {
 int pic_set_graphs(pic_ctx *x, int on) {
   if (!x) return PIC_E_CONFIG;
   x->graphs = on ? 1 : 0;
+  return PIC_OK;
+}
+
+int pic_set_device_picard(pic_ctx *x, int on) {
+  if (!x || (on != 0 && on != 1)) return PIC_E_CONFIG;
+  x->dloop = on;
   return PIC_OK;
 }
 

@@ -40,11 +40,12 @@ def same(a, b):
     assert np.array_equal(wa, wb)
 
 
-@pytest.mark.parametrize("precision,graphs", [(0, 0), (1, 0), (1, 1)])
+@pytest.mark.parametrize("precision,graphs", [(0, 0), (1, 0), (0, 1), (1, 1)])
 def test_noconv_leaves_state_n(precision, graphs):
     """Sec. 2.1's convergence test cannot be met (tol 1e-30) within K_max = 2:
     PIC_E_NOCONV, and particles, fields, wall tallies and the step index are
-    those of step n, bit for bit (no pass of the failed step wrote them)."""
+    those of step n, bit for bit (no pass of the failed step wrote them).
+    With graph replay the iteration runs on the device (after the first step)."""
     M = P()
     cfg = M.small_reactor(np_init=20000, volt=200.0, precision=precision)
     pic = M.Pic(cfg, device=DEV, stream=torch.cuda.Stream(device=DEV) if graphs else None)
@@ -90,14 +91,16 @@ def test_capacity_appends_no_pair(precision):
         assert ids.max() < ids0[s]
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_nan_field_reports_nan(precision):
+@pytest.mark.parametrize("precision,graphs", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_nan_field_reports_nan(precision, graphs):
     """A NaN written into E^n from the host (through pic_state_upload): the
     Picard residual is not finite, pic_step returns PIC_E_NAN without
-    committing, and after a clean upload the context steps again."""
+    committing, and after a clean upload the context steps again.  With graph
+    replay the iteration runs on the device and stops at the first pass."""
     M = P()
     cfg = M.small_reactor(np_init=20000, volt=200.0, precision=precision)
-    pic = M.Pic(cfg, device=DEV)
+    pic = M.Pic(cfg, device=DEV, stream=torch.cuda.Stream(device=DEV) if graphs else None)
+    M.set_graphs(pic, bool(graphs))
     pic.load_particles()
     pic.step(2)
     hs = pic.host_state(pinned=True)
@@ -112,6 +115,8 @@ def test_nan_field_reports_nan(precision):
     rc, st = pic.step(1, check=False)
     assert rc == M.PIC_E_NAN
     assert pic.view()["step"] == step0
+    if graphs:
+        assert st["picard_iters"] == 1
     hs["er"].copy_(clean)
     pic.state_upload(hs)
     rc, st = pic.step(1)
