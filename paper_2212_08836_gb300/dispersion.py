@@ -124,18 +124,23 @@ def bessel_zero0(m):
 
 def ring(model="es", mode="symmetric", m=1, nr=64, nz=128, R=0.1, L=0.03, n0=1e16, ppc=64,
          sheath=1.8e-3, u0=5e4, steps=800, z_sample=1e-3, dt=1e-10, mu=0.0, te_ev=3.0, seed=0,
-         device="cuda:0", precision=PIC_FP64, tol=1e-7, base=None):
+         device="cuda:0", precision=PIC_FP64, tol=1e-7, base=None, band=None):
     """Free oscillation of one surface mode: the electrons of the loaded slab
     get the axial velocity u0 J_0(chi_{0,m} r / R), uniform in z (symmetric
     mode: the slab moves between the two sheaths, the plasma series resonance
     at k -> 0) or of opposite sign in the two halves of the gap (antisymmetric
     mode); the ringing of the Fourier-Bessel coefficient c_m of E_z in the
-    powered sheath gives the mode's frequency at k = chi_{0,m} / R (the
-    perturbed potential vanishes on the side wall, so both symmetries use the
-    zeros of J_0).  base: the series c_m of the same run with u0 = 0, which
-    is subtracted so that only the response to the kick remains.  Returns the
-    frequency from the FFT peak (parabolic interpolation on a 16x zero-padded
-    spectrum) and the raw series."""
+    sheaths gives the mode's frequency at k = chi_{0,m} / R (the perturbed
+    potential vanishes on the side wall, so both symmetries use the zeros of
+    J_0).  Symmetric: c_m in the powered sheath.  Antisymmetric: half the
+    difference of c_m in the two sheaths, at the same distance from either
+    plate, in which the symmetric mode (E_z even about the midplane) cancels
+    and the antisymmetric one (E_z odd) adds.  base: the series of the same
+    run with u0 = 0, which is subtracted so that only the response to the kick
+    remains.  band: (f_lo, f_hi) [Hz] to which the peak search is limited
+    (None: the whole spectrum).  Returns the frequency from the FFT peak
+    (parabolic interpolation on a 16x zero-padded spectrum) and the raw
+    series."""
     import torch
     fm = PIC_FIELD_ES if model == "es" else PIC_FIELD_EM
     cfg = small_reactor(nr=nr, nz=nz, R=R, L=L, dt=dt, freq=1e6, volt=0.0, n0=n0,
@@ -159,13 +164,20 @@ def ring(model="es", mode="symmetric", m=1, nr=64, nz=128, R=0.1, L=0.03, n0=1e1
     torch.cuda.synchronize(device)
     pic.set_state(sp, er=er.cpu().numpy(), ez=ez.cpu().numpy())
     row = int(round(z_sample / (L / nz) - 0.5))
+    anti = mode != "symmetric"
     coef = torch.empty((steps, m), dtype=torch.float64, device=device)
+    coef2 = torch.empty((steps, m), dtype=torch.float64, device=device) if anti else None
     iters, relaxed = [], []
     for k in range(steps):
         st = advance(pic, tol, relaxed, k)
         iters.append(st["picard_iters"])
         pic.fourier_bessel(0, row, m, out=coef[k])
+        if anti:   # the mirror row in the grounded sheath
+            pic.fourier_bessel(0, nz - 1 - row, m, out=coef2[k])
     c = coef[:, m - 1].cpu().numpy()
+    if anti:
+        c = 0.5 * (c - coef2[:, m - 1].cpu().numpy())
+    series = c.copy()
     if base is not None:
         # the response to the kick alone: the unkicked run with the same
         # particles carries the loaded slab's own oscillation and the noise
@@ -174,11 +186,13 @@ def ring(model="es", mode="symmetric", m=1, nr=64, nz=128, R=0.1, L=0.03, n0=1e1
     pad = 16 * len(c)
     P = np.abs(np.fft.rfft(c * np.hanning(len(c)), n=pad)) ** 2
     f = np.fft.rfftfreq(pad, dt)
-    k0 = int(np.argmax(P[1:])) + 1
+    lo, hi = (1, len(P)) if band is None else (max(1, int(np.ceil(band[0] / f[1]))),
+                                               min(len(P), int(band[1] / f[1]) + 1))
+    k0 = int(np.argmax(P[lo:hi])) + lo
     if 1 <= k0 < len(P) - 1:
         a, b, cc = np.log(P[k0 - 1]), np.log(P[k0]), np.log(P[k0 + 1])
         k0 = k0 + 0.5 * (a - cc) / (a - 2 * b + cc)
-    return {"freq": float(k0 * (f[1] - f[0])), "series": coef[:, m - 1].cpu().numpy(),
+    return {"freq": float(k0 * (f[1] - f[0])), "series": series,
             "k": chi / R, "model": model,
             "mode": mode, "m": m, "picard_iters_mean": float(np.mean(iters)),
             "relaxed_steps": len(relaxed)}
