@@ -13,8 +13,12 @@ on the axial edges, and Gauss's law is imposed on every interior node
 A_r(i) = 2 pi r_{i+1/2} dz, A_z(i) = 2 pi r_i dr (pi (dr/2)^2 on the axis).
 Boundary values: phi = phi0 on the powered plate z = 0, 0 on the grounded
 plate z = L, and phi0 (1 - z/L) across the drive gap at r = R (the potential
-of the lumped gap source, E_z = phi0 / L there).  The linear system is solved
-directly with scipy's sparse LU.
+of the lumped gap source, E_z = phi0 / L there).  With the axial port (port =
+ip, Sec. 2.2's electrostatic model): the powered electrode is the disc r <=
+r_p = r(ip) of z = 0, the port's opening r_p < r < R carries the potential of
+the coaxial line's TEM field, phi0 ln(r / R) / ln(r_p / R), and the side wall
+r = R is grounded.  The linear system is solved directly with scipy's sparse
+LU.
 """
 from __future__ import annotations
 
@@ -48,11 +52,17 @@ def _areas(nr, nz, dr, dz, xa=0, nd=0, erd=1.0):
     return ar, az
 
 
-def boundary_phi(nr, nz, phi0):
-    """Node potentials with the Dirichlet values set (interior zero)."""
+def boundary_phi(nr, nz, phi0, port=None, rn=None):
+    """Node potentials with the Dirichlet values set (interior zero); port:
+    the node index ip of the electrode's rim (rn: the node radii)."""
     phi = np.zeros((nr + 1, nz + 1))
-    phi[:, 0] = phi0
-    phi[nr, :] = phi0 * (1.0 - np.arange(nz + 1) / nz)
+    if port is None:
+        phi[:, 0] = phi0
+        phi[nr, :] = phi0 * (1.0 - np.arange(nz + 1) / nz)
+    else:
+        ip = int(port)
+        phi[: ip + 1, 0] = phi0
+        phi[ip + 1:, 0] = phi0 * np.log(rn[ip + 1:] / rn[nr]) / np.log(rn[ip] / rn[nr])
     return phi
 
 
@@ -64,15 +74,15 @@ def fields(phi, dr, dz, xa=0):
     return er.ravel(), ez.ravel()
 
 
-def solve(nr, nz, dr, dz, Q, phi0, eps=EPS0, xa=0, nd=0, erd=1.0):
+def solve(nr, nz, dr, dz, Q, phi0, eps=EPS0, xa=0, nd=0, erd=1.0, port=None):
     """Potential and fields for node charges Q ((nr+1) x (nz+1), only interior
-    nodes used) and powered-plate potential phi0."""
+    nodes used) and powered-plate potential phi0 (port: see boundary_phi)."""
     import scipy.sparse as sp
     import scipy.sparse.linalg as spla
     ar, az = _areas(nr, nz, dr, dz, xa, nd, erd)
     wr = radii(nr, dr, xa)[2]
     Q = np.asarray(Q, dtype=np.float64).reshape(nr + 1, nz + 1)
-    phi = boundary_phi(nr, nz, phi0)
+    phi = boundary_phi(nr, nz, phi0, port, radii(nr, dr, xa)[0])
     M = nz - 1
     idx = lambda i, j: i * M + (j - 1)
     rows, cols, vals = [], [], []
@@ -106,14 +116,16 @@ def solve(nr, nz, dr, dz, Q, phi0, eps=EPS0, xa=0, nd=0, erd=1.0):
     return phi, er, ez
 
 
-def electrode_charge_flow(nr, nz, dr, dz, ez_new, ez_old, iz, eps=EPS0, xa=0, nd=0, erd=1.0):
+def electrode_charge_flow(nr, nz, dr, dz, ez_new, ez_old, iz, eps=EPS0, xa=0, nd=0, erd=1.0,
+                          port=None):
     """dt times the reactor-side current of Eq. 6: the displacement current
     plus the crossed charge through the dual faces of the first row of E_z
-    edges above the powered plate (i < nr, j = 1/2), i.e. the integral over
-    the electrode in Eq. 6 on the integral-form mesh."""
+    edges above the powered plate (i < nr, j = 1/2; with the port i < ip, the
+    electrode disc), i.e. the integral over the electrode in Eq. 6 on the
+    integral-form mesh."""
     _, az = _areas(nr, nz, dr, dz, xa, nd, erd)
     s = 0.0
-    for i in range(nr):
+    for i in range(nr if port is None else int(port)):
         s += eps * az[i] * (ez_new[i * nz] - (ez_old[i * nz] if ez_old is not None else 0.0))
         if iz is not None:
             s += iz[i * nz]
@@ -121,15 +133,15 @@ def electrode_charge_flow(nr, nz, dr, dz, ez_new, ez_old, iz, eps=EPS0, xa=0, nd
 
 
 def circuit_potential(nr, nz, dr, dz, Q, ez_old, iz, v1, qn, cblock, eps=EPS0, xa=0, nd=0,
-                      erd=1.0):
+                      erd=1.0, port=None):
     """Electrode potential phi^{n+1} of Eq. 6 with a blocking capacitor cblock
     between the generator V^{n+1} = v1 and the electrode: the reactor-side
     charge flow must equal C (V^{n+1} - phi^{n+1}) - q^n.  The field is affine
     in phi^{n+1}; a solve at v1 and the unit-potential solve fix it."""
-    _, _, eza = solve(nr, nz, dr, dz, Q, v1, eps, xa, nd, erd)
-    _, _, ezu = solve(nr, nz, dr, dz, np.zeros((nr + 1) * (nz + 1)), 1.0, eps, xa, nd, erd)
-    dq = electrode_charge_flow(nr, nz, dr, dz, eza, ez_old, iz, eps, xa, nd, erd)
-    gu = electrode_charge_flow(nr, nz, dr, dz, ezu, None, None, eps, xa, nd, erd)
+    _, _, eza = solve(nr, nz, dr, dz, Q, v1, eps, xa, nd, erd, port)
+    _, _, ezu = solve(nr, nz, dr, dz, np.zeros((nr + 1) * (nz + 1)), 1.0, eps, xa, nd, erd, port)
+    dq = electrode_charge_flow(nr, nz, dr, dz, eza, ez_old, iz, eps, xa, nd, erd, port)
+    gu = electrode_charge_flow(nr, nz, dr, dz, ezu, None, None, eps, xa, nd, erd, port)
     return v1 - (qn + dq) / (cblock + gu)
 
 
@@ -159,15 +171,16 @@ class Sim:
 
     def __init__(self, grid, dt, *, freq=0.0, volt=0.0, tol=1e-8, kmax=50, eps=EPS0,
                  cblock=0.0, species=(), charges=None, masses=None, cap=None, drive=None,
-                 fixed=()):
+                 fixed=(), port=None):
         """drive: optional V(t) replacing volt sin(2 pi freq t); fixed: indices of
-        species that stay in place (not pushed, deposited or sorted)."""
+        species that stay in place (not pushed, deposited or sorted); port: the
+        node index ip of the axial port's inner radius (see boundary_phi)."""
         import oracle as O
         if getattr(grid, "sgd", 0.0) > 0.0:
             # Sec. 2.1: electrostatic runs model metals by a large permittivity
             raise ValueError("a conducting ring needs the electromagnetic model")
         self.O = O
-        self.drive, self.fixed = drive, tuple(fixed)
+        self.drive, self.fixed, self.port = drive, tuple(fixed), port
         self.g, self.dt, self.freq, self.volt = grid, dt, freq, volt
         self.tol, self.kmax, self.eps, self.cblock = tol, kmax, eps, cblock
         charges = charges or (-O.QE, O.QE)
@@ -210,7 +223,7 @@ class Sim:
             wr = self.wall[2]
             Qn.reshape(nr + 1, nz + 1)[nr - g.nd, :] += wr[: nz + 1] + wr[nz + 1:]
         er1, ez1 = self.er.copy(), self.ez.copy()
-        if not self.cblock > 0.0:
+        if not self.cblock > 0.0 and self.port is None:
             ez1[nr * nz:] = v1 / g.L
         phi1 = v1
         conv, res, k = False, 0.0, 0
@@ -223,8 +236,9 @@ class Sim:
             Q1 = Qn - divergence_out(nr, nz, ir, iz)
             if self.cblock > 0.0:
                 phi1 = circuit_potential(nr, nz, g.dr, g.dz, Q1, self.ez, iz, v1, self.circ[0],
-                                         self.cblock, self.eps, g.xa, g.nd, g.erd)
-            _, ern, ezn = solve(nr, nz, g.dr, g.dz, Q1, phi1, self.eps, g.xa, g.nd, g.erd)
+                                         self.cblock, self.eps, g.xa, g.nd, g.erd, self.port)
+            _, ern, ezn = solve(nr, nz, g.dr, g.dz, Q1, phi1, self.eps, g.xa, g.nd, g.erd,
+                                self.port)
             mr = np.ones((nr, nz + 1), bool)
             mr[:, 0] = mr[:, nz] = False
             dr_ = (ern - er1)[mr.ravel()]

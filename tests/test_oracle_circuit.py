@@ -162,3 +162,34 @@ def test_em_vacuum_divider_tends_to_the_electrostatic_one_like_mu():
             e = max(e, abs(s.circ[1] / volt(k, dt) - div))
         errs.append(e)
     assert errs[1] < 0.02 * errs[0] and errs[1] < 1e-5, errs
+
+
+# ---- the electrostatic model's axial port (Sec. 2.2): the electrode is the
+# disc r <= r_p, its circuit current the flow through the E_z faces over it
+
+def test_es_port_large_capacitor_reduces_to_the_driven_electrode():
+    g = O.Grid(12, 16, 0.1, 0.03)
+    e, i = plasma(g)
+    a = ES.Sim(g, 1e-10, freq=F, volt=V0, tol=1e-12, species=[e, i], port=8)
+    b = ES.Sim(g, 1e-10, freq=F, volt=V0, tol=1e-12, cblock=1e3, species=[e, i], port=8)
+    for k in range(1, 4):
+        assert a.step()[0] == 0 and b.step()[0] == 0
+        assert abs(b.circ[1] - volt(k, 1e-10)) <= 1e-12 * V0
+        for x, y in ((a.er, b.er), (a.ez, b.ez)):
+            assert np.max(np.abs(x - y)) <= 1e-9 * np.max(np.abs(x))
+
+
+def test_es_port_step_gauss_with_the_moved_particles():
+    g = O.Grid(12, 16, 0.1, 0.03)
+    e, i = plasma(g, te=8.0)
+    s = ES.Sim(g, 2e-10, freq=F, volt=V0, tol=1e-12, cblock=3e-11, species=[e, i], port=8)
+    for k in range(3):
+        rc, st = s.step()
+        assert rc == 0
+        Q = np.zeros(g.n_node)
+        for sp in range(2):
+            O.node_charge(g, (-O.QE, O.QE)[sp], s.state(sp), Q)
+        G = O.gauss_residual(g, s.er, s.ez, Q).reshape(g.nr + 1, g.nz + 1)
+        assert np.max(np.abs(G)) <= 1e-9 * np.max(np.abs(Q)), k
+        # the side wall is grounded: no E_z on it
+        assert np.max(np.abs(s.ez.reshape(g.nr + 1, g.nz)[g.nr])) == 0.0

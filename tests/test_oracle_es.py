@@ -41,3 +41,43 @@ def test_energy_identity_through_the_c_oracle():
     phi, er, ez = ES.solve(nr, nz, dr, dz, Q.ravel(), 0.0)
     W = O.field_energy(g, er, ez, np.zeros(nr * nz))
     assert abs(W - 0.5 * np.sum(Q * phi)) <= 1e-10 * abs(W)
+
+
+# ---- the axial port of the electrostatic model (Sec. 2.2): the disc r <= r_p
+# powered, the port's opening at the coaxial line's potential, side wall grounded
+
+def test_port_solve_keeps_gauss_law_through_the_c_oracle():
+    nr, nz, dr, dz, R, L = grid(12, 10, 0.1, 0.03)
+    g = O.Grid(nr, nz, R, L)
+    rng = np.random.default_rng(4)
+    Q = rng.normal(size=(nr + 1) * (nz + 1)) * 1e-12
+    phi, er, ez = ES.solve(nr, nz, dr, dz, Q, 55.0, port=7)
+    G = O.gauss_residual(g, er, ez, Q).reshape(nr + 1, nz + 1)
+    assert np.max(np.abs(G[:nr, 1:nz])) <= 1e-10 * np.max(np.abs(Q))
+
+
+def test_port_boundary_is_the_coaxial_tem_field():
+    """Along the port's opening r E_r is the TEM constant phi0 / ln(R / r_p) (to
+    the mesh's O(dr^2 / r^2)), the electrode disc is an equipotential (E_r = 0
+    on it) and the grounded side wall carries no E_z."""
+    nr, nz, dr, dz, R, L = grid(40, 12, 0.1, 0.03)
+    ip, phi0 = 24, 80.0
+    _, er, ez = ES.solve(nr, nz, dr, dz, np.zeros((nr + 1) * (nz + 1)), phi0, port=ip)
+    Er0 = er.reshape(nr, nz + 1)[:, 0]
+    rc = (np.arange(nr) + 0.5) * dr
+    tem = phi0 / np.log(R / (ip * dr))
+    np.testing.assert_allclose(rc[ip:] * Er0[ip:], tem, rtol=2e-3)
+    assert np.max(np.abs(Er0[:ip])) == 0.0
+    assert np.max(np.abs(ez.reshape(nr + 1, nz)[nr])) == 0.0
+
+
+def test_port_field_near_the_axis_is_the_plate_field():
+    """More than three gaps inside the electrode's rim the vacuum field is that
+    of two infinite plates, phi0 / L, up to the rim's exp(-pi d / L) influence."""
+    nr, nz, dr, dz, R, L = grid(48, 12, 0.16, 0.03)
+    ip, phi0 = 36, -60.0           # r_p = 0.12 m = 4 L
+    _, er, ez = ES.solve(nr, nz, dr, dz, np.zeros((nr + 1) * (nz + 1)), phi0, port=ip)
+    Ez = ez.reshape(nr + 1, nz)
+    d = ip * dr - 6 * dr            # distance of the outermost node checked from the rim
+    assert d / L >= 3.0
+    np.testing.assert_allclose(Ez[:7], phi0 / L, rtol=5e-4)
