@@ -74,8 +74,11 @@ extern "C" {
                                condition) in the form E_r + eta H = 2 E_r^+ with the incoming TEM
                                wave of Eq. 7's reading, E_r^+ = (V(t) / 2) / (r ln(R / r_p)): half
                                the electrode potential (with cblock > 0, Eq. 6's phi(t) instead
-                               of V(t)).  EM model, no rings or wave port; the port's fields
-                               through pic_get_view. */
+                               of V(t)); the port's fields through pic_get_view.  Electrostatic
+                               model (Sec. 2.2's counterpart): the port's opening r_p < r < R of
+                               z = 0 carries the coaxial line's potential phi ln(r/R)/ln(r_p/R)
+                               as a Dirichlet value, the disc r <= r_p is at phi, the side wall
+                               grounded.  No rings or wave port. */
 
 typedef struct pic_ctx pic_ctx; /* opaque; host memory owned by the library */
 
@@ -104,7 +107,7 @@ typedef struct pic_config {
   int ions_fixed;             /* 1: ions stay at their positions (no push, deposit or sort), as in
                                  the dispersion test of Sec. 3.1; requires mcc_on = 0 */
   int feed;                   /* PIC_FEED_GAP, PIC_FEED_WAVE (EM model, no capacitor) or
-                                 PIC_FEED_AXIAL (EM model) */
+                                 PIC_FEED_AXIAL */
   int ring_cells;             /* dielectric ring: the outer ring_cells cells (r > R_d) are filled
                                  with a dielectric of relative permittivity eps_ring; particles
                                  move in r < R_d and stick at the ring face (0 = none) */
@@ -117,11 +120,13 @@ typedef struct pic_config {
                                  at the half step); a large value models a metal (Sec. 2.1).
                                  Needs ring_cells > 0 and the EM model (an electrostatic run
                                  models a metal by a large eps_ring); 0 = none */
-  int port_cells;             /* PIC_FEED_AXIAL: cells along z of the port (>= 1) */
-  double port_len;            /* PIC_FEED_AXIAL: the port's length [m] */
+  int port_cells;             /* PIC_FEED_AXIAL: cells along z of the port (>= 1; EM only,
+                                 checked for both models) */
+  double port_len;            /* PIC_FEED_AXIAL: the port's length [m] (EM only) */
   int port_rin;               /* PIC_FEED_AXIAL: the port's inner radius is the node r(port_rin),
                                  1 <= port_rin < nr (the powered electrode's radius) */
-  double eps_port;            /* PIC_FEED_AXIAL: relative permittivity of the port (>= 1) */
+  double eps_port;            /* PIC_FEED_AXIAL: relative permittivity of the port (>= 1; EM
+                                 only) */
 } pic_config;
 
 /* Per-step statistics (host struct). */

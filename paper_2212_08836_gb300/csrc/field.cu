@@ -701,25 +701,29 @@ __device__ __forceinline__ double es_phi0(const EsOp &E, double phi0) {
   return E.vd ? E.vd[1] : phi0;
 }
 
-// node potential with the Dirichlet values on the plates and across the gap;
-// dl: the circuit's correction of the electrode potential (phi0 includes it),
-// whose response is the vacuum solution dl (1 - z/L)
+// node potential with the Dirichlet values on the plates and across the gap
+// (axial port: the disc and the port's opening on z = 0, a grounded side
+// wall); dl: the circuit's correction of the electrode potential (phi0
+// includes it), whose response is the vacuum solution dl (1 - z/L) (with the
+// port: dl uphi)
 __device__ __forceinline__ double es_node(const EsOp &E, double phi0, double dl, int i, int j) {
-  if (j == 0) return phi0;
+  if (j == 0) return E.pip ? phi0 * E.g0[i] : phi0;
   if (j == E.nz) return 0.0;
-  if (i == E.nr) return phi0 * (1.0 - (double)j / E.nz);
-  return E.phi[i * E.M + j - 1] + dl * (1.0 - (double)j / E.nz);
+  if (i == E.nr) return E.pip ? 0.0 : phi0 * (1.0 - (double)j / E.nz);
+  const int c = i * E.M + j - 1;
+  return E.phi[c] + dl * (E.pip ? E.uphi[c] : 1.0 - (double)j / E.nz);
 }
 
 // Eq. 6 with the blocking capacitor: dt x the reactor-side current through the
-// dual faces of the first row of E_z edges (i < nr), displacement plus crossed
-// charge, for the solve at V^{n+1}; the response per unit potential is the
-// closed-form vacuum value cr.  One block, fixed summation order.
+// dual faces of the first row of E_z edges (i < nr; with the axial port the
+// electrode disc, i < pip), displacement plus crossed charge, for the solve at
+// V^{n+1}; the response per unit potential is the vacuum value cr (closed
+// form, or from the unit solve with the port).  One block, fixed summation order.
 __global__ void __launch_bounds__(256) k_es_circuit(EsOp E, const double *iz, double phi0) {
   phi0 = es_phi0(E, phi0);
-  const int nr = E.nr, nz = E.nz;
+  const int nr = E.nr, nz = E.nz, ne = E.pip ? E.pip : nr;
   double v = 0.0;
-  for (int i = threadIdx.x; i < nr; i += blockDim.x) {
+  for (int i = threadIdx.x; i < ne; i += blockDim.x) {
     const double ea = E.tab[2 * nr + i];  // eps A_z(i) / dz
     const double ez1 = (phi0 - E.phi[i * E.M]) / E.dz;
     v += ea * E.dz * (ez1 - E.ez0[i * nz]) + iz[i * nz];
@@ -759,8 +763,8 @@ __global__ void __launch_bounds__(256) k_es_rhs(EsOp E, const double *Q, const d
     q -= out;
   }
   const double cR = E.tab[i], cZ = E.tab[2 * nr + i];
-  if (i == nr - 1) q += cR * phi0 * (1.0 - (double)j / nz);
-  if (j == 1) q += cZ * phi0;
+  if (i == nr - 1 && !E.pip) q += cR * phi0 * (1.0 - (double)j / nz);
+  if (j == 1) q += cZ * phi0 * (E.pip ? E.g0[i] : 1.0);
   E.rhs[t] = q;
 }
 

@@ -271,7 +271,7 @@ bool valid(const pic_config *c) {
   if (c->axis_cells < 0 || c->axis_cells > kMaxAxisCells || c->axis_cells >= c->nr) return false;
   if (c->feed != PIC_FEED_GAP && c->feed != PIC_FEED_WAVE && c->feed != PIC_FEED_AXIAL) return false;
   if (c->feed == PIC_FEED_AXIAL &&
-      (c->field_model != PIC_FIELD_EM || c->ring_cells != 0 ||
+      (c->ring_cells != 0 ||
        c->sigma_ring != 0.0 || c->port_cells < 1 || !(c->port_len > 0.0) ||
        !isfinite(c->port_len) || c->port_rin < 1 || c->port_rin >= c->nr ||
        !(c->eps_port >= 1.0) || !isfinite(c->eps_port) ||
@@ -368,7 +368,7 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
   x->F.rhs = (double *)K.take(nh * 8);
   x->F.hat = (double *)K.take(nh * 8);
   x->F.hhalf = (double *)K.take(nh * 8);
-  if (c->feed == PIC_FEED_AXIAL) {
+  if (c->feed == PIC_FEED_AXIAL && c->field_model == PIC_FIELD_EM) {
     PortOp &P = x->F.port;
     const int m = nr - c->port_rin, nzp = c->port_cells, np = m * nzp, nzz = (m + 1) * nzp;
     P.Binv = (const double *)K.take((size_t)np * np * 8);
@@ -402,6 +402,10 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
     x->es.phi = (double *)K.take((size_t)nr * M * 8);
     x->qn = (double *)K.take((size_t)(nr + 1) * (nz + 1) * 8);
     x->es.tw2 = (const double2 *)K.take((size_t)2 * nz * 16);
+    if (c->feed == PIC_FEED_AXIAL && c->field_model == PIC_FIELD_ES) {
+      x->es.g0 = (const double *)K.take((size_t)(nr + 1) * 8);
+      x->es.uphi = (const double *)K.take((size_t)nr * M * 8);
+    }
   }
   x->F.tw = (const double2 *)K.take((size_t)nz * 16);
   x->F.pw = (const double2 *)K.take((size_t)nz * 16);
@@ -1296,11 +1300,39 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
   x->hist_n = 1;
   x->fb_alpha = -1;
   x->dloop = 1;
-  if (cfg->feed == PIC_FEED_AXIAL) {
+  if (cfg->feed == PIC_FEED_AXIAL && cfg->field_model == PIC_FIELD_EM) {
     const int pr = port_setup(x, cfg);
     if (pr) {
       pic_destroy(x);
       return pr;
+    }
+  }
+  if (cfg->feed == PIC_FEED_AXIAL && cfg->field_model == PIC_FIELD_ES) {
+    // the electrostatic port: the coaxial line's potential on the opening
+    const int ip = cfg->port_rin;
+    std::vector<double> g0(nr + 1);
+    const double lr = log(g_rnode(x->g, ip) / g_rnode(x->g, nr));
+    for (int i = 0; i <= nr; ++i)
+      g0[i] = i <= ip ? 1.0 : log(g_rnode(x->g, i) / g_rnode(x->g, nr)) / lr;
+    x->es.pip = ip;
+    if (e == cudaSuccess)
+      e = cudaMemcpy((void *)x->es.g0, g0.data(), (nr + 1) * 8, cudaMemcpyHostToDevice);
+    // the interior potential of a unit electrode potential (no charge)
+    EsOp U = x->es;
+    U.vd = nullptr;
+    U.cc = Circuit{};
+    const size_t nn = (size_t)(nr + 1) * (nz + 1);
+    if (e == cudaSuccess) e = cudaMemsetAsync(x->qn, 0, nn * 8, x->s);
+    if (e == cudaSuccess)
+      e = launch_es_solve(U, x->qn, nullptr, nullptr, 1.0, x->er2, x->ez2, nullptr, nullptr,
+                          nullptr, x->s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync((void *)x->es.uphi, x->es.phi, (size_t)nr * (nz - 1) * 8,
+                          cudaMemcpyDeviceToDevice, x->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(x->s);
+    if (e != cudaSuccess) {
+      pic_destroy(x);
+      return PIC_E_CUDA;
     }
   }
   if (cfg->cblock > 0.0) {
@@ -1321,9 +1353,19 @@ int pic_init(const pic_config *cfg, void *workspace_dev, size_t workspace_bytes,
     }
     double cr = 0.0;
     for (int i = 0; i < nr; ++i) cr += x->eps * az(i);
+    cr /= cfg->L;
+    if (x->es.pip && e == cudaSuccess) {
+      // the flow of the unit solve through the faces over the electrode disc
+      const int M = nz - 1, ip = x->es.pip;
+      std::vector<double> up((size_t)nr * M), tb((size_t)4 * nr);
+      e = cudaMemcpy(up.data(), x->es.uphi, up.size() * 8, cudaMemcpyDeviceToHost);
+      if (e == cudaSuccess) e = cudaMemcpy(tb.data(), x->es.tab, tb.size() * 8, cudaMemcpyDeviceToHost);
+      cr = 0.0;
+      for (int i = 0; i < ip; ++i) cr += tb[2 * nr + i] * (1.0 - up[(size_t)i * M]);
+    }
     x->circ_on = 1;
     x->F.cc = Circuit{x->vdev + 4, x->hu, cfg->cblock, 0.0};
-    x->es.cc = Circuit{x->vdev + 4, nullptr, cfg->cblock, cr / cfg->L};
+    x->es.cc = Circuit{x->vdev + 4, nullptr, cfg->cblock, cr};
     x->es.ez0 = nullptr;
     if (e == cudaSuccess) e = circuit_reset(x);
     if (e == cudaSuccess) e = cudaStreamSynchronize(x->s);
@@ -1775,8 +1817,9 @@ int plain_start(pic_ctx *x, double v1) {
   const size_t ner = (size_t)nr * (nz + 1), nez = (size_t)(nr + 1) * nz;
   cudaError_t e = cudaMemcpyAsync(x->er1, x->er, ner * 8, cudaMemcpyDeviceToDevice, x->s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(x->ez1, x->ez, nez * 8, cudaMemcpyDeviceToDevice, x->s);
-  // with the blocking capacitor or the wave port the gap edges keep E^n's
-  if (e == cudaSuccess && !x->circ_on && !x->F.wave && !x->F.port.on) {
+  // with the blocking capacitor, the wave port or the axial port the gap edges
+  // keep E^n's
+  if (e == cudaSuccess && !x->circ_on && !x->F.wave && !x->F.port.on && !x->es.pip) {
     k_fill<<<(nz + 127) / 128, 128, 0, x->s>>>(x->ez1 + (size_t)nr * nz, nz, v1 / x->cfg.L);
     e = cudaGetLastError();
     x->launches += 1;
@@ -1808,7 +1851,7 @@ int guess_start(pic_ctx *x, double v1, int *used) {
   if (launch_guess_apply(A, y, cp, v1 / x->cfg.L, x->er1, x->ez1, x->gbad, x->s) != cudaSuccess)
     return PIC_E_CUDA;
   x->launches += 1;
-  if (x->circ_on || x->F.wave || x->F.port.on) {
+  if (x->circ_on || x->F.wave || x->F.port.on || x->es.pip) {
     // the gap edges keep E^n's, as in the plain start
     const size_t g0 = (size_t)x->g.nr * x->g.nz;
     if (cudaMemcpyAsync(x->ez1 + g0, x->ez + g0, (size_t)x->g.nz * 8, cudaMemcpyDeviceToDevice,

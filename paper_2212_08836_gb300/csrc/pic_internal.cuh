@@ -309,6 +309,12 @@ struct EsOp {
   const double2 *tw2;      // exp(-2 pi i k / (2 nz))
   Circuit cc;
   const double *ez0;       // E_z^n (the plate flow of Eq. 6 with the circuit)
+  // axial port (PIC_FEED_AXIAL; pip = 0: none): the powered electrode is the
+  // disc of nodes i <= pip on z = 0, the port's opening carries phi0 g0[i]
+  // (g0 = ln(r_i / R) / ln(r_pip / R), 1 on the disc), the side wall is grounded
+  int pip;
+  const double *g0;        // nr + 1
+  const double *uphi;      // nr x M: the interior potential of a unit phi0 (no charge)
 };
 // E (Yee layouts) of the node charges Q (Q = Qn - div I if ir is given);
 // Picard norms against er_it / ez_it into cnt when cnt is given

@@ -26,20 +26,27 @@ def P():
     return M
 
 
-def setup(field_model, cblock, precision=0, n=40000, volt=300.0):
+def setup(field_model, cblock, precision=0, n=40000, volt=300.0, port=0):
+    """port > 0: the axial port with its inner radius at node port (the
+    electrostatic model's Dirichlet port of Sec. 2.2)."""
     M = P()
     # the FP32 push converges to ~1e-7 relative: looser tolerance for the mixed form
+    kw = {}
+    if port:
+        kw = dict(feed=M.PIC_FEED_AXIAL, port_rin=port, port_cells=4, port_len=0.02,
+                  eps_port=3.8)
     cfg = M.small_reactor(np_init=n, capacity_factor=1.5, mcc_on=0,
                           picard_tol=1e-10 if precision == 0 else 1e-6,
                           volt=volt, field_model=field_model, cblock=cblock,
-                          precision=precision)
+                          precision=precision, **kw)
     g = O.Grid(cfg["nr"], cfg["nz"], cfg["R"], cfg["L"])
     e, i = O.load(g, n, 1e15, 8.0, 0.026, 21)
     pic = M.Pic(cfg, device=DEV)
     pic.set_state([e, i])
     if field_model == M.PIC_FIELD_ES:
         sim = ES.Sim(g, cfg["dt"], freq=cfg["freq"], volt=cfg["volt"], tol=1e-10,
-                     kmax=cfg["picard_max"], cblock=cblock, species=[e, i], cap=int(n * 1.5))
+                     kmax=cfg["picard_max"], cblock=cblock, species=[e, i], cap=int(n * 1.5),
+                     port=port or None)
     else:
         sim = O.Sim(g, cfg["dt"], freq=cfg["freq"], volt=cfg["volt"], tol=1e-10,
                     kmax=cfg["picard_max"], species=[e, i], cap=int(n * 1.5), cblock=cblock)
@@ -52,9 +59,11 @@ def sim_step(sim):
     return rc, it
 
 
-@pytest.mark.parametrize("field_model,cblock", [(0, 4e-11), (1, 4e-11), (1, 0.0)])
-def test_step_parity_with_oracle(field_model, cblock):
-    cfg, pic, sim = setup(field_model, cblock)
+@pytest.mark.parametrize("field_model,cblock,port", [(0, 4e-11, 0), (1, 4e-11, 0), (1, 0.0, 0),
+                                                     (1, 4e-11, 20), (1, 0.0, 20)],
+                         ids=["em-cap", "es-cap", "es", "es-port-cap", "es-port"])
+def test_step_parity_with_oracle(field_model, cblock, port):
+    cfg, pic, sim = setup(field_model, cblock, port=port)
     nz = cfg["nz"]
     for step in range(3):
         rc, st = pic.step(1)
