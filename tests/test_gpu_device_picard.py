@@ -28,6 +28,11 @@ def P():
 
 def pair(guess=0, **kw):
     M = P()
+    if kw.get("precision", 0) == 1:
+        # FP32 particles: a step converged at 1e-8 sits near the rounding floor
+        # of the FP32 push, where the order of the atomic sums can cost one pass
+        # more or less; at 1e-6 the loops' decisions are the same in both
+        kw.setdefault("picard_tol", 1e-6)
     cfg = M.small_reactor(np_init=30000, volt=200.0, **kw)
     out = []
     for dev_loop in (False, True):
