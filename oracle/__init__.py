@@ -108,6 +108,8 @@ def _declare(L):
     L.oracle_field_solve.argtypes = [_P, _P, _P, _P, _P, _P, _D, _D, _D, _P, _P, _P, _P]
     L.oracle_port_create.argtypes = [_I, _I, _D, _D, _I, _I, _I, _D, _D, _D, _D, _D]
     L.oracle_port_create.restype = _P
+    L.oracle_port_create_graded.argtypes = [_I, _I, _D, _D, _I, _I, _I, _P, _D, _D, _D, _D]
+    L.oracle_port_create_graded.restype = _P
     L.oracle_port_destroy.argtypes = [_P]
     L.oracle_port_solve.argtypes = [_P] + [_P] * 8 + [_D, _D] + [_P] * 7
     L.oracle_port_energy.argtypes = [_P] * 7
@@ -303,18 +305,37 @@ class FieldSolver:
                                               _p(qc))
 
 
+def port_heights(nzp, port_len, grade=1.0):
+    """Row heights of the axial port, q = 0 at its end to nzp - 1 at the
+    junction with the reactor: a geometric progression of ratio grade from the
+    junction down (grade 1: uniform) that sums to port_len."""
+    if grade == 1.0:
+        return np.full(nzp, port_len / nzp)
+    top = port_len * (grade - 1.0) / (grade ** nzp - 1.0)
+    return np.array([top * grade ** (nzp - 1 - q) for q in range(nzp)])
+
+
 class PortSolver:
     """Implicit CN Maxwell solve with the axial dielectric port below the
     powered electrode (Sec. 2.2, Eqs. 5 and 7), by banded Cholesky of the
     H system of reactor and port together.  ip: the port's inner radius is
-    r(ip) (the electrode's); nzp cells of height dzp; erq: its relative
+    r(ip) (the electrode's); nzp cells of height dzp, or of the row heights
+    `heights` (q = 0 at the port's end; see port_heights); erq: its relative
     permittivity."""
 
-    def __init__(self, grid: Grid, dt, ip, nzp, dzp, erq, eps=EPS0, mu=MU0):
+    def __init__(self, grid: Grid, dt, ip, nzp, dzp, erq, eps=EPS0, mu=MU0, heights=None):
         self.grid, self.dt, self.eps, self.mu = grid, dt, eps, mu
         self.ip, self.nzp, self.dzp, self.erq = ip, nzp, dzp, erq
-        self._h = lib().oracle_port_create(grid.nr, grid.nz, grid.dr, grid.dz, grid.xa, ip, nzp,
-                                           dzp, erq, dt, eps, mu)
+        if heights is None:
+            self.heights = np.full(nzp, float(dzp))
+            self._h = lib().oracle_port_create(grid.nr, grid.nz, grid.dr, grid.dz, grid.xa, ip,
+                                               nzp, dzp, erq, dt, eps, mu)
+        else:
+            self.heights = np.ascontiguousarray(heights, dtype=np.float64)
+            assert self.heights.shape == (nzp,)
+            self._h = lib().oracle_port_create_graded(grid.nr, grid.nz, grid.dr, grid.dz,
+                                                      grid.xa, ip, nzp, _p(self.heights), erq,
+                                                      dt, eps, mu)
         if not self._h:
             raise RuntimeError("oracle port matrix not positive definite")
 
@@ -396,7 +417,8 @@ class Sim:
                  cblock=0.0, wave=False, port=None):
         """cblock: blocking capacitor [F] in series with the generator (Eq. 6),
         0 = the electrode follows V(t); its state is self.circ = [q^n, phi^n].
-        port: (ip, nzp, port_len, erq) for the axial dielectric port (the reactor's
+        port: (ip, nzp, port_len, erq[, grade]) for the axial dielectric port (rows
+        graded by port_heights; the reactor's
         side wall then a conductor; the electrode at V(t) or, with cblock, Eq. 6's
         circuit); its fields are self.hp, self.erp, self.ezp."""
         self.grid = grid
@@ -421,8 +443,10 @@ class Sim:
             c.pnull_i = -np.expm1(-nu_i * dt)
         self.port = None
         if port is not None:
-            ip, nzp, lp, erq = port
-            self.port = PortSolver(grid, dt, ip, nzp, lp / nzp, erq, eps, mu)
+            ip, nzp, lp, erq = port[:4]
+            grade = port[4] if len(port) > 4 else 1.0
+            self.port = PortSolver(grid, dt, ip, nzp, lp / nzp, erq, eps, mu,
+                                   heights=port_heights(nzp, lp, grade) if grade != 1.0 else None)
             self.erp, self.ezp, self.hp = self.port.zeros_port()
         else:
             self.field = FieldSolver(grid, dt, eps, mu, wave)

@@ -1194,14 +1194,17 @@ int64_t oracle_sort(int ncell, int64_t n, int32_t *cell, double *a, double *b, d
 /* ------------------------------------------------ axial dielectric port */
 /* The paper's feed (Sec. 2.2, Fig. 1): below the powered electrode, a coaxial
  * port filled with a dielectric (relative permittivity erq) runs from the
- * electrode radius r_p = r(ip) to r = R, nzp cells of height dzp deep; the
+ * electrode radius r_p = r(ip) to r = R, nzp rows of cells deep, of heights
+ * hq[q] (q = 0 at the port's end, q = nzp - 1 at the junction; uniform, or
+ * graded to lengthen the waveguide in few cells, Sec. 2.1's nonuniform mesh); the
  * electrode's stem (r < r_p) and the outer wall (r = R) are conductors (E_z = 0
  * on them), the powered electrode face (z = 0, r < r_p) stays a plate (E_r = 0)
  * and the reactor's side wall r = R a conductor (E_z = 0).  The port cells
  * carry H_theta like the reactor's; the E_r edges on z = 0 for r > r_p join the
  * two (interface edges: their dual face is half in the port, half in the
- * reactor, D = eps 2 pi r (erq dzp / 2 + dz / 2)).  At the port's end (z = -nzp
- * dzp) Eq. 5, Mur's condition for the outgoing TEM wave with an incoming one,
+ * reactor, D = eps 2 pi r (erq hq[nzp-1] / 2 + dz / 2); the E_r edges between
+ * port rows q - 1 and q have the dual length (hq[q-1] + hq[q]) / 2).  At the
+ * port's end Eq. 5, Mur's condition for the outgoing TEM wave with an incoming one,
  * is taken in its characteristic form E_r + eta H_theta = 2 E_r^+ (eta =
  * sqrt(mu / (erq eps))), CN-centred, with the incoming wave of Eq. 7's
  * reading: the coaxial TEM field E_r^+(r) = phi^+ / (r ln(R / r_p)) of half
@@ -1213,7 +1216,8 @@ int64_t oracle_sort(int ncell, int64_t n, int32_t *cell, double *a, double *b, d
  * r < r_p), so the system is banded with bandwidth nzp + nz; banded Cholesky. */
 typedef struct {
   int nr, nz, ip, nzp, cs, n, bw, xa;
-  double dr, dz, dzp, erq, dt, eps, mu, lnr;
+  double dr, dz, erq, dt, eps, mu, lnr;
+  double *hq;   /* nzp row heights */
   double *Lb;
 } o_pfield;
 
@@ -1222,42 +1226,50 @@ static double *o_pband(o_pfield *F, int i, int j) {
 }
 static int o_pidx(const o_pfield *F, int i, int jj) { return i * F->cs + F->nzp + jj; }
 static double o_dint(const og_grid *g, const o_pfield *F, int i) {
-  return F->eps * O_TWO_PI * o_rhalf(g, i) * (0.5 * F->erq * F->dzp + 0.5 * F->dz);
+  return F->eps * O_TWO_PI * o_rhalf(g, i) * (0.5 * F->erq * F->hq[F->nzp - 1] + 0.5 * F->dz);
 }
-static double o_dpr(const og_grid *g, const o_pfield *F, int i) {
-  return F->eps * F->erq * O_TWO_PI * o_rhalf(g, i) * F->dzp;
+/* the E_r edge between port rows q - 1 and q (q >= 1) */
+static double o_dpr(const og_grid *g, const o_pfield *F, int i, int q) {
+  return F->eps * F->erq * O_TWO_PI * o_rhalf(g, i) * (0.5 * (F->hq[q - 1] + F->hq[q]));
 }
 static double o_dpz(const og_grid *g, const o_pfield *F, int i) {
   return F->eps * F->erq * o_area_z(g, i);
 }
-static double o_vol_hp(const og_grid *g, const o_pfield *F, int i) {
-  return O_TWO_PI * o_rhalf(g, i) * o_drc(g, i) * F->dzp;
+static double o_vol_hp(const og_grid *g, const o_pfield *F, int i, int q) {
+  return O_TWO_PI * o_rhalf(g, i) * o_drc(g, i) * F->hq[q];
 }
 /* 2 E_r^+ at the half step on the port's end edge (i + 1/2) */
 static double o_port_ein2(const og_grid *g, const o_pfield *F, int i, double phi_half) {
   return phi_half / (o_rhalf(g, i) * F->lnr);
 }
 
-void *oracle_port_create(int nr, int nz, double dr, double dz, int xa, int ip, int nzp,
-                         double dzp, double erq, double dt, double eps, double mu) {
-  if (ip < 1 || ip >= nr || nzp < 1) return NULL;
+/* hq: the nzp row heights (copied) */
+void *oracle_port_create_graded(int nr, int nz, double dr, double dz, int xa, int ip, int nzp,
+                                const double *hq, double erq, double dt, double eps,
+                                double mu) {
+  if (ip < 1 || ip >= nr || nzp < 1 || !hq) return NULL;
+  for (int q = 0; q < nzp; ++q)
+    if (!(hq[q] > 0.0)) return NULL;
   o_pfield *F = (o_pfield *)calloc(1, sizeof(o_pfield));
   og_grid g = {nr, nz, dr, dz, xa, 0, 1.0, 0.0};
   F->nr = nr; F->nz = nz; F->ip = ip; F->nzp = nzp; F->xa = xa;
-  F->dr = dr; F->dz = dz; F->dzp = dzp; F->erq = erq; F->dt = dt; F->eps = eps; F->mu = mu;
+  F->dr = dr; F->dz = dz; F->erq = erq; F->dt = dt; F->eps = eps; F->mu = mu;
+  F->hq = (double *)malloc(sizeof(double) * nzp);
+  if (!F->hq) { free(F); return NULL; }
+  memcpy(F->hq, hq, sizeof(double) * nzp);
   F->lnr = log(o_rnode(&g, nr) / o_rnode(&g, ip));
   F->cs = nzp + nz;
   F->n = nr * F->cs;
   F->bw = F->cs;
   F->Lb = (double *)calloc((size_t)F->n * (F->bw + 1), sizeof(double));
-  if (!F->Lb) { free(F); return NULL; }
+  if (!F->Lb) { free(F->hq); free(F); return NULL; }
   const double hdt2 = 0.5 * dt * dt, eta = sqrt(mu / (erq * eps));
   for (int i = 0; i < nr; ++i) {
     const double s = O_TWO_PI * o_rhalf(&g, i), L = o_drc(&g, i);
     for (int j = 0; j < nz; ++j) *o_pband(F, o_pidx(F, i, j), o_pidx(F, i, j)) += 2.0 * mu * o_vol_h(&g, i);
     for (int q = 0; q < nzp; ++q) {
       const int c = o_pidx(F, i, q - nzp);
-      *o_pband(F, c, c) += i >= ip ? 2.0 * mu * o_vol_hp(&g, F, i) : 1.0;
+      *o_pband(F, c, c) += i >= ip ? 2.0 * mu * o_vol_hp(&g, F, i, q) : 1.0;
     }
     /* reactor E_r edges j = 1..nz-1 */
     for (int j = 1; j < nz; ++j) {
@@ -1277,7 +1289,7 @@ void *oracle_port_create(int nr, int nz, double dr, double dz, int xa, int ip, i
       *o_pband(F, hi, lo) -= hdt2 * W * s * s;
     }
     for (int q = 1; q < nzp; ++q) {
-      const double W = L / o_dpr(&g, F, i);
+      const double W = L / o_dpr(&g, F, i, q);
       const int lo = o_pidx(F, i, q - 1 - nzp), hi = o_pidx(F, i, q - nzp);
       *o_pband(F, lo, lo) += hdt2 * W * s * s;
       *o_pband(F, hi, hi) += hdt2 * W * s * s;
@@ -1303,7 +1315,7 @@ void *oracle_port_create(int nr, int nz, double dr, double dz, int xa, int ip, i
     }
     if (i <= ip) continue;
     for (int q = 0; q < nzp; ++q) {
-      const double W = dzp / o_dpz(&g, F, i);
+      const double W = F->hq[q] / o_dpz(&g, F, i);
       const int cr = o_pidx(F, i, q - nzp), cl = o_pidx(F, i - 1, q - nzp);
       *o_pband(F, cr, cr) += hdt2 * W * sr * sr;
       *o_pband(F, cl, cl) += hdt2 * W * sl * sl;
@@ -1318,7 +1330,7 @@ void *oracle_port_create(int nr, int nz, double dr, double dz, int xa, int ip, i
       int k0 = j0 > j - bw ? j0 : j - bw;
       for (int k = k0; k < j; ++k) sum -= *o_pband(F, i, k) * *o_pband(F, j, k);
       if (i == j) {
-        if (!(sum > 0.0)) { free(F->Lb); free(F); return NULL; }
+        if (!(sum > 0.0)) { free(F->Lb); free(F->hq); free(F); return NULL; }
         *o_pband(F, i, i) = sqrt(sum);
       } else {
         *o_pband(F, i, j) = sum / *o_pband(F, j, j);
@@ -1328,10 +1340,22 @@ void *oracle_port_create(int nr, int nz, double dr, double dz, int xa, int ip, i
   return F;
 }
 
+void *oracle_port_create(int nr, int nz, double dr, double dz, int xa, int ip, int nzp,
+                         double dzp, double erq, double dt, double eps, double mu) {
+  if (nzp < 1) return NULL;
+  double *hq = (double *)malloc(sizeof(double) * nzp);
+  if (!hq) return NULL;
+  for (int q = 0; q < nzp; ++q) hq[q] = dzp;
+  void *F = oracle_port_create_graded(nr, nz, dr, dz, xa, ip, nzp, hq, erq, dt, eps, mu);
+  free(hq);
+  return F;
+}
+
 void oracle_port_destroy(void *p) {
   o_pfield *F = (o_pfield *)p;
   if (!F) return;
   free(F->Lb);
+  free(F->hq);
   free(F);
 }
 
@@ -1356,7 +1380,7 @@ void oracle_port_solve(void *p, const double *er0, const double *ez0, const doub
     for (int j = 0; j < nz; ++j) x[o_pidx(F, i, j)] = 2.0 * mu * o_vol_h(&g, i) * h0[i * nz + j];
     if (i >= ip)
       for (int q = 0; q < nzp; ++q)
-        x[o_pidx(F, i, q - nzp)] = 2.0 * mu * o_vol_hp(&g, F, i) * hp0[(i - ip) * nzp + q];
+        x[o_pidx(F, i, q - nzp)] = 2.0 * mu * o_vol_hp(&g, F, i, q) * hp0[(i - ip) * nzp + q];
   }
   /* - dt C^T L Et over the unknown edges (and the end edges' 2 E^+) */
   for (int i = 0; i < nr; ++i) {
@@ -1393,8 +1417,8 @@ void oracle_port_solve(void *p, const double *er0, const double *ez0, const doub
     if (i <= ip) continue;
     for (int q = 0; q < nzp; ++q) {
       const double et = ezp0[(i - ip) * nzp + q];
-      x[o_pidx(F, i, q - nzp)] -= dt * sr * F->dzp * et;
-      x[o_pidx(F, i - 1, q - nzp)] -= dt * (-sl) * F->dzp * et;
+      x[o_pidx(F, i, q - nzp)] -= dt * sr * F->hq[q] * et;
+      x[o_pidx(F, i - 1, q - nzp)] -= dt * (-sl) * F->hq[q] * et;
     }
   }
   /* banded Cholesky solve: x = H^{n+1/2} */
@@ -1439,7 +1463,7 @@ void oracle_port_solve(void *p, const double *er0, const double *ez0, const doub
         srcE += eh * L * dt * s * xb;
       } else {
         const double ch = -s * x[o_pidx(F, i, q - nzp)] + s * x[o_pidx(F, i, q - 1 - nzp)];
-        erp1[e] = erp0[e] + dt * ch / o_dpr(&g, F, i);
+        erp1[e] = erp0[e] + dt * ch / o_dpr(&g, F, i, q);
       }
     }
   }
@@ -1486,10 +1510,10 @@ double oracle_port_energy(void *p, const double *er, const double *ez, const dou
       W += 0.5 * o_dint(&g, F, i) * L * e * e;
       for (int q = 0; q < nzp; ++q) {
         const double hv = hp[(i - ip) * nzp + q];
-        W += 0.5 * F->mu * o_vol_hp(&g, F, i) * hv * hv;
+        W += 0.5 * F->mu * o_vol_hp(&g, F, i, q) * hv * hv;
         if (q >= 1) {
           const double ev = erp[(i - ip) * nzp + q];
-          W += 0.5 * o_dpr(&g, F, i) * L * ev * ev;
+          W += 0.5 * o_dpr(&g, F, i, q) * L * ev * ev;
         }
       }
     }
@@ -1502,7 +1526,7 @@ double oracle_port_energy(void *p, const double *er, const double *ez, const dou
   for (int i = ip + 1; i < nr; ++i)
     for (int q = 0; q < nzp; ++q) {
       const double e = ezp[(i - ip) * nzp + q];
-      W += 0.5 * o_dpz(&g, F, i) * F->dzp * e * e;
+      W += 0.5 * o_dpz(&g, F, i) * F->hq[q] * e * e;
     }
   return W;
 }

@@ -142,3 +142,82 @@ def test_port_capacitor_charge_follows_amperes_law(C):
             assert abs(flow) <= 1e-6 * scale
         np.testing.assert_allclose(s.circ[0], C * (volt(k, dt) - s.circ[1]), rtol=1e-12,
                                    atol=1e-40)
+
+
+# ---- a graded port (rows growing from the junction down: Sec. 2.1's
+# nonuniform mesh, which lengthens the waveguide in few cells) ----------------
+
+def graded(nzp=12, Lp=0.06, grade=1.2, nr=16, nz=12, ip=10, erq=3.8, dt=2e-11):
+    g = O.Grid(nr, nz, 0.1, 0.02)
+    return g, O.PortSolver(g, dt, ip, nzp, Lp / nzp, erq, heights=O.port_heights(nzp, Lp, grade))
+
+
+def test_port_heights_are_a_geometric_progression_summing_to_the_length():
+    h = O.port_heights(12, 0.06, 1.2)
+    assert abs(h.sum() - 0.06) <= 1e-15
+    np.testing.assert_allclose(h[:-1] / h[1:], 1.2, rtol=1e-13)   # q = 0 (the end) largest
+    np.testing.assert_allclose(O.port_heights(5, 0.03, 1.0), 0.006, rtol=1e-15)
+
+
+def test_graded_port_energy_identity_from_random_fields():
+    g, P = graded()
+    rng = np.random.default_rng(9)
+    er, ez, h = (rng.normal(size=g.n_er) * 1e3, rng.normal(size=g.n_ez) * 1e3,
+                 rng.normal(size=g.nr * g.nz))
+    erp, ezp, hp = P.zeros_port()
+    erp[:] = rng.normal(size=erp.size) * 1e3
+    ezp[:] = rng.normal(size=ezp.size) * 1e3
+    hp[:] = rng.normal(size=hp.size)
+    er.reshape(g.nr, g.nz + 1)[:, g.nz] = 0.0
+    er.reshape(g.nr, g.nz + 1)[: P.ip, 0] = 0.0
+    ez.reshape(g.nr + 1, g.nz)[g.nr, :] = 0.0
+    m = g.nr - P.ip
+    ezp.reshape(m + 1, P.nzp)[0, :] = 0.0
+    ezp.reshape(m + 1, P.nzp)[m, :] = 0.0
+    ir, iz = np.zeros(g.n_er), np.zeros(g.n_ez)
+    for phi0, phi1 in ((0.0, 0.0), (3.0, 7.5)):
+        W0 = P.energy(er, ez, h, erp, ezp, hp)
+        er1, ez1, h1, erp1, ezp1, hp1, src = P.solve(er, ez, h, erp, ezp, hp, ir, iz, phi0, phi1)
+        W1 = P.energy(er1, ez1, h1, erp1, ezp1, hp1)
+        assert abs(W1 - W0 - src) <= 1e-11 * W0, (W1 - W0, src)
+
+
+def test_graded_port_carries_the_electrode_potential_at_every_height():
+    """Quasi-static drive: the coaxial voltage across the annulus equals the
+    electrode potential in every row, coarse or fine."""
+    g, P = graded(dt=1e-11)
+    omega = 2 * np.pi / (4000 * P.dt)
+    er, ez, h, erp, ezp, hp, phi = drive(P, g, 1000, omega, 100.0)
+    m = g.nr - P.ip
+    Erp = erp.reshape(m, P.nzp)
+    dr = np.diff(g.r_nodes()[P.ip:])
+    for q in range(P.nzp):
+        assert abs(Erp[:, q] @ dr - phi) <= 1e-2 * phi, q
+
+
+def test_graded_port_transit_time_matches_a_fine_uniform_port():
+    """A smooth rise of the potential reaches the junction after the port's
+    transit time L_p sqrt(eps_q) / c: the half-rise time of E_r in the top
+    port row through 12 graded rows (1.5 to 11 mm) agrees with that through
+    48 uniform rows of 1.25 mm to 3 %."""
+    c = 1.0 / np.sqrt(O.EPS0 * O.MU0)
+    Lp, erq, dt = 0.06, 3.8, 2e-12
+    T = Lp * np.sqrt(erq) / c
+
+    def half_rise(P, g):
+        er, ez, h = g.zeros_fields()
+        erp, ezp, hp = P.zeros_port()
+        ir, iz = np.zeros(g.n_er), np.zeros(g.n_ez)
+        V = lambda t: 50.0 * (1.0 - np.cos(np.pi * min(t, T) / T))
+        m, y = g.nr - P.ip, []
+        for n in range(900):
+            er, ez, h, erp, ezp, hp, _ = P.solve(er, ez, h, erp, ezp, hp, ir, iz, V(n * dt),
+                                                 V((n + 1) * dt))
+            y.append(erp.reshape(m, P.nzp)[0, P.nzp - 1])
+        y = np.array(y)
+        return np.argmax(y > 0.5 * y.max()) * dt
+
+    tg = half_rise(*graded(nzp=12, Lp=Lp, grade=1.2, dt=dt)[::-1])
+    tu = half_rise(*graded(nzp=48, Lp=Lp, grade=1.0, dt=dt)[::-1])
+    assert tu > T  # the rise has crossed the port
+    assert abs(tg / tu - 1.0) <= 0.03, (tg, tu)
