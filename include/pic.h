@@ -127,6 +127,10 @@ typedef struct pic_config {
                                  1 <= port_rin < nr (the powered electrode's radius) */
   double eps_port;            /* PIC_FEED_AXIAL: relative permittivity of the port (>= 1; EM
                                  only) */
+  double port_grade;          /* PIC_FEED_AXIAL, EM: the port's rows grow by this ratio from the
+                                 junction down to its end (a geometric progression summing to
+                                 port_len; the nonuniform axial mesh of Sec. 2.1, lengthening
+                                 the waveguide in few cells); 0 or 1: uniform; 0.25..4 */
 } pic_config;
 
 /* Per-step statistics (host struct). */

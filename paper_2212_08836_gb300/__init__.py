@@ -49,7 +49,7 @@ class Config(C.Structure):
                 ("field_model", _I), ("cblock", _D), ("ions_fixed", _I), ("feed", _I),
                 ("ring_cells", _I), ("eps_ring", _D), ("axis_cells", _I),
                 ("sigma_ring", _D), ("port_cells", _I), ("port_len", _D), ("port_rin", _I),
-                ("eps_port", _D)]
+                ("eps_port", _D), ("port_grade", _D)]
 
 
 class StepStats(C.Structure):
@@ -196,7 +196,8 @@ def small_reactor(**kw):
                np_init=40000, capacity_factor=1.5, picard_tol=1e-8, picard_max=50, mcc_on=1,
                bz=0.0, eps=0.0, mu=0.0, seed=0, precision=PIC_FP64, field_model=0, cblock=0.0,
                ions_fixed=0, feed=0, ring_cells=0, eps_ring=1.0, axis_cells=0,
-               sigma_ring=0.0, port_cells=0, port_len=0.0, port_rin=0, eps_port=1.0)
+               sigma_ring=0.0, port_cells=0, port_len=0.0, port_rin=0, eps_port=1.0,
+               port_grade=1.0)
     cfg.update(kw)
     return cfg
 
@@ -211,7 +212,8 @@ def large_reactor(**kw):
                np_init=16 * 1024 * 1024, capacity_factor=1.25, picard_tol=1e-8, picard_max=50,
                mcc_on=1, bz=0.0, eps=0.0, mu=0.0, seed=1, precision=PIC_FP64, field_model=0,
                cblock=0.0, ions_fixed=0, feed=0, ring_cells=0, eps_ring=1.0, axis_cells=0,
-               sigma_ring=0.0, port_cells=0, port_len=0.0, port_rin=0, eps_port=1.0)
+               sigma_ring=0.0, port_cells=0, port_len=0.0, port_rin=0, eps_port=1.0,
+               port_grade=1.0)
     cfg.update(kw)
     return cfg
 

@@ -85,12 +85,13 @@ __device__ __forceinline__ double tab(const FieldOp &F, int k, int i) {
   return F.rtab[k * (F.nr + 1) + i];
 }
 // axial port: D of the interface edge (i + 1/2, 0), half in the port and half in
-// the reactor; of the port's E_r and E_z edges; 2 E^+ on the end edge
+// the reactor; of the port's E_r edge between rows q - 1 and q (dual length
+// the mean of their heights) and of its E_z edges; 2 E^+ on the end edge
 __device__ __forceinline__ double port_dint(const FieldOp &F, int i) {
-  return F.eps * tab(F, kTs, i) * 0.5 * (F.port.erq * F.port.dzp + F.dz);
+  return F.eps * tab(F, kTs, i) * 0.5 * (F.port.erq * F.port.htop + F.dz);
 }
-__device__ __forceinline__ double port_dr(const FieldOp &F, int i) {
-  return F.eps * F.port.erq * tab(F, kTs, i) * F.port.dzp;
+__device__ __forceinline__ double port_dr(const FieldOp &F, int i, int q) {
+  return F.eps * F.port.erq * tab(F, kTs, i) * (0.5 * (F.port.hq[q - 1] + F.port.hq[q]));
 }
 __device__ __forceinline__ double port_dz(const FieldOp &F, int i) {
   return F.port.erq / tab(F, kTeaz, i);  // erq eps A_z
@@ -447,7 +448,7 @@ __global__ void k_rhs_port(FieldOp F, const double *er0, const double *ir, doubl
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= P.np) return;
   const int k = p / P.nzp, q = p - k * P.nzp, i = P.ip + k, nz1 = F.nz + 1;
-  const double s = tab(F, kTs, i), L = tab(F, kTw, i), dzp = P.dzp;
+  const double s = tab(F, kTs, i), L = tab(F, kTw, i), dzp = P.hq[q];
   const double etb = q == 0 ? port_ein2(F, i, 0.5 * (v0 + v1)) : P.erp0[p];
   const double ett = q + 1 == P.nzp ? er0[i * nz1] - ir[i * nz1] / (2.0 * port_dint(F, i))
                                      : P.erp0[p + 1];
@@ -531,7 +532,7 @@ __global__ void __launch_bounds__(256) k_update_port(FieldOp F, double v0, doubl
       src = eh * L * F.dt * s * hh;
     } else {
       const double ch = -s * hh + s * hhp_at(F, dl, t - 1);
-      P.erp1[t] = P.erp0[t] + F.dt * ch / port_dr(F, i);
+      P.erp1[t] = P.erp0[t] + F.dt * ch / port_dr(F, i, q);
     }
   }
   const int nez = (P.m + 1) * nzp;

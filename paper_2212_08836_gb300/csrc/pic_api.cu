@@ -275,6 +275,7 @@ bool valid(const pic_config *c) {
        c->sigma_ring != 0.0 || c->port_cells < 1 || !(c->port_len > 0.0) ||
        !isfinite(c->port_len) || c->port_rin < 1 || c->port_rin >= c->nr ||
        !(c->eps_port >= 1.0) || !isfinite(c->eps_port) ||
+       !(c->port_grade == 0.0 || (c->port_grade >= 0.25 && c->port_grade <= 4.0)) ||
        c->nr - c->port_rin > 4096 || (long long)(c->nr - c->port_rin) * c->port_cells > 8192))
     return false;
   if (c->ring_cells < 0 || (c->ring_cells > 0 && (!(c->eps_ring >= 1.0) || !isfinite(c->eps_ring) ||
@@ -378,6 +379,7 @@ bool layout(pic_ctx *x, const pic_config *c, char *base, size_t cap, size_t *use
     P.rhsp = (double *)K.take((size_t)np * 8);
     P.hhp = (double *)K.take((size_t)np * 8);
     P.ws = (double *)K.take((size_t)m * 8);
+    P.hq = (const double *)K.take((size_t)nzp * 8);
     x->hp = (double *)K.take((size_t)np * 8);
     x->erp = (double *)K.take((size_t)np * 8);
     x->ezp = (double *)K.take((size_t)nzz * 8);
@@ -856,7 +858,19 @@ int port_setup(pic_ctx *x, const pic_config *cfg) {
   P.nzp = nzp;
   P.m = m;
   P.np = np;
-  P.dzp = cfg->port_len / nzp;
+  // row heights: a geometric progression of ratio port_grade from the
+  // junction down (0 or 1: uniform), summing to port_len
+  std::vector<double> hq(nzp);
+  {
+    const double gr = cfg->port_grade == 0.0 ? 1.0 : cfg->port_grade;
+    if (gr == 1.0) {
+      for (int q = 0; q < nzp; ++q) hq[q] = cfg->port_len / nzp;
+    } else {
+      const double top = cfg->port_len * (gr - 1.0) / (pow(gr, (double)nzp) - 1.0);
+      for (int q = 0; q < nzp; ++q) hq[q] = top * pow(gr, (double)(nzp - 1 - q));
+    }
+  }
+  P.htop = hq[nzp - 1];
   P.erq = cfg->eps_port;
   P.eta = sqrt(x->mu / (cfg->eps_port * x->eps));
   P.lnr = log(g_rnode(G, nr) / g_rnode(G, ip));
@@ -867,7 +881,7 @@ int port_setup(pic_ctx *x, const pic_config *cfg) {
   P.erp1 = x->erp2;
   P.ezp1 = x->ezp2;
   const double dt = cfg->dt, hdt2 = 0.5 * dt * dt, eps = x->eps, mu = x->mu;
-  const double dzp = P.dzp, erq = P.erq;
+  const double erq = P.erq;
   // the port block (mass, the E_r edges between its rows, its interior E_z
   // edges, Mur's term at the end), lower band of width nzp
   const int bw = nzp;
@@ -876,9 +890,9 @@ int port_setup(pic_ctx *x, const pic_config *cfg) {
   for (int k = 0; k < m; ++k) {
     const int i = ip + k;
     const double sv = kTwoPi * g_rcentre(G, i), L = g_width(G, i);
-    for (int q = 0; q < nzp; ++q) band(k * nzp + q, k * nzp + q) += 2.0 * mu * sv * L * dzp;
+    for (int q = 0; q < nzp; ++q) band(k * nzp + q, k * nzp + q) += 2.0 * mu * sv * L * hq[q];
     for (int q = 1; q < nzp; ++q) {
-      const double w = hdt2 * (L / (eps * erq * sv * dzp)) * sv * sv;
+      const double w = hdt2 * (L / (eps * erq * sv * (0.5 * (hq[q - 1] + hq[q])))) * sv * sv;
       const int lo = k * nzp + q - 1, hi = k * nzp + q;
       band(lo, lo) += w;
       band(hi, hi) += w;
@@ -889,8 +903,8 @@ int port_setup(pic_ctx *x, const pic_config *cfg) {
   for (int k = 1; k < m; ++k) {
     const int i = ip + k;
     const double sr = kTwoPi * g_rcentre(G, i), sl = kTwoPi * g_rcentre(G, i - 1);
-    const double W = dzp / (eps * erq * g_area_z(G, i));
     for (int q = 0; q < nzp; ++q) {
+      const double W = hq[q] / (eps * erq * g_area_z(G, i));
       const int cr = k * nzp + q, cl = (k - 1) * nzp + q;
       band(cr, cr) += hdt2 * W * sr * sr;
       band(cl, cl) += hdt2 * W * sl * sl;
@@ -953,7 +967,7 @@ int port_setup(pic_ctx *x, const pic_config *cfg) {
   for (int e = 0; e < m; ++e) {
     const int i = ip + e;
     const double sv = kTwoPi * g_rcentre(G, i), L = g_width(G, i);
-    const double dint = eps * sv * 0.5 * (erq * dzp + G.dz);
+    const double dint = eps * sv * 0.5 * (erq * P.htop + G.dz);
     const double w = hdt2 * (L / dint) * sv * sv;
     for (int f = 0; f < m; ++f)
       cap[(size_t)e * m + f] = (e == f ? 1.0 / w : 0.0) + h0of(zr.data() + (size_t)f * nh, i) +
@@ -989,6 +1003,8 @@ int port_setup(pic_ctx *x, const pic_config *cfg) {
   }
   const size_t nzz = (size_t)(m + 1) * nzp;
   ce = cudaMemcpyAsync((void *)P.Binv, Binv.data(), Binv.size() * 8, cudaMemcpyHostToDevice, x->s);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync((void *)P.hq, hq.data(), (size_t)nzp * 8, cudaMemcpyHostToDevice, x->s);
   if (ce == cudaSuccess)
     ce = cudaMemcpyAsync((void *)P.ZP, zp.data(), zp.size() * 8, cudaMemcpyHostToDevice, x->s);
   if (ce == cudaSuccess)

@@ -163,7 +163,8 @@ struct Circuit {
 };
 
 // Axial dielectric port below the powered electrode (PIC_FEED_AXIAL): m = nr -
-// ip columns of nzp cells of height dzp, relative permittivity erq, Mur's
+// ip columns of nzp rows of cells, of heights hq[q] (q = 0 at the port's end;
+// uniform, or graded from the junction down), relative permittivity erq, Mur's
 // condition at the end with the incoming wave of half the electrode potential.
 // The H system of reactor and port is B + U W U^T: B = the reactor's separable
 // operator and the port block (its dense inverse Binv), U W U^T the m interface
@@ -173,7 +174,8 @@ struct Circuit {
 // Cinv = (W^{-1} + U^T Z)^{-1}.
 struct PortOp {
   int on, ip, nzp, m, np;
-  double dzp, erq, eta, lnr;
+  double htop, erq, eta, lnr;  // htop = hq[nzp - 1], the row at the junction
+  const double *hq;            // nzp row heights [m]
   const double *Binv;  // np x np, row-major
   const double *ZR;    // m blocks of the reactor hhalf layout
   const double *ZP;    // m x np

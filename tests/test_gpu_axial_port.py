@@ -47,12 +47,14 @@ def close(a, b, tol=1e-10):
     return np.max(np.abs(a - b)) <= tol * max(np.max(np.abs(b)), 1e-300)
 
 
-@pytest.mark.parametrize("nr,nz,ip,nzp", [(16, 12, 10, 6), (20, 20, 13, 8), (18, 15, 11, 5)],
-                         ids=["fft", "split", "dense"])
-def test_port_field_solve_matches_oracle(nr, nz, ip, nzp):
-    pic, cfg = make(nr, nz, ip, nzp)
+@pytest.mark.parametrize("nr,nz,ip,nzp,grade", [(16, 12, 10, 6, 1.0), (20, 20, 13, 8, 1.0),
+                                                (18, 15, 11, 5, 1.0), (16, 12, 10, 9, 1.3)],
+                         ids=["fft", "split", "dense", "graded"])
+def test_port_field_solve_matches_oracle(nr, nz, ip, nzp, grade):
+    pic, cfg = make(nr, nz, ip, nzp, port_grade=grade)
     g = O.Grid(nr, nz, cfg["R"], cfg["L"])
-    S = O.PortSolver(g, cfg["dt"], ip, nzp, cfg["port_len"] / nzp, cfg["eps_port"])
+    S = O.PortSolver(g, cfg["dt"], ip, nzp, cfg["port_len"] / nzp, cfg["eps_port"],
+                     heights=O.port_heights(nzp, cfg["port_len"], grade))
     rng = np.random.default_rng(nr + nz)
     er, ez, h = rng.normal(size=g.n_er) * 1e3, rng.normal(size=g.n_ez) * 1e3, rng.normal(size=nr * nz)
     er.reshape(nr, nz + 1)[:, nz] = 0.0
@@ -168,8 +170,9 @@ def test_discharge_energy_and_gauss():
     assert np.max(np.abs(gauss_interior() - G0)) <= 1e-9 * qs
 
 
-@pytest.mark.parametrize("cblock", [0.0, 1e-11], ids=["driven", "capacitor"])
-def test_full_steps_with_the_port_match_the_oracle(cblock):
+@pytest.mark.parametrize("cblock,grade", [(0.0, 1.0), (1e-11, 1.0), (0.0, 1.4)],
+                         ids=["driven", "capacitor", "graded"])
+def test_full_steps_with_the_port_match_the_oracle(cblock, grade):
     """Whole steps (Picard iteration of push, deposit and the port's field
     solve, commit, sort) of a small discharge fed through the axial port,
     against the oracle's steps with the same port: same iteration counts,
@@ -179,13 +182,14 @@ def test_full_steps_with_the_port_match_the_oracle(cblock):
     M = P()
     nr, nz, ip, nzp, n = 24, 32, 16, 10, 30000
     pic, cfg = make(nr, nz, ip, nzp, Lp=0.04, dt=5e-11, freq=100e6, volt=200.0, mcc_on=0,
-                    np_init=n, capacity_factor=1.5, picard_tol=1e-10, cblock=cblock)
+                    np_init=n, capacity_factor=1.5, picard_tol=1e-10, cblock=cblock,
+                    port_grade=grade)
     g = O.Grid(nr, nz, cfg["R"], cfg["L"])
     e, i = O.load(g, n, 1e15, 6.0, 0.026, 23)
     pic.set_state([e, i])
     sim = O.Sim(g, cfg["dt"], freq=cfg["freq"], volt=cfg["volt"], tol=cfg["picard_tol"],
                 kmax=cfg["picard_max"], species=[e, i], cap=int(n * 1.5), cblock=cblock,
-                port=(ip, nzp, cfg["port_len"], cfg["eps_port"]))
+                port=(ip, nzp, cfg["port_len"], cfg["eps_port"], grade))
     for step in range(3):
         rc, st = pic.step(1)
         rco, sto = sim.step()
