@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(32) k_push_promoted32(PushLaunchT<float> L) {
   G.q = L.q; G.m = L.m; G.qf = L.q; G.ir = L.ir; G.iz = L.iz; G.write = L.write; G.p = L.p;
   G.oop = L.oop; G.dst = L.dst; G.hist = L.hist;
   G.wall_z0 = L.wall_z0; G.wall_zl = L.wall_zl; G.wall_r = L.wall_r; G.ke_lost = L.ke_lost;
-  Tally tl = {0, 0, 0, 0, 0, 0};
+  Tally tl = {0, 0, 0, 0, 0, 0, 0};
   // consecutive entries go to different blocks (the list is short: this
   // spreads it over the SMs)
   const long long stride = (long long)gridDim.x * blockDim.x;

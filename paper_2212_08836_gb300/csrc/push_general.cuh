@@ -518,8 +518,69 @@ __device__ __forceinline__ bool landing_z_scalar(const SubT<T> &s, T X, T t0, T 
   return false;
 }
 
+// The same landing as one Newton iteration on the pair (tau, d): the cleared
+// in-cell radial equation of a sub-step of length tau with db = X,
+//   G(tau, d) = (d - K) r1^2 - (tau ut)^2 (2 rho + d) / 4 = 0,
+//   K = tau ur + tau^2/2 Ar,  r1 = rho + d,
+// (fast_solve's form with k1 = 1) and the z-equation
+//   F(tau, d) = tau uz + tau^2/2 (az0 + gaz (a + d/2)) - X = 0,
+// with their exact partial derivatives: one 2x2 step per iteration instead of
+// a scalar solve inside each step in tau, in plain arithmetic (the FP64 form's
+// integer-pipe products stay in the in-cell kernel).  Start: (t0, d0).  The
+// root is that of landing_z_scalar and of the 2x2 landing system
+// (landing_gen); false when the reduction does not apply (close to the axis)
+// or does not converge.
+template <typename T>
+__device__ __forceinline__ bool landing_z_joint(const SubT<T> &s, T X, T t0, T d0, T &ptau,
+                                                T &pda, unsigned &nit) {
+  typedef Num<T> N;
+  const T h = (T)0.5, q = (T)0.25, zero = (T)0;
+  if (!(s.rho > zero)) return false;
+  const T Ar = s.ar0 + s.gar * (s.b + h * X);
+  const T aza = s.az0 + s.gaz * s.a;
+  const T ut2 = s.ut * s.ut, r2 = s.rho + s.rho;
+  T tau = t0, d = d0, pct = zero, pcd = zero;
+  if (!(s.rho + d > zero)) d = zero;
+  for (int it = 0; it < kNewtonMaxGen; ++it) {
+    if (!(tau > zero) || !(fabs(tau * s.ut) < q * s.rho)) return false;
+    const T r1 = s.rho + d;
+    const T R2 = r1 * r1, t2 = tau * tau;
+    const T qut2 = q * t2 * ut2;
+    const T e = d - (tau * s.ur + h * t2 * Ar);
+    const T G = e * R2 - qut2 * (r2 + d);
+    const T Gd = R2 + (e + e) * r1 - qut2;
+    const T Gt = -(s.ur + tau * Ar) * R2 - h * tau * ut2 * (r2 + d);
+    const T Az = aza + h * s.gaz * d;
+    const T F = tau * s.uz + h * t2 * Az - X;
+    const T Ft = s.uz + tau * Az;
+    const T Fd = q * t2 * s.gaz;
+    const T det = Gd * Ft - Gt * Fd;
+    nit++;
+    if (!(det != zero) || !N::finite(det)) return false;
+    const T idet = N::rcp(det);
+    T nd = d + (Gt * F - G * Ft) * idet;
+    const T ntau = tau + (Fd * G - Gd * F) * idet;
+    if (s.rho + nd <= zero) nd = h * (d - s.rho);
+    const T cd = N::absb(nd - d), ct = N::absb(ntau - tau);
+    d = nd;
+    tau = ntau;
+    if (!N::finite(d) || !N::finite(tau)) return false;
+    const T td = tol_r<T>(s.rho + d, d), tt = tol_x<T>(tau);
+    if ((N::le(cd, td) && N::le(ct, tt)) || (contracted(cd, pcd, td) && contracted(ct, pct, tt))) {
+      if (!(tau > zero) || !(fabs(tau * s.ut) < q * s.rho)) return false;
+      ptau = tau;
+      pda = d;
+      return true;
+    }
+    pcd = cd;
+    pct = ct;
+  }
+  return false;
+}
+
 struct Tally {
   unsigned err, abs, sub, fb, newton, snewton;  // snewton: scalar Newton iterations
+  unsigned jnewton;                              // joint (tau, d) landing iterations
 };
 
 // T: the arithmetic type of the path; S: the scalar type of the particle store
@@ -774,7 +835,7 @@ __device__ __forceinline__ void deposit_sub(const GenArgs<T, S> &L, int ic, int 
 // A crosser without B_z whose converged whole-step trial (tr_da, tr_db) keeps
 // its radial offset inside the cell and leaves it through one z-face (cells
 // are flat in z: most crossings), as straight-line code: the landing on that
-// face (landing_z_scalar), the transition to the next cell and the rest of the
+// face (landing_z_joint), the transition to the next cell and the rest of the
 // step there through the in-cell scalar solve, so that a warp of such crossers
 // runs converged.  The steps and their arithmetic are those of the sub-step
 // loop for it; at any other turn (a landing that fails or leaves the cell, a
@@ -810,9 +871,11 @@ __device__ void push_zcross(const GenArgs<T, S> &L, long long p, int c0, T a, T 
   const T face = b + tr_db > one ? one : zero;
   const T X = face - b;
   const T g0 = (T)first_crossing<float>((float)X, (float)tr_db, (float)uz, 1.f);
+  // the radial offset at g0 on the quadratic path through the trial's end
+  const T d0 = g0 * (ur + g0 * (tr_da - ur));
   T tt = zero, da = zero;
   if (!N::in01(a) || !N::in01(b) || !(g0 > zero) ||
-      !landing_z_scalar<T>(s, X, g0, tt, da, Tl.snewton) || !(tt > zero) || tt > one ||
+      !landing_z_joint<T>(s, X, g0, d0, tt, da, Tl.jnewton) || !(tt > zero) || tt > one ||
       !(a + da >= zero && a + da <= one)) {
     push_sub<T, false, S>(L, p, ic, jc, a, b, ur, ut, uz, w, tr_da, tr_db, one, 0, 0, Tl);
     return;
@@ -884,8 +947,9 @@ __device__ void push_zcross(const GenArgs<T, S> &L, long long p, int c0, T a, T 
 }
 
 // algorithmic operation counts of the general path: 75 per Newton iteration
-// (one residual/Jacobian evaluation and update), 93 per accepted sub-step
-constexpr unsigned kOpGenNewton = 75, kOpGenAccept = 93;
+// (one residual/Jacobian evaluation and update), 93 per accepted sub-step, 60
+// per joint landing iteration (landing_z_joint)
+constexpr unsigned kOpGenNewton = 75, kOpGenAccept = 93, kOpJointNewton = 60;
 
 // counters[0..4] += errors, absorbed, accepted sub-steps, fallbacks, operations;
 // per-thread counts are small, so the warp sums use the 32-bit redux unit
@@ -897,7 +961,7 @@ __device__ __forceinline__ void flush_tally(unsigned long long *counters, const 
            e2 = __reduce_add_sync(full, T.sub), e3 = __reduce_add_sync(full, T.fb),
            e4 = __reduce_add_sync(full, T.newton),
            e5 = __reduce_add_sync(full, fast_newton + T.snewton),
-           e6 = __reduce_add_sync(full, fast_acc);
+           e6 = __reduce_add_sync(full, fast_acc), e7 = __reduce_add_sync(full, T.jnewton);
   if (lane == 0) {
     if (e0) atomicAdd(&counters[0], (unsigned long long)e0);
     if (e1) atomicAdd(&counters[1], (unsigned long long)e1);
@@ -906,7 +970,8 @@ __device__ __forceinline__ void flush_tally(unsigned long long *counters, const 
     unsigned long long fl = (unsigned long long)kOpGenNewton * e4 +
                             (unsigned long long)kOpGenAccept * e2 +
                             (unsigned long long)kOpFastNewton * e5 +
-                            (unsigned long long)kOpFastAccept * e6;
+                            (unsigned long long)kOpFastAccept * e6 +
+                            (unsigned long long)kOpJointNewton * e7;
     if (fl) atomicAdd(&counters[4], fl);
   }
 }

@@ -306,7 +306,7 @@ __device__ __forceinline__ void push_fast_body(const PushLaunchT<T> &L, int bid,
     L.qblock[bid] = s_qn[0];
     L.qblock[L.qgrid + bid] = s_qn[1];
   }
-  Tally T0 = {0, 0, 0, 0, 0, 0};
+  Tally T0 = {0, 0, 0, 0, 0, 0, 0};
   flush_tally(L.counters, T0, lane, n_newton, n_acc);
 }
 
@@ -326,7 +326,7 @@ __device__ __forceinline__ void push_general_body(const PushLaunchT<T> &L, int b
   G.q = L.q; G.m = L.m; G.qf = L.qf; G.ir = L.ir; G.iz = L.iz; G.write = L.write; G.p = L.p;
   G.oop = L.oop; G.dst = L.dst; G.hist = L.hist;
   G.wall_z0 = L.wall_z0; G.wall_zl = L.wall_zl; G.wall_r = L.wall_r; G.ke_lost = L.ke_lost;
-  Tally tl = {0, 0, 0, 0, 0, 0};
+  Tally tl = {0, 0, 0, 0, 0, 0, 0};
   const long long gstride = (long long)nblk * blockDim.x;
   const long long gtid = (long long)bid * blockDim.x + threadIdx.x;
   if (L.queue) {
@@ -382,11 +382,17 @@ __device__ __forceinline__ void push_general_body(const PushLaunchT<T> &L, int b
         }
       }
     } else {
+      // FP64 form: the start state from the store; z-face crossers (the front
+      // kind) through the straight-line routine as well
       for (long long q = gtid; q < total; q += gstride) {
         long long k = entry(q);
         long long p = L.queue[k];
-        push_general<T, kB>(G, p, L.p.cell[p], L.p.a[p], L.p.b[p], L.p.vr[p], L.p.vt[p],
-                            L.p.vz[p], L.p.w[p], L.q_da[k], L.q_db[k], tl);
+        if (!kB && q < total_f)
+          push_zcross<T>(G, p, L.p.cell[p], L.p.a[p], L.p.b[p], L.p.vr[p], L.p.vt[p],
+                         L.p.vz[p], L.p.w[p], L.q_da[k], L.q_db[k], tl);
+        else
+          push_general<T, kB>(G, p, L.p.cell[p], L.p.a[p], L.p.b[p], L.p.vr[p], L.p.vt[p],
+                              L.p.vz[p], L.p.w[p], L.q_da[k], L.q_db[k], tl);
       }
     }
   } else {
