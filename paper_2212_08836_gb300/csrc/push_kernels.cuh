@@ -240,7 +240,8 @@ __device__ __forceinline__ void push_fast_body(const PushLaunchT<T> &L, int bid,
           // may need FP64: the centrifugal term grows like 1/r)
           if (sizeof(T) == 4 && acc && ic < kPromoteRows)
             acc = !((T)64 * (rho + d) * (rho + d) < rho * rho);
-          zcross = Num<T>::in01(a1) && (b1 < zero || b1 > one);
+          // the trial crosses one z-face (two or more: the loop)
+          zcross = Num<T>::in01(a1) && ((b1 < zero && b1 > -one) || (b1 > one && b1 < (T)2));
           if (acc) {
             n_acc++;
             const T qw = N::mul(L.qf, w);
