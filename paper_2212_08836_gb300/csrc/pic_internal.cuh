@@ -267,7 +267,7 @@ struct PushLaunchT {
   unsigned long long *hist;  // accepted sub-steps per particle, 16 bins (nullptr: off)
   // work queue of the general path (queue == nullptr: all particles).  Block b
   // of the fast kernel appends the particles whose whole-step trial leaves the
-  // cell through a z-face only to entries [b*qseg, b*qseg + qblock[b]) and the
+  // cell through one z-face only to entries [b*qseg, b*qseg + qblock[b]) and the
   // rest from the back of its segment, qblock[qgrid + b] of them, so that the
   // general kernel's warps take those two kinds one after the other.
   int *queue, *qblock;

@@ -175,7 +175,7 @@ __device__ __forceinline__ void push_fast_body(const PushLaunchT<T> &L, int bid,
   const T zero = (T)0, one = (T)1, h = (T)0.5, q = (T)0.25;
   const long long stride = (long long)nblk * blockDim.x;
   unsigned n_newton = 0, n_acc = 0;
-  // entries this block appended to its queue segment: [0] z-face-only
+  // entries this block appended to its queue segment: [0] single z-face
   // crossings of the trial from the front, [1] the rest from the back
   __shared__ int s_qn[2];
   if (threadIdx.x < 2) s_qn[threadIdx.x] = 0;
@@ -279,7 +279,7 @@ __device__ __forceinline__ void push_fast_body(const PushLaunchT<T> &L, int bid,
     }
     // queue the rest for the general path (warp-aggregated append to the
     // block's segment; the shared-memory counter keeps it off global atomics),
-    // in two kinds: the crossings of the trial through a z-face only from the
+    // in two kinds: the crossings of the trial through one z-face only from the
     // front, the rest from the back, so that the general kernel's warps take
     // one sub-step sequence at a time.  FP32 entries carry the start state
     // (written coalesced here, read coalesced there: no scattered re-read)
@@ -331,7 +331,7 @@ __device__ __forceinline__ void push_general_body(const PushLaunchT<T> &L, int b
   const long long gstride = (long long)nblk * blockDim.x;
   const long long gtid = (long long)bid * blockDim.x + threadIdx.x;
   if (L.queue) {
-    // the z-face-only crossings first, then the rest (uniform warps)
+    // the single z-face crossings first, then the rest (uniform warps)
     __shared__ int s_pre[kMaxFastBlocks + 1], s_preb[kMaxFastBlocks + 1];
     const int total_f = seg_prefix(L.qblock, L.qgrid, s_pre);
     const int total = total_f + seg_prefix(L.qblock + L.qgrid, L.qgrid, s_preb);
