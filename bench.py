@@ -674,6 +674,22 @@ def run_ours(args):
                                  "peak_kind": "FP32: 128 lanes x 152 SMs x 2 x max SM clock"}}}
         wall["mixed"] = tm / args.steps * 1e-3 * steps_per_cycle
         line["picard_loop"]["mixed"] = rm["picard_loop"]
+    # ---- the paper's feed: the axial dielectric port below a 0.2 m electrode
+    # (quartz, 16 rows graded over 6.5 cm) with the blocking capacitor, FP64
+    if "port" in forms:
+        cfgp = P.large_reactor(seed=replica_seed(1, rank), feed=P.PIC_FEED_AXIAL, port_rin=171,
+                               port_cells=16, port_len=0.065, eps_port=3.8, port_grade=1.15,
+                               cblock=1e-9)
+        if args.np:
+            cfgp["np_init"] = args.np
+        rp = measure(P, torch, dev, cfgp, args, dist, D, False, False, local)
+        tp, totp = maxsum(rp["t_ms"], rp["pushes"])
+        line["axial_port_form"] = {
+            "value": totp / (tp * 1e-3), "unit": UNIT, "ms_per_step": tp / args.steps,
+            "picard_iters": rp["iters"], "gpu_launches": rp["launches"],
+            "config": "256x384 reactor, electrode r_p = 0.2 m fed through the axial port "
+                      "(R = 0.3 m, quartz, 16 rows graded 1.15 over 6.5 cm), blocking "
+                      "capacitor 1 nF, FP64, %d macro-particles/species" % cfgp["np_init"]}
     # ---- electrostatic field model (Eq. 8) on the same reactor, mixed form
     if "es" in forms:
         cfge = P.large_reactor(seed=replica_seed(1, rank), precision=P.PIC_MIXED, field_model=P.PIC_FIELD_ES)
@@ -757,9 +773,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--np", type=int, default=0, help="macro-particles per species (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--forms", default="plain,mixed,es,developed,ensemble",
+    ap.add_argument("--forms", default="plain,mixed,es,port,developed,ensemble",
                     help="comma list of plain (FP64), mixed (FP32 push), es (electrostatic "
-                         "model), guess (mixed form "
+                         "model), port (the axial port with the capacitor), guess (mixed form "
                          "with the learned Picard start), developed (the FP64 form after 5 RF "
                          "cycles) and ensemble (16 uneven discharges) to time")
     ap.add_argument("--guess-warmup", type=int, default=400)

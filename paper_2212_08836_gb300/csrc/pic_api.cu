@@ -1667,7 +1667,7 @@ int pic_field_solve(pic_ctx *x, const double *er0, const double *ez0, const doub
   F.cc = Circuit{};
   cudaError_t e = launch_field_solve(F, er0, ez0, h0, ir, iz, v0, v1, er1, ez1, h1, nullptr,
                                      nullptr, x->cnt, x->s);
-  x->launches += 5;
+  x->launches += F.port.on ? 10 : 5;
   if (e == cudaSuccess && src)
     e = cudaMemcpyAsync(src, &x->cnt->src, 8, cudaMemcpyDeviceToDevice, x->s);
   return cuda_rc(e);
@@ -1939,7 +1939,7 @@ int enqueue_post(pic_ctx *x) {
     if (launch_field_solve(x->F, x->er, x->ez, x->h, x->ir, x->iz, 0.0, 0.0, x->er2, x->ez2,
                            x->h2, x->er1, x->ez1, x->cnt, s) != cudaSuccess)
       return PIC_E_CUDA;
-    x->launches += 5;
+    x->launches += x->F.port.on ? 10 : 5;  // the axial port adds five kernels
   }
   // (a pass inside the device loop leaves the norms to its convergence test)
   if (!x->dl_capture &&
