@@ -7,8 +7,8 @@ the models must agree: the self-bias the capacitor builds, cycle by cycle, to
 3 % of the drive amplitude (measured: 1-2 V of a -70..-79 V bias), the
 electrode's RF amplitude to 2 %, and the electron and ion densities averaged
 over the last two cycles to 6 % along the axis over the electrode and 12 %
-across the radius at mid-gap (particle noise of 40k macro-particles per
-species; measured 2 % and 5 %).  The bias is a large negative one, set by the
+across the radius at mid-gap, off the axis node (particle noise of 40k
+macro-particles per species; measured 2 % and 5 %).  The bias is a large negative one, set by the
 area asymmetry: in the same discharge between equal plates (the side-gap
 feed) the start's transient bias decays to a fraction of it."""
 import numpy as np
@@ -42,7 +42,9 @@ def test_electrostatic_and_electromagnetic_self_bias_agree_at_13_56_mhz():
     mid = es["ne"].shape[1] // 2
     for k in ("ne", "ni"):
         assert rel(em[k][:ip].mean(axis=0), es[k][:ip].mean(axis=0)) <= 0.06, k
-        assert rel(em[k][:, mid], es[k][:, mid]) <= 0.12, k
+        # across the radius at mid-gap, off the axis node (its dual volume is a
+        # disc of radius dr/2: a handful of macro-particles, noise of tens of %)
+        assert rel(em[k][1:, mid], es[k][1:, mid]) <= 0.12, k
     # the same discharge between equal plates: the start's transient bias
     # decays and stays far below the asymmetric reactor's
     sym = LF.run("es", cycles=6, device=DEV, volt=V0, feed=PIC_FEED_GAP)
