@@ -46,15 +46,17 @@ def test_es_solve_matches_oracle(nr, nz):
     assert np.max(np.abs(ez.cpu().numpy() - ezo)) <= 1e-10 * scale
 
 
-@pytest.mark.parametrize("nr,nz,ip", [(8, 12, 5), (32, 64, 20), (37, 50, 30)])
-def test_es_port_solve_matches_oracle(nr, nz, ip):
+@pytest.mark.parametrize("nr,nz,ip,xa", [(8, 12, 5, 0), (32, 64, 20, 0), (37, 50, 30, 0),
+                                          (32, 64, 20, 3)],
+                         ids=["small", "fft", "dense", "mapped"])
+def test_es_port_solve_matches_oracle(nr, nz, ip, xa):
     """The electrostatic model's axial port (Sec. 2.2): the electrode disc, the
     port's opening at the coaxial line's potential and the grounded side wall
     as Dirichlet values of the same solve (three transform paths)."""
     M = P()
     cfg = M.small_reactor(nr=nr, nz=nz, np_init=100, field_model=M.PIC_FIELD_ES,
                           feed=M.PIC_FEED_AXIAL, port_rin=ip, port_cells=4, port_len=0.02,
-                          eps_port=3.8)
+                          eps_port=3.8, axis_cells=xa)
     pic = M.Pic(cfg, device=DEV)
     rng = np.random.default_rng(nr + nz + ip)
     Q = rng.normal(size=(nr + 1) * (nz + 1)) * 1e-13
@@ -62,7 +64,8 @@ def test_es_port_solve_matches_oracle(nr, nz, ip):
     ez = torch.zeros((nr + 1) * nz, dtype=torch.float64, device=DEV)
     pic.es_solve(torch.tensor(Q, device=DEV), -41.0, er, ez)
     torch.cuda.synchronize()
-    _, ero, ezo = ES.solve(nr, nz, cfg["R"] / nr, cfg["L"] / nz, Q, -41.0, port=ip)
+    _, ero, ezo = ES.solve(nr, nz, cfg["R"] / (nr + xa), cfg["L"] / nz, Q, -41.0, xa=xa,
+                           port=ip)
     scale = max(np.max(np.abs(ero)), np.max(np.abs(ezo)))
     assert np.max(np.abs(er.cpu().numpy() - ero)) <= 1e-10 * scale
     assert np.max(np.abs(ez.cpu().numpy() - ezo)) <= 1e-10 * scale

@@ -3,6 +3,7 @@ itself: the exact vacuum solution between the plates, Gauss's law through the
 C oracle's own discrete divergence, and the discrete energy identity
 W = 1/2 sum Q phi through the C oracle's field energy."""
 import numpy as np
+import pytest
 
 import oracle as O
 from oracle import es as ES
@@ -46,12 +47,14 @@ def test_energy_identity_through_the_c_oracle():
 # ---- the axial port of the electrostatic model (Sec. 2.2): the disc r <= r_p
 # powered, the port's opening at the coaxial line's potential, side wall grounded
 
-def test_port_solve_keeps_gauss_law_through_the_c_oracle():
+@pytest.mark.parametrize("xa", [0, 3])
+def test_port_solve_keeps_gauss_law_through_the_c_oracle(xa):
     nr, nz, dr, dz, R, L = grid(12, 10, 0.1, 0.03)
-    g = O.Grid(nr, nz, R, L)
+    dr = R / (nr + xa)
+    g = O.Grid(nr, nz, R, L, xa)
     rng = np.random.default_rng(4)
     Q = rng.normal(size=(nr + 1) * (nz + 1)) * 1e-12
-    phi, er, ez = ES.solve(nr, nz, dr, dz, Q, 55.0, port=7)
+    phi, er, ez = ES.solve(nr, nz, dr, dz, Q, 55.0, xa=xa, port=7)
     G = O.gauss_residual(g, er, ez, Q).reshape(nr + 1, nz + 1)
     assert np.max(np.abs(G[:nr, 1:nz])) <= 1e-10 * np.max(np.abs(Q))
 
