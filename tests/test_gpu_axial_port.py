@@ -47,12 +47,13 @@ def close(a, b, tol=1e-10):
     return np.max(np.abs(a - b)) <= tol * max(np.max(np.abs(b)), 1e-300)
 
 
-@pytest.mark.parametrize("nr,nz,ip,nzp,grade", [(16, 12, 10, 6, 1.0), (20, 20, 13, 8, 1.0),
-                                                (18, 15, 11, 5, 1.0), (16, 12, 10, 9, 1.3)],
-                         ids=["fft", "split", "dense", "graded"])
-def test_port_field_solve_matches_oracle(nr, nz, ip, nzp, grade):
-    pic, cfg = make(nr, nz, ip, nzp, port_grade=grade)
-    g = O.Grid(nr, nz, cfg["R"], cfg["L"])
+@pytest.mark.parametrize("nr,nz,ip,nzp,grade,xa", [(16, 12, 10, 6, 1.0, 0), (20, 20, 13, 8, 1.0, 0),
+                                                   (18, 15, 11, 5, 1.0, 0), (16, 12, 10, 9, 1.3, 0),
+                                                   (16, 12, 10, 6, 1.0, 2)],
+                         ids=["fft", "split", "dense", "graded", "mapped"])
+def test_port_field_solve_matches_oracle(nr, nz, ip, nzp, grade, xa):
+    pic, cfg = make(nr, nz, ip, nzp, port_grade=grade, axis_cells=xa)
+    g = O.Grid(nr, nz, cfg["R"], cfg["L"], xa)
     S = O.PortSolver(g, cfg["dt"], ip, nzp, cfg["port_len"] / nzp, cfg["eps_port"],
                      heights=O.port_heights(nzp, cfg["port_len"], grade))
     rng = np.random.default_rng(nr + nz)
